@@ -1,0 +1,175 @@
+"""Covariance-free EM (CoFEM) in FP64 on the CPU (oracle side; test infrastructure).
+
+Follows the paper's two algorithms step by step:
+
+Alg. 1 (CovarianceFreeEM)   for t = 1..T:
+    A <- beta Phi^T Phi + diag(alpha^(t))
+    draw p_1..p_K Rademacher (fresh each t)
+    B <- [beta Phi^T y | p_1 .. p_K]         (mu in column 0: see "readings")
+    X <- LinearSolver(A, B)
+    s_j <- (1/K) sum_k p_kj x_kj            (Eq. diag-estimate)
+    if t < T: alpha_j^(t+1) <- 1 / (mu_j^2 + s_j)
+    return alpha^(T), mu, s
+
+Alg. 2 (ParallelConjGradient) with the diagonal preconditioner
+M = diag(beta theta + alpha) of Sec. III-C.
+
+Readings of the paper taken here (each a choice where the text is silent,
+garbled or at odds with itself):
+ 1. Alg. 2 initialises P <- B and updates P <- R + P H.  With M != I that is not
+    preconditioned CG, while the text defines W = M^-1 R and rho = R^T W.  We use
+    P_0 = W_0 = M^-1 B and P <- W + P H (standard PCG, Hestenes-Stiefel /
+    Shewchuk, both cited for CG).  For M = I both readings agree.
+ 2. The pi_q sum is printed with index d; it is the row index j.
+ 3. Stopping: default is per column, delta_q = ||r_q|| / ||b_q|| <= tol with
+    that column then frozen ("masked"); conv="frobenius" reproduces the
+    printed global test ||R||_F / ||B||_F <= tol.  A column with ||b_q|| = 0 has
+    x_q = 0 and starts converged.
+ 4. The test uses the unpreconditioned residual after the X, R update and
+    before W.  cg_iters[t] = number of operator applications in EM iteration t
+    (the largest over columns), residual-replacement applications excluded.
+ 5. X starts at 0 in every EM iteration (cold start, as printed).
+ 6. b = beta Phi^T y is computed once per fit (it does not depend on t).
+ 7. Probes: Philox4x64-10 rule of oracle.philox, fresh for every t.
+ 8. T E-steps and T-1 M-steps; the returned alpha is alpha^(T).
+ 9. theta: Jacobi (theta_j = ||phi_j||^2) by default, or theta = 1 ("one").
+10. The second moment mu_j^2 + s_j can be <= 0 for finite K (s is unbiased,
+    not positive); alpha_j = 1 / max(mu_j^2 + s_j, 1/alpha_max), alpha_max = 1e12.
+11. Residual replacement (precision form, rr_period > 0): when the iteration
+    count u is a multiple of rr_period, right after the X, R update the still
+    active columns take R <- B - A X before the stopping test, then W, rho and
+    P continue from that R.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .operators import apply_A
+from .philox import rademacher_probes
+
+FLAG_CG_NOT_CONVERGED = 1
+FLAG_ALPHA_CLAMPED = 2
+FLAG_BREAKDOWN = 4
+
+
+def diag_estimate(P, X):
+    """s_j = (1/K) sum_k p_kj x_kj for Rademacher probes (Eq. diag-estimate).
+    P, X: (D, K) arrays whose column k is p_k and x_k = Sigma p_k."""
+    K = P.shape[1]
+    return np.sum(P * X, axis=1) / K
+
+
+def diag_estimate_general(P, X):
+    """The general rule of Prop. 1 (Eq. single-diag-estimator):
+    s_j = sum_k p_kj x_kj / sum_k p_kj^2."""
+    return np.sum(P * X, axis=1) / np.sum(P * P, axis=1)
+
+
+def pcg(apply_a, B, minv, tol, maxit, conv="per_column", rr_period=0, history=None):
+    """Alg. 2 (ParallelConjGradient) on the D x Q block B with M^-1 = diag(minv).
+
+    Returns (X, iters, flags).  `history`, if a list, receives a copy of X after
+    every iteration (for convergence-bound tests)."""
+    B = np.asarray(B, dtype=np.float64)
+    D, Q = B.shape
+    minv = np.asarray(minv, dtype=np.float64)[:, None]
+    X = np.zeros((D, Q))
+    R = B.copy()
+    W = minv * R
+    P = W.copy()
+    rho = np.sum(R * W, axis=0)
+    bnorm = np.linalg.norm(B, axis=0)
+    bnorm_f = np.linalg.norm(B)
+    active = bnorm > 0.0
+    flags = 0
+    u = 0
+    while u < maxit and active.any():
+        Psi = apply_a(P)                                   # Apply matrix
+        pi = np.sum(P * Psi, axis=0)
+        a = active
+        if np.any(~(pi[a] > 0.0)) or not np.all(np.isfinite(pi[a])):
+            flags |= FLAG_BREAKDOWN
+            bad = a & ~(pi > 0.0)
+            active = active & ~bad
+            a = active
+        gamma = np.zeros(Q)
+        gamma[a] = rho[a] / pi[a]
+        X[:, a] += P[:, a] * gamma[a]
+        R[:, a] -= Psi[:, a] * gamma[a]
+        u += 1
+        if rr_period > 0 and u % rr_period == 0:
+            R[:, a] = (B - apply_a(X))[:, a]               # residual replacement
+        if conv == "per_column":
+            delta = np.full(Q, np.inf)
+            delta[a] = np.linalg.norm(R[:, a], axis=0) / bnorm[a]
+            active = active & ~(delta <= tol)
+        elif conv == "frobenius":
+            if np.linalg.norm(R) / bnorm_f <= tol:
+                active = np.zeros(Q, dtype=bool)
+        else:
+            raise ValueError(conv)
+        a = active
+        W = minv * R                                       # Apply preconditioner
+        rho_new = np.sum(R * W, axis=0)
+        eta = np.zeros(Q)
+        eta[a] = rho_new[a] / rho[a]
+        P[:, a] = W[:, a] + P[:, a] * eta[a]
+        rho[a] = rho_new[a]
+        if history is not None:
+            history.append(X.copy())
+    if active.any():
+        flags |= FLAG_CG_NOT_CONVERGED
+    return X, u, flags
+
+
+def cofem(op, y, beta, K, T, cg_tol, cg_maxit, seed, alpha0=None, precond="jacobi",
+          alpha_max=1e12, conv="per_column", rr_period=0, probe_fn=None,
+          solver="pcg", return_x=False):
+    """Alg. 1 (CovarianceFreeEM) with Alg. 2 as the linear solver.
+
+    op        oracle.operators.DenseOperator / ToeplitzOperator
+    probe_fn  optional callable (t, K, D) -> (K, D) probe block; default is the
+              Philox Rademacher rule with `seed`.
+    solver    "pcg" (Alg. 2) or "direct" (exact dense solve, small D only).
+    Returns dict(alpha, mu, s, cg_iters, flags[, X]).
+    """
+    D = op.D
+    yv = np.asarray(y, dtype=np.float64)
+    b = beta * op.apply_t(yv)                              # computed once per fit
+    theta = op.column_sq_norms() if precond == "jacobi" else np.ones(D)
+    alpha = np.ones(D) if alpha0 is None else np.asarray(alpha0, dtype=np.float64).copy()
+    cg_iters = np.zeros(T, dtype=np.int64)
+    flags = 0
+    mu = s = X = None
+    for t in range(1, T + 1):
+        probes = (rademacher_probes(seed, t, K, D) if probe_fn is None
+                  else np.asarray(probe_fn(t, K, D), dtype=np.float64))
+        B = np.empty((D, K + 1))
+        B[:, 0] = b
+        B[:, 1:] = probes.T
+        minv = 1.0 / (beta * theta + alpha)
+
+        def apply_a(V, alpha=alpha):
+            return apply_A(op, V, alpha, beta)
+
+        if solver == "pcg":
+            X, u, f = pcg(apply_a, B, minv, cg_tol, cg_maxit, conv=conv, rr_period=rr_period)
+            cg_iters[t - 1] = u
+            flags |= f
+        elif solver == "direct":
+            Phi = op.dense()
+            A = beta * (Phi.T @ Phi) + np.diag(alpha)
+            X = np.linalg.solve(A, B)
+        else:
+            raise ValueError(solver)
+        mu = X[:, 0].copy()
+        s = diag_estimate(B[:, 1:], X[:, 1:])
+        if t < T:
+            m2 = mu ** 2 + s
+            if np.any(m2 < 1.0 / alpha_max):
+                flags |= FLAG_ALPHA_CLAMPED
+            alpha = 1.0 / np.maximum(m2, 1.0 / alpha_max)
+    out = dict(alpha=alpha, mu=mu, s=s, cg_iters=cg_iters, flags=flags)
+    if return_x:
+        out["X"] = X
+    return out

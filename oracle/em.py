@@ -1,0 +1,87 @@
+"""Classic EM for sparse Bayesian learning with an explicit covariance
+(oracle side; test infrastructure, FP64, CPU).
+
+Model (Sec. II-A, Eq. model): z ~ N(0, diag(alpha)^-1), y | z ~ N(Phi z, beta^-1 I).
+E-step (Sec. II-B, Eq. estep-params):
+    Sigma = (beta Phi^T Phi + diag(alpha))^-1,   mu = beta Sigma Phi^T y.
+M-step (Eq. mstep): alpha_j <- 1 / (mu_j^2 + Sigma_jj).
+Objective (Eq. mle2): log p(y | alpha) = log N(y; 0, C_y),
+    C_y = beta^-1 I + Phi diag(alpha)^-1 Phi^T  (standard Gaussian marginal).
+
+Two independent E-step routes:
+* explicit : Cholesky of the D x D matrix A = Sigma^-1.
+* woodbury : the IRLS form of Sec. II-C (Eq. woodbury) with an N x N inverse.
+  The printed form omits beta; with C = diag(alpha)^-1 the identity reads
+      Sigma = C - C Phi^T (beta^-1 I + Phi C Phi^T)^-1 Phi C.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+
+def estep_explicit(Phi, y, beta, alpha):
+    """(mu, Sigma) by a D x D Cholesky factorisation of A = beta Phi^T Phi + diag(alpha)."""
+    Phi = np.asarray(Phi, dtype=np.float64)
+    A = beta * (Phi.T @ Phi) + np.diag(np.asarray(alpha, dtype=np.float64))
+    c = sla.cho_factor(A, lower=True)
+    Sigma = sla.cho_solve(c, np.eye(A.shape[0]))
+    mu = beta * (Sigma @ (Phi.T @ np.asarray(y, dtype=np.float64)))
+    return mu, Sigma
+
+
+def estep_woodbury(Phi, y, beta, alpha):
+    """(mu, diag Sigma) through the N x N Woodbury form (beta restored)."""
+    Phi = np.asarray(Phi, dtype=np.float64)
+    c = 1.0 / np.asarray(alpha, dtype=np.float64)           # C = diag(c)
+    PhiC = Phi * c[None, :]                                   # Phi C
+    S = np.eye(Phi.shape[0]) / beta + PhiC @ Phi.T           # beta^-1 I + Phi C Phi^T
+    cf = sla.cho_factor(S, lower=True)
+    G = sla.cho_solve(cf, PhiC)                               # S^-1 Phi C
+    diag = c - np.einsum("ij,ij->j", PhiC, G)                 # diag(C - C Phi^T S^-1 Phi C)
+    Phity = Phi.T @ np.asarray(y, dtype=np.float64)
+    # Sigma Phi^T y = C Phi^T y - C Phi^T S^-1 Phi C Phi^T y
+    mu = beta * (c * Phity - PhiC.T @ sla.cho_solve(cf, PhiC @ Phity))
+    return mu, diag
+
+
+def log_marginal_likelihood(Phi, y, beta, alpha):
+    """log p(y | alpha) of Eq. mle2 for the Gaussian model (closed form)."""
+    Phi = np.asarray(Phi, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    N = Phi.shape[0]
+    Cy = np.eye(N) / beta + (Phi / np.asarray(alpha, dtype=np.float64)[None, :]) @ Phi.T
+    cf = sla.cho_factor(Cy, lower=True)
+    logdet = 2.0 * np.sum(np.log(np.diag(cf[0])))
+    quad = float(y @ sla.cho_solve(cf, y))
+    return -0.5 * (N * np.log(2.0 * np.pi) + logdet + quad)
+
+
+def mstep(mu, diag_sigma, alpha_max=np.inf):
+    """alpha_j <- 1 / (mu_j^2 + Sigma_jj) (Eq. mstep), with the second moment
+    floored at 1/alpha_max (a no-op for exact EM, where it is >= Sigma_jj > 0)."""
+    m2 = np.asarray(mu) ** 2 + np.asarray(diag_sigma)
+    return 1.0 / np.maximum(m2, 1.0 / alpha_max)
+
+
+def em(Phi, y, beta, T, alpha0=None, estep="explicit", alpha_max=np.inf, track_loglik=False):
+    """T iterations of classic EM, laid out like Alg. 1 (T E-steps, T-1
+    M-steps; returns alpha^(T) with the mu, diag Sigma of the last E-step)."""
+    Phi = np.asarray(Phi, dtype=np.float64)
+    D = Phi.shape[1]
+    alpha = np.ones(D) if alpha0 is None else np.asarray(alpha0, dtype=np.float64).copy()
+    loglik = []
+    mu = dsig = None
+    for t in range(1, T + 1):
+        if estep == "explicit":
+            mu, Sigma = estep_explicit(Phi, y, beta, alpha)
+            dsig = np.diag(Sigma).copy()
+        elif estep == "woodbury":
+            mu, dsig = estep_woodbury(Phi, y, beta, alpha)
+        else:
+            raise ValueError(estep)
+        if track_loglik:
+            loglik.append(log_marginal_likelihood(Phi, y, beta, alpha))
+        if t < T:
+            alpha = mstep(mu, dsig, alpha_max)
+    return dict(alpha=alpha, mu=mu, diag_sigma=dsig, loglik=np.array(loglik))

@@ -1,0 +1,142 @@
+"""Pins for the whole CoFEM oracle (Alg. 1 + Alg. 2)."""
+import numpy as np
+import pytest
+
+from oracle import cofem as cofem_mod
+from oracle.cofem import cofem, FLAG_ALPHA_CLAMPED
+from oracle.em import em, estep_explicit
+from oracle.operators import DenseOperator, ToeplitzOperator
+from oracle.philox import rademacher_probes
+from synth import dense_gaussian, toeplitz_calcium
+
+
+def _hadamard(n):
+    H = np.array([[1.0]])
+    while H.shape[0] < n:
+        H = np.block([[H, H], [H, -H]])
+    return H
+
+
+@pytest.mark.parametrize("solver,tol", [("direct", None), ("pcg", 1e-13)])
+def test_hadamard_probes_reproduce_em(solver, tol):
+    """With the D Hadamard columns as probes, s = diag(Sigma) exactly, so
+    CoFEM with an exact (or tight) solve is EM (Prop. 1 expansion, K = D)."""
+    p = dense_gaussian(24, 64, 5, 25.0, seed=3)
+    H = _hadamard(64)
+    T = 10
+    r = cofem(DenseOperator(p.phi), p.y, p.beta, 64, T, tol or 1e-10, 2000, seed=0,
+              probe_fn=lambda t, K, D: H, solver=solver)
+    e = em(p.phi, p.y, p.beta, T)
+    np.testing.assert_allclose(r["mu"], e["mu"], rtol=1e-7, atol=1e-10)
+    np.testing.assert_allclose(r["s"], e["diag_sigma"], rtol=1e-7)
+    np.testing.assert_allclose(r["alpha"], e["alpha"], rtol=1e-7)
+
+
+def test_rademacher_error_matches_lemma1():
+    """One E-step: the error s_j - Sigma_jj, normalised by Lemma 1's
+    nu_j = sqrt((1/K) sum_{j' != j} Sigma_jj'^2), has mean square about 1;
+    and it shrinks as 1/sqrt(K)."""
+    p = dense_gaussian(64, 256, 10, 20.0, seed=8)
+    op = DenseOperator(p.phi)
+    alpha = np.exp(np.random.default_rng(1).uniform(-1, 3, 256))
+    _, Sigma = estep_explicit(p.phi, p.y, p.beta, alpha)
+    off2 = (Sigma ** 2).sum(axis=1) - np.diag(Sigma) ** 2
+    rms = []
+    for K in (20, 200, 2000):
+        r = cofem(op, p.y, p.beta, K, 1, 1e-12, 2000, seed=2, alpha0=alpha)
+        z2 = (r["s"] - np.diag(Sigma)) ** 2 / (off2 / K)
+        assert 0.75 < z2.mean() < 1.3, (K, z2.mean())
+        rms.append(np.sqrt(np.mean((r["s"] - np.diag(Sigma)) ** 2)))
+    assert 2.3 < rms[0] / rms[1] < 4.5 and 2.3 < rms[1] / rms[2] < 4.5
+
+
+def test_identity_dictionary_closed_form():
+    """Phi = I, Jacobi theta = 1: M = A exactly, PCG takes one step, and
+    mu_j = beta y_j/(beta+alpha_j), s_j = 1/(beta+alpha_j) for any probes."""
+    D = 128
+    rng = np.random.default_rng(2)
+    y = rng.standard_normal(D)
+    beta = 9.0
+    T = 12
+    r = cofem(DenseOperator(np.eye(D)), y, beta, 8, T, 1e-10, 50, seed=5)
+    assert np.all(r["cg_iters"] == 1)
+    a = np.ones(D)
+    for _ in range(T - 1):
+        m = beta * y / (beta + a)
+        a = 1.0 / (m * m + 1.0 / (beta + a))
+    np.testing.assert_allclose(r["alpha"], a, rtol=1e-12)
+    np.testing.assert_allclose(r["mu"], beta * y / (beta + a), rtol=1e-12)
+    np.testing.assert_allclose(r["s"], 1.0 / (beta + a), rtol=1e-12)
+
+
+def test_zero_dictionary_gives_inverse_alpha():
+    """Phi = 0: b = 0 (mu column starts converged), A = M = diag(alpha),
+    s_j = (1/K) sum_k p_kj^2 / alpha_j = 1/alpha_j exactly."""
+    D = 100
+    alpha0 = np.linspace(0.5, 9.0, D)
+    r = cofem(DenseOperator(np.zeros((10, D))), np.ones(10), 4.0, 6, 1, 1e-12, 20, seed=1,
+              alpha0=alpha0)
+    assert np.all(r["mu"] == 0.0)
+    np.testing.assert_allclose(r["s"], 1.0 / alpha0, rtol=1e-14)
+
+
+def test_column_zero_is_mu_and_probes_are_philox():
+    p = dense_gaussian(16, 40, 3, 20.0, seed=1)
+    r = cofem(DenseOperator(p.phi), p.y, p.beta, 4, 1, 1e-13, 500, seed=9, return_x=True)
+    Phi = p.phi.astype(np.float64)
+    A = p.beta * Phi.T @ Phi + np.eye(40)
+    P = rademacher_probes(9, 1, 4, 40).T
+    np.testing.assert_allclose(r["X"][:, 0], np.linalg.solve(A, p.beta * Phi.T @ p.y.astype(np.float64)), rtol=1e-8)
+    np.testing.assert_allclose(r["X"][:, 1:], np.linalg.solve(A, P), rtol=1e-7, atol=1e-12)
+
+
+def test_support_recovery_gaussian():
+    """Sec. V-C: CoFEM (K = 20, U = 400, theta = 1) reaches NRMSE < 2 % after
+    T = 30 EM iterations on a dense Gaussian Phi with N = D/4, d = 0.06 D.
+    The paper's eps = 1e-4 leaves the mu column too inexact at this SNR for the
+    inactive alpha_j to grow; eps = 1e-5 (per column or Frobenius) reproduces
+    the < 2 % figure, as does an exact solve."""
+    D = 1024
+    p = dense_gaussian(D // 4, D, int(0.06 * D), 40.0, seed=11, spike="uniform2")
+    for conv in ("per_column", "frobenius"):
+        r = cofem(DenseOperator(p.phi), p.y, p.beta, 20, 30, 1e-5, 400, seed=3, precond="one",
+                  conv=conv)
+        nrmse = np.linalg.norm(r["mu"] - p.z) / np.linalg.norm(p.z)
+        assert nrmse < 0.02, (conv, nrmse)
+        # every spike clearly above the noise floor is found, nothing else is
+        off = np.ones(p.D, bool)
+        off[p.support] = False
+        big = np.abs(p.z) > 0.1
+        assert np.all(np.abs(r["mu"][big]) > 0.05)
+        assert np.max(np.abs(r["mu"][off])) < 0.05
+
+
+def test_toeplitz_cofem_matches_dense_route():
+    """The convolution operator (FFT) and its explicit matrix give the same fit."""
+    p = toeplitz_calcium(300, 32, 0.05, 20.0, seed=4)
+    opT = ToeplitzOperator(p.phi, 300)
+    opD = DenseOperator(opT.dense())
+    r1 = cofem(opT, p.y, p.beta, 6, 5, 1e-10, 500, seed=2)
+    r2 = cofem(opD, p.y, p.beta, 6, 5, 1e-10, 500, seed=2)
+    for k in ("mu", "s"):
+        np.testing.assert_allclose(r1[k], r2[k], rtol=1e-5, atol=1e-9)
+    # alpha_j near the clamp is 1/(mu_j^2 + s_j) of a tiny difference: compare
+    # the second moment 1/alpha, the quantity the M-step actually forms
+    np.testing.assert_allclose(1.0 / r1["alpha"], 1.0 / r2["alpha"], rtol=1e-5, atol=1e-12)
+
+
+def test_alpha_clamp_flag():
+    """An M-step with mu^2 + s <= 1/alpha_max clamps alpha at alpha_max and flags it."""
+    D = 8
+    r = cofem(DenseOperator(np.zeros((4, D))), np.zeros(4), 1.0, 1, 2, 1e-12, 10, seed=1,
+              alpha0=np.full(D, 1e13), alpha_max=1e12)
+    assert r["flags"] & FLAG_ALPHA_CLAMPED
+    assert np.all(r["alpha"] == 1e12)
+
+
+def test_last_iteration_skips_mstep():
+    """Alg. 1 returns alpha^(T): with T = 1 alpha stays at alpha0."""
+    p = dense_gaussian(16, 40, 3, 20.0, seed=1)
+    a0 = np.linspace(1, 2, 40)
+    r = cofem(DenseOperator(p.phi), p.y, p.beta, 4, 1, 1e-8, 100, seed=1, alpha0=a0)
+    np.testing.assert_array_equal(r["alpha"], a0)
