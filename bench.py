@@ -1,0 +1,310 @@
+#!/usr/bin/env python3
+"""Benchmark of the CoFEM hot path on GB300 (one JSON line on stdout).
+
+A step is one CoFEM fit (Alg. 1 with Alg. 2: T EM iterations, each a batched
+PCG solve of the K+1 systems plus the diagonal estimate and M-step) on one
+synthetic problem whose inputs are already resident in HBM.  The metric is EM
+iterations per second over the whole job (all ranks).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference this method has)
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import WORKLOADS, workload  # noqa: E402
+
+DEFAULT_WORKLOAD = "dense_n8192_d32768_k32_bf16"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _metric_name(name, spec):
+    if spec["kind"] == "dense":
+        shape = f"dense N={spec['N']} D={spec['D']}"
+    else:
+        shape = f"convolutional N=D={spec['D']} L={spec['L']}"
+    return f"CoFEM EM-iter/s ({shape}, K={spec['K']}, T={spec['T']}, {spec['precision'].upper()} Phi)"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _nmse_db(mu, z):
+    return 20.0 * math.log10(max(np.linalg.norm(np.asarray(mu, np.float64) - z), 1e-300) / np.linalg.norm(z))
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+def _cpu_baseline(prob, run, budget_s=20.0):
+    """FP64 oracle on a bounded sample: as many leading EM iterations of the same
+    fit as fit in about `budget_s` (at least one)."""
+    from oracle import make_operator, cofem as oracle_cofem
+    op = make_operator(prob.kind, prob.phi, prob.N)
+    t0 = time.perf_counter()
+    oracle_cofem(op, prob.y, prob.beta, run["K"], 1, run["cg_tol"], run["cg_maxit"], run["seed"],
+                 rr_period=run["rr_period"])
+    t1 = time.perf_counter() - t0
+    n = int(max(1, min(run["T"], budget_s // max(t1, 1e-9))))
+    if n > 1:
+        t0 = time.perf_counter()
+        oracle_cofem(op, prob.y, prob.beta, run["K"], n, run["cg_tol"], run["cg_maxit"], run["seed"],
+                     rr_period=run["rr_period"])
+        t1 = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0))
+    return {"value": n / t1, "unit": "EM-iter/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {n} EM iteration(s) of the same fit, FP64 numpy/BLAS, {t1:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    name = args.workload
+    spec = WORKLOADS[name]
+    prob, run = workload(name)
+    vals = []
+    base = None
+    for _ in range(max(1, args.steps)):
+        base = _cpu_baseline(prob, run, budget_s=max(5.0, 60.0 / max(1, args.steps)))
+        vals.append(base["value"])
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": _metric_name(name, spec), "value": v, "unit": "EM-iter/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * run["T"] / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": name},
+            "cpu_baseline": dict(base, value=v),
+            "e2e": {"value": v, "unit": "EM-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _launches_per_fit(cg_iters, rr_period):
+    n = 2 + 1          # b = beta Phi^T y, finiteness check of y, fit setup
+    for u in cg_iters:
+        u = int(u)
+        rr = u // rr_period if rr_period > 0 else 0
+        n += 2 + 4 * u + 3 * rr   # init + mstep; per CG step: 2 operator + update + direction
+    return n
+
+
+def run_ours(args):
+    import torch
+    import paper_2105_10439_gb300 as cf
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    name = args.workload
+    spec = WORKLOADS[name]
+    prob, run = workload(name, seed=1 + rank)   # independent problem per rank (weak scaling)
+    K, T, tol, maxit = run["K"], run["T"], run["cg_tol"], run["cg_maxit"]
+    D, N = prob.D, prob.N
+    stream = torch.cuda.Stream(device=dev)
+    prec = cf.COFEM_BF16 if run["precision"] == "bf16" else cf.COFEM_F32
+    kind = cf.COFEM_OP_DENSE if prob.kind == "dense" else cf.COFEM_OP_TOEPLITZ
+
+    phi_d = torch.from_numpy(prob.phi).to(dev)
+    y_d = torch.from_numpy(prob.y).to(dev)
+    outs = [torch.empty(D, device=dev) for _ in range(3)]
+    iters = torch.empty(T, dtype=torch.int32, device=dev)
+
+    def make(precision):
+        return cf.CoFEM(N, D, kind, phi_d, prob.L, precision=precision, rr_period=run["rr_period"],
+                        seed=run["seed"], stream=stream)
+
+    def timed_fits(model, steps, warmup):
+        for _ in range(warmup):
+            cf.cofem_fit(model.h, y_d, prob.beta, None, K, T, tol, maxit, *outs, iters)
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            dist.barrier()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        flags = 0
+        all_iters = []
+        for _ in range(steps):
+            flags |= cf.cofem_fit(model.h, y_d, prob.beta, None, K, T, tol, maxit, *outs, iters)
+            all_iters.append(iters.cpu().numpy().copy())
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = ev0.elapsed_time(ev1)
+        return ms, flags, all_iters
+
+    clocks = Clocks(local)
+    model = make(prec)
+    clocks.start()
+    ms, flags, all_iters = timed_fits(model, args.steps, args.warmup)
+    clk = clocks.stop()
+    t_max = ms
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = ws * args.steps * T / (t_max / 1000.0)
+    mu_bf = outs[0].cpu().numpy().copy()
+    nmse = _nmse_db(mu_bf, prob.z)
+
+    # dominant kernel: the dense operator pair (or the convolution kernel), timed live
+    Q = K + 1
+    reps = 20
+    op_ms = cf.cofem_time_operator(model.h, Q, reps)
+    hbm_gbs, _, peak_kind = _peaks()
+    if prob.kind == "dense":
+        elem = 2 if prec == cf.COFEM_BF16 else 4
+        alg_bytes = 2.0 * N * D * elem                       # Phi read twice per application
+        roof = {"bound": "hbm", "kernel": "dense operator (Phi V then Phi^T T)"}
+    else:
+        alg_bytes = 2.0 * Q * D * 4                          # read V, write U
+        roof = {"bound": "hbm", "kernel": "convolution operator"}
+    achieved = alg_bytes / (op_ms / 1000.0) / 1e9
+    roof.update({"achieved": achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved / hbm_gbs,
+                 "traffic": None, "peak_source": peak_kind, "ms_per_launch": op_ms,
+                 "algorithmic_bytes_per_launch": alg_bytes})
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    y_h = torch.from_numpy(prob.y).pin_memory()
+    outs_h = [torch.empty(D).pin_memory() for _ in range(3)]
+    it_h = torch.empty(T, dtype=torch.int32).pin_memory()
+    torch.cuda.synchronize(dev)
+    e0 = time.perf_counter()
+    e2e_steps = max(1, args.steps)
+    for _ in range(e2e_steps):
+        cf.cofem_fit(model.h, y_h, prob.beta, None, K, T, tol, maxit, *outs_h, it_h)
+    e2e_s = time.perf_counter() - e0
+    e2e = {"value": ws * e2e_steps * T / e2e_s, "unit": "EM-iter/s", "h2d_bytes_per_step": int(N * 4),
+           "d2h_bytes_per_step": int(3 * D * 4 + T * 4 + 4)}
+
+    launches = sum(_launches_per_fit(it, run["rr_period"]) for it in all_iters)
+    model.close()
+
+    # the FP32 form on the same problem (precision comparison at equal NMSE)
+    fp32 = None
+    if prob.kind == "dense" and prec == cf.COFEM_BF16 and not args.no_fp32_form:
+        m32 = make(cf.COFEM_F32)
+        ms32, f32flags, _ = timed_fits(m32, max(1, args.steps), 1)
+        nm32 = _nmse_db(outs[0].cpu().numpy(), prob.z)
+        op32 = cf.cofem_time_operator(m32.h, Q, 10)
+        m32.close()
+        fp32 = {"value": max(1, args.steps) * T / (ms32 / 1000.0), "unit": "EM-iter/s", "nmse_db": nm32,
+                "operator_ms": op32, "flags": f32flags}
+
+    line = {
+        "metric": _metric_name(name, spec), "value": value, "unit": "EM-iter/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": run["precision"], "data": "synthetic",
+        "config": {"workload": name, "N": N, "D": D, "K": K, "T": T, "cg_tol": tol, "cg_maxit": maxit,
+                   "rr_period": run["rr_period"], "l2": "inputs larger than L2" if prob.kind == "dense" and
+                   N * D * (2 if prec == cf.COFEM_BF16 else 4) > 129e6 else "L2 not flushed between fits",
+                   "cg_iters_last_fit": [int(v) for v in all_iters[-1]]},
+        "nmse_db": nmse, "flags": flags,
+        "roofline": roof, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if fp32 is not None:
+        line["fp32_form"] = fp32
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = _cpu_baseline(prob, run)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp32-form", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

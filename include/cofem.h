@@ -1,0 +1,171 @@
+/*
+ * cofem.h — C ABI of libcofem, a GB300 (sm_103a) implementation of the hot
+ * path of covariance-free expectation-maximisation (CoFEM) for sparse Bayesian
+ * learning (Lin, Song, Bilgic, Ba, "Covariance-Free Sparse Bayesian Learning").
+ *
+ * Problem (Sec. I, Eq. sparse-coding; Sec. II-A, Eq. model):
+ *     y = Phi z + eps,  z ~ N(0, diag(alpha)^-1),  y | z ~ N(Phi z, beta^-1 I),
+ *     Phi in R^{N x D}.
+ * One fit runs Alg. 1 (CovarianceFreeEM): for t = 1..T_em it solves the K+1
+ * systems A X = B,  A = beta Phi^T Phi + diag(alpha^(t)),
+ *     B = [beta Phi^T y | p_1 .. p_K]  (Sec. III-A, Eq. mat-eq; mu in column 0),
+ * by Alg. 2 (ParallelConjGradient) with the diagonal preconditioner
+ * M = diag(beta theta + alpha) (Sec. III-C), forms mu = x_0 and the diagonal
+ * estimate s_j = (1/K) sum_k p_kj x_kj (Eq. diag-estimate) and, for t < T_em,
+ * applies the M-step alpha_j = 1 / (mu_j^2 + s_j) (Eq. mstep with s for Sigma_jj).
+ *
+ * Conventions for every function below:
+ *  - Return value is a cofem_status; COFEM_OK (0) on success.  No C++
+ *    exception crosses this boundary.  On failure, cofem_last_error() returns a
+ *    human-readable message for the calling thread.
+ *  - "Device or host" pointers are classified with cudaPointerGetAttributes;
+ *    host memory may be pageable or pinned.  "Device" pointers must be CUDA
+ *    device (or managed) memory of the handle's device.
+ *  - The caller owns every buffer it passes; the library never frees them.
+ *    The library owns the memory it allocates inside a handle.
+ *  - Floating-point inputs are IEEE binary32; vectors are dense, unit stride.
+ *  - Calls on one handle are serialised on that handle's stream; different
+ *    handles may be used from different threads concurrently.
+ *  - Errors in arguments are detected before any device work is enqueued.
+ */
+#ifndef COFEM_H
+#define COFEM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define COFEM_API_VERSION 1
+
+typedef int cofem_status;
+#define COFEM_OK               0
+#define COFEM_ERR_INVALID_ARG  1  /* bad size, null pointer, unsupported combination */
+#define COFEM_ERR_NOMEM        2  /* device allocation failed / over the memory budget */
+#define COFEM_ERR_CUDA         3  /* a CUDA runtime call failed (message has details) */
+#define COFEM_ERR_NONFINITE    4  /* NaN/Inf in inputs, or CG breakdown (p^T A p <= 0) */
+#define COFEM_ERR_UNSUPPORTED  5  /* no sm_103a device, or feature not built */
+#define COFEM_ERR_NOT_FOUND    6  /* unknown ticket (serving) */
+
+/* Dictionary kinds (Sec. V-A "Dictionary"). */
+#define COFEM_OP_DENSE     0  /* explicit N x D matrix, row-major (Phi_ij at phi[i*D + j]) */
+#define COFEM_OP_TOEPLITZ  1  /* causal convolution, N = D: (Phi v)_i = sum_{tau<L} h[tau] v[i-tau];
+                                 column j of Phi is h delayed by j and truncated at N (Sec. V-A, VI-A) */
+
+/* Storage / multiply precision of a dense Phi (the CG state is always FP32,
+ * CG inner products always FP64). */
+#define COFEM_F32   0  /* Phi kept in FP32 */
+#define COFEM_BF16  1  /* Phi quantised once to bfloat16 (round to nearest even); the
+                          method then runs exactly on that quantised dictionary */
+
+/* Preconditioner theta (Sec. III-C): M = diag(beta theta + alpha). */
+#define COFEM_PRECOND_JACOBI 0  /* theta_j = sum_i Phi_ij^2  (M_jj = A_jj) */
+#define COFEM_PRECOND_ONE    1  /* theta_j = 1 (the paper's experiments, Sec. V-C) */
+
+/* CG stopping rule (Alg. 2). */
+#define COFEM_CONV_PER_COLUMN 0  /* column q stops (and is frozen) once ||r_q|| <= tol ||b_q|| */
+#define COFEM_CONV_FROBENIUS  1  /* all columns stop once ||R||_F <= tol ||B||_F (as printed in Alg. 2) */
+
+/* Fit flags (bit set in *flags). */
+#define COFEM_FLAG_CG_NOT_CONVERGED 1u /* some EM iteration hit cg_maxit with a column still active */
+#define COFEM_FLAG_ALPHA_CLAMPED    2u /* some mu_j^2 + s_j fell below 1/alpha_max and was clamped */
+#define COFEM_FLAG_BREAKDOWN        4u /* p^T A p <= 0 or non-finite in some column (column frozen) */
+
+typedef struct cofem_opts {
+    int precision;            /* COFEM_F32 | COFEM_BF16 (dense only) */
+    int precond;              /* COFEM_PRECOND_JACOBI | COFEM_PRECOND_ONE */
+    int conv;                 /* COFEM_CONV_PER_COLUMN | COFEM_CONV_FROBENIUS */
+    int rr_period;            /* residual replacement R <- B - A X every rr_period CG
+                                 iterations (0 = off) */
+    double alpha_max;         /* alpha_j = 1 / max(mu_j^2 + s_j, 1/alpha_max); default 1e12 */
+    unsigned long long seed;  /* probe seed: p_{t,k,j} from Philox4x64-10 with key (seed, 0),
+                                 counter (j >> 8, k, t, 0), bit j & 255 (1 -> -1, 0 -> +1) */
+    void* stream;             /* cudaStream_t to run on; NULL = a stream owned by the handle */
+    int use_graph;            /* 1 (default): the whole fit is one CUDA-graph launch whose EM and
+                                 CG loops are device-side conditional WHILE nodes;
+                                 0: host-driven loop (one host sync per CG iteration) */
+} cofem_opts;
+
+/* Fill *o with the defaults: F32, Jacobi, per-column, rr_period 0,
+ * alpha_max 1e12, seed 2, stream NULL, use_graph 1. */
+void cofem_default_opts(cofem_opts* o);
+
+/* Create a handle for one dictionary (step a0: upload, optional BF16
+ * quantisation, theta).
+ *   N, D   : Phi is N x D (TOEPLITZ: N must equal D).  1 <= N, D <= 2^31 - 1.
+ *   kind   : COFEM_OP_DENSE or COFEM_OP_TOEPLITZ.
+ *   phi    : DENSE: N*D floats, row-major; TOEPLITZ: the filter h[0..L).
+ *            Host or device; copied (and quantised) into memory the handle owns.
+ *   L      : TOEPLITZ filter length, 1 <= L <= 1024 and L <= N; must be 0 for DENSE.
+ *   opts   : NULL for defaults.
+ * Errors: INVALID_ARG for bad sizes/kind/pointers, NONFINITE if phi holds
+ * NaN/Inf, NOMEM, CUDA, UNSUPPORTED (no sm_103a device). */
+cofem_status cofem_create(struct cofem_ctx** out, long long N, long long D, int kind,
+                          const float* phi, long long L, const cofem_opts* opts);
+
+/* Run one CoFEM fit (Alg. 1 with Alg. 2): steps a1-a8 of the hot path.
+ *   y         : N floats (host or device).
+ *   beta      : noise precision, > 0.
+ *   alpha0    : D floats (host or device) or NULL for alpha^(1) = 1 (Alg. 1 initialisation).
+ *   K         : probes per EM iteration, 1 <= K <= 63 (Q = K + 1 systems).
+ *   T_em      : EM iterations, >= 1 (T_em E-steps, T_em - 1 M-steps).
+ *   cg_tol    : > 0, relative residual tolerance of Alg. 2.
+ *   cg_maxit  : >= 1, the U of Alg. 2.
+ *   mu, s     : D floats each (host or device): mu and s of the last E-step.
+ *   alpha     : D floats (host or device): alpha^(T_em), the precisions used in the
+ *               last E-step (Alg. 1 return value).
+ *   cg_iters  : T_em ints (host or device) or NULL: CG iterations in each EM iteration.
+ *   flags     : host unsigned or NULL: COFEM_FLAG_* bits.
+ * Blocks until the results are written.  Non-convergence is not an error
+ * (Alg. 2 returns X after U steps); it is reported in flags.  Errors:
+ * INVALID_ARG, NONFINITE (y, alpha0 or beta non-finite), NOMEM, CUDA. */
+cofem_status cofem_fit(struct cofem_ctx* h, const float* y, double beta, const float* alpha0,
+                       int K, int T_em, double cg_tol, int cg_maxit,
+                       float* mu, float* s, float* alpha, int* cg_iters, unsigned* flags);
+
+/* Release the handle and all memory it owns.  NULL is accepted. */
+cofem_status cofem_destroy(struct cofem_ctx* h);
+
+/* Static string for a status code. */
+const char* cofem_status_string(cofem_status s);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* cofem_last_error(void);
+
+/* ---- Step-level entry points (one row of the hot path each; used for
+ * ---- parity checks of the individual steps).  All run on the handle's
+ * ---- stream and block until done. */
+
+/* Step a2: probe block P (K x D floats, row k-1 = p_k at EM iteration t, entries
+ * +-1) written to `out` (device).  K >= 1, D >= 1, t >= 0. */
+cofem_status cofem_probe_fill(unsigned long long seed, int t, int K, long long D,
+                              float* out, void* stream);
+
+/* Step a4 (Alg. 2 "Apply matrix"): Psi = A V = beta Phi^T (Phi V) + diag(alpha) V
+ * for a block of Q vectors.  V and Psi are Q x D row-major (row q = vector q),
+ * alpha is D floats; all three device pointers.  1 <= Q <= 64.  If pi is not
+ * NULL, pi[q] = v_q^T A v_q is written there (host, Q doubles). */
+cofem_status cofem_apply_operator(struct cofem_ctx* h, const float* V, int Q,
+                                  const float* alpha, double beta, float* Psi, double* pi);
+
+/* Step a0: theta as used by the preconditioner (D floats, host or device). */
+cofem_status cofem_get_theta(struct cofem_ctx* h, float* theta);
+
+/* Step a1: b = beta Phi^T y (y: N floats, b: D floats; host or device). */
+cofem_status cofem_phit_y(struct cofem_ctx* h, const float* y, double beta, float* b);
+
+/* Step a4 timing: run the operator kernels of a K+1 = Q column fit `reps` times
+ * on the handle's current CG direction block, in the launch configuration a fit
+ * uses, bracketed by CUDA events on the handle's stream.  *ms_per_apply gets the
+ * mean event time of one application (all operator kernels of one CG step).
+ * Requires a previous cofem_fit (or cofem_apply_operator) with the same Q. */
+cofem_status cofem_time_operator(struct cofem_ctx* h, int Q, int reps, double* ms_per_apply);
+
+/* Bytes of device memory the handle holds (Phi copy, theta, fit workspace). */
+long long cofem_device_bytes(struct cofem_ctx* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COFEM_H */

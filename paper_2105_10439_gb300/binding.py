@@ -1,0 +1,207 @@
+"""ctypes binding of libcofem (include/cofem.h).
+
+Argument marshalling only: every function here converts Python arguments to
+the C types of the same-named entry point and raises on a non-zero status.
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA
+memory); both must be contiguous float32 (int32 for cg_iters).  No computation
+happens on this side.  If libcofem.so has not been built, importing the
+package raises immediately: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcofem.so")
+
+COFEM_OK = 0
+COFEM_ERR_INVALID_ARG = 1
+COFEM_ERR_NOMEM = 2
+COFEM_ERR_CUDA = 3
+COFEM_ERR_NONFINITE = 4
+COFEM_ERR_UNSUPPORTED = 5
+COFEM_ERR_NOT_FOUND = 6
+
+COFEM_OP_DENSE = 0
+COFEM_OP_TOEPLITZ = 1
+COFEM_F32 = 0
+COFEM_BF16 = 1
+COFEM_PRECOND_JACOBI = 0
+COFEM_PRECOND_ONE = 1
+COFEM_CONV_PER_COLUMN = 0
+COFEM_CONV_FROBENIUS = 1
+COFEM_FLAG_CG_NOT_CONVERGED = 1
+COFEM_FLAG_ALPHA_CLAMPED = 2
+COFEM_FLAG_BREAKDOWN = 4
+
+
+class cofem_opts(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int),
+        ("precond", C.c_int),
+        ("conv", C.c_int),
+        ("rr_period", C.c_int),
+        ("alpha_max", C.c_double),
+        ("seed", C.c_ulonglong),
+        ("stream", C.c_void_p),
+        ("use_graph", C.c_int),
+    ]
+
+
+class CofemError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"libcofem status {status}: {message}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(LIB_PATH)
+    vp, i, ll, d, ull = C.c_void_p, C.c_int, C.c_longlong, C.c_double, C.c_ulonglong
+    sig = {
+        "cofem_default_opts": (None, [C.POINTER(cofem_opts)]),
+        "cofem_create": (i, [C.POINTER(vp), ll, ll, i, vp, ll, C.POINTER(cofem_opts)]),
+        "cofem_fit": (i, [vp, vp, d, vp, i, i, d, i, vp, vp, vp, vp, vp]),
+        "cofem_destroy": (i, [vp]),
+        "cofem_status_string": (C.c_char_p, [i]),
+        "cofem_last_error": (C.c_char_p, []),
+        "cofem_probe_fill": (i, [ull, i, i, ll, vp, vp]),
+        "cofem_apply_operator": (i, [vp, vp, i, vp, d, vp, vp]),
+        "cofem_get_theta": (i, [vp, vp]),
+        "cofem_phit_y": (i, [vp, vp, d, vp]),
+        "cofem_device_bytes": (ll, [vp]),
+        "cofem_time_operator": (i, [vp, i, i, C.POINTER(d)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(status: int):
+    if status != COFEM_OK:
+        msg = lib.cofem_last_error().decode(errors="replace")
+        raise CofemError(status, msg or lib.cofem_status_string(status).decode())
+
+
+def _ptr(x, dtype=np.float32, allow_none=False):
+    """Address of a contiguous array (numpy host array or torch tensor)."""
+    if x is None:
+        if allow_none:
+            return None
+        raise ValueError("array argument is None")
+    if isinstance(x, np.ndarray):
+        if x.dtype != dtype or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"need a C-contiguous {np.dtype(dtype).name} array")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        import torch  # only for the dtype check
+        want = {np.float32: torch.float32, np.int32: torch.int32, np.float64: torch.float64}[dtype]
+        if x.dtype != want or not x.is_contiguous():
+            raise TypeError(f"need a contiguous {want} tensor")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def default_opts(**kw) -> cofem_opts:
+    o = cofem_opts()
+    lib.cofem_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if k == "stream" and v is not None and not isinstance(v, int):
+            v = v.cuda_stream if hasattr(v, "cuda_stream") else int(v)
+        setattr(o, k, v)
+    return o
+
+
+def cofem_create(N: int, D: int, kind: int, phi, L: int = 0, opts: cofem_opts | None = None) -> int:
+    h = C.c_void_p()
+    _check(lib.cofem_create(C.byref(h), N, D, kind, _ptr(phi), L, C.byref(opts) if opts is not None else None))
+    return h.value
+
+
+def cofem_fit(h: int, y, beta: float, alpha0, K: int, T_em: int, cg_tol: float, cg_maxit: int,
+              mu, s, alpha, cg_iters=None) -> int:
+    """Returns the COFEM_FLAG_* bits of the fit."""
+    flags = C.c_uint(0)
+    _check(lib.cofem_fit(h, _ptr(y), float(beta), _ptr(alpha0, allow_none=True), int(K), int(T_em),
+                         float(cg_tol), int(cg_maxit), _ptr(mu), _ptr(s), _ptr(alpha),
+                         _ptr(cg_iters, np.int32, allow_none=True), C.byref(flags)))
+    return flags.value
+
+
+def cofem_destroy(h: int) -> None:
+    _check(lib.cofem_destroy(h))
+
+
+def cofem_probe_fill(seed: int, t: int, K: int, D: int, out, stream=None) -> None:
+    st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib.cofem_probe_fill(seed, t, K, D, _ptr(out), st))
+
+
+def cofem_apply_operator(h: int, V, Q: int, alpha, beta: float, Psi, want_pi: bool = True):
+    pi = np.zeros(Q, dtype=np.float64) if want_pi else None
+    _check(lib.cofem_apply_operator(h, _ptr(V), Q, _ptr(alpha), float(beta), _ptr(Psi),
+                                    pi.ctypes.data if pi is not None else None))
+    return pi
+
+
+def cofem_get_theta(h: int, theta) -> None:
+    _check(lib.cofem_get_theta(h, _ptr(theta)))
+
+
+def cofem_phit_y(h: int, y, beta: float, b) -> None:
+    _check(lib.cofem_phit_y(h, _ptr(y), float(beta), _ptr(b)))
+
+
+def cofem_time_operator(h: int, Q: int, reps: int) -> float:
+    ms = C.c_double(0.0)
+    _check(lib.cofem_time_operator(h, Q, reps, C.byref(ms)))
+    return ms.value
+
+
+def cofem_device_bytes(h: int) -> int:
+    return int(lib.cofem_device_bytes(h))
+
+
+class CoFEM:
+    """Owning wrapper of one handle (closes it on exit / garbage collection)."""
+
+    def __init__(self, N, D, kind, phi, L=0, **opts):
+        self.N, self.D, self.kind = int(N), int(D), kind
+        self.opts = default_opts(**opts)
+        self.h = cofem_create(N, D, kind, phi, L, self.opts)
+
+    def fit(self, y, beta, K, T, cg_tol, cg_maxit, alpha0=None, out=None):
+        """Host-array convenience: returns dict(mu, s, alpha, cg_iters, flags)."""
+        if out is None:
+            out = dict(mu=np.empty(self.D, np.float32), s=np.empty(self.D, np.float32),
+                       alpha=np.empty(self.D, np.float32), cg_iters=np.empty(T, np.int32))
+        out["flags"] = cofem_fit(self.h, y, beta, alpha0, K, T, cg_tol, cg_maxit, out["mu"], out["s"],
+                                 out["alpha"], out["cg_iters"])
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            cofem_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,591 @@
+// C ABI of libcofem: handle lifetime, workspace, and the fit driver.  A fit is
+// one CUDA-graph launch: an EM WHILE loop whose body runs the PCG
+// initialisation, a CG WHILE loop (operator, fused update, an IF branch for
+// residual replacement, direction update) and the fused M-step; the loop
+// conditions are set on the device (cudaGraphSetConditional), so the host is
+// only involved at the start and the end of the fit.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+
+#include "cofem_internal.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+cofem_status fail(cofem_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+cofem_status cuda_fail(cudaError_t e, const char* what) {
+    cudaGetLastError();  // clear sticky-free errors
+    return fail(e == cudaErrorMemoryAllocation ? COFEM_ERR_NOMEM : COFEM_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
+
+template <typename T>
+cofem_status dalloc(cofem_ctx* c, T** p, size_t count) {
+    if (*p) return COFEM_OK;
+    const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e, "cudaMalloc");
+    }
+    c->bytes += (long long)bytes;
+    return COFEM_OK;
+}
+
+template <typename T>
+void dfree(cofem_ctx* c, T** p, size_t count) {
+    if (*p) {
+        cudaFree(*p);
+        c->bytes -= (long long)(count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+        *p = nullptr;
+    }
+}
+
+void free_graph(cofem_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    c->graph_Q = -1;
+}
+
+// Sizes of the Q-dependent workspace (recomputed on every (re)allocation).
+struct WsSizes {
+    size_t xrp, u, t, tpart, part, ttpart, counters;
+};
+
+WsSizes ws_sizes(cofem_ctx* c, int Qcap) {
+    WsSizes w{};
+    w.xrp = (size_t)Qcap * c->Dp;
+    const int QP = ((Qcap + 7) / 8) * 8;
+    if (c->kind == COFEM_OP_DENSE) {
+        w.u = (size_t)c->S2 * Qcap * c->Dp;
+        w.t = (size_t)c->Np * QP;
+        w.tpart = (size_t)c->S1 * c->Np * QP;
+        w.ttpart = (size_t)Qcap * (c->Np / 64 + 1);
+    } else {
+        w.u = (size_t)Qcap * c->Dp;
+        w.t = 0;
+        w.tpart = 0;
+        const long long Bout = 2048 - (c->L - 1);
+        w.ttpart = (size_t)Qcap * ((c->Dp + Bout - 1) / Bout + 1);
+    }
+    w.part = (size_t)3 * Qcap * c->nch;
+    w.counters = 16 + (size_t)(c->Np / 64 + 1);
+    return w;
+}
+
+void free_workspace(cofem_ctx* c) {
+    if (c->Qcap == 0) return;
+    const WsSizes w = ws_sizes(c, c->Qcap);
+    dfree(c, &c->X, w.xrp);
+    dfree(c, &c->R, w.xrp);
+    dfree(c, &c->P, w.xrp);
+    dfree(c, &c->U, w.u);
+    dfree(c, &c->T, w.t);
+    dfree(c, &c->Tpart, w.tpart);
+    dfree(c, &c->part, w.part);
+    dfree(c, &c->tt_part, w.ttpart);
+    dfree(c, &c->counters, w.counters);
+    c->Qcap = 0;
+    free_graph(c);
+}
+
+// Make sure the fit workspace holds Q columns (the split configuration
+// depends on Q, so any change of Q re-derives it and rebuilds the graph).
+cofem_status ensure_workspace(cofem_ctx* c, int Q) {
+    if (c->Qcap == Q) return COFEM_OK;
+    free_workspace(c);
+    if (c->kind == COFEM_OP_DENSE) dense_configure(c, Q);
+    const WsSizes w = ws_sizes(c, Q);
+    cofem_status st;
+    if ((st = dalloc(c, &c->X, w.xrp)) || (st = dalloc(c, &c->R, w.xrp)) || (st = dalloc(c, &c->P, w.xrp)) ||
+        (st = dalloc(c, &c->U, w.u)) || (st = dalloc(c, &c->part, w.part)) ||
+        (st = dalloc(c, &c->tt_part, w.ttpart)) || (st = dalloc(c, &c->counters, w.counters))) {
+        c->Qcap = Q;
+        free_workspace(c);
+        return st;
+    }
+    if (c->kind == COFEM_OP_DENSE) {
+        if ((st = dalloc(c, &c->T, w.t)) || (st = dalloc(c, &c->Tpart, w.tpart))) {
+            c->Qcap = Q;
+            free_workspace(c);
+            return st;
+        }
+    }
+    c->Qcap = Q;
+    CK(cudaMemsetAsync(c->counters, 0, w.counters * sizeof(unsigned), c->stream));
+    CK(cudaMemsetAsync(c->X, 0, w.xrp * sizeof(float), c->stream));
+    CK(cudaMemsetAsync(c->R, 0, w.xrp * sizeof(float), c->stream));
+    CK(cudaMemsetAsync(c->P, 0, w.xrp * sizeof(float), c->stream));
+    CK(cudaMemsetAsync(c->U, 0, w.u * sizeof(float), c->stream));
+    return COFEM_OK;
+}
+
+cofem_status ensure_iters(cofem_ctx* c, int T) {
+    if (c->iters_cap >= T) return COFEM_OK;
+    dfree(c, &c->iters_dev, (size_t)c->iters_cap);
+    c->iters_cap = 0;
+    cofem_status st = dalloc(c, &c->iters_dev, (size_t)T);
+    if (st) return st;
+    c->iters_cap = T;
+    return COFEM_OK;
+}
+
+// Record the whole fit (after the host-side prologue) into a graph.
+cofem_status build_graph(cofem_ctx* c, int Q) {
+    free_graph(c);
+    CK(cudaGraphCreate(&c->graph, 0));
+    Sink root;
+    root.stream = c->stream;
+    root.graph = c->graph;
+    launch_fit_setup(root, c, Q);
+    const cudaGraphConditionalHandle h_em = root.make_handle(1u, true);
+    Sink em = root.conditional(h_em, cudaGraphCondTypeWhile);
+    const cudaGraphConditionalHandle h_cg = em.make_handle(0u, false);
+    launch_cg_init(em, c, Q, h_cg);
+    Sink cg = em.conditional(h_cg, cudaGraphCondTypeWhile);
+    launch_operator(cg, c, Q, c->P, OP_CG);
+    const cudaGraphConditionalHandle h_rr = cg.make_handle(0u, false);
+    launch_cg_update(cg, c, Q, h_rr);
+    Sink rr = cg.conditional(h_rr, cudaGraphCondTypeIf);
+    launch_operator(rr, c, Q, c->X, OP_RR);
+    launch_rr_residual(rr, c, Q);
+    launch_cg_direction(cg, c, Q, h_cg);
+    launch_mstep(em, c, Q, h_em);
+    cudaError_t e = root.err ? root.err : (em.err ? em.err : (cg.err ? cg.err : rr.err));
+    if (e != cudaSuccess) {
+        free_graph(c);
+        return cuda_fail(e, "recording the fit graph");
+    }
+    e = cudaGraphInstantiate(&c->gexec, c->graph, 0);
+    if (e != cudaSuccess) {
+        free_graph(c);
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    c->graph_Q = Q;
+    return COFEM_OK;
+}
+
+cofem_status read_ctl(cofem_ctx* c) {
+    CK(cudaMemcpyAsync(c->ctl_host, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return COFEM_OK;
+}
+
+// The same sequence as the graph, driven from the host (one sync per CG iteration).
+cofem_status run_fit_direct(cofem_ctx* c, int Q, int T) {
+    Sink s;
+    s.stream = c->stream;
+    launch_fit_setup(s, c, Q);
+    for (int t = 1; t <= T; ++t) {
+        launch_cg_init(s, c, Q, 0);
+        if (s.err) return cuda_fail(s.err, "launch");
+        cofem_status st = read_ctl(c);
+        if (st) return st;
+        while (c->ctl_host->any_active && c->ctl_host->u < c->ctl_host->maxit) {
+            launch_operator(s, c, Q, c->P, OP_CG);
+            launch_cg_update(s, c, Q, 0);
+            if (s.err) return cuda_fail(s.err, "launch");
+            if ((st = read_ctl(c))) return st;
+            const int u = c->ctl_host->u;
+            if (c->ctl_host->rr_period > 0 && u % c->ctl_host->rr_period == 0) {
+                launch_operator(s, c, Q, c->X, OP_RR);
+                launch_rr_residual(s, c, Q);
+            }
+            launch_cg_direction(s, c, Q, 0);
+            if (s.err) return cuda_fail(s.err, "launch");
+            if ((st = read_ctl(c))) return st;
+        }
+        launch_mstep(s, c, Q, 0);
+        if (s.err) return cuda_fail(s.err, "launch");
+    }
+    return COFEM_OK;
+}
+
+cofem_status check_finite_dev(cofem_ctx* c, const float* x, long long n, const char* name) {
+    unsigned* bad = &c->ctl_host->flags;   // scratch: pinned host word, device-visible
+    (void)bad;
+    unsigned* dbad = c->counters + 15;
+    CK(cudaMemsetAsync(dbad, 0, sizeof(unsigned), c->stream));
+    launch_check_finite(c->stream, x, n, dbad);
+    unsigned h = 0;
+    CK(cudaMemcpyAsync(&h, dbad, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (h) return fail(COFEM_ERR_NONFINITE, "%s contains NaN or Inf", name);
+    return COFEM_OK;
+}
+
+cofem_status check_device(int* dev, int* sms) {
+    CK(cudaGetDevice(dev));
+    cudaDeviceProp p;
+    CK(cudaGetDeviceProperties(&p, *dev));
+    if (!(p.major == 10 && p.minor == 3))
+        return fail(COFEM_ERR_UNSUPPORTED, "libcofem is built for sm_103a (GB300); device %d is sm_%d%d (%s)", *dev,
+                    p.major, p.minor, p.name);
+    *sms = p.multiProcessorCount;
+    return COFEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cofem_default_opts(cofem_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->precision = COFEM_F32;
+    o->precond = COFEM_PRECOND_JACOBI;
+    o->conv = COFEM_CONV_PER_COLUMN;
+    o->rr_period = 0;
+    o->alpha_max = 1e12;
+    o->seed = 2;
+    o->stream = nullptr;
+    o->use_graph = 1;
+}
+
+const char* cofem_status_string(cofem_status s) {
+    switch (s) {
+        case COFEM_OK: return "ok";
+        case COFEM_ERR_INVALID_ARG: return "invalid argument";
+        case COFEM_ERR_NOMEM: return "out of device memory";
+        case COFEM_ERR_CUDA: return "CUDA error";
+        case COFEM_ERR_NONFINITE: return "non-finite value";
+        case COFEM_ERR_UNSUPPORTED: return "unsupported";
+        case COFEM_ERR_NOT_FOUND: return "not found";
+        default: return "unknown status";
+    }
+}
+
+const char* cofem_last_error(void) { return g_err; }
+
+cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, const float* phi, long long L,
+                          const cofem_opts* opts) {
+    g_err[0] = 0;
+    if (!out) return fail(COFEM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (N < 1 || D < 1 || N > 0x7fffffffLL || D > 0x7fffffffLL) return fail(COFEM_ERR_INVALID_ARG, "bad N/D");
+    if (!phi) return fail(COFEM_ERR_INVALID_ARG, "phi is NULL");
+    cofem_opts o;
+    cofem_default_opts(&o);
+    if (opts) o = *opts;
+    if (kind == COFEM_OP_DENSE) {
+        if (L != 0) return fail(COFEM_ERR_INVALID_ARG, "L must be 0 for a dense dictionary");
+        if (o.precision != COFEM_F32 && o.precision != COFEM_BF16)
+            return fail(COFEM_ERR_INVALID_ARG, "precision must be COFEM_F32 or COFEM_BF16");
+    } else if (kind == COFEM_OP_TOEPLITZ) {
+        if (N != D) return fail(COFEM_ERR_INVALID_ARG, "a convolutional dictionary needs N == D");
+        if (L < 1 || L > 1024 || L > N) return fail(COFEM_ERR_INVALID_ARG, "need 1 <= L <= min(1024, N)");
+        if (o.precision != COFEM_F32) return fail(COFEM_ERR_INVALID_ARG, "convolutional dictionary is FP32 only");
+    } else {
+        return fail(COFEM_ERR_INVALID_ARG, "unknown dictionary kind %d", kind);
+    }
+    if (o.precond != COFEM_PRECOND_JACOBI && o.precond != COFEM_PRECOND_ONE)
+        return fail(COFEM_ERR_INVALID_ARG, "bad precond");
+    if (o.conv != COFEM_CONV_PER_COLUMN && o.conv != COFEM_CONV_FROBENIUS)
+        return fail(COFEM_ERR_INVALID_ARG, "bad conv");
+    if (o.rr_period < 0) return fail(COFEM_ERR_INVALID_ARG, "rr_period < 0");
+    if (!(o.alpha_max > 0.0) || !std::isfinite(o.alpha_max)) return fail(COFEM_ERR_INVALID_ARG, "bad alpha_max");
+
+    int dev = 0, sms = 0;
+    cofem_status st = check_device(&dev, &sms);
+    if (st) return st;
+
+    cofem_ctx* c = new cofem_ctx();
+    c->N = N;
+    c->D = D;
+    c->kind = kind;
+    c->L = (int)L;
+    c->opts = o;
+    c->device = dev;
+    c->num_sms = sms;
+    c->Np = round_up(N, 128);
+    c->Dp = round_up(D, 128);
+    c->nch = vec_chunks(c->Dp);
+    if (o.stream) {
+        c->stream = (cudaStream_t)o.stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+        c->own_stream = true;
+    }
+    auto bail = [&](cofem_status s2) {
+        cofem_destroy(c);
+        return s2;
+    };
+#define CKB(call)                                              \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return bail(cuda_fail(e_, #call)); \
+    } while (0)
+
+    if ((st = dalloc(c, &c->ctl, 1))) return bail(st);
+    CKB(cudaMallocHost((void**)&c->ctl_host, sizeof(DevCtl)));
+    memset(c->ctl_host, 0, sizeof(DevCtl));
+    if ((st = dalloc(c, &c->theta, (size_t)c->Dp)) || (st = dalloc(c, &c->alpha, (size_t)c->Dp)) ||
+        (st = dalloc(c, &c->minv, (size_t)c->Dp)) || (st = dalloc(c, &c->b, (size_t)c->Dp)) ||
+        (st = dalloc(c, &c->mu_out, (size_t)c->Dp)) || (st = dalloc(c, &c->s_out, (size_t)c->Dp)) ||
+        (st = dalloc(c, &c->yv, (size_t)c->Np)))
+        return bail(st);
+    CKB(cudaMemsetAsync(c->alpha, 0, c->Dp * sizeof(float), c->stream));
+    CKB(cudaMemsetAsync(c->yv, 0, c->Np * sizeof(float), c->stream));
+    // a small counter block for input checks before any fit workspace exists
+    if ((st = ensure_workspace(c, 1))) return bail(st);
+
+    if (kind == COFEM_OP_DENSE) {
+        // upload into a padded FP32 copy (zero rows/columns beyond N, D)
+        float* tmp = nullptr;
+        if ((st = dalloc(c, &tmp, (size_t)c->Np * c->Dp))) return bail(st);
+        CKB(cudaMemsetAsync(tmp, 0, (size_t)c->Np * c->Dp * sizeof(float), c->stream));
+        CKB(cudaMemcpy2DAsync(tmp, c->Dp * sizeof(float), phi, D * sizeof(float), D * sizeof(float), N,
+                              cudaMemcpyDefault, c->stream));
+        if ((st = check_finite_dev(c, tmp, (long long)c->Np * c->Dp, "phi"))) {
+            dfree(c, &tmp, (size_t)c->Np * c->Dp);
+            return bail(st);
+        }
+        if (o.precision == COFEM_BF16) {
+            if ((st = dalloc(c, &c->phi16, (size_t)c->Np * c->Dp))) {
+                dfree(c, &tmp, (size_t)c->Np * c->Dp);
+                return bail(st);
+            }
+            launch_quantize_bf16(c->stream, tmp, c->Np, c->Dp, c->Dp, c->phi16, c->Np, c->Dp);
+            CKB(cudaStreamSynchronize(c->stream));
+            dfree(c, &tmp, (size_t)c->Np * c->Dp);
+        } else {
+            c->phi32 = tmp;
+        }
+        launch_dense_colreduce(c->stream, c, nullptr, 1.0, c->theta);
+    } else {
+        if ((st = dalloc(c, &c->h, (size_t)L))) return bail(st);
+        CKB(cudaMemcpyAsync(c->h, phi, L * sizeof(float), cudaMemcpyDefault, c->stream));
+        if ((st = check_finite_dev(c, c->h, L, "h"))) return bail(st);
+        CKB(toeplitz_prepare(c->L));
+        launch_toeplitz_theta(c->stream, c);
+    }
+    CKB(cudaGetLastError());
+    if (o.precond == COFEM_PRECOND_ONE) {
+        std::vector<float> ones((size_t)c->Dp, 0.0f);
+        for (long long j = 0; j < D; ++j) ones[(size_t)j] = 1.0f;
+        CKB(cudaMemcpyAsync(c->theta, ones.data(), c->Dp * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    }
+    CKB(cudaStreamSynchronize(c->stream));
+#undef CKB
+    *out = c;
+    return COFEM_OK;
+}
+
+cofem_status cofem_destroy(cofem_ctx* c) {
+    if (!c) return COFEM_OK;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_workspace(c);
+    free_graph(c);
+    dfree(c, &c->phi32, (size_t)c->Np * c->Dp);
+    dfree(c, &c->phi16, (size_t)c->Np * c->Dp);
+    dfree(c, &c->h, (size_t)c->L);
+    dfree(c, &c->theta, (size_t)c->Dp);
+    dfree(c, &c->alpha, (size_t)c->Dp);
+    dfree(c, &c->minv, (size_t)c->Dp);
+    dfree(c, &c->b, (size_t)c->Dp);
+    dfree(c, &c->mu_out, (size_t)c->Dp);
+    dfree(c, &c->s_out, (size_t)c->Dp);
+    dfree(c, &c->yv, (size_t)c->Np);
+    dfree(c, &c->iters_dev, (size_t)c->iters_cap);
+    dfree(c, &c->ctl, 1);
+    if (c->ctl_host) cudaFreeHost(c->ctl_host);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return COFEM_OK;
+}
+
+// b = beta Phi^T y into c->b, after y is staged in c->yv.
+static cofem_status stage_y_and_b(cofem_ctx* c, const float* y, double beta) {
+    CK(cudaMemcpyAsync(c->yv, y, c->N * sizeof(float), cudaMemcpyDefault, c->stream));
+    cofem_status st = check_finite_dev(c, c->yv, c->N, "y");
+    if (st) return st;
+    if (c->kind == COFEM_OP_DENSE) launch_dense_colreduce(c->stream, c, c->yv, beta, c->b);
+    else launch_toeplitz_phit_y(c->stream, c, c->yv, beta, c->b);
+    CK(cudaGetLastError());
+    return COFEM_OK;
+}
+
+cofem_status cofem_fit(cofem_ctx* c, const float* y, double beta, const float* alpha0, int K, int T_em,
+                       double cg_tol, int cg_maxit, float* mu, float* s, float* alpha, int* cg_iters,
+                       unsigned* flags) {
+    g_err[0] = 0;
+    if (!c) return fail(COFEM_ERR_INVALID_ARG, "handle is NULL");
+    if (!y || !mu || !s || !alpha) return fail(COFEM_ERR_INVALID_ARG, "y, mu, s and alpha are required");
+    if (K < 1 || K > COFEM_QMAX - 1) return fail(COFEM_ERR_INVALID_ARG, "need 1 <= K <= %d", COFEM_QMAX - 1);
+    if (T_em < 1) return fail(COFEM_ERR_INVALID_ARG, "need T_em >= 1");
+    if (cg_maxit < 1) return fail(COFEM_ERR_INVALID_ARG, "need cg_maxit >= 1");
+    if (!(cg_tol > 0.0) || !std::isfinite(cg_tol)) return fail(COFEM_ERR_INVALID_ARG, "need cg_tol > 0");
+    if (!std::isfinite(beta)) return fail(COFEM_ERR_NONFINITE, "beta is not finite");
+    if (!(beta > 0.0)) return fail(COFEM_ERR_INVALID_ARG, "need beta > 0");
+    CK(cudaSetDevice(c->device));
+    const int Q = K + 1;
+    cofem_status st;
+    if ((st = ensure_workspace(c, Q)) || (st = ensure_iters(c, T_em))) return st;
+
+    DevCtl* hc = c->ctl_host;
+    memset(hc, 0, sizeof(DevCtl));
+    hc->beta = beta;
+    hc->tol = cg_tol;
+    hc->alpha_max = c->opts.alpha_max;
+    hc->seed = c->opts.seed;
+    hc->T = T_em;
+    hc->K = K;
+    hc->Q = Q;
+    hc->maxit = cg_maxit;
+    hc->conv = c->opts.conv;
+    hc->rr_period = c->opts.rr_period;
+    CK(cudaMemcpyAsync(c->ctl, hc, sizeof(DevCtl), cudaMemcpyHostToDevice, c->stream));
+    if ((st = stage_y_and_b(c, y, beta))) return st;
+    if (alpha0) {
+        CK(cudaMemcpyAsync(c->alpha, alpha0, c->D * sizeof(float), cudaMemcpyDefault, c->stream));
+        if ((st = check_finite_dev(c, c->alpha, c->D, "alpha0"))) return st;
+    } else {
+        std::vector<float> ones((size_t)c->D, 1.0f);
+        CK(cudaMemcpyAsync(c->alpha, ones.data(), c->D * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    if (c->opts.use_graph) {
+        if (c->graph_Q != Q || !c->gexec) {
+            if ((st = build_graph(c, Q))) return st;
+        }
+        CK(cudaGraphLaunch(c->gexec, c->stream));
+    } else {
+        if ((st = run_fit_direct(c, Q, T_em))) return st;
+    }
+    CK(cudaMemcpyAsync(mu, c->mu_out, c->D * sizeof(float), cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(s, c->s_out, c->D * sizeof(float), cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(alpha, c->alpha, c->D * sizeof(float), cudaMemcpyDefault, c->stream));
+    if (cg_iters) CK(cudaMemcpyAsync(cg_iters, c->iters_dev, T_em * sizeof(int), cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(hc, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaGetLastError());
+    if (flags) *flags = hc->flags;
+    return COFEM_OK;
+}
+
+cofem_status cofem_probe_fill(unsigned long long seed, int t, int K, long long D, float* out, void* stream) {
+    g_err[0] = 0;
+    if (!out || K < 1 || D < 1 || t < 0) return fail(COFEM_ERR_INVALID_ARG, "bad arguments");
+    if (K > 65535) return fail(COFEM_ERR_INVALID_ARG, "K too large");
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_probe_fill(st, seed, t, K, D, D, out);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    return COFEM_OK;
+}
+
+cofem_status cofem_apply_operator(cofem_ctx* c, const float* V, int Q, const float* alpha, double beta,
+                                  float* Psi, double* pi) {
+    g_err[0] = 0;
+    if (!c || !V || !alpha || !Psi) return fail(COFEM_ERR_INVALID_ARG, "NULL argument");
+    if (Q < 1 || Q > COFEM_QMAX) return fail(COFEM_ERR_INVALID_ARG, "need 1 <= Q <= %d", COFEM_QMAX);
+    if (!std::isfinite(beta)) return fail(COFEM_ERR_NONFINITE, "beta is not finite");
+    CK(cudaSetDevice(c->device));
+    cofem_status st = ensure_workspace(c, Q);
+    if (st) return st;
+    // stage V (Q x D, stride D) into the padded P block and alpha into c->alpha
+    CK(cudaMemsetAsync(c->P, 0, (size_t)Q * c->Dp * sizeof(float), c->stream));
+    CK(cudaMemcpy2DAsync(c->P, c->Dp * sizeof(float), V, c->D * sizeof(float), c->D * sizeof(float), Q,
+                         cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(c->alpha, alpha, c->D * sizeof(float), cudaMemcpyDefault, c->stream));
+    DevCtl* hc = c->ctl_host;
+    memset(hc, 0, sizeof(DevCtl));
+    hc->beta = beta;
+    hc->Q = Q;
+    CK(cudaMemcpyAsync(c->ctl, hc, sizeof(DevCtl), cudaMemcpyHostToDevice, c->stream));
+    Sink s;
+    s.stream = c->stream;
+    launch_operator(s, c, Q, c->P, OP_PLAIN);
+    if (s.err) return cuda_fail(s.err, "operator launch");
+    float* out = Psi;
+    const bool dev_out = [&] {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, Psi) != cudaSuccess) { cudaGetLastError(); return false; }
+        return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    }();
+    if (!dev_out) out = c->X;   // stage in the X block (Q x D fits in Q x Dp)
+    launch_plain_psi(c->stream, c, Q, c->P, c->alpha, beta, out);
+    CK(cudaGetLastError());
+    if (pi) {
+        double* dpi = c->part;   // Q doubles of scratch
+        launch_dot_rows(c->stream, c->P, c->Dp, out, c->D, c->D, Q, dpi);
+        CK(cudaMemcpyAsync(pi, dpi, Q * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (!dev_out) CK(cudaMemcpyAsync(Psi, out, (size_t)Q * c->D * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return COFEM_OK;
+}
+
+cofem_status cofem_get_theta(cofem_ctx* c, float* theta) {
+    g_err[0] = 0;
+    if (!c || !theta) return fail(COFEM_ERR_INVALID_ARG, "NULL argument");
+    CK(cudaSetDevice(c->device));
+    CK(cudaMemcpyAsync(theta, c->theta, c->D * sizeof(float), cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return COFEM_OK;
+}
+
+cofem_status cofem_phit_y(cofem_ctx* c, const float* y, double beta, float* b) {
+    g_err[0] = 0;
+    if (!c || !y || !b) return fail(COFEM_ERR_INVALID_ARG, "NULL argument");
+    if (!std::isfinite(beta)) return fail(COFEM_ERR_NONFINITE, "beta is not finite");
+    CK(cudaSetDevice(c->device));
+    cofem_status st = stage_y_and_b(c, y, beta);
+    if (st) return st;
+    CK(cudaMemcpyAsync(b, c->b, c->D * sizeof(float), cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return COFEM_OK;
+}
+
+cofem_status cofem_time_operator(cofem_ctx* c, int Q, int reps, double* ms_per_apply) {
+    g_err[0] = 0;
+    if (!c || !ms_per_apply || reps < 1) return fail(COFEM_ERR_INVALID_ARG, "bad arguments");
+    if (Q != c->Qcap) return fail(COFEM_ERR_INVALID_ARG, "Q must match the last fit (%d)", c->Qcap);
+    CK(cudaSetDevice(c->device));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    Sink s;
+    s.stream = c->stream;
+    launch_operator(s, c, Q, c->P, OP_PLAIN);   // warm-up
+    CK(cudaEventRecord(e0, c->stream));
+    for (int r = 0; r < reps; ++r) launch_operator(s, c, Q, c->P, OP_PLAIN);
+    CK(cudaEventRecord(e1, c->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s.err) return cuda_fail(s.err, "operator launch");
+    *ms_per_apply = (double)ms / reps;
+    return COFEM_OK;
+}
+
+long long cofem_device_bytes(cofem_ctx* c) { return c ? c->bytes : 0; }
+
+}  // extern "C"

@@ -1,0 +1,465 @@
+// Vector kernels of the CoFEM hot path: PCG initialisation, the fused CG
+// update with the per-column stopping test, residual replacement, the
+// direction update, and the fused diagonal-estimate + M-step.
+//
+// Layout: each of X, R, P is Q columns of Dp floats ("column q" of Alg. 2 is
+// the contiguous run [q*Dp, q*Dp + D)); padding entries are kept at zero.
+// Vector kernels run on a (chunk, q) grid: block (ch, q) owns elements
+// [ch*1024, ch*1024 + 1024) of column q, so the per-column reductions of Alg. 2
+// are one partial per block, reduced by the last block (fixed order).
+#include "cofem_internal.cuh"
+
+namespace {
+
+constexpr int CH = COFEM_VEC_CHUNK;
+constexpr int NT = COFEM_VEC_THREADS;
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+// Sum the per-block partials part[(k*Q + q)*nch + ch] over ch for k < nk,
+// into out[k*COFEM_QMAX + q] (shared).  One warp per (k, q).
+__device__ void reduce_parts(const double* part, int nk, int Q, int nch, double* out) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int kq = w; kq < nk * Q; kq += nw) {
+        const int k = kq / Q, q = kq % Q;
+        const double* src = part + (size_t)(k * Q + q) * nch;
+        double v = 0.0;
+        for (int i = lane; i < nch; i += 32) v += __ldcg(src + i);
+        v = warp_sum(v);
+        if (lane == 0) out[k * COFEM_QMAX + q] = v;
+    }
+    __syncthreads();
+}
+
+// Alg. 2 stopping test and direction scalars for the columns still active
+// (thread 0 of the last block).  rr[q] = ||r_q||^2, rz[q] = r_q^T M^-1 r_q.
+__device__ void cg_stop_test(DevCtl* ctl, const double* rr, const double* rz) {
+    const int Q = ctl->Q;
+    if (ctl->conv == COFEM_CONV_FROBENIUS) {
+        double num = 0.0, den = 0.0;
+        for (int q = 0; q < Q; ++q) {
+            if (ctl->active[q]) num += rr[q];
+            den += ctl->bnorm2[q];
+        }
+        if (sqrt(num) / sqrt(den) <= ctl->tol)
+            for (int q = 0; q < Q; ++q) ctl->active[q] = 0;
+    }
+    int any = 0;
+    for (int q = 0; q < Q; ++q) {
+        if (!ctl->active[q]) continue;
+        ctl->rnorm2[q] = rr[q];
+        if (ctl->conv == COFEM_CONV_PER_COLUMN && sqrt(rr[q]) / sqrt(ctl->bnorm2[q]) <= ctl->tol) {
+            ctl->active[q] = 0;
+            continue;
+        }
+        ctl->eta[q] = rz[q] / ctl->rho[q];
+        ctl->rho[q] = rz[q];
+        any = 1;
+    }
+    ctl->any_active = any;
+}
+
+// ---------------------------------------------------------------------------
+// Fit set-up: M^-1 = 1 / (beta theta + alpha); t = 1.
+// ---------------------------------------------------------------------------
+__global__ void k_fit_setup(DevCtl* ctl, const float* __restrict__ theta, const float* __restrict__ alpha,
+                            float* __restrict__ minv, long long D, long long Dp) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const double beta = ctl->beta;
+    if (j < Dp) minv[j] = j < D ? (float)(1.0 / (beta * (double)theta[j] + (double)alpha[j])) : 0.0f;
+    if (j == 0) {
+        ctl->t = 1;
+        ctl->u = 0;
+        ctl->flags = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// PCG initialisation (Alg. 2 "Initialize", PCG reading: P_0 = W_0 = M^-1 B):
+// B column 0 = b = beta Phi^T y, columns q >= 1 = probe p_q of EM iteration t.
+// X = 0, R = B, P = M^-1 B; rho_q = B^T M^-1 B, ||b_q||^2, p^T diag(alpha) p.
+// ---------------------------------------------------------------------------
+__global__ __launch_bounds__(NT) void k_cg_init(DevCtl* ctl, const float* __restrict__ b,
+                                                const float* __restrict__ minv, const float* __restrict__ alpha,
+                                                float* __restrict__ X, float* __restrict__ R, float* __restrict__ P,
+                                                long long D, long long Dp, int nch, double* part,
+                                                unsigned* counter, cudaGraphConditionalHandle h_cg) {
+    __shared__ double sh[NT / 32];
+    __shared__ double red[3 * COFEM_QMAX];
+    const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q, t = ctl->t;
+    const unsigned long long seed = ctl->seed;
+    double bb = 0.0, rz = 0.0, ap = 0.0;
+    const size_t off = (size_t)q * Dp;
+    for (int e = threadIdx.x * 4; e < CH; e += NT * 4) {
+        const long long j = (long long)ch * CH + e;
+        if (j >= Dp) break;
+        float4 bv;
+        if (q == 0) {
+            bv = ld4(b + j);
+        } else {
+            const uint64_t w = probe_word(seed, t, q, j);   // j..j+3 share one 64-bit word
+            bv.x = j + 0 < D ? probe_sign_from_word(w, j + 0) : 0.0f;
+            bv.y = j + 1 < D ? probe_sign_from_word(w, j + 1) : 0.0f;
+            bv.z = j + 2 < D ? probe_sign_from_word(w, j + 2) : 0.0f;
+            bv.w = j + 3 < D ? probe_sign_from_word(w, j + 3) : 0.0f;
+        }
+        const float4 mv = ld4(minv + j), av = ld4(alpha + j);
+        const float4 wv = make_float4(bv.x * mv.x, bv.y * mv.y, bv.z * mv.z, bv.w * mv.w);
+        st4(X + off + j, make_float4(0.f, 0.f, 0.f, 0.f));
+        st4(R + off + j, bv);
+        st4(P + off + j, wv);
+        bb += (double)bv.x * bv.x + (double)bv.y * bv.y + (double)bv.z * bv.z + (double)bv.w * bv.w;
+        rz += (double)bv.x * wv.x + (double)bv.y * wv.y + (double)bv.z * wv.z + (double)bv.w * wv.w;
+        ap += (double)av.x * wv.x * wv.x + (double)av.y * wv.y * wv.y + (double)av.z * wv.z * wv.z +
+              (double)av.w * wv.w * wv.w;
+    }
+    bb = block_sum(bb, sh);
+    rz = block_sum(rz, sh);
+    ap = block_sum(ap, sh);
+    if (threadIdx.x == 0) {
+        part[(size_t)(0 * Q + q) * nch + ch] = bb;
+        part[(size_t)(1 * Q + q) * nch + ch] = rz;
+        part[(size_t)(2 * Q + q) * nch + ch] = ap;
+    }
+    if (!last_block_arrive(counter, gridDim.x * gridDim.y)) return;
+    reduce_parts(part, 3, Q, nch, red);
+    if (threadIdx.x == 0) {
+        int any = 0;
+        for (int qq = 0; qq < Q; ++qq) {
+            ctl->bnorm2[qq] = red[qq];
+            ctl->rho[qq] = red[COFEM_QMAX + qq];
+            ctl->ap[qq] = red[2 * COFEM_QMAX + qq];
+            ctl->rnorm2[qq] = red[qq];
+            ctl->active[qq] = red[qq] > 0.0;   // a zero right-hand side starts converged (x = 0)
+            any |= ctl->active[qq];
+        }
+        ctl->u = 0;
+        ctl->any_active = any;
+        set_cond(h_cg, any && ctl->maxit > 0);
+    }
+}
+
+// Psi_j for column q from the operator partials: beta * sum_s U_s + alpha_j v_j.
+__device__ __forceinline__ float4 psi_from_parts(const float* __restrict__ U, int S2, size_t sstride,
+                                                 size_t idx, float beta, float4 av, float4 vv) {
+    float4 u = ld4(U + idx);
+    for (int s = 1; s < S2; ++s) {
+        const float4 w = ld4(U + (size_t)s * sstride + idx);
+        u.x += w.x; u.y += w.y; u.z += w.z; u.w += w.w;
+    }
+    return make_float4(beta * u.x + av.x * vv.x, beta * u.y + av.y * vv.y,
+                       beta * u.z + av.z * vv.z, beta * u.w + av.w * vv.w);
+}
+
+// ---------------------------------------------------------------------------
+// Fused CG update (Alg. 2: X += P Gamma, R -= Psi Gamma, then ||r||, r^T M^-1 r,
+// stopping test and eta), for the active columns.
+// ---------------------------------------------------------------------------
+__global__ __launch_bounds__(NT) void k_cg_update(DevCtl* ctl, const float* __restrict__ P,
+                                                  const float* __restrict__ U, int S2, const float* __restrict__ alpha,
+                                                  const float* __restrict__ minv, float* __restrict__ X,
+                                                  float* __restrict__ R, long long Dp, int Qcap, int nch,
+                                                  double* part, unsigned* counter,
+                                                  cudaGraphConditionalHandle h_rr) {
+    __shared__ double sh[NT / 32];
+    __shared__ double red[2 * COFEM_QMAX];
+    const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q;
+    double rr = 0.0, rz = 0.0;
+    if (ctl->active[q]) {
+        const float gamma = (float)ctl->gamma[q];
+        const float beta = (float)ctl->beta;
+        const size_t off = (size_t)q * Dp, sstride = (size_t)Qcap * Dp;
+        for (int e = threadIdx.x * 4; e < CH; e += NT * 4) {
+            const long long j = (long long)ch * CH + e;
+            if (j >= Dp) break;
+            const float4 pv = ld4(P + off + j), av = ld4(alpha + j), mv = ld4(minv + j);
+            const float4 psi = psi_from_parts(U, S2, sstride, off + j, beta, av, pv);
+            float4 xv = ld4(X + off + j), rv = ld4(R + off + j);
+            xv.x += gamma * pv.x; xv.y += gamma * pv.y; xv.z += gamma * pv.z; xv.w += gamma * pv.w;
+            rv.x -= gamma * psi.x; rv.y -= gamma * psi.y; rv.z -= gamma * psi.z; rv.w -= gamma * psi.w;
+            st4(X + off + j, xv);
+            st4(R + off + j, rv);
+            rr += (double)rv.x * rv.x + (double)rv.y * rv.y + (double)rv.z * rv.z + (double)rv.w * rv.w;
+            rz += (double)rv.x * (rv.x * mv.x) + (double)rv.y * (rv.y * mv.y) + (double)rv.z * (rv.z * mv.z) +
+                  (double)rv.w * (rv.w * mv.w);
+        }
+    }
+    rr = block_sum(rr, sh);
+    rz = block_sum(rz, sh);
+    if (threadIdx.x == 0) {
+        part[(size_t)(0 * Q + q) * nch + ch] = rr;
+        part[(size_t)(1 * Q + q) * nch + ch] = rz;
+    }
+    if (!last_block_arrive(counter, gridDim.x * gridDim.y)) return;
+    reduce_parts(part, 2, Q, nch, red);
+    if (threadIdx.x == 0) {
+        const int u = ++ctl->u;
+        if (ctl->rr_period > 0 && u % ctl->rr_period == 0) {
+            set_cond(h_rr, 1);   // residual replacement finishes this iteration
+            return;
+        }
+        set_cond(h_rr, 0);
+        cg_stop_test(ctl, red, red + COFEM_QMAX);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Residual replacement (precision form): R = B - A X for the active columns,
+// with B regenerated (b, probes), then the stopping test and eta.
+// ---------------------------------------------------------------------------
+__global__ __launch_bounds__(NT) void k_rr_residual(DevCtl* ctl, const float* __restrict__ b,
+                                                    const float* __restrict__ X, const float* __restrict__ U, int S2,
+                                                    const float* __restrict__ alpha, const float* __restrict__ minv,
+                                                    float* __restrict__ R, long long D, long long Dp, int Qcap,
+                                                    int nch, double* part, unsigned* counter) {
+    __shared__ double sh[NT / 32];
+    __shared__ double red[2 * COFEM_QMAX];
+    const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q, t = ctl->t;
+    double rr = 0.0, rz = 0.0;
+    if (ctl->active[q]) {
+        const float beta = (float)ctl->beta;
+        const size_t off = (size_t)q * Dp, sstride = (size_t)Qcap * Dp;
+        for (int e = threadIdx.x * 4; e < CH; e += NT * 4) {
+            const long long j = (long long)ch * CH + e;
+            if (j >= Dp) break;
+            float4 bv;
+            if (q == 0) {
+                bv = ld4(b + j);
+            } else {
+                const uint64_t w = probe_word(ctl->seed, t, q, j);
+                bv.x = j + 0 < D ? probe_sign_from_word(w, j + 0) : 0.0f;
+                bv.y = j + 1 < D ? probe_sign_from_word(w, j + 1) : 0.0f;
+                bv.z = j + 2 < D ? probe_sign_from_word(w, j + 2) : 0.0f;
+                bv.w = j + 3 < D ? probe_sign_from_word(w, j + 3) : 0.0f;
+            }
+            const float4 xv = ld4(X + off + j), av = ld4(alpha + j), mv = ld4(minv + j);
+            const float4 ax = psi_from_parts(U, S2, sstride, off + j, beta, av, xv);
+            const float4 rv = make_float4(bv.x - ax.x, bv.y - ax.y, bv.z - ax.z, bv.w - ax.w);
+            st4(R + off + j, rv);
+            rr += (double)rv.x * rv.x + (double)rv.y * rv.y + (double)rv.z * rv.z + (double)rv.w * rv.w;
+            rz += (double)rv.x * (rv.x * mv.x) + (double)rv.y * (rv.y * mv.y) + (double)rv.z * (rv.z * mv.z) +
+                  (double)rv.w * (rv.w * mv.w);
+        }
+    }
+    rr = block_sum(rr, sh);
+    rz = block_sum(rz, sh);
+    if (threadIdx.x == 0) {
+        part[(size_t)(0 * Q + q) * nch + ch] = rr;
+        part[(size_t)(1 * Q + q) * nch + ch] = rz;
+    }
+    if (!last_block_arrive(counter, gridDim.x * gridDim.y)) return;
+    reduce_parts(part, 2, Q, nch, red);
+    if (threadIdx.x == 0) cg_stop_test(ctl, red, red + COFEM_QMAX);
+}
+
+// ---------------------------------------------------------------------------
+// Direction update (Alg. 2, PCG reading: W = M^-1 R, P = W + P H) for the active
+// columns, plus p^T diag(alpha) p for the next pi, and the CG loop condition.
+// ---------------------------------------------------------------------------
+__global__ __launch_bounds__(NT) void k_cg_direction(DevCtl* ctl, const float* __restrict__ R,
+                                                     const float* __restrict__ alpha,
+                                                     const float* __restrict__ minv, float* __restrict__ P,
+                                                     long long Dp, int nch, double* part, unsigned* counter,
+                                                     cudaGraphConditionalHandle h_cg) {
+    __shared__ double sh[NT / 32];
+    __shared__ double red[COFEM_QMAX];
+    const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q;
+    double ap = 0.0;
+    if (ctl->active[q]) {
+        const float eta = (float)ctl->eta[q];
+        const size_t off = (size_t)q * Dp;
+        for (int e = threadIdx.x * 4; e < CH; e += NT * 4) {
+            const long long j = (long long)ch * CH + e;
+            if (j >= Dp) break;
+            const float4 rv = ld4(R + off + j), mv = ld4(minv + j), av = ld4(alpha + j);
+            float4 pv = ld4(P + off + j);
+            pv.x = rv.x * mv.x + eta * pv.x;
+            pv.y = rv.y * mv.y + eta * pv.y;
+            pv.z = rv.z * mv.z + eta * pv.z;
+            pv.w = rv.w * mv.w + eta * pv.w;
+            st4(P + off + j, pv);
+            ap += (double)av.x * pv.x * pv.x + (double)av.y * pv.y * pv.y + (double)av.z * pv.z * pv.z +
+                  (double)av.w * pv.w * pv.w;
+        }
+    }
+    ap = block_sum(ap, sh);
+    if (threadIdx.x == 0) part[(size_t)(2 * Q + q) * nch + ch] = ap;
+    if (!last_block_arrive(counter, gridDim.x * gridDim.y)) return;
+    // reduce only the k = 2 slab
+    {
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int qq = w; qq < Q; qq += nw) {
+            const double* src = part + (size_t)(2 * Q + qq) * nch;
+            double v = 0.0;
+            for (int i = lane; i < nch; i += 32) v += __ldcg(src + i);
+            v = warp_sum(v);
+            if (lane == 0) red[qq] = v;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int qq = 0; qq < Q; ++qq)
+            if (ctl->active[qq]) ctl->ap[qq] = red[qq];
+        const int cont = ctl->any_active && ctl->u < ctl->maxit;
+        if (ctl->any_active && !cont) ctl->flags |= COFEM_FLAG_CG_NOT_CONVERGED;
+        set_cond(h_cg, cont);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused diagonal estimate + M-step (Alg. 1: s_j = (1/K) sum_k p_kj x_kj; if t < T,
+// alpha_j = 1 / max(mu_j^2 + s_j, 1/alpha_max); then M^-1 for the next E-step),
+// probes regenerated from Philox, plus EM loop bookkeeping.
+// ---------------------------------------------------------------------------
+__global__ __launch_bounds__(NT) void k_mstep(DevCtl* ctl, const float* __restrict__ X,
+                                              const float* __restrict__ theta, float* __restrict__ alpha,
+                                              float* __restrict__ minv, float* __restrict__ mu_out,
+                                              float* __restrict__ s_out, int* __restrict__ iters, long long D,
+                                              long long Dp, unsigned* counter, cudaGraphConditionalHandle h_em) {
+    const int t = ctl->t, T = ctl->T, K = ctl->K;
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int clamped = 0;
+    if (j < Dp) {
+        const float mu = X[j];
+        double s = 0.0;
+        if (j < D) {
+            const unsigned long long seed = ctl->seed;
+            for (int k = 1; k <= K; ++k) {
+                const uint64_t w = probe_word(seed, t, k, j);
+                s += (double)probe_sign_from_word(w, j) * (double)X[(size_t)k * Dp + j];
+            }
+            s /= (double)K;
+        }
+        mu_out[j] = mu;
+        s_out[j] = (float)s;
+        if (t < T && j < D) {
+            const double m2 = (double)mu * mu + s;
+            const double floor_ = 1.0 / ctl->alpha_max;
+            clamped = m2 < floor_;
+            const double a = 1.0 / (m2 > floor_ ? m2 : floor_);
+            alpha[j] = (float)a;
+            minv[j] = (float)(1.0 / (ctl->beta * (double)theta[j] + (double)(float)a));
+        }
+    }
+    if (__syncthreads_or(clamped) && threadIdx.x == 0) atomicOr(&ctl->flags, COFEM_FLAG_ALPHA_CLAMPED);
+    if (!last_block_arrive(counter, gridDim.x)) return;
+    if (threadIdx.x == 0) {
+        iters[t - 1] = ctl->u;
+        ctl->t = t + 1;
+        set_cond(h_em, t + 1 <= T);
+    }
+}
+
+// Probe block for the step-level entry point: out[k-1][j] = p_{t,k,j}.
+__global__ void k_probe_fill(unsigned long long seed, int t, int K, long long D, long long ld, float* out) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y + 1;
+    if (j >= D || k > K) return;
+    out[(size_t)(k - 1) * ld + j] = probe_sign_from_word(probe_word(seed, t, k, j), j);
+}
+
+// Psi = beta U + alpha V for the step-level operator entry point.
+__global__ void k_plain_psi(const float* __restrict__ U, int S2, size_t sstride, const float* __restrict__ V,
+                            const float* __restrict__ alpha, float beta, float* __restrict__ Psi, long long D,
+                            long long Dp) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = blockIdx.y;
+    if (j >= D) return;
+    float u = 0.0f;
+    for (int s = 0; s < S2; ++s) u += U[(size_t)s * sstride + (size_t)q * Dp + j];
+    Psi[(size_t)q * D + j] = beta * u + alpha[j] * V[(size_t)q * Dp + j];
+}
+
+// dst (rows_dst x ld_dst, bf16) = round-to-nearest-even(src) inside rows x cols, zero outside.
+__global__ void k_quantize_bf16(const float* __restrict__ src, long long rows, long long cols, long long ld_src,
+                                __nv_bfloat16* __restrict__ dst, long long rows_dst, long long ld_dst) {
+    const long long n = rows_dst * ld_dst;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e / ld_dst, j = e % ld_dst;
+        dst[e] = __float2bfloat16_rn(j < cols && i < rows ? src[i * ld_src + j] : 0.0f);
+    }
+}
+
+// out[r] = sum_j a[r*lda + j] * b[r*ldb + j] in FP64, one block per row.
+__global__ void k_dot_rows(const float* __restrict__ a, long long lda, const float* __restrict__ b, long long ldb,
+                           long long n, double* out) {
+    __shared__ double sh[NT / 32];
+    const int r = blockIdx.x;
+    double acc = 0.0;
+    for (long long j = threadIdx.x; j < n; j += blockDim.x) acc += (double)a[r * lda + j] * (double)b[r * ldb + j];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[r] = acc;
+}
+
+__global__ void k_check_finite(const float* __restrict__ x, long long n, unsigned* bad) {
+    int b = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b |= !isfinite(x[i]);
+    if (__syncthreads_or(b) && threadIdx.x == 0) atomicOr(bad, 1u);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+void launch_fit_setup(Sink& s, cofem_ctx* c, int /*Q*/) {
+    s.launch(k_fit_setup, dim3((unsigned)((c->Dp + 255) / 256)), dim3(256), 0, c->ctl, c->theta, c->alpha, c->minv,
+             c->D, c->Dp);
+}
+
+void launch_cg_init(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg) {
+    s.launch(k_cg_init, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->b, c->minv, c->alpha, c->X, c->R, c->P, c->D, c->Dp,
+             c->nch, c->part, c->counters + 0, h_cg);
+}
+
+void launch_cg_update(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_rr) {
+    s.launch(k_cg_update, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->P, c->U, c->kind == COFEM_OP_DENSE ? c->S2 : 1,
+             c->alpha, c->minv, c->X, c->R, c->Dp, c->Qcap, c->nch, c->part, c->counters + 1, h_rr);
+}
+
+void launch_rr_residual(Sink& s, cofem_ctx* c, int Q) {
+    s.launch(k_rr_residual, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->b, c->X, c->U,
+             c->kind == COFEM_OP_DENSE ? c->S2 : 1, c->alpha, c->minv, c->R, c->D, c->Dp, c->Qcap, c->nch, c->part,
+             c->counters + 2);
+}
+
+void launch_cg_direction(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg) {
+    s.launch(k_cg_direction, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->R, c->alpha, c->minv, c->P, c->Dp, c->nch,
+             c->part, c->counters + 3, h_cg);
+}
+
+void launch_mstep(Sink& s, cofem_ctx* c, int /*Q*/, cudaGraphConditionalHandle h_em) {
+    s.launch(k_mstep, dim3((unsigned)((c->Dp + NT - 1) / NT)), dim3(NT), 0, c->ctl, c->X, c->theta, c->alpha, c->minv,
+             c->mu_out, c->s_out, c->iters_dev, c->D, c->Dp, c->counters + 4, h_em);
+}
+
+void launch_probe_fill(cudaStream_t st, unsigned long long seed, int t, int K, long long D, long long ld,
+                       float* out) {
+    k_probe_fill<<<dim3((unsigned)((D + 255) / 256), K), 256, 0, st>>>(seed, t, K, D, ld, out);
+}
+
+void launch_plain_psi(cudaStream_t st, cofem_ctx* c, int Q, const float* V, const float* alpha, double beta,
+                      float* Psi) {
+    const int S2 = c->kind == COFEM_OP_DENSE ? c->S2 : 1;
+    k_plain_psi<<<dim3((unsigned)((c->D + 255) / 256), Q), 256, 0, st>>>(
+        c->U, S2, (size_t)c->Qcap * c->Dp, V, alpha, (float)beta, Psi, c->D, c->Dp);
+}
+
+void launch_quantize_bf16(cudaStream_t st, const float* src, long long rows, long long cols, long long ld_src,
+                          __nv_bfloat16* dst, long long rows_dst, long long ld_dst) {
+    k_quantize_bf16<<<4096, 256, 0, st>>>(src, rows, cols, ld_src, dst, rows_dst, ld_dst);
+}
+
+void launch_dot_rows(cudaStream_t st, const float* a, long long lda, const float* b, long long ldb, long long n,
+                     int rows, double* out) {
+    k_dot_rows<<<rows, NT, 0, st>>>(a, lda, b, ldb, n, out);
+}
+
+void launch_check_finite(cudaStream_t st, const float* x, long long n, unsigned* bad) {
+    if (n <= 0) return;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_check_finite<<<(unsigned)blocks, 256, 0, st>>>(x, n, bad);
+}

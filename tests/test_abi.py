@@ -1,0 +1,86 @@
+"""C-ABI checks that need no GPU: libcofem builds/loads, exports every entry
+point declared in include/*.h, and rejects bad arguments before touching a device."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+DECL = re.compile(r"^\s*(?:cofem_status|void|const char\s*\*|long long)\s+(cofem_\w+)\s*\(", re.M)
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        names |= set(DECL.findall(open(h).read()))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def cf():
+    lib = os.path.join(ROOT, "paper_2105_10439_gb300", "libcofem.so")
+    if not os.path.exists(lib):
+        from paper_2105_10439_gb300.build_lib import build
+        build()
+    import paper_2105_10439_gb300 as m
+    return m
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for n in ("cofem_create", "cofem_fit", "cofem_destroy", "cofem_status_string",
+              "cofem_probe_fill", "cofem_apply_operator"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(cf):
+    lib = ctypes.CDLL(cf.LIB_PATH)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_defaults(cf):
+    assert cf.lib.cofem_status_string(0) == b"ok"
+    assert cf.lib.cofem_status_string(1) == b"invalid argument"
+    o = cf.default_opts()
+    assert o.precision == cf.COFEM_F32 and o.alpha_max == 1e12 and o.use_graph == 1 and o.seed == 2
+
+
+@pytest.mark.parametrize("args,msg", [
+    ((0, 4, 0, 0), "bad N/D"),
+    ((4, -1, 0, 0), "bad N/D"),
+    ((4, 4, 7, 0), "unknown dictionary kind"),
+    ((4, 4, 0, 3), "L must be 0"),
+    ((4, 5, 1, 2), "N == D"),
+    ((8, 8, 1, 0), "1 <= L"),
+    ((8, 8, 1, 2000), "1 <= L"),
+])
+def test_create_rejects_bad_arguments_without_gpu(cf, args, msg):
+    N, D, kind, L = args
+    with pytest.raises(cf.CofemError) as e:
+        cf.cofem_create(N, D, kind, np.zeros(64, np.float32), L, cf.default_opts())
+    assert e.value.status == cf.COFEM_ERR_INVALID_ARG
+    assert msg in str(e.value)
+
+
+def test_create_rejects_bad_opts(cf):
+    for kw in (dict(precision=9), dict(precond=4), dict(conv=3), dict(rr_period=-1), dict(alpha_max=-1.0)):
+        with pytest.raises(cf.CofemError) as e:
+            cf.cofem_create(4, 4, 0, np.zeros(16, np.float32), 0, cf.default_opts(**kw))
+        assert e.value.status == cf.COFEM_ERR_INVALID_ARG
+
+
+def test_null_handle_calls(cf):
+    with pytest.raises(cf.CofemError) as e:
+        cf.cofem_fit(None, np.zeros(4, np.float32), 1.0, None, 2, 2, 1e-5, 10,
+                     np.zeros(4, np.float32), np.zeros(4, np.float32), np.zeros(4, np.float32))
+    assert e.value.status == cf.COFEM_ERR_INVALID_ARG
+    cf.cofem_destroy(None)   # accepted
+
+
+def test_probe_fill_rejects_bad_sizes(cf):
+    with pytest.raises(cf.CofemError):
+        cf.cofem_probe_fill(1, 1, 0, 10, np.zeros(10, np.float32))

@@ -1,0 +1,273 @@
+"""GPU parity: libcofem (through its C ABI) against the FP64 CPU oracle on the
+same seeded inputs and the same Philox probes.
+
+Tolerances: probes are bit-exact (integer work); operator applications are
+compared per column in relative l2 (FP32 accumulation over up to N*D terms,
+bound 2e-5); whole fits use relative l2 <= 1e-4 on mu and <= 1e-3 on s and on
+the second moment 1/alpha = max(mu^2 + s, 1/alpha_max) (the quantity the M-step
+forms; alpha itself near the clamp is the reciprocal of a small difference)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import DenseOperator, ToeplitzOperator, apply_A, cofem as oracle_cofem  # noqa: E402
+from oracle.philox import rademacher_probes  # noqa: E402
+from synth import dense_gaussian, toeplitz_calcium, double_exponential_filter  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def cf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2105_10439_gb300 as m
+    return m
+
+
+DEV = "cuda:0"
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    n = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (n if n > 0 else 1.0))
+
+
+def bf16_round(x):
+    """Round float32 to the nearest bfloat16 (ties to even), returned as float32."""
+    b = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16 << 16
+    return b.astype(np.uint32).view(np.float32)
+
+
+def gpu_fit(cf, prob, K, T, tol, maxit, seed=2, alpha0=None, host=False, **opts):
+    D = prob.D
+    if host:
+        mu, s, al = (np.empty(D, np.float32) for _ in range(3))
+        it = np.empty(T, np.int32)
+        y = prob.y
+        a0 = alpha0
+        phi = prob.phi
+    else:
+        mu, s, al = (torch.empty(D, device=DEV) for _ in range(3))
+        it = torch.empty(T, dtype=torch.int32, device=DEV)
+        y = torch.from_numpy(prob.y).to(DEV)
+        a0 = None if alpha0 is None else torch.from_numpy(alpha0).to(DEV)
+        phi = torch.from_numpy(prob.phi).to(DEV)
+    kind = cf.COFEM_OP_DENSE if prob.kind == "dense" else cf.COFEM_OP_TOEPLITZ
+    with cf.CoFEM(prob.N, D, kind, phi, prob.L, seed=seed, **opts) as m:
+        flags = cf.cofem_fit(m.h, y, prob.beta, a0, K, T, tol, maxit, mu, s, al, it)
+    cvt = (lambda v: v) if host else (lambda v: v.cpu().numpy())
+    return dict(mu=cvt(mu), s=cvt(s), alpha=cvt(al), cg_iters=cvt(it), flags=flags)
+
+
+def oracle_fit(prob, K, T, tol, maxit, seed=2, phi=None, **kw):
+    if prob.kind == "dense":
+        op = DenseOperator(prob.phi if phi is None else phi)
+    else:
+        op = ToeplitzOperator(prob.phi, prob.N)
+    return oracle_cofem(op, prob.y, prob.beta, K, T, tol, maxit, seed, **kw)
+
+
+def assert_fit_close(g, r, tol_mu=1e-4, tol_s=1e-3, tol_a=1e-3):
+    e = (rel(g["mu"], r["mu"]), rel(g["s"], r["s"]), rel(1.0 / g["alpha"], 1.0 / r["alpha"]))
+    assert e[0] <= tol_mu and e[1] <= tol_s and e[2] <= tol_a, (e, g["cg_iters"], r["cg_iters"])
+    return e
+
+
+# ---------------------------------------------------------------------------
+# a2: probes (bit-exact)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed,t,K,D", [(2, 1, 20, 1024), (2, 7, 3, 1), (99, 50, 5, 1000), (1, 0, 2, 70001)])
+def test_probes_bit_exact(cf, seed, t, K, D):
+    out = torch.empty((K, D), device=DEV)
+    cf.cofem_probe_fill(seed, t, K, D, out)
+    np.testing.assert_array_equal(out.cpu().numpy(), rademacher_probes(seed, t, K, D).astype(np.float32))
+
+
+# ---------------------------------------------------------------------------
+# a0 / a1: theta and b = beta Phi^T y
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N,D", [(77, 301), (256, 1024), (1, 5), (300, 129)])
+def test_theta_and_phity_dense(cf, N, D):
+    p = dense_gaussian(N, D, max(1, D // 20), 20.0, seed=N + D)
+    th = np.empty(D, np.float32)
+    b = np.empty(D, np.float32)
+    with cf.CoFEM(N, D, cf.COFEM_OP_DENSE, p.phi) as m:
+        cf.cofem_get_theta(m.h, th)
+        cf.cofem_phit_y(m.h, p.y, p.beta, b)
+    op = DenseOperator(p.phi)
+    np.testing.assert_allclose(th, op.column_sq_norms(), rtol=2e-6)
+    assert rel(b, p.beta * op.apply_t(p.y.astype(np.float64))) < 2e-6
+
+
+def test_theta_and_phity_toeplitz(cf):
+    D, L = 5000, 256
+    p = toeplitz_calcium(D, L, 0.02, 15.0, seed=3)
+    th = np.empty(D, np.float32)
+    b = np.empty(D, np.float32)
+    with cf.CoFEM(D, D, cf.COFEM_OP_TOEPLITZ, p.phi, L) as m:
+        cf.cofem_get_theta(m.h, th)
+        cf.cofem_phit_y(m.h, p.y, p.beta, b)
+    op = ToeplitzOperator(p.phi, D)
+    np.testing.assert_allclose(th, op.column_sq_norms(), rtol=2e-6, atol=1e-12)
+    assert th[-1] == 0.0          # h[0] = 0: the last column of Phi is zero
+    assert rel(b, p.beta * op.apply_t(p.y.astype(np.float64))) < 2e-6
+
+
+# ---------------------------------------------------------------------------
+# a4: operator A V and pi = v^T A v
+# ---------------------------------------------------------------------------
+def _check_operator(cf, m, op, D, Q, seed, tol=2e-5):
+    rng = np.random.default_rng(seed)
+    V = rng.standard_normal((Q, D)).astype(np.float32)
+    alpha = np.exp(rng.uniform(-2, 6, D)).astype(np.float32)
+    beta = 37.5
+    Psi = torch.empty((Q, D), device=DEV)
+    pi = cf.cofem_apply_operator(m.h, torch.from_numpy(V).to(DEV), Q, torch.from_numpy(alpha).to(DEV), beta, Psi)
+    want = apply_A(op, V.T.astype(np.float64), alpha, beta).T
+    got = Psi.cpu().numpy()
+    for q in range(Q):
+        assert rel(got[q], want[q]) < tol, (q, rel(got[q], want[q]))
+    np.testing.assert_allclose(pi, np.sum(V.astype(np.float64) * want, axis=1), rtol=tol)
+
+
+@pytest.mark.parametrize("N,D,Q", [(77, 301, 1), (77, 301, 7), (256, 1024, 21), (130, 700, 33), (64, 128, 64),
+                                   (2500, 10000, 33)])
+def test_operator_dense_f32(cf, N, D, Q):
+    p = dense_gaussian(N, D, 3, 20.0, seed=Q)
+    with cf.CoFEM(N, D, cf.COFEM_OP_DENSE, torch.from_numpy(p.phi).to(DEV)) as m:
+        _check_operator(cf, m, DenseOperator(p.phi), D, Q, seed=Q)
+
+
+@pytest.mark.parametrize("N,D,Q", [(77, 301, 5), (256, 1024, 33), (1000, 3000, 17)])
+def test_operator_dense_bf16(cf, N, D, Q):
+    """The BF16 form runs exactly on the quantised dictionary bf16(Phi)."""
+    p = dense_gaussian(N, D, 3, 20.0, seed=Q + 1)
+    with cf.CoFEM(N, D, cf.COFEM_OP_DENSE, p.phi, precision=cf.COFEM_BF16) as m:
+        _check_operator(cf, m, DenseOperator(bf16_round(p.phi)), D, Q, seed=Q)
+
+
+@pytest.mark.parametrize("D,L,Q", [(5000, 256, 3), (3000, 256, 17), (200, 7, 2), (1793, 256, 1), (4097, 1, 4),
+                                   (3000, 1024, 2)])
+def test_operator_toeplitz(cf, D, L, Q):
+    rng = np.random.default_rng(D + L)
+    h = (double_exponential_filter(L) if L >= 16 else rng.standard_normal(L)).astype(np.float32)
+    with cf.CoFEM(D, D, cf.COFEM_OP_TOEPLITZ, h, L) as m:
+        _check_operator(cf, m, ToeplitzOperator(h, D), D, Q, seed=L)
+
+
+# ---------------------------------------------------------------------------
+# whole fits (a0-a8)
+# ---------------------------------------------------------------------------
+def test_fit_dense_n256_d1024_k20(cf):
+    """Plain FP32 form on the 256 x 1024 Gaussian workload, K = 20, T = 50, tol 1e-5."""
+    from synth import workload
+    p, run = workload("dense_n256_d1024_k20")
+    g = gpu_fit(cf, p, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], seed=run["seed"])
+    r = oracle_fit(p, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], seed=run["seed"])
+    assert_fit_close(g, r)
+    assert np.all(np.abs(g["cg_iters"] - r["cg_iters"]) <= 3)
+    assert g["flags"] == r["flags"]
+
+
+def test_fit_graph_and_direct_modes_identical(cf):
+    p = dense_gaussian(77, 301, 9, 20.0, seed=5)
+    a = gpu_fit(cf, p, 5, 6, 1e-6, 300, use_graph=1)
+    b = gpu_fit(cf, p, 5, 6, 1e-6, 300, use_graph=0)
+    for k in ("mu", "s", "alpha", "cg_iters"):
+        np.testing.assert_array_equal(a[k], b[k])
+    assert a["flags"] == b["flags"]
+
+
+def test_fit_deterministic_and_host_pointers(cf):
+    p = dense_gaussian(100, 400, 10, 25.0, seed=6)
+    a = gpu_fit(cf, p, 8, 5, 1e-6, 300)
+    b = gpu_fit(cf, p, 8, 5, 1e-6, 300, host=True)
+    for k in ("mu", "s", "alpha", "cg_iters"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+@pytest.mark.parametrize("K", [1, 5, 63])
+def test_fit_ragged_sizes_and_probe_counts(cf, K):
+    p = dense_gaussian(77, 301, 9, 20.0, seed=K)
+    g = gpu_fit(cf, p, K, 6, 1e-6, 400)
+    r = oracle_fit(p, K, 6, 1e-6, 400)
+    assert_fit_close(g, r)
+
+
+@pytest.mark.parametrize("variant", ["frobenius", "precond_one", "rr3", "alpha0"])
+def test_fit_variants(cf, variant):
+    p = dense_gaussian(120, 500, 15, 25.0, seed=11)
+    kw_g, kw_o = {}, {}
+    alpha0 = None
+    if variant == "frobenius":
+        kw_g["conv"], kw_o["conv"] = cf.COFEM_CONV_FROBENIUS, "frobenius"
+    elif variant == "precond_one":
+        kw_g["precond"], kw_o["precond"] = cf.COFEM_PRECOND_ONE, "one"
+    elif variant == "rr3":
+        kw_g["rr_period"], kw_o["rr_period"] = 3, 3
+    else:
+        alpha0 = np.exp(np.random.default_rng(0).uniform(-1, 3, 500)).astype(np.float32)
+        kw_o["alpha0"] = alpha0.astype(np.float64)
+    g = gpu_fit(cf, p, 6, 8, 1e-6, 400, alpha0=alpha0, **kw_g)
+    r = oracle_fit(p, 6, 8, 1e-6, 400, **kw_o)
+    assert_fit_close(g, r)
+
+
+def test_fit_toeplitz_small(cf):
+    p = toeplitz_calcium(6000, 256, 0.01, 15.0, seed=2)
+    g = gpu_fit(cf, p, 8, 6, 1e-6, 400)
+    r = oracle_fit(p, 8, 6, 1e-6, 400)
+    assert_fit_close(g, r)
+
+
+def test_fit_bf16_matches_oracle_on_quantised_dictionary(cf):
+    p = dense_gaussian(200, 800, 16, 25.0, seed=12)
+    g = gpu_fit(cf, p, 8, 8, 1e-6, 400, precision=cf.COFEM_BF16)
+    r = oracle_fit(p, 8, 8, 1e-6, 400, phi=bf16_round(p.phi))
+    assert_fit_close(g, r)
+
+
+def test_fit_edge_cases(cf):
+    p = dense_gaussian(50, 130, 5, 20.0, seed=1)
+    a0 = np.linspace(0.5, 2.0, 130).astype(np.float32)
+    # T = 1: no M-step, alpha^(T) = alpha0
+    g = gpu_fit(cf, p, 3, 1, 1e-6, 200, alpha0=a0)
+    np.testing.assert_array_equal(g["alpha"], a0)
+    # cg_maxit = 1: not converged flag, one iteration per EM step
+    g = gpu_fit(cf, p, 3, 2, 1e-12, 1)
+    assert g["flags"] & cf.COFEM_FLAG_CG_NOT_CONVERGED and np.all(g["cg_iters"] == 1)
+    r = oracle_fit(p, 3, 2, 1e-12, 1)
+    assert_fit_close(g, r)
+    # y = 0: b = 0, the mu column starts converged, mu = 0
+    import dataclasses
+    z = dataclasses.replace(p, y=np.zeros_like(p.y))
+    g = gpu_fit(cf, z, 3, 2, 1e-6, 200)
+    assert np.all(g["mu"] == 0.0)
+
+
+def test_fit_rejects_nonfinite_and_bad_args(cf):
+    p = dense_gaussian(20, 40, 2, 20.0, seed=1)
+    with cf.CoFEM(20, 40, cf.COFEM_OP_DENSE, p.phi) as m:
+        out = [np.empty(40, np.float32) for _ in range(3)]
+        bad = p.y.copy()
+        bad[3] = np.nan
+        with pytest.raises(cf.CofemError) as e:
+            cf.cofem_fit(m.h, bad, p.beta, None, 2, 2, 1e-5, 10, *out)
+        assert e.value.status == cf.COFEM_ERR_NONFINITE
+        with pytest.raises(cf.CofemError) as e:
+            cf.cofem_fit(m.h, p.y, -1.0, None, 2, 2, 1e-5, 10, *out)
+        assert e.value.status == cf.COFEM_ERR_INVALID_ARG
+        with pytest.raises(cf.CofemError) as e:
+            cf.cofem_fit(m.h, p.y, p.beta, None, 64, 2, 1e-5, 10, *out)
+        assert e.value.status == cf.COFEM_ERR_INVALID_ARG
+        # the handle still works after rejected calls
+        cf.cofem_fit(m.h, p.y, p.beta, None, 2, 2, 1e-5, 10, *out)
+    badphi = p.phi.copy()
+    badphi[1, 1] = np.inf
+    with pytest.raises(cf.CofemError) as e:
+        cf.cofem_create(20, 40, cf.COFEM_OP_DENSE, badphi, 0, cf.default_opts())
+    assert e.value.status == cf.COFEM_ERR_NONFINITE
