@@ -152,12 +152,15 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _launches_per_fit(cg_iters, rr_period):
-    n = 2 + 1          # b = beta Phi^T y, finiteness check of y, fit setup
+def _launches_per_fit(cg_iters, rr_period, op_kernels):
+    """Kernels of one fit: b = beta Phi^T y, finiteness check of y, fit set-up;
+    per EM iteration init + M-step; per CG step the operator kernels, update and
+    direction; per residual replacement the operator kernels and the residual."""
+    n = 3
     for u in cg_iters:
         u = int(u)
         rr = u // rr_period if rr_period > 0 else 0
-        n += 2 + 4 * u + 3 * rr   # init + mstep; per CG step: 2 operator + update + direction
+        n += 2 + (op_kernels + 2) * u + (op_kernels + 1) * rr
     return n
 
 
@@ -252,7 +255,8 @@ def run_ours(args):
     e2e = {"value": ws * e2e_steps * T / e2e_s, "unit": "EM-iter/s", "h2d_bytes_per_step": int(N * 4),
            "d2h_bytes_per_step": int(3 * D * 4 + T * 4 + 4)}
 
-    launches = sum(_launches_per_fit(it, run["rr_period"]) for it in all_iters)
+    op_kernels = 1 if prob.kind != "dense" else (5 if prec == cf.COFEM_BF16 else 2)
+    launches = sum(_launches_per_fit(it, run["rr_period"], op_kernels) for it in all_iters)
     model.close()
 
     # the FP32 form on the same problem (precision comparison at equal NMSE)

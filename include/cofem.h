@@ -71,6 +71,7 @@ typedef int cofem_status;
 #define COFEM_FLAG_CG_NOT_CONVERGED 1u /* some EM iteration hit cg_maxit with a column still active */
 #define COFEM_FLAG_ALPHA_CLAMPED    2u /* some mu_j^2 + s_j fell below 1/alpha_max and was clamped */
 #define COFEM_FLAG_BREAKDOWN        4u /* p^T A p <= 0 or non-finite in some column (column frozen) */
+#define COFEM_FLAG_DEVICE_TIMEOUT   8u /* a bounded on-device wait gave up (the call returns COFEM_ERR_CUDA) */
 
 typedef struct cofem_opts {
     int precision;            /* COFEM_F32 | COFEM_BF16 (dense only) */

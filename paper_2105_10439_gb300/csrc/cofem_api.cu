@@ -76,7 +76,12 @@ WsSizes ws_sizes(cofem_ctx* c, int Qcap) {
     WsSizes w{};
     w.xrp = (size_t)Qcap * c->Dp;
     const int QP = ((Qcap + 7) / 8) * 8;
-    if (c->kind == COFEM_OP_DENSE) {
+    if (c->kind == COFEM_OP_DENSE && c->phi16) {
+        w.u = (size_t)Qcap * c->Dp;
+        w.t = 0;
+        w.tpart = 0;
+        w.ttpart = (size_t)Qcap * ((c->Np + 1023) / 1024 + 1);
+    } else if (c->kind == COFEM_OP_DENSE) {
         w.u = (size_t)c->S2 * Qcap * c->Dp;
         w.t = (size_t)c->Np * QP;
         w.tpart = (size_t)c->S1 * c->Np * QP;
@@ -105,6 +110,7 @@ void free_workspace(cofem_ctx* c) {
     dfree(c, &c->part, w.part);
     dfree(c, &c->tt_part, w.ttpart);
     dfree(c, &c->counters, w.counters);
+    tc_release(c);
     c->Qcap = 0;
     free_graph(c);
 }
@@ -124,7 +130,7 @@ cofem_status ensure_workspace(cofem_ctx* c, int Q) {
         free_workspace(c);
         return st;
     }
-    if (c->kind == COFEM_OP_DENSE) {
+    if (c->kind == COFEM_OP_DENSE && !c->phi16) {
         if ((st = dalloc(c, &c->T, w.t)) || (st = dalloc(c, &c->Tpart, w.tpart))) {
             c->Qcap = Q;
             free_workspace(c);
@@ -132,6 +138,13 @@ cofem_status ensure_workspace(cofem_ctx* c, int Q) {
         }
     }
     c->Qcap = Q;
+    if (c->kind == COFEM_OP_DENSE && c->phi16) {
+        cudaError_t e = tc_setup(c, Q);
+        if (e != cudaSuccess) {
+            free_workspace(c);
+            return cuda_fail(e, "tensor-core operator set-up");
+        }
+    }
     CK(cudaMemsetAsync(c->counters, 0, w.counters * sizeof(unsigned), c->stream));
     CK(cudaMemsetAsync(c->X, 0, w.xrp * sizeof(float), c->stream));
     CK(cudaMemsetAsync(c->R, 0, w.xrp * sizeof(float), c->stream));
@@ -372,6 +385,8 @@ cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, c
             launch_quantize_bf16(c->stream, tmp, c->Np, c->Dp, c->Dp, c->phi16, c->Np, c->Dp);
             CKB(cudaStreamSynchronize(c->stream));
             dfree(c, &tmp, (size_t)c->Np * c->Dp);
+            if ((st = dalloc(c, &c->phiT16, (size_t)c->Np * c->Dp))) return bail(st);
+            CKB(tc_make_transpose(c, c->stream));
         } else {
             c->phi32 = tmp;
         }
@@ -403,6 +418,7 @@ cofem_status cofem_destroy(cofem_ctx* c) {
     free_graph(c);
     dfree(c, &c->phi32, (size_t)c->Np * c->Dp);
     dfree(c, &c->phi16, (size_t)c->Np * c->Dp);
+    dfree(c, &c->phiT16, (size_t)c->Np * c->Dp);
     dfree(c, &c->h, (size_t)c->L);
     dfree(c, &c->theta, (size_t)c->Dp);
     dfree(c, &c->alpha, (size_t)c->Dp);
@@ -485,6 +501,8 @@ cofem_status cofem_fit(cofem_ctx* c, const float* y, double beta, const float* a
     CK(cudaStreamSynchronize(c->stream));
     CK(cudaGetLastError());
     if (flags) *flags = hc->flags;
+    if (hc->flags & COFEM_FLAG_DEVICE_TIMEOUT)
+        return fail(COFEM_ERR_CUDA, "a bounded on-device wait timed out (tensor-core pipeline)");
     return COFEM_OK;
 }
 

@@ -199,6 +199,8 @@ struct cofem_ctx {
     // operator storage
     float* phi32 = nullptr;          // dense FP32, Np x Dp row-major, zero padded
     __nv_bfloat16* phi16 = nullptr;  // dense BF16, Np x Dp row-major, zero padded
+    __nv_bfloat16* phiT16 = nullptr; // its transpose, Dp x Np row-major (tensor-core GEMM2 operand)
+    void* tc = nullptr;              // tensor-core operator plan (kernels_tc.cu)
     float* h = nullptr;              // Toeplitz filter, L floats
     float* theta = nullptr;          // Dp
 
@@ -254,6 +256,12 @@ void launch_dot_rows(cudaStream_t st, const float* a, long long lda, const float
 void dense_configure(cofem_ctx* c, int Q);
 void launch_dense_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode);
 void launch_dense_colreduce(cudaStream_t st, cofem_ctx* c, const float* y, double scale, float* out);
+
+// kernels_tc.cu (BF16 dictionary on tcgen05 tensor cores)
+cudaError_t tc_setup(cofem_ctx* c, int Q);
+void tc_release(cofem_ctx* c);
+cudaError_t tc_make_transpose(cofem_ctx* c, cudaStream_t st);
+void launch_tc_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode);
 
 // kernels_toeplitz.cu
 size_t toeplitz_smem_bytes(int L);

@@ -183,22 +183,39 @@ void launch_pair(Sink& s, cofem_ctx* c, int Q, const float* V, int mode) {
 // Split factors for a block of Q columns.
 void dense_configure(cofem_ctx* c, int Q) {
     c->QP = ((Q + 7) / 8) * 8;
+    if (c->phi16) {   // tensor-core path: U is one Q x Dp block, T lives in the plan
+        c->S1 = 1;
+        c->S2 = 1;
+        c->chunk1 = c->Dp;
+        c->rchunk2 = c->Np;
+        return;
+    }
+    // split factors: enough blocks to cover the SMs twice, but no more than 8
+    // slices and no slice shorter than 512 columns / 128 rows (the slice
+    // partials are summed by a dependent chain in the last block)
     const long long nrb = c->Np / G1_BM;
     long long S1 = (2LL * c->num_sms + nrb - 1) / nrb;
     if (S1 < 1) S1 = 1;
+    if (S1 > 8) S1 = 8;
     long long chunk1 = ((c->Dp + S1 - 1) / S1 + G1_BK - 1) / G1_BK * G1_BK;
-    if (chunk1 < 256 && c->Dp >= 256) chunk1 = 256;
+    if (chunk1 < 512) chunk1 = 512;
     c->chunk1 = chunk1;
     c->S1 = (int)((c->Dp + chunk1 - 1) / chunk1);
     const long long ncb = c->Dp / 128;
     long long S2 = (2LL * c->num_sms + ncb - 1) / ncb;
     if (S2 < 1) S2 = 1;
+    if (S2 > 8) S2 = 8;
     long long r2 = ((c->Np + S2 - 1) / S2 + G2_BI - 1) / G2_BI * G2_BI;
+    if (r2 < 128) r2 = 128;
     c->rchunk2 = r2;
     c->S2 = (int)((c->Np + r2 - 1) / r2);
 }
 
 void launch_dense_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode) {
+    if (c->phi16) {
+        launch_tc_operator(s, c, Q, V, mode);
+        return;
+    }
     switch (c->QP / 8) {
         case 1: launch_pair<1>(s, c, Q, V, mode); break;
         case 2: launch_pair<2>(s, c, Q, V, mode); break;

@@ -23,8 +23,8 @@ def _declared():
 def cf():
     lib = os.path.join(ROOT, "paper_2105_10439_gb300", "libcofem.so")
     if not os.path.exists(lib):
-        from paper_2105_10439_gb300.build_lib import build
-        build()
+        import __graft_entry__
+        __graft_entry__.build()
     import paper_2105_10439_gb300 as m
     return m
 
