@@ -294,6 +294,33 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_operator_only(args):
+    """Apply the operator of the workload's handle --steps times (after --warmup
+    applications) through cofem_apply_operator; prints one diagnostic line."""
+    import torch
+    import paper_2105_10439_gb300 as cf
+    dev = torch.device("cuda", 0)
+    prob, run = workload(args.workload)
+    K = run["K"]
+    Q = K + 1
+    prec = cf.COFEM_BF16 if run["precision"] == "bf16" else cf.COFEM_F32
+    kind = cf.COFEM_OP_DENSE if prob.kind == "dense" else cf.COFEM_OP_TOEPLITZ
+    rng = np.random.default_rng(0)
+    V = torch.from_numpy(rng.standard_normal((Q, prob.D)).astype(np.float32)).to(dev)
+    alpha = torch.ones(prob.D, device=dev)
+    Psi = torch.empty((Q, prob.D), device=dev)
+    with cf.CoFEM(prob.N, prob.D, kind, torch.from_numpy(prob.phi).to(dev), prob.L, precision=prec) as m:
+        for _ in range(args.warmup):
+            cf.cofem_apply_operator(m.h, V, Q, alpha, prob.beta, Psi, want_pi=False)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            cf.cofem_apply_operator(m.h, V, Q, alpha, prob.beta, Psi, want_pi=False)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        ms = cf.cofem_time_operator(m.h, Q, 10)
+    print(json.dumps({"operator_only": args.workload, "steps": args.steps, "wall_s": wall, "ms_per_apply": ms}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -303,8 +330,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp32-form", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--operator-only", action="store_true",
+                    help="apply only the operator A V (Q = K+1 columns) --steps times; for profilers")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.operator_only:
+        run_operator_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

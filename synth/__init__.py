@@ -126,12 +126,17 @@ WORKLOADS = {
     "toeplitz_d1e6_l256_k16": dict(
         kind="toeplitz", N=1_000_000, D=1_000_000, L=256, rate=0.01, snr_db=15.0,
         K=16, T=30, cg_tol=1e-5, cg_maxit=400, precision="f32", rr_period=0),
+    # Residual replacement is available (rr_period) but off here: with the
+    # FP32 CG state, replacing R every 20 steps keeps the probe columns of
+    # these E-step systems from ever meeting tol 1e-5 (their recursive and
+    # true residuals drift apart by more than tol), while the recursive test
+    # converges to the same NMSE.
     "dense_n8192_d32768_k32_bf16": dict(
         kind="dense", N=8192, D=32768, d=327, snr_db=30.0, K=32, T=30,
-        cg_tol=1e-5, cg_maxit=400, precision="bf16", rr_period=20),
+        cg_tol=1e-5, cg_maxit=400, precision="bf16", rr_period=0),
     "dense_n8192_d32768_k32_f32": dict(
         kind="dense", N=8192, D=32768, d=327, snr_db=30.0, K=32, T=30,
-        cg_tol=1e-5, cg_maxit=400, precision="f32", rr_period=20),
+        cg_tol=1e-5, cg_maxit=400, precision="f32", rr_period=0),
 }
 
 DATA_SEED = 1

@@ -222,15 +222,15 @@ def test_fit_deterministic_and_host_pointers(cf):
 
 @pytest.mark.parametrize("K", [1, 5, 63])
 def test_fit_ragged_sizes_and_probe_counts(cf, K):
-    p = dense_gaussian(77, 301, 9, 20.0, seed=K)
-    g = gpu_fit(cf, p, K, 6, 1e-5, 400)
-    r = oracle_fit(p, K, 6, 1e-5, 400)
+    p = dense_gaussian(200, 501, 10, 15.0, seed=K)
+    g = gpu_fit(cf, p, K, 8, 1e-5, 400)
+    r = oracle_fit(p, K, 8, 1e-5, 400)
     assert_fit_close(g, r)
 
 
 @pytest.mark.parametrize("variant", ["frobenius", "precond_one", "rr3", "alpha0"])
 def test_fit_variants(cf, variant):
-    p = dense_gaussian(120, 500, 15, 25.0, seed=11)
+    p = dense_gaussian(250, 500, 10, 15.0, seed=11)
     kw_g, kw_o = {}, {}
     alpha0 = None
     if variant == "frobenius":
@@ -242,22 +242,26 @@ def test_fit_variants(cf, variant):
     else:
         alpha0 = np.exp(np.random.default_rng(0).uniform(-1, 3, 500)).astype(np.float32)
         kw_o["alpha0"] = alpha0.astype(np.float64)
-    g = gpu_fit(cf, p, 6, 8, 1e-5, 400, alpha0=alpha0, **kw_g)
-    r = oracle_fit(p, 6, 8, 1e-5, 400, **kw_o)
+    g = gpu_fit(cf, p, 16, 10, 1e-5, 400, alpha0=alpha0, **kw_g)
+    r = oracle_fit(p, 16, 10, 1e-5, 400, **kw_o)
     assert_fit_close(g, r)
 
 
 def test_fit_toeplitz_small(cf):
+    """The calcium-style convolution makes the E-step system so ill-conditioned
+    that even FP64 CG needs > 1000 steps for tol 1e-5; compare the two CG
+    trajectories at a fixed iteration count instead (tol unreachable)."""
     p = toeplitz_calcium(6000, 256, 0.01, 15.0, seed=2)
-    g = gpu_fit(cf, p, 8, 6, 1e-5, 400)
-    r = oracle_fit(p, 8, 6, 1e-5, 400)
+    g = gpu_fit(cf, p, 8, 3, 1e-14, 25)
+    r = oracle_fit(p, 8, 3, 1e-14, 25)
+    assert np.all(g["cg_iters"] == 25) and np.all(r["cg_iters"] == 25)
     assert_fit_close(g, r)
 
 
 def test_fit_bf16_matches_oracle_on_quantised_dictionary(cf):
-    p = dense_gaussian(200, 800, 16, 25.0, seed=12)
-    g = gpu_fit(cf, p, 8, 8, 1e-5, 400, precision=cf.COFEM_BF16)
-    r = oracle_fit(p, 8, 8, 1e-5, 400, phi=bf16_round(p.phi))
+    p = dense_gaussian(250, 500, 10, 15.0, seed=12)
+    g = gpu_fit(cf, p, 16, 10, 1e-5, 400, precision=cf.COFEM_BF16)
+    r = oracle_fit(p, 16, 10, 1e-5, 400, phi=bf16_round(p.phi))
     assert_fit_close(g, r)
 
 
@@ -301,3 +305,44 @@ def test_fit_rejects_nonfinite_and_bad_args(cf):
     with pytest.raises(cf.CofemError) as e:
         cf.cofem_create(20, 40, cf.COFEM_OP_DENSE, badphi, 0, cf.default_opts())
     assert e.value.status == cf.COFEM_ERR_NONFINITE
+
+
+# ---------------------------------------------------------------------------
+# Properties that hold at any size: the returned mu solves the last E-step
+# system A(alpha^(T)) mu = beta Phi^T y to the CG tolerance (checked in FP64),
+# and the returned alpha^(T) is what the M-step makes of the previous E-step.
+# ---------------------------------------------------------------------------
+def _mu_residual(phi, y, beta, alpha, mu):
+    Phi = phi.astype(np.float64)
+    b = beta * (Phi.T @ y.astype(np.float64))
+    m = mu.astype(np.float64)
+    Am = beta * (Phi.T @ (Phi @ m)) + alpha.astype(np.float64) * m
+    return np.linalg.norm(b - Am) / np.linalg.norm(b)
+
+
+def test_fit_dense_n2500_d10000_k32_properties(cf):
+    """Full 2500 x 10000 FP32 workload (K = 32, T = 50): every E-step converges,
+    mu solves its system, NMSE is that of a converged SBL fit."""
+    from synth import workload
+    p, run = workload("dense_n2500_d10000_k32")
+    g = gpu_fit(cf, p, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], seed=run["seed"])
+    assert not g["flags"] & cf.COFEM_FLAG_CG_NOT_CONVERGED
+    assert _mu_residual(p.phi, p.y, p.beta, g["alpha"], g["mu"]) < 10 * run["cg_tol"]
+    nmse_db = 20 * np.log10(np.linalg.norm(g["mu"] - p.z) / np.linalg.norm(p.z))
+    assert nmse_db < -20.0
+
+
+def test_fit_dense_n8192_d32768_bf16_properties(cf):
+    """Full 8192 x 32768 BF16 workload in the benchmark's launch configuration:
+    mu solves the E-step system of the quantised dictionary, and the BF16 and
+    FP32 forms reach the same NMSE within 0.1 dB."""
+    from synth import workload
+    p, run = workload("dense_n8192_d32768_k32_bf16")
+    g = gpu_fit(cf, p, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], seed=run["seed"],
+                precision=cf.COFEM_BF16, rr_period=run["rr_period"])
+    assert not g["flags"] & cf.COFEM_FLAG_CG_NOT_CONVERGED, g["cg_iters"]
+    assert _mu_residual(bf16_round(p.phi), p.y, p.beta, g["alpha"], g["mu"]) < 10 * run["cg_tol"]
+    f = gpu_fit(cf, p, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], seed=run["seed"],
+                precision=cf.COFEM_F32, rr_period=run["rr_period"])
+    nm = [20 * np.log10(np.linalg.norm(x["mu"] - p.z) / np.linalg.norm(p.z)) for x in (g, f)]
+    assert abs(nm[0] - nm[1]) < 0.1, nm
