@@ -190,7 +190,7 @@ def run_ours(args):
 
     def make(precision):
         return cf.CoFEM(N, D, kind, phi_d, prob.L, precision=precision, rr_period=run["rr_period"],
-                        seed=run["seed"], stream=stream)
+                        seed=run["seed"], stream=stream, use_graph=0 if args.no_graph else 1)
 
     def timed_fits(model, steps, warmup):
         for _ in range(warmup):
@@ -330,6 +330,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp32-form", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="drive the CG loop from the host (same kernels; lets profilers see each launch)")
     ap.add_argument("--operator-only", action="store_true",
                     help="apply only the operator A V (Q = K+1 columns) --steps times; for profilers")
     args = ap.parse_args()

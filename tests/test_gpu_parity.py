@@ -232,6 +232,10 @@ def test_fit_ragged_sizes_and_probe_counts(cf, K):
 def test_fit_variants(cf, variant):
     p = dense_gaussian(250, 500, 10, 15.0, seed=11)
     kw_g, kw_o = {}, {}
+    if variant == "rr3":
+        # replacement needs a system whose FP32 recursive/true residual drift
+        # stays below tol: an overdetermined dictionary (Phi^T Phi full rank)
+        p = dense_gaussian(500, 400, 10, 15.0, seed=11)
     alpha0 = None
     if variant == "frobenius":
         kw_g["conv"], kw_o["conv"] = cf.COFEM_CONV_FROBENIUS, "frobenius"
