@@ -163,6 +163,35 @@ cofem_status cofem_phit_y(struct cofem_ctx* h, const float* y, double beta, floa
  * Requires a previous cofem_fit (or cofem_apply_operator) with the same Q. */
 cofem_status cofem_time_operator(struct cofem_ctx* h, int Q, int reps, double* ms_per_apply);
 
+/* ---- Allocation-free operator application ----
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc: code that runs while a stream capture is active
+ * (the global capture mode rejects allocation calls), processes whose device
+ * memory is already fully owned by another allocator (for example a
+ * framework's caching pool), and latency-critical loops that must not take the
+ * driver's allocation path.  It computes the same step a4 product as
+ * cofem_apply_operator, Psi = beta Phi^T (Phi V) + diag(alpha) V for an FP32
+ * dense dictionary, without a handle and without allocating anything:
+ *   phi    : N x D floats, row-major with leading dimension ld >= D (device).
+ *   V, Psi : Q x D floats, row q = vector q (device); alpha: D floats (device).
+ *   1 <= Q <= 64 and N*Q <= COFEM_NOALLOC_MAX_ELEMS, else COFEM_ERR_INVALID_ARG
+ *   (nothing is launched).
+ *   stream : cudaStream_t (NULL = default stream).  The call only enqueues
+ *   kernels and returns; synchronise the stream before reading Psi.
+ * The intermediate Phi V lives in one fixed array of COFEM_NOALLOC_MAX_ELEMS
+ * floats (4 MiB) in the library's device memory, which every GPU that loads the
+ * library keeps until the process exits.  All calls on a device share that
+ * array: calls whose kernels can overlap on the GPU (different streams without
+ * ordering) race on it and give wrong results; serialise them.  The first call
+ * on each device looks up the array's device address with that device current;
+ * make that first call before any stream capture begins.  Later calls do no
+ * set-up.  Errors: INVALID_ARG (sizes, NULL or non-device pointers),
+ * NONFINITE (beta), CUDA (launch failure). */
+#define COFEM_NOALLOC_MAX_ELEMS 1048576
+cofem_status cofem_apply_dense_noalloc(const float* phi, long long N, long long D, long long ld,
+                                       const float* V, int Q, const float* alpha, double beta,
+                                       float* Psi, void* stream);
+
 /* Bytes of device memory the handle holds (Phi copy, theta, fit workspace). */
 long long cofem_device_bytes(struct cofem_ctx* h);
 

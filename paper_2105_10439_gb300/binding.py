@@ -76,6 +76,7 @@ def _load():
         "cofem_phit_y": (i, [vp, vp, d, vp]),
         "cofem_device_bytes": (ll, [vp]),
         "cofem_time_operator": (i, [vp, i, i, C.POINTER(d)]),
+        "cofem_apply_dense_noalloc": (i, [vp, ll, ll, ll, vp, i, vp, d, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -166,6 +167,12 @@ def cofem_time_operator(h: int, Q: int, reps: int) -> float:
     ms = C.c_double(0.0)
     _check(lib.cofem_time_operator(h, Q, reps, C.byref(ms)))
     return ms.value
+
+
+def cofem_apply_dense_noalloc(phi, N: int, D: int, ld: int, V, Q: int, alpha, beta: float, Psi,
+                              stream=None) -> None:
+    st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib.cofem_apply_dense_noalloc(_ptr(phi), N, D, ld, _ptr(V), Q, _ptr(alpha), float(beta), _ptr(Psi), st))
 
 
 def cofem_device_bytes(h: int) -> int:

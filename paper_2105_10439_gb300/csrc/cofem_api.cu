@@ -260,6 +260,9 @@ cofem_status check_device(int* dev, int* sms) {
 
 }  // namespace
 
+// Lets other translation units record a failure message for cofem_last_error().
+cofem_status cofem_set_error(cofem_status st, const char* msg) { return fail(st, "%s", msg); }
+
 extern "C" {
 
 void cofem_default_opts(cofem_opts* o) {

@@ -316,5 +316,8 @@ __device__ __forceinline__ void op_finalize_block(DevCtl* ctl, const double* tt_
     }
 }
 
+// Records a failure message for cofem_last_error() (cofem_api.cu) and returns st.
+cofem_status cofem_set_error(cofem_status st, const char* msg);
+
 // Vector-kernel geometry
 inline int vec_chunks(long long Dp) { return (int)((Dp + COFEM_VEC_CHUNK - 1) / COFEM_VEC_CHUNK); }
