@@ -55,9 +55,15 @@ typedef int cofem_status;
 
 /* Storage / multiply precision of a dense Phi (the CG state is always FP32,
  * CG inner products always FP64). */
-#define COFEM_F32   0  /* Phi kept in FP32 */
+#define COFEM_F32   0  /* Phi kept in FP32; products on the tensor cores with the
+                          error-compensated TF32 split (Phi = Phi_hi + Phi_lo and
+                          V = V_hi + V_lo with the _hi parts truncated to TF32; the
+                          products hi*hi, hi*lo, lo*hi accumulate in FP32), about
+                          2^-21 relative error per product */
 #define COFEM_BF16  1  /* Phi quantised once to bfloat16 (round to nearest even); the
-                          method then runs exactly on that quantised dictionary */
+                          method then runs exactly on that quantised dictionary (the
+                          vector block enters the tensor cores as three bf16 terms) */
+#define COFEM_F32_SIMT 2 /* Phi kept in FP32; products in FP32 FMA on the CUDA cores */
 
 /* Preconditioner theta (Sec. III-C): M = diag(beta theta + alpha). */
 #define COFEM_PRECOND_JACOBI 0  /* theta_j = sum_i Phi_ij^2  (M_jj = A_jj) */
@@ -74,7 +80,7 @@ typedef int cofem_status;
 #define COFEM_FLAG_DEVICE_TIMEOUT   8u /* a bounded on-device wait gave up (the call returns COFEM_ERR_CUDA) */
 
 typedef struct cofem_opts {
-    int precision;            /* COFEM_F32 | COFEM_BF16 (dense only) */
+    int precision;            /* COFEM_F32 | COFEM_BF16 | COFEM_F32_SIMT (the last two dense only) */
     int precond;              /* COFEM_PRECOND_JACOBI | COFEM_PRECOND_ONE */
     int conv;                 /* COFEM_CONV_PER_COLUMN | COFEM_CONV_FROBENIUS */
     int rr_period;            /* residual replacement R <- B - A X every rr_period CG
@@ -162,6 +168,63 @@ cofem_status cofem_phit_y(struct cofem_ctx* h, const float* y, double beta, floa
  * mean event time of one application (all operator kernels of one CG step).
  * Requires a previous cofem_fit (or cofem_apply_operator) with the same Q. */
 cofem_status cofem_time_operator(struct cofem_ctx* h, int Q, int reps, double* ms_per_apply);
+
+/* ---- Serving: continuous batching of independent fits ----
+ * A server runs up to max_slots fits at once, each on its own CUDA stream, so
+ * their kernels overlap on the GPU.  Requests are admitted in FIFO order as soon
+ * as a slot is idle and the request's device-memory estimate
+ * (cofem_estimate_bytes) fits in the unused part of hbm_budget_bytes; each fit
+ * is the same computation as cofem_create + cofem_fit (one graph launch with
+ * device-side EM and CG loops), so a request gives the same result alone and
+ * among others.  The server uses the device that is current when it is created. */
+typedef struct cofem_request {
+    int kind;                 /* COFEM_OP_DENSE | COFEM_OP_TOEPLITZ */
+    long long N, D, L;        /* as cofem_create */
+    const float* phi;         /* as cofem_create (host or device) */
+    const float* y;           /* N floats (host or device) */
+    double beta;
+    const float* alpha0;      /* D floats or NULL */
+    int K, T_em;
+    double cg_tol;
+    int cg_maxit;
+    int precision, precond, conv, rr_period;   /* as cofem_opts */
+    double alpha_max;         /* <= 0 means 1e12 */
+    unsigned long long seed;
+    float* mu;                /* outputs, as cofem_fit (host or device) */
+    float* s;
+    float* alpha;
+    int* cg_iters;            /* T_em ints or NULL */
+} cofem_request;              /* every pointer must stay valid until the ticket completes */
+
+typedef struct cofem_result {
+    cofem_status status;      /* status of the fit (COFEM_OK or the failing call's code) */
+    unsigned flags;           /* COFEM_FLAG_* of the fit */
+    double queue_ms;          /* submit -> a worker started the request */
+    double run_ms;            /* start -> results written */
+    char message[160];        /* error text when status != COFEM_OK */
+} cofem_result;
+
+typedef struct cofem_server cofem_server;
+
+/* Device bytes a request is admitted with (an upper estimate of what
+ * cofem_create + cofem_fit allocate for it). */
+long long cofem_estimate_bytes(int kind, long long N, long long D, long long L, int precision, int K);
+
+/* Start a server with max_slots workers (1..256) and an HBM budget in bytes. */
+cofem_status cofem_server_create(cofem_server** out, long long hbm_budget_bytes, int max_slots);
+
+/* Queue a request (never blocks on the GPU).  *ticket identifies it.  Errors:
+ * INVALID_ARG (incomplete request), NOMEM (needs more than the whole budget). */
+cofem_status cofem_submit(cofem_server* srv, const cofem_request* req, unsigned long long* ticket);
+
+/* *done = 1 once the request's outputs are written. NOT_FOUND for an unknown ticket. */
+cofem_status cofem_poll(cofem_server* srv, unsigned long long ticket, int* done);
+
+/* Block until the request completes, fill *out and forget the ticket. */
+cofem_status cofem_wait(cofem_server* srv, unsigned long long ticket, cofem_result* out);
+
+/* Finish every queued request, stop the workers and free the server. */
+cofem_status cofem_server_destroy(cofem_server* srv);
 
 /* ---- Allocation-free operator application ----
  * The paper has no counterpart to this entry point; it exists for callers

@@ -29,6 +29,7 @@ COFEM_OP_DENSE = 0
 COFEM_OP_TOEPLITZ = 1
 COFEM_F32 = 0
 COFEM_BF16 = 1
+COFEM_F32_SIMT = 2
 COFEM_PRECOND_JACOBI = 0
 COFEM_PRECOND_ONE = 1
 COFEM_CONV_PER_COLUMN = 0
@@ -49,6 +50,22 @@ class cofem_opts(C.Structure):
         ("stream", C.c_void_p),
         ("use_graph", C.c_int),
     ]
+
+
+class cofem_request(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int), ("N", C.c_longlong), ("D", C.c_longlong), ("L", C.c_longlong),
+        ("phi", C.c_void_p), ("y", C.c_void_p), ("beta", C.c_double), ("alpha0", C.c_void_p),
+        ("K", C.c_int), ("T_em", C.c_int), ("cg_tol", C.c_double), ("cg_maxit", C.c_int),
+        ("precision", C.c_int), ("precond", C.c_int), ("conv", C.c_int), ("rr_period", C.c_int),
+        ("alpha_max", C.c_double), ("seed", C.c_ulonglong),
+        ("mu", C.c_void_p), ("s", C.c_void_p), ("alpha", C.c_void_p), ("cg_iters", C.c_void_p),
+    ]
+
+
+class cofem_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("flags", C.c_uint), ("queue_ms", C.c_double), ("run_ms", C.c_double),
+                ("message", C.c_char * 160)]
 
 
 class CofemError(RuntimeError):
@@ -77,6 +94,12 @@ def _load():
         "cofem_device_bytes": (ll, [vp]),
         "cofem_time_operator": (i, [vp, i, i, C.POINTER(d)]),
         "cofem_apply_dense_noalloc": (i, [vp, ll, ll, ll, vp, i, vp, d, vp, vp]),
+        "cofem_estimate_bytes": (ll, [i, ll, ll, ll, i, i]),
+        "cofem_server_create": (i, [C.POINTER(vp), ll, i]),
+        "cofem_submit": (i, [vp, C.POINTER(cofem_request), C.POINTER(C.c_ulonglong)]),
+        "cofem_poll": (i, [vp, C.c_ulonglong, C.POINTER(i)]),
+        "cofem_wait": (i, [vp, C.c_ulonglong, C.POINTER(cofem_result)]),
+        "cofem_server_destroy": (i, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -173,6 +196,48 @@ def cofem_apply_dense_noalloc(phi, N: int, D: int, ld: int, V, Q: int, alpha, be
                               stream=None) -> None:
     st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(lib.cofem_apply_dense_noalloc(_ptr(phi), N, D, ld, _ptr(V), Q, _ptr(alpha), float(beta), _ptr(Psi), st))
+
+
+def cofem_estimate_bytes(kind: int, N: int, D: int, L: int, precision: int, K: int) -> int:
+    return int(lib.cofem_estimate_bytes(kind, N, D, L, precision, K))
+
+
+def cofem_server_create(hbm_budget_bytes: int, max_slots: int) -> int:
+    h = C.c_void_p()
+    _check(lib.cofem_server_create(C.byref(h), int(hbm_budget_bytes), int(max_slots)))
+    return h.value
+
+
+def make_request(kind, N, D, phi, y, beta, K, T_em, cg_tol, cg_maxit, mu, s, alpha, cg_iters=None, L=0,
+                 alpha0=None, **opts) -> cofem_request:
+    o = default_opts(**opts)
+    return cofem_request(kind=kind, N=N, D=D, L=L, phi=_ptr(phi), y=_ptr(y), beta=float(beta),
+                         alpha0=_ptr(alpha0, allow_none=True), K=K, T_em=T_em, cg_tol=float(cg_tol),
+                         cg_maxit=cg_maxit, precision=o.precision, precond=o.precond, conv=o.conv,
+                         rr_period=o.rr_period, alpha_max=o.alpha_max, seed=o.seed, mu=_ptr(mu), s=_ptr(s),
+                         alpha=_ptr(alpha), cg_iters=_ptr(cg_iters, np.int32, allow_none=True))
+
+
+def cofem_submit(srv: int, req: cofem_request) -> int:
+    t = C.c_ulonglong(0)
+    _check(lib.cofem_submit(srv, C.byref(req), C.byref(t)))
+    return t.value
+
+
+def cofem_poll(srv: int, ticket: int) -> bool:
+    d = C.c_int(0)
+    _check(lib.cofem_poll(srv, ticket, C.byref(d)))
+    return bool(d.value)
+
+
+def cofem_wait(srv: int, ticket: int) -> cofem_result:
+    r = cofem_result()
+    _check(lib.cofem_wait(srv, ticket, C.byref(r)))
+    return r
+
+
+def cofem_server_destroy(srv: int) -> None:
+    _check(lib.cofem_server_destroy(srv))
 
 
 def cofem_device_bytes(h: int) -> int:

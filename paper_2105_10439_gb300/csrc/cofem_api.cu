@@ -6,6 +6,7 @@
 // only involved at the start and the end of the fit.
 #include <cstdarg>
 #include <cstdio>
+#include <mutex>
 #include <cstring>
 #include <cmath>
 
@@ -37,24 +38,33 @@ cofem_status cuda_fail(cudaError_t e, const char* what) {
 
 long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
 
+// Device memory of a handle is stream-ordered (cudaMallocAsync / cudaFreeAsync
+// on the handle's stream): unlike cudaFree, releasing it does not synchronise the
+// whole device, so handles on different streams (concurrent requests) do not
+// serialise each other.
 template <typename T>
 cofem_status dalloc(cofem_ctx* c, T** p, size_t count) {
     if (*p) return COFEM_OK;
     const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
-    cudaError_t e = cudaMalloc((void**)p, bytes);
+    cudaError_t e = cudaMallocAsync((void**)p, bytes, c->stream);
     if (e != cudaSuccess) {
         *p = nullptr;
         return cuda_fail(e, "cudaMalloc");
     }
     c->bytes += (long long)bytes;
+    c->alloc_bytes[(void*)*p] = bytes;
     return COFEM_OK;
 }
 
 template <typename T>
-void dfree(cofem_ctx* c, T** p, size_t count) {
+void dfree(cofem_ctx* c, T** p, size_t /*count*/) {
     if (*p) {
-        cudaFree(*p);
-        c->bytes -= (long long)(count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+        cudaFreeAsync(*p, c->stream);
+        auto it = c->alloc_bytes.find((void*)*p);
+        if (it != c->alloc_bytes.end()) {
+            c->bytes -= (long long)it->second;
+            c->alloc_bytes.erase(it);
+        }
         *p = nullptr;
     }
 }
@@ -76,7 +86,7 @@ WsSizes ws_sizes(cofem_ctx* c, int Qcap) {
     WsSizes w{};
     w.xrp = (size_t)Qcap * c->Dp;
     const int QP = ((Qcap + 7) / 8) * 8;
-    if (c->kind == COFEM_OP_DENSE && c->phi16) {
+    if (c->kind == COFEM_OP_DENSE && c->use_tc) {
         w.u = (size_t)Qcap * c->Dp;
         w.t = 0;
         w.tpart = 0;
@@ -130,7 +140,7 @@ cofem_status ensure_workspace(cofem_ctx* c, int Q) {
         free_workspace(c);
         return st;
     }
-    if (c->kind == COFEM_OP_DENSE && !c->phi16) {
+    if (c->kind == COFEM_OP_DENSE && !c->use_tc) {
         if ((st = dalloc(c, &c->T, w.t)) || (st = dalloc(c, &c->Tpart, w.tpart))) {
             c->Qcap = Q;
             free_workspace(c);
@@ -138,7 +148,7 @@ cofem_status ensure_workspace(cofem_ctx* c, int Q) {
         }
     }
     c->Qcap = Q;
-    if (c->kind == COFEM_OP_DENSE && c->phi16) {
+    if (c->kind == COFEM_OP_DENSE && c->use_tc) {
         cudaError_t e = tc_setup(c, Q);
         if (e != cudaSuccess) {
             free_workspace(c);
@@ -247,15 +257,33 @@ cofem_status check_finite_dev(cofem_ctx* c, const float* x, long long n, const c
     return COFEM_OK;
 }
 
+// Kernel attributes that are device-wide (dynamic shared-memory limits) are set
+// once per device, before the first handle on it runs anything.
+std::mutex g_attr_mu;
+bool g_attr_done[64] = {};
+
+cofem_status set_kernel_attributes(int dev) {
+    if (dev < 0 || dev >= 64) return fail(COFEM_ERR_UNSUPPORTED, "device index too large");
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    if (g_attr_done[dev]) return COFEM_OK;
+    int optin = 0;
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    CK(tc_kernel_attributes(optin));
+    CK(toeplitz_kernel_attributes());
+    g_attr_done[dev] = true;
+    return COFEM_OK;
+}
+
 cofem_status check_device(int* dev, int* sms) {
     CK(cudaGetDevice(dev));
-    cudaDeviceProp p;
-    CK(cudaGetDeviceProperties(&p, *dev));
-    if (!(p.major == 10 && p.minor == 3))
-        return fail(COFEM_ERR_UNSUPPORTED, "libcofem is built for sm_103a (GB300); device %d is sm_%d%d (%s)", *dev,
-                    p.major, p.minor, p.name);
-    *sms = p.multiProcessorCount;
-    return COFEM_OK;
+    int major = 0, minor = 0;
+    CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, *dev));
+    CK(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, *dev));
+    if (!(major == 10 && minor == 3))
+        return fail(COFEM_ERR_UNSUPPORTED, "libcofem is built for sm_103a (GB300); device %d is sm_%d%d", *dev,
+                    major, minor);
+    CK(cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, *dev));
+    return set_kernel_attributes(*dev);
 }
 
 }  // namespace
@@ -305,8 +333,8 @@ cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, c
     if (opts) o = *opts;
     if (kind == COFEM_OP_DENSE) {
         if (L != 0) return fail(COFEM_ERR_INVALID_ARG, "L must be 0 for a dense dictionary");
-        if (o.precision != COFEM_F32 && o.precision != COFEM_BF16)
-            return fail(COFEM_ERR_INVALID_ARG, "precision must be COFEM_F32 or COFEM_BF16");
+        if (o.precision != COFEM_F32 && o.precision != COFEM_BF16 && o.precision != COFEM_F32_SIMT)
+            return fail(COFEM_ERR_INVALID_ARG, "precision must be COFEM_F32, COFEM_BF16 or COFEM_F32_SIMT");
     } else if (kind == COFEM_OP_TOEPLITZ) {
         if (N != D) return fail(COFEM_ERR_INVALID_ARG, "a convolutional dictionary needs N == D");
         if (L < 1 || L > 1024 || L > N) return fail(COFEM_ERR_INVALID_ARG, "need 1 <= L <= min(1024, N)");
@@ -335,6 +363,7 @@ cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, c
     c->num_sms = sms;
     c->Np = round_up(N, 128);
     c->Dp = round_up(D, 128);
+    c->use_tc = kind == COFEM_OP_DENSE && o.precision != COFEM_F32_SIMT;
     c->nch = vec_chunks(c->Dp);
     if (o.stream) {
         c->stream = (cudaStream_t)o.stream;
@@ -357,7 +386,7 @@ cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, c
     } while (0)
 
     if ((st = dalloc(c, &c->ctl, 1))) return bail(st);
-    CKB(cudaMallocHost((void**)&c->ctl_host, sizeof(DevCtl)));
+    c->ctl_host = new DevCtl();
     memset(c->ctl_host, 0, sizeof(DevCtl));
     if ((st = dalloc(c, &c->theta, (size_t)c->Dp)) || (st = dalloc(c, &c->alpha, (size_t)c->Dp)) ||
         (st = dalloc(c, &c->minv, (size_t)c->Dp)) || (st = dalloc(c, &c->b, (size_t)c->Dp)) ||
@@ -367,7 +396,12 @@ cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, c
     CKB(cudaMemsetAsync(c->alpha, 0, c->Dp * sizeof(float), c->stream));
     CKB(cudaMemsetAsync(c->yv, 0, c->Np * sizeof(float), c->stream));
     // a small counter block for input checks before any fit workspace exists
-    if ((st = ensure_workspace(c, 1))) return bail(st);
+    // (the tensor-core plan is made on the first fit, once Phi is resident)
+    const bool use_tc = c->use_tc;
+    c->use_tc = false;
+    st = ensure_workspace(c, 1);
+    c->use_tc = use_tc;
+    if (st) return bail(st);
 
     if (kind == COFEM_OP_DENSE) {
         // upload into a padded FP32 copy (zero rows/columns beyond N, D)
@@ -388,8 +422,6 @@ cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, c
             launch_quantize_bf16(c->stream, tmp, c->Np, c->Dp, c->Dp, c->phi16, c->Np, c->Dp);
             CKB(cudaStreamSynchronize(c->stream));
             dfree(c, &tmp, (size_t)c->Np * c->Dp);
-            if ((st = dalloc(c, &c->phiT16, (size_t)c->Np * c->Dp))) return bail(st);
-            CKB(tc_make_transpose(c, c->stream));
         } else {
             c->phi32 = tmp;
         }
@@ -421,7 +453,6 @@ cofem_status cofem_destroy(cofem_ctx* c) {
     free_graph(c);
     dfree(c, &c->phi32, (size_t)c->Np * c->Dp);
     dfree(c, &c->phi16, (size_t)c->Np * c->Dp);
-    dfree(c, &c->phiT16, (size_t)c->Np * c->Dp);
     dfree(c, &c->h, (size_t)c->L);
     dfree(c, &c->theta, (size_t)c->Dp);
     dfree(c, &c->alpha, (size_t)c->Dp);
@@ -432,7 +463,7 @@ cofem_status cofem_destroy(cofem_ctx* c) {
     dfree(c, &c->yv, (size_t)c->Np);
     dfree(c, &c->iters_dev, (size_t)c->iters_cap);
     dfree(c, &c->ctl, 1);
-    if (c->ctl_host) cudaFreeHost(c->ctl_host);
+    delete c->ctl_host;
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return COFEM_OK;
@@ -593,9 +624,9 @@ cofem_status cofem_time_operator(cofem_ctx* c, int Q, int reps, double* ms_per_a
     CK(cudaEventCreate(&e1));
     Sink s;
     s.stream = c->stream;
-    launch_operator(s, c, Q, c->P, OP_PLAIN);   // warm-up
+    launch_operator(s, c, Q, c->P, OP_TIME);   // warm-up
     CK(cudaEventRecord(e0, c->stream));
-    for (int r = 0; r < reps; ++r) launch_operator(s, c, Q, c->P, OP_PLAIN);
+    for (int r = 0; r < reps; ++r) launch_operator(s, c, Q, c->P, OP_TIME);
     CK(cudaEventRecord(e1, c->stream));
     CK(cudaEventSynchronize(e1));
     float ms = 0.0f;

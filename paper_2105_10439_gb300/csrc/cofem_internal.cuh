@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/cofem.h"
@@ -38,7 +39,14 @@ struct DevCtl {
 };
 
 // Modes of the operator kernels.
-enum OpMode { OP_CG = 0, OP_RR = 1, OP_PLAIN = 2 };
+// OP_CG: apply to P inside the CG loop (forms pi, gamma; the tensor-core path
+//        reads the split of P written by the direction kernel and leaves Psi as
+//        segment partials for the update kernel);
+// OP_RR: apply to X for residual replacement (split of X made here, partials
+//        read by the residual kernel);
+// OP_PLAIN: stand-alone application (split made here, Psi summed into U);
+// OP_TIME: the OP_CG launch sequence without touching the CG scalars (timing).
+enum OpMode { OP_CG = 0, OP_RR = 1, OP_PLAIN = 2, OP_TIME = 3 };
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) and the probe rule:
@@ -71,7 +79,11 @@ __device__ __forceinline__ float probe_sign_from_word(uint64_t word, long long j
 }
 
 // ---------------------------------------------------------------------------
-// Reductions
+// Reductions.  GB300 runs FP64 at a small fraction of the FP32 rate, so the
+// per-element work of every inner product stays in FP32 and only the
+// cross-warp, cross-block and grid levels are FP64.  All CG inner products of
+// this path (r^T r, r^T M^-1 r, p^T diag(alpha) p, ||Phi p||^2, b^T b) are sums
+// of non-negative terms, so the FP32 warp sums carry no cancellation.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -79,7 +91,30 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Block-wide sum; every thread gets the result.  `sh` needs blockDim/32 doubles.
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block sum of per-thread FP32 values: FP32 within each warp, FP64 across warps
+// (fixed order, deterministic).  The result is valid in thread 0.  `sh` needs
+// blockDim/32 doubles.
+__device__ __forceinline__ double block_sum_f(float v, double* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum_f(v);
+    __syncthreads();   // sh may still be read by a previous call
+    if (lane == 0) sh[wid] = (double)v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        r = lane < nw ? sh[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+// Block sum of FP64 values (cold paths), result valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     v = warp_sum(v);
@@ -87,25 +122,133 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     if (lane == 0) sh[wid] = v;
     __syncthreads();
     double r = 0.0;
-    for (int i = 0; i < nw; ++i) r += sh[i];   // fixed order: deterministic
+    if (wid == 0) {
+        r = lane < nw ? sh[lane] : 0.0;
+        r = warp_sum(r);
+    }
     return r;
 }
 
-// "Last block done" arrival (threadfence reduction pattern, no spinning):
-// every thread fences its own partial writes, thread 0 counts arrivals, the
-// block that arrives last gets true and resets the counter for the next launch.
+// "Last block done" arrival (threadfence reduction pattern, no spinning): the
+// block barrier orders every thread's partial writes before thread 0's
+// device-scope fence, thread 0 counts arrivals, and the block that arrives last
+// gets true (after a second fence, so its reads see all partials) and resets
+// the counter for the next launch.  One fence per block, not per thread.
 __device__ __forceinline__ bool last_block_arrive(unsigned* counter, unsigned total) {
     __shared__ int s_last;
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
         const unsigned prev = atomicAdd(counter, 1u);
         s_last = (prev == total - 1);
-        if (s_last) *counter = 0u;
+        if (s_last) {
+            __threadfence();
+            *counter = 0u;
+        }
     }
     __syncthreads();
-    if (s_last) __threadfence();
     return s_last != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core operand formats (used by kernels_tc.cu and by the vector kernels
+// that write the split direction block directly).
+// ---------------------------------------------------------------------------
+// Offset (in elements) of element (row, col) inside a tiled, 128-byte-swizzled
+// image of a matrix with `rows_per_tile` rows per 64-column tile: tile k = col/64
+// holds rows_per_tile x 64 bf16, row r at r * 64, 16-byte chunk c of the row at
+// chunk position c ^ (r & 7).
+__device__ __forceinline__ size_t swz_offset(int row, long long col, int rows_per_tile) {
+    const long long k = col >> 6;
+    const int cc = (int)(col & 63);
+    return (size_t)k * rows_per_tile * 64 + (size_t)row * 64 + (size_t)((((cc >> 3) ^ (row & 7)) << 3) | (cc & 7));
+}
+
+// v = hi + mid + lo with hi = bf16(v), mid = bf16(v - hi), lo = bf16(v - hi - mid)
+__device__ __forceinline__ void split3(float v, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+    a = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(a);
+    b = __float2bfloat16_rn(r1);
+    c = __float2bfloat16_rn(r1 - __bfloat162float(b));
+}
+
+// Write the three bf16 terms of v.x..v.w (columns j..j+3 of column q; j % 4 == 0,
+// so the four share one 16-byte chunk) into the tiled image Vs.
+__device__ __forceinline__ void store_split4(__nv_bfloat16* Vs, int QS, int q, long long j, float4 v) {
+    __nv_bfloat16 t[3][4];
+    split3(v.x, t[0][0], t[1][0], t[2][0]);
+    split3(v.y, t[0][1], t[1][1], t[2][1]);
+    split3(v.z, t[0][2], t[1][2], t[2][2]);
+    split3(v.w, t[0][3], t[1][3], t[2][3]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        *reinterpret_cast<uint2*>(Vs + swz_offset(3 * q + k, j, QS)) = *reinterpret_cast<const uint2*>(t[k]);
+}
+
+// FP32 counterpart of swz_offset: 32-column tiles of 128-byte rows, 4 floats
+// per 16-byte chunk.
+__device__ __forceinline__ size_t swz32_offset(int row, long long col, int rows_per_tile) {
+    const long long k = col >> 5;
+    const int cc = (int)(col & 31);
+    return (size_t)k * rows_per_tile * 32 + (size_t)row * 32 + (size_t)((((cc >> 2) ^ (row & 7)) << 2) | (cc & 3));
+}
+
+// TF32 split v = hi + lo with hi = v truncated to TF32 (what the tensor core
+// reads) and lo = v - hi (exact): hi at row q, lo at row QH + q of the tiled
+// fp32 image (columns j..j+3, j % 4 == 0: one 16-byte chunk).
+__device__ __forceinline__ void store_split_tf32(float* Vs, int QS, int QH, int q, long long j, float4 v) {
+    float4 hi, lo;
+    hi.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+    hi.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+    hi.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+    hi.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+    lo = make_float4(v.x - hi.x, v.y - hi.y, v.z - hi.z, v.w - hi.w);
+    *reinterpret_cast<float4*>(Vs + swz32_offset(q, j, QS)) = hi;
+    *reinterpret_cast<float4*>(Vs + swz32_offset(QH + q, j, QS)) = lo;
+}
+
+// Where the CG direction kernels write the split of P for the tensor-core
+// GEMM (fmt 0: no tensor-core operator, 1: bf16 3-term image, 2: TF32 image).
+struct SplitOut {
+    void* Vs;
+    int fmt, QS, QH;
+};
+
+__device__ __forceinline__ void store_split(const SplitOut& so, int q, long long j, float4 v) {
+    if (so.fmt == 1) store_split4((__nv_bfloat16*)so.Vs, so.QS, q, j, v);
+    else if (so.fmt == 2) store_split_tf32((float*)so.Vs, so.QS, so.QH, q, j, v);
+}
+
+// Operator output: either S2 dense slices U_s (Q x Dp each, stride sstride) or,
+// for the tensor-core path, stream-K segment partials part[seg][Q][GR] with
+// the segments of row group g listed in grp_seg[2g], grp_seg[2g+1].
+struct OpOut {
+    const float* U;
+    int S2;
+    size_t sstride;
+    const int* grp_seg;   // null for dense slices
+    int GR;
+};
+
+// Psi for elements j..j+3 of column q: beta * (Phi^T Phi v) + alpha_j v_j.
+__device__ __forceinline__ float4 psi4(const OpOut& o, int Q, int q, long long Dp, long long j, float beta,
+                                       float4 av, float4 vv) {
+    float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (o.grp_seg) {
+        const int g = (int)(j / o.GR), r = (int)(j % o.GR);
+        const int s0 = o.grp_seg[2 * g], ns = o.grp_seg[2 * g + 1];
+        for (int s = 0; s < ns; ++s) {
+            const float4 w = *reinterpret_cast<const float4*>(o.U + ((size_t)(s0 + s) * Q + q) * o.GR + r);
+            u.x += w.x; u.y += w.y; u.z += w.z; u.w += w.w;
+        }
+    } else {
+        for (int s = 0; s < o.S2; ++s) {
+            const float4 w = *reinterpret_cast<const float4*>(o.U + (size_t)s * o.sstride + (size_t)q * Dp + j);
+            u.x += w.x; u.y += w.y; u.z += w.z; u.w += w.w;
+        }
+    }
+    return make_float4(beta * u.x + av.x * vv.x, beta * u.y + av.y * vv.y, beta * u.z + av.z * vv.z,
+                       beta * u.w + av.w * vv.w);
 }
 
 // ---------------------------------------------------------------------------
@@ -199,8 +342,8 @@ struct cofem_ctx {
     // operator storage
     float* phi32 = nullptr;          // dense FP32, Np x Dp row-major, zero padded
     __nv_bfloat16* phi16 = nullptr;  // dense BF16, Np x Dp row-major, zero padded
-    __nv_bfloat16* phiT16 = nullptr; // its transpose, Dp x Np row-major (tensor-core GEMM2 operand)
     void* tc = nullptr;              // tensor-core operator plan (kernels_tc.cu)
+    bool use_tc = false;             // dense dictionary applied on the tensor cores
     float* h = nullptr;              // Toeplitz filter, L floats
     float* theta = nullptr;          // Dp
 
@@ -230,6 +373,7 @@ struct cofem_ctx {
     int graph_Q = -1;
 
     long long bytes = 0;
+    std::unordered_map<void*, size_t> alloc_bytes;   // size of every live device allocation
 };
 
 // ---------------------------------------------------------------------------
@@ -259,13 +403,18 @@ void launch_dense_colreduce(cudaStream_t st, cofem_ctx* c, const float* y, doubl
 
 // kernels_tc.cu (BF16 dictionary on tcgen05 tensor cores)
 cudaError_t tc_setup(cofem_ctx* c, int Q);
+cudaError_t tc_kernel_attributes(int max_smem);
 void tc_release(cofem_ctx* c);
-cudaError_t tc_make_transpose(cofem_ctx* c, cudaStream_t st);
 void launch_tc_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode);
+// Split image of the CG direction block (written by k_cg_init / k_cg_direction)
+// and the description of the operator output (null / dense slices otherwise).
+SplitOut tc_direction_split(cofem_ctx* c);
+OpOut op_output(cofem_ctx* c);
 
 // kernels_toeplitz.cu
 size_t toeplitz_smem_bytes(int L);
 cudaError_t toeplitz_prepare(int L);
+cudaError_t toeplitz_kernel_attributes();
 void launch_toeplitz_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode);
 void launch_toeplitz_theta(cudaStream_t st, cofem_ctx* c);
 void launch_toeplitz_phit_y(cudaStream_t st, cofem_ctx* c, const float* y, double scale, float* out);
@@ -294,26 +443,26 @@ __device__ __forceinline__ void op_finalize_block(DevCtl* ctl, const double* tt_
         if (lane == 0) s_tt[q] = v;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const double beta = ctl->beta;
-        int any = 0;
-        for (int q = 0; q < Q; ++q) {
-            ctl->tt[q] = s_tt[q];
-            if (mode == OP_CG && ctl->active[q]) {
-                const double pi = beta * s_tt[q] + ctl->ap[q];
-                ctl->pi[q] = pi;
-                if (!(pi > 0.0) || !isfinite(pi)) {
-                    ctl->flags |= COFEM_FLAG_BREAKDOWN;
-                    ctl->active[q] = 0;
-                    ctl->gamma[q] = 0.0;
-                } else {
-                    ctl->gamma[q] = ctl->rho[q] / pi;
-                }
+    // one column per thread (the block has at least COFEM_QMAX threads)
+    const int q = threadIdx.x;
+    int act = 0;
+    if (q < Q) {
+        ctl->tt[q] = s_tt[q];
+        if (mode == OP_CG && ctl->active[q]) {
+            const double pi = ctl->beta * s_tt[q] + ctl->ap[q];
+            ctl->pi[q] = pi;
+            if (!(pi > 0.0) || !isfinite(pi)) {
+                atomicOr(&ctl->flags, COFEM_FLAG_BREAKDOWN);
+                ctl->active[q] = 0;
+                ctl->gamma[q] = 0.0;
+            } else {
+                ctl->gamma[q] = ctl->rho[q] / pi;
             }
-            any |= ctl->active[q];
         }
-        if (mode == OP_CG) ctl->any_active = any;
+        act = ctl->active[q];
     }
+    act = __syncthreads_or(act);
+    if (threadIdx.x == 0 && mode == OP_CG) ctl->any_active = act;
 }
 
 // Records a failure message for cofem_last_error() (cofem_api.cu) and returns st.

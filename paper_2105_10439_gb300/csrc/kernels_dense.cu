@@ -86,9 +86,14 @@ __global__ __launch_bounds__(256) void k_gemm1_simt(const TPhi* __restrict__ phi
         sT[r][qq] = v;
     }
     __syncthreads();
-    if (tid < Q) {
+    if (tid < Q) {   // ||T_q||^2 over this row block: FP32 runs of 8 rows, FP64 across them
         double a = 0.0;
-        for (int r = 0; r < G1_BM; ++r) a += (double)sT[r][tid] * (double)sT[r][tid];
+        for (int r0 = 0; r0 < G1_BM; r0 += 8) {
+            float f = 0.0f;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) f = fmaf(sT[r0 + r][tid], sT[r0 + r][tid], f);
+            a += (double)f;
+        }
         tt_part[(size_t)tid * nrb + rb] = a;
     }
     if (!last_block_arrive(cnt_all, (unsigned)nrb)) return;
@@ -183,7 +188,7 @@ void launch_pair(Sink& s, cofem_ctx* c, int Q, const float* V, int mode) {
 // Split factors for a block of Q columns.
 void dense_configure(cofem_ctx* c, int Q) {
     c->QP = ((Q + 7) / 8) * 8;
-    if (c->phi16) {   // tensor-core path: U is one Q x Dp block, T lives in the plan
+    if (c->use_tc) {   // tensor-core path: T and the partial sums live in the plan
         c->S1 = 1;
         c->S2 = 1;
         c->chunk1 = c->Dp;
@@ -212,7 +217,7 @@ void dense_configure(cofem_ctx* c, int Q) {
 }
 
 void launch_dense_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode) {
-    if (c->phi16) {
+    if (c->use_tc) {
         launch_tc_operator(s, c, Q, V, mode);
         return;
     }

@@ -12,6 +12,13 @@
 // applied to the quantised dictionary at FP32 accuracy.  Term t of column q is
 // B row 3q + t; the epilogue adds the three accumulator columns back.
 //
+// Memory layout: the library's copies of Phi~ and Phi~^T are stored pre-tiled,
+// each 128 x 64 tile as the exact 128-byte-swizzled shared-memory image the
+// MMA reads (16 KiB contiguous), tiles ordered (group, k tile, row tile), so the
+// range of work units of one CTA is one contiguous run of HBM, fetched with 1-D
+// bulk copies.  The B operands (split vector blocks) are written in the same
+// per-k-tile swizzled image by the kernels that produce them.
+//
 // The GEMM kernel is persistent (one CTA per SM) and stream-K: the work units
 // (group of G row tiles of 128 rows, one 64-wide k tile) are split into equal
 // contiguous ranges, one per CTA; the B tile of a k step is reused by the G A
@@ -24,8 +31,6 @@
 // sub-partition).  Every mbarrier wait is bounded: on timeout the kernel sets
 // COFEM_FLAG_DEVICE_TIMEOUT, waits (bounded) for its in-flight copies and MMAs,
 // frees TMEM and returns.
-#include <cuda.h>
-
 #include <algorithm>
 #include <vector>
 
@@ -33,14 +38,17 @@
 
 namespace {
 
-constexpr int TC_BM = 128, TC_BK = 64;
-constexpr int TC_NA = 8, TC_NB = 3;
+constexpr int TC_BM = 128, TC_BK = 64;   // BF16 tile: 128 rows x 64 bf16 (128-byte rows)
+constexpr int TC_BK32 = 32;               // TF32 tile: 128 rows x 32 fp32 (128-byte rows)
+constexpr int TC_NA = 8, TC_NA_TF = 5, TC_NB = 3;
 constexpr int TC_THREADS = 192;
 constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK * 2;
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
 constexpr uint32_t TC_TMEM_COLS = 512;
 
 struct TcParams {
+    const void* A;        // tiled A image: unit u, row tile r at byte (u * G + r) * 16384
+    const void* B;        // tiled B image: k tile at byte k * QS * 128
     long long W;          // work units = groups * K_tiles
     int K_tiles;          // 64-wide k tiles
     int M_tiles;          // 128-row tiles
@@ -48,7 +56,9 @@ struct TcParams {
     int acc_stride;       // TMEM columns per accumulator
     int QS;               // MMA N (3 Q rounded up to 16)
     int Q;                // output columns
-    uint32_t idesc;       // tcgen05 instruction descriptor
+    uint32_t idesc;       // tcgen05 instruction descriptor (N = QS)
+    uint32_t idesc_lo;    // TF32: descriptor of the Phi_lo product (N = QH)
+    int QH;               // TF32: row of the first P_lo term in B
     const int* seg_base;  // first segment id of each CTA
     float* part;          // [segment][Q][G * 128]
     unsigned* flags;      // error flag word (DevCtl::flags)
@@ -96,11 +106,19 @@ __device__ __noinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
     }
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+// 1-D bulk copy global -> shared, completion counted on an mbarrier.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"((uint64_t)src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// Same, with an L2 policy (evict-first for data streamed once).
+__device__ __forceinline__ void bulk_load_hint(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar,
+                                               uint64_t policy) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            dst),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(dst),
+        "l"((uint64_t)src), "r"(bytes), "r"(bar), "l"(policy)
         : "memory");
 }
 
@@ -116,6 +134,13 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accum));
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accum));
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -141,19 +166,28 @@ __device__ __forceinline__ void tmem_ld_wait(uint32_t* r, int n) {
                      "+r"(r[i + 5]), "+r"(r[i + 6]), "+r"(r[i + 7]));
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcParams p) {
+// Tensor-core skinny GEMM.  TF = false: A, B bf16 (B = 3-term split), one MMA
+// chain per tile.  TF = true: A, B fp32 read as TF32 (B = [P_hi | P_lo]); the
+// epilogue warps also write Phi_lo = A - tf32(A) next to each A tile and a
+// second MMA chain adds Phi_lo * P_hi into the same accumulator columns.
+template <bool TF>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
+    constexpr int NA = TF ? TC_NA_TF : TC_NA;
+    constexpr int KE = TF ? TC_BK32 : TC_BK;    // elements per 128-byte tile row
+    constexpr int KM = TF ? 8 : 16;             // K of one MMA instruction
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t B_BYTES = (uint32_t)p.QS * 128u;
     uint8_t* ringA = smem;
-    uint8_t* ringB = smem + TC_NA * TC_A_BYTES;
+    uint8_t* ringL = smem + NA * TC_A_BYTES;                      // TF32 only: Phi_lo tiles
+    uint8_t* ringB = ringL + (TF ? NA * TC_A_BYTES : 0);
     uint64_t* bars = (uint64_t*)(ringB + TC_NB * B_BYTES);
     uint64_t* a_full = bars;
-    uint64_t* a_empty = bars + TC_NA;
-    uint64_t* b_full = bars + 2 * TC_NA;
-    uint64_t* b_empty = bars + 2 * TC_NA + TC_NB;
-    uint64_t* acc_full = bars + 2 * TC_NA + 2 * TC_NB;
+    uint64_t* a_empty = bars + NA;
+    uint64_t* lo_full = bars + 2 * NA;                            // TF32 only
+    uint64_t* b_full = bars + 3 * NA;
+    uint64_t* b_empty = bars + 3 * NA + TC_NB;
+    uint64_t* acc_full = bars + 3 * NA + 2 * TC_NB;
     uint64_t* acc_empty = acc_full + 1;
     uint64_t* drain = acc_full + 2;
     uint32_t* tmem_slot = (uint32_t*)(acc_full + 3);
@@ -161,9 +195,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < TC_NA; ++i) {
+        for (int i = 0; i < NA; ++i) {
             mbar_init(smem_u32(a_full + i), 1);
             mbar_init(smem_u32(a_empty + i), 1);
+            mbar_init(smem_u32(lo_full + i), 4);
         }
         for (int i = 0; i < TC_NB; ++i) {
             mbar_init(smem_u32(b_full + i), 1);
@@ -189,13 +224,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     const long long u0 = (long long)blockIdx.x * p.W / gridDim.x;
     const long long u1 = (long long)(blockIdx.x + 1) * p.W / gridDim.x;
-    long long na = 0, nb = 0;   // TMA loads issued into the A and B rings (producer thread)
+    long long na = 0, nb = 0;   // bulk loads issued into the A and B rings (producer thread)
+    const char* Ab = (const char*)p.A;
+    const char* Bb = (const char*)p.B;
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- TMA producer ----------------
-            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapA) : "memory");
-            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapB) : "memory");
+            // ---------------- bulk-copy producer ----------------
+            uint64_t evict_first;
+            asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(evict_first));
             for (long long u = u0; u < u1; ++u) {
                 const int g = (int)(u / p.K_tiles), k = (int)(u % p.K_tiles);
                 const int valid = min(p.G, p.M_tiles - g * p.G);
@@ -203,19 +240,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 long long use = nb / TC_NB;
                 if (use > 0 && !mbar_wait(smem_u32(b_empty + slot), (uint32_t)((use - 1) & 1), abort_flag)) break;
                 mbar_expect_tx(smem_u32(b_full + slot), B_BYTES);
-                tma_load_2d(smem_u32(ringB + slot * B_BYTES), &mapB, k * TC_BK, 0, smem_u32(b_full + slot));
+                bulk_load(smem_u32(ringB + slot * B_BYTES), Bb + (size_t)k * B_BYTES, B_BYTES, smem_u32(b_full + slot));
                 ++nb;
                 bool ok = true;
                 for (int r = 0; r < valid; ++r) {
-                    slot = (int)(na % TC_NA);
-                    use = na / TC_NA;
+                    slot = (int)(na % NA);
+                    use = na / NA;
                     if (use > 0 && !mbar_wait(smem_u32(a_empty + slot), (uint32_t)((use - 1) & 1), abort_flag)) {
                         ok = false;
                         break;
                     }
                     mbar_expect_tx(smem_u32(a_full + slot), TC_A_BYTES);
-                    tma_load_2d(smem_u32(ringA + slot * TC_A_BYTES), &mapA, k * TC_BK, (g * p.G + r) * TC_BM,
-                                smem_u32(a_full + slot));
+                    bulk_load_hint(smem_u32(ringA + slot * TC_A_BYTES), Ab + ((size_t)u * p.G + r) * TC_A_BYTES,
+                                   TC_A_BYTES, smem_u32(a_full + slot), evict_first);
                     ++na;
                 }
                 if (!ok) break;
@@ -243,8 +280,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     const uint64_t db = desc_sw128(smem_u32(ringB + sb * B_BYTES));
                     for (int r = 0; r < valid; ++r) {
-                        const int sa = (int)(ma % TC_NA);
-                        if (!mbar_wait(smem_u32(a_full + sa), (uint32_t)((ma / TC_NA) & 1), abort_flag)) {
+                        const int sa = (int)(ma % NA);
+                        const uint32_t par = (uint32_t)((ma / NA) & 1);
+                        if (!mbar_wait(smem_u32(a_full + sa), par, abort_flag)) {
                             ok = false;
                             break;
                         }
@@ -252,9 +290,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         const uint64_t da = desc_sw128(smem_u32(ringA + sa * TC_A_BYTES));
                         const uint32_t dt = tmem + (uint32_t)(r * p.acc_stride);
 #pragma unroll
-                        for (int kk = 0; kk < TC_BK / 16; ++kk)
-                            mma_bf16(dt, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), p.idesc,
-                                     (u > seg_start || kk > 0) ? 1u : 0u);
+                        for (int kk = 0; kk < KE / KM; ++kk) {
+                            const uint32_t acc = (u > seg_start || kk > 0) ? 1u : 0u;
+                            if (TF) mma_tf32(dt, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), p.idesc, acc);
+                            else mma_bf16(dt, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), p.idesc, acc);
+                        }
+                        if (TF) {
+                            if (!mbar_wait(smem_u32(lo_full + sa), par, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint64_t dl = desc_sw128(smem_u32(ringL + sa * TC_A_BYTES));
+#pragma unroll
+                            for (int kk = 0; kk < KE / KM; ++kk)
+                                mma_tf32(dt, dl + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), p.idesc_lo, 1u);
+                        }
                         mma_commit(smem_u32(a_empty + sa));
                         ++ma;
                     }
@@ -271,16 +322,48 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_drain(smem_u32(drain), 0);
         }
     } else {
-        // ---------------- epilogue: TMEM -> partial sums ----------------
+        // ------- epilogue warps: (TF32) Phi_lo tiles; TMEM -> partial sums -------
         const int sub = warp & 3;
+        const int ew = warp - 2;
         const int GR = p.G * TC_BM;
         const int NC = p.QS / 16;
         int nseg = 0;
+        long long ne = 0;   // A tiles converted
         long long u = u0;
-        while (u < u1) {
+        bool ok = true;
+        while (u < u1 && ok) {
             const int g = (int)(u / p.K_tiles);
             const long long seg_end = min(u1, (long long)(g + 1) * p.K_tiles);
             const int valid = min(p.G, p.M_tiles - g * p.G);
+            if (TF) {
+                for (long long uu = u; uu < seg_end && ok; ++uu) {
+                    for (int r = 0; r < valid; ++r) {
+                        const int sa = (int)(ne % NA);
+                        if (!mbar_wait(smem_u32(a_full + sa), (uint32_t)((ne / NA) & 1), abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        // this warp's quarter of the tile: 1024 floats, 8 float4 per lane
+                        const float4* src = reinterpret_cast<const float4*>(ringA + sa * TC_A_BYTES) + ew * 256;
+                        float4* dst = reinterpret_cast<float4*>(ringL + sa * TC_A_BYTES) + ew * 256;
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const float4 x = src[lane + 32 * i];
+                            float4 l;
+                            l.x = x.x - __uint_as_float(__float_as_uint(x.x) & 0xFFFFE000u);
+                            l.y = x.y - __uint_as_float(__float_as_uint(x.y) & 0xFFFFE000u);
+                            l.z = x.z - __uint_as_float(__float_as_uint(x.z) & 0xFFFFE000u);
+                            l.w = x.w - __uint_as_float(__float_as_uint(x.w) & 0xFFFFE000u);
+                            dst[lane + 32 * i] = l;
+                        }
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(lo_full + sa));
+                        ++ne;
+                    }
+                }
+                if (!ok) break;
+            }
             if (!mbar_wait(smem_u32(acc_full), (uint32_t)(nseg & 1), abort_flag)) break;
             tc_fence_after();
             float* out = p.part + (size_t)(p.seg_base[blockIdx.x] + nseg) * p.Q * GR;
@@ -289,18 +372,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const uint32_t tbase = tmem + ((uint32_t)(32 * sub) << 16) + (uint32_t)(r * p.acc_stride);
                 for (int qb = 0; qb * 16 < p.Q; ++qb) {
                     uint32_t v[48];
-                    const int c0 = 3 * qb;
+                    if (TF) {
+                        tmem_ld16(tbase + (uint32_t)(qb * 16), v);
+                        tmem_ld16(tbase + (uint32_t)(p.QH + qb * 16), v + 16);
+                        tmem_ld_wait(v, 32);
+                    } else {
+                        const int c0 = 3 * qb;
 #pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        if (c0 + c < NC) tmem_ld16(tbase + (uint32_t)((c0 + c) * 16), v + 16 * c);
-                    tmem_ld_wait(v, 48);
+                        for (int c = 0; c < 3; ++c)
+                            if (c0 + c < NC) tmem_ld16(tbase + (uint32_t)((c0 + c) * 16), v + 16 * c);
+                        tmem_ld_wait(v, 48);
+                    }
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         const int q = 16 * qb + i;
-                        if (q < p.Q)
-                            out[(size_t)q * GR + r * TC_BM + row] =
-                                __uint_as_float(v[3 * i]) + __uint_as_float(v[3 * i + 1]) +
-                                __uint_as_float(v[3 * i + 2]);
+                        if (q < p.Q) {
+                            const float val = TF ? __uint_as_float(v[i]) + __uint_as_float(v[16 + i])
+                                                 : __uint_as_float(v[3 * i]) + __uint_as_float(v[3 * i + 1]) +
+                                                       __uint_as_float(v[3 * i + 2]);
+                            out[(size_t)q * GR + r * TC_BM + row] = val;
+                        }
                     }
                 }
             }
@@ -316,8 +407,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (threadIdx.x == 0 && *abort_flag) {
         // some role gave up: the latest load issued into every ring slot must
         // land before the CTA exits
-        for (int s = 0; s < TC_NA; ++s) {
-            const long long n_s = na > s ? (na - s + TC_NA - 1) / TC_NA : 0;
+        for (int s = 0; s < NA; ++s) {
+            const long long n_s = na > s ? (na - s + NA - 1) / NA : 0;
             if (n_s > 0) mbar_drain(smem_u32(a_full + s), (uint32_t)((n_s - 1) & 1));
         }
         for (int s = 0; s < TC_NB; ++s) {
@@ -333,40 +424,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (threadIdx.x == 0 && *abort_flag) atomicOr(p.flags, COFEM_FLAG_DEVICE_TIMEOUT);
 }
 
-// v = hi + mid + lo with hi = bf16(v), mid = bf16(v - hi), lo = bf16(v - hi - mid)
-__device__ __forceinline__ void split3(float v, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
-    a = __float2bfloat16_rn(v);
-    const float r1 = v - __bfloat162float(a);
-    b = __float2bfloat16_rn(r1);
-    c = __float2bfloat16_rn(r1 - __bfloat162float(b));
-}
-
-// Vs (QS x ld, bf16), row 3q + t = term t of column q of V (Q x Dp, FP32).
-__global__ void k_split3(const float* __restrict__ V, long long Dp, __nv_bfloat16* __restrict__ Vs, long long ld) {
+// Vs = tiled swizzled image of the split of V (Q x Dp, FP32): bf16 3-term
+// (fmt 1, row 3q + t) or TF32 hi / lo (fmt 2, rows q and QH + q).
+__global__ void k_split(const float* __restrict__ V, long long Dp, SplitOut so) {
     const int q = blockIdx.y;
     const long long j = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (j >= Dp) return;
-    const float4 v = *reinterpret_cast<const float4*>(V + (size_t)q * Dp + j);
-    __nv_bfloat16 t[3][4];
-    split3(v.x, t[0][0], t[1][0], t[2][0]);
-    split3(v.y, t[0][1], t[1][1], t[2][1]);
-    split3(v.z, t[0][2], t[1][2], t[2][2]);
-    split3(v.w, t[0][3], t[1][3], t[2][3]);
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-        *reinterpret_cast<uint2*>(Vs + (size_t)(3 * q + k) * ld + j) = *reinterpret_cast<const uint2*>(t[k]);
+    store_split(so, q, j, *reinterpret_cast<const float4*>(V + (size_t)q * Dp + j));
 }
 
 // GEMM1 epilogue: T = sum of the segment partials of its group (fixed order),
-// split into bf16 terms for GEMM2, and ||T_q||^2 partials -> pi, gamma.
+// split into the B image of GEMM2, and ||T_q||^2 partials -> pi, gamma.
 __global__ __launch_bounds__(256) void k_tc_reduce_T(const float* __restrict__ part, const int* __restrict__ grp_seg,
-                                                     int GR, int Q, long long Np, __nv_bfloat16* __restrict__ Ts,
-                                                     double* tt_part, int nblk, unsigned* counter, DevCtl* ctl,
-                                                     int mode) {
+                                                     int GR, int Q, long long Np, SplitOut so, double* tt_part,
+                                                     int nblk, unsigned* counter, DevCtl* ctl, int mode) {
     __shared__ double sh[8];
     const int q = blockIdx.y;
     const long long i = (long long)blockIdx.x * 1024 + threadIdx.x * 4;
-    double tt = 0.0;
+    float tt = 0.0f;
     if (i < Np) {
         const int g = (int)(i / GR), r = (int)(i % GR);
         const int s0 = grp_seg[2 * g], ns = grp_seg[2 * g + 1];
@@ -375,23 +450,17 @@ __global__ __launch_bounds__(256) void k_tc_reduce_T(const float* __restrict__ p
             const float4 b = *reinterpret_cast<const float4*>(part + ((size_t)(s0 + s) * Q + q) * GR + r);
             a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
         }
-        __nv_bfloat16 t[3][4];
-        split3(a.x, t[0][0], t[1][0], t[2][0]);
-        split3(a.y, t[0][1], t[1][1], t[2][1]);
-        split3(a.z, t[0][2], t[1][2], t[2][2]);
-        split3(a.w, t[0][3], t[1][3], t[2][3]);
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-            *reinterpret_cast<uint2*>(Ts + (size_t)(3 * q + k) * Np + i) = *reinterpret_cast<const uint2*>(t[k]);
-        tt = (double)a.x * a.x + (double)a.y * a.y + (double)a.z * a.z + (double)a.w * a.w;
+        store_split(so, q, i, a);
+        tt = a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
     }
-    tt = block_sum(tt, sh);
-    if (threadIdx.x == 0) tt_part[(size_t)q * nblk + blockIdx.x] = tt;
+    const double ttd = block_sum_f(tt, sh);
+    if (threadIdx.x == 0) tt_part[(size_t)q * nblk + blockIdx.x] = ttd;
     if (!last_block_arrive(counter, gridDim.x * gridDim.y)) return;
     op_finalize_block(ctl, tt_part, nblk, Q, mode);
 }
 
-// GEMM2 epilogue: U (Q x Dp) = sum of the segment partials of its group.
+// GEMM2 epilogue for a stand-alone application: U (Q x Dp) = sum of the
+// segment partials of its group.
 __global__ __launch_bounds__(256) void k_tc_reduce_U(const float* __restrict__ part, const int* __restrict__ grp_seg,
                                                      int GR, int Q, long long Dp, float* __restrict__ U) {
     const int q = blockIdx.y;
@@ -407,93 +476,93 @@ __global__ __launch_bounds__(256) void k_tc_reduce_U(const float* __restrict__ p
     *reinterpret_cast<float4*>(U + (size_t)q * Dp + j) = a;
 }
 
-// dst (cols x rows) = src^T (rows x cols), bf16, 32 x 32 tiles.
-__global__ void k_transpose_bf16(const __nv_bfloat16* __restrict__ src, long long rows, long long cols,
-                                 __nv_bfloat16* __restrict__ dst) {
-    __shared__ __nv_bfloat16 tile[32][33];
-    const long long c0 = (long long)blockIdx.x * 32, r0 = (long long)blockIdx.y * 32;
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const long long r = r0 + k, c = c0 + threadIdx.x;
-        if (r < rows && c < cols) tile[k][threadIdx.x] = src[r * cols + c];
+// A image of GEMM1: tile (g, k, r) = rows (g G + r) 128 .. +127 and the k-th
+// 128-byte column block of the row-major dictionary (ld elements per row),
+// each row's eight 16-byte chunks swizzled (chunk c at c ^ (row & 7)); zero
+// tiles beyond M_tiles.  TE = element type (64 bf16 or 32 fp32 per row).
+template <typename TE>
+__global__ __launch_bounds__(128) void k_tile_rows(const TE* __restrict__ src, long long ld, int M_tiles, int K_tiles,
+                                                   int G, TE* __restrict__ dst) {
+    constexpr int KE = 128 / sizeof(TE);
+    const int k = blockIdx.x, gr = blockIdx.y, g = gr / G, r = gr % G;
+    const int m = g * G + r, rr = threadIdx.x;
+    char* tile = (char*)dst + (((size_t)g * K_tiles + k) * G + r) * TC_A_BYTES;
+    const uint4* s4 = reinterpret_cast<const uint4*>(src + ((size_t)m * TC_BM + rr) * ld + (size_t)k * KE);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const uint4 v = m < M_tiles ? s4[c] : make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(tile + rr * 128 + ((c ^ (rr & 7)) << 4)) = v;
     }
+}
+
+// A image of GEMM2 (rows of the transpose = columns of the dictionary): tile
+// (g, k, r) holds element (rr, cc) = src[k KE + cc][(g G + r) 128 + rr], swizzled.
+template <typename TE>
+__global__ __launch_bounds__(128) void k_tile_cols(const TE* __restrict__ src, long long ld, int M_tiles, int K_tiles,
+                                                   int G, TE* __restrict__ dst) {
+    constexpr int KE = 128 / sizeof(TE), PER = 16 / sizeof(TE);
+    __shared__ TE sm[KE][TC_BM + 8];
+    const int k = blockIdx.x, gr = blockIdx.y, g = gr / G, r = gr % G;
+    const int m = g * G + r, t = threadIdx.x;
+    for (int n = 0; n < KE; ++n) sm[n][t] = m < M_tiles ? src[((size_t)k * KE + n) * ld + (size_t)m * TC_BM + t] : TE(0.0f);
     __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const long long c = c0 + k, r = r0 + threadIdx.x;
-        if (r < rows && c < cols) dst[c * rows + r] = tile[threadIdx.x][k];
+    char* tile = (char*)dst + (((size_t)g * K_tiles + k) * G + r) * TC_A_BYTES;
+    for (int c = 0; c < 8; ++c) {
+        TE v[PER];
+#pragma unroll
+        for (int e = 0; e < PER; ++e) v[e] = sm[c * PER + e][t];
+        *reinterpret_cast<uint4*>(tile + t * 128 + ((c ^ (t & 7)) << 4)) = *reinterpret_cast<const uint4*>(v);
     }
 }
 
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn get_encoder() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        void* f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)f;
-    }
-    return fn;
-}
-
-// 2-D bf16 row-major matrix (rows x cols, leading dimension ld elements),
-// box = box_rows x 64 columns, 128-byte swizzle.
-bool encode_map(CUtensorMap* m, const void* base, long long rows, long long cols, long long ld, int box_rows) {
-    EncodeTiledFn enc = get_encoder();
-    if (!enc) return false;
-    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-    const cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
-    const cuuint32_t estr[2] = {1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 struct GemmPlan {
     TcParams p{};
     int nCTA = 0;
     int nseg = 0, groups = 0;
-    int* seg_base = nullptr;   // device
-    int* grp_seg = nullptr;    // device
-    float* part = nullptr;     // device
-    CUtensorMap mapA, mapB;
+    int* seg_base = nullptr;         // device
+    int* grp_seg = nullptr;          // device
+    float* part = nullptr;           // device
+    void* A = nullptr;               // device, tiled image of the A operand
+    size_t A_bytes = 0;
 };
 
 struct TcPlan {
-    int Q = 0, QS = 0, G = 0;
+    bool tf = false;                 // TF32 format (FP32 dictionary)
+    int Q = 0, QS = 0, QH = 0, G = 0;
     size_t smem = 0;
-    __nv_bfloat16* Vs = nullptr;   // QS x Dp
-    __nv_bfloat16* Ts = nullptr;   // QS x Np
+    void* Vs = nullptr;              // tiled image of split(P), QS x Dp
+    void* Ts = nullptr;              // tiled image of split(T), QS x Np
+    size_t esz = 2;                  // bytes per image element
     GemmPlan g1, g2;
     long long bytes = 0;
 };
 
-constexpr uint32_t make_idesc(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+constexpr uint32_t make_idesc(int M, int N, bool tf) {
+    const uint32_t fmt = tf ? 2u : 1u;   // TF32 : BF16
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-cudaError_t plan_gemm(GemmPlan& gp, int num_sms, long long M_rows, long long K_cols, int G, int acc_stride, int QS,
-                      int Q, unsigned* flags, long long* bytes) {
+cudaError_t plan_gemm(GemmPlan& gp, int num_sms, long long M_rows, long long K_cols, int KE, int G, int acc_stride,
+                      int QS, int QH, int Q, bool tf, unsigned* flags, long long* bytes, cudaStream_t st) {
     TcParams& p = gp.p;
     p.M_tiles = (int)((M_rows + TC_BM - 1) / TC_BM);
-    p.K_tiles = (int)((K_cols + TC_BK - 1) / TC_BK);
+    p.K_tiles = (int)((K_cols + KE - 1) / KE);
     p.G = G;
     p.acc_stride = acc_stride;
     p.QS = QS;
+    p.QH = QH;
     p.Q = Q;
-    p.idesc = make_idesc(TC_BM, QS);
+    p.idesc = make_idesc(TC_BM, QS, tf);
+    p.idesc_lo = make_idesc(TC_BM, tf ? QH : QS, tf);
     p.flags = flags;
     gp.groups = (p.M_tiles + G - 1) / G;
     p.W = (long long)gp.groups * p.K_tiles;
-    gp.nCTA = (int)std::min<long long>(num_sms, p.W);
+    // at least ~16 units per CTA: small problems then leave SMs to other work
+    // (concurrent requests) instead of paying the pipeline fill on every SM
+    gp.nCTA = (int)std::max<long long>(1, std::min<long long>(num_sms, p.W / 16));
     // segments: each CTA's unit range split at group boundaries
     std::vector<int> seg_base(gp.nCTA + 1), grp_first(gp.groups, -1), grp_count(gp.groups, 0);
     int nseg = 0;
@@ -517,24 +586,36 @@ cudaError_t plan_gemm(GemmPlan& gp, int num_sms, long long M_rows, long long K_c
         grp[2 * g + 1] = grp_count[g];
     }
     cudaError_t e;
-    if ((e = cudaMalloc(&gp.seg_base, seg_base.size() * sizeof(int)))) return e;
-    if ((e = cudaMalloc(&gp.grp_seg, grp.size() * sizeof(int)))) return e;
+    if ((e = cudaMallocAsync(&gp.seg_base, seg_base.size() * sizeof(int), st))) return e;
+    if ((e = cudaMallocAsync(&gp.grp_seg, grp.size() * sizeof(int), st))) return e;
     const size_t part_elems = (size_t)nseg * Q * G * TC_BM;
-    if ((e = cudaMalloc(&gp.part, part_elems * sizeof(float)))) return e;
-    *bytes += (long long)(seg_base.size() + grp.size()) * 4 + (long long)part_elems * 4;
-    if ((e = cudaMemcpy(gp.seg_base, seg_base.data(), seg_base.size() * sizeof(int), cudaMemcpyHostToDevice))) return e;
-    if ((e = cudaMemcpy(gp.grp_seg, grp.data(), grp.size() * sizeof(int), cudaMemcpyHostToDevice))) return e;
+    if ((e = cudaMallocAsync(&gp.part, part_elems * sizeof(float), st))) return e;
+    gp.A_bytes = (size_t)gp.groups * G * (size_t)p.K_tiles * TC_A_BYTES;
+    if ((e = cudaMallocAsync(&gp.A, gp.A_bytes, st))) return e;
+    *bytes += (long long)(seg_base.size() + grp.size()) * 4 + (long long)part_elems * 4 + (long long)gp.A_bytes;
+    if ((e = cudaMemcpyAsync(gp.seg_base, seg_base.data(), seg_base.size() * sizeof(int), cudaMemcpyHostToDevice, st)))
+        return e;
+    if ((e = cudaMemcpyAsync(gp.grp_seg, grp.data(), grp.size() * sizeof(int), cudaMemcpyHostToDevice, st))) return e;
+    if ((e = cudaStreamSynchronize(st))) return e;   // the host tables go out of scope
     p.seg_base = gp.seg_base;
     p.part = gp.part;
+    p.A = gp.A;
     return cudaSuccess;
 }
 
-void free_gemm(GemmPlan& gp) {
-    if (gp.seg_base) cudaFree(gp.seg_base);
-    if (gp.grp_seg) cudaFree(gp.grp_seg);
-    if (gp.part) cudaFree(gp.part);
+void free_gemm(GemmPlan& gp, cudaStream_t st) {
+    if (gp.seg_base) cudaFreeAsync(gp.seg_base, st);
+    if (gp.grp_seg) cudaFreeAsync(gp.grp_seg, st);
+    if (gp.part) cudaFreeAsync(gp.part, st);
+    if (gp.A) cudaFreeAsync(gp.A, st);
     gp.seg_base = gp.grp_seg = nullptr;
     gp.part = nullptr;
+    gp.A = nullptr;
+}
+
+size_t gemm_smem(bool tf, int QS) {
+    const int na = tf ? TC_NA_TF : TC_NA;
+    return 1024 + (size_t)na * TC_A_BYTES * (tf ? 2 : 1) + (size_t)TC_NB * QS * 128 + 512;
 }
 
 }  // namespace
@@ -542,22 +623,36 @@ void free_gemm(GemmPlan& gp) {
 void tc_release(cofem_ctx* c) {
     TcPlan* t = (TcPlan*)c->tc;
     if (!t) return;
-    free_gemm(t->g1);
-    free_gemm(t->g2);
-    if (t->Vs) cudaFree(t->Vs);
-    if (t->Ts) cudaFree(t->Ts);
+    free_gemm(t->g1, c->stream);
+    free_gemm(t->g2, c->stream);
+    if (t->Vs) cudaFreeAsync(t->Vs, c->stream);
+    if (t->Ts) cudaFreeAsync(t->Ts, c->stream);
     c->bytes -= t->bytes;
     delete t;
     c->tc = nullptr;
 }
 
+// Plan for a Q-column block: split factors, segment tables, and the tiled
+// images of the dictionary (GEMM1) and of its transpose (GEMM2), built from the
+// row-major copy (bf16 for the BF16 form, fp32 for the FP32 form).
 cudaError_t tc_setup(cofem_ctx* c, int Q) {
     tc_release(c);
     TcPlan* t = new TcPlan();
     c->tc = t;
+    t->tf = c->phi16 == nullptr;
     t->Q = Q;
-    t->QS = ((3 * Q + 15) / 16) * 16;
-    int acc_stride;
+    int KE, acc_stride;
+    if (t->tf) {
+        t->QH = ((Q + 15) / 16) * 16;
+        t->QS = 2 * t->QH;
+        t->esz = 4;
+        KE = TC_BK32;
+    } else {
+        t->QH = 0;
+        t->QS = ((3 * Q + 15) / 16) * 16;
+        t->esz = 2;
+        KE = TC_BK;
+    }
     if (t->QS <= 128) {
         t->G = 4;
         acc_stride = 128;
@@ -567,37 +662,77 @@ cudaError_t tc_setup(cofem_ctx* c, int Q) {
     }
     cudaError_t e;
     unsigned* flags = &c->ctl->flags;
-    if ((e = plan_gemm(t->g1, c->num_sms, c->Np, c->Dp, t->G, acc_stride, t->QS, Q, flags, &t->bytes))) return e;
-    if ((e = plan_gemm(t->g2, c->num_sms, c->Dp, c->Np, t->G, acc_stride, t->QS, Q, flags, &t->bytes))) return e;
-    if ((e = cudaMalloc(&t->Vs, (size_t)t->QS * c->Dp * 2))) return e;
-    if ((e = cudaMalloc(&t->Ts, (size_t)t->QS * c->Np * 2))) return e;
-    t->bytes += (long long)t->QS * (c->Dp + c->Np) * 2;
+    cudaStream_t st = c->stream;
+    if ((e = plan_gemm(t->g1, c->num_sms, c->Np, c->Dp, KE, t->G, acc_stride, t->QS, t->QH, Q, t->tf, flags,
+                       &t->bytes, st)))
+        return e;
+    if ((e = plan_gemm(t->g2, c->num_sms, c->Dp, c->Np, KE, t->G, acc_stride, t->QS, t->QH, Q, t->tf, flags,
+                       &t->bytes, st)))
+        return e;
+    if ((e = cudaMallocAsync(&t->Vs, (size_t)t->QS * c->Dp * t->esz, st))) return e;
+    if ((e = cudaMallocAsync(&t->Ts, (size_t)t->QS * c->Np * t->esz, st))) return e;
+    t->bytes += (long long)t->QS * (c->Dp + c->Np) * (long long)t->esz;
     c->bytes += t->bytes;
-    if ((e = cudaMemset(t->Vs, 0, (size_t)t->QS * c->Dp * 2))) return e;
-    if ((e = cudaMemset(t->Ts, 0, (size_t)t->QS * c->Np * 2))) return e;
-    if (!encode_map(&t->g1.mapA, c->phi16, c->Np, c->Dp, c->Dp, TC_BM) ||
-        !encode_map(&t->g1.mapB, t->Vs, t->QS, c->Dp, c->Dp, t->QS) ||
-        !encode_map(&t->g2.mapA, c->phiT16, c->Dp, c->Np, c->Np, TC_BM) ||
-        !encode_map(&t->g2.mapB, t->Ts, t->QS, c->Np, c->Np, t->QS))
-        return cudaErrorInvalidValue;
-    t->smem = 1024 + (size_t)TC_NA * TC_A_BYTES + (size_t)TC_NB * t->QS * 128 + 256;
-    return cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem);
+    if ((e = cudaMemsetAsync(t->Vs, 0, (size_t)t->QS * c->Dp * t->esz, st))) return e;   // padding rows stay zero
+    if ((e = cudaMemsetAsync(t->Ts, 0, (size_t)t->QS * c->Np * t->esz, st))) return e;
+    t->g1.p.B = t->Vs;
+    t->g2.p.B = t->Ts;
+    if (t->tf) {
+        k_tile_rows<float><<<dim3(t->g1.p.K_tiles, t->g1.groups * t->G), 128, 0, st>>>(
+            c->phi32, c->Dp, t->g1.p.M_tiles, t->g1.p.K_tiles, t->G, (float*)t->g1.A);
+        k_tile_cols<float><<<dim3(t->g2.p.K_tiles, t->g2.groups * t->G), 128, 0, st>>>(
+            c->phi32, c->Dp, t->g2.p.M_tiles, t->g2.p.K_tiles, t->G, (float*)t->g2.A);
+    } else {
+        k_tile_rows<__nv_bfloat16><<<dim3(t->g1.p.K_tiles, t->g1.groups * t->G), 128, 0, st>>>(
+            c->phi16, c->Dp, t->g1.p.M_tiles, t->g1.p.K_tiles, t->G, (__nv_bfloat16*)t->g1.A);
+        k_tile_cols<__nv_bfloat16><<<dim3(t->g2.p.K_tiles, t->g2.groups * t->G), 128, 0, st>>>(
+            c->phi16, c->Dp, t->g2.p.M_tiles, t->g2.p.K_tiles, t->G, (__nv_bfloat16*)t->g2.A);
+    }
+    if ((e = cudaGetLastError())) return e;
+    if ((e = cudaStreamSynchronize(st))) return e;
+    t->smem = gemm_smem(t->tf, t->QS);
+    return cudaSuccess;
 }
 
-cudaError_t tc_make_transpose(cofem_ctx* c, cudaStream_t st) {
-    const dim3 grid((unsigned)(c->Dp / 32), (unsigned)(c->Np / 32));
-    k_transpose_bf16<<<grid, dim3(32, 8), 0, st>>>(c->phi16, c->Np, c->Dp, c->phiT16);
-    return cudaGetLastError();
+// The shared-memory limit of a kernel is one device-wide attribute; handles with
+// different K running concurrently must not lower it under each other, so it is
+// raised once, to the opt-in maximum, when the library first runs on a device.
+cudaError_t tc_kernel_attributes(int max_smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
 }
 
+SplitOut tc_direction_split(cofem_ctx* c) {
+    TcPlan* t = (TcPlan*)c->tc;
+    if (!t || c->kind != COFEM_OP_DENSE) return SplitOut{nullptr, 0, 0, 0};
+    return SplitOut{t->Vs, t->tf ? 2 : 1, t->QS, t->QH};
+}
+
+OpOut op_output(cofem_ctx* c) {
+    TcPlan* t = (TcPlan*)c->tc;
+    if (c->kind == COFEM_OP_DENSE && t) return OpOut{t->g2.part, 1, 0, t->g2.grp_seg, t->G * TC_BM};
+    const int S2 = c->kind == COFEM_OP_DENSE ? c->S2 : 1;
+    return OpOut{c->U, S2, (size_t)c->Qcap * c->Dp, nullptr, 0};
+}
+
+// In the CG loop (OP_CG, OP_TIME) the split of P is already in Vs (written by
+// k_cg_init / k_cg_direction) and the update kernel reads GEMM2's segment
+// partials directly; residual replacement (OP_RR) splits X here; a stand-alone
+// application (OP_PLAIN) also sums the partials into U.
 void launch_tc_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode) {
     TcPlan* t = (TcPlan*)c->tc;
-    s.launch(k_split3, dim3((unsigned)((c->Dp / 4 + 255) / 256), Q), dim3(256), 0, V, c->Dp, t->Vs, c->Dp);
-    s.launch(k_gemm_tc, dim3(t->g1.nCTA), dim3(TC_THREADS), t->smem, t->g1.mapA, t->g1.mapB, t->g1.p);
+    const SplitOut sv{t->Vs, t->tf ? 2 : 1, t->QS, t->QH};
+    const SplitOut st{t->Ts, t->tf ? 2 : 1, t->QS, t->QH};
+    if (mode == OP_RR || mode == OP_PLAIN)
+        s.launch(k_split, dim3((unsigned)((c->Dp / 4 + 255) / 256), Q), dim3(256), 0, V, c->Dp, sv);
+    void (*gemm)(TcParams) = t->tf ? k_gemm_tc<true> : k_gemm_tc<false>;
+    s.launch(gemm, dim3(t->g1.nCTA), dim3(TC_THREADS), t->smem, t->g1.p);
     const int nblk = (int)((c->Np + 1023) / 1024);
-    s.launch(k_tc_reduce_T, dim3(nblk, Q), dim3(256), 0, t->g1.part, t->g1.grp_seg, t->G * TC_BM, Q, c->Np, t->Ts,
+    s.launch(k_tc_reduce_T, dim3(nblk, Q), dim3(256), 0, t->g1.part, t->g1.grp_seg, t->G * TC_BM, Q, c->Np, st,
              c->tt_part, nblk, c->counters + 8, c->ctl, mode);
-    s.launch(k_gemm_tc, dim3(t->g2.nCTA), dim3(TC_THREADS), t->smem, t->g2.mapA, t->g2.mapB, t->g2.p);
-    s.launch(k_tc_reduce_U, dim3((unsigned)((c->Dp + 1023) / 1024), Q), dim3(256), 0, t->g2.part, t->g2.grp_seg,
-             t->G * TC_BM, Q, c->Dp, c->U);
+    s.launch(gemm, dim3(t->g2.nCTA), dim3(TC_THREADS), t->smem, t->g2.p);
+    if (mode == OP_PLAIN)
+        s.launch(k_tc_reduce_U, dim3((unsigned)((c->Dp + 1023) / 1024), Q), dim3(256), 0, t->g2.part,
+                 t->g2.grp_seg, t->G * TC_BM, Q, c->Dp, c->U);
 }

@@ -67,14 +67,14 @@ __global__ __launch_bounds__(TZ_THREADS) void k_toeplitz(const float* __restrict
     // T_i = sum_tau h[tau] v[i - tau] for i = j0 + 8 th + m
     float tv[8];
     slide_corr8(shr, sV, th * TZ_R, Lp, tv);
-    double tt = 0.0;
+    float tt = 0.0f;
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
         const int idx = th * TZ_R + m;
         const long long i = j0 + idx;
         const float v = i < N ? tv[m] : 0.0f;
         sT[idx] = v;
-        if (idx < Bout) tt += (double)v * (double)v;   // T_i owned by this tile
+        if (idx < Bout) tt = fmaf(v, v, tt);   // T_i owned by this tile
     }
     __syncthreads();
     // U_j = sum_tau h[tau] T[j + tau] for j = j0 + 8 th + m < j0 + Bout
@@ -89,8 +89,8 @@ __global__ __launch_bounds__(TZ_THREADS) void k_toeplitz(const float* __restrict
             if (idx < Bout && j < Dp) Uq[j] = j < N ? uv[m] : 0.0f;
         }
     }
-    tt = block_sum(tt, red);
-    if (th == 0) tt_part[(size_t)q * nblk + blk] = tt;
+    const double ttd = block_sum_f(tt, red);
+    if (th == 0) tt_part[(size_t)q * nblk + blk] = ttd;
     if (!last_block_arrive(counter, gridDim.x * gridDim.y)) return;
     op_finalize_block(ctl, tt_part, nblk, Q, mode);
 }
@@ -99,10 +99,14 @@ __global__ void k_toeplitz_theta(const float* __restrict__ h, int L, long long N
                                  float* __restrict__ theta) {
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= Dp) return;
-    double a = 0.0;
+    double a = 0.0;   // FP32 runs of 8 taps, FP64 across runs
     if (j < N) {
         const long long m = (N - j) < L ? (N - j) : L;
-        for (long long tau = 0; tau < m; ++tau) a += (double)h[tau] * (double)h[tau];
+        for (long long t0 = 0; t0 < m; t0 += 8) {
+            float f = 0.0f;
+            for (long long tau = t0; tau < t0 + 8 && tau < m; ++tau) f = fmaf(h[tau], h[tau], f);
+            a += (double)f;
+        }
     }
     theta[j] = (float)a;
 }
@@ -111,10 +115,14 @@ __global__ void k_toeplitz_phit_y(const float* __restrict__ h, int L, long long 
                                   const float* __restrict__ y, double scale, float* __restrict__ out) {
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= Dp) return;
-    double a = 0.0;
+    double a = 0.0;   // FP32 runs of 8 taps, FP64 across runs
     if (j < N) {
         const long long m = (N - j) < L ? (N - j) : L;
-        for (long long tau = 0; tau < m; ++tau) a += (double)__ldg(h + tau) * (double)__ldg(y + j + tau);
+        for (long long t0 = 0; t0 < m; t0 += 8) {
+            float f = 0.0f;
+            for (long long tau = t0; tau < t0 + 8 && tau < m; ++tau) f = fmaf(__ldg(h + tau), __ldg(y + j + tau), f);
+            a += (double)f;
+        }
     }
     out[j] = (float)(scale * a);
 }
@@ -147,6 +155,14 @@ size_t toeplitz_smem_bytes(int L) {
 }
 
 cudaError_t toeplitz_prepare(int L) {
+    // all supported L (<= 1024) stay within the default 48 KiB; raising the limit
+    // per handle would race with concurrent handles, so it is set once for the
+    // largest L in cofem_kernel_attributes
+    (void)L;
+    return cudaSuccess;
+}
+
+cudaError_t toeplitz_kernel_attributes() {
     return cudaFuncSetAttribute(k_toeplitz, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)toeplitz_smem_bytes(L));
+                                (int)toeplitz_smem_bytes(1024));
 }

@@ -32,32 +32,40 @@ __device__ void reduce_parts(const double* part, int nk, int Q, int nch, double*
     __syncthreads();
 }
 
-// Alg. 2 stopping test and direction scalars for the columns still active
-// (thread 0 of the last block).  rr[q] = ||r_q||^2, rz[q] = r_q^T M^-1 r_q.
+// Alg. 2 stopping test and direction scalars for the columns still active,
+// run by every thread of the last block (one column per thread).
+// rr[q] = ||r_q||^2, rz[q] = r_q^T M^-1 r_q.  ||r_q|| / ||b_q|| <= tol is tested
+// as ||r_q||^2 <= tol^2 ||b_q||^2.
 __device__ void cg_stop_test(DevCtl* ctl, const double* rr, const double* rz) {
+    __shared__ int s_stop_all;
     const int Q = ctl->Q;
-    if (ctl->conv == COFEM_CONV_FROBENIUS) {
-        double num = 0.0, den = 0.0;
-        for (int q = 0; q < Q; ++q) {
-            if (ctl->active[q]) num += rr[q];
-            den += ctl->bnorm2[q];
+    const double t2 = ctl->tol * ctl->tol;
+    if (threadIdx.x == 0) {
+        s_stop_all = 0;
+        if (ctl->conv == COFEM_CONV_FROBENIUS) {
+            double num = 0.0, den = 0.0;
+            for (int q = 0; q < Q; ++q) {
+                if (ctl->active[q]) num += rr[q];
+                den += ctl->bnorm2[q];
+            }
+            s_stop_all = num <= t2 * den;
         }
-        if (sqrt(num) / sqrt(den) <= ctl->tol)
-            for (int q = 0; q < Q; ++q) ctl->active[q] = 0;
     }
-    int any = 0;
-    for (int q = 0; q < Q; ++q) {
-        if (!ctl->active[q]) continue;
+    __syncthreads();
+    const int q = threadIdx.x;
+    int act = 0;
+    if (q < Q && ctl->active[q]) {
         ctl->rnorm2[q] = rr[q];
-        if (ctl->conv == COFEM_CONV_PER_COLUMN && sqrt(rr[q]) / sqrt(ctl->bnorm2[q]) <= ctl->tol) {
+        if (s_stop_all || (ctl->conv == COFEM_CONV_PER_COLUMN && rr[q] <= t2 * ctl->bnorm2[q])) {
             ctl->active[q] = 0;
-            continue;
+        } else {
+            ctl->eta[q] = rz[q] / ctl->rho[q];
+            ctl->rho[q] = rz[q];
+            act = 1;
         }
-        ctl->eta[q] = rz[q] / ctl->rho[q];
-        ctl->rho[q] = rz[q];
-        any = 1;
     }
-    ctl->any_active = any;
+    act = __syncthreads_or(act);
+    if (threadIdx.x == 0) ctl->any_active = act;
 }
 
 // ---------------------------------------------------------------------------
@@ -66,8 +74,8 @@ __device__ void cg_stop_test(DevCtl* ctl, const double* rr, const double* rz) {
 __global__ void k_fit_setup(DevCtl* ctl, const float* __restrict__ theta, const float* __restrict__ alpha,
                             float* __restrict__ minv, long long D, long long Dp) {
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const double beta = ctl->beta;
-    if (j < Dp) minv[j] = j < D ? (float)(1.0 / (beta * (double)theta[j] + (double)alpha[j])) : 0.0f;
+    const float beta = (float)ctl->beta;
+    if (j < Dp) minv[j] = j < D ? 1.0f / (beta * theta[j] + alpha[j]) : 0.0f;
     if (j == 0) {
         ctl->t = 1;
         ctl->u = 0;
@@ -84,12 +92,13 @@ __global__ __launch_bounds__(NT) void k_cg_init(DevCtl* ctl, const float* __rest
                                                 const float* __restrict__ minv, const float* __restrict__ alpha,
                                                 float* __restrict__ X, float* __restrict__ R, float* __restrict__ P,
                                                 long long D, long long Dp, int nch, double* part,
-                                                unsigned* counter, cudaGraphConditionalHandle h_cg) {
+                                                unsigned* counter, cudaGraphConditionalHandle h_cg,
+                                                SplitOut so) {
     __shared__ double sh[NT / 32];
     __shared__ double red[3 * COFEM_QMAX];
     const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q, t = ctl->t;
     const unsigned long long seed = ctl->seed;
-    double bb = 0.0, rz = 0.0, ap = 0.0;
+    float bb = 0.0f, rz = 0.0f, ap = 0.0f;
     const size_t off = (size_t)q * Dp;
     for (int e = threadIdx.x * 4; e < CH; e += NT * 4) {
         const long long j = (long long)ch * CH + e;
@@ -109,99 +118,87 @@ __global__ __launch_bounds__(NT) void k_cg_init(DevCtl* ctl, const float* __rest
         st4(X + off + j, make_float4(0.f, 0.f, 0.f, 0.f));
         st4(R + off + j, bv);
         st4(P + off + j, wv);
-        bb += (double)bv.x * bv.x + (double)bv.y * bv.y + (double)bv.z * bv.z + (double)bv.w * bv.w;
-        rz += (double)bv.x * wv.x + (double)bv.y * wv.y + (double)bv.z * wv.z + (double)bv.w * wv.w;
-        ap += (double)av.x * wv.x * wv.x + (double)av.y * wv.y * wv.y + (double)av.z * wv.z * wv.z +
-              (double)av.w * wv.w * wv.w;
+        store_split(so, q, j, wv);
+        bb += bv.x * bv.x + bv.y * bv.y + bv.z * bv.z + bv.w * bv.w;
+        rz += bv.x * wv.x + bv.y * wv.y + bv.z * wv.z + bv.w * wv.w;
+        ap += av.x * wv.x * wv.x + av.y * wv.y * wv.y + av.z * wv.z * wv.z + av.w * wv.w * wv.w;
     }
-    bb = block_sum(bb, sh);
-    rz = block_sum(rz, sh);
-    ap = block_sum(ap, sh);
+    const double bbd = block_sum_f(bb, sh);
+    const double rzd = block_sum_f(rz, sh);
+    const double apd = block_sum_f(ap, sh);
     if (threadIdx.x == 0) {
-        part[(size_t)(0 * Q + q) * nch + ch] = bb;
-        part[(size_t)(1 * Q + q) * nch + ch] = rz;
-        part[(size_t)(2 * Q + q) * nch + ch] = ap;
+        part[(size_t)(0 * Q + q) * nch + ch] = bbd;
+        part[(size_t)(1 * Q + q) * nch + ch] = rzd;
+        part[(size_t)(2 * Q + q) * nch + ch] = apd;
     }
     if (!last_block_arrive(counter, gridDim.x * gridDim.y)) return;
     reduce_parts(part, 3, Q, nch, red);
+    const int qq = threadIdx.x;
+    int act = 0;
+    if (qq < Q) {
+        ctl->bnorm2[qq] = red[qq];
+        ctl->rho[qq] = red[COFEM_QMAX + qq];
+        ctl->ap[qq] = red[2 * COFEM_QMAX + qq];
+        ctl->rnorm2[qq] = red[qq];
+        act = red[qq] > 0.0;   // a zero right-hand side starts converged (x = 0)
+        ctl->active[qq] = act;
+    }
+    act = __syncthreads_or(act);
     if (threadIdx.x == 0) {
-        int any = 0;
-        for (int qq = 0; qq < Q; ++qq) {
-            ctl->bnorm2[qq] = red[qq];
-            ctl->rho[qq] = red[COFEM_QMAX + qq];
-            ctl->ap[qq] = red[2 * COFEM_QMAX + qq];
-            ctl->rnorm2[qq] = red[qq];
-            ctl->active[qq] = red[qq] > 0.0;   // a zero right-hand side starts converged (x = 0)
-            any |= ctl->active[qq];
-        }
         ctl->u = 0;
-        ctl->any_active = any;
-        set_cond(h_cg, any && ctl->maxit > 0);
+        ctl->any_active = act;
+        set_cond(h_cg, act && ctl->maxit > 0);
     }
-}
-
-// Psi_j for column q from the operator partials: beta * sum_s U_s + alpha_j v_j.
-__device__ __forceinline__ float4 psi_from_parts(const float* __restrict__ U, int S2, size_t sstride,
-                                                 size_t idx, float beta, float4 av, float4 vv) {
-    float4 u = ld4(U + idx);
-    for (int s = 1; s < S2; ++s) {
-        const float4 w = ld4(U + (size_t)s * sstride + idx);
-        u.x += w.x; u.y += w.y; u.z += w.z; u.w += w.w;
-    }
-    return make_float4(beta * u.x + av.x * vv.x, beta * u.y + av.y * vv.y,
-                       beta * u.z + av.z * vv.z, beta * u.w + av.w * vv.w);
 }
 
 // ---------------------------------------------------------------------------
 // Fused CG update (Alg. 2: X += P Gamma, R -= Psi Gamma, then ||r||, r^T M^-1 r,
 // stopping test and eta), for the active columns.
 // ---------------------------------------------------------------------------
-__global__ __launch_bounds__(NT) void k_cg_update(DevCtl* ctl, const float* __restrict__ P,
-                                                  const float* __restrict__ U, int S2, const float* __restrict__ alpha,
+__global__ __launch_bounds__(NT) void k_cg_update(DevCtl* ctl, const float* __restrict__ P, OpOut uo,
+                                                  const float* __restrict__ alpha,
                                                   const float* __restrict__ minv, float* __restrict__ X,
-                                                  float* __restrict__ R, long long Dp, int Qcap, int nch,
+                                                  float* __restrict__ R, long long Dp, int nch,
                                                   double* part, unsigned* counter,
                                                   cudaGraphConditionalHandle h_rr) {
     __shared__ double sh[NT / 32];
     __shared__ double red[2 * COFEM_QMAX];
     const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q;
-    double rr = 0.0, rz = 0.0;
+    float rr = 0.0f, rz = 0.0f;
     if (ctl->active[q]) {
         const float gamma = (float)ctl->gamma[q];
         const float beta = (float)ctl->beta;
-        const size_t off = (size_t)q * Dp, sstride = (size_t)Qcap * Dp;
+        const size_t off = (size_t)q * Dp;
         for (int e = threadIdx.x * 4; e < CH; e += NT * 4) {
             const long long j = (long long)ch * CH + e;
             if (j >= Dp) break;
             const float4 pv = ld4(P + off + j), av = ld4(alpha + j), mv = ld4(minv + j);
-            const float4 psi = psi_from_parts(U, S2, sstride, off + j, beta, av, pv);
+            const float4 psi = psi4(uo, Q, q, Dp, j, beta, av, pv);
             float4 xv = ld4(X + off + j), rv = ld4(R + off + j);
             xv.x += gamma * pv.x; xv.y += gamma * pv.y; xv.z += gamma * pv.z; xv.w += gamma * pv.w;
             rv.x -= gamma * psi.x; rv.y -= gamma * psi.y; rv.z -= gamma * psi.z; rv.w -= gamma * psi.w;
             st4(X + off + j, xv);
             st4(R + off + j, rv);
-            rr += (double)rv.x * rv.x + (double)rv.y * rv.y + (double)rv.z * rv.z + (double)rv.w * rv.w;
-            rz += (double)rv.x * (rv.x * mv.x) + (double)rv.y * (rv.y * mv.y) + (double)rv.z * (rv.z * mv.z) +
-                  (double)rv.w * (rv.w * mv.w);
+            rr += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
+            rz += rv.x * (rv.x * mv.x) + rv.y * (rv.y * mv.y) + rv.z * (rv.z * mv.z) + rv.w * (rv.w * mv.w);
         }
     }
-    rr = block_sum(rr, sh);
-    rz = block_sum(rz, sh);
+    const double rrd = block_sum_f(rr, sh);
+    const double rzd = block_sum_f(rz, sh);
     if (threadIdx.x == 0) {
-        part[(size_t)(0 * Q + q) * nch + ch] = rr;
-        part[(size_t)(1 * Q + q) * nch + ch] = rz;
+        part[(size_t)(0 * Q + q) * nch + ch] = rrd;
+        part[(size_t)(1 * Q + q) * nch + ch] = rzd;
     }
     if (!last_block_arrive(counter, gridDim.x * gridDim.y)) return;
     reduce_parts(part, 2, Q, nch, red);
+    __shared__ int s_rr;
     if (threadIdx.x == 0) {
         const int u = ++ctl->u;
-        if (ctl->rr_period > 0 && u % ctl->rr_period == 0) {
-            set_cond(h_rr, 1);   // residual replacement finishes this iteration
-            return;
-        }
-        set_cond(h_rr, 0);
-        cg_stop_test(ctl, red, red + COFEM_QMAX);
+        s_rr = ctl->rr_period > 0 && u % ctl->rr_period == 0;   // replacement finishes this iteration
+        set_cond(h_rr, s_rr);
     }
+    __syncthreads();
+    if (!s_rr) cg_stop_test(ctl, red, red + COFEM_QMAX);
 }
 
 // ---------------------------------------------------------------------------
@@ -209,17 +206,17 @@ __global__ __launch_bounds__(NT) void k_cg_update(DevCtl* ctl, const float* __re
 // with B regenerated (b, probes), then the stopping test and eta.
 // ---------------------------------------------------------------------------
 __global__ __launch_bounds__(NT) void k_rr_residual(DevCtl* ctl, const float* __restrict__ b,
-                                                    const float* __restrict__ X, const float* __restrict__ U, int S2,
+                                                    const float* __restrict__ X, OpOut uo,
                                                     const float* __restrict__ alpha, const float* __restrict__ minv,
-                                                    float* __restrict__ R, long long D, long long Dp, int Qcap,
+                                                    float* __restrict__ R, long long D, long long Dp,
                                                     int nch, double* part, unsigned* counter) {
     __shared__ double sh[NT / 32];
     __shared__ double red[2 * COFEM_QMAX];
     const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q, t = ctl->t;
-    double rr = 0.0, rz = 0.0;
+    float rr = 0.0f, rz = 0.0f;
     if (ctl->active[q]) {
         const float beta = (float)ctl->beta;
-        const size_t off = (size_t)q * Dp, sstride = (size_t)Qcap * Dp;
+        const size_t off = (size_t)q * Dp;
         for (int e = threadIdx.x * 4; e < CH; e += NT * 4) {
             const long long j = (long long)ch * CH + e;
             if (j >= Dp) break;
@@ -234,23 +231,22 @@ __global__ __launch_bounds__(NT) void k_rr_residual(DevCtl* ctl, const float* __
                 bv.w = j + 3 < D ? probe_sign_from_word(w, j + 3) : 0.0f;
             }
             const float4 xv = ld4(X + off + j), av = ld4(alpha + j), mv = ld4(minv + j);
-            const float4 ax = psi_from_parts(U, S2, sstride, off + j, beta, av, xv);
+            const float4 ax = psi4(uo, Q, q, Dp, j, beta, av, xv);
             const float4 rv = make_float4(bv.x - ax.x, bv.y - ax.y, bv.z - ax.z, bv.w - ax.w);
             st4(R + off + j, rv);
-            rr += (double)rv.x * rv.x + (double)rv.y * rv.y + (double)rv.z * rv.z + (double)rv.w * rv.w;
-            rz += (double)rv.x * (rv.x * mv.x) + (double)rv.y * (rv.y * mv.y) + (double)rv.z * (rv.z * mv.z) +
-                  (double)rv.w * (rv.w * mv.w);
+            rr += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
+            rz += rv.x * (rv.x * mv.x) + rv.y * (rv.y * mv.y) + rv.z * (rv.z * mv.z) + rv.w * (rv.w * mv.w);
         }
     }
-    rr = block_sum(rr, sh);
-    rz = block_sum(rz, sh);
+    const double rrd = block_sum_f(rr, sh);
+    const double rzd = block_sum_f(rz, sh);
     if (threadIdx.x == 0) {
-        part[(size_t)(0 * Q + q) * nch + ch] = rr;
-        part[(size_t)(1 * Q + q) * nch + ch] = rz;
+        part[(size_t)(0 * Q + q) * nch + ch] = rrd;
+        part[(size_t)(1 * Q + q) * nch + ch] = rzd;
     }
     if (!last_block_arrive(counter, gridDim.x * gridDim.y)) return;
     reduce_parts(part, 2, Q, nch, red);
-    if (threadIdx.x == 0) cg_stop_test(ctl, red, red + COFEM_QMAX);
+    cg_stop_test(ctl, red, red + COFEM_QMAX);
 }
 
 // ---------------------------------------------------------------------------
@@ -261,11 +257,11 @@ __global__ __launch_bounds__(NT) void k_cg_direction(DevCtl* ctl, const float* _
                                                      const float* __restrict__ alpha,
                                                      const float* __restrict__ minv, float* __restrict__ P,
                                                      long long Dp, int nch, double* part, unsigned* counter,
-                                                     cudaGraphConditionalHandle h_cg) {
+                                                     cudaGraphConditionalHandle h_cg, SplitOut so) {
     __shared__ double sh[NT / 32];
     __shared__ double red[COFEM_QMAX];
     const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q;
-    double ap = 0.0;
+    float ap = 0.0f;
     if (ctl->active[q]) {
         const float eta = (float)ctl->eta[q];
         const size_t off = (size_t)q * Dp;
@@ -279,12 +275,12 @@ __global__ __launch_bounds__(NT) void k_cg_direction(DevCtl* ctl, const float* _
             pv.z = rv.z * mv.z + eta * pv.z;
             pv.w = rv.w * mv.w + eta * pv.w;
             st4(P + off + j, pv);
-            ap += (double)av.x * pv.x * pv.x + (double)av.y * pv.y * pv.y + (double)av.z * pv.z * pv.z +
-                  (double)av.w * pv.w * pv.w;
+            store_split(so, q, j, pv);
+            ap += av.x * pv.x * pv.x + av.y * pv.y * pv.y + av.z * pv.z * pv.z + av.w * pv.w * pv.w;
         }
     }
-    ap = block_sum(ap, sh);
-    if (threadIdx.x == 0) part[(size_t)(2 * Q + q) * nch + ch] = ap;
+    const double apd = block_sum_f(ap, sh);
+    if (threadIdx.x == 0) part[(size_t)(2 * Q + q) * nch + ch] = apd;
     if (!last_block_arrive(counter, gridDim.x * gridDim.y)) return;
     // reduce only the k = 2 slab
     {
@@ -298,9 +294,8 @@ __global__ __launch_bounds__(NT) void k_cg_direction(DevCtl* ctl, const float* _
         }
         __syncthreads();
     }
+    if (threadIdx.x < Q && ctl->active[threadIdx.x]) ctl->ap[threadIdx.x] = red[threadIdx.x];
     if (threadIdx.x == 0) {
-        for (int qq = 0; qq < Q; ++qq)
-            if (ctl->active[qq]) ctl->ap[qq] = red[qq];
         const int cont = ctl->any_active && ctl->u < ctl->maxit;
         if (ctl->any_active && !cont) ctl->flags |= COFEM_FLAG_CG_NOT_CONVERGED;
         set_cond(h_cg, cont);
@@ -322,24 +317,24 @@ __global__ __launch_bounds__(NT) void k_mstep(DevCtl* ctl, const float* __restri
     int clamped = 0;
     if (j < Dp) {
         const float mu = X[j];
-        double s = 0.0;
+        float s = 0.0f;
         if (j < D) {
             const unsigned long long seed = ctl->seed;
             for (int k = 1; k <= K; ++k) {
                 const uint64_t w = probe_word(seed, t, k, j);
-                s += (double)probe_sign_from_word(w, j) * (double)X[(size_t)k * Dp + j];
+                s = fmaf(probe_sign_from_word(w, j), X[(size_t)k * Dp + j], s);
             }
-            s /= (double)K;
+            s /= (float)K;
         }
         mu_out[j] = mu;
-        s_out[j] = (float)s;
+        s_out[j] = s;
         if (t < T && j < D) {
-            const double m2 = (double)mu * mu + s;
-            const double floor_ = 1.0 / ctl->alpha_max;
+            const float m2 = fmaf(mu, mu, s);
+            const float floor_ = (float)(1.0 / ctl->alpha_max);
             clamped = m2 < floor_;
-            const double a = 1.0 / (m2 > floor_ ? m2 : floor_);
-            alpha[j] = (float)a;
-            minv[j] = (float)(1.0 / (ctl->beta * (double)theta[j] + (double)(float)a));
+            const float a = 1.0f / (m2 > floor_ ? m2 : floor_);
+            alpha[j] = a;
+            minv[j] = 1.0f / ((float)ctl->beta * theta[j] + a);
         }
     }
     if (__syncthreads_or(clamped) && threadIdx.x == 0) atomicOr(&ctl->flags, COFEM_FLAG_ALPHA_CLAMPED);
@@ -411,23 +406,22 @@ void launch_fit_setup(Sink& s, cofem_ctx* c, int /*Q*/) {
 
 void launch_cg_init(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg) {
     s.launch(k_cg_init, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->b, c->minv, c->alpha, c->X, c->R, c->P, c->D, c->Dp,
-             c->nch, c->part, c->counters + 0, h_cg);
+             c->nch, c->part, c->counters + 0, h_cg, tc_direction_split(c));
 }
 
 void launch_cg_update(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_rr) {
-    s.launch(k_cg_update, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->P, c->U, c->kind == COFEM_OP_DENSE ? c->S2 : 1,
-             c->alpha, c->minv, c->X, c->R, c->Dp, c->Qcap, c->nch, c->part, c->counters + 1, h_rr);
+    s.launch(k_cg_update, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->P, op_output(c), c->alpha, c->minv, c->X, c->R,
+             c->Dp, c->nch, c->part, c->counters + 1, h_rr);
 }
 
 void launch_rr_residual(Sink& s, cofem_ctx* c, int Q) {
-    s.launch(k_rr_residual, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->b, c->X, c->U,
-             c->kind == COFEM_OP_DENSE ? c->S2 : 1, c->alpha, c->minv, c->R, c->D, c->Dp, c->Qcap, c->nch, c->part,
-             c->counters + 2);
+    s.launch(k_rr_residual, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->b, c->X, op_output(c), c->alpha, c->minv, c->R,
+             c->D, c->Dp, c->nch, c->part, c->counters + 2);
 }
 
 void launch_cg_direction(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg) {
     s.launch(k_cg_direction, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->R, c->alpha, c->minv, c->P, c->Dp, c->nch,
-             c->part, c->counters + 3, h_cg);
+             c->part, c->counters + 3, h_cg, tc_direction_split(c));
 }
 
 void launch_mstep(Sink& s, cofem_ctx* c, int /*Q*/, cudaGraphConditionalHandle h_em) {

@@ -134,11 +134,15 @@ def _check_operator(cf, m, op, D, Q, seed, tol=2e-5):
     np.testing.assert_allclose(pi, np.sum(V.astype(np.float64) * want, axis=1), rtol=tol)
 
 
+@pytest.mark.parametrize("precision", ["tf32x3", "simt"])
 @pytest.mark.parametrize("N,D,Q", [(77, 301, 1), (77, 301, 7), (256, 1024, 21), (130, 700, 33), (64, 128, 64),
-                                   (2500, 10000, 33)])
-def test_operator_dense_f32(cf, N, D, Q):
+                                   (2500, 10000, 33), (1000, 3000, 17)])
+def test_operator_dense_f32(cf, N, D, Q, precision):
+    """FP32 dictionary: tensor cores with the error-compensated TF32 split, or
+    FP32 FMA on the CUDA cores."""
     p = dense_gaussian(N, D, 3, 20.0, seed=Q)
-    with cf.CoFEM(N, D, cf.COFEM_OP_DENSE, torch.from_numpy(p.phi).to(DEV)) as m:
+    prec = cf.COFEM_F32 if precision == "tf32x3" else cf.COFEM_F32_SIMT
+    with cf.CoFEM(N, D, cf.COFEM_OP_DENSE, torch.from_numpy(p.phi).to(DEV), precision=prec) as m:
         _check_operator(cf, m, DenseOperator(p.phi), D, Q, seed=Q)
 
 
@@ -201,6 +205,19 @@ def test_fit_dense_n256_d1024_k20(cf):
     # FP32 CG loses orthogonality a little faster than FP64 CG near the tolerance
     assert np.all(np.abs(g["cg_iters"] - r["cg_iters"]) <= np.maximum(3, 0.1 * r["cg_iters"]))
     assert g["flags"] == r["flags"]
+
+
+def test_fit_f32_forms_agree(cf):
+    """The tensor-core (TF32 split) and CUDA-core FP32 forms give the same fit
+    within the FP32 parity tolerance, and both match the oracle."""
+    from synth import workload
+    p, run = workload("dense_n256_d1024_k20")
+    a = gpu_fit(cf, p, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], seed=run["seed"], precision=cf.COFEM_F32)
+    b = gpu_fit(cf, p, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], seed=run["seed"],
+                precision=cf.COFEM_F32_SIMT)
+    r = oracle_fit(p, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], seed=run["seed"])
+    assert_fit_close(a, r)
+    assert_fit_close(b, r)
 
 
 def test_fit_graph_and_direct_modes_identical(cf):
