@@ -39,6 +39,11 @@ def _dist():
     return ws, rank, local
 
 
+# workload precision name -> C-ABI precision code
+_PRECISIONS = {"f32": lambda cf: cf.COFEM_F32, "bf16": lambda cf: cf.COFEM_BF16,
+               "tf32x3": lambda cf: cf.COFEM_F32_TF32X3}
+
+
 def _metric_name(name, spec):
     if spec["kind"] == "dense":
         shape = f"dense N={spec['N']} D={spec['D']}"
@@ -212,7 +217,7 @@ def run_ours(args):
     K, T, tol, maxit = run["K"], run["T"], run["cg_tol"], run["cg_maxit"]
     D, N = prob.D, prob.N
     stream = torch.cuda.Stream(device=dev)
-    prec = cf.COFEM_BF16 if run["precision"] == "bf16" else cf.COFEM_F32
+    prec = _PRECISIONS[run["precision"]](cf)
     kind = cf.COFEM_OP_DENSE if prob.kind == "dense" else cf.COFEM_OP_TOEPLITZ
 
     phi_d = torch.from_numpy(prob.phi).to(dev)
@@ -291,16 +296,19 @@ def run_ours(args):
     launches = sum(_launches_per_fit(it, run["rr_period"], op_kernels) for it in all_iters)
     model.close()
 
-    # the FP32 form on the same problem (precision comparison at equal NMSE)
+    # the FP32 forms on the same problem (precision comparison at equal NMSE):
+    # tensor-core 3xTF32 and plain FP32 FMA
     fp32 = None
     if prob.kind == "dense" and prec == cf.COFEM_BF16 and not args.no_fp32_form:
-        m32 = make(cf.COFEM_F32)
-        ms32, f32flags, _ = timed_fits(m32, max(1, args.steps), 1)
-        nm32 = _nmse_db(outs[0].cpu().numpy(), prob.z)
-        op32 = cf.cofem_time_operator(m32.h, Q, 10)
-        m32.close()
-        fp32 = {"value": max(1, args.steps) * T / (ms32 / 1000.0), "unit": "EM-iter/s", "nmse_db": nm32,
-                "operator_ms": op32, "flags": f32flags}
+        fp32 = {}
+        for key, form in (("tf32x3", cf.COFEM_F32_TF32X3), ("f32_fma", cf.COFEM_F32)):
+            m32 = make(form)
+            ms32, f32flags, _ = timed_fits(m32, 1, 1)
+            nm32 = _nmse_db(outs[0].cpu().numpy(), prob.z)
+            op32 = cf.cofem_time_operator(m32.h, Q, 10)
+            m32.close()
+            fp32[key] = {"value": T / (ms32 / 1000.0), "unit": "EM-iter/s", "nmse_db": nm32,
+                         "operator_ms": op32, "flags": f32flags}
 
     line = {
         "metric": _metric_name(name, spec), "value": value, "unit": "EM-iter/s", "n_gpus": ws,
@@ -348,7 +356,7 @@ def serving_run(cf, dev, n, precision, rate_hz=None, slots=16, budget_bytes=96 <
         N = D // 4
         bank[D] = torch.randn(N, D, generator=g, device=dev) / math.sqrt(N)
     reqs = serving_requests(n, base_seed=seed, rate_hz=rate_hz or 1.0)
-    prec = cf.COFEM_BF16 if precision == "bf16" else cf.COFEM_F32
+    prec = _PRECISIONS[precision](cf)
     prepared = []
     for r in reqs:
         D = min(sizes, key=lambda v: abs(v - r["D"]))
@@ -414,7 +422,7 @@ def run_operator_only(args):
     prob, run = workload(args.workload)
     K = run["K"]
     Q = K + 1
-    prec = cf.COFEM_BF16 if run["precision"] == "bf16" else cf.COFEM_F32
+    prec = _PRECISIONS[run["precision"]](cf)
     kind = cf.COFEM_OP_DENSE if prob.kind == "dense" else cf.COFEM_OP_TOEPLITZ
     rng = np.random.default_rng(0)
     V = torch.from_numpy(rng.standard_normal((Q, prob.D)).astype(np.float32)).to(dev)
@@ -445,7 +453,7 @@ def main():
                     help="requests of the serving measurement added to the line (0 = skip)")
     ap.add_argument("--serve", action="store_true",
                     help="only the serving measurement (2000 requests unless --serve-requests is given)")
-    ap.add_argument("--serve-precision", default="bf16", choices=["f32", "bf16"])
+    ap.add_argument("--serve-precision", default="bf16", choices=["f32", "bf16", "tf32x3"])
     ap.add_argument("--em-iters", type=int, default=0,
                     help="override T (profiling runs only; the benchmark line uses the workload's T)")
     ap.add_argument("--no-graph", action="store_true",

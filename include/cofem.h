@@ -55,15 +55,15 @@ typedef int cofem_status;
 
 /* Storage / multiply precision of a dense Phi (the CG state is always FP32,
  * CG inner products always FP64). */
-#define COFEM_F32   0  /* Phi kept in FP32; products on the tensor cores with the
-                          error-compensated TF32 split (Phi = Phi_hi + Phi_lo and
-                          V = V_hi + V_lo with the _hi parts truncated to TF32; the
-                          products hi*hi, hi*lo, lo*hi accumulate in FP32), about
-                          2^-21 relative error per product */
+#define COFEM_F32   0  /* Phi kept in FP32; products in FP32 FMA on the CUDA cores */
 #define COFEM_BF16  1  /* Phi quantised once to bfloat16 (round to nearest even); the
                           method then runs exactly on that quantised dictionary (the
                           vector block enters the tensor cores as three bf16 terms) */
-#define COFEM_F32_SIMT 2 /* Phi kept in FP32; products in FP32 FMA on the CUDA cores */
+#define COFEM_F32_TF32X3 2 /* Phi kept in FP32; products on the tensor cores with the
+                          error-compensated TF32 split: x = x_hi + x_lo for the
+                          dictionary and the vector block, x_hi and x_lo rounded to
+                          TF32, all four partial products accumulated in FP32
+                          (about 2^-22 relative error per product) */
 
 /* Preconditioner theta (Sec. III-C): M = diag(beta theta + alpha). */
 #define COFEM_PRECOND_JACOBI 0  /* theta_j = sum_i Phi_ij^2  (M_jj = A_jj) */
@@ -80,7 +80,7 @@ typedef int cofem_status;
 #define COFEM_FLAG_DEVICE_TIMEOUT   8u /* a bounded on-device wait gave up (the call returns COFEM_ERR_CUDA) */
 
 typedef struct cofem_opts {
-    int precision;            /* COFEM_F32 | COFEM_BF16 | COFEM_F32_SIMT (the last two dense only) */
+    int precision;            /* COFEM_F32 | COFEM_BF16 | COFEM_F32_TF32X3 (the last two dense only) */
     int precond;              /* COFEM_PRECOND_JACOBI | COFEM_PRECOND_ONE */
     int conv;                 /* COFEM_CONV_PER_COLUMN | COFEM_CONV_FROBENIUS */
     int rr_period;            /* residual replacement R <- B - A X every rr_period CG

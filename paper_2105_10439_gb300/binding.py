@@ -29,7 +29,7 @@ COFEM_OP_DENSE = 0
 COFEM_OP_TOEPLITZ = 1
 COFEM_F32 = 0
 COFEM_BF16 = 1
-COFEM_F32_SIMT = 2
+COFEM_F32_TF32X3 = 2
 COFEM_PRECOND_JACOBI = 0
 COFEM_PRECOND_ONE = 1
 COFEM_CONV_PER_COLUMN = 0

@@ -128,7 +128,7 @@ void free_workspace(cofem_ctx* c) {
 // Make sure the fit workspace holds Q columns (the split configuration
 // depends on Q, so any change of Q re-derives it and rebuilds the graph).
 cofem_status ensure_workspace(cofem_ctx* c, int Q) {
-    if (c->Qcap == Q) return COFEM_OK;
+    if (c->Qcap == Q && (!c->use_tc || c->tc)) return COFEM_OK;
     free_workspace(c);
     if (c->kind == COFEM_OP_DENSE) dense_configure(c, Q);
     const WsSizes w = ws_sizes(c, Q);
@@ -245,9 +245,7 @@ cofem_status run_fit_direct(cofem_ctx* c, int Q, int T) {
 }
 
 cofem_status check_finite_dev(cofem_ctx* c, const float* x, long long n, const char* name) {
-    unsigned* bad = &c->ctl_host->flags;   // scratch: pinned host word, device-visible
-    (void)bad;
-    unsigned* dbad = c->counters + 15;
+    unsigned* dbad = c->check_flag;
     CK(cudaMemsetAsync(dbad, 0, sizeof(unsigned), c->stream));
     launch_check_finite(c->stream, x, n, dbad);
     unsigned h = 0;
@@ -333,8 +331,8 @@ cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, c
     if (opts) o = *opts;
     if (kind == COFEM_OP_DENSE) {
         if (L != 0) return fail(COFEM_ERR_INVALID_ARG, "L must be 0 for a dense dictionary");
-        if (o.precision != COFEM_F32 && o.precision != COFEM_BF16 && o.precision != COFEM_F32_SIMT)
-            return fail(COFEM_ERR_INVALID_ARG, "precision must be COFEM_F32, COFEM_BF16 or COFEM_F32_SIMT");
+        if (o.precision != COFEM_F32 && o.precision != COFEM_BF16 && o.precision != COFEM_F32_TF32X3)
+            return fail(COFEM_ERR_INVALID_ARG, "precision must be COFEM_F32, COFEM_BF16 or COFEM_F32_TF32X3");
     } else if (kind == COFEM_OP_TOEPLITZ) {
         if (N != D) return fail(COFEM_ERR_INVALID_ARG, "a convolutional dictionary needs N == D");
         if (L < 1 || L > 1024 || L > N) return fail(COFEM_ERR_INVALID_ARG, "need 1 <= L <= min(1024, N)");
@@ -363,7 +361,7 @@ cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, c
     c->num_sms = sms;
     c->Np = round_up(N, 128);
     c->Dp = round_up(D, 128);
-    c->use_tc = kind == COFEM_OP_DENSE && o.precision != COFEM_F32_SIMT;
+    c->use_tc = kind == COFEM_OP_DENSE && o.precision != COFEM_F32;
     c->nch = vec_chunks(c->Dp);
     if (o.stream) {
         c->stream = (cudaStream_t)o.stream;
@@ -395,13 +393,9 @@ cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, c
         return bail(st);
     CKB(cudaMemsetAsync(c->alpha, 0, c->Dp * sizeof(float), c->stream));
     CKB(cudaMemsetAsync(c->yv, 0, c->Np * sizeof(float), c->stream));
-    // a small counter block for input checks before any fit workspace exists
-    // (the tensor-core plan is made on the first fit, once Phi is resident)
-    const bool use_tc = c->use_tc;
-    c->use_tc = false;
-    st = ensure_workspace(c, 1);
-    c->use_tc = use_tc;
-    if (st) return bail(st);
+    // one device word for the finiteness checks of inputs (the fit workspace,
+    // and the tensor-core plan with it, is made by the first call that needs it)
+    if ((st = dalloc(c, &c->check_flag, 1))) return bail(st);
 
     if (kind == COFEM_OP_DENSE) {
         // upload into a padded FP32 copy (zero rows/columns beyond N, D)
@@ -462,6 +456,7 @@ cofem_status cofem_destroy(cofem_ctx* c) {
     dfree(c, &c->s_out, (size_t)c->Dp);
     dfree(c, &c->yv, (size_t)c->Np);
     dfree(c, &c->iters_dev, (size_t)c->iters_cap);
+    dfree(c, &c->check_flag, 1);
     dfree(c, &c->ctl, 1);
     delete c->ctl_host;
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

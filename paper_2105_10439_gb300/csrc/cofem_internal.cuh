@@ -193,16 +193,20 @@ __device__ __forceinline__ size_t swz32_offset(int row, long long col, int rows_
     return (size_t)k * rows_per_tile * 32 + (size_t)row * 32 + (size_t)((((cc >> 2) ^ (row & 7)) << 2) | (cc & 3));
 }
 
-// TF32 split v = hi + lo with hi = v truncated to TF32 (what the tensor core
-// reads) and lo = v - hi (exact): hi at row q, lo at row QH + q of the tiled
-// fp32 image (columns j..j+3, j % 4 == 0: one 16-byte chunk).
+// Round to the nearest TF32 value (10 explicit mantissa bits, ties away from
+// zero), kept as an FP32 bit pattern whose low 13 bits are zero, so the tensor
+// core reads it exactly.
+__device__ __forceinline__ float tf32_rn(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// TF32 split v = hi + lo with hi = tf32_rn(v) and lo = tf32_rn(v - hi): hi at row
+// q, lo at row QH + q of the tiled fp32 image (columns j..j+3, j % 4 == 0: one
+// 16-byte chunk).
 __device__ __forceinline__ void store_split_tf32(float* Vs, int QS, int QH, int q, long long j, float4 v) {
     float4 hi, lo;
-    hi.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
-    hi.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
-    hi.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
-    hi.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
-    lo = make_float4(v.x - hi.x, v.y - hi.y, v.z - hi.z, v.w - hi.w);
+    hi = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
+    lo = make_float4(tf32_rn(v.x - hi.x), tf32_rn(v.y - hi.y), tf32_rn(v.z - hi.z), tf32_rn(v.w - hi.w));
     *reinterpret_cast<float4*>(Vs + swz32_offset(q, j, QS)) = hi;
     *reinterpret_cast<float4*>(Vs + swz32_offset(QH + q, j, QS)) = lo;
 }
@@ -359,6 +363,7 @@ struct cofem_ctx {
     double* part = nullptr;          // vector-kernel partials: 3 x Qcap x nch
     double* tt_part = nullptr;       // operator partials of ||Phi p||^2
     unsigned* counters = nullptr;    // last-block counters
+    unsigned* check_flag = nullptr;  // one word for input finiteness checks
     int* iters_dev = nullptr;        // T_em
     int iters_cap = 0;
     DevCtl* ctl = nullptr;

@@ -168,8 +168,9 @@ __device__ __forceinline__ void tmem_ld_wait(uint32_t* r, int n) {
 
 // Tensor-core skinny GEMM.  TF = false: A, B bf16 (B = 3-term split), one MMA
 // chain per tile.  TF = true: A, B fp32 read as TF32 (B = [P_hi | P_lo]); the
-// epilogue warps also write Phi_lo = A - tf32(A) next to each A tile and a
-// second MMA chain adds Phi_lo * P_hi into the same accumulator columns.
+// epilogue warps round each A tile to Phi_hi = tf32_rn(A) in place and write
+// Phi_lo = tf32_rn(A - Phi_hi) beside it, and a second MMA chain adds
+// Phi_lo [P_hi | P_lo] into the same accumulator columns (all four products).
 template <bool TF>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
     constexpr int NA = TF ? TC_NA_TF : TC_NA;
@@ -286,6 +287,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
                             ok = false;
                             break;
                         }
+                        if (TF && !mbar_wait(smem_u32(lo_full + sa), par, abort_flag)) {   // hi / lo written
+                            ok = false;
+                            break;
+                        }
                         tc_fence_after();
                         const uint64_t da = desc_sw128(smem_u32(ringA + sa * TC_A_BYTES));
                         const uint32_t dt = tmem + (uint32_t)(r * p.acc_stride);
@@ -296,11 +301,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
                             else mma_bf16(dt, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), p.idesc, acc);
                         }
                         if (TF) {
-                            if (!mbar_wait(smem_u32(lo_full + sa), par, abort_flag)) {
-                                ok = false;
-                                break;
-                            }
-                            tc_fence_after();
                             const uint64_t dl = desc_sw128(smem_u32(ringL + sa * TC_A_BYTES));
 #pragma unroll
                             for (int kk = 0; kk < KE / KM; ++kk)
@@ -343,18 +343,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
                             ok = false;
                             break;
                         }
-                        // this warp's quarter of the tile: 1024 floats, 8 float4 per lane
-                        const float4* src = reinterpret_cast<const float4*>(ringA + sa * TC_A_BYTES) + ew * 256;
+                        // this warp's quarter of the tile: 1024 floats, 8 float4 per lane;
+                        // x -> hi = tf32_rn(x) in place, lo = tf32_rn(x - hi) beside it
+                        float4* src = reinterpret_cast<float4*>(ringA + sa * TC_A_BYTES) + ew * 256;
                         float4* dst = reinterpret_cast<float4*>(ringL + sa * TC_A_BYTES) + ew * 256;
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
                             const float4 x = src[lane + 32 * i];
-                            float4 l;
-                            l.x = x.x - __uint_as_float(__float_as_uint(x.x) & 0xFFFFE000u);
-                            l.y = x.y - __uint_as_float(__float_as_uint(x.y) & 0xFFFFE000u);
-                            l.z = x.z - __uint_as_float(__float_as_uint(x.z) & 0xFFFFE000u);
-                            l.w = x.w - __uint_as_float(__float_as_uint(x.w) & 0xFFFFE000u);
-                            dst[lane + 32 * i] = l;
+                            const float4 h = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
+                            src[lane + 32 * i] = h;
+                            dst[lane + 32 * i] = make_float4(tf32_rn(x.x - h.x), tf32_rn(x.y - h.y),
+                                                             tf32_rn(x.z - h.z), tf32_rn(x.w - h.w));
                         }
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                         __syncwarp();
@@ -556,7 +555,7 @@ cudaError_t plan_gemm(GemmPlan& gp, int num_sms, long long M_rows, long long K_c
     p.QH = QH;
     p.Q = Q;
     p.idesc = make_idesc(TC_BM, QS, tf);
-    p.idesc_lo = make_idesc(TC_BM, tf ? QH : QS, tf);
+    p.idesc_lo = make_idesc(TC_BM, QS, tf);   // TF32: Phi_lo times [P_hi | P_lo]
     p.flags = flags;
     gp.groups = (p.M_tiles + G - 1) / G;
     p.W = (long long)gp.groups * p.K_tiles;

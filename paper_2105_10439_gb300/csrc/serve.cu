@@ -59,12 +59,12 @@ extern "C" long long cofem_estimate_bytes(int kind, long long N, long long D, lo
         const long long img = round_up_ll(Np, 512) * Dp + round_up_ll(Dp, 512) * Np;
         if (precision == COFEM_BF16) {
             b += Np * Dp * 4 + Np * Dp * 2 + img * 2;          // FP32 staging, bf16 copy, images
-        } else if (precision == COFEM_F32) {
+        } else if (precision == COFEM_F32_TF32X3) {
             b += Np * Dp * 4 + img * 4;                        // FP32 copy, images
         } else {
             b += Np * Dp * 4 + 9 * Np * QP * 4 + 8 * Q * Dp * 4;   // FP32 copy, T and slices, U slices
         }
-        if (precision != COFEM_F32_SIMT)
+        if (precision != COFEM_F32)
             b += 2 * 200 * Q * 512 * 4 + 2 * 3 * Q * (Np + Dp) * 4;   // segment partials, split blocks
     } else {
         b += L * 4 + Q * Dp * 4;

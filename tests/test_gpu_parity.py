@@ -141,7 +141,7 @@ def test_operator_dense_f32(cf, N, D, Q, precision):
     """FP32 dictionary: tensor cores with the error-compensated TF32 split, or
     FP32 FMA on the CUDA cores."""
     p = dense_gaussian(N, D, 3, 20.0, seed=Q)
-    prec = cf.COFEM_F32 if precision == "tf32x3" else cf.COFEM_F32_SIMT
+    prec = cf.COFEM_F32_TF32X3 if precision == "tf32x3" else cf.COFEM_F32
     with cf.CoFEM(N, D, cf.COFEM_OP_DENSE, torch.from_numpy(p.phi).to(DEV), precision=prec) as m:
         _check_operator(cf, m, DenseOperator(p.phi), D, Q, seed=Q)
 
@@ -212,9 +212,9 @@ def test_fit_f32_forms_agree(cf):
     within the FP32 parity tolerance, and both match the oracle."""
     from synth import workload
     p, run = workload("dense_n256_d1024_k20")
-    a = gpu_fit(cf, p, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], seed=run["seed"], precision=cf.COFEM_F32)
-    b = gpu_fit(cf, p, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], seed=run["seed"],
-                precision=cf.COFEM_F32_SIMT)
+    a = gpu_fit(cf, p, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], seed=run["seed"],
+                precision=cf.COFEM_F32_TF32X3)
+    b = gpu_fit(cf, p, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], seed=run["seed"], precision=cf.COFEM_F32)
     r = oracle_fit(p, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], seed=run["seed"])
     assert_fit_close(a, r)
     assert_fit_close(b, r)
