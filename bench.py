@@ -39,6 +39,9 @@ def _dist():
     return ws, rank, local
 
 
+# --dense-path -> cofem_opts.dense_path
+_DENSE_PATHS = {"auto": 0, "two_pass": 1, "single_pass": 2}
+
 # workload precision name -> C-ABI precision code
 _PRECISIONS = {"f32": lambda cf: cf.COFEM_F32, "bf16": lambda cf: cf.COFEM_BF16,
                "tf32x3": lambda cf: cf.COFEM_F32_TF32X3}
@@ -187,15 +190,16 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _launches_per_fit(cg_iters, rr_period, op_kernels):
+def _launches_per_fit(cg_iters, rr_period, op_cg, op_rr):
     """Kernels of one fit: b = beta Phi^T y, finiteness check of y, fit set-up;
-    per EM iteration init + M-step; per CG step the operator kernels, update and
-    direction; per residual replacement the operator kernels and the residual."""
+    per EM iteration init + M-step; per CG step the operator kernels (op_cg),
+    update and direction; per residual replacement the operator kernels
+    (op_rr) and the residual."""
     n = 3
     for u in cg_iters:
         u = int(u)
         rr = u // rr_period if rr_period > 0 else 0
-        n += 2 + (op_kernels + 2) * u + (op_kernels + 1) * rr
+        n += 2 + (op_cg + 2) * u + (op_rr + 1) * rr
     return n
 
 
@@ -227,7 +231,8 @@ def run_ours(args):
 
     def make(precision):
         return cf.CoFEM(N, D, kind, phi_d, prob.L, precision=precision, rr_period=run["rr_period"],
-                        seed=run["seed"], stream=stream, use_graph=0 if args.no_graph else 1)
+                        seed=run["seed"], stream=stream, use_graph=0 if args.no_graph else 1,
+                        dense_path=_DENSE_PATHS[args.dense_path])
 
     def timed_fits(model, steps, warmup):
         for _ in range(warmup):
@@ -267,10 +272,17 @@ def run_ours(args):
     reps = 20
     op_ms = cf.cofem_time_operator(model.h, Q, reps)
     hbm_gbs, _, peak_kind = _peaks()
+    path, op_cg, op_rr = cf.cofem_operator_info(model.h)
     if prob.kind == "dense":
         elem = 2 if prec == cf.COFEM_BF16 else 4
-        alg_bytes = 2.0 * N * D * elem                       # Phi read twice per application
-        roof = {"bound": "hbm", "kernel": "dense operator (Phi V then Phi^T T)"}
+        if path == cf.COFEM_PATH_SINGLE_PASS:
+            # Phi read once, V read, U written
+            alg_bytes = 1.0 * N * D * elem + 2.0 * Q * D * 4
+            roof = {"bound": "hbm", "kernel": "single-pass dense operator (k_operator_fused)"}
+        else:
+            # Phi read once per product, V read, U written
+            alg_bytes = 2.0 * N * D * elem + 2.0 * Q * D * 4
+            roof = {"bound": "hbm", "kernel": "two-pass dense operator (k_gemm_tc x2 + k_tc_reduce_T)"}
     else:
         alg_bytes = 2.0 * Q * D * 4                          # read V, write U
         roof = {"bound": "hbm", "kernel": "convolution operator"}
@@ -292,8 +304,7 @@ def run_ours(args):
     e2e = {"value": ws * e2e_steps * T / e2e_s, "unit": "EM-iter/s", "h2d_bytes_per_step": int(N * 4),
            "d2h_bytes_per_step": int(3 * D * 4 + T * 4 + 4)}
 
-    op_kernels = 1 if prob.kind != "dense" else (5 if prec == cf.COFEM_BF16 else 2)
-    launches = sum(_launches_per_fit(it, run["rr_period"], op_kernels) for it in all_iters)
+    launches = sum(_launches_per_fit(it, run["rr_period"], op_cg, op_rr) for it in all_iters)
     model.close()
 
     # the FP32 forms on the same problem (precision comparison at equal NMSE):
@@ -428,7 +439,8 @@ def run_operator_only(args):
     V = torch.from_numpy(rng.standard_normal((Q, prob.D)).astype(np.float32)).to(dev)
     alpha = torch.ones(prob.D, device=dev)
     Psi = torch.empty((Q, prob.D), device=dev)
-    with cf.CoFEM(prob.N, prob.D, kind, torch.from_numpy(prob.phi).to(dev), prob.L, precision=prec) as m:
+    with cf.CoFEM(prob.N, prob.D, kind, torch.from_numpy(prob.phi).to(dev), prob.L, precision=prec,
+                  dense_path=_DENSE_PATHS[args.dense_path]) as m:
         for _ in range(args.warmup):
             cf.cofem_apply_operator(m.h, V, Q, alpha, prob.beta, Psi, want_pi=False)
         t0 = time.perf_counter()
@@ -437,7 +449,9 @@ def run_operator_only(args):
         torch.cuda.synchronize(dev)
         wall = time.perf_counter() - t0
         ms = cf.cofem_time_operator(m.h, Q, 10)
-    print(json.dumps({"operator_only": args.workload, "steps": args.steps, "wall_s": wall, "ms_per_apply": ms}))
+        path = cf.cofem_operator_info(m.h)[0]
+    print(json.dumps({"operator_only": args.workload, "dense_path": path, "steps": args.steps, "wall_s": wall,
+                      "ms_per_apply": ms}))
 
 
 def main():
@@ -454,6 +468,8 @@ def main():
     ap.add_argument("--serve", action="store_true",
                     help="only the serving measurement (2000 requests unless --serve-requests is given)")
     ap.add_argument("--serve-precision", default="bf16", choices=["f32", "bf16", "tf32x3"])
+    ap.add_argument("--dense-path", default="auto", choices=sorted(_DENSE_PATHS),
+                    help="BF16 dense operator form (default: the library's choice)")
     ap.add_argument("--em-iters", type=int, default=0,
                     help="override T (profiling runs only; the benchmark line uses the workload's T)")
     ap.add_argument("--no-graph", action="store_true",

@@ -92,10 +92,26 @@ typedef struct cofem_opts {
     int use_graph;            /* 1 (default): the whole fit is one CUDA-graph launch whose EM and
                                  CG loops are device-side conditional WHILE nodes;
                                  0: host-driven loop (one host sync per CG iteration) */
+    int dense_path;           /* BF16 dense operator: COFEM_PATH_AUTO (default),
+                                 COFEM_PATH_TWO_PASS or COFEM_PATH_SINGLE_PASS */
 } cofem_opts;
 
+/* Dense BF16 operator forms.  TWO_PASS streams the dictionary for Phi V and a
+ * transposed copy for Phi^T T (2 N D bytes of HBM per application).
+ * SINGLE_PASS reads each dictionary tile from HBM once: a cooperative kernel
+ * (one CTA per SM) forms Phi V for a wave of rows, then Phi^T T from the same
+ * tiles while they are still in L2; it needs 3(K+1) <= 128, at most two
+ * 128-column tiles of D per SM, and occupies the whole GPU while it runs.
+ * AUTO takes TWO_PASS (on GB300 the two-pass kernels are faster so far: the
+ * single-pass kernel is bound by its shared-memory fill, not by HBM).
+ * Requesting SINGLE_PASS where it does not apply makes the first fit or
+ * application fail with COFEM_ERR_UNSUPPORTED. */
+#define COFEM_PATH_AUTO        0
+#define COFEM_PATH_TWO_PASS    1
+#define COFEM_PATH_SINGLE_PASS 2
+
 /* Fill *o with the defaults: F32, Jacobi, per-column, rr_period 0,
- * alpha_max 1e12, seed 2, stream NULL, use_graph 1. */
+ * alpha_max 1e12, seed 2, stream NULL, use_graph 1, dense_path AUTO. */
 void cofem_default_opts(cofem_opts* o);
 
 /* Create a handle for one dictionary (step a0: upload, optional BF16
@@ -257,6 +273,15 @@ cofem_status cofem_apply_dense_noalloc(const float* phi, long long N, long long 
 
 /* Bytes of device memory the handle holds (Phi copy, theta, fit workspace). */
 long long cofem_device_bytes(struct cofem_ctx* h);
+
+/* How the operator of Alg. 2 is applied for the current Q (valid after a fit
+ * or cofem_apply_operator): *path = COFEM_PATH_TWO_PASS or
+ * COFEM_PATH_SINGLE_PASS for a BF16 or 3xTF32 dense dictionary, COFEM_PATH_AUTO
+ * (0) for the CUDA-core forms (FP32 FMA, convolution); *kernels_cg = kernels
+ * launched per application inside the CG loop; *kernels_rr = per application
+ * in a residual replacement.  Any output pointer may be NULL.  Errors:
+ * INVALID_ARG (NULL handle, or no fit or application yet). */
+cofem_status cofem_operator_info(struct cofem_ctx* h, int* path, int* kernels_cg, int* kernels_rr);
 
 #ifdef __cplusplus
 }

@@ -34,6 +34,9 @@ COFEM_PRECOND_JACOBI = 0
 COFEM_PRECOND_ONE = 1
 COFEM_CONV_PER_COLUMN = 0
 COFEM_CONV_FROBENIUS = 1
+COFEM_PATH_AUTO = 0
+COFEM_PATH_TWO_PASS = 1
+COFEM_PATH_SINGLE_PASS = 2
 COFEM_FLAG_CG_NOT_CONVERGED = 1
 COFEM_FLAG_ALPHA_CLAMPED = 2
 COFEM_FLAG_BREAKDOWN = 4
@@ -49,6 +52,7 @@ class cofem_opts(C.Structure):
         ("seed", C.c_ulonglong),
         ("stream", C.c_void_p),
         ("use_graph", C.c_int),
+        ("dense_path", C.c_int),
     ]
 
 
@@ -92,6 +96,7 @@ def _load():
         "cofem_get_theta": (i, [vp, vp]),
         "cofem_phit_y": (i, [vp, vp, d, vp]),
         "cofem_device_bytes": (ll, [vp]),
+        "cofem_operator_info": (i, [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
         "cofem_time_operator": (i, [vp, i, i, C.POINTER(d)]),
         "cofem_apply_dense_noalloc": (i, [vp, ll, ll, ll, vp, i, vp, d, vp, vp]),
         "cofem_estimate_bytes": (ll, [i, ll, ll, ll, i, i]),
@@ -242,6 +247,13 @@ def cofem_server_destroy(srv: int) -> None:
 
 def cofem_device_bytes(h: int) -> int:
     return int(lib.cofem_device_bytes(h))
+
+
+def cofem_operator_info(h: int) -> tuple[int, int, int]:
+    """(path, kernels per CG-loop application, kernels per residual replacement)."""
+    path, kc, kr = C.c_int(), C.c_int(), C.c_int()
+    _check(lib.cofem_operator_info(h, C.byref(path), C.byref(kc), C.byref(kr)))
+    return path.value, kc.value, kr.value
 
 
 class CoFEM:

@@ -152,6 +152,9 @@ cofem_status ensure_workspace(cofem_ctx* c, int Q) {
         cudaError_t e = tc_setup(c, Q);
         if (e != cudaSuccess) {
             free_workspace(c);
+            if (e == cudaErrorNotSupported)
+                return fail(COFEM_ERR_UNSUPPORTED,
+                            "the single-pass dense operator needs BF16, 3(K+1) <= 128 and D <= 256 x SMs");
             return cuda_fail(e, "tensor-core operator set-up");
         }
     }
@@ -331,6 +334,8 @@ cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, c
     if (opts) o = *opts;
     if (kind == COFEM_OP_DENSE) {
         if (L != 0) return fail(COFEM_ERR_INVALID_ARG, "L must be 0 for a dense dictionary");
+        if (o.dense_path < COFEM_PATH_AUTO || o.dense_path > COFEM_PATH_SINGLE_PASS)
+            return fail(COFEM_ERR_INVALID_ARG, "dense_path must be AUTO, TWO_PASS or SINGLE_PASS");
         if (o.precision != COFEM_F32 && o.precision != COFEM_BF16 && o.precision != COFEM_F32_TF32X3)
             return fail(COFEM_ERR_INVALID_ARG, "precision must be COFEM_F32, COFEM_BF16 or COFEM_F32_TF32X3");
     } else if (kind == COFEM_OP_TOEPLITZ) {
@@ -634,5 +639,21 @@ cofem_status cofem_time_operator(cofem_ctx* c, int Q, int reps, double* ms_per_a
 }
 
 long long cofem_device_bytes(cofem_ctx* c) { return c ? c->bytes : 0; }
+
+cofem_status cofem_operator_info(cofem_ctx* c, int* path, int* kernels_cg, int* kernels_rr) {
+    g_err[0] = 0;
+    if (!c) return fail(COFEM_ERR_INVALID_ARG, "handle is NULL");
+    if (c->Qcap == 0) return fail(COFEM_ERR_INVALID_ARG, "no fit or application yet");
+    int pth = COFEM_PATH_AUTO, kc = 1, kr = 1;
+    if (c->kind == COFEM_OP_DENSE && c->use_tc) {
+        tc_operator_info(c, &pth, &kc, &kr);
+    } else if (c->kind == COFEM_OP_DENSE) {
+        kc = kr = 2;   // k_gemm1_simt, k_gemm2_simt
+    }
+    if (path) *path = pth;
+    if (kernels_cg) *kernels_cg = kc;
+    if (kernels_rr) *kernels_rr = kr;
+    return COFEM_OK;
+}
 
 }  // extern "C"

@@ -11,7 +11,7 @@
 #include "../../include/cofem.h"
 
 #define COFEM_QMAX 64          // K <= 63
-#define COFEM_VEC_CHUNK 1024   // elements of one column handled by a vector-kernel block
+#define COFEM_VEC_CHUNK 4096   // elements of one column handled by a vector-kernel block
 #define COFEM_VEC_THREADS 256
 
 // ---------------------------------------------------------------------------
@@ -295,6 +295,44 @@ struct Sink {
         if (err == cudaSuccess) last = n;
     }
 
+    // Cooperative launch (all CTAs co-resident; the kernel may wait on other CTAs).
+    template <typename... P, typename... A>
+    void launch_cooperative(void (*f)(P...), dim3 grid, dim3 block, size_t smem, A... args) {
+        if (err != cudaSuccess) return;
+        coop_typed<P...>(f, grid, block, smem, static_cast<P>(args)...);
+    }
+
+    template <typename... P>
+    void coop_typed(void (*f)(P...), dim3 grid, dim3 block, size_t smem, P... args) {
+        void* ptrs[sizeof...(P) > 0 ? sizeof...(P) : 1] = {(void*)&args...};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        if (!graph) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = grid;
+            cfg.blockDim = block;
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = stream;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            err = cudaLaunchKernelExC(&cfg, (const void*)f, ptrs);
+            return;
+        }
+        cudaKernelNodeParams p = {};
+        p.func = (void*)f;
+        p.gridDim = grid;
+        p.blockDim = block;
+        p.sharedMemBytes = (unsigned)smem;
+        p.kernelParams = ptrs;
+        p.extra = nullptr;
+        cudaGraphNode_t n;
+        err = cudaGraphAddKernelNode(&n, graph, last ? &last : nullptr, last ? 1 : 0, &p);
+        if (err != cudaSuccess) return;
+        err = cudaGraphKernelNodeSetAttribute(n, cudaLaunchAttributeCooperative, &attr[0].val);
+        if (err == cudaSuccess) last = n;
+    }
+
     // Conditional handle owned by this sink's graph (0 in direct mode).
     cudaGraphConditionalHandle make_handle(unsigned default_value, bool assign_default) {
         cudaGraphConditionalHandle h = 0;
@@ -469,6 +507,19 @@ __device__ __forceinline__ void op_finalize_block(DevCtl* ctl, const double* tt_
     act = __syncthreads_or(act);
     if (threadIdx.x == 0 && mode == OP_CG) ctl->any_active = act;
 }
+
+void tc_operator_info(cofem_ctx* c, int* path, int* k_cg, int* k_rr);
+
+// Single-pass BF16 dense operator (kernels_fused.cu).
+struct FusedPlan;
+size_t fused_smem_bytes(int QS);
+bool fused_supported(int num_sms, long long Dp, int QS, bool coop, int max_smem);
+cudaError_t fused_create(FusedPlan** out, int num_sms, long long Np, long long Dp, int Q, int QS,
+                         const void* A_image, const void* Bv, void* Bt, float* U, DevCtl* ctl, cudaStream_t st,
+                         long long* bytes);
+void fused_destroy(FusedPlan* f, cudaStream_t st);
+void launch_fused(Sink& s, const FusedPlan* f, int mode);
+cudaError_t fused_kernel_attributes(int max_smem);
 
 // Records a failure message for cofem_last_error() (cofem_api.cu) and returns st.
 cofem_status cofem_set_error(cofem_status st, const char* msg);

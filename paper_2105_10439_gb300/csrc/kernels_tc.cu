@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "cofem_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace {
 
@@ -43,7 +44,6 @@ constexpr int TC_BK32 = 32;               // TF32 tile: 128 rows x 32 fp32 (128-
 constexpr int TC_NA = 8, TC_NA_TF = 5, TC_NB = 3;
 constexpr int TC_THREADS = 192;
 constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK * 2;
-constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
 constexpr uint32_t TC_TMEM_COLS = 512;
 
 struct TcParams {
@@ -64,108 +64,6 @@ struct TcParams {
     unsigned* flags;      // error flag word (DevCtl::flags)
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait for the completion of the phase with the given parity.  Returns
-// false on timeout (and raises the block's abort flag) or when another role
-// has already aborted.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-    for (uint32_t i = 0; i < TC_WAIT_LIMIT; ++i) {
-        if (mbar_try(bar, parity)) return true;
-        if ((i & 127) == 127) {
-            if (*abort_flag) return false;
-            __nanosleep(64);
-        }
-    }
-    *abort_flag = 1;
-    return false;
-}
-// Bounded wait that ignores the abort flag (used to drain in-flight work).
-__device__ __noinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
-    for (uint32_t i = 0; i < TC_WAIT_LIMIT; ++i) {
-        if (mbar_try(bar, parity)) return;
-        if ((i & 127) == 127) __nanosleep(64);
-    }
-}
-
-// 1-D bulk copy global -> shared, completion counted on an mbarrier.
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"((uint64_t)src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-// Same, with an L2 policy (evict-first for data streamed once).
-__device__ __forceinline__ void bulk_load_hint(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar,
-                                               uint64_t policy) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
-            "r"(dst),
-        "l"((uint64_t)src), "r"(bytes), "r"(bar), "l"(policy)
-        : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row core-matrix groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
-    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                         uint32_t accum) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accum));
-}
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                         uint32_t accum) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accum));
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
-// Registers written by tcgen05.ld are valid only after tcgen05.wait::ld; the
-// empty asm statements re-define them after the wait so no use moves above it.
-__device__ __forceinline__ void tmem_ld_wait(uint32_t* r, int n) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    for (int i = 0; i < n; i += 8)
-        asm volatile("" : "+r"(r[i]), "+r"(r[i + 1]), "+r"(r[i + 2]), "+r"(r[i + 3]), "+r"(r[i + 4]),
-                     "+r"(r[i + 5]), "+r"(r[i + 6]), "+r"(r[i + 7]));
-}
-
 // Tensor-core skinny GEMM.  TF = false: A, B bf16 (B = 3-term split), one MMA
 // chain per tile.  TF = true: A, B fp32 read as TF32 (B = [P_hi | P_lo]); the
 // epilogue warps round each A tile to Phi_hi = tf32_rn(A) in place and write
@@ -175,6 +73,12 @@ template <bool TF>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
     constexpr int NA = TF ? TC_NA_TF : TC_NA;
     constexpr int KE = TF ? TC_BK32 : TC_BK;    // elements per 128-byte tile row
+    // A-ring element: one tile (TF32, converted tile by tile) or the G row
+    // tiles of a unit, fetched as one bulk copy (a copy costs a fixed ~0.3 us
+    // of issue time, so fewer, larger copies keep the stream at HBM rate)
+    const int EPT = TF ? 1 : p.G;
+    const int NE = TF ? NA : NA / p.G;           // ring elements
+    const uint32_t E_BYTES = (uint32_t)EPT * TC_A_BYTES;
     constexpr int KM = TF ? 8 : 16;             // K of one MMA instruction
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -244,16 +148,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
                 bulk_load(smem_u32(ringB + slot * B_BYTES), Bb + (size_t)k * B_BYTES, B_BYTES, smem_u32(b_full + slot));
                 ++nb;
                 bool ok = true;
-                for (int r = 0; r < valid; ++r) {
-                    slot = (int)(na % NA);
-                    use = na / NA;
+                for (int r = 0; r < (TF ? valid : 1); ++r) {
+                    slot = (int)(na % NE);
+                    use = na / NE;
                     if (use > 0 && !mbar_wait(smem_u32(a_empty + slot), (uint32_t)((use - 1) & 1), abort_flag)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(smem_u32(a_full + slot), TC_A_BYTES);
-                    bulk_load_hint(smem_u32(ringA + slot * TC_A_BYTES), Ab + ((size_t)u * p.G + r) * TC_A_BYTES,
-                                   TC_A_BYTES, smem_u32(a_full + slot), evict_first);
+                    // BF16: all G tiles of the unit (tiles beyond M_tiles are zero in the image)
+                    mbar_expect_tx(smem_u32(a_full + slot), E_BYTES);
+                    bulk_load_hint(smem_u32(ringA + slot * E_BYTES), Ab + ((size_t)u * p.G + r) * TC_A_BYTES,
+                                   E_BYTES, smem_u32(a_full + slot), evict_first);
                     ++na;
                 }
                 if (!ok) break;
@@ -280,19 +185,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
                         break;
                     }
                     const uint64_t db = desc_sw128(smem_u32(ringB + sb * B_BYTES));
+                    int sa = 0;
                     for (int r = 0; r < valid; ++r) {
-                        const int sa = (int)(ma % NA);
-                        const uint32_t par = (uint32_t)((ma / NA) & 1);
-                        if (!mbar_wait(smem_u32(a_full + sa), par, abort_flag)) {
-                            ok = false;
-                            break;
+                        if (TF || r == 0) {
+                            sa = (int)(ma % NE);
+                            const uint32_t par = (uint32_t)((ma / NE) & 1);
+                            if (!mbar_wait(smem_u32(a_full + sa), par, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            if (TF && !mbar_wait(smem_u32(lo_full + sa), par, abort_flag)) {   // hi / lo written
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
                         }
-                        if (TF && !mbar_wait(smem_u32(lo_full + sa), par, abort_flag)) {   // hi / lo written
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint64_t da = desc_sw128(smem_u32(ringA + sa * TC_A_BYTES));
+                        const uint64_t da =
+                            desc_sw128(smem_u32(ringA + sa * E_BYTES + (TF ? 0 : r) * TC_A_BYTES));
                         const uint32_t dt = tmem + (uint32_t)(r * p.acc_stride);
 #pragma unroll
                         for (int kk = 0; kk < KE / KM; ++kk) {
@@ -306,8 +215,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
                             for (int kk = 0; kk < KE / KM; ++kk)
                                 mma_tf32(dt, dl + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), p.idesc_lo, 1u);
                         }
-                        mma_commit(smem_u32(a_empty + sa));
-                        ++ma;
+                        if (TF || r == valid - 1) {   // the element is free once its MMAs are done
+                            mma_commit(smem_u32(a_empty + sa));
+                            ++ma;
+                        }
                     }
                     if (!ok) break;
                     mma_commit(smem_u32(b_empty + sb));
@@ -406,8 +317,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
     if (threadIdx.x == 0 && *abort_flag) {
         // some role gave up: the latest load issued into every ring slot must
         // land before the CTA exits
-        for (int s = 0; s < NA; ++s) {
-            const long long n_s = na > s ? (na - s + NA - 1) / NA : 0;
+        for (int s = 0; s < NE; ++s) {
+            const long long n_s = na > s ? (na - s + NE - 1) / NE : 0;
             if (n_s > 0) mbar_drain(smem_u32(a_full + s), (uint32_t)((n_s - 1) & 1));
         }
         for (int s = 0; s < TC_NB; ++s) {
@@ -445,8 +356,9 @@ __global__ __launch_bounds__(256) void k_tc_reduce_T(const float* __restrict__ p
         const int g = (int)(i / GR), r = (int)(i % GR);
         const int s0 = grp_seg[2 * g], ns = grp_seg[2 * g + 1];
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 8
         for (int s = 0; s < ns; ++s) {
-            const float4 b = *reinterpret_cast<const float4*>(part + ((size_t)(s0 + s) * Q + q) * GR + r);
+            const float4 b = __ldcg(reinterpret_cast<const float4*>(part + ((size_t)(s0 + s) * Q + q) * GR + r));
             a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
         }
         store_split(so, q, i, a);
@@ -536,6 +448,9 @@ struct TcPlan {
     void* Ts = nullptr;              // tiled image of split(T), QS x Np
     size_t esz = 2;                  // bytes per image element
     GemmPlan g1, g2;
+    FusedPlan* fused = nullptr;      // single-pass form (then g1, g2 are unused)
+    void* fimg = nullptr;            // its tiled image of Phi~ (groups of 2 row tiles)
+    size_t fimg_bytes = 0;
     long long bytes = 0;
 };
 
@@ -624,6 +539,8 @@ void tc_release(cofem_ctx* c) {
     if (!t) return;
     free_gemm(t->g1, c->stream);
     free_gemm(t->g2, c->stream);
+    fused_destroy(t->fused, c->stream);
+    if (t->fimg) cudaFreeAsync(t->fimg, c->stream);
     if (t->Vs) cudaFreeAsync(t->Vs, c->stream);
     if (t->Ts) cudaFreeAsync(t->Ts, c->stream);
     c->bytes -= t->bytes;
@@ -662,6 +579,34 @@ cudaError_t tc_setup(cofem_ctx* c, int Q) {
     cudaError_t e;
     unsigned* flags = &c->ctl->flags;
     cudaStream_t st = c->stream;
+    // single-pass form: BF16, where it applies, on request (AUTO takes the
+    // two-pass form, the faster of the two as measured on GB300 so far)
+    int coop = 0, max_smem = 0;
+    if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device))) return e;
+    if ((e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device))) return e;
+    const bool can_fuse = !t->tf && fused_supported(c->num_sms, c->Dp, t->QS, coop != 0, max_smem);
+    const int path = c->opts.dense_path;
+    if (path == COFEM_PATH_SINGLE_PASS && !can_fuse) return cudaErrorNotSupported;
+    if (can_fuse && path == COFEM_PATH_SINGLE_PASS) {
+        const int G = 2;
+        const long long M_tiles = c->Np / TC_BM, K_tiles = c->Dp / TC_BK, groups = (M_tiles + G - 1) / G;
+        t->fimg_bytes = (size_t)groups * G * K_tiles * TC_A_BYTES;
+        if ((e = cudaMallocAsync(&t->fimg, t->fimg_bytes, st))) return e;
+        if ((e = cudaMallocAsync(&t->Vs, (size_t)t->QS * c->Dp * t->esz, st))) return e;
+        if ((e = cudaMallocAsync(&t->Ts, (size_t)t->QS * c->Np * t->esz, st))) return e;
+        t->bytes += (long long)t->fimg_bytes + (long long)t->QS * (c->Dp + c->Np) * (long long)t->esz;
+        if ((e = cudaMemsetAsync(t->Vs, 0, (size_t)t->QS * c->Dp * t->esz, st))) return e;
+        if ((e = cudaMemsetAsync(t->Ts, 0, (size_t)t->QS * c->Np * t->esz, st))) return e;
+        k_tile_rows<__nv_bfloat16><<<dim3((unsigned)K_tiles, (unsigned)(groups * G)), 128, 0, st>>>(
+            c->phi16, c->Dp, (int)M_tiles, (int)K_tiles, G, (__nv_bfloat16*)t->fimg);
+        if ((e = cudaGetLastError())) return e;
+        if ((e = fused_create(&t->fused, c->num_sms, c->Np, c->Dp, Q, t->QS, t->fimg, t->Vs, t->Ts, c->U, c->ctl,
+                              st, &t->bytes)))
+            return e;
+        c->bytes += t->bytes;
+        t->smem = fused_smem_bytes(t->QS);
+        return cudaStreamSynchronize(st);
+    }
     if ((e = plan_gemm(t->g1, c->num_sms, c->Np, c->Dp, KE, t->G, acc_stride, t->QS, t->QH, Q, t->tf, flags,
                        &t->bytes, st)))
         return e;
@@ -699,6 +644,7 @@ cudaError_t tc_setup(cofem_ctx* c, int Q) {
 cudaError_t tc_kernel_attributes(int max_smem) {
     cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e != cudaSuccess) return e;
+    if ((e = fused_kernel_attributes(max_smem)) != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
 }
 
@@ -710,6 +656,7 @@ SplitOut tc_direction_split(cofem_ctx* c) {
 
 OpOut op_output(cofem_ctx* c) {
     TcPlan* t = (TcPlan*)c->tc;
+    if (c->kind == COFEM_OP_DENSE && t && t->fused) return OpOut{c->U, 1, (size_t)c->Qcap * c->Dp, nullptr, 0};
     if (c->kind == COFEM_OP_DENSE && t) return OpOut{t->g2.part, 1, 0, t->g2.grp_seg, t->G * TC_BM};
     const int S2 = c->kind == COFEM_OP_DENSE ? c->S2 : 1;
     return OpOut{c->U, S2, (size_t)c->Qcap * c->Dp, nullptr, 0};
@@ -725,6 +672,10 @@ void launch_tc_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode) 
     const SplitOut st{t->Ts, t->tf ? 2 : 1, t->QS, t->QH};
     if (mode == OP_RR || mode == OP_PLAIN)
         s.launch(k_split, dim3((unsigned)((c->Dp / 4 + 255) / 256), Q), dim3(256), 0, V, c->Dp, sv);
+    if (t->fused) {   // writes U and finishes pi, gamma itself
+        launch_fused(s, t->fused, mode);
+        return;
+    }
     void (*gemm)(TcParams) = t->tf ? k_gemm_tc<true> : k_gemm_tc<false>;
     s.launch(gemm, dim3(t->g1.nCTA), dim3(TC_THREADS), t->smem, t->g1.p);
     const int nblk = (int)((c->Np + 1023) / 1024);
@@ -734,4 +685,12 @@ void launch_tc_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode) 
     if (mode == OP_PLAIN)
         s.launch(k_tc_reduce_U, dim3((unsigned)((c->Dp + 1023) / 1024), Q), dim3(256), 0, t->g2.part,
                  t->g2.grp_seg, t->G * TC_BM, Q, c->Dp, c->U);
+}
+
+// Operator form in use and kernels per application (CG loop, residual replacement).
+void tc_operator_info(cofem_ctx* c, int* path, int* k_cg, int* k_rr) {
+    TcPlan* t = (TcPlan*)c->tc;
+    *path = t->fused ? COFEM_PATH_SINGLE_PASS : COFEM_PATH_TWO_PASS;
+    *k_cg = t->fused ? 1 : 3;
+    *k_rr = *k_cg + 1;   // k_split of X first
 }

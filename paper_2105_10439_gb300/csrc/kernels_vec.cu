@@ -20,14 +20,22 @@ __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<floa
 // Sum the per-block partials part[(k*Q + q)*nch + ch] over ch for k < nk,
 // into out[k*COFEM_QMAX + q] (shared).  One warp per (k, q).
 __device__ void reduce_parts(const double* part, int nk, int Q, int nch, double* out) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int kq = w; kq < nk * Q; kq += nw) {
+    // one (slab, column) per thread: its nch partials are independent loads,
+    // issued together, then added in order (one L2 round trip, fixed order)
+    for (int kq = threadIdx.x; kq < nk * Q; kq += blockDim.x) {
         const int k = kq / Q, q = kq % Q;
         const double* src = part + (size_t)(k * Q + q) * nch;
         double v = 0.0;
-        for (int i = lane; i < nch; i += 32) v += __ldcg(src + i);
-        v = warp_sum(v);
-        if (lane == 0) out[k * COFEM_QMAX + q] = v;
+        int i = 0;
+        for (; i + 8 <= nch; i += 8) {
+            double x[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) x[t] = __ldcg(src + i + t);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v += x[t];
+        }
+        for (; i < nch; ++i) v += __ldcg(src + i);
+        out[k * COFEM_QMAX + q] = v;
     }
     __syncthreads();
 }

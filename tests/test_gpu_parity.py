@@ -146,18 +146,42 @@ def test_operator_dense_f32(cf, N, D, Q, precision):
         _check_operator(cf, m, DenseOperator(p.phi), D, Q, seed=Q)
 
 
+PATHS = {"two_pass": 1, "single_pass": 2}
+
+
+@pytest.mark.parametrize("path", ["two_pass", "single_pass"])
 @pytest.mark.parametrize("N,D,Q", [(77, 301, 5), (256, 1024, 33), (1000, 3000, 17), (300, 700, 64),
-                                   (2500, 10000, 33), (128, 128, 2)])
-def test_operator_dense_bf16(cf, N, D, Q):
-    """The BF16 form runs exactly on the quantised dictionary bf16(Phi)."""
+                                   (2500, 10000, 33), (128, 128, 2), (1, 5, 1), (1153, 4000, 42), (640, 9000, 9)])
+def test_operator_dense_bf16(cf, N, D, Q, path):
+    """The BF16 form runs exactly on the quantised dictionary bf16(Phi), in
+    both operator forms (the single-pass form takes 3Q <= 128)."""
+    if path == "single_pass" and 3 * Q > 128:
+        pytest.skip("single-pass form needs 3Q <= 128")
     p = dense_gaussian(N, D, 3, 20.0, seed=Q + 1)
-    with cf.CoFEM(N, D, cf.COFEM_OP_DENSE, p.phi, precision=cf.COFEM_BF16) as m:
+    with cf.CoFEM(N, D, cf.COFEM_OP_DENSE, p.phi, precision=cf.COFEM_BF16, dense_path=PATHS[path]) as m:
         _check_operator(cf, m, DenseOperator(bf16_round(p.phi)), D, Q, seed=Q)
+        assert cf.cofem_operator_info(m.h)[0] == PATHS[path]
 
 
-def test_operator_dense_bf16_full_size_sampled(cf):
+def test_single_pass_rejected_where_it_does_not_apply(cf):
+    p = dense_gaussian(100, 300, 3, 20.0, seed=1)
+    with cf.CoFEM(100, 300, cf.COFEM_OP_DENSE, p.phi, precision=cf.COFEM_BF16, dense_path=2) as m:
+        V = torch.zeros((50, 300), device=DEV)
+        with pytest.raises(cf.CofemError) as e:   # 3 x 50 > 128
+            cf.cofem_apply_operator(m.h, V, 50, torch.ones(300, device=DEV), 1.0, torch.empty((50, 300), device=DEV))
+        assert e.value.status == cf.COFEM_ERR_UNSUPPORTED
+    with cf.CoFEM(100, 300, cf.COFEM_OP_DENSE, p.phi, precision=cf.COFEM_F32_TF32X3, dense_path=2) as m:
+        V = torch.zeros((3, 300), device=DEV)
+        with pytest.raises(cf.CofemError) as e:   # BF16 only
+            cf.cofem_apply_operator(m.h, V, 3, torch.ones(300, device=DEV), 1.0, torch.empty((3, 300), device=DEV))
+        assert e.value.status == cf.COFEM_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("path", ["auto", "single_pass"])
+def test_operator_dense_bf16_full_size_sampled(cf, path):
     """8192 x 32768 BF16 dictionary, 33 columns, in the launch configuration of
-    the benchmark: sampled rows of Psi against FP64 on the quantised dictionary."""
+    the benchmark (the default, two-pass form) and in the single-pass form:
+    sampled rows of Psi against FP64 on the quantised dictionary."""
     N, D, Q = 8192, 32768, 33
     p = dense_gaussian(N, D, 4, 30.0, seed=77)
     phq = bf16_round(p.phi)
@@ -165,10 +189,12 @@ def test_operator_dense_bf16_full_size_sampled(cf):
     V = rng.standard_normal((Q, D)).astype(np.float32)
     alpha = np.exp(rng.uniform(-2, 6, D)).astype(np.float32)
     beta = 1234.5
-    with cf.CoFEM(N, D, cf.COFEM_OP_DENSE, torch.from_numpy(p.phi).to(DEV), precision=cf.COFEM_BF16) as m:
+    with cf.CoFEM(N, D, cf.COFEM_OP_DENSE, torch.from_numpy(p.phi).to(DEV), precision=cf.COFEM_BF16,
+                  dense_path={"auto": 0, "single_pass": 2}[path]) as m:
         Psi = torch.empty((Q, D), device=DEV)
         pi = cf.cofem_apply_operator(m.h, torch.from_numpy(V).to(DEV), Q, torch.from_numpy(alpha).to(DEV),
                                      beta, Psi)
+        assert cf.cofem_operator_info(m.h)[0] == (1 if path == "auto" else 2)
     got = Psi.cpu().numpy()
     T = np.zeros((N, Q))
     for i0 in range(0, N, 1024):                      # T = Phi~ V in FP64, by row blocks
@@ -279,11 +305,27 @@ def test_fit_toeplitz_small(cf):
     assert_fit_close(g, r)
 
 
-def test_fit_bf16_matches_oracle_on_quantised_dictionary(cf):
+@pytest.mark.parametrize("path", ["two_pass", "single_pass"])
+def test_fit_bf16_matches_oracle_on_quantised_dictionary(cf, path):
     p = dense_gaussian(250, 500, 10, 15.0, seed=12)
-    g = gpu_fit(cf, p, 16, 10, 1e-5, 400, precision=cf.COFEM_BF16)
+    g = gpu_fit(cf, p, 16, 10, 1e-5, 400, precision=cf.COFEM_BF16, dense_path=PATHS[path])
     r = oracle_fit(p, 16, 10, 1e-5, 400, phi=bf16_round(p.phi))
     assert_fit_close(g, r)
+
+
+def test_fit_single_pass_graph_direct_and_repeat_identical(cf):
+    """The cooperative single-pass operator inside the CUDA graph and from the
+    host loop, and twice in a row: identical bits (its reductions have a fixed
+    order)."""
+    p = dense_gaussian(700, 3000, 30, 20.0, seed=9)
+    kw = dict(precision=cf.COFEM_BF16, dense_path=2)
+    a = gpu_fit(cf, p, 12, 5, 1e-6, 300, use_graph=1, **kw)
+    b = gpu_fit(cf, p, 12, 5, 1e-6, 300, use_graph=0, **kw)
+    c = gpu_fit(cf, p, 12, 5, 1e-6, 300, use_graph=1, **kw)
+    for k in ("mu", "s", "alpha", "cg_iters"):
+        np.testing.assert_array_equal(a[k], b[k])
+        np.testing.assert_array_equal(a[k], c[k])
+    assert a["flags"] == b["flags"] == c["flags"] == 0
 
 
 def test_fit_edge_cases(cf):
