@@ -100,7 +100,7 @@ typedef struct cofem_opts {
  * transposed copy for Phi^T T (2 N D bytes of HBM per application).
  * SINGLE_PASS reads each dictionary tile from HBM once: a cooperative kernel
  * (one CTA per SM) forms Phi V for a wave of rows, then Phi^T T from the same
- * tiles while they are still in L2; it needs 3(K+1) <= 128, at most two
+ * tiles while they are still in L2; it needs 3(K+1) <= 112, at most two
  * 128-column tiles of D per SM, and occupies the whole GPU while it runs.
  * AUTO takes TWO_PASS (on GB300 the two-pass kernels are faster so far: the
  * single-pass kernel is bound by its shared-memory fill, not by HBM).

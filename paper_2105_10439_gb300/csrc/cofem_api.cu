@@ -154,7 +154,7 @@ cofem_status ensure_workspace(cofem_ctx* c, int Q) {
             free_workspace(c);
             if (e == cudaErrorNotSupported)
                 return fail(COFEM_ERR_UNSUPPORTED,
-                            "the single-pass dense operator needs BF16, 3(K+1) <= 128 and D <= 256 x SMs");
+                            "the single-pass dense operator needs BF16, 3(K+1) <= 112 and D <= 256 x SMs");
             return cuda_fail(e, "tensor-core operator set-up");
         }
     }

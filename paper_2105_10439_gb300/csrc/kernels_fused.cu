@@ -37,10 +37,12 @@
 
 namespace {
 
-constexpr int FU_NA = 8, FU_NB = 3, FU_THREADS = 192, FU_BM = 128, FU_G = 2;
+constexpr int FU_NE = 4, FU_NB = 3, FU_THREADS = 192, FU_BM = 128, FU_G = 2;
 constexpr uint32_t FU_TILE = 16384;                 // 128 rows x 64 bf16
+constexpr uint32_t FU_EBYTES = FU_G * FU_TILE;      // A-ring element: one unit (G tiles), one bulk copy
 constexpr uint64_t FU_GRID_WAIT_NS = 2000000000ull; // 2 s
 constexpr int FU_ACC_STRIDE = 128;                  // TMEM columns per accumulator
+constexpr int FU_DEPTH = 2;                         // waves of phase 1 issued ahead of phase 2
 
 struct FusedParams {
     const uint8_t* A;      // tiled Phi~: tile (g, k, r) at byte ((g K_tiles + k) G + r) 16384
@@ -101,13 +103,14 @@ __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" :::
 __global__ void __launch_bounds__(FU_THREADS, 1) k_operator_fused(FusedParams p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const uint32_t B_BYTES = (uint32_t)p.QS * 128u;
+    const uint32_t B_BYTES = (uint32_t)p.QS * 128u;   // one 64-wide k tile of a split block
+    const uint32_t BS_BYTES = 2 * B_BYTES;              // B-ring slot: two k tiles
     uint8_t* ringA = smem;
-    uint8_t* ringB = smem + FU_NA * FU_TILE;
-    uint64_t* bars = (uint64_t*)(ringB + FU_NB * B_BYTES);
+    uint8_t* ringB = smem + FU_NE * FU_EBYTES;
+    uint64_t* bars = (uint64_t*)(ringB + FU_NB * BS_BYTES);
     uint64_t* a_full = bars;
-    uint64_t* a_empty = bars + FU_NA;
-    uint64_t* b_full = bars + 2 * FU_NA;
+    uint64_t* a_empty = bars + FU_NE;
+    uint64_t* b_full = bars + 2 * FU_NE;
     uint64_t* b_empty = b_full + FU_NB;
     uint64_t* acc_full = b_empty + FU_NB;
     uint64_t* acc_empty = acc_full + 1;
@@ -124,7 +127,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_operator_fused(FusedParams p)
     const int n_own = c < p.Dt ? (p.Dt - 1 - c) / n + 1 : 0;   // U tiles j = c, c + n, ...
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < FU_NA; ++i) {
+        for (int i = 0; i < FU_NE; ++i) {
             mbar_init(smem_u32(a_full + i), 1);
             mbar_init(smem_u32(a_empty + i), 1);
         }
@@ -171,27 +174,38 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_operator_fused(FusedParams p)
             // ---------------- bulk-copy producer ----------------
             uint64_t evict_first;
             asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(evict_first));
-            auto getA = [&](const uint8_t* src, bool last_use) -> bool {
-                const int slot = (int)(na % FU_NA);
-                const long long use = na / FU_NA;
+            auto getA = [&](const uint8_t* src, uint32_t bytes, bool last_use) -> bool {
+                const int slot = (int)(na % FU_NE);
+                const long long use = na / FU_NE;
                 if (use > 0 && !mbar_wait(smem_u32(a_empty + slot), (uint32_t)((use - 1) & 1), abort_flag))
                     return false;
-                mbar_expect_tx(smem_u32(a_full + slot), FU_TILE);
+                mbar_expect_tx(smem_u32(a_full + slot), bytes);
                 if (last_use)
-                    bulk_load_hint(smem_u32(ringA + slot * FU_TILE), src, FU_TILE, smem_u32(a_full + slot),
+                    bulk_load_hint(smem_u32(ringA + (size_t)slot * FU_EBYTES), src, bytes, smem_u32(a_full + slot),
                                    evict_first);
                 else
-                    bulk_load(smem_u32(ringA + slot * FU_TILE), src, FU_TILE, smem_u32(a_full + slot));
+                    bulk_load(smem_u32(ringA + (size_t)slot * FU_EBYTES), src, bytes, smem_u32(a_full + slot));
                 ++na;
                 return true;
             };
-            auto getB = [&](const uint8_t* src) -> bool {
+            // an element passed over without data (a phase-2 pair must start at an
+            // even ring position, so its two elements are adjacent in shared memory)
+            auto skipA = [&]() -> bool {
+                const int slot = (int)(na % FU_NE);
+                const long long use = na / FU_NE;
+                if (use > 0 && !mbar_wait(smem_u32(a_empty + slot), (uint32_t)((use - 1) & 1), abort_flag))
+                    return false;
+                mbar_arrive(smem_u32(a_full + slot));
+                ++na;
+                return true;
+            };
+            auto getB = [&](const uint8_t* src, uint32_t bytes) -> bool {
                 const int slot = (int)(nb % FU_NB);
                 const long long use = nb / FU_NB;
                 if (use > 0 && !mbar_wait(smem_u32(b_empty + slot), (uint32_t)((use - 1) & 1), abort_flag))
                     return false;
-                mbar_expect_tx(smem_u32(b_full + slot), B_BYTES);
-                bulk_load(smem_u32(ringB + slot * B_BYTES), src, B_BYTES, smem_u32(b_full + slot));
+                mbar_expect_tx(smem_u32(b_full + slot), bytes);
+                bulk_load(smem_u32(ringB + (size_t)slot * BS_BYTES), src, bytes, smem_u32(b_full + slot));
                 ++nb;
                 return true;
             };
@@ -200,37 +214,38 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_operator_fused(FusedParams p)
                 wave_units(w, u0, u1);
                 for (long long u = u0; u < u1; ++u) {
                     const int k = (int)(u % KT);
-                    if (!getB(p.Bv + (size_t)k * B_BYTES)) return false;
-                    for (int r = 0; r < G; ++r)
-                        if (!getA(p.A + ((size_t)u * G + r) * FU_TILE, false)) return false;
+                    if (!getB(p.Bv + (size_t)k * B_BYTES, B_BYTES)) return false;
+                    if (!getA(p.A + (size_t)u * G * FU_TILE, FU_EBYTES, false)) return false;
                 }
                 return true;
             };
             auto phase2 = [&](int w) -> bool {
                 if (n_own == 0) return true;
-                int r0, r1;
-                wave_rows(w, r0, r1);
+                const int g0 = w * p.GW, g1 = min(p.groups, g0 + p.GW);
                 bool ready = false;
-                for (int r = r0; r < r1; ++r) {
-                    const int g = r / G, rr = r % G;
+                for (int g = g0; g < g1; ++g) {
+                    const int valid = min(G, p.M_tiles - g * G);
                     for (int i = 0; i < n_own; ++i) {
-                        const int j = c + i * n;   // k tiles 2j, 2j + 1 of the image
+                        const int j = c + i * n;   // units (g, 2j) and (g, 2j + 1): adjacent elements
+                        if ((na & 1) && !skipA()) return false;
                         for (int h = 0; h < 2; ++h)
-                            if (!getA(p.A + (((size_t)g * KT + 2 * j + h) * G + rr) * FU_TILE, true)) return false;
+                            if (!getA(p.A + ((size_t)g * KT + 2 * j + h) * G * FU_TILE, FU_EBYTES, true)) return false;
+                        if (i > 0) continue;
+                        if (!ready) {   // the split of T_w is written by all CTAs
+                            if (!grid_wait(p.sync + 1, (unsigned)((w + 1) * n), abort_flag, p.flags)) return false;
+                            asm volatile("fence.proxy.async.global;" ::: "memory");
+                            ready = true;
+                        }
+                        for (int rr = 0; rr < valid; ++rr)   // k tiles 2r, 2r + 1 of split(T), r = g G + rr
+                            if (!getB(p.Bt + (size_t)(2 * (g * G + rr)) * B_BYTES, 2 * B_BYTES)) return false;
                     }
-                    if (!ready) {   // the split of T_w is written by all CTAs
-                        if (!grid_wait(p.sync + 1, (unsigned)((w + 1) * n), abort_flag, p.flags)) return false;
-                        asm volatile("fence.proxy.async.global;" ::: "memory");
-                        ready = true;
-                    }
-                    for (int h = 0; h < 2; ++h)
-                        if (!getB(p.Bt + (size_t)(2 * r + h) * B_BYTES)) return false;
                 }
                 return true;
             };
-            bool ok = phase1(0);
+            bool ok = true;
+            for (int w = 0; ok && w < FU_DEPTH && w < p.NW; ++w) ok = phase1(w);
             for (int w = 0; ok && w < p.NW; ++w) {
-                if (w + 1 < p.NW) ok = phase1(w + 1);
+                if (w + FU_DEPTH < p.NW) ok = phase1(w + FU_DEPTH);
                 if (ok) ok = phase2(w);
             }
         }
@@ -240,8 +255,8 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_operator_fused(FusedParams p)
             long long ma = 0, mb = 0;
             int nseg = 0;
             auto takeA = [&](int& slot) -> bool {
-                slot = (int)(ma % FU_NA);
-                if (!mbar_wait(smem_u32(a_full + slot), (uint32_t)((ma / FU_NA) & 1), abort_flag)) return false;
+                slot = (int)(ma % FU_NE);
+                if (!mbar_wait(smem_u32(a_full + slot), (uint32_t)((ma / FU_NE) & 1), abort_flag)) return false;
                 ++ma;
                 return true;
             };
@@ -263,21 +278,19 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_operator_fused(FusedParams p)
                     tc_fence_after();
                     const long long seg_start = u;
                     for (; u < seg_end; ++u) {
-                        int sb;
-                        if (!takeB(sb)) return false;
-                        const uint64_t db = desc_sw128(smem_u32(ringB + sb * B_BYTES));
+                        int sb, sa;
+                        if (!takeB(sb) || !takeA(sa)) return false;
+                        tc_fence_after();
+                        const uint64_t db = desc_sw128(smem_u32(ringB + (size_t)sb * BS_BYTES));
                         for (int r = 0; r < G; ++r) {
-                            int sa;
-                            if (!takeA(sa)) return false;
-                            tc_fence_after();
-                            const uint64_t da = desc_sw128(smem_u32(ringA + sa * FU_TILE));
+                            const uint64_t da = desc_sw128(smem_u32(ringA + (size_t)sa * FU_EBYTES + r * FU_TILE));
                             const uint32_t dt = tmem + (uint32_t)(r * FU_ACC_STRIDE);
 #pragma unroll
                             for (int kk = 0; kk < 4; ++kk)
                                 mma_bf16(dt, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), p.idesc_k,
                                          (u > seg_start || kk > 0) ? 1u : 0u);
-                            mma_commit(smem_u32(a_empty + sa));
                         }
+                        mma_commit(smem_u32(a_empty + sa));
                         mma_commit(smem_u32(b_empty + sb));
                     }
                     mma_commit(smem_u32(acc_full));
@@ -287,42 +300,52 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_operator_fused(FusedParams p)
             };
             auto phase2 = [&](int w) -> bool {
                 if (n_own == 0) return true;
-                int r0, r1;
-                wave_rows(w, r0, r1);
-                for (int r = r0; r < r1; ++r) {
-                    int sa0, sa1, sb0, sb1;
-                    // the A pairs of row tile r were issued before its two B tiles
+                const int g0 = w * p.GW, g1 = min(p.groups, g0 + p.GW);
+                for (int g = g0; g < g1; ++g) {
+                    const int valid = min(G, p.M_tiles - g * G);
+                    int sbs[FU_G];
                     for (int i = 0; i < n_own; ++i) {
-                        if (!takeA(sa0) || !takeA(sa1)) return false;
-                        if (i == 0 && (!takeB(sb0) || !takeB(sb1))) return false;
-                        if (sa1 != sa0 + 1) {   // pairs start at even ring positions
+                        int sa, sa1;
+                        if (ma & 1) {   // element passed over by the producer
+                            if (!takeA(sa)) return false;
+                            mbar_arrive(smem_u32(a_empty + sa));
+                        }
+                        if (!takeA(sa) || !takeA(sa1)) return false;
+                        if (sa1 != sa + 1) {   // cannot happen: pairs start at even positions
                             *abort_flag = 1;
                             return false;
                         }
+                        if (i == 0)
+                            for (int rr = 0; rr < valid; ++rr)
+                                if (!takeB(sbs[rr])) return false;
                         tc_fence_after();
-                        // 128 x 128 block of Phi~ (two adjacent 64-column tiles), read
-                        // as A = Phi~^T: M along the tile columns, K along its rows
-                        const uint64_t da = desc_sw128_mn(smem_u32(ringA + sa0 * FU_TILE), FU_TILE, 1024);
-                        const uint64_t db0 = desc_sw128(smem_u32(ringB + sb0 * B_BYTES));
-                        const uint64_t db1 = desc_sw128(smem_u32(ringB + sb1 * B_BYTES));
                         const uint32_t dt = tmem + (uint32_t)((G + i) * FU_ACC_STRIDE);
+                        for (int rr = 0; rr < valid; ++rr) {
+                            // 128 x 128 block of Phi~ (row tile g G + rr, k tiles 2j and 2j + 1 in
+                            // adjacent elements, 32 KiB apart), read as A = Phi~^T: M along the
+                            // columns, K along the rows
+                            const uint64_t da = desc_sw128_mn(
+                                smem_u32(ringA + (size_t)sa * FU_EBYTES + rr * FU_TILE), FU_EBYTES, 1024);
+                            const uint64_t db0 = desc_sw128(smem_u32(ringB + (size_t)sbs[rr] * BS_BYTES));
 #pragma unroll
-                        for (int s = 0; s < 8; ++s) {   // 16 rows per step: 2048 bytes of A
-                            const uint64_t db = (s < 4 ? db0 : db1) + (uint64_t)(2 * (s & 3));
-                            mma_bf16(dt, da + (uint64_t)(128 * s), db, p.idesc_t,
-                                     (w > 0 || r > r0 || s > 0) ? 1u : 0u);
+                            for (int s = 0; s < 8; ++s) {   // 16 rows per step: 2048 bytes of A
+                                const uint64_t db =
+                                    db0 + (uint64_t)(s < 4 ? 0u : (B_BYTES >> 4)) + (uint64_t)(2 * (s & 3));
+                                mma_bf16(dt, da + (uint64_t)(128 * s), db, p.idesc_t,
+                                         (w > 0 || g > g0 || rr > 0 || s > 0) ? 1u : 0u);
+                            }
                         }
-                        mma_commit(smem_u32(a_empty + sa0));
+                        mma_commit(smem_u32(a_empty + sa));
                         mma_commit(smem_u32(a_empty + sa1));
                     }
-                    mma_commit(smem_u32(b_empty + sb0));
-                    mma_commit(smem_u32(b_empty + sb1));
+                    for (int rr = 0; rr < valid; ++rr) mma_commit(smem_u32(b_empty + sbs[rr]));
                 }
                 return true;
             };
-            bool ok = phase1(0);
+            bool ok = true;
+            for (int w = 0; ok && w < FU_DEPTH && w < p.NW; ++w) ok = phase1(w);
             for (int w = 0; ok && w < p.NW; ++w) {
-                if (w + 1 < p.NW) ok = phase1(w + 1);
+                if (w + FU_DEPTH < p.NW) ok = phase1(w + FU_DEPTH);
                 if (ok) ok = phase2(w);
             }
             if (ok) mma_commit(smem_u32(u_full));
@@ -410,10 +433,21 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_operator_fused(FusedParams p)
                 const int s0 = (w & 1) * p.seg_cap + gs[0], ns = gs[1];
                 float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (has_q) {
-                    for (int s = sl_e; s < ns; s += S) {
-                        const float4 b = __ldcg(reinterpret_cast<const float4*>(
-                            p.part + ((size_t)(s0 + s) * p.Q + q_e) * GR + rig));
-                        a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+                    // eight independent loads in flight, added in segment order
+                    const float* base = p.part + ((size_t)s0 * p.Q + q_e) * GR + rig;
+                    const size_t sstride = (size_t)p.Q * GR;
+                    for (int s = sl_e; s < ns; s += 8 * S) {
+                        float4 b[8];
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) {
+                            const int ss = s + t * S;
+                            b[t] = ss < ns ? __ldcg(reinterpret_cast<const float4*>(base + (size_t)ss * sstride))
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) {
+                            a.x += b[t].x; a.y += b[t].y; a.z += b[t].z; a.w += b[t].w;
+                        }
                     }
                     red[e] = a;
                 }
@@ -467,8 +501,8 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_operator_fused(FusedParams p)
     if (threadIdx.x == 0 && *abort_flag) {
         // some role gave up: the latest copy issued into every ring slot must
         // land before the CTA exits
-        for (int s = 0; s < FU_NA; ++s) {
-            const long long n_s = na > s ? (na - s + FU_NA - 1) / FU_NA : 0;
+        for (int s = 0; s < FU_NE; ++s) {
+            const long long n_s = na > s ? (na - s + FU_NE - 1) / FU_NE : 0;
             if (n_s > 0) mbar_drain(smem_u32(a_full + s), (uint32_t)((n_s - 1) & 1));
         }
         for (int s = 0; s < FU_NB; ++s) {
@@ -516,7 +550,7 @@ struct FusedPlan {
 };
 
 size_t fused_smem_bytes(int QS) {
-    return 1024 + (size_t)FU_NA * FU_TILE + (size_t)FU_NB * QS * 128 + 8 * (2 * FU_NA + 2 * FU_NB + 4) + 16 +
+    return 1024 + (size_t)FU_NE * FU_EBYTES + (size_t)FU_NB * 2 * QS * 128 + 8 * (2 * FU_NE + 2 * FU_NB + 4) + 16 +
            128 * 16 + 64;
 }
 
