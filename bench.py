@@ -190,16 +190,16 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _launches_per_fit(cg_iters, rr_period, op_cg, op_rr):
+def _launches_per_fit(cg_iters, rr_period, op_cg, op_rr, step):
     """Kernels of one fit: b = beta Phi^T y, finiteness check of y, fit set-up;
-    per EM iteration init + M-step; per CG step the operator kernels (op_cg),
-    update and direction; per residual replacement the operator kernels
-    (op_rr) and the residual."""
+    per EM iteration init + M-step; per CG step the operator kernels (op_cg)
+    and the update/direction kernels (step); per residual replacement the
+    operator kernels (op_rr) and the residual."""
     n = 3
     for u in cg_iters:
         u = int(u)
         rr = u // rr_period if rr_period > 0 else 0
-        n += 2 + (op_cg + 2) * u + (op_rr + 1) * rr
+        n += 2 + (op_cg + step) * u + (op_rr + 1) * rr
     return n
 
 
@@ -272,7 +272,7 @@ def run_ours(args):
     reps = 20
     op_ms = cf.cofem_time_operator(model.h, Q, reps)
     hbm_gbs, _, peak_kind = _peaks()
-    path, op_cg, op_rr = cf.cofem_operator_info(model.h)
+    path, op_cg, op_rr, op_step = cf.cofem_operator_info(model.h)
     if prob.kind == "dense":
         elem = 2 if prec == cf.COFEM_BF16 else 4
         if path == cf.COFEM_PATH_SINGLE_PASS:
@@ -304,7 +304,7 @@ def run_ours(args):
     e2e = {"value": ws * e2e_steps * T / e2e_s, "unit": "EM-iter/s", "h2d_bytes_per_step": int(N * 4),
            "d2h_bytes_per_step": int(3 * D * 4 + T * 4 + 4)}
 
-    launches = sum(_launches_per_fit(it, run["rr_period"], op_cg, op_rr) for it in all_iters)
+    launches = sum(_launches_per_fit(it, run["rr_period"], op_cg, op_rr, op_step) for it in all_iters)
     model.close()
 
     # the FP32 forms on the same problem (precision comparison at equal NMSE):

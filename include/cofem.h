@@ -274,14 +274,18 @@ cofem_status cofem_apply_dense_noalloc(const float* phi, long long N, long long 
 /* Bytes of device memory the handle holds (Phi copy, theta, fit workspace). */
 long long cofem_device_bytes(struct cofem_ctx* h);
 
-/* How the operator of Alg. 2 is applied for the current Q (valid after a fit
- * or cofem_apply_operator): *path = COFEM_PATH_TWO_PASS or
+/* How the CG loop of Alg. 2 runs for the current Q (valid after a fit or
+ * cofem_apply_operator): *path = COFEM_PATH_TWO_PASS or
  * COFEM_PATH_SINGLE_PASS for a BF16 or 3xTF32 dense dictionary, COFEM_PATH_AUTO
  * (0) for the CUDA-core forms (FP32 FMA, convolution); *kernels_cg = kernels
- * launched per application inside the CG loop; *kernels_rr = per application
- * in a residual replacement.  Any output pointer may be NULL.  Errors:
+ * launched per operator application inside the CG loop; *kernels_rr = per
+ * application in a residual replacement; *kernels_step = kernels of the CG
+ * update, stopping test and direction per CG step (1 when they run as one
+ * cooperative kernel, which needs rr_period = 0 and all (K+1) x ceil(D/4096)
+ * blocks co-resident; else 2).  Any output pointer may be NULL.  Errors:
  * INVALID_ARG (NULL handle, or no fit or application yet). */
-cofem_status cofem_operator_info(struct cofem_ctx* h, int* path, int* kernels_cg, int* kernels_rr);
+cofem_status cofem_operator_info(struct cofem_ctx* h, int* path, int* kernels_cg, int* kernels_rr,
+                                 int* kernels_step);
 
 #ifdef __cplusplus
 }

@@ -96,7 +96,7 @@ def _load():
         "cofem_get_theta": (i, [vp, vp]),
         "cofem_phit_y": (i, [vp, vp, d, vp]),
         "cofem_device_bytes": (ll, [vp]),
-        "cofem_operator_info": (i, [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
+        "cofem_operator_info": (i, [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
         "cofem_time_operator": (i, [vp, i, i, C.POINTER(d)]),
         "cofem_apply_dense_noalloc": (i, [vp, ll, ll, ll, vp, i, vp, d, vp, vp]),
         "cofem_estimate_bytes": (ll, [i, ll, ll, ll, i, i]),
@@ -249,11 +249,12 @@ def cofem_device_bytes(h: int) -> int:
     return int(lib.cofem_device_bytes(h))
 
 
-def cofem_operator_info(h: int) -> tuple[int, int, int]:
-    """(path, kernels per CG-loop application, kernels per residual replacement)."""
-    path, kc, kr = C.c_int(), C.c_int(), C.c_int()
-    _check(lib.cofem_operator_info(h, C.byref(path), C.byref(kc), C.byref(kr)))
-    return path.value, kc.value, kr.value
+def cofem_operator_info(h: int) -> tuple[int, int, int, int]:
+    """(path, kernels per CG-loop operator application, per residual
+    replacement, kernels of the CG update/direction per step)."""
+    path, kc, kr, ks = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    _check(lib.cofem_operator_info(h, C.byref(path), C.byref(kc), C.byref(kr), C.byref(ks)))
+    return path.value, kc.value, kr.value, ks.value
 
 
 class CoFEM:
