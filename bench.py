@@ -279,6 +279,10 @@ def run_ours(args):
             # Phi read once, V read, U written
             alg_bytes = 1.0 * N * D * elem + 2.0 * Q * D * 4
             roof = {"bound": "hbm", "kernel": "single-pass dense operator (k_operator_fused)"}
+        elif path == cf.COFEM_PATH_AUTO:
+            # FP32 FMA on the CUDA cores: Phi read once per product
+            alg_bytes = 2.0 * N * D * elem + 2.0 * Q * D * 4
+            roof = {"bound": "alu", "kernel": "FP32 FMA dense operator (k_gemm1_simt + k_gemm2_simt)"}
         else:
             # Phi read once per product, V read, U written
             alg_bytes = 2.0 * N * D * elem + 2.0 * Q * D * 4

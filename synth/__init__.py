@@ -120,9 +120,10 @@ WORKLOADS = {
     "dense_n256_d1024_k20": dict(
         kind="dense", N=256, D=1024, d=51, snr_db=20.0, K=20, T=50,
         cg_tol=1e-5, cg_maxit=400, precision="f32", rr_period=0),
+    # FP32 dictionary with the skinny products on the tensor cores (3xTF32)
     "dense_n2500_d10000_k32": dict(
         kind="dense", N=2500, D=10000, d=200, snr_db=25.0, K=32, T=50,
-        cg_tol=1e-5, cg_maxit=400, precision="f32", rr_period=0),
+        cg_tol=1e-5, cg_maxit=400, precision="tf32x3", rr_period=0),
     "toeplitz_d1e6_l256_k16": dict(
         kind="toeplitz", N=1_000_000, D=1_000_000, L=256, rate=0.01, snr_db=15.0,
         K=16, T=30, cg_tol=1e-5, cg_maxit=400, precision="f32", rr_period=0),

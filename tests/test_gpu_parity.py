@@ -384,15 +384,24 @@ def _mu_residual(phi, y, beta, alpha, mu):
 
 
 def test_fit_dense_n2500_d10000_k32_properties(cf):
-    """Full 2500 x 10000 FP32 workload (K = 32, T = 50): every E-step converges,
-    mu solves its system, NMSE is that of a converged SBL fit."""
+    """Full 2500 x 10000 FP32 workload (K = 32, T = 50) in its benchmark form
+    (3xTF32 tensor-core products) and with FP32 FMA: every E-step converges, mu
+    solves its system, NMSE is that of a converged SBL fit."""
     from synth import workload
     p, run = workload("dense_n2500_d10000_k32")
+    assert run["precision"] == "tf32x3"
+    g = gpu_fit(cf, p, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], seed=run["seed"],
+                precision=cf.COFEM_F32_TF32X3)
+    assert not g["flags"] & cf.COFEM_FLAG_CG_NOT_CONVERGED
+    assert _mu_residual(p.phi, p.y, p.beta, g["alpha"], g["mu"]) < 10 * run["cg_tol"]
+    nmse_tc = 20 * np.log10(np.linalg.norm(g["mu"] - p.z) / np.linalg.norm(p.z))
+    assert nmse_tc < -20.0
     g = gpu_fit(cf, p, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], seed=run["seed"])
     assert not g["flags"] & cf.COFEM_FLAG_CG_NOT_CONVERGED
     assert _mu_residual(p.phi, p.y, p.beta, g["alpha"], g["mu"]) < 10 * run["cg_tol"]
     nmse_db = 20 * np.log10(np.linalg.norm(g["mu"] - p.z) / np.linalg.norm(p.z))
     assert nmse_db < -20.0
+    assert abs(nmse_db - nmse_tc) < 0.1
 
 
 def test_fit_dense_n8192_d32768_bf16_properties(cf):
