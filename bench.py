@@ -39,6 +39,16 @@ def _dist():
     return ws, rank, local
 
 
+# DRAM bytes (read + write) per operator application from one ncu capture of
+# the current kernels, keyed by (workload, operator form); the source summary
+# is named beside each entry.  An entry must be removed when its kernels change.
+_MEASURED_TRAFFIC = {
+    # profiles/k_gemm_tc_bf16_two_pass_dense_n8192_d32768_q33.md and
+    # profiles/cg_vector_kernels_dense_n8192_d32768_q33.md: two k_gemm_tc
+    # launches (548.0 + 544.1 MB) and k_tc_reduce_T (10.8 MB, cold cache)
+    ("dense_n8192_d32768_k32_bf16", 1): 1102.9e6,
+}
+
 # --dense-path -> cofem_opts.dense_path
 _DENSE_PATHS = {"auto": 0, "two_pass": 1, "single_pass": 2}
 
@@ -291,8 +301,9 @@ def run_ours(args):
         alg_bytes = 2.0 * Q * D * 4                          # read V, write U
         roof = {"bound": "hbm", "kernel": "convolution operator"}
     achieved = alg_bytes / (op_ms / 1000.0) / 1e9
+    traffic = _MEASURED_TRAFFIC.get((name, path)) if prob.kind == "dense" else None
     roof.update({"achieved": achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved / hbm_gbs,
-                 "traffic": None, "peak_source": peak_kind, "ms_per_launch": op_ms,
+                 "traffic": traffic, "peak_source": peak_kind, "ms_per_launch": op_ms,
                  "algorithmic_bytes_per_launch": alg_bytes})
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
