@@ -54,7 +54,7 @@ _DENSE_PATHS = {"auto": 0, "two_pass": 1, "single_pass": 2}
 
 # workload precision name -> C-ABI precision code
 _PRECISIONS = {"f32": lambda cf: cf.COFEM_F32, "bf16": lambda cf: cf.COFEM_BF16,
-               "tf32x3": lambda cf: cf.COFEM_F32_TF32X3}
+               "tf32x3": lambda cf: cf.COFEM_F32_TF32X3, "fp8": lambda cf: cf.COFEM_FP8_E4M3}
 
 
 def _metric_name(name, spec):
@@ -284,7 +284,7 @@ def run_ours(args):
     hbm_gbs, _, peak_kind = _peaks()
     path, op_cg, op_rr, op_step = cf.cofem_operator_info(model.h)
     if prob.kind == "dense":
-        elem = 2 if prec == cf.COFEM_BF16 else 4
+        elem = {cf.COFEM_BF16: 2, cf.COFEM_FP8_E4M3: 1}.get(prec, 4)
         if path == cf.COFEM_PATH_SINGLE_PASS:
             # Phi read once, V read, U written
             alg_bytes = 1.0 * N * D * elem + 2.0 * Q * D * 4
@@ -296,7 +296,8 @@ def run_ours(args):
         else:
             # Phi read once per product, V read, U written
             alg_bytes = 2.0 * N * D * elem + 2.0 * Q * D * 4
-            roof = {"bound": "hbm", "kernel": "two-pass dense operator (k_gemm_tc x2 + k_tc_reduce_T)"}
+            gk = "k_gemm8" if prec == cf.COFEM_FP8_E4M3 else "k_gemm_tc"
+            roof = {"bound": "hbm", "kernel": f"two-pass dense operator ({gk} x2 + k_tc_reduce_T)"}
     else:
         alg_bytes = 2.0 * Q * D * 4                          # read V, write U
         roof = {"bound": "hbm", "kernel": "convolution operator"}
@@ -335,6 +336,12 @@ def run_ours(args):
             m32.close()
             fp32[key] = {"value": T / (ms32 / 1000.0), "unit": "EM-iter/s", "nmse_db": nm32,
                          "operator_ms": op32, "flags": f32flags}
+        # the FP8 E4M3 storage variant (per-row scales) on the same problem
+        m8 = make(cf.COFEM_FP8_E4M3)
+        ms8, f8flags, _ = timed_fits(m8, 1, 1)
+        fp8 = {"value": T / (ms8 / 1000.0), "unit": "EM-iter/s", "nmse_db": _nmse_db(outs[0].cpu().numpy(), prob.z),
+               "operator_ms": cf.cofem_time_operator(m8.h, Q, 10), "flags": f8flags}
+        m8.close()
 
     line = {
         "metric": _metric_name(name, spec), "value": value, "unit": "EM-iter/s", "n_gpus": ws,
@@ -351,6 +358,7 @@ def run_ours(args):
     }
     if fp32 is not None:
         line["fp32_form"] = fp32
+        line["fp8_form"] = fp8
     if args.serve_requests > 0 and ws == 1:
         line["serving"] = serving_report(cf, dev, args.serve_requests, run["precision"])
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
@@ -482,7 +490,7 @@ def main():
                     help="requests of the serving measurement added to the line (0 = skip)")
     ap.add_argument("--serve", action="store_true",
                     help="only the serving measurement (2000 requests unless --serve-requests is given)")
-    ap.add_argument("--serve-precision", default="bf16", choices=["f32", "bf16", "tf32x3"])
+    ap.add_argument("--serve-precision", default="bf16", choices=["f32", "bf16", "tf32x3", "fp8"])
     ap.add_argument("--dense-path", default="auto", choices=sorted(_DENSE_PATHS),
                     help="BF16 dense operator form (default: the library's choice)")
     ap.add_argument("--em-iters", type=int, default=0,

@@ -59,6 +59,12 @@ typedef int cofem_status;
 #define COFEM_BF16  1  /* Phi quantised once to bfloat16 (round to nearest even); the
                           method then runs exactly on that quantised dictionary (the
                           vector block enters the tensor cores as three bf16 terms) */
+#define COFEM_FP8_E4M3 3 /* Phi stored as FP8 E4M3 codes with per-row FP32 scales:
+                          s_i = max_j |Phi_ij| / 448, code = E4M3(Phi_ij / s_i) (round to
+                          nearest even, saturating); the method runs on
+                          Phi~_ij = s_i code_ij.  The codes are widened to BF16 in shared
+                          memory (exactly) for the tensor cores; the vector block is split
+                          into three bf16 terms as in COFEM_BF16.  Needs 3(K+1) <= 128. */
 #define COFEM_F32_TF32X3 2 /* Phi kept in FP32; products on the tensor cores with the
                           error-compensated TF32 split: x = x_hi + x_lo for the
                           dictionary and the vector block, x_hi and x_lo rounded to
@@ -80,7 +86,8 @@ typedef int cofem_status;
 #define COFEM_FLAG_DEVICE_TIMEOUT   8u /* a bounded on-device wait gave up (the call returns COFEM_ERR_CUDA) */
 
 typedef struct cofem_opts {
-    int precision;            /* COFEM_F32 | COFEM_BF16 | COFEM_F32_TF32X3 (the last two dense only) */
+    int precision;            /* COFEM_F32 | COFEM_BF16 | COFEM_F32_TF32X3 | COFEM_FP8_E4M3 (the
+                                 last three dense only) */
     int precond;              /* COFEM_PRECOND_JACOBI | COFEM_PRECOND_ONE */
     int conv;                 /* COFEM_CONV_PER_COLUMN | COFEM_CONV_FROBENIUS */
     int rr_period;            /* residual replacement R <- B - A X every rr_period CG
@@ -273,6 +280,13 @@ cofem_status cofem_apply_dense_noalloc(const float* phi, long long N, long long 
 
 /* Bytes of device memory the handle holds (Phi copy, theta, fit workspace). */
 long long cofem_device_bytes(struct cofem_ctx* h);
+
+/* The dense dictionary the handle computes with, as FP32 (N x D row-major, host
+ * or device pointer): the FP32 copy, bf16(Phi) for COFEM_BF16, or s_i code_ij
+ * (each product rounded to FP32) for COFEM_FP8_E4M3.  Paper counterpart: the
+ * Phi of Sec. III in the stored precision.  Errors: INVALID_ARG (NULL, or a
+ * convolution handle), NOMEM, CUDA. */
+cofem_status cofem_get_dictionary(struct cofem_ctx* h, float* out);
 
 /* How the CG loop of Alg. 2 runs for the current Q (valid after a fit or
  * cofem_apply_operator): *path = COFEM_PATH_TWO_PASS or

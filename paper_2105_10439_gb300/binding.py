@@ -30,6 +30,7 @@ COFEM_OP_TOEPLITZ = 1
 COFEM_F32 = 0
 COFEM_BF16 = 1
 COFEM_F32_TF32X3 = 2
+COFEM_FP8_E4M3 = 3
 COFEM_PRECOND_JACOBI = 0
 COFEM_PRECOND_ONE = 1
 COFEM_CONV_PER_COLUMN = 0
@@ -96,6 +97,7 @@ def _load():
         "cofem_get_theta": (i, [vp, vp]),
         "cofem_phit_y": (i, [vp, vp, d, vp]),
         "cofem_device_bytes": (ll, [vp]),
+        "cofem_get_dictionary": (i, [vp, vp]),
         "cofem_operator_info": (i, [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
         "cofem_time_operator": (i, [vp, i, i, C.POINTER(d)]),
         "cofem_apply_dense_noalloc": (i, [vp, ll, ll, ll, vp, i, vp, d, vp, vp]),
@@ -247,6 +249,11 @@ def cofem_server_destroy(srv: int) -> None:
 
 def cofem_device_bytes(h: int) -> int:
     return int(lib.cofem_device_bytes(h))
+
+
+def cofem_get_dictionary(h: int, out) -> None:
+    """The dictionary the handle computes with, FP32 N x D (host or device array)."""
+    _check(lib.cofem_get_dictionary(h, _ptr(out)))
 
 
 def cofem_operator_info(h: int) -> tuple[int, int, int, int]:

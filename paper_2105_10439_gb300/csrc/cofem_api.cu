@@ -347,8 +347,10 @@ cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, c
         if (L != 0) return fail(COFEM_ERR_INVALID_ARG, "L must be 0 for a dense dictionary");
         if (o.dense_path < COFEM_PATH_AUTO || o.dense_path > COFEM_PATH_SINGLE_PASS)
             return fail(COFEM_ERR_INVALID_ARG, "dense_path must be AUTO, TWO_PASS or SINGLE_PASS");
-        if (o.precision != COFEM_F32 && o.precision != COFEM_BF16 && o.precision != COFEM_F32_TF32X3)
-            return fail(COFEM_ERR_INVALID_ARG, "precision must be COFEM_F32, COFEM_BF16 or COFEM_F32_TF32X3");
+        if (o.precision != COFEM_F32 && o.precision != COFEM_BF16 && o.precision != COFEM_F32_TF32X3 &&
+            o.precision != COFEM_FP8_E4M3)
+            return fail(COFEM_ERR_INVALID_ARG,
+                        "precision must be COFEM_F32, COFEM_BF16, COFEM_F32_TF32X3 or COFEM_FP8_E4M3");
     } else if (kind == COFEM_OP_TOEPLITZ) {
         if (N != D) return fail(COFEM_ERR_INVALID_ARG, "a convolutional dictionary needs N == D");
         if (L < 1 || L > 1024 || L > N) return fail(COFEM_ERR_INVALID_ARG, "need 1 <= L <= min(1024, N)");
@@ -432,6 +434,14 @@ cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, c
             launch_quantize_bf16(c->stream, tmp, c->Np, c->Dp, c->Dp, c->phi16, c->Np, c->Dp);
             CKB(cudaStreamSynchronize(c->stream));
             dfree(c, &tmp, (size_t)c->Np * c->Dp);
+        } else if (o.precision == COFEM_FP8_E4M3) {
+            if ((st = dalloc(c, &c->phi8, (size_t)c->Np * c->Dp)) || (st = dalloc(c, &c->scale8, (size_t)c->Np))) {
+                dfree(c, &tmp, (size_t)c->Np * c->Dp);
+                return bail(st);
+            }
+            launch_quantize_fp8(c->stream, tmp, c->Dp, c->N, c->D, c->Np, c->Dp, c->phi8, c->scale8);
+            CKB(cudaStreamSynchronize(c->stream));
+            dfree(c, &tmp, (size_t)c->Np * c->Dp);
         } else {
             c->phi32 = tmp;
         }
@@ -463,6 +473,8 @@ cofem_status cofem_destroy(cofem_ctx* c) {
     free_graph(c);
     dfree(c, &c->phi32, (size_t)c->Np * c->Dp);
     dfree(c, &c->phi16, (size_t)c->Np * c->Dp);
+    dfree(c, &c->phi8, (size_t)c->Np * c->Dp);
+    dfree(c, &c->scale8, (size_t)c->Np);
     dfree(c, &c->h, (size_t)c->L);
     dfree(c, &c->theta, (size_t)c->Dp);
     dfree(c, &c->alpha, (size_t)c->Dp);
@@ -650,6 +662,31 @@ cofem_status cofem_time_operator(cofem_ctx* c, int Q, int reps, double* ms_per_a
 }
 
 long long cofem_device_bytes(cofem_ctx* c) { return c ? c->bytes : 0; }
+
+cofem_status cofem_get_dictionary(cofem_ctx* c, float* out) {
+    g_err[0] = 0;
+    if (!c || !out) return fail(COFEM_ERR_INVALID_ARG, "NULL argument");
+    if (c->kind != COFEM_OP_DENSE) return fail(COFEM_ERR_INVALID_ARG, "the handle holds a convolution filter");
+    CK(cudaSetDevice(c->device));
+    if (c->phi32) {
+        CK(cudaMemcpy2DAsync(out, c->D * sizeof(float), c->phi32, c->Dp * sizeof(float), c->D * sizeof(float), c->N,
+                             cudaMemcpyDefault, c->stream));
+    } else {
+        float* tmp = nullptr;
+        cofem_status st = dalloc(c, &tmp, (size_t)c->N * c->D);
+        if (st) return st;
+        if (c->phi8) launch_dequant_fp8(c->stream, c->phi8, c->scale8, c->N, c->D, c->Dp, tmp);
+        else launch_bf16_to_f32(c->stream, c->phi16, c->N, c->D, c->Dp, tmp);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out, tmp, (size_t)c->N * c->D * sizeof(float), cudaMemcpyDefault, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        dfree(c, &tmp, (size_t)c->N * c->D);
+        if (e != cudaSuccess) return cuda_fail(e, "reading the dictionary");
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return COFEM_OK;
+}
 
 cofem_status cofem_operator_info(cofem_ctx* c, int* path, int* kernels_cg, int* kernels_rr, int* kernels_step) {
     g_err[0] = 0;

@@ -216,9 +216,11 @@ __device__ __forceinline__ void store_split_tf32(float* Vs, int QS, int QH, int 
 struct SplitOut {
     void* Vs;
     int fmt, QS, QH;
+    float scale = 1.0f;   // power of two applied before the split (FP8 operator: 2^64)
 };
 
 __device__ __forceinline__ void store_split(const SplitOut& so, int q, long long j, float4 v) {
+    if (so.scale != 1.0f) v = make_float4(v.x * so.scale, v.y * so.scale, v.z * so.scale, v.w * so.scale);
     if (so.fmt == 1) store_split4((__nv_bfloat16*)so.Vs, so.QS, q, j, v);
     else if (so.fmt == 2) store_split_tf32((float*)so.Vs, so.QS, so.QH, q, j, v);
 }
@@ -232,6 +234,7 @@ struct OpOut {
     size_t sstride;
     const int* grp_seg;   // null for dense slices
     int GR;
+    float uscale = 1.0f;  // power of two the partials carry (FP8 operator: 2^56)
 };
 
 // Psi for elements j..j+3 of column q: beta * (Phi^T Phi v) + alpha_j v_j.
@@ -251,8 +254,9 @@ __device__ __forceinline__ float4 psi4(const OpOut& o, int Q, int q, long long D
             u.x += w.x; u.y += w.y; u.z += w.z; u.w += w.w;
         }
     }
-    return make_float4(beta * u.x + av.x * vv.x, beta * u.y + av.y * vv.y, beta * u.z + av.z * vv.z,
-                       beta * u.w + av.w * vv.w);
+    const float bu = beta * o.uscale;
+    return make_float4(bu * u.x + av.x * vv.x, bu * u.y + av.y * vv.y, bu * u.z + av.z * vv.z,
+                       bu * u.w + av.w * vv.w);
 }
 
 // ---------------------------------------------------------------------------
@@ -402,6 +406,8 @@ struct cofem_ctx {
     double* tt_part = nullptr;       // operator partials of ||Phi p||^2
     unsigned* counters = nullptr;    // last-block counters
     unsigned* check_flag = nullptr;  // one word for input finiteness checks
+    uint8_t* phi8 = nullptr;         // FP8 E4M3 codes (Np x Dp), FP8 form
+    float* scale8 = nullptr;         // per-row scales (Np), FP8 form
     int step_capacity = -1;          // co-resident blocks of k_cg_step (-1: not queried yet)
     int* iters_dev = nullptr;        // T_em
     int iters_cap = 0;
@@ -512,6 +518,16 @@ __device__ __forceinline__ void op_finalize_block(DevCtl* ctl, const double* tt_
 }
 
 void tc_operator_info(cofem_ctx* c, int* path, int* k_cg, int* k_rr);
+
+// FP8 E4M3 dictionary storage (kernels_fp8.cu).
+void launch_quantize_fp8(cudaStream_t st, const float* src, long long ld, long long N, long long D, long long Np,
+                         long long Dp, uint8_t* codes, float* scales);
+void launch_colreduce_fp8(cudaStream_t st, const uint8_t* codes, const float* scales, long long Dp, long long N,
+                          long long D, const float* y, double scale, float* out);
+void launch_dequant_fp8(cudaStream_t st, const uint8_t* codes, const float* scales, long long N, long long D,
+                        long long Dp, float* out);
+void launch_bf16_to_f32(cudaStream_t st, const __nv_bfloat16* src, long long N, long long D, long long ld,
+                        float* out);
 
 // Single-pass BF16 dense operator (kernels_fused.cu).
 struct FusedPlan;

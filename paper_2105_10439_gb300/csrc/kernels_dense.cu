@@ -235,7 +235,9 @@ void launch_dense_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mod
 
 void launch_dense_colreduce(cudaStream_t st, cofem_ctx* c, const float* y, double scale, float* out) {
     const dim3 grid((unsigned)(c->Dp / 128));
-    if (c->phi16)
+    if (c->phi8)
+        launch_colreduce_fp8(st, c->phi8, c->scale8, c->Dp, c->N, c->D, y, scale, out);
+    else if (c->phi16)
         k_colreduce<__nv_bfloat16><<<grid, 128, 0, st>>>(c->phi16, c->Dp, c->N, c->D, y, scale, out);
     else
         k_colreduce<float><<<grid, 128, 0, st>>>(c->phi32, c->Dp, c->N, c->D, y, scale, out);

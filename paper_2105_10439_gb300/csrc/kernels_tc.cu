@@ -334,6 +334,311 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
     if (threadIdx.x == 0 && *abort_flag) atomicOr(p.flags, COFEM_FLAG_DEVICE_TIMEOUT);
 }
 
+// ---------------------------------------------------------------------------
+// FP8 E4M3 dictionary.  The A image holds codes, 128 rows x 128 codes per
+// 16 KiB tile, tiles ordered (group of 2 row tiles, 128-wide k tile, row
+// tile); a unit's two tiles arrive as one 32 KiB bulk copy.  Four converter
+// warps widen each tile to two BF16 sub-tiles (128 x 64, 128-byte swizzle) in
+// shared memory: the BF16 bit pattern (b & 0x80) << 8 | (b & 0x7F) << 4 is the
+// code's value times 2^-120 exactly (zero and subnormals included), so the
+// MMA sees the codes up to one power of two.  The split vector blocks carry
+// 2^64 (SplitOut::scale) so that every product stays in the FP32 normal range;
+// the T reduction applies s_i 2^56 and the U partials carry 2^-56.
+// Warp roles (448 threads): 0 producer, 1 TMEM + MMA, 2-5 epilogue,
+// 6-13 converters.  Accumulators are double-buffered (2 x 2 x 128 columns).
+// ---------------------------------------------------------------------------
+constexpr int F8_THREADS = 448, F8_G = 2, F8_NL = 3, F8_NC = 4, F8_NB = 2, F8_CW = 8;   // F8_CW converter warps
+constexpr uint32_t F8_LAND = F8_G * TC_A_BYTES;     // one unit of codes
+constexpr float F8_BSCALE = 18446744073709551616.0f;   // 2^64 on the split vector blocks
+constexpr float F8_RFAC = 72057594037927936.0f;        // 2^56 = 2^120 / 2^64 back on the products
+
+__device__ __forceinline__ uint32_t f8_pair(uint32_t x) {   // codes in bytes 0 and 2
+    return ((x << 4) & 0x07F007F0u) | ((x & 0x00800080u) << 8);
+}
+
+__global__ void __launch_bounds__(F8_THREADS, 1) k_gemm8(TcParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t B_BYTES = (uint32_t)p.QS * 128u;   // one 64-wide k tile of the split block
+    uint8_t* land = smem;
+    uint8_t* conv = land + F8_NL * F8_LAND;
+    uint8_t* ringB = conv + F8_NC * TC_A_BYTES;
+    uint64_t* bars = (uint64_t*)(ringB + F8_NB * 2 * B_BYTES);
+    uint64_t* land_full = bars;
+    uint64_t* land_empty = land_full + F8_NL;
+    uint64_t* conv_full = land_empty + F8_NL;
+    uint64_t* conv_empty = conv_full + F8_NC;
+    uint64_t* b_full = conv_empty + F8_NC;
+    uint64_t* b_empty = b_full + F8_NB;
+    uint64_t* acc_full = b_empty + F8_NB;   // [2]
+    uint64_t* acc_empty = acc_full + 2;     // [2]
+    uint64_t* drain = acc_empty + 2;
+    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < F8_NL; ++i) {
+            mbar_init(smem_u32(land_full + i), 1);
+            mbar_init(smem_u32(land_empty + i), F8_CW);
+        }
+        for (int i = 0; i < F8_NC; ++i) {
+            mbar_init(smem_u32(conv_full + i), F8_CW);
+            mbar_init(smem_u32(conv_empty + i), 1);
+        }
+        for (int i = 0; i < F8_NB; ++i) {
+            mbar_init(smem_u32(b_full + i), 1);
+            mbar_init(smem_u32(b_empty + i), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(acc_full + i), 1);
+            mbar_init(smem_u32(acc_empty + i), 4);
+        }
+        mbar_init(smem_u32(drain), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const long long u0 = (long long)blockIdx.x * p.W / gridDim.x;
+    const long long u1 = (long long)(blockIdx.x + 1) * p.W / gridDim.x;
+    long long nl = 0, nb = 0;   // copies issued into the landing and B rings (producer thread)
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- bulk-copy producer ----------------
+            uint64_t evict_first;
+            asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(evict_first));
+            for (long long u = u0; u < u1; ++u) {
+                const int k = (int)(u % p.K_tiles);
+                int slot = (int)(nb % F8_NB);
+                long long use = nb / F8_NB;
+                if (use > 0 && !mbar_wait(smem_u32(b_empty + slot), (uint32_t)((use - 1) & 1), abort_flag)) break;
+                mbar_expect_tx(smem_u32(b_full + slot), 2 * B_BYTES);
+                bulk_load(smem_u32(ringB + slot * 2 * B_BYTES), (const char*)p.B + (size_t)(2 * k) * B_BYTES,
+                          2 * B_BYTES, smem_u32(b_full + slot));
+                ++nb;
+                slot = (int)(nl % F8_NL);
+                use = nl / F8_NL;
+                if (use > 0 && !mbar_wait(smem_u32(land_empty + slot), (uint32_t)((use - 1) & 1), abort_flag))
+                    break;
+                mbar_expect_tx(smem_u32(land_full + slot), F8_LAND);
+                bulk_load_hint(smem_u32(land + slot * F8_LAND), (const char*)p.A + (size_t)u * F8_LAND, F8_LAND,
+                               smem_u32(land_full + slot), evict_first);
+                ++nl;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            long long mc = 0, mb = 0;
+            int nseg = 0;
+            long long u = u0;
+            bool ok = true;
+            while (u < u1 && ok) {
+                const int g = (int)(u / p.K_tiles);
+                const long long seg_end = min(u1, (long long)(g + 1) * p.K_tiles);
+                const int buf = nseg & 1;
+                if (nseg >= 2 &&
+                    !mbar_wait(smem_u32(acc_empty + buf), (uint32_t)(((nseg - 2) >> 1) & 1), abort_flag))
+                    break;
+                tc_fence_after();
+                const long long seg_start = u;
+                for (; u < seg_end; ++u) {
+                    const int sb = (int)(mb % F8_NB);
+                    if (!mbar_wait(smem_u32(b_full + sb), (uint32_t)((mb / F8_NB) & 1), abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    for (int sub = 0; sub < 2 * F8_G; ++sub) {   // (row tile r, k half h)
+                        const int r = sub >> 1, h = sub & 1;
+                        const int cs = (int)(mc % F8_NC);
+                        if (!mbar_wait(smem_u32(conv_full + cs), (uint32_t)((mc / F8_NC) & 1), abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t da = desc_sw128(smem_u32(conv + cs * TC_A_BYTES));
+                        const uint64_t db = desc_sw128(smem_u32(ringB + sb * 2 * B_BYTES + h * B_BYTES));
+                        const uint32_t dt = tmem + (uint32_t)(buf * 2 * p.acc_stride + r * p.acc_stride);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma_bf16(dt, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), p.idesc,
+                                     (u > seg_start || h > 0 || kk > 0) ? 1u : 0u);
+                        mma_commit(smem_u32(conv_empty + cs));
+                        ++mc;
+                    }
+                    if (!ok) break;
+                    mma_commit(smem_u32(b_empty + sb));
+                    ++mb;
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(acc_full + buf));
+                ++nseg;
+            }
+            // every issued MMA must finish before TMEM is released
+            mma_commit(smem_u32(drain));
+            mbar_drain(smem_u32(drain), 0);
+        }
+    } else if (warp < 6) {
+        // ---------------- epilogue warps: TMEM -> segment partials ----------------
+        const int sub = warp & 3;
+        const int GR = F8_G * TC_BM;
+        const int NC = p.QS / 16;
+        int nseg = 0;
+        long long u = u0;
+        while (u < u1) {
+            const int g = (int)(u / p.K_tiles);
+            const long long seg_end = min(u1, (long long)(g + 1) * p.K_tiles);
+            const int valid = min(F8_G, p.M_tiles - g * F8_G);
+            const int buf = nseg & 1;
+            if (!mbar_wait(smem_u32(acc_full + buf), (uint32_t)((nseg >> 1) & 1), abort_flag)) break;
+            tc_fence_after();
+            float* out = p.part + (size_t)(p.seg_base[blockIdx.x] + nseg) * p.Q * GR;
+            const int row = 32 * sub + lane;
+            for (int r = 0; r < valid; ++r) {
+                const uint32_t tbase =
+                    tmem + ((uint32_t)(32 * sub) << 16) + (uint32_t)(buf * 2 * p.acc_stride + r * p.acc_stride);
+                for (int qb = 0; qb * 16 < p.Q; ++qb) {
+                    uint32_t v[48];
+                    const int c0 = 3 * qb;
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc)
+                        if (c0 + cc < NC) tmem_ld16(tbase + (uint32_t)((c0 + cc) * 16), v + 16 * cc);
+                    tmem_ld_wait(v, 48);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int q = 16 * qb + i;
+                        if (q < p.Q)
+                            out[(size_t)q * GR + r * TC_BM + row] =
+                                __uint_as_float(v[3 * i]) + __uint_as_float(v[3 * i + 1]) +
+                                __uint_as_float(v[3 * i + 2]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(acc_empty + buf));
+            ++nseg;
+            u = seg_end;
+        }
+    } else {
+        // ---------------- converter warps: codes -> BF16 sub-tiles ----------------
+        // One code tile (128 x 128) at a time into two consecutive sub-tile slots
+        // (h = 0: codes 0..63, h = 1: codes 64..127).  Eight threads read one
+        // 128-byte code row (no bank conflict); threads 4..7 of the eight write
+        // their odd 16-byte chunk first, so each store touches all 32 banks once.
+        const int ct = threadIdx.x - 192;   // 0 .. 255
+        const int j8 = ct & 7, h = j8 >> 2, cpart = j8 & 3;
+        long long cl = 0, cc = 0;           // landing units and sub-tiles converted
+        bool ok = true;
+        for (long long u = u0; u < u1 && ok; ++u) {
+            const int ls = (int)(cl % F8_NL);
+            if (!mbar_wait(smem_u32(land_full + ls), (uint32_t)((cl / F8_NL) & 1), abort_flag)) break;
+            for (int r = 0; r < F8_G; ++r) {
+                const int cs0 = (int)(cc % F8_NC), cs1 = (int)((cc + 1) % F8_NC);
+                const long long use0 = cc / F8_NC, use1 = (cc + 1) / F8_NC;
+                if ((use0 > 0 && !mbar_wait(smem_u32(conv_empty + cs0), (uint32_t)((use0 - 1) & 1), abort_flag)) ||
+                    (use1 > 0 && !mbar_wait(smem_u32(conv_empty + cs1), (uint32_t)((use1 - 1) & 1), abort_flag))) {
+                    ok = false;
+                    break;
+                }
+                const uint8_t* src = land + ls * F8_LAND + r * TC_A_BYTES;
+                uint8_t* dst = conv + (h ? cs1 : cs0) * TC_A_BYTES;
+#pragma unroll
+                for (int it = 0; it < 4; ++it) {
+                    const int rr = (ct >> 3) + 32 * it;
+                    const uint4 w = *reinterpret_cast<const uint4*>(src + rr * 128 + j8 * 16);
+                    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+                    uint32_t o[8];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        o[2 * k] = f8_pair(__byte_perm(ws[k], 0u, 0x4140));
+                        o[2 * k + 1] = f8_pair(__byte_perm(ws[k], 0u, 0x4342));
+                    }
+                    const int c8 = 2 * cpart;   // bf16 16-byte chunks c8, c8 + 1 of row rr
+                    const uint4 lo = make_uint4(o[0], o[1], o[2], o[3]), hi = make_uint4(o[4], o[5], o[6], o[7]);
+                    uint4* p0 = reinterpret_cast<uint4*>(dst + rr * 128 + ((c8 ^ (rr & 7)) << 4));
+                    uint4* p1 = reinterpret_cast<uint4*>(dst + rr * 128 + (((c8 + 1) ^ (rr & 7)) << 4));
+                    if (h) {
+                        *p1 = hi;
+                        *p0 = lo;
+                    } else {
+                        *p0 = lo;
+                        *p1 = hi;
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(smem_u32(conv_full + cs0));
+                    mbar_arrive(smem_u32(conv_full + cs1));
+                }
+                cc += 2;
+            }
+            if (!ok) break;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(land_empty + ls));
+            ++cl;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag) {
+        for (int s = 0; s < F8_NL; ++s) {
+            const long long n_s = nl > s ? (nl - s + F8_NL - 1) / F8_NL : 0;
+            if (n_s > 0) mbar_drain(smem_u32(land_full + s), (uint32_t)((n_s - 1) & 1));
+        }
+        for (int s = 0; s < F8_NB; ++s) {
+            const long long n_s = nb > s ? (nb - s + F8_NB - 1) / F8_NB : 0;
+            if (n_s > 0) mbar_drain(smem_u32(b_full + s), (uint32_t)((n_s - 1) & 1));
+        }
+    }
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+    if (threadIdx.x == 0 && *abort_flag) atomicOr(p.flags, COFEM_FLAG_DEVICE_TIMEOUT);
+}
+
+// FP8 code images: tile (g, k, r) = rows (g G + r) 128 .. +127, codes
+// k 128 .. +127 of the row-major code matrix (ld bytes per row), plain rows.
+__global__ __launch_bounds__(128) void k_tile8_rows(const uint8_t* __restrict__ src, long long ld, int M_tiles,
+                                                    int K_tiles, int G, uint8_t* __restrict__ dst) {
+    const int k = blockIdx.x, gr = blockIdx.y, g = gr / G, r = gr % G;
+    const int m = g * G + r, rr = threadIdx.x;
+    uint8_t* tile = dst + (((size_t)g * K_tiles + k) * G + r) * TC_A_BYTES;
+    const uint4* s4 = reinterpret_cast<const uint4*>(src + ((size_t)m * TC_BM + rr) * ld + (size_t)k * 128);
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        reinterpret_cast<uint4*>(tile + rr * 128)[c] = m < M_tiles ? s4[c] : make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Transposed code image: tile (g, k, r) holds element (rr, cc) =
+// src[k 128 + cc][(g G + r) 128 + rr].
+__global__ __launch_bounds__(128) void k_tile8_cols(const uint8_t* __restrict__ src, long long ld, int M_tiles,
+                                                    int K_tiles, int G, uint8_t* __restrict__ dst) {
+    __shared__ uint8_t sm[128][129];
+    const int k = blockIdx.x, gr = blockIdx.y, g = gr / G, r = gr % G;
+    const int m = g * G + r, t = threadIdx.x;
+    for (int n = 0; n < 128; ++n)
+        sm[n][t] = m < M_tiles ? src[((size_t)k * 128 + n) * ld + (size_t)m * TC_BM + t] : (uint8_t)0;
+    __syncthreads();
+    uint8_t* tile = dst + (((size_t)g * K_tiles + k) * G + r) * TC_A_BYTES;
+    for (int c = 0; c < 128; ++c) tile[t * 128 + c] = sm[c][t];
+}
+
 // Vs = tiled swizzled image of the split of V (Q x Dp, FP32): bf16 3-term
 // (fmt 1, row 3q + t) or TF32 hi / lo (fmt 2, rows q and QH + q).
 __global__ void k_split(const float* __restrict__ V, long long Dp, SplitOut so) {
@@ -347,7 +652,8 @@ __global__ void k_split(const float* __restrict__ V, long long Dp, SplitOut so) 
 // split into the B image of GEMM2, and ||T_q||^2 partials -> pi, gamma.
 __global__ __launch_bounds__(256) void k_tc_reduce_T(const float* __restrict__ part, const int* __restrict__ grp_seg,
                                                      int GR, int Q, long long Np, SplitOut so, double* tt_part,
-                                                     int nblk, unsigned* counter, DevCtl* ctl, int mode) {
+                                                     int nblk, unsigned* counter, DevCtl* ctl, int mode,
+                                                     const float* __restrict__ rscale, float rfac) {
     __shared__ double sh[8];
     const int q = blockIdx.y;
     const long long i = (long long)blockIdx.x * 1024 + threadIdx.x * 4;
@@ -361,7 +667,13 @@ __global__ __launch_bounds__(256) void k_tc_reduce_T(const float* __restrict__ p
             const float4 b = __ldcg(reinterpret_cast<const float4*>(part + ((size_t)(s0 + s) * Q + q) * GR + r));
             a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
         }
-        store_split(so, q, i, a);
+        if (rscale) {   // FP8 dictionary: T_i = s_i 2^56 (Q V)_i; the second product takes s_i T_i
+            const float4 sv = *reinterpret_cast<const float4*>(rscale + i);
+            a = make_float4(a.x * (sv.x * rfac), a.y * (sv.y * rfac), a.z * (sv.z * rfac), a.w * (sv.w * rfac));
+            store_split(so, q, i, make_float4(a.x * sv.x, a.y * sv.y, a.z * sv.z, a.w * sv.w));
+        } else {
+            store_split(so, q, i, a);
+        }
         tt = a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
     }
     const double ttd = block_sum_f(tt, sh);
@@ -373,7 +685,8 @@ __global__ __launch_bounds__(256) void k_tc_reduce_T(const float* __restrict__ p
 // GEMM2 epilogue for a stand-alone application: U (Q x Dp) = sum of the
 // segment partials of its group.
 __global__ __launch_bounds__(256) void k_tc_reduce_U(const float* __restrict__ part, const int* __restrict__ grp_seg,
-                                                     int GR, int Q, long long Dp, float* __restrict__ U) {
+                                                     int GR, int Q, long long Dp, float* __restrict__ U,
+                                                     float uscale) {
     const int q = blockIdx.y;
     const long long j = (long long)blockIdx.x * 1024 + threadIdx.x * 4;
     if (j >= Dp) return;
@@ -384,7 +697,8 @@ __global__ __launch_bounds__(256) void k_tc_reduce_U(const float* __restrict__ p
         const float4 b = *reinterpret_cast<const float4*>(part + ((size_t)(s0 + s) * Q + q) * GR + r);
         a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
     }
-    *reinterpret_cast<float4*>(U + (size_t)q * Dp + j) = a;
+    *reinterpret_cast<float4*>(U + (size_t)q * Dp + j) =
+        make_float4(a.x * uscale, a.y * uscale, a.z * uscale, a.w * uscale);
 }
 
 // A image of GEMM1: tile (g, k, r) = rows (g G + r) 128 .. +127 and the k-th
@@ -442,6 +756,7 @@ struct GemmPlan {
 
 struct TcPlan {
     bool tf = false;                 // TF32 format (FP32 dictionary)
+    bool f8 = false;                 // FP8 E4M3 codes with row scales (k_gemm8)
     int Q = 0, QS = 0, QH = 0, G = 0;
     size_t smem = 0;
     void* Vs = nullptr;              // tiled image of split(P), QS x Dp
@@ -527,6 +842,10 @@ void free_gemm(GemmPlan& gp, cudaStream_t st) {
     gp.A = nullptr;
 }
 
+size_t gemm8_smem(int QS) {
+    return 1024 + (size_t)F8_NL * F8_LAND + (size_t)F8_NC * TC_A_BYTES + (size_t)F8_NB * 2 * QS * 128 + 512;
+}
+
 size_t gemm_smem(bool tf, int QS) {
     const int na = tf ? TC_NA_TF : TC_NA;
     return 1024 + (size_t)na * TC_A_BYTES * (tf ? 2 : 1) + (size_t)TC_NB * QS * 128 + 512;
@@ -555,10 +874,17 @@ cudaError_t tc_setup(cofem_ctx* c, int Q) {
     tc_release(c);
     TcPlan* t = new TcPlan();
     c->tc = t;
-    t->tf = c->phi16 == nullptr;
+    t->f8 = c->phi8 != nullptr;
+    t->tf = c->phi16 == nullptr && !t->f8;
     t->Q = Q;
     int KE, acc_stride;
-    if (t->tf) {
+    if (t->f8) {   // codes: 128 per 128-byte tile row; split blocks in BF16
+        t->QH = 0;
+        t->QS = ((3 * Q + 15) / 16) * 16;
+        t->esz = 2;
+        KE = 128;
+        if (t->QS > 128) return cudaErrorNotSupported;
+    } else if (t->tf) {
         t->QH = ((Q + 15) / 16) * 16;
         t->QS = 2 * t->QH;
         t->esz = 4;
@@ -569,7 +895,10 @@ cudaError_t tc_setup(cofem_ctx* c, int Q) {
         t->esz = 2;
         KE = TC_BK;
     }
-    if (t->QS <= 128) {
+    if (t->f8) {
+        t->G = F8_G;
+        acc_stride = 128;
+    } else if (t->QS <= 128) {
         t->G = 4;
         acc_stride = 128;
     } else {
@@ -584,7 +913,7 @@ cudaError_t tc_setup(cofem_ctx* c, int Q) {
     int coop = 0, max_smem = 0;
     if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device))) return e;
     if ((e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device))) return e;
-    const bool can_fuse = !t->tf && fused_supported(c->num_sms, c->Dp, t->QS, coop != 0, max_smem);
+    const bool can_fuse = !t->tf && !t->f8 && fused_supported(c->num_sms, c->Dp, t->QS, coop != 0, max_smem);
     const int path = c->opts.dense_path;
     if (path == COFEM_PATH_SINGLE_PASS && !can_fuse) return cudaErrorNotSupported;
     if (can_fuse && path == COFEM_PATH_SINGLE_PASS) {
@@ -621,7 +950,12 @@ cudaError_t tc_setup(cofem_ctx* c, int Q) {
     if ((e = cudaMemsetAsync(t->Ts, 0, (size_t)t->QS * c->Np * t->esz, st))) return e;
     t->g1.p.B = t->Vs;
     t->g2.p.B = t->Ts;
-    if (t->tf) {
+    if (t->f8) {
+        k_tile8_rows<<<dim3(t->g1.p.K_tiles, t->g1.groups * t->G), 128, 0, st>>>(
+            c->phi8, c->Dp, t->g1.p.M_tiles, t->g1.p.K_tiles, t->G, (uint8_t*)t->g1.A);
+        k_tile8_cols<<<dim3(t->g2.p.K_tiles, t->g2.groups * t->G), 128, 0, st>>>(
+            c->phi8, c->Dp, t->g2.p.M_tiles, t->g2.p.K_tiles, t->G, (uint8_t*)t->g2.A);
+    } else if (t->tf) {
         k_tile_rows<float><<<dim3(t->g1.p.K_tiles, t->g1.groups * t->G), 128, 0, st>>>(
             c->phi32, c->Dp, t->g1.p.M_tiles, t->g1.p.K_tiles, t->G, (float*)t->g1.A);
         k_tile_cols<float><<<dim3(t->g2.p.K_tiles, t->g2.groups * t->G), 128, 0, st>>>(
@@ -634,7 +968,7 @@ cudaError_t tc_setup(cofem_ctx* c, int Q) {
     }
     if ((e = cudaGetLastError())) return e;
     if ((e = cudaStreamSynchronize(st))) return e;
-    t->smem = gemm_smem(t->tf, t->QS);
+    t->smem = t->f8 ? gemm8_smem(t->QS) : gemm_smem(t->tf, t->QS);
     return cudaSuccess;
 }
 
@@ -645,19 +979,22 @@ cudaError_t tc_kernel_attributes(int max_smem) {
     cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e != cudaSuccess) return e;
     if ((e = fused_kernel_attributes(max_smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_gemm8, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem)) != cudaSuccess)
+        return e;
     return cudaFuncSetAttribute(k_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
 }
 
 SplitOut tc_direction_split(cofem_ctx* c) {
     TcPlan* t = (TcPlan*)c->tc;
     if (!t || c->kind != COFEM_OP_DENSE) return SplitOut{nullptr, 0, 0, 0};
-    return SplitOut{t->Vs, t->tf ? 2 : 1, t->QS, t->QH};
+    return SplitOut{t->Vs, t->tf ? 2 : 1, t->QS, t->QH, t->f8 ? F8_BSCALE : 1.0f};
 }
 
 OpOut op_output(cofem_ctx* c) {
     TcPlan* t = (TcPlan*)c->tc;
     if (c->kind == COFEM_OP_DENSE && t && t->fused) return OpOut{c->U, 1, (size_t)c->Qcap * c->Dp, nullptr, 0};
-    if (c->kind == COFEM_OP_DENSE && t) return OpOut{t->g2.part, 1, 0, t->g2.grp_seg, t->G * TC_BM};
+    if (c->kind == COFEM_OP_DENSE && t)
+        return OpOut{t->g2.part, 1, 0, t->g2.grp_seg, t->G * TC_BM, t->f8 ? F8_RFAC : 1.0f};
     const int S2 = c->kind == COFEM_OP_DENSE ? c->S2 : 1;
     return OpOut{c->U, S2, (size_t)c->Qcap * c->Dp, nullptr, 0};
 }
@@ -668,23 +1005,25 @@ OpOut op_output(cofem_ctx* c) {
 // application (OP_PLAIN) also sums the partials into U.
 void launch_tc_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode) {
     TcPlan* t = (TcPlan*)c->tc;
-    const SplitOut sv{t->Vs, t->tf ? 2 : 1, t->QS, t->QH};
-    const SplitOut st{t->Ts, t->tf ? 2 : 1, t->QS, t->QH};
+    const SplitOut sv{t->Vs, t->tf ? 2 : 1, t->QS, t->QH, t->f8 ? F8_BSCALE : 1.0f};
+    const SplitOut st{t->Ts, t->tf ? 2 : 1, t->QS, t->QH, t->f8 ? F8_BSCALE : 1.0f};
     if (mode == OP_RR || mode == OP_PLAIN)
         s.launch(k_split, dim3((unsigned)((c->Dp / 4 + 255) / 256), Q), dim3(256), 0, V, c->Dp, sv);
     if (t->fused) {   // writes U and finishes pi, gamma itself
         launch_fused(s, t->fused, mode);
         return;
     }
-    void (*gemm)(TcParams) = t->tf ? k_gemm_tc<true> : k_gemm_tc<false>;
-    s.launch(gemm, dim3(t->g1.nCTA), dim3(TC_THREADS), t->smem, t->g1.p);
+    void (*gemm)(TcParams) = t->f8 ? k_gemm8 : (t->tf ? k_gemm_tc<true> : k_gemm_tc<false>);
+    const unsigned nthreads = t->f8 ? F8_THREADS : TC_THREADS;
+    s.launch(gemm, dim3(t->g1.nCTA), dim3(nthreads), t->smem, t->g1.p);
     const int nblk = (int)((c->Np + 1023) / 1024);
     s.launch(k_tc_reduce_T, dim3(nblk, Q), dim3(256), 0, t->g1.part, t->g1.grp_seg, t->G * TC_BM, Q, c->Np, st,
-             c->tt_part, nblk, c->counters + 8, c->ctl, mode);
-    s.launch(gemm, dim3(t->g2.nCTA), dim3(TC_THREADS), t->smem, t->g2.p);
+             c->tt_part, nblk, c->counters + 8, c->ctl, mode, t->f8 ? (const float*)c->scale8 : (const float*)nullptr,
+             t->f8 ? F8_RFAC : 1.0f);
+    s.launch(gemm, dim3(t->g2.nCTA), dim3(nthreads), t->smem, t->g2.p);
     if (mode == OP_PLAIN)
         s.launch(k_tc_reduce_U, dim3((unsigned)((c->Dp + 1023) / 1024), Q), dim3(256), 0, t->g2.part,
-                 t->g2.grp_seg, t->G * TC_BM, Q, c->Dp, c->U);
+                 t->g2.grp_seg, t->G * TC_BM, Q, c->Dp, c->U, t->f8 ? F8_RFAC : 1.0f);
 }
 
 // Operator form in use and kernels per application (CG loop, residual replacement).

@@ -42,6 +42,31 @@ def bf16_round(x):
     return b.astype(np.uint32).view(np.float32)
 
 
+def _e4m3_grid():
+    """Non-negative E4M3 values in code order (codes 0x00 .. 0x7E): subnormals
+    m/8 * 2^-6, normals (1 + m/8) * 2^(e-7); 0x7F is NaN and never produced."""
+    v = [m / 8 * 2.0 ** -6 for m in range(8)]
+    v += [(1 + m / 8) * 2.0 ** (e - 7) for e in range(1, 16) for m in range(8)]
+    return np.array(v[:127])
+
+
+def e4m3_quantise(phi):
+    """Per-row scales s_i = max|Phi_i| / 448 (FP32) and E4M3 codes of
+    Phi_ij / s_i (FP32 division, round to nearest, ties to the even code,
+    saturating at 448).  Returns (s float32 [N], decoded values float64 [N, D])."""
+    p32 = np.ascontiguousarray(phi, np.float32)
+    s = (np.abs(p32).max(axis=1) / np.float32(448.0)).astype(np.float32)
+    safe = np.where(s > 0, s, np.float32(1.0))
+    x = np.where(s[:, None] > 0, p32 / safe[:, None], np.float32(0.0)).astype(np.float32).astype(np.float64)
+    g = _e4m3_grid()
+    a = np.minimum(np.abs(x), g[-1])
+    hi = np.clip(np.searchsorted(g, a, side="left"), 0, len(g) - 1)
+    lo = np.maximum(hi - 1, 0)
+    dlo, dhi = a - g[lo], g[hi] - a
+    pick = np.where(dlo < dhi, lo, np.where(dhi < dlo, hi, np.where(lo % 2 == 0, lo, hi)))
+    return s, np.sign(x) * g[pick]
+
+
 def gpu_fit(cf, prob, K, T, tol, maxit, seed=2, alpha0=None, host=False, **opts):
     D = prob.D
     if host:
@@ -161,6 +186,28 @@ def test_operator_dense_bf16(cf, N, D, Q, path):
     with cf.CoFEM(N, D, cf.COFEM_OP_DENSE, p.phi, precision=cf.COFEM_BF16, dense_path=PATHS[path]) as m:
         _check_operator(cf, m, DenseOperator(bf16_round(p.phi)), D, Q, seed=Q)
         assert cf.cofem_operator_info(m.h)[0] == PATHS[path]
+
+
+@pytest.mark.parametrize("N,D", [(77, 301), (256, 1024), (1000, 3000), (1, 5)])
+def test_fp8_dictionary_is_the_e4m3_quantisation(cf, N, D):
+    """a0, FP8 form: the stored dictionary is s_i * e4m3(Phi_ij / s_i) bit for bit."""
+    p = dense_gaussian(N, D, 3, 20.0, seed=N)
+    s, dec = e4m3_quantise(p.phi)
+    want = (s[:, None] * dec.astype(np.float32)).astype(np.float32)
+    got = np.empty((N, D), np.float32)
+    with cf.CoFEM(N, D, cf.COFEM_OP_DENSE, p.phi, precision=cf.COFEM_FP8_E4M3) as m:
+        cf.cofem_get_dictionary(m.h, got)
+    np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("N,D,Q", [(77, 301, 5), (256, 1024, 33), (1000, 3000, 17), (2500, 10000, 33),
+                                   (128, 128, 2), (1, 5, 1), (1153, 4000, 42)])
+def test_operator_dense_fp8(cf, N, D, Q):
+    """FP8 form: the operator on the quantised dictionary s_i e4m3(Phi_ij / s_i)."""
+    p = dense_gaussian(N, D, 3, 20.0, seed=Q + 2)
+    s, dec = e4m3_quantise(p.phi)
+    with cf.CoFEM(N, D, cf.COFEM_OP_DENSE, p.phi, precision=cf.COFEM_FP8_E4M3) as m:
+        _check_operator(cf, m, DenseOperator(s.astype(np.float64)[:, None] * dec), D, Q, seed=Q)
 
 
 def test_single_pass_rejected_where_it_does_not_apply(cf):
@@ -313,6 +360,14 @@ def test_fit_bf16_matches_oracle_on_quantised_dictionary(cf, path):
     assert_fit_close(g, r)
 
 
+def test_fit_fp8_matches_oracle_on_quantised_dictionary(cf):
+    p = dense_gaussian(250, 500, 10, 15.0, seed=12)
+    s, dec = e4m3_quantise(p.phi)
+    g = gpu_fit(cf, p, 16, 10, 1e-5, 400, precision=cf.COFEM_FP8_E4M3)
+    r = oracle_fit(p, 16, 10, 1e-5, 400, phi=s.astype(np.float64)[:, None] * dec)
+    assert_fit_close(g, r)
+
+
 def test_fit_single_pass_graph_direct_and_repeat_identical(cf):
     """The cooperative single-pass operator inside the CUDA graph and from the
     host loop, and twice in a row: identical bits (its reductions have a fixed
@@ -402,6 +457,26 @@ def test_fit_dense_n2500_d10000_k32_properties(cf):
     nmse_db = 20 * np.log10(np.linalg.norm(g["mu"] - p.z) / np.linalg.norm(p.z))
     assert nmse_db < -20.0
     assert abs(nmse_db - nmse_tc) < 0.1
+
+
+def test_fit_dense_n8192_d32768_fp8_properties(cf):
+    """The 8192 x 32768 problem with the FP8 E4M3 dictionary: every E-step
+    converges, mu solves the E-step system of the quantised dictionary, and
+    the NMSE stays within 4 dB of the BF16 form."""
+    from synth import workload
+    p, run = workload("dense_n8192_d32768_k32_bf16")
+    g = gpu_fit(cf, p, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], seed=run["seed"],
+                precision=cf.COFEM_FP8_E4M3)
+    assert not g["flags"] & cf.COFEM_FLAG_CG_NOT_CONVERGED, g["cg_iters"]
+    phq = np.empty(p.phi.shape, np.float32)
+    for i0 in range(0, p.N, 512):                      # quantise by row blocks
+        s, dec = e4m3_quantise(p.phi[i0:i0 + 512])
+        phq[i0:i0 + 512] = s[:, None] * dec
+    assert _mu_residual(phq, p.y, p.beta, g["alpha"], g["mu"]) < 10 * run["cg_tol"]
+    b = gpu_fit(cf, p, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], seed=run["seed"],
+                precision=cf.COFEM_BF16)
+    nm = [20 * np.log10(np.linalg.norm(x["mu"] - p.z) / np.linalg.norm(p.z)) for x in (g, b)]
+    assert nm[0] < nm[1] + 4.0, nm
 
 
 def test_fit_dense_n8192_d32768_bf16_properties(cf):
