@@ -294,9 +294,8 @@ cofem_status cofem_get_dictionary(struct cofem_ctx* h, float* out);
  * (0) for the CUDA-core forms (FP32 FMA, convolution); *kernels_cg = kernels
  * launched per operator application inside the CG loop; *kernels_rr = per
  * application in a residual replacement; *kernels_step = kernels of the CG
- * update, stopping test and direction per CG step (1 when they run as one
- * cooperative kernel, which needs rr_period = 0 and all (K+1) x ceil(D/4096)
- * blocks co-resident; else 2).  Any output pointer may be NULL.  Errors:
+ * update, stopping test and direction per CG step (2).  Any output pointer
+ * may be NULL.  Errors:
  * INVALID_ARG (NULL handle, or no fit or application yet). */
 cofem_status cofem_operator_info(struct cofem_ctx* h, int* path, int* kernels_cg, int* kernels_rr,
                                  int* kernels_step);

@@ -190,17 +190,12 @@ cofem_status build_graph(cofem_ctx* c, int Q) {
     launch_cg_init(em, c, Q, h_cg);
     Sink cg = em.conditional(h_cg, cudaGraphCondTypeWhile);
     launch_operator(cg, c, Q, c->P, OP_CG);
-    Sink rr;
-    if (cg_step_fusable(c, Q)) {   // update, stopping test and direction in one launch
-        launch_cg_step(cg, c, Q, h_cg);
-    } else {
-        const cudaGraphConditionalHandle h_rr = cg.make_handle(0u, false);
-        launch_cg_update(cg, c, Q, h_rr);
-        rr = cg.conditional(h_rr, cudaGraphCondTypeIf);
-        launch_operator(rr, c, Q, c->X, OP_RR);
-        launch_rr_residual(rr, c, Q);
-        launch_cg_direction(cg, c, Q, h_cg);
-    }
+    const cudaGraphConditionalHandle h_rr = cg.make_handle(0u, false);
+    launch_cg_update(cg, c, Q, h_rr);
+    Sink rr = cg.conditional(h_rr, cudaGraphCondTypeIf);
+    launch_operator(rr, c, Q, c->X, OP_RR);
+    launch_rr_residual(rr, c, Q);
+    launch_cg_direction(cg, c, Q, h_cg);
     launch_mstep(em, c, Q, h_em);
     cudaError_t e = root.err ? root.err : (em.err ? em.err : (cg.err ? cg.err : rr.err));
     if (e != cudaSuccess) {
@@ -234,12 +229,6 @@ cofem_status run_fit_direct(cofem_ctx* c, int Q, int T) {
         if (st) return st;
         while (c->ctl_host->any_active && c->ctl_host->u < c->ctl_host->maxit) {
             launch_operator(s, c, Q, c->P, OP_CG);
-            if (cg_step_fusable(c, Q)) {
-                launch_cg_step(s, c, Q, 0);
-                if (s.err) return cuda_fail(s.err, "launch");
-                if ((st = read_ctl(c))) return st;
-                continue;
-            }
             launch_cg_update(s, c, Q, 0);
             if (s.err) return cuda_fail(s.err, "launch");
             if ((st = read_ctl(c))) return st;
@@ -701,7 +690,7 @@ cofem_status cofem_operator_info(cofem_ctx* c, int* path, int* kernels_cg, int* 
     if (path) *path = pth;
     if (kernels_cg) *kernels_cg = kc;
     if (kernels_rr) *kernels_rr = kr;
-    if (kernels_step) *kernels_step = cg_step_fusable(c, c->Qcap) ? 1 : 2;
+    if (kernels_step) *kernels_step = 2;   // k_cg_update, k_cg_direction
     return COFEM_OK;
 }
 

@@ -408,7 +408,6 @@ struct cofem_ctx {
     unsigned* check_flag = nullptr;  // one word for input finiteness checks
     uint8_t* phi8 = nullptr;         // FP8 E4M3 codes (Np x Dp), FP8 form
     float* scale8 = nullptr;         // per-row scales (Np), FP8 form
-    int step_capacity = -1;          // co-resident blocks of k_cg_step (-1: not queried yet)
     int* iters_dev = nullptr;        // T_em
     int iters_cap = 0;
     DevCtl* ctl = nullptr;
@@ -435,8 +434,6 @@ void launch_cg_init(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_c
 void launch_cg_update(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_rr);
 void launch_rr_residual(Sink& s, cofem_ctx* c, int Q);
 void launch_cg_direction(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg);
-bool cg_step_fusable(cofem_ctx* c, int Q);
-void launch_cg_step(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg);
 void launch_mstep(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_em);
 void launch_probe_fill(cudaStream_t st, unsigned long long seed, int t, int K, long long D,
                        long long ld, float* out);

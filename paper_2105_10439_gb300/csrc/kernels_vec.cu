@@ -311,139 +311,6 @@ __global__ __launch_bounds__(NT) void k_cg_direction(DevCtl* ctl, const float* _
 }
 
 // ---------------------------------------------------------------------------
-// Fused CG step for runs without residual replacement: the update, the
-// stopping test and the direction update of Alg. 2 in one cooperative launch
-// (all blocks co-resident).  Each thread keeps its elements of R and P in
-// registers across the grid-wide hand-off: the last block to post its ||r||^2
-// and r^T M^-1 r partials runs the stopping test and writes eta, then bumps a
-// generation word that the other blocks wait on (bounded: 2 s of
-// %globaltimer, then COFEM_FLAG_DEVICE_TIMEOUT).  ctl fields written in the
-// hand-off are read with ld.global.cg so no stale L1 line is used.
-// counter[0]: blocks arrived at the hand-off, [1]: generation, [2]: blocks done.
-// ---------------------------------------------------------------------------
-constexpr int STEP_V = CH / (NT * 4);   // float4 per thread
-__device__ __forceinline__ uint64_t vec_globaltimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__global__ __launch_bounds__(NT) void k_cg_step(DevCtl* ctl, OpOut uo, const float* __restrict__ alpha,
-                                                const float* __restrict__ minv, float* __restrict__ X,
-                                                float* __restrict__ R, float* __restrict__ P, long long Dp, int nch,
-                                                double* part, unsigned* counter, cudaGraphConditionalHandle h_cg,
-                                                SplitOut so) {
-    __shared__ double sh[NT / 32];
-    __shared__ double red[2 * COFEM_QMAX];
-    __shared__ int s_role;
-    __shared__ unsigned s_gen;
-    const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q;
-    const unsigned total = gridDim.x * gridDim.y;
-    const size_t off = (size_t)q * Dp;
-    float4 rv[STEP_V], pv[STEP_V];
-    float rr = 0.0f, rz = 0.0f;
-    if (ctl->active[q]) {
-        const float gamma = (float)ctl->gamma[q];
-        const float beta = (float)ctl->beta;
-#pragma unroll
-        for (int i = 0; i < STEP_V; ++i) {
-            const long long j = (long long)ch * CH + (threadIdx.x + i * NT) * 4;
-            if (j >= Dp) continue;
-            pv[i] = ld4(P + off + j);
-            const float4 av = ld4(alpha + j), mv = ld4(minv + j);
-            const float4 psi = psi4(uo, Q, q, Dp, j, beta, av, pv[i]);
-            float4 xv = ld4(X + off + j);
-            rv[i] = ld4(R + off + j);
-            xv.x += gamma * pv[i].x; xv.y += gamma * pv[i].y; xv.z += gamma * pv[i].z; xv.w += gamma * pv[i].w;
-            rv[i].x -= gamma * psi.x; rv[i].y -= gamma * psi.y; rv[i].z -= gamma * psi.z; rv[i].w -= gamma * psi.w;
-            st4(X + off + j, xv);
-            st4(R + off + j, rv[i]);
-            rr += rv[i].x * rv[i].x + rv[i].y * rv[i].y + rv[i].z * rv[i].z + rv[i].w * rv[i].w;
-            rz += rv[i].x * (rv[i].x * mv.x) + rv[i].y * (rv[i].y * mv.y) + rv[i].z * (rv[i].z * mv.z) +
-                  rv[i].w * (rv[i].w * mv.w);
-        }
-    }
-    const double rrd = block_sum_f(rr, sh);
-    const double rzd = block_sum_f(rz, sh);
-    if (threadIdx.x == 0) {
-        part[(size_t)(0 * Q + q) * nch + ch] = rrd;
-        part[(size_t)(1 * Q + q) * nch + ch] = rzd;
-    }
-    // ---- hand-off: stopping test and eta by the last block ----
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        s_gen = *(volatile unsigned*)(counter + 1);   // read before arriving
-        __threadfence();
-        s_role = atomicAdd(counter, 1u) == total - 1 ? 1 : 0;
-    }
-    __syncthreads();
-    if (s_role == 1) {
-        __threadfence();
-        reduce_parts(part, 2, Q, nch, red);
-        if (threadIdx.x == 0) ++ctl->u;
-        cg_stop_test(ctl, red, red + COFEM_QMAX);
-        if (threadIdx.x == 0) {
-            counter[0] = 0u;
-            __threadfence();
-            atomicAdd(counter + 1, 1u);
-        }
-    } else if (threadIdx.x == 0) {
-        const uint64_t t0 = vec_globaltimer();
-        for (uint32_t it = 0;; ++it) {
-            unsigned g;
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(counter + 1) : "memory");
-            if (g != s_gen) break;
-            if ((it & 15) == 15 && (vec_globaltimer() - t0 > 2000000000ull || it > (1u << 26))) {
-                atomicOr(&ctl->flags, COFEM_FLAG_DEVICE_TIMEOUT);
-                s_role = -1;
-                break;
-            }
-            __nanosleep(64);
-        }
-    }
-    __syncthreads();
-    // ---- direction: P = M^-1 R + eta P for the columns still active ----
-    float ap = 0.0f;
-    if (s_role >= 0 && __ldcg(&ctl->active[q])) {
-        const float eta = (float)__ldcg(&ctl->eta[q]);
-#pragma unroll
-        for (int i = 0; i < STEP_V; ++i) {
-            const long long j = (long long)ch * CH + (threadIdx.x + i * NT) * 4;
-            if (j >= Dp) continue;
-            const float4 mv = ld4(minv + j), av = ld4(alpha + j);
-            float4 p4;
-            p4.x = rv[i].x * mv.x + eta * pv[i].x;
-            p4.y = rv[i].y * mv.y + eta * pv[i].y;
-            p4.z = rv[i].z * mv.z + eta * pv[i].z;
-            p4.w = rv[i].w * mv.w + eta * pv[i].w;
-            st4(P + off + j, p4);
-            store_split(so, q, j, p4);
-            ap += av.x * p4.x * p4.x + av.y * p4.y * p4.y + av.z * p4.z * p4.z + av.w * p4.w * p4.w;
-        }
-    }
-    const double apd = block_sum_f(ap, sh);
-    if (threadIdx.x == 0) part[(size_t)(2 * Q + q) * nch + ch] = apd;
-    if (!last_block_arrive(counter + 2, total)) return;
-    {
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        for (int qq = w; qq < Q; qq += nw) {
-            const double* src = part + (size_t)(2 * Q + qq) * nch;
-            double v = 0.0;
-            for (int i = lane; i < nch; i += 32) v += __ldcg(src + i);
-            v = warp_sum(v);
-            if (lane == 0) red[qq] = v;
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x < Q && ctl->active[threadIdx.x]) ctl->ap[threadIdx.x] = red[threadIdx.x];
-    if (threadIdx.x == 0) {
-        const int cont = ctl->any_active && ctl->u < ctl->maxit;
-        if (ctl->any_active && !cont) ctl->flags |= COFEM_FLAG_CG_NOT_CONVERGED;
-        set_cond(h_cg, cont);
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Fused diagonal estimate + M-step (Alg. 1: s_j = (1/K) sum_k p_kj x_kj; if t < T,
 // alpha_j = 1 / max(mu_j^2 + s_j, 1/alpha_max); then M^-1 for the next E-step),
 // probes regenerated from Philox, plus EM loop bookkeeping.
@@ -563,23 +430,6 @@ void launch_rr_residual(Sink& s, cofem_ctx* c, int Q) {
 void launch_cg_direction(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg) {
     s.launch(k_cg_direction, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->R, c->alpha, c->minv, c->P, c->Dp, c->nch,
              c->part, c->counters + 3, h_cg, tc_direction_split(c));
-}
-
-// The fused step applies when residual replacement is off and all Q x nch
-// blocks fit on the device at once (cooperative launch).
-bool cg_step_fusable(cofem_ctx* c, int Q) {
-    if (c->opts.rr_period > 0) return false;
-    if (c->step_capacity < 0) {
-        int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_step, NT, 0) != cudaSuccess) per_sm = 0;
-        c->step_capacity = per_sm * c->num_sms;
-    }
-    return (long long)Q * c->nch <= c->step_capacity;
-}
-
-void launch_cg_step(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg) {
-    s.launch_cooperative(k_cg_step, dim3(c->nch, Q), dim3(NT), 0, c->ctl, op_output(c), c->alpha, c->minv, c->X,
-                         c->R, c->P, c->Dp, c->nch, c->part, c->counters + 5, h_cg, tc_direction_split(c));
 }
 
 void launch_mstep(Sink& s, cofem_ctx* c, int /*Q*/, cudaGraphConditionalHandle h_em) {
