@@ -57,6 +57,16 @@ _PRECISIONS = {"f32": lambda cf: cf.COFEM_F32, "bf16": lambda cf: cf.COFEM_BF16,
                "tf32x3": lambda cf: cf.COFEM_F32_TF32X3, "fp8": lambda cf: cf.COFEM_FP8_E4M3}
 
 
+def _aggregate_over_ranks(ms, ws, dist_mod=None, device=None):
+    """Max over ranks of the timed region (ms); one all-reduce, none at ws = 1."""
+    if ws <= 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _metric_name(name, spec):
     if spec["kind"] == "dense":
         shape = f"dense N={spec['N']} D={spec['D']}"
@@ -188,7 +198,7 @@ def run_reference(args):
     vals = []
     base = None
     for _ in range(max(1, args.steps)):
-        base = _cpu_baseline(prob, run, budget_s=max(5.0, 60.0 / max(1, args.steps)))
+        base = _cpu_baseline(prob, run, budget_s=max(1.0, args.cpu_budget / max(1, args.steps)))
         vals.append(base["value"])
     v = float(np.mean(vals))
     line = {"impl": "reference", "metric": _metric_name(name, spec), "value": v, "unit": "EM-iter/s",
@@ -268,11 +278,7 @@ def run_ours(args):
     clocks.start()
     ms, flags, all_iters = timed_fits(model, args.steps, args.warmup)
     clk = clocks.stop()
-    t_max = ms
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = _aggregate_over_ranks(ms, ws, dist if ws > 1 else None, dev)
     value = ws * args.steps * T / (t_max / 1000.0)
     mu_bf = outs[0].cpu().numpy().copy()
     nmse = _nmse_db(mu_bf, prob.z)
@@ -491,6 +497,8 @@ def main():
     ap.add_argument("--serve", action="store_true",
                     help="only the serving measurement (2000 requests unless --serve-requests is given)")
     ap.add_argument("--serve-precision", default="bf16", choices=["f32", "bf16", "tf32x3", "fp8"])
+    ap.add_argument("--cpu-budget", type=float, default=60.0,
+                    help="seconds of oracle time the reference arm samples in total")
     ap.add_argument("--dense-path", default="auto", choices=sorted(_DENSE_PATHS),
                     help="BF16 dense operator form (default: the library's choice)")
     ap.add_argument("--em-iters", type=int, default=0,
