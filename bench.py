@@ -376,7 +376,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def serving_run(cf, dev, n, precision, rate_hz=None, slots=16, budget_bytes=96 << 30, seed=1000):
+def serving_run(cf, dev, n, precision, rate_hz=None, slots=16, budget_bytes=96 << 30, seed=1000, max_sms=0):
     """Continuous-batching serving: n requests through cofem_submit/cofem_wait.
 
     Requests follow synth.serving_requests (D ~ U[1024, 16384], N = D/4, 3 %
@@ -414,7 +414,8 @@ def serving_run(cf, dev, n, precision, rate_hz=None, slots=16, budget_bytes=96 <
                  alpha=torch.empty(D, device=dev), it=torch.empty(r["T"], dtype=torch.int32, device=dev),
                  idx=idx, zv=zv)
         o["req"] = cf.make_request(cf.COFEM_OP_DENSE, N, D, phi, y, 1.0 / sigma2, r["K"], r["T"], 1e-5, 400,
-                                   o["mu"], o["s"], o["alpha"], o["it"], precision=prec, seed=r["seed"])
+                                   o["mu"], o["s"], o["alpha"], o["it"], precision=prec, seed=r["seed"],
+                                   max_sms=max_sms)
         prepared.append(o)
     torch.cuda.synchronize(dev)
     srv = cf.cofem_server_create(budget_bytes, slots)

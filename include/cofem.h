@@ -101,6 +101,8 @@ typedef struct cofem_opts {
                                  0: host-driven loop (one host sync per CG iteration) */
     int dense_path;           /* BF16 dense operator: COFEM_PATH_AUTO (default),
                                  COFEM_PATH_TWO_PASS or COFEM_PATH_SINGLE_PASS */
+    int max_sms;              /* upper bound on the SMs the handle's persistent operator
+                                 kernels occupy (0 = all): lets concurrent fits share the GPU */
 } cofem_opts;
 
 /* Dense BF16 operator forms.  TWO_PASS streams the dictionary for Phi V and a
@@ -118,7 +120,7 @@ typedef struct cofem_opts {
 #define COFEM_PATH_SINGLE_PASS 2
 
 /* Fill *o with the defaults: F32, Jacobi, per-column, rr_period 0,
- * alpha_max 1e12, seed 2, stream NULL, use_graph 1, dense_path AUTO. */
+ * alpha_max 1e12, seed 2, stream NULL, use_graph 1, dense_path AUTO, max_sms 0. */
 void cofem_default_opts(cofem_opts* o);
 
 /* Create a handle for one dictionary (step a0: upload, optional BF16
@@ -217,6 +219,7 @@ typedef struct cofem_request {
     float* s;
     float* alpha;
     int* cg_iters;            /* T_em ints or NULL */
+    int max_sms;              /* as cofem_opts (0 = all SMs) */
 } cofem_request;              /* every pointer must stay valid until the ticket completes */
 
 typedef struct cofem_result {

@@ -334,6 +334,7 @@ cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, c
     if (opts) o = *opts;
     if (kind == COFEM_OP_DENSE) {
         if (L != 0) return fail(COFEM_ERR_INVALID_ARG, "L must be 0 for a dense dictionary");
+        if (o.max_sms < 0) return fail(COFEM_ERR_INVALID_ARG, "max_sms must be >= 0");
         if (o.dense_path < COFEM_PATH_AUTO || o.dense_path > COFEM_PATH_SINGLE_PASS)
             return fail(COFEM_ERR_INVALID_ARG, "dense_path must be AUTO, TWO_PASS or SINGLE_PASS");
         if (o.precision != COFEM_F32 && o.precision != COFEM_BF16 && o.precision != COFEM_F32_TF32X3 &&
@@ -365,7 +366,7 @@ cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, c
     c->L = (int)L;
     c->opts = o;
     c->device = dev;
-    c->num_sms = sms;
+    c->num_sms = (o.max_sms > 0 && o.max_sms < sms) ? o.max_sms : sms;
     c->Np = round_up(N, 128);
     c->Dp = round_up(D, 128);
     c->use_tc = kind == COFEM_OP_DENSE && o.precision != COFEM_F32;
