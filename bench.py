@@ -252,7 +252,7 @@ def run_ours(args):
     def make(precision):
         return cf.CoFEM(N, D, kind, phi_d, prob.L, precision=precision, rr_period=run["rr_period"],
                         seed=run["seed"], stream=stream, use_graph=0 if args.no_graph else 1,
-                        dense_path=_DENSE_PATHS[args.dense_path])
+                        dense_path=_DENSE_PATHS[args.dense_path], overlap_launch=0 if args.no_overlap else 1)
 
     def timed_fits(model, steps, warmup):
         for _ in range(warmup):
@@ -289,6 +289,7 @@ def run_ours(args):
     op_ms = cf.cofem_time_operator(model.h, Q, reps)
     hbm_gbs, _, peak_kind = _peaks()
     path, op_cg, op_rr, op_step = cf.cofem_operator_info(model.h)
+    graph_overlap = cf.cofem_graph_info(model.h)[1]
     if prob.kind == "dense":
         elem = {cf.COFEM_BF16: 2, cf.COFEM_FP8_E4M3: 1}.get(prec, 4)
         if path == cf.COFEM_PATH_SINGLE_PASS:
@@ -357,7 +358,9 @@ def run_ours(args):
         "config": {"workload": name, "N": N, "D": D, "K": K, "T": T, "cg_tol": tol, "cg_maxit": maxit,
                    "rr_period": run["rr_period"], "l2": "inputs larger than L2" if prob.kind == "dense" and
                    N * D * (2 if prec == cf.COFEM_BF16 else 4) > 129e6 else "L2 not flushed between fits",
-                   "cg_iters_last_fit": [int(v) for v in all_iters[-1]]},
+                   "cg_iters_last_fit": [int(v) for v in all_iters[-1]],
+                   "launch": "cuda graph, programmatic edges" if graph_overlap else
+                   ("cuda graph" if not args.no_graph else "host loop")},
         "nmse_db": nmse, "flags": flags,
         "roofline": roof, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk,
@@ -506,6 +509,8 @@ def main():
                     help="override T (profiling runs only; the benchmark line uses the workload's T)")
     ap.add_argument("--no-graph", action="store_true",
                     help="drive the CG loop from the host (same kernels; lets profilers see each launch)")
+    ap.add_argument("--no-overlap", action="store_true",
+                    help="plain stream order for the CG-step kernels (no programmatic dependent launch)")
     ap.add_argument("--operator-only", action="store_true",
                     help="apply only the operator A V (Q = K+1 columns) --steps times; for profilers")
     args = ap.parse_args()

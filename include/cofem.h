@@ -103,6 +103,11 @@ typedef struct cofem_opts {
                                  COFEM_PATH_TWO_PASS or COFEM_PATH_SINGLE_PASS */
     int max_sms;              /* upper bound on the SMs the handle's persistent operator
                                  kernels occupy (0 = all): lets concurrent fits share the GPU */
+    int overlap_launch;       /* 1 (default): the kernels of the CG step after the first use
+                                 programmatic dependent launch (a kernel starts, and the dense
+                                 GEMMs prefetch dictionary tiles, while its predecessor
+                                 finishes; data dependences still wait for completion);
+                                 0: plain stream order */
 } cofem_opts;
 
 /* Dense BF16 operator forms.  TWO_PASS streams the dictionary for Phi V and a
@@ -120,7 +125,8 @@ typedef struct cofem_opts {
 #define COFEM_PATH_SINGLE_PASS 2
 
 /* Fill *o with the defaults: F32, Jacobi, per-column, rr_period 0,
- * alpha_max 1e12, seed 2, stream NULL, use_graph 1, dense_path AUTO, max_sms 0. */
+ * alpha_max 1e12, seed 2, stream NULL, use_graph 1, dense_path AUTO, max_sms 0,
+ * overlap_launch 1. */
 void cofem_default_opts(cofem_opts* o);
 
 /* Create a handle for one dictionary (step a0: upload, optional BF16
@@ -302,6 +308,14 @@ cofem_status cofem_get_dictionary(struct cofem_ctx* h, float* out);
  * INVALID_ARG (NULL handle, or no fit or application yet). */
 cofem_status cofem_operator_info(struct cofem_ctx* h, int* path, int* kernels_cg, int* kernels_rr,
                                  int* kernels_step);
+
+/* The fit graph of the handle (use_graph = 1): *built = 1 once a fit has
+ * recorded it, else 0; *overlapped = 1 if its CG-step kernels are joined by
+ * programmatic (overlapping) edges, 0 if by plain ones (overlap_launch = 0,
+ * or the driver did not take the programmatic edges and the graph was
+ * rebuilt plain).  Either pointer may be NULL.  Errors: INVALID_ARG (NULL
+ * handle). */
+cofem_status cofem_graph_info(struct cofem_ctx* h, int* built, int* overlapped);
 
 #ifdef __cplusplus
 }

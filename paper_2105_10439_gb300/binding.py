@@ -55,6 +55,7 @@ class cofem_opts(C.Structure):
         ("use_graph", C.c_int),
         ("dense_path", C.c_int),
         ("max_sms", C.c_int),
+        ("overlap_launch", C.c_int),
     ]
 
 
@@ -101,6 +102,7 @@ def _load():
         "cofem_device_bytes": (ll, [vp]),
         "cofem_get_dictionary": (i, [vp, vp]),
         "cofem_operator_info": (i, [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
+        "cofem_graph_info": (i, [vp, C.POINTER(i), C.POINTER(i)]),
         "cofem_time_operator": (i, [vp, i, i, C.POINTER(d)]),
         "cofem_apply_dense_noalloc": (i, [vp, ll, ll, ll, vp, i, vp, d, vp, vp]),
         "cofem_estimate_bytes": (ll, [i, ll, ll, ll, i, i]),
@@ -264,6 +266,13 @@ def cofem_operator_info(h: int) -> tuple[int, int, int, int]:
     path, kc, kr, ks = C.c_int(), C.c_int(), C.c_int(), C.c_int()
     _check(lib.cofem_operator_info(h, C.byref(path), C.byref(kc), C.byref(kr), C.byref(ks)))
     return path.value, kc.value, kr.value, ks.value
+
+
+def cofem_graph_info(h: int) -> tuple[int, int]:
+    """(fit graph built, its CG-step kernels joined by programmatic edges)."""
+    built, ov = C.c_int(), C.c_int()
+    _check(lib.cofem_graph_info(h, C.byref(built), C.byref(ov)))
+    return built.value, ov.value
 
 
 class CoFEM:

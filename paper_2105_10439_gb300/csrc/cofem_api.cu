@@ -177,12 +177,13 @@ cofem_status ensure_iters(cofem_ctx* c, int T) {
 }
 
 // Record the whole fit (after the host-side prologue) into a graph.
-cofem_status build_graph(cofem_ctx* c, int Q) {
+cofem_status build_graph(cofem_ctx* c, int Q, bool pdl) {
     free_graph(c);
     CK(cudaGraphCreate(&c->graph, 0));
     Sink root;
     root.stream = c->stream;
     root.graph = c->graph;
+    root.pdl = pdl;
     launch_fit_setup(root, c, Q);
     const cudaGraphConditionalHandle h_em = root.make_handle(1u, true);
     Sink em = root.conditional(h_em, cudaGraphCondTypeWhile);
@@ -190,11 +191,17 @@ cofem_status build_graph(cofem_ctx* c, int Q) {
     launch_cg_init(em, c, Q, h_cg);
     Sink cg = em.conditional(h_cg, cudaGraphCondTypeWhile);
     launch_operator(cg, c, Q, c->P, OP_CG);
-    const cudaGraphConditionalHandle h_rr = cg.make_handle(0u, false);
+    // residual replacement (an IF node) only where it is on: a conditional
+    // node between the update and the direction would end their overlap
+    const bool with_rr = c->opts.rr_period > 0;
+    const cudaGraphConditionalHandle h_rr = with_rr ? cg.make_handle(0u, false) : 0;
     launch_cg_update(cg, c, Q, h_rr);
-    Sink rr = cg.conditional(h_rr, cudaGraphCondTypeIf);
-    launch_operator(rr, c, Q, c->X, OP_RR);
-    launch_rr_residual(rr, c, Q);
+    Sink rr;
+    if (with_rr) {
+        rr = cg.conditional(h_rr, cudaGraphCondTypeIf);
+        launch_operator(rr, c, Q, c->X, OP_RR);
+        launch_rr_residual(rr, c, Q);
+    }
     launch_cg_direction(cg, c, Q, h_cg);
     launch_mstep(em, c, Q, h_em);
     cudaError_t e = root.err ? root.err : (em.err ? em.err : (cg.err ? cg.err : rr.err));
@@ -208,6 +215,7 @@ cofem_status build_graph(cofem_ctx* c, int Q) {
         return cuda_fail(e, "cudaGraphInstantiate");
     }
     c->graph_Q = Q;
+    c->graph_pdl = pdl;
     return COFEM_OK;
 }
 
@@ -221,6 +229,7 @@ cofem_status read_ctl(cofem_ctx* c) {
 cofem_status run_fit_direct(cofem_ctx* c, int Q, int T) {
     Sink s;
     s.stream = c->stream;
+    s.pdl = c->opts.overlap_launch != 0;
     launch_fit_setup(s, c, Q);
     for (int t = 1; t <= T; ++t) {
         launch_cg_init(s, c, Q, 0);
@@ -305,6 +314,7 @@ void cofem_default_opts(cofem_opts* o) {
     o->seed = 2;
     o->stream = nullptr;
     o->use_graph = 1;
+    o->overlap_launch = 1;
 }
 
 const char* cofem_status_string(cofem_status s) {
@@ -353,6 +363,7 @@ cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, c
     if (o.conv != COFEM_CONV_PER_COLUMN && o.conv != COFEM_CONV_FROBENIUS)
         return fail(COFEM_ERR_INVALID_ARG, "bad conv");
     if (o.rr_period < 0) return fail(COFEM_ERR_INVALID_ARG, "rr_period < 0");
+    if (o.overlap_launch != 0 && o.overlap_launch != 1) return fail(COFEM_ERR_INVALID_ARG, "overlap_launch must be 0 or 1");
     if (!(o.alpha_max > 0.0) || !std::isfinite(o.alpha_max)) return fail(COFEM_ERR_INVALID_ARG, "bad alpha_max");
 
     int dev = 0, sms = 0;
@@ -534,7 +545,12 @@ cofem_status cofem_fit(cofem_ctx* c, const float* y, double beta, const float* a
     }
     if (c->opts.use_graph) {
         if (c->graph_Q != Q || !c->gexec) {
-            if ((st = build_graph(c, Q))) return st;
+            // programmatic edges where the driver takes them, else plain ones
+            const bool pdl = c->opts.overlap_launch != 0;
+            if (!pdl || build_graph(c, Q, true) != COFEM_OK) {
+                (void)cudaGetLastError();
+                if ((st = build_graph(c, Q, false))) return st;
+            }
         }
         CK(cudaGraphLaunch(c->gexec, c->stream));
     } else {
@@ -692,6 +708,14 @@ cofem_status cofem_operator_info(cofem_ctx* c, int* path, int* kernels_cg, int* 
     if (kernels_cg) *kernels_cg = kc;
     if (kernels_rr) *kernels_rr = kr;
     if (kernels_step) *kernels_step = 2;   // k_cg_update, k_cg_direction
+    return COFEM_OK;
+}
+
+cofem_status cofem_graph_info(cofem_ctx* c, int* built, int* overlapped) {
+    g_err[0] = 0;
+    if (!c) return fail(COFEM_ERR_INVALID_ARG, "handle is NULL");
+    if (built) *built = c->gexec ? 1 : 0;
+    if (overlapped) *overlapped = c->gexec && c->graph_pdl ? 1 : 0;
     return COFEM_OK;
 }
 

@@ -11,7 +11,9 @@
 #include "../../include/cofem.h"
 
 #define COFEM_QMAX 64          // K <= 63
+#ifndef COFEM_VEC_CHUNK
 #define COFEM_VEC_CHUNK 4096   // elements of one column handled by a vector-kernel block
+#endif
 #define COFEM_VEC_THREADS 256
 
 // ---------------------------------------------------------------------------
@@ -268,6 +270,8 @@ struct Sink {
     cudaStream_t stream = nullptr;
     cudaGraph_t graph = nullptr;   // null -> direct launches
     cudaGraphNode_t last = nullptr;
+    bool last_kernel = false;      // whether `last` is a kernel node
+    bool pdl = false;              // launch_pdl() may overlap (else a plain launch)
     cudaError_t err = cudaSuccess;
 
     bool recording() const { return graph != nullptr; }
@@ -296,7 +300,69 @@ struct Sink {
         p.extra = nullptr;
         cudaGraphNode_t n;
         err = cudaGraphAddKernelNode(&n, graph, last ? &last : nullptr, last ? 1 : 0, &p);
-        if (err == cudaSuccess) last = n;
+        if (err == cudaSuccess) {
+            last = n;
+            last_kernel = true;
+        }
+    }
+
+    // Launch that may start while the previous kernel (of this sink) is still
+    // running: a programmatic edge in a graph, programmatic stream serialisation
+    // when launching directly.  The kernel must call griddep_wait() before it
+    // reads what the previous kernel writes.  After a non-kernel node it is an
+    // ordinary launch.
+    template <typename... P, typename... A>
+    void launch_pdl(void (*f)(P...), dim3 grid, dim3 block, size_t smem, A... args) {
+        if (err != cudaSuccess) return;
+        if (grid.x == 0 || grid.y == 0 || grid.z == 0) return;
+        if (!pdl) {
+            launch(f, grid, block, smem, args...);
+            return;
+        }
+        pdl_typed<P...>(f, grid, block, smem, static_cast<P>(args)...);
+    }
+
+    template <typename... P>
+    void pdl_typed(void (*f)(P...), dim3 grid, dim3 block, size_t smem, P... args) {
+        void* ptrs[sizeof...(P) > 0 ? sizeof...(P) : 1] = {(void*)&args...};
+        if (!graph) {
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = grid;
+            cfg.blockDim = block;
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = stream;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            err = cudaLaunchKernelExC(&cfg, (const void*)f, ptrs);
+            return;
+        }
+        cudaKernelNodeParams p = {};
+        p.func = (void*)f;
+        p.gridDim = grid;
+        p.blockDim = block;
+        p.sharedMemBytes = (unsigned)smem;
+        p.kernelParams = ptrs;
+        p.extra = nullptr;
+        cudaGraphNode_t n;
+        if (!last || !last_kernel) {
+            err = cudaGraphAddKernelNode(&n, graph, last ? &last : nullptr, last ? 1 : 0, &p);
+        } else {
+            err = cudaGraphAddKernelNode(&n, graph, nullptr, 0, &p);
+            if (err == cudaSuccess) {
+                cudaGraphEdgeData e = {};
+                e.from_port = cudaGraphKernelNodePortProgrammatic;
+                e.to_port = 0;
+                e.type = cudaGraphDependencyTypeProgrammatic;
+                err = cudaGraphAddDependencies(graph, &last, &n, &e, 1);
+            }
+        }
+        if (err == cudaSuccess) {
+            last = n;
+            last_kernel = true;
+        }
     }
 
     // Cooperative launch (all CTAs co-resident; the kernel may wait on other CTAs).
@@ -334,7 +400,10 @@ struct Sink {
         err = cudaGraphAddKernelNode(&n, graph, last ? &last : nullptr, last ? 1 : 0, &p);
         if (err != cudaSuccess) return;
         err = cudaGraphKernelNodeSetAttribute(n, cudaLaunchAttributeCooperative, &attr[0].val);
-        if (err == cudaSuccess) last = n;
+        if (err == cudaSuccess) {
+            last = n;
+            last_kernel = true;
+        }
     }
 
     // Conditional handle owned by this sink's graph (0 in direct mode).
@@ -350,6 +419,7 @@ struct Sink {
     Sink conditional(cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type) {
         Sink body;
         body.stream = stream;
+        body.pdl = pdl;
         if (err != cudaSuccess || !graph) { body.err = err ? err : cudaErrorInvalidValue; return body; }
         cudaGraphNodeParams np = {};
         np.type = cudaGraphNodeTypeConditional;
@@ -360,6 +430,7 @@ struct Sink {
         err = cudaGraphAddNode(&n, graph, last ? &last : nullptr, nullptr, last ? 1 : 0, &np);
         if (err != cudaSuccess) { body.err = err; return body; }
         last = n;
+        last_kernel = false;
         body.graph = np.conditional.phGraph_out[0];
         return body;
     }
@@ -367,6 +438,13 @@ struct Sink {
 
 // Sets a graph conditional from one device thread (no-op for a zero handle,
 // used in the direct-launch mode).
+// Programmatic dependent launch: a kernel launched with a programmatic edge
+// may start before its predecessor finishes; griddep_wait() blocks until the
+// predecessor has completed and its writes are visible (no-op otherwise), and
+// griddep_launch() lets this kernel's own dependents start early.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, int v) {
     if (h) cudaGraphSetConditional(h, v ? 1u : 0u);
 }
@@ -420,6 +498,7 @@ struct cofem_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int graph_Q = -1;
+    bool graph_pdl = false;   // the fit graph has programmatic edges
 
     long long bytes = 0;
     std::unordered_map<void*, size_t> alloc_bytes;   // size of every live device allocation

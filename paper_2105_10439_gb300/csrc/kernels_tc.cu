@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
     const int NE = TF ? NA : NA / p.G;           // ring elements
     const uint32_t E_BYTES = (uint32_t)EPT * TC_A_BYTES;
     constexpr int KM = TF ? 8 : 16;             // K of one MMA instruction
+    griddep_launch();   // the next kernel may start its prologue; it waits for this grid's completion
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t B_BYTES = (uint32_t)p.QS * 128u;
@@ -138,6 +139,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
             // ---------------- bulk-copy producer ----------------
             uint64_t evict_first;
             asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(evict_first));
+            // The A operand is the dictionary image, which no earlier kernel
+            // writes: fill the A ring before waiting for the previous kernel
+            // (programmatic launch), whose output is the B operand.
+            long long npre = 0;
+            for (long long u = u0; u < u1 && npre < NE; ++u) {
+                const int valid = min(p.G, p.M_tiles - (int)(u / p.K_tiles) * p.G);
+                for (int r = 0; r < (TF ? valid : 1) && npre < NE; ++r, ++npre) {
+                    mbar_expect_tx(smem_u32(a_full + npre), E_BYTES);
+                    bulk_load_hint(smem_u32(ringA + npre * E_BYTES), Ab + ((size_t)u * p.G + r) * TC_A_BYTES,
+                                   E_BYTES, smem_u32(a_full + npre), evict_first);
+                }
+            }
+            na = npre;
+            griddep_wait();
+            long long ea = 0;   // A ring elements walked
             for (long long u = u0; u < u1; ++u) {
                 const int g = (int)(u / p.K_tiles), k = (int)(u % p.K_tiles);
                 const int valid = min(p.G, p.M_tiles - g * p.G);
@@ -148,9 +164,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
                 bulk_load(smem_u32(ringB + slot * B_BYTES), Bb + (size_t)k * B_BYTES, B_BYTES, smem_u32(b_full + slot));
                 ++nb;
                 bool ok = true;
-                for (int r = 0; r < (TF ? valid : 1); ++r) {
-                    slot = (int)(na % NE);
-                    use = na / NE;
+                for (int r = 0; r < (TF ? valid : 1); ++r, ++ea) {
+                    if (ea < npre) continue;   // issued before the wait
+                    slot = (int)(ea % NE);
+                    use = ea / NE;
                     if (use > 0 && !mbar_wait(smem_u32(a_empty + slot), (uint32_t)((use - 1) & 1), abort_flag)) {
                         ok = false;
                         break;
@@ -165,6 +182,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
             }
         }
     } else if (warp == 1) {
+        // the bounded barrier waits below start once the previous kernel has
+        // completed (a programmatic launch can begin while it still runs)
+        griddep_wait();
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
             long long ma = 0, mb = 0;   // ring positions consumed
@@ -234,6 +254,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
         }
     } else {
         // ------- epilogue warps: (TF32) Phi_lo tiles; TMEM -> partial sums -------
+        griddep_wait();
         const int sub = warp & 3;
         const int ew = warp - 2;
         const int GR = p.G * TC_BM;
@@ -357,6 +378,7 @@ __device__ __forceinline__ uint32_t f8_pair(uint32_t x) {   // codes in bytes 0 
 }
 
 __global__ void __launch_bounds__(F8_THREADS, 1) k_gemm8(TcParams p) {
+    griddep_launch();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t B_BYTES = (uint32_t)p.QS * 128u;   // one 64-wide k tile of the split block
@@ -409,6 +431,7 @@ __global__ void __launch_bounds__(F8_THREADS, 1) k_gemm8(TcParams p) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    griddep_wait();   // B is the previous kernel's output; bounded waits start after it completed
 
     const long long u0 = (long long)blockIdx.x * p.W / gridDim.x;
     const long long u1 = (long long)(blockIdx.x + 1) * p.W / gridDim.x;
@@ -655,6 +678,8 @@ __global__ __launch_bounds__(256) void k_tc_reduce_T(const float* __restrict__ p
                                                      int nblk, unsigned* counter, DevCtl* ctl, int mode,
                                                      const float* __restrict__ rscale, float rfac) {
     __shared__ double sh[8];
+    griddep_launch();
+    griddep_wait();   // the partials are the previous kernel's output
     const int q = blockIdx.y;
     const long long i = (long long)blockIdx.x * 1024 + threadIdx.x * 4;
     float tt = 0.0f;
@@ -1015,12 +1040,14 @@ void launch_tc_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode) 
     }
     void (*gemm)(TcParams) = t->f8 ? k_gemm8 : (t->tf ? k_gemm_tc<true> : k_gemm_tc<false>);
     const unsigned nthreads = t->f8 ? F8_THREADS : TC_THREADS;
-    s.launch(gemm, dim3(t->g1.nCTA), dim3(nthreads), t->smem, t->g1.p);
+    // programmatic launches: each kernel waits (griddep_wait) for its
+    // predecessor before it reads that kernel's output
+    s.launch_pdl(gemm, dim3(t->g1.nCTA), dim3(nthreads), t->smem, t->g1.p);
     const int nblk = (int)((c->Np + 1023) / 1024);
-    s.launch(k_tc_reduce_T, dim3(nblk, Q), dim3(256), 0, t->g1.part, t->g1.grp_seg, t->G * TC_BM, Q, c->Np, st,
+    s.launch_pdl(k_tc_reduce_T, dim3(nblk, Q), dim3(256), 0, t->g1.part, t->g1.grp_seg, t->G * TC_BM, Q, c->Np, st,
              c->tt_part, nblk, c->counters + 8, c->ctl, mode, t->f8 ? (const float*)c->scale8 : (const float*)nullptr,
              t->f8 ? F8_RFAC : 1.0f);
-    s.launch(gemm, dim3(t->g2.nCTA), dim3(nthreads), t->smem, t->g2.p);
+    s.launch_pdl(gemm, dim3(t->g2.nCTA), dim3(nthreads), t->smem, t->g2.p);
     if (mode == OP_PLAIN)
         s.launch(k_tc_reduce_U, dim3((unsigned)((c->Dp + 1023) / 1024), Q), dim3(256), 0, t->g2.part,
                  t->g2.grp_seg, t->G * TC_BM, Q, c->Dp, c->U, t->f8 ? F8_RFAC : 1.0f);

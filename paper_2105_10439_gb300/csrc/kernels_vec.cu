@@ -171,6 +171,8 @@ __global__ __launch_bounds__(NT) void k_cg_update(DevCtl* ctl, const float* __re
                                                   cudaGraphConditionalHandle h_rr) {
     __shared__ double sh[NT / 32];
     __shared__ double red[2 * COFEM_QMAX];
+    griddep_launch();
+    griddep_wait();   // gamma and the operator output come from the previous kernels
     const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q;
     float rr = 0.0f, rz = 0.0f;
     if (ctl->active[q]) {
@@ -268,6 +270,8 @@ __global__ __launch_bounds__(NT) void k_cg_direction(DevCtl* ctl, const float* _
                                                      cudaGraphConditionalHandle h_cg, SplitOut so) {
     __shared__ double sh[NT / 32];
     __shared__ double red[COFEM_QMAX];
+    griddep_launch();
+    griddep_wait();   // R and eta come from the previous kernel
     const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q;
     float ap = 0.0f;
     if (ctl->active[q]) {
@@ -418,7 +422,7 @@ void launch_cg_init(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_c
 }
 
 void launch_cg_update(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_rr) {
-    s.launch(k_cg_update, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->P, op_output(c), c->alpha, c->minv, c->X, c->R,
+    s.launch_pdl(k_cg_update, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->P, op_output(c), c->alpha, c->minv, c->X, c->R,
              c->Dp, c->nch, c->part, c->counters + 1, h_rr);
 }
 
@@ -428,7 +432,7 @@ void launch_rr_residual(Sink& s, cofem_ctx* c, int Q) {
 }
 
 void launch_cg_direction(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg) {
-    s.launch(k_cg_direction, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->R, c->alpha, c->minv, c->P, c->Dp, c->nch,
+    s.launch_pdl(k_cg_direction, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->R, c->alpha, c->minv, c->P, c->Dp, c->nch,
              c->part, c->counters + 3, h_cg, tc_direction_split(c));
 }
 

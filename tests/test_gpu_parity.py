@@ -383,6 +383,27 @@ def test_fit_single_pass_graph_direct_and_repeat_identical(cf):
     assert a["flags"] == b["flags"] == c["flags"] == 0
 
 
+@pytest.mark.parametrize("precision", ["bf16", "tf32x3", "fp8"])
+@pytest.mark.parametrize("rr_period", [0, 7])
+def test_fit_overlapped_launch_identical(cf, precision, rr_period):
+    """Programmatic dependent launch of the CG-step kernels (graph edges and
+    direct launches) changes only when kernels start: the fit has the same bits
+    as with plain stream order."""
+    prec = {"bf16": cf.COFEM_BF16, "tf32x3": cf.COFEM_F32_TF32X3, "fp8": cf.COFEM_FP8_E4M3}[precision]
+    p = dense_gaussian(700, 3000, 30, 20.0, seed=11)
+    kw = dict(precision=prec, dense_path=1, rr_period=rr_period)
+    ref = gpu_fit(cf, p, 12, 4, 1e-6, 300, use_graph=1, overlap_launch=0, **kw)
+    for use_graph in (1, 0):
+        g = gpu_fit(cf, p, 12, 4, 1e-6, 300, use_graph=use_graph, overlap_launch=1, **kw)
+        for k in ("mu", "s", "alpha", "cg_iters"):
+            np.testing.assert_array_equal(g[k], ref[k])
+        assert g["flags"] == ref["flags"]
+    with cf.CoFEM(p.N, p.D, cf.COFEM_OP_DENSE, p.phi, 0, **kw) as m:
+        assert cf.cofem_graph_info(m.h) == (0, 0)
+        m.fit(p.y, p.beta, 12, 2, 1e-6, 300)
+        assert cf.cofem_graph_info(m.h) == (1, 1)
+
+
 def test_fit_edge_cases(cf):
     p = dense_gaussian(50, 130, 5, 20.0, seed=1)
     a0 = np.linspace(0.5, 2.0, 130).astype(np.float32)
