@@ -42,7 +42,12 @@ namespace {
 constexpr int TC_BM = 128, TC_BK = 64;   // BF16 tile: 128 rows x 64 bf16 (128-byte rows)
 constexpr int TC_BK32 = 32;               // TF32 tile: 128 rows x 32 fp32 (128-byte rows)
 constexpr int TC_NA = 8, TC_NA_TF = 5, TC_NB = 3;
-constexpr int TC_THREADS = 192;
+// Epilogue warps: four (one per TMEM sub-partition) convert the TF32 tiles;
+// all of them drain the accumulators, the warps of a sub-partition splitting
+// the row tiles.  A lone warp per scheduler drained a 4-tile segment in ~6 us
+// (dependent TMEM load -> add -> store chains at one warp's issue rate).
+constexpr int tc_epi_warps(bool tf) { return tf ? 8 : 16; }
+constexpr int tc_threads(bool tf) { return 64 + 32 * tc_epi_warps(tf); }
 constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK * 2;
 constexpr uint32_t TC_TMEM_COLS = 512;
 
@@ -64,13 +69,49 @@ struct TcParams {
     unsigned* flags;      // error flag word (DevCtl::flags)
 };
 
+// TMEM -> segment partials for one epilogue warp: accumulator r (r0 <= r <
+// valid, step rstep) holds, in this warp's 32 TMEM lanes (rows), the split
+// terms of every output column (BF16: columns 3q..3q+2; TF32: q and QH + q);
+// their sum goes to out[q * GR + r * 128 + row].
+template <bool TF>
+__device__ __forceinline__ void drain_tmem(uint32_t tbase, int r0, int rstep, int valid, int acc_stride, int Q,
+                                           int QH, int NC, int GR, float* out, int row) {
+    for (int r = r0; r < valid; r += rstep) {
+        const uint32_t tb = tbase + (uint32_t)(r * acc_stride);
+        for (int qb = 0; qb * 16 < Q; ++qb) {
+            uint32_t v[48];
+            if (TF) {
+                tmem_ld16(tb + (uint32_t)(qb * 16), v);
+                tmem_ld16(tb + (uint32_t)(QH + qb * 16), v + 16);
+                tmem_ld_wait(v, 32);
+            } else {
+                const int c0 = 3 * qb;
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    if (c0 + c < NC) tmem_ld16(tb + (uint32_t)((c0 + c) * 16), v + 16 * c);
+                tmem_ld_wait(v, 48);
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int q = 16 * qb + i;
+                if (q < Q) {
+                    const float val = TF ? __uint_as_float(v[i]) + __uint_as_float(v[16 + i])
+                                         : __uint_as_float(v[3 * i]) + __uint_as_float(v[3 * i + 1]) +
+                                               __uint_as_float(v[3 * i + 2]);
+                    out[(size_t)q * GR + r * TC_BM + row] = val;
+                }
+            }
+        }
+    }
+}
+
 // Tensor-core skinny GEMM.  TF = false: A, B bf16 (B = 3-term split), one MMA
 // chain per tile.  TF = true: A, B fp32 read as TF32 (B = [P_hi | P_lo]); the
 // epilogue warps round each A tile to Phi_hi = tf32_rn(A) in place and write
 // Phi_lo = tf32_rn(A - Phi_hi) beside it, and a second MMA chain adds
 // Phi_lo [P_hi | P_lo] into the same accumulator columns (all four products).
 template <bool TF>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
+__global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc(TcParams p) {
     constexpr int NA = TF ? TC_NA_TF : TC_NA;
     constexpr int KE = TF ? TC_BK32 : TC_BK;    // elements per 128-byte tile row
     // A-ring element: one tile (TF32, converted tile by tile) or the G row
@@ -111,7 +152,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
             mbar_init(smem_u32(b_empty + i), 1);
         }
         mbar_init(smem_u32(acc_full), 1);
-        mbar_init(smem_u32(acc_empty), 4);
+        mbar_init(smem_u32(acc_empty), tc_epi_warps(TF));
         mbar_init(smem_u32(drain), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -254,11 +295,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
         }
     } else {
         // ------- epilogue warps: (TF32) Phi_lo tiles; TMEM -> partial sums -------
-        griddep_wait();
-        const int sub = warp & 3;
+        const int seg0 = p.seg_base[blockIdx.x];
+        const int sub = warp & 3;   // TMEM lanes 32 sub .. 32 sub + 31 (warp id mod 4)
         const int ew = warp - 2;
         const int GR = p.G * TC_BM;
         const int NC = p.QS / 16;
+        griddep_wait();
         int nseg = 0;
         long long ne = 0;   // A tiles converted
         long long u = u0;
@@ -267,7 +309,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
             const int g = (int)(u / p.K_tiles);
             const long long seg_end = min(u1, (long long)(g + 1) * p.K_tiles);
             const int valid = min(p.G, p.M_tiles - g * p.G);
-            if (TF) {
+            if (TF && ew < 4) {
                 for (long long uu = u; uu < seg_end && ok; ++uu) {
                     for (int r = 0; r < valid; ++r) {
                         const int sa = (int)(ne % NA);
@@ -297,35 +339,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcParams p) {
             }
             if (!mbar_wait(smem_u32(acc_full), (uint32_t)(nseg & 1), abort_flag)) break;
             tc_fence_after();
-            float* out = p.part + (size_t)(p.seg_base[blockIdx.x] + nseg) * p.Q * GR;
-            const int row = 32 * sub + lane;
-            for (int r = 0; r < valid; ++r) {
-                const uint32_t tbase = tmem + ((uint32_t)(32 * sub) << 16) + (uint32_t)(r * p.acc_stride);
-                for (int qb = 0; qb * 16 < p.Q; ++qb) {
-                    uint32_t v[48];
-                    if (TF) {
-                        tmem_ld16(tbase + (uint32_t)(qb * 16), v);
-                        tmem_ld16(tbase + (uint32_t)(p.QH + qb * 16), v + 16);
-                        tmem_ld_wait(v, 32);
-                    } else {
-                        const int c0 = 3 * qb;
-#pragma unroll
-                        for (int c = 0; c < 3; ++c)
-                            if (c0 + c < NC) tmem_ld16(tbase + (uint32_t)((c0 + c) * 16), v + 16 * c);
-                        tmem_ld_wait(v, 48);
-                    }
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int q = 16 * qb + i;
-                        if (q < p.Q) {
-                            const float val = TF ? __uint_as_float(v[i]) + __uint_as_float(v[16 + i])
-                                                 : __uint_as_float(v[3 * i]) + __uint_as_float(v[3 * i + 1]) +
-                                                       __uint_as_float(v[3 * i + 2]);
-                            out[(size_t)q * GR + r * TC_BM + row] = val;
-                        }
-                    }
-                }
-            }
+            float* out = p.part + (size_t)(seg0 + nseg) * p.Q * GR;
+            drain_tmem<TF>(tmem + ((uint32_t)(32 * sub) << 16), ew >> 2, tc_epi_warps(TF) / 4, valid, p.acc_stride,
+                           p.Q, p.QH, NC, GR, out, 32 * sub + lane);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(acc_empty));
@@ -515,9 +531,11 @@ __global__ void __launch_bounds__(F8_THREADS, 1) k_gemm8(TcParams p) {
         }
     } else if (warp < 6) {
         // ---------------- epilogue warps: TMEM -> segment partials ----------------
+        const int seg0 = p.seg_base[blockIdx.x];
         const int sub = warp & 3;
         const int GR = F8_G * TC_BM;
         const int NC = p.QS / 16;
+
         int nseg = 0;
         long long u = u0;
         while (u < u1) {
@@ -527,28 +545,9 @@ __global__ void __launch_bounds__(F8_THREADS, 1) k_gemm8(TcParams p) {
             const int buf = nseg & 1;
             if (!mbar_wait(smem_u32(acc_full + buf), (uint32_t)((nseg >> 1) & 1), abort_flag)) break;
             tc_fence_after();
-            float* out = p.part + (size_t)(p.seg_base[blockIdx.x] + nseg) * p.Q * GR;
-            const int row = 32 * sub + lane;
-            for (int r = 0; r < valid; ++r) {
-                const uint32_t tbase =
-                    tmem + ((uint32_t)(32 * sub) << 16) + (uint32_t)(buf * 2 * p.acc_stride + r * p.acc_stride);
-                for (int qb = 0; qb * 16 < p.Q; ++qb) {
-                    uint32_t v[48];
-                    const int c0 = 3 * qb;
-#pragma unroll
-                    for (int cc = 0; cc < 3; ++cc)
-                        if (c0 + cc < NC) tmem_ld16(tbase + (uint32_t)((c0 + cc) * 16), v + 16 * cc);
-                    tmem_ld_wait(v, 48);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int q = 16 * qb + i;
-                        if (q < p.Q)
-                            out[(size_t)q * GR + r * TC_BM + row] =
-                                __uint_as_float(v[3 * i]) + __uint_as_float(v[3 * i + 1]) +
-                                __uint_as_float(v[3 * i + 2]);
-                    }
-                }
-            }
+            float* out = p.part + (size_t)(seg0 + nseg) * p.Q * GR;
+            drain_tmem<false>(tmem + ((uint32_t)(32 * sub) << 16) + (uint32_t)(buf * 2 * p.acc_stride), 0, 1, valid,
+                              p.acc_stride, p.Q, 0, NC, GR, out, 32 * sub + lane);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(acc_empty + buf));
@@ -1039,7 +1038,7 @@ void launch_tc_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode) 
         return;
     }
     void (*gemm)(TcParams) = t->f8 ? k_gemm8 : (t->tf ? k_gemm_tc<true> : k_gemm_tc<false>);
-    const unsigned nthreads = t->f8 ? F8_THREADS : TC_THREADS;
+    const unsigned nthreads = t->f8 ? F8_THREADS : (unsigned)tc_threads(t->tf);
     // programmatic launches: each kernel waits (griddep_wait) for its
     // predecessor before it reads that kernel's output
     s.launch_pdl(gemm, dim3(t->g1.nCTA), dim3(nthreads), t->smem, t->g1.p);
