@@ -239,6 +239,46 @@ struct OpOut {
     float uscale = 1.0f;  // power of two the partials carry (FP8 operator: 2^56)
 };
 
+// The operator partials for elements j..j+3: the segment range [s0, s0 + ns) of
+// their row group (tensor-core path), or the S2 dense slices.
+__device__ __forceinline__ void op_range(const OpOut& o, long long j, int& s0, int& ns) {
+    if (o.grp_seg) {
+        const int g = (int)(j / o.GR);
+        s0 = o.grp_seg[2 * g];
+        ns = o.grp_seg[2 * g + 1];
+    } else {
+        s0 = 0;
+        ns = o.S2;
+    }
+}
+
+// Sum of those partials in segment order; the loads of the first four are
+// issued together (one memory round trip for the usual two to four).
+__device__ __forceinline__ float4 op_sum4(const OpOut& o, int Q, int q, long long Dp, long long j, int s0, int ns) {
+    float4 w[4];
+    const float* base;
+    size_t step;
+    if (o.grp_seg) {
+        base = o.U + ((size_t)s0 * Q + q) * o.GR + (size_t)(j % o.GR);
+        step = (size_t)Q * o.GR;
+    } else {
+        base = o.U + (size_t)q * Dp + j;
+        step = o.sstride;
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+        if (s < ns) w[s] = *reinterpret_cast<const float4*>(base + (size_t)s * step);
+    float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+        if (s < ns) { u.x += w[s].x; u.y += w[s].y; u.z += w[s].z; u.w += w[s].w; }
+    for (int s = 4; s < ns; ++s) {
+        const float4 x = *reinterpret_cast<const float4*>(base + (size_t)s * step);
+        u.x += x.x; u.y += x.y; u.z += x.z; u.w += x.w;
+    }
+    return u;
+}
+
 // Psi for elements j..j+3 of column q: beta * (Phi^T Phi v) + alpha_j v_j.
 __device__ __forceinline__ float4 psi4(const OpOut& o, int Q, int q, long long Dp, long long j, float beta,
                                        float4 av, float4 vv) {

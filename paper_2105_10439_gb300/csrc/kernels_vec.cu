@@ -13,6 +13,8 @@ namespace {
 
 constexpr int CH = COFEM_VEC_CHUNK;
 constexpr int NT = COFEM_VEC_THREADS;
+constexpr int IT = CH / (NT * 4);   // float4 positions per thread in a chunk
+static_assert(CH % (NT * 4) == 0, "a chunk is a whole number of float4 sweeps of the block");
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
@@ -163,7 +165,7 @@ __global__ __launch_bounds__(NT) void k_cg_init(DevCtl* ctl, const float* __rest
 // Fused CG update (Alg. 2: X += P Gamma, R -= Psi Gamma, then ||r||, r^T M^-1 r,
 // stopping test and eta), for the active columns.
 // ---------------------------------------------------------------------------
-__global__ __launch_bounds__(NT) void k_cg_update(DevCtl* ctl, const float* __restrict__ P, OpOut uo,
+__global__ __launch_bounds__(NT, 2) void k_cg_update(DevCtl* ctl, const float* __restrict__ P, OpOut uo,
                                                   const float* __restrict__ alpha,
                                                   const float* __restrict__ minv, float* __restrict__ X,
                                                   float* __restrict__ R, long long Dp, int nch,
@@ -179,18 +181,51 @@ __global__ __launch_bounds__(NT) void k_cg_update(DevCtl* ctl, const float* __re
         const float gamma = (float)ctl->gamma[q];
         const float beta = (float)ctl->beta;
         const size_t off = (size_t)q * Dp;
-        for (int e = threadIdx.x * 4; e < CH; e += NT * 4) {
-            const long long j = (long long)ch * CH + e;
+        // all loads of the thread's IT float4 positions first (the kernel is
+        // bound by memory round trips, not bandwidth), then the partial sums
+        // of the operator, then the arithmetic in element order
+        float4 pv[IT], av[IT], mv[IT], xv[IT], rv[IT], uv[IT];
+        int s0[IT], ns[IT];
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const long long j = (long long)ch * CH + (long long)(threadIdx.x + it * NT) * 4;
+            if (j < Dp) {
+                pv[it] = ld4(P + off + j);
+                av[it] = ld4(alpha + j);
+                mv[it] = ld4(minv + j);
+                xv[it] = ld4(X + off + j);
+                rv[it] = ld4(R + off + j);
+                op_range(uo, j, s0[it], ns[it]);
+            }
+        }
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {   // X needs no operator output: store it now
+            const long long j = (long long)ch * CH + (long long)(threadIdx.x + it * NT) * 4;
+            if (j < Dp) {
+                float4 x4 = xv[it];
+                const float4 p4 = pv[it];
+                x4.x += gamma * p4.x; x4.y += gamma * p4.y; x4.z += gamma * p4.z; x4.w += gamma * p4.w;
+                st4(X + off + j, x4);
+            }
+        }
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const long long j = (long long)ch * CH + (long long)(threadIdx.x + it * NT) * 4;
+            if (j < Dp) uv[it] = op_sum4(uo, Q, q, Dp, j, s0[it], ns[it]);
+        }
+        const float bu = beta * uo.uscale;
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const long long j = (long long)ch * CH + (long long)(threadIdx.x + it * NT) * 4;
             if (j >= Dp) break;
-            const float4 pv = ld4(P + off + j), av = ld4(alpha + j), mv = ld4(minv + j);
-            const float4 psi = psi4(uo, Q, q, Dp, j, beta, av, pv);
-            float4 xv = ld4(X + off + j), rv = ld4(R + off + j);
-            xv.x += gamma * pv.x; xv.y += gamma * pv.y; xv.z += gamma * pv.z; xv.w += gamma * pv.w;
-            rv.x -= gamma * psi.x; rv.y -= gamma * psi.y; rv.z -= gamma * psi.z; rv.w -= gamma * psi.w;
-            st4(X + off + j, xv);
-            st4(R + off + j, rv);
-            rr += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
-            rz += rv.x * (rv.x * mv.x) + rv.y * (rv.y * mv.y) + rv.z * (rv.z * mv.z) + rv.w * (rv.w * mv.w);
+            const float4 p4 = pv[it], a4 = av[it], m4 = mv[it], u4 = uv[it];
+            const float4 psi = make_float4(bu * u4.x + a4.x * p4.x, bu * u4.y + a4.y * p4.y,
+                                           bu * u4.z + a4.z * p4.z, bu * u4.w + a4.w * p4.w);
+            float4 r4 = rv[it];
+            r4.x -= gamma * psi.x; r4.y -= gamma * psi.y; r4.z -= gamma * psi.z; r4.w -= gamma * psi.w;
+            st4(R + off + j, r4);
+            rr += r4.x * r4.x + r4.y * r4.y + r4.z * r4.z + r4.w * r4.w;
+            rz += r4.x * (r4.x * m4.x) + r4.y * (r4.y * m4.y) + r4.z * (r4.z * m4.z) + r4.w * (r4.w * m4.w);
         }
     }
     const double rrd = block_sum_f(rr, sh);
@@ -277,18 +312,30 @@ __global__ __launch_bounds__(NT) void k_cg_direction(DevCtl* ctl, const float* _
     if (ctl->active[q]) {
         const float eta = (float)ctl->eta[q];
         const size_t off = (size_t)q * Dp;
-        for (int e = threadIdx.x * 4; e < CH; e += NT * 4) {
-            const long long j = (long long)ch * CH + e;
+        float4 rv[IT], mv[IT], av[IT], pv[IT];   // loads first (see k_cg_update)
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const long long j = (long long)ch * CH + (long long)(threadIdx.x + it * NT) * 4;
+            if (j < Dp) {
+                rv[it] = ld4(R + off + j);
+                mv[it] = ld4(minv + j);
+                av[it] = ld4(alpha + j);
+                pv[it] = ld4(P + off + j);
+            }
+        }
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const long long j = (long long)ch * CH + (long long)(threadIdx.x + it * NT) * 4;
             if (j >= Dp) break;
-            const float4 rv = ld4(R + off + j), mv = ld4(minv + j), av = ld4(alpha + j);
-            float4 pv = ld4(P + off + j);
-            pv.x = rv.x * mv.x + eta * pv.x;
-            pv.y = rv.y * mv.y + eta * pv.y;
-            pv.z = rv.z * mv.z + eta * pv.z;
-            pv.w = rv.w * mv.w + eta * pv.w;
-            st4(P + off + j, pv);
-            store_split(so, q, j, pv);
-            ap += av.x * pv.x * pv.x + av.y * pv.y * pv.y + av.z * pv.z * pv.z + av.w * pv.w * pv.w;
+            float4 p4 = pv[it];
+            const float4 r4 = rv[it], m4 = mv[it], a4 = av[it];
+            p4.x = r4.x * m4.x + eta * p4.x;
+            p4.y = r4.y * m4.y + eta * p4.y;
+            p4.z = r4.z * m4.z + eta * p4.z;
+            p4.w = r4.w * m4.w + eta * p4.w;
+            st4(P + off + j, p4);
+            store_split(so, q, j, p4);
+            ap += a4.x * p4.x * p4.x + a4.y * p4.y * p4.y + a4.z * p4.z * p4.z + a4.w * p4.w * p4.w;
         }
     }
     const double apd = block_sum_f(ap, sh);
