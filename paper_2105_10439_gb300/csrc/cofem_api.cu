@@ -195,7 +195,7 @@ cofem_status build_graph(cofem_ctx* c, int Q, bool pdl) {
     // node between the update and the direction would end their overlap
     const bool with_rr = c->opts.rr_period > 0;
     const cudaGraphConditionalHandle h_rr = with_rr ? cg.make_handle(0u, false) : 0;
-    launch_cg_update(cg, c, Q, h_rr);
+    launch_cg_update(cg, c, Q, h_rr, h_cg);
     Sink rr;
     if (with_rr) {
         rr = cg.conditional(h_rr, cudaGraphCondTypeIf);
@@ -238,7 +238,7 @@ cofem_status run_fit_direct(cofem_ctx* c, int Q, int T) {
         if (st) return st;
         while (c->ctl_host->any_active && c->ctl_host->u < c->ctl_host->maxit) {
             launch_operator(s, c, Q, c->P, OP_CG);
-            launch_cg_update(s, c, Q, 0);
+            launch_cg_update(s, c, Q, 0, 0);
             if (s.err) return cuda_fail(s.err, "launch");
             if ((st = read_ctl(c))) return st;
             const int u = c->ctl_host->u;
@@ -533,6 +533,8 @@ cofem_status cofem_fit(cofem_ctx* c, const float* y, double beta, const float* a
     hc->maxit = cg_maxit;
     hc->conv = c->opts.conv;
     hc->rr_period = c->opts.rr_period;
+    hc->ap_part = c->part + (size_t)2 * Q * c->nch;   // slab 2 of the CG partials
+    hc->ap_n = c->nch;
     CK(cudaMemcpyAsync(c->ctl, hc, sizeof(DevCtl), cudaMemcpyHostToDevice, c->stream));
     if ((st = stage_y_and_b(c, y, beta))) return st;
     if (alpha0) {

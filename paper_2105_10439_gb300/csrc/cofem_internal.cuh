@@ -30,7 +30,7 @@ struct DevCtl {
     int any_active;   // some column still iterating
     unsigned flags;   // COFEM_FLAG_* bits
     int active[COFEM_QMAX];
-    double rho[COFEM_QMAX];     // r^T M^-1 r
+    double rho[2][COFEM_QMAX];  // r^T M^-1 r of the residual after u CG iterations, at [u & 1]
     double pi[COFEM_QMAX];      // p^T A p
     double gamma[COFEM_QMAX];   // rho / pi
     double eta[COFEM_QMAX];     // rho_new / rho_old
@@ -38,6 +38,8 @@ struct DevCtl {
     double rnorm2[COFEM_QMAX];  // ||r_q||^2
     double ap[COFEM_QMAX];      // p^T diag(alpha) p
     double tt[COFEM_QMAX];      // ||Phi p||^2
+    const double* ap_part;      // per-block partials of p^T diag(alpha) p: [q][ap_n]
+    int ap_n;
 };
 
 // Modes of the operator kernels.
@@ -550,7 +552,8 @@ struct cofem_ctx {
 // kernels_vec.cu
 void launch_fit_setup(Sink& s, cofem_ctx* c, int Q);                 // alpha -> minv, ctl t = 1
 void launch_cg_init(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg);
-void launch_cg_update(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_rr);
+void launch_cg_update(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_rr,
+                      cudaGraphConditionalHandle h_cg);
 void launch_rr_residual(Sink& s, cofem_ctx* c, int Q);
 void launch_cg_direction(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg);
 void launch_mstep(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_em);
@@ -617,14 +620,20 @@ __device__ __forceinline__ void op_finalize_block(DevCtl* ctl, const double* tt_
     if (q < Q) {
         ctl->tt[q] = s_tt[q];
         if (mode == OP_CG && ctl->active[q]) {
-            const double pi = ctl->beta * s_tt[q] + ctl->ap[q];
+            // p^T diag(alpha) p from the direction (or initialisation) kernel's
+            // per-block partials, in block order
+            const double* src = ctl->ap_part + (size_t)q * ctl->ap_n;
+            double ap = 0.0;
+            for (int i = 0; i < ctl->ap_n; ++i) ap += __ldcg(src + i);
+            ctl->ap[q] = ap;
+            const double pi = ctl->beta * s_tt[q] + ap;
             ctl->pi[q] = pi;
             if (!(pi > 0.0) || !isfinite(pi)) {
                 atomicOr(&ctl->flags, COFEM_FLAG_BREAKDOWN);
                 ctl->active[q] = 0;
                 ctl->gamma[q] = 0.0;
             } else {
-                ctl->gamma[q] = ctl->rho[q] / pi;
+                ctl->gamma[q] = ctl->rho[ctl->u & 1][q] / pi;
             }
         }
         act = ctl->active[q];

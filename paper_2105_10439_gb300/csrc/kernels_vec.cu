@@ -42,40 +42,19 @@ __device__ void reduce_parts(const double* part, int nk, int Q, int nch, double*
     __syncthreads();
 }
 
-// Alg. 2 stopping test and direction scalars for the columns still active,
-// run by every thread of the last block (one column per thread).
-// rr[q] = ||r_q||^2, rz[q] = r_q^T M^-1 r_q.  ||r_q|| / ||b_q|| <= tol is tested
-// as ||r_q||^2 <= tol^2 ||b_q||^2.
-__device__ void cg_stop_test(DevCtl* ctl, const double* rr, const double* rz) {
-    __shared__ int s_stop_all;
-    const int Q = ctl->Q;
-    const double t2 = ctl->tol * ctl->tol;
-    if (threadIdx.x == 0) {
-        s_stop_all = 0;
-        if (ctl->conv == COFEM_CONV_FROBENIUS) {
-            double num = 0.0, den = 0.0;
-            for (int q = 0; q < Q; ++q) {
-                if (ctl->active[q]) num += rr[q];
-                den += ctl->bnorm2[q];
-            }
-            s_stop_all = num <= t2 * den;
-        }
+// Sum of n per-block partials in block order (loads issued eight at a time).
+__device__ __forceinline__ double sum_parts(const double* src, int n) {
+    double v = 0.0;
+    int i = 0;
+    for (; i + 8 <= n; i += 8) {
+        double x[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) x[t] = __ldcg(src + i + t);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v += x[t];
     }
-    __syncthreads();
-    const int q = threadIdx.x;
-    int act = 0;
-    if (q < Q && ctl->active[q]) {
-        ctl->rnorm2[q] = rr[q];
-        if (s_stop_all || (ctl->conv == COFEM_CONV_PER_COLUMN && rr[q] <= t2 * ctl->bnorm2[q])) {
-            ctl->active[q] = 0;
-        } else {
-            ctl->eta[q] = rz[q] / ctl->rho[q];
-            ctl->rho[q] = rz[q];
-            act = 1;
-        }
-    }
-    act = __syncthreads_or(act);
-    if (threadIdx.x == 0) ctl->any_active = act;
+    for (; i < n; ++i) v += __ldcg(src + i);
+    return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -147,7 +126,7 @@ __global__ __launch_bounds__(NT) void k_cg_init(DevCtl* ctl, const float* __rest
     int act = 0;
     if (qq < Q) {
         ctl->bnorm2[qq] = red[qq];
-        ctl->rho[qq] = red[COFEM_QMAX + qq];
+        ctl->rho[0][qq] = red[COFEM_QMAX + qq];
         ctl->ap[qq] = red[2 * COFEM_QMAX + qq];
         ctl->rnorm2[qq] = red[qq];
         act = red[qq] > 0.0;   // a zero right-hand side starts converged (x = 0)
@@ -162,20 +141,28 @@ __global__ __launch_bounds__(NT) void k_cg_init(DevCtl* ctl, const float* __rest
 }
 
 // ---------------------------------------------------------------------------
-// Fused CG update (Alg. 2: X += P Gamma, R -= Psi Gamma, then ||r||, r^T M^-1 r,
-// stopping test and eta), for the active columns.
+// Fused CG update (Alg. 2: X += P Gamma, R -= Psi Gamma, and the per-block
+// partials of ||r||^2 and r^T M^-1 r), for the active columns.
 // ---------------------------------------------------------------------------
 __global__ __launch_bounds__(NT, 2) void k_cg_update(DevCtl* ctl, const float* __restrict__ P, OpOut uo,
                                                   const float* __restrict__ alpha,
                                                   const float* __restrict__ minv, float* __restrict__ X,
                                                   float* __restrict__ R, long long Dp, int nch,
-                                                  double* part, unsigned* counter,
-                                                  cudaGraphConditionalHandle h_rr) {
+                                                  double* part, cudaGraphConditionalHandle h_rr,
+                                                  cudaGraphConditionalHandle h_cg) {
     __shared__ double sh[NT / 32];
-    __shared__ double red[2 * COFEM_QMAX];
     griddep_launch();
     griddep_wait();   // gamma and the operator output come from the previous kernels
     const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        // iteration bookkeeping; the stopping test and the loop condition are
+        // the direction kernel's (it reads this kernel's partials)
+        const int u = ctl->u + 1;
+        ctl->u = u;
+        ctl->any_active = 0;
+        set_cond(h_rr, ctl->rr_period > 0 && u % ctl->rr_period == 0);
+        set_cond(h_cg, 0);
+    }
     float rr = 0.0f, rz = 0.0f;
     if (ctl->active[q]) {
         const float gamma = (float)ctl->gamma[q];
@@ -234,29 +221,18 @@ __global__ __launch_bounds__(NT, 2) void k_cg_update(DevCtl* ctl, const float* _
         part[(size_t)(0 * Q + q) * nch + ch] = rrd;
         part[(size_t)(1 * Q + q) * nch + ch] = rzd;
     }
-    if (!last_block_arrive(counter, gridDim.x * gridDim.y)) return;
-    reduce_parts(part, 2, Q, nch, red);
-    __shared__ int s_rr;
-    if (threadIdx.x == 0) {
-        const int u = ++ctl->u;
-        s_rr = ctl->rr_period > 0 && u % ctl->rr_period == 0;   // replacement finishes this iteration
-        set_cond(h_rr, s_rr);
-    }
-    __syncthreads();
-    if (!s_rr) cg_stop_test(ctl, red, red + COFEM_QMAX);
 }
 
 // ---------------------------------------------------------------------------
 // Residual replacement (precision form): R = B - A X for the active columns,
-// with B regenerated (b, probes), then the stopping test and eta.
+// with B regenerated (b, probes), and the partials of ||r||^2 and r^T M^-1 r.
 // ---------------------------------------------------------------------------
 __global__ __launch_bounds__(NT) void k_rr_residual(DevCtl* ctl, const float* __restrict__ b,
                                                     const float* __restrict__ X, OpOut uo,
                                                     const float* __restrict__ alpha, const float* __restrict__ minv,
                                                     float* __restrict__ R, long long D, long long Dp,
-                                                    int nch, double* part, unsigned* counter) {
+                                                    int nch, double* part) {
     __shared__ double sh[NT / 32];
-    __shared__ double red[2 * COFEM_QMAX];
     const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q, t = ctl->t;
     float rr = 0.0f, rz = 0.0f;
     if (ctl->active[q]) {
@@ -285,33 +261,86 @@ __global__ __launch_bounds__(NT) void k_rr_residual(DevCtl* ctl, const float* __
     }
     const double rrd = block_sum_f(rr, sh);
     const double rzd = block_sum_f(rz, sh);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {   // the direction kernel takes the stopping test from these
         part[(size_t)(0 * Q + q) * nch + ch] = rrd;
         part[(size_t)(1 * Q + q) * nch + ch] = rzd;
     }
-    if (!last_block_arrive(counter, gridDim.x * gridDim.y)) return;
-    reduce_parts(part, 2, Q, nch, red);
-    cg_stop_test(ctl, red, red + COFEM_QMAX);
 }
 
 // ---------------------------------------------------------------------------
-// Direction update (Alg. 2, PCG reading: W = M^-1 R, P = W + P H) for the active
-// columns, plus p^T diag(alpha) p for the next pi, and the CG loop condition.
+// Stopping test and direction update (Alg. 2, PCG reading: W = M^-1 R,
+// P = W + P H) for the active columns, plus the partials of p^T diag(alpha) p
+// for the next pi, and the CG loop condition.  Every block sums the update's
+// (or the residual replacement's) partials of its column itself, in block
+// order, so all blocks of a column take the same decision without a grid-wide
+// hand-off; block 0 of each column records it.  Per column:
+// ||r_q||^2 <= tol^2 ||b_q||^2 ends column q (per-column test), or
+// sum_q ||r_q||^2 <= tol^2 sum_q ||b_q||^2 ends all of them (Frobenius test);
+// otherwise eta_q = rho_new / rho_old.
 // ---------------------------------------------------------------------------
 __global__ __launch_bounds__(NT) void k_cg_direction(DevCtl* ctl, const float* __restrict__ R,
                                                      const float* __restrict__ alpha,
                                                      const float* __restrict__ minv, float* __restrict__ P,
-                                                     long long Dp, int nch, double* part, unsigned* counter,
+                                                     long long Dp, int nch, double* part,
                                                      cudaGraphConditionalHandle h_cg, SplitOut so) {
     __shared__ double sh[NT / 32];
-    __shared__ double red[COFEM_QMAX];
+    __shared__ double s_rr[COFEM_QMAX];
+    __shared__ int s_act;
+    __shared__ float s_eta;
     griddep_launch();
-    griddep_wait();   // R and eta come from the previous kernel
+    griddep_wait();   // R and the partials come from the previous kernel
     const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q;
+    const int u = ctl->u;
+    // a column that left the loop stays out; block 0 of this column may already
+    // have recorded this iteration's decision, which gives the same result
+    const int prev = ctl->active[q];
+    const double t2 = ctl->tol * ctl->tol;
+    const bool frob = ctl->conv == COFEM_CONV_FROBENIUS;
+    double rr = 0.0, rz = 0.0;
+    if (frob) {
+        if (threadIdx.x < Q) s_rr[threadIdx.x] = sum_parts(part + (size_t)threadIdx.x * nch, nch);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int act = 0;
+        float eta = 0.0f;
+        if (prev) {
+            rr = frob ? s_rr[q] : sum_parts(part + (size_t)q * nch, nch);
+            rz = sum_parts(part + (size_t)(Q + q) * nch, nch);
+            bool stop;
+            if (frob) {
+                double num = 0.0, den = 0.0;
+                for (int k = 0; k < Q; ++k) {
+                    if (ctl->active[k]) num += s_rr[k];
+                    den += ctl->bnorm2[k];
+                }
+                stop = num <= t2 * den;
+            } else {
+                stop = rr <= t2 * ctl->bnorm2[q];
+            }
+            act = !stop;
+            if (act) eta = (float)(rz / ctl->rho[(u - 1) & 1][q]);
+        }
+        s_act = act;
+        s_eta = eta;
+        if (ch == 0 && prev) {
+            ctl->rnorm2[q] = rr;
+            ctl->active[q] = act;
+            if (act) {
+                ctl->eta[q] = rz / ctl->rho[(u - 1) & 1][q];
+                ctl->rho[u & 1][q] = rz;
+                ctl->any_active = 1;
+                if (u < ctl->maxit) set_cond(h_cg, 1);
+                else atomicOr(&ctl->flags, COFEM_FLAG_CG_NOT_CONVERGED);
+            }
+        }
+    }
+    __syncthreads();
+    const int act = s_act;
+    const size_t off = (size_t)q * Dp;
     float ap = 0.0f;
-    if (ctl->active[q]) {
-        const float eta = (float)ctl->eta[q];
-        const size_t off = (size_t)q * Dp;
+    if (act) {
+        const float eta = s_eta;
         float4 rv[IT], mv[IT], av[IT], pv[IT];   // loads first (see k_cg_update)
 #pragma unroll
         for (int it = 0; it < IT; ++it) {
@@ -339,26 +368,7 @@ __global__ __launch_bounds__(NT) void k_cg_direction(DevCtl* ctl, const float* _
         }
     }
     const double apd = block_sum_f(ap, sh);
-    if (threadIdx.x == 0) part[(size_t)(2 * Q + q) * nch + ch] = apd;
-    if (!last_block_arrive(counter, gridDim.x * gridDim.y)) return;
-    // reduce only the k = 2 slab
-    {
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        for (int qq = w; qq < Q; qq += nw) {
-            const double* src = part + (size_t)(2 * Q + qq) * nch;
-            double v = 0.0;
-            for (int i = lane; i < nch; i += 32) v += __ldcg(src + i);
-            v = warp_sum(v);
-            if (lane == 0) red[qq] = v;
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x < Q && ctl->active[threadIdx.x]) ctl->ap[threadIdx.x] = red[threadIdx.x];
-    if (threadIdx.x == 0) {
-        const int cont = ctl->any_active && ctl->u < ctl->maxit;
-        if (ctl->any_active && !cont) ctl->flags |= COFEM_FLAG_CG_NOT_CONVERGED;
-        set_cond(h_cg, cont);
-    }
+    if (threadIdx.x == 0) part[(size_t)(2 * Q + q) * nch + ch] = apd;   // reduced by the operator's finish
 }
 
 // ---------------------------------------------------------------------------
@@ -468,19 +478,20 @@ void launch_cg_init(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_c
              c->nch, c->part, c->counters + 0, h_cg, tc_direction_split(c));
 }
 
-void launch_cg_update(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_rr) {
+void launch_cg_update(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_rr,
+                      cudaGraphConditionalHandle h_cg) {
     s.launch_pdl(k_cg_update, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->P, op_output(c), c->alpha, c->minv, c->X, c->R,
-             c->Dp, c->nch, c->part, c->counters + 1, h_rr);
+                 c->Dp, c->nch, c->part, h_rr, h_cg);
 }
 
 void launch_rr_residual(Sink& s, cofem_ctx* c, int Q) {
     s.launch(k_rr_residual, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->b, c->X, op_output(c), c->alpha, c->minv, c->R,
-             c->D, c->Dp, c->nch, c->part, c->counters + 2);
+             c->D, c->Dp, c->nch, c->part);
 }
 
 void launch_cg_direction(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg) {
     s.launch_pdl(k_cg_direction, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->R, c->alpha, c->minv, c->P, c->Dp, c->nch,
-             c->part, c->counters + 3, h_cg, tc_direction_split(c));
+                 c->part, h_cg, tc_direction_split(c));
 }
 
 void launch_mstep(Sink& s, cofem_ctx* c, int /*Q*/, cudaGraphConditionalHandle h_em) {
