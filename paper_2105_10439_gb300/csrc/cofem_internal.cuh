@@ -40,6 +40,8 @@ struct DevCtl {
     double tt[COFEM_QMAX];      // ||Phi p||^2
     const double* ap_part;      // per-block partials of p^T diag(alpha) p: [q][ap_n]
     int ap_n;
+    const double* tt_part;      // the CG operator's partials of ||Phi p||^2: [q][tt_n]
+    int tt_n;
 };
 
 // Modes of the operator kernels.
@@ -596,15 +598,23 @@ inline void launch_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mo
     else launch_toeplitz_operator(s, c, Q, V, mode);
 }
 
-// Finish an operator application (run by the last block of an operator kernel):
-// reduce the ||Phi p_q||^2 partials (layout [q][nparts]) into ctl->tt and, in
-// OP_CG mode, form pi_q = p^T A p = beta ||Phi p_q||^2 + p^T diag(alpha) p and
-// gamma_q = rho_q / pi_q (Alg. 2, "pi" and "gamma").  Writing pi through Phi p
-// instead of sum_j P_jq Psi_jq is the same number in exact arithmetic and is a
-// sum of non-negative terms.  A column with pi <= 0 or non-finite is frozen
-// and flagged (CG breakdown).
-__device__ __forceinline__ void op_finalize_block(DevCtl* ctl, const double* tt_part, int nparts,
-                                                   int Q, int mode) {
+// End of an operator application that left per-block partials of
+// ||Phi p_q||^2 (layout [q][nparts]).  Outside the CG loop one block (the
+// last to arrive) reduces them into ctl->tt (op_finalize_block).  In the CG
+// loop (OP_CG) nothing is reduced here: the update kernel's blocks form
+// pi_q = p^T A p = beta ||Phi p_q||^2 + p^T diag(alpha) p and
+// gamma_q = rho_q / pi_q (Alg. 2, "pi" and "gamma") from the partials
+// themselves; one thread of the operator records where the partials are and
+// counts the CG iteration (op_cg_begin).  Writing pi through Phi p instead of
+// sum_j P_jq Psi_jq is the same number in exact arithmetic and is a sum of
+// non-negative terms.
+__device__ __forceinline__ void op_cg_begin(DevCtl* ctl, const double* tt_part, int nparts) {
+    ctl->tt_part = tt_part;
+    ctl->tt_n = nparts;
+    ctl->u += 1;
+}
+
+__device__ __forceinline__ void op_finalize_block(DevCtl* ctl, const double* tt_part, int nparts, int Q) {
     __shared__ double s_tt[COFEM_QMAX];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int q = w; q < Q; q += nw) {
@@ -614,32 +624,7 @@ __device__ __forceinline__ void op_finalize_block(DevCtl* ctl, const double* tt_
         if (lane == 0) s_tt[q] = v;
     }
     __syncthreads();
-    // one column per thread (the block has at least COFEM_QMAX threads)
-    const int q = threadIdx.x;
-    int act = 0;
-    if (q < Q) {
-        ctl->tt[q] = s_tt[q];
-        if (mode == OP_CG && ctl->active[q]) {
-            // p^T diag(alpha) p from the direction (or initialisation) kernel's
-            // per-block partials, in block order
-            const double* src = ctl->ap_part + (size_t)q * ctl->ap_n;
-            double ap = 0.0;
-            for (int i = 0; i < ctl->ap_n; ++i) ap += __ldcg(src + i);
-            ctl->ap[q] = ap;
-            const double pi = ctl->beta * s_tt[q] + ap;
-            ctl->pi[q] = pi;
-            if (!(pi > 0.0) || !isfinite(pi)) {
-                atomicOr(&ctl->flags, COFEM_FLAG_BREAKDOWN);
-                ctl->active[q] = 0;
-                ctl->gamma[q] = 0.0;
-            } else {
-                ctl->gamma[q] = ctl->rho[ctl->u & 1][q] / pi;
-            }
-        }
-        act = ctl->active[q];
-    }
-    act = __syncthreads_or(act);
-    if (threadIdx.x == 0 && mode == OP_CG) ctl->any_active = act;
+    if (threadIdx.x < Q) ctl->tt[threadIdx.x] = s_tt[threadIdx.x];
 }
 
 void tc_operator_info(cofem_ctx* c, int* path, int* k_cg, int* k_rr);

@@ -96,8 +96,12 @@ __global__ __launch_bounds__(256) void k_gemm1_simt(const TPhi* __restrict__ phi
         }
         tt_part[(size_t)tid * nrb + rb] = a;
     }
+    if (mode == OP_CG) {   // the update kernel reduces the partials (op_cg_begin)
+        if (rb == 0 && tid == 0) op_cg_begin(ctl, tt_part, nrb);
+        return;
+    }
     if (!last_block_arrive(cnt_all, (unsigned)nrb)) return;
-    op_finalize_block(ctl, tt_part, nrb, Q, mode);
+    op_finalize_block(ctl, tt_part, nrb, Q);
 }
 
 template <int QG, typename TPhi>

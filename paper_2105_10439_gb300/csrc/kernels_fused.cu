@@ -529,7 +529,11 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_operator_fused(FusedParams p)
             p.sync[1] = 0;
             p.sync[2] = 0;
         }
-        op_finalize_block(p.ctl, p.tt_part, n, p.Q, p.mode);
+        if (p.mode == OP_CG) {   // the update kernel reduces the partials
+            if (threadIdx.x == 0) op_cg_begin(p.ctl, p.tt_part, n);
+        } else {
+            op_finalize_block(p.ctl, p.tt_part, n, p.Q);
+        }
     }
 }
 

@@ -702,8 +702,12 @@ __global__ __launch_bounds__(256) void k_tc_reduce_T(const float* __restrict__ p
     }
     const double ttd = block_sum_f(tt, sh);
     if (threadIdx.x == 0) tt_part[(size_t)q * nblk + blockIdx.x] = ttd;
+    if (mode == OP_CG) {   // the update kernel reduces the partials (op_cg_begin)
+        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) op_cg_begin(ctl, tt_part, nblk);
+        return;
+    }
     if (!last_block_arrive(counter, gridDim.x * gridDim.y)) return;
-    op_finalize_block(ctl, tt_part, nblk, Q, mode);
+    op_finalize_block(ctl, tt_part, nblk, Q);
 }
 
 // GEMM2 epilogue for a stand-alone application: U (Q x Dp) = sum of the

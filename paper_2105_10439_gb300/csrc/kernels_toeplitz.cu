@@ -91,8 +91,12 @@ __global__ __launch_bounds__(TZ_THREADS) void k_toeplitz(const float* __restrict
     }
     const double ttd = block_sum_f(tt, red);
     if (th == 0) tt_part[(size_t)q * nblk + blk] = ttd;
+    if (mode == OP_CG) {   // the update kernel reduces the partials (op_cg_begin)
+        if (blk == 0 && q == 0 && th == 0) op_cg_begin(ctl, tt_part, nblk);
+        return;
+    }
     if (!last_block_arrive(counter, gridDim.x * gridDim.y)) return;
-    op_finalize_block(ctl, tt_part, nblk, Q, mode);
+    op_finalize_block(ctl, tt_part, nblk, Q);
 }
 
 __global__ void k_toeplitz_theta(const float* __restrict__ h, int L, long long N, long long Dp,

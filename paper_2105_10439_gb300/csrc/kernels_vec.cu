@@ -151,28 +151,55 @@ __global__ __launch_bounds__(NT, 2) void k_cg_update(DevCtl* ctl, const float* _
                                                   double* part, cudaGraphConditionalHandle h_rr,
                                                   cudaGraphConditionalHandle h_cg) {
     __shared__ double sh[NT / 32];
+    __shared__ int s_act;
+    __shared__ float s_gamma;
     griddep_launch();
-    griddep_wait();   // gamma and the operator output come from the previous kernels
+    griddep_wait();   // the operator's output and partials come from the previous kernels
     const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q;
+    const int u = ctl->u;   // this CG iteration (counted by the operator)
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-        // iteration bookkeeping; the stopping test and the loop condition are
-        // the direction kernel's (it reads this kernel's partials)
-        const int u = ctl->u + 1;
-        ctl->u = u;
+        // the stopping test and the loop condition are the direction kernel's
+        // (it reads this kernel's partials)
         ctl->any_active = 0;
         set_cond(h_rr, ctl->rr_period > 0 && u % ctl->rr_period == 0);
         set_cond(h_cg, 0);
     }
-    float rr = 0.0f, rz = 0.0f;
+    if (threadIdx.x == 0) {
+        // pi_q = beta ||Phi p_q||^2 + p^T diag(alpha) p and gamma_q = rho_q / pi_q
+        // (Alg. 2) from the operator's and the direction kernel's partials, in
+        // block order: every block of the column gets the same value; block 0
+        // records it.  pi_q <= 0 or non-finite freezes the column (breakdown).
+        int act = ctl->active[q];
+        float gamma = 0.0f;
+        if (act) {
+            const double tt = sum_parts(ctl->tt_part + (size_t)q * ctl->tt_n, ctl->tt_n);
+            const double ap = sum_parts(ctl->ap_part + (size_t)q * ctl->ap_n, ctl->ap_n);
+            const double pi = ctl->beta * tt + ap;
+            const bool ok = pi > 0.0 && isfinite(pi);
+            const double g = ok ? ctl->rho[(u - 1) & 1][q] / pi : 0.0;
+            act = ok;
+            gamma = (float)g;
+            if (ch == 0) {
+                ctl->tt[q] = tt;
+                ctl->ap[q] = ap;
+                ctl->pi[q] = pi;
+                ctl->gamma[q] = g;
+                if (!ok) {
+                    atomicOr(&ctl->flags, COFEM_FLAG_BREAKDOWN);
+                    ctl->active[q] = 0;
+                }
+            }
+        }
+        s_act = act;
+        s_gamma = gamma;
+    }
+    // all loads of the thread's IT float4 positions first (the kernel is bound
+    // by memory round trips, not bandwidth), issued while thread 0 forms gamma;
+    // then the partial sums of the operator, then the arithmetic in element order
+    const size_t off = (size_t)q * Dp;
+    float4 pv[IT], av[IT], mv[IT], xv[IT], rv[IT], uv[IT];
+    int s0[IT], ns[IT];
     if (ctl->active[q]) {
-        const float gamma = (float)ctl->gamma[q];
-        const float beta = (float)ctl->beta;
-        const size_t off = (size_t)q * Dp;
-        // all loads of the thread's IT float4 positions first (the kernel is
-        // bound by memory round trips, not bandwidth), then the partial sums
-        // of the operator, then the arithmetic in element order
-        float4 pv[IT], av[IT], mv[IT], xv[IT], rv[IT], uv[IT];
-        int s0[IT], ns[IT];
 #pragma unroll
         for (int it = 0; it < IT; ++it) {
             const long long j = (long long)ch * CH + (long long)(threadIdx.x + it * NT) * 4;
@@ -185,6 +212,12 @@ __global__ __launch_bounds__(NT, 2) void k_cg_update(DevCtl* ctl, const float* _
                 op_range(uo, j, s0[it], ns[it]);
             }
         }
+    }
+    __syncthreads();
+    float rr = 0.0f, rz = 0.0f;
+    if (s_act) {   // (implies the loads above were issued)
+        const float gamma = s_gamma;
+        const float beta = (float)ctl->beta;
 #pragma unroll
         for (int it = 0; it < IT; ++it) {   // X needs no operator output: store it now
             const long long j = (long long)ch * CH + (long long)(threadIdx.x + it * NT) * 4;
