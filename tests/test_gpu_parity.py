@@ -422,6 +422,23 @@ def test_fit_edge_cases(cf):
     assert np.all(g["mu"] == 0.0)
 
 
+def test_fit_breakdown_flagged_and_column_frozen(cf):
+    """A column whose p^T A p is not a positive finite number is flagged and
+    frozen, and the fit goes on: with Phi = 0 and alpha0 = 0 the Jacobi
+    preconditioner M = beta theta + alpha is zero, so the probe columns start
+    with an infinite direction and pi = NaN; mu stays 0 (b = 0), the M-step
+    then clamps alpha at alpha_max and the next E-step is regular."""
+    import dataclasses
+    p = dense_gaussian(50, 130, 5, 20.0, seed=3)
+    z = dataclasses.replace(p, phi=np.zeros_like(p.phi))
+    g = gpu_fit(cf, z, 3, 3, 1e-6, 200, alpha0=np.zeros(130, np.float32))
+    assert g["flags"] & cf.COFEM_FLAG_BREAKDOWN
+    for k in ("mu", "s", "alpha"):
+        assert np.all(np.isfinite(g[k])), k
+    assert np.all(g["mu"] == 0.0)
+    np.testing.assert_allclose(g["alpha"], 1e12, rtol=1e-5)
+
+
 def test_fit_rejects_nonfinite_and_bad_args(cf):
     p = dense_gaussian(20, 40, 2, 20.0, seed=1)
     with cf.CoFEM(20, 40, cf.COFEM_OP_DENSE, p.phi) as m:
