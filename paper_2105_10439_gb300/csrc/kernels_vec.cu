@@ -1,12 +1,14 @@
 // Vector kernels of the CoFEM hot path: PCG initialisation, the fused CG
-// update with the per-column stopping test, residual replacement, the
-// direction update, and the fused diagonal-estimate + M-step.
+// update (with pi and gamma), residual replacement, the per-column stopping
+// test with the direction update, and the fused diagonal-estimate + M-step.
 //
 // Layout: each of X, R, P is Q columns of Dp floats ("column q" of Alg. 2 is
 // the contiguous run [q*Dp, q*Dp + D)); padding entries are kept at zero.
 // Vector kernels run on a (chunk, q) grid: block (ch, q) owns elements
-// [ch*1024, ch*1024 + 1024) of column q, so the per-column reductions of Alg. 2
-// are one partial per block, reduced by the last block (fixed order).
+// [ch*CH, ch*CH + CH) of column q, so the per-column reductions of Alg. 2 are
+// one partial per block, summed in block order either by the last block to
+// arrive (initialisation, M-step) or, inside the CG loop, by every block of
+// the next kernel for its own column.
 #include "cofem_internal.cuh"
 
 namespace {
