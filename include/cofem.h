@@ -79,6 +79,17 @@ typedef int cofem_status;
 #define COFEM_CONV_PER_COLUMN 0  /* column q stops (and is frozen) once ||r_q|| <= tol ||b_q|| */
 #define COFEM_CONV_FROBENIUS  1  /* all columns stop once ||R||_F <= tol ||B||_F (as printed in Alg. 2) */
 
+/* Prior of the weights z_j (selects the M-step).  GAUSSIAN: N(0, 1/alpha_j),
+ * alpha_j = 1 / (mu_j^2 + s_j) (Alg. 1).  RECTIFIED: the rectified Gaussian
+ * prior of the non-negativity subsection of Sec. III; alpha_j = 1 / E[z_j^2]
+ * with E[z_j^2] the second moment of N(mu_j, s_j) restricted to z_j >= 0,
+ * mu_j^2 + s_j + mu_j sqrt(2 s_j / pi) / erfcx(-mu_j / sqrt(2 s_j)) (the
+ * printed formula with its third term's factor 2 restored; no term where
+ * s_j <= 0), evaluated in FP64.  Both floor the moment at 1/alpha_max.  mu is
+ * the Gaussian posterior mean in both cases. */
+#define COFEM_PRIOR_GAUSSIAN  0
+#define COFEM_PRIOR_RECTIFIED 1
+
 /* Fit flags (bit set in *flags). */
 #define COFEM_FLAG_CG_NOT_CONVERGED 1u /* some EM iteration hit cg_maxit with a column still active */
 #define COFEM_FLAG_ALPHA_CLAMPED    2u /* some mu_j^2 + s_j fell below 1/alpha_max and was clamped */
@@ -108,6 +119,7 @@ typedef struct cofem_opts {
                                  GEMMs prefetch dictionary tiles, while its predecessor
                                  finishes; data dependences still wait for completion);
                                  0: plain stream order */
+    int prior;                /* COFEM_PRIOR_GAUSSIAN (default) | COFEM_PRIOR_RECTIFIED */
 } cofem_opts;
 
 /* Dense BF16 operator forms.  TWO_PASS streams the dictionary for Phi V and a
@@ -126,7 +138,7 @@ typedef struct cofem_opts {
 
 /* Fill *o with the defaults: F32, Jacobi, per-column, rr_period 0,
  * alpha_max 1e12, seed 2, stream NULL, use_graph 1, dense_path AUTO, max_sms 0,
- * overlap_launch 1. */
+ * overlap_launch 1, prior GAUSSIAN. */
 void cofem_default_opts(cofem_opts* o);
 
 /* Create a handle for one dictionary (step a0: upload, optional BF16

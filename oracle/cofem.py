@@ -39,10 +39,21 @@ garbled or at odds with itself):
     count u is a multiple of rr_period, right after the X, R update the still
     active columns take R <- B - A X before the stopping test, then W, rho and
     P continue from that R.
+12. Non-negativity (prior="rectified", the rectified Gaussian prior of the
+    non-negativity subsection): the M-step takes alpha_j = 1 / E[z_j^2] with
+    E[z_j^2] the second moment of N(mu_j, Sigma_jj) truncated to z_j >= 0,
+    mu_j^2 + Sigma_jj + mu_j sqrt(2 Sigma_jj / pi) exp(-xi_j^2) / erfc(-xi_j),
+    xi_j = mu_j / sqrt(2 Sigma_jj).  The printed third term has sqrt(Sigma_jj /
+    pi); with the printed xi that is not the truncated moment the text
+    describes, so the factor 2 is restored.  Sigma_jj is replaced by s_j (as
+    the paper says); where s_j <= 0 the term is undefined and dropped, and the
+    floor 1/alpha_max applies as in reading 10.  exp(-xi^2) / erfc(-xi) is
+    evaluated as 1 / erfcx(-xi), the same function without overflow.
 """
 from __future__ import annotations
 
 import numpy as np
+from scipy import special
 
 from .operators import apply_A
 from .philox import rademacher_probes
@@ -50,6 +61,22 @@ from .philox import rademacher_probes
 FLAG_CG_NOT_CONVERGED = 1
 FLAG_ALPHA_CLAMPED = 2
 FLAG_BREAKDOWN = 4
+
+
+def second_moment(mu, s, prior="gaussian"):
+    """E[z_j^2] of the M-step (Eq. mstep; reading 12 for prior="rectified")."""
+    mu = np.asarray(mu, dtype=np.float64)
+    s = np.asarray(s, dtype=np.float64)
+    m2 = mu ** 2 + s
+    if prior == "gaussian":
+        return m2
+    if prior != "rectified":
+        raise ValueError(prior)
+    pos = s > 0
+    sp = np.where(pos, s, 1.0)
+    xi = mu / np.sqrt(2.0 * sp)
+    corr = mu * np.sqrt(2.0 * sp / np.pi) / special.erfcx(-xi)
+    return m2 + np.where(pos, corr, 0.0)
 
 
 def diag_estimate(P, X):
@@ -124,13 +151,14 @@ def pcg(apply_a, B, minv, tol, maxit, conv="per_column", rr_period=0, history=No
 
 def cofem(op, y, beta, K, T, cg_tol, cg_maxit, seed, alpha0=None, precond="jacobi",
           alpha_max=1e12, conv="per_column", rr_period=0, probe_fn=None,
-          solver="pcg", return_x=False):
+          solver="pcg", return_x=False, prior="gaussian"):
     """Alg. 1 (CovarianceFreeEM) with Alg. 2 as the linear solver.
 
     op        oracle.operators.DenseOperator / ToeplitzOperator
     probe_fn  optional callable (t, K, D) -> (K, D) probe block; default is the
               Philox Rademacher rule with `seed`.
     solver    "pcg" (Alg. 2) or "direct" (exact dense solve, small D only).
+    prior     "gaussian" (Eq. mstep) or "rectified" (non-negativity, reading 12).
     Returns dict(alpha, mu, s, cg_iters, flags[, X]).
     """
     D = op.D
@@ -165,7 +193,7 @@ def cofem(op, y, beta, K, T, cg_tol, cg_maxit, seed, alpha0=None, precond="jacob
         mu = X[:, 0].copy()
         s = diag_estimate(B[:, 1:], X[:, 1:])
         if t < T:
-            m2 = mu ** 2 + s
+            m2 = second_moment(mu, s, prior)
             if np.any(m2 < 1.0 / alpha_max):
                 flags |= FLAG_ALPHA_CLAMPED
             alpha = 1.0 / np.maximum(m2, 1.0 / alpha_max)

@@ -38,6 +38,8 @@ COFEM_CONV_FROBENIUS = 1
 COFEM_PATH_AUTO = 0
 COFEM_PATH_TWO_PASS = 1
 COFEM_PATH_SINGLE_PASS = 2
+COFEM_PRIOR_GAUSSIAN = 0
+COFEM_PRIOR_RECTIFIED = 1
 COFEM_FLAG_CG_NOT_CONVERGED = 1
 COFEM_FLAG_ALPHA_CLAMPED = 2
 COFEM_FLAG_BREAKDOWN = 4
@@ -56,6 +58,7 @@ class cofem_opts(C.Structure):
         ("dense_path", C.c_int),
         ("max_sms", C.c_int),
         ("overlap_launch", C.c_int),
+        ("prior", C.c_int),
     ]
 
 

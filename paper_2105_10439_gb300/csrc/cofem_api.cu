@@ -364,6 +364,8 @@ cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, c
         return fail(COFEM_ERR_INVALID_ARG, "bad conv");
     if (o.rr_period < 0) return fail(COFEM_ERR_INVALID_ARG, "rr_period < 0");
     if (o.overlap_launch != 0 && o.overlap_launch != 1) return fail(COFEM_ERR_INVALID_ARG, "overlap_launch must be 0 or 1");
+    if (o.prior != COFEM_PRIOR_GAUSSIAN && o.prior != COFEM_PRIOR_RECTIFIED)
+        return fail(COFEM_ERR_INVALID_ARG, "prior must be COFEM_PRIOR_GAUSSIAN or COFEM_PRIOR_RECTIFIED");
     if (!(o.alpha_max > 0.0) || !std::isfinite(o.alpha_max)) return fail(COFEM_ERR_INVALID_ARG, "bad alpha_max");
 
     int dev = 0, sms = 0;
@@ -533,6 +535,7 @@ cofem_status cofem_fit(cofem_ctx* c, const float* y, double beta, const float* a
     hc->maxit = cg_maxit;
     hc->conv = c->opts.conv;
     hc->rr_period = c->opts.rr_period;
+    hc->prior = c->opts.prior;
     hc->ap_part = c->part + (size_t)2 * Q * c->nch;   // slab 2 of the CG partials
     hc->ap_n = c->nch;
     CK(cudaMemcpyAsync(c->ctl, hc, sizeof(DevCtl), cudaMemcpyHostToDevice, c->stream));

@@ -24,7 +24,7 @@
 struct DevCtl {
     double beta, tol, alpha_max;
     unsigned long long seed;
-    int T, K, Q, maxit, conv, rr_period;
+    int T, K, Q, maxit, conv, rr_period, prior;
     int t;            // current EM iteration, 1-based
     int u;            // CG iterations done in EM iteration t
     int any_active;   // some column still iterating

@@ -408,8 +408,10 @@ __global__ __launch_bounds__(NT) void k_cg_direction(DevCtl* ctl, const float* _
 
 // ---------------------------------------------------------------------------
 // Fused diagonal estimate + M-step (Alg. 1: s_j = (1/K) sum_k p_kj x_kj; if t < T,
-// alpha_j = 1 / max(mu_j^2 + s_j, 1/alpha_max); then M^-1 for the next E-step),
-// probes regenerated from Philox, plus EM loop bookkeeping.
+// alpha_j = 1 / max(E[z_j^2], 1/alpha_max) with E[z_j^2] = mu_j^2 + s_j, or under
+// the rectified Gaussian prior the second moment of N(mu_j, s_j) restricted to
+// z_j >= 0 (non-negativity subsection of Sec. III); then M^-1 for the next
+// E-step), probes regenerated from Philox, plus EM loop bookkeeping.
 // ---------------------------------------------------------------------------
 __global__ __launch_bounds__(NT) void k_mstep(DevCtl* ctl, const float* __restrict__ X,
                                               const float* __restrict__ theta, float* __restrict__ alpha,
@@ -433,7 +435,16 @@ __global__ __launch_bounds__(NT) void k_mstep(DevCtl* ctl, const float* __restri
         mu_out[j] = mu;
         s_out[j] = s;
         if (t < T && j < D) {
-            const float m2 = fmaf(mu, mu, s);
+            float m2 = fmaf(mu, mu, s);
+            if (ctl->prior == COFEM_PRIOR_RECTIFIED && s > 0.0f) {
+                // mu^2 + s + mu sqrt(2 s / pi) exp(-xi^2) / erfc(-xi), xi = mu / sqrt(2 s);
+                // exp(-xi^2) / erfc(-xi) = 1 / erfcx(-xi).  FP64: for mu << -sqrt(s)
+                // the moment is a small difference of large terms.
+                const double md = mu, sd = s;
+                const double xi = md / sqrt(2.0 * sd);
+                const double pi_ = 3.14159265358979323846;
+                m2 = (float)(md * md + sd + md * sqrt(2.0 * sd / pi_) / erfcx(-xi));
+            }
             const float floor_ = (float)(1.0 / ctl->alpha_max);
             clamped = m2 < floor_;
             const float a = 1.0f / (m2 > floor_ ? m2 : floor_);

@@ -352,6 +352,26 @@ def test_fit_toeplitz_small(cf):
     assert_fit_close(g, r)
 
 
+@pytest.mark.parametrize("kind", ["dense", "toeplitz"])
+def test_fit_rectified_prior_matches_oracle(cf, kind):
+    """Rectified Gaussian prior (non-negativity subsection): the M-step takes
+    the truncated second moment (FP64, erfcx) on the GPU; the fit matches the
+    oracle's.  The convolution case is the paper's calcium setting (non-negative
+    spikes), compared at a fixed CG iteration count as in the test above."""
+    if kind == "dense":
+        p = dense_gaussian(200, 501, 10, 15.0, seed=5)
+        args = (12, 8, 1e-5, 400)
+    else:
+        p = toeplitz_calcium(6000, 256, 0.01, 15.0, seed=2)
+        args = (8, 3, 1e-14, 25)
+    g = gpu_fit(cf, p, *args, prior=cf.COFEM_PRIOR_RECTIFIED)
+    r = oracle_fit(p, *args, prior="rectified")
+    assert_fit_close(g, r)
+    # the prior changed the M-step: alpha differs from the Gaussian prior's
+    ga = gpu_fit(cf, p, *args)
+    assert not np.array_equal(ga["alpha"], g["alpha"])
+
+
 @pytest.mark.parametrize("path", ["two_pass", "single_pass"])
 def test_fit_bf16_matches_oracle_on_quantised_dictionary(cf, path):
     p = dense_gaussian(250, 500, 10, 15.0, seed=12)

@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 from oracle import cofem as cofem_mod
-from oracle.cofem import cofem, FLAG_ALPHA_CLAMPED
+from oracle.cofem import cofem, second_moment, FLAG_ALPHA_CLAMPED
 from oracle.em import em, estep_explicit
 from oracle.operators import DenseOperator, ToeplitzOperator
 from oracle.philox import rademacher_probes
@@ -140,3 +140,56 @@ def test_last_iteration_skips_mstep():
     a0 = np.linspace(1, 2, 40)
     r = cofem(DenseOperator(p.phi), p.y, p.beta, 4, 1, 1e-8, 100, seed=1, alpha0=a0)
     np.testing.assert_array_equal(r["alpha"], a0)
+
+
+@pytest.mark.parametrize("mu", [-4.0, -1.0, -0.2, 0.0, 0.5, 2.0, 6.0])
+@pytest.mark.parametrize("s", [0.01, 0.3, 1.0, 4.0])
+def test_rectified_second_moment_is_the_truncated_normal_moment(mu, s):
+    """Non-negativity subsection: the M-step's E[z_j^2] is the second moment
+    of N(mu, Sigma) restricted to z >= 0 (reading 12), checked against
+    quadrature of that density (no error function involved)."""
+    from scipy import integrate
+    sd = np.sqrt(s)
+    if mu >= 0.0:   # unnormalised density, peak 1 at z = mu
+        pdf = lambda z: np.exp(-0.5 * ((z - mu) / sd) ** 2)   # noqa: E731
+        hi = mu + 40.0 * sd
+    else:           # the same times exp(mu^2 / 2s): peak 1 at z = 0
+        pdf = lambda z: np.exp(-z * z / (2.0 * s) + z * mu / s)   # noqa: E731
+        hi = 40.0 * min(sd, s / -mu)
+    lo = 0.0
+    mass = integrate.quad(pdf, lo, hi, epsabs=0.0, epsrel=1e-13, limit=200)[0]
+    m2 = integrate.quad(lambda z: z * z * pdf(z), lo, hi, epsabs=0.0, epsrel=1e-13, limit=200)[0] / mass
+    got = second_moment(mu, s, "rectified")
+    np.testing.assert_allclose(got, m2, rtol=1e-8)
+
+
+def test_rectified_second_moment_special_cases():
+    """mu = 0: the half-normal moment, Sigma; s <= 0: no truncation term
+    (reading 12); the sign of mu orders it against the Gaussian prior's
+    mu^2 + s (the inverse Mills ratio is positive)."""
+    s = np.array([0.5, 2.0, 1e-3])
+    np.testing.assert_array_equal(second_moment(np.zeros(3), s, "rectified"), s)
+    mu = np.array([1.5, -2.0, 0.3])
+    neg = np.array([-0.1, 0.0, -1e-9])
+    np.testing.assert_array_equal(second_moment(mu, neg, "rectified"), mu ** 2 + neg)
+    g = second_moment(mu, np.full(3, 0.7), "gaussian")
+    r = second_moment(mu, np.full(3, 0.7), "rectified")
+    assert np.all((r > g) == (mu > 0)) and np.all(r > 0)
+
+
+def test_rectified_prior_enters_the_m_step():
+    """With T = 2 the returned alpha is the M-step of E-step 1, whose mu and s
+    do not depend on the prior: under the rectified prior the components with
+    a negative posterior mean (and s > 0) get a larger alpha than under the
+    Gaussian prior, those with a positive mean a smaller one, and alpha is the
+    reciprocal of the truncated moment of E-step 1's (mu, s)."""
+    p = toeplitz_calcium(1024, 32, 0.02, 20.0, seed=4)
+    op = ToeplitzOperator(p.phi, p.N)
+    e1 = cofem(op, p.y, p.beta, 16, 1, 1e-9, 2000, seed=2)
+    g = cofem(op, p.y, p.beta, 16, 2, 1e-9, 2000, seed=2)
+    r = cofem(op, p.y, p.beta, 16, 2, 1e-9, 2000, seed=2, prior="rectified")
+    mu, sv = e1["mu"], e1["s"]
+    m2 = second_moment(mu, sv, "rectified")
+    np.testing.assert_allclose(r["alpha"], 1.0 / np.maximum(m2, 1e-12), rtol=1e-12)
+    sel = (sv > 0) & (np.abs(mu) > 1e-6)
+    assert np.all((r["alpha"][sel] > g["alpha"][sel]) == (mu[sel] < 0))
