@@ -238,6 +238,7 @@ typedef struct cofem_request {
     float* alpha;
     int* cg_iters;            /* T_em ints or NULL */
     int max_sms;              /* as cofem_opts (0 = all SMs) */
+    int prior;                /* as cofem_opts (COFEM_PRIOR_*) */
 } cofem_request;              /* every pointer must stay valid until the ticket completes */
 
 typedef struct cofem_result {

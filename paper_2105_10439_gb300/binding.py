@@ -70,7 +70,7 @@ class cofem_request(C.Structure):
         ("precision", C.c_int), ("precond", C.c_int), ("conv", C.c_int), ("rr_period", C.c_int),
         ("alpha_max", C.c_double), ("seed", C.c_ulonglong),
         ("mu", C.c_void_p), ("s", C.c_void_p), ("alpha", C.c_void_p), ("cg_iters", C.c_void_p),
-        ("max_sms", C.c_int),
+        ("max_sms", C.c_int), ("prior", C.c_int),
     ]
 
 
@@ -229,7 +229,8 @@ def make_request(kind, N, D, phi, y, beta, K, T_em, cg_tol, cg_maxit, mu, s, alp
                          alpha0=_ptr(alpha0, allow_none=True), K=K, T_em=T_em, cg_tol=float(cg_tol),
                          cg_maxit=cg_maxit, precision=o.precision, precond=o.precond, conv=o.conv,
                          rr_period=o.rr_period, alpha_max=o.alpha_max, seed=o.seed, mu=_ptr(mu), s=_ptr(s),
-                         alpha=_ptr(alpha), cg_iters=_ptr(cg_iters, np.int32, allow_none=True), max_sms=max_sms)
+                         alpha=_ptr(alpha), cg_iters=_ptr(cg_iters, np.int32, allow_none=True), max_sms=max_sms,
+                         prior=o.prior)
 
 
 def cofem_submit(srv: int, req: cofem_request) -> int:

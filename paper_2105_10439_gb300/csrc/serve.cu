@@ -110,6 +110,7 @@ void worker_loop(cofem_server* s) {
         // no SM cap by default: on the serving mix (D up to 16384) capping each
         // request at 2 SMs / slots halved throughput (the GEMMs are the bound)
         o.max_sms = r.max_sms > 0 ? r.max_sms : 0;
+        o.prior = r.prior;
         cofem_ctx* h = nullptr;
         unsigned flags = 0;
         cofem_status stat = cofem_create(&h, r.N, r.D, r.kind, r.phi, r.L, &o);

@@ -42,6 +42,36 @@ def test_library_exports_every_declared_symbol(cf):
     assert not missing, missing
 
 
+def test_struct_layouts_match_binding(cf, tmp_path):
+    """Every field of the ABI structs sits at the same offset, and every struct
+    has the same size, in the C header (compiled here with the host C compiler)
+    as in the ctypes binding."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {"cofem_opts": cf.cofem_opts, "cofem_request": cf.cofem_request, "cofem_result": cf.cofem_result}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cofem.h"', "int main(void) {"]
+    for sname, cls in structs.items():
+        lines.append(f'    printf("{sname} size %zu\\n", sizeof({sname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'    printf("{sname} {fname} %zu\\n", offsetof({sname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        a, b, v = ln.split()
+        got[(a, b)] = int(v)
+    for sname, cls in structs.items():
+        assert got[(sname, "size")] == ctypes.sizeof(cls), sname
+        for fname, _ in cls._fields_:
+            assert got[(sname, fname)] == getattr(cls, fname).offset, (sname, fname)
+
+
 def test_status_strings_and_defaults(cf):
     assert cf.lib.cofem_status_string(0) == b"ok"
     assert cf.lib.cofem_status_string(1) == b"invalid argument"
