@@ -153,12 +153,14 @@ def _cpu_baseline(prob, run, budget_s=20.0, avg_iters=None):
         # CG loop capped to the budget
         t0 = time.perf_counter()
         r = oracle_cofem(op, prob.y, prob.beta, run["K"], 1, run["cg_tol"], 3, run["seed"],
-                         rr_period=run["rr_period"])
+                         rr_period=run["rr_period"],
+                         prior=run.get("prior", "gaussian"))
         per_cg = (time.perf_counter() - t0) / max(1, int(r["cg_iters"][0]))
         cap = int(max(3, min(run["cg_maxit"], budget_s // max(per_cg, 1e-9))))
         t0 = time.perf_counter()
         r = oracle_cofem(op, prob.y, prob.beta, run["K"], 1, run["cg_tol"], cap, run["seed"],
-                         rr_period=run["rr_period"])
+                         rr_period=run["rr_period"],
+                         prior=run.get("prior", "gaussian"))
         t1 = time.perf_counter() - t0
         steps = max(1, int(r["cg_iters"][0]))
         if steps < cap or cap >= run["cg_maxit"]:   # a whole EM iteration ran
@@ -166,7 +168,8 @@ def _cpu_baseline(prob, run, budget_s=20.0, avg_iters=None):
             if n > 1:
                 t0 = time.perf_counter()
                 oracle_cofem(op, prob.y, prob.beta, run["K"], n, run["cg_tol"], run["cg_maxit"], run["seed"],
-                             rr_period=run["rr_period"])
+                             rr_period=run["rr_period"],
+                         prior=run.get("prior", "gaussian"))
                 t1 = time.perf_counter() - t0
             return {"value": n / t1, "unit": "EM-iter/s", "cores": cores, "kind": "oracle",
                     "sample": f"first {n} EM iteration(s) of the same fit, FP64 numpy/BLAS, {t1:.1f} s"}
@@ -175,11 +178,13 @@ def _cpu_baseline(prob, run, budget_s=20.0, avg_iters=None):
                 "sample": f"one EM iteration with CG capped at {steps} steps ({t1:.1f} s, FP64 numpy/BLAS), "
                           f"per-step time scaled to cg_maxit = {run['cg_maxit']} steps"}
     t0 = time.perf_counter()
-    r = oracle_cofem(op, prob.y, prob.beta, run["K"], 1, run["cg_tol"], 3, run["seed"], rr_period=run["rr_period"])
+    r = oracle_cofem(op, prob.y, prob.beta, run["K"], 1, run["cg_tol"], 3, run["seed"], rr_period=run["rr_period"],
+                         prior=run.get("prior", "gaussian"))
     per_cg = (time.perf_counter() - t0) / max(1, int(r["cg_iters"][0]))
     cap = int(max(3, min(run["cg_maxit"], budget_s // max(per_cg, 1e-9))))
     t0 = time.perf_counter()
-    r = oracle_cofem(op, prob.y, prob.beta, run["K"], 1, run["cg_tol"], cap, run["seed"], rr_period=run["rr_period"])
+    r = oracle_cofem(op, prob.y, prob.beta, run["K"], 1, run["cg_tol"], cap, run["seed"], rr_period=run["rr_period"],
+                         prior=run.get("prior", "gaussian"))
     t1 = time.perf_counter() - t0
     steps = max(1, int(r["cg_iters"][0]))
     t_em = t1 * float(avg_iters) / steps
@@ -195,6 +200,7 @@ def run_reference(args):
     name = args.workload
     spec = WORKLOADS[name]
     prob, run = workload(name)
+    run["prior"] = args.prior
     vals = []
     base = None
     for _ in range(max(1, args.steps)):
@@ -236,6 +242,7 @@ def run_ours(args):
     name = args.workload
     spec = WORKLOADS[name]
     prob, run = workload(name, seed=1 + rank)   # independent problem per rank (weak scaling)
+    run["prior"] = args.prior
     if args.em_iters > 0:
         run["T"] = args.em_iters
     K, T, tol, maxit = run["K"], run["T"], run["cg_tol"], run["cg_maxit"]
@@ -252,7 +259,8 @@ def run_ours(args):
     def make(precision):
         return cf.CoFEM(N, D, kind, phi_d, prob.L, precision=precision, rr_period=run["rr_period"],
                         seed=run["seed"], stream=stream, use_graph=0 if args.no_graph else 1,
-                        dense_path=_DENSE_PATHS[args.dense_path], overlap_launch=0 if args.no_overlap else 1)
+                        dense_path=_DENSE_PATHS[args.dense_path], overlap_launch=0 if args.no_overlap else 1,
+                        prior=cf.COFEM_PRIOR_RECTIFIED if args.prior == "rectified" else cf.COFEM_PRIOR_GAUSSIAN)
 
     def timed_fits(model, steps, warmup):
         for _ in range(warmup):
@@ -356,7 +364,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": run["precision"], "data": "synthetic",
         "config": {"workload": name, "N": N, "D": D, "K": K, "T": T, "cg_tol": tol, "cg_maxit": maxit,
-                   "rr_period": run["rr_period"], "l2": "inputs larger than L2" if prob.kind == "dense" and
+                   "rr_period": run["rr_period"], "prior": args.prior, "l2": "inputs larger than L2" if prob.kind == "dense" and
                    N * D * (2 if prec == cf.COFEM_BF16 else 4) > 129e6 else "L2 not flushed between fits",
                    "cg_iters_last_fit": [int(v) for v in all_iters[-1]],
                    "launch": "cuda graph, programmatic edges" if graph_overlap else
@@ -509,6 +517,8 @@ def main():
                     help="override T (profiling runs only; the benchmark line uses the workload's T)")
     ap.add_argument("--no-graph", action="store_true",
                     help="drive the CG loop from the host (same kernels; lets profilers see each launch)")
+    ap.add_argument("--prior", default="gaussian", choices=["gaussian", "rectified"],
+                    help="M-step prior: Gaussian (Alg. 1) or rectified Gaussian (non-negativity)")
     ap.add_argument("--no-overlap", action="store_true",
                     help="plain stream order for the CG-step kernels (no programmatic dependent launch)")
     ap.add_argument("--operator-only", action="store_true",
