@@ -44,19 +44,14 @@ __device__ void reduce_parts(const double* part, int nk, int Q, int nch, double*
     __syncthreads();
 }
 
-// Sum of n per-block partials in block order (loads issued eight at a time).
-__device__ __forceinline__ double sum_parts(const double* src, int n) {
+// Sum of n per-block partials by one warp: lane l adds partials l, l + 32, ...
+// in order, then a butterfly over the lanes; every lane, and every block that
+// sums the same partials, gets the same bits.
+__device__ __forceinline__ double warp_sum_parts(const double* src, int n) {
     double v = 0.0;
-    int i = 0;
-    for (; i + 8 <= n; i += 8) {
-        double x[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) x[t] = __ldcg(src + i + t);
-#pragma unroll
-        for (int t = 0; t < 8; ++t) v += x[t];
-    }
-    for (; i < n; ++i) v += __ldcg(src + i);
-    return v;
+#pragma unroll 4
+    for (int i = threadIdx.x & 31; i < n; i += 32) v += __ldcg(src + i);
+    return warp_sum(v);
 }
 
 // ---------------------------------------------------------------------------
@@ -153,6 +148,7 @@ __global__ __launch_bounds__(NT, 2) void k_cg_update(DevCtl* ctl, const float* _
                                                   double* part, cudaGraphConditionalHandle h_rr,
                                                   cudaGraphConditionalHandle h_cg) {
     __shared__ double sh[NT / 32];
+    __shared__ double s_sum[2];
     __shared__ int s_act;
     __shared__ float s_gamma;
     griddep_launch();
@@ -166,16 +162,41 @@ __global__ __launch_bounds__(NT, 2) void k_cg_update(DevCtl* ctl, const float* _
         set_cond(h_rr, ctl->rr_period > 0 && u % ctl->rr_period == 0);
         set_cond(h_cg, 0);
     }
+    // all loads of the thread's IT float4 positions first (the kernel is bound
+    // by memory round trips, not bandwidth); then the partial sums of the
+    // operator, then the arithmetic in element order
+    const size_t off = (size_t)q * Dp;
+    float4 pv[IT], av[IT], mv[IT], xv[IT], rv[IT], uv[IT];
+    int s0[IT], ns[IT];
+    if (ctl->active[q]) {
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const long long j = (long long)ch * CH + (long long)(threadIdx.x + it * NT) * 4;
+            if (j < Dp) {
+                pv[it] = ld4(P + off + j);
+                av[it] = ld4(alpha + j);
+                mv[it] = ld4(minv + j);
+                xv[it] = ld4(X + off + j);
+                rv[it] = ld4(R + off + j);
+                op_range(uo, j, s0[it], ns[it]);
+            }
+        }
+    }
+    // pi_q = beta ||Phi p_q||^2 + p^T diag(alpha) p and gamma_q = rho_q / pi_q
+    // (Alg. 2) from the operator's and the direction kernel's partials (warps 0
+    // and 1, in a fixed order): every block of the column gets the same value;
+    // block 0 records it.  pi_q <= 0 or non-finite freezes the column (breakdown).
+    if (threadIdx.x < 64) {
+        const double v = threadIdx.x < 32 ? warp_sum_parts(ctl->tt_part + (size_t)q * ctl->tt_n, ctl->tt_n)
+                                          : warp_sum_parts(ctl->ap_part + (size_t)q * ctl->ap_n, ctl->ap_n);
+        if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        // pi_q = beta ||Phi p_q||^2 + p^T diag(alpha) p and gamma_q = rho_q / pi_q
-        // (Alg. 2) from the operator's and the direction kernel's partials, in
-        // block order: every block of the column gets the same value; block 0
-        // records it.  pi_q <= 0 or non-finite freezes the column (breakdown).
         int act = ctl->active[q];
         float gamma = 0.0f;
         if (act) {
-            const double tt = sum_parts(ctl->tt_part + (size_t)q * ctl->tt_n, ctl->tt_n);
-            const double ap = sum_parts(ctl->ap_part + (size_t)q * ctl->ap_n, ctl->ap_n);
+            const double tt = s_sum[0], ap = s_sum[1];
             const double pi = ctl->beta * tt + ap;
             const bool ok = pi > 0.0 && isfinite(pi);
             const double g = ok ? ctl->rho[(u - 1) & 1][q] / pi : 0.0;
@@ -194,26 +215,6 @@ __global__ __launch_bounds__(NT, 2) void k_cg_update(DevCtl* ctl, const float* _
         }
         s_act = act;
         s_gamma = gamma;
-    }
-    // all loads of the thread's IT float4 positions first (the kernel is bound
-    // by memory round trips, not bandwidth), issued while thread 0 forms gamma;
-    // then the partial sums of the operator, then the arithmetic in element order
-    const size_t off = (size_t)q * Dp;
-    float4 pv[IT], av[IT], mv[IT], xv[IT], rv[IT], uv[IT];
-    int s0[IT], ns[IT];
-    if (ctl->active[q]) {
-#pragma unroll
-        for (int it = 0; it < IT; ++it) {
-            const long long j = (long long)ch * CH + (long long)(threadIdx.x + it * NT) * 4;
-            if (j < Dp) {
-                pv[it] = ld4(P + off + j);
-                av[it] = ld4(alpha + j);
-                mv[it] = ld4(minv + j);
-                xv[it] = ld4(X + off + j);
-                rv[it] = ld4(R + off + j);
-                op_range(uo, j, s0[it], ns[it]);
-            }
-        }
     }
     __syncthreads();
     float rr = 0.0f, rz = 0.0f;
@@ -320,6 +321,7 @@ __global__ __launch_bounds__(NT) void k_cg_direction(DevCtl* ctl, const float* _
                                                      cudaGraphConditionalHandle h_cg, SplitOut so) {
     __shared__ double sh[NT / 32];
     __shared__ double s_rr[COFEM_QMAX];
+    __shared__ double s_sum[2];
     __shared__ int s_act;
     __shared__ float s_eta;
     griddep_launch();
@@ -331,17 +333,31 @@ __global__ __launch_bounds__(NT) void k_cg_direction(DevCtl* ctl, const float* _
     const int prev = ctl->active[q];
     const double t2 = ctl->tol * ctl->tol;
     const bool frob = ctl->conv == COFEM_CONV_FROBENIUS;
-    double rr = 0.0, rz = 0.0;
+    // the update's (or replacement's) partials of column q, one warp each, in a
+    // fixed order (every block of the column gets the same bits); the Frobenius
+    // test needs ||r_k||^2 of every column
+    const int w = threadIdx.x >> 5;
     if (frob) {
-        if (threadIdx.x < Q) s_rr[threadIdx.x] = sum_parts(part + (size_t)threadIdx.x * nch, nch);
-        __syncthreads();
+        for (int k = w; k < Q; k += NT / 32) {
+            const double v = warp_sum_parts(part + (size_t)k * nch, nch);
+            if ((threadIdx.x & 31) == 0) s_rr[k] = v;
+        }
+        if (w == NT / 32 - 1) {
+            const double v = warp_sum_parts(part + (size_t)(Q + q) * nch, nch);
+            if ((threadIdx.x & 31) == 0) s_sum[1] = v;
+        }
+    } else if (w < 2) {
+        const double v = warp_sum_parts(part + (size_t)(w * Q + q) * nch, nch);
+        if ((threadIdx.x & 31) == 0) s_sum[w] = v;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         int act = 0;
         float eta = 0.0f;
+        double rr = 0.0, rz = 0.0;
         if (prev) {
-            rr = frob ? s_rr[q] : sum_parts(part + (size_t)q * nch, nch);
-            rz = sum_parts(part + (size_t)(Q + q) * nch, nch);
+            rr = frob ? s_rr[q] : s_sum[0];
+            rz = s_sum[1];
             bool stop;
             if (frob) {
                 double num = 0.0, den = 0.0;
