@@ -53,30 +53,14 @@ garbled or at odds with itself):
 from __future__ import annotations
 
 import numpy as np
-from scipy import special
 
+from .em import second_moment  # noqa: F401  (the M-step's E[z_j^2], reading 12)
 from .operators import apply_A
 from .philox import rademacher_probes
 
 FLAG_CG_NOT_CONVERGED = 1
 FLAG_ALPHA_CLAMPED = 2
 FLAG_BREAKDOWN = 4
-
-
-def second_moment(mu, s, prior="gaussian"):
-    """E[z_j^2] of the M-step (Eq. mstep; reading 12 for prior="rectified")."""
-    mu = np.asarray(mu, dtype=np.float64)
-    s = np.asarray(s, dtype=np.float64)
-    m2 = mu ** 2 + s
-    if prior == "gaussian":
-        return m2
-    if prior != "rectified":
-        raise ValueError(prior)
-    pos = s > 0
-    sp = np.where(pos, s, 1.0)
-    xi = mu / np.sqrt(2.0 * sp)
-    corr = mu * np.sqrt(2.0 * sp / np.pi) / special.erfcx(-xi)
-    return m2 + np.where(pos, corr, 0.0)
 
 
 def diag_estimate(P, X):

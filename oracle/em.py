@@ -17,6 +17,7 @@ Two independent E-step routes:
 from __future__ import annotations
 
 import numpy as np
+from scipy import special
 import scipy.linalg as sla
 
 
@@ -57,14 +58,37 @@ def log_marginal_likelihood(Phi, y, beta, alpha):
     return -0.5 * (N * np.log(2.0 * np.pi) + logdet + quad)
 
 
-def mstep(mu, diag_sigma, alpha_max=np.inf):
-    """alpha_j <- 1 / (mu_j^2 + Sigma_jj) (Eq. mstep), with the second moment
-    floored at 1/alpha_max (a no-op for exact EM, where it is >= Sigma_jj > 0)."""
-    m2 = np.asarray(mu) ** 2 + np.asarray(diag_sigma)
+def second_moment(mu, s, prior="gaussian"):
+    """E[z_j^2] of the M-step: mu_j^2 + Sigma_jj under the Gaussian prior (Eq.
+    mstep); under the rectified Gaussian prior (non-negativity subsection) the
+    second moment of N(mu_j, Sigma_jj) restricted to z_j >= 0,
+    mu^2 + Sigma + mu sqrt(2 Sigma / pi) exp(-xi^2) / erfc(-xi),
+    xi = mu / sqrt(2 Sigma) (the printed third term's factor 2 restored; no
+    term where Sigma <= 0; exp(-xi^2) / erfc(-xi) evaluated as 1 / erfcx(-xi)).
+    `s` is Sigma_jj or its estimate."""
+    mu = np.asarray(mu, dtype=np.float64)
+    s = np.asarray(s, dtype=np.float64)
+    m2 = mu ** 2 + s
+    if prior == "gaussian":
+        return m2
+    if prior != "rectified":
+        raise ValueError(prior)
+    pos = s > 0
+    sp = np.where(pos, s, 1.0)
+    xi = mu / np.sqrt(2.0 * sp)
+    corr = mu * np.sqrt(2.0 * sp / np.pi) / special.erfcx(-xi)
+    return m2 + np.where(pos, corr, 0.0)
+
+
+def mstep(mu, diag_sigma, alpha_max=np.inf, prior="gaussian"):
+    """alpha_j <- 1 / E[z_j^2] (Eq. mstep), with the second moment floored at
+    1/alpha_max (a no-op for exact EM, where it is >= Sigma_jj > 0)."""
+    m2 = second_moment(mu, diag_sigma, prior)
     return 1.0 / np.maximum(m2, 1.0 / alpha_max)
 
 
-def em(Phi, y, beta, T, alpha0=None, estep="explicit", alpha_max=np.inf, track_loglik=False):
+def em(Phi, y, beta, T, alpha0=None, estep="explicit", alpha_max=np.inf, track_loglik=False,
+       prior="gaussian"):
     """T iterations of classic EM, laid out like Alg. 1 (T E-steps, T-1
     M-steps; returns alpha^(T) with the mu, diag Sigma of the last E-step)."""
     Phi = np.asarray(Phi, dtype=np.float64)
@@ -83,5 +107,5 @@ def em(Phi, y, beta, T, alpha0=None, estep="explicit", alpha_max=np.inf, track_l
         if track_loglik:
             loglik.append(log_marginal_likelihood(Phi, y, beta, alpha))
         if t < T:
-            alpha = mstep(mu, dsig, alpha_max)
+            alpha = mstep(mu, dsig, alpha_max, prior)
     return dict(alpha=alpha, mu=mu, diag_sigma=dsig, loglik=np.array(loglik))

@@ -193,3 +193,21 @@ def test_rectified_prior_enters_the_m_step():
     np.testing.assert_allclose(r["alpha"], 1.0 / np.maximum(m2, 1e-12), rtol=1e-12)
     sel = (sv > 0) & (np.abs(mu) > 1e-6)
     assert np.all((r["alpha"][sel] > g["alpha"][sel]) == (mu[sel] < 0))
+
+
+def test_hadamard_probes_reproduce_em_with_rectified_prior():
+    """The Hadamard-probe equivalence (s = diag Sigma exactly) holds under the
+    rectified prior too: CoFEM with an exact solve is EM with the truncated
+    second moment in its M-step."""
+    p = toeplitz_calcium(64, 16, 0.1, 25.0, seed=5)
+    H = _hadamard(64)
+    T = 8
+    op = ToeplitzOperator(p.phi, p.N)
+    r = cofem(op, p.y, p.beta, 64, T, 1e-10, 2000, seed=0, probe_fn=lambda t, K, D: H,
+              solver="direct", prior="rectified")
+    e = em(op.dense(), p.y, p.beta, T, alpha_max=1e12, prior="rectified")
+    np.testing.assert_allclose(r["mu"], e["mu"], rtol=1e-7, atol=1e-10)
+    np.testing.assert_allclose(r["s"], e["diag_sigma"], rtol=1e-7)
+    np.testing.assert_allclose(r["alpha"], e["alpha"], rtol=1e-7)
+    g = em(op.dense(), p.y, p.beta, T, alpha_max=1e12)
+    assert not np.allclose(g["alpha"], e["alpha"])
