@@ -4,7 +4,9 @@
 Model (Sec. II-A, Eq. model): z ~ N(0, diag(alpha)^-1), y | z ~ N(Phi z, beta^-1 I).
 E-step (Sec. II-B, Eq. estep-params):
     Sigma = (beta Phi^T Phi + diag(alpha))^-1,   mu = beta Sigma Phi^T y.
-M-step (Eq. mstep): alpha_j <- 1 / (mu_j^2 + Sigma_jj).
+M-step (Eq. mstep): alpha_j <- 1 / (mu_j^2 + Sigma_jj); under the rectified
+    Gaussian prior of the non-negativity subsection, 1 / E[z_j^2] of N(mu_j,
+    Sigma_jj) restricted to z_j >= 0 (second_moment).
 Objective (Eq. mle2): log p(y | alpha) = log N(y; 0, C_y),
     C_y = beta^-1 I + Phi diag(alpha)^-1 Phi^T  (standard Gaussian marginal).
 
