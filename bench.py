@@ -20,6 +20,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -85,7 +86,9 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples (the JSON line carries their summary)
+        self.path = os.path.join(os.environ.get("COFEM_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"cofem_clocks_rank{index}.csv")
 
     def start(self):
         try:
