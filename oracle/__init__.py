@@ -12,10 +12,11 @@ Modules and the passages they follow:
              (Sec. V-A "Dictionary", Sec. VI-A) and A V (Sec. III).
   em         classic EM with explicit covariance (Sec. II-B, Eqs. estep-params,
              mstep), the Woodbury/IRLS E-step (Sec. II-C, Eq. woodbury, beta
-             restored) and the log marginal likelihood (Eq. mle2).
+             restored), the log marginal likelihood (Eq. mle2), the rectified
+             Gaussian prior's M-step and multi-task EM (Sec. III extensions).
   cofem      Alg. 1 (CovarianceFreeEM) with Alg. 2 (ParallelConjGradient) and
              the diagonal preconditioner (Sec. III-C); the diagonal estimation
-             rule (Prop. 1, Eq. diag-estimate).
+             rule (Prop. 1, Eq. diag-estimate); multi-task CoFEM.
 
 Every function is pinned by tests/test_oracle_*.py against something other
 than itself (numpy's Philox, brute-force enumeration, closed forms, the two
@@ -25,6 +26,6 @@ independent EM routes, CG convergence theory).  No function here is marked
 from .philox import philox4x64_10, probe_bits, rademacher_probes  # noqa: F401
 from .operators import DenseOperator, ToeplitzOperator, make_operator, apply_A  # noqa: F401
 from .em import (estep_explicit, estep_woodbury, log_marginal_likelihood,  # noqa: F401
-                 mstep, em)
-from .cofem import (cofem, pcg, diag_estimate, diag_estimate_general,  # noqa: F401
+                 mstep, em, em_multitask, second_moment)
+from .cofem import (cofem, cofem_multitask, pcg, diag_estimate, diag_estimate_general,  # noqa: F401
                     FLAG_CG_NOT_CONVERGED, FLAG_ALPHA_CLAMPED, FLAG_BREAKDOWN)

@@ -39,6 +39,13 @@ garbled or at odds with itself):
     count u is a multiple of rr_period, right after the X, R update the still
     active columns take R <- B - A X before the stopping test, then W, rho and
     P continue from that R.
+13. Multi-task CoFEM (cofem_multitask; multi-task subsection of Sec. III):
+    the L tasks share alpha and beta; each task l draws its own probes
+    (Philox counter word 3 = l; task 0 is the single-task rule), its own
+    preconditioner M_l = beta theta_l + alpha, and its K+1 columns join one
+    batched PCG (per-column stopping, so each task's columns stop on their
+    own); cg_iters[t] is the batched loop's count, the largest over tasks.
+    M-step: alpha_j = L / sum_l (mu_lj^2 + s_lj), floored at 1/alpha_max.
 12. Non-negativity (prior="rectified", the rectified Gaussian prior of the
     non-negativity subsection): the M-step takes alpha_j = 1 / E[z_j^2] with
     E[z_j^2] the second moment of N(mu_j, Sigma_jj) truncated to z_j >= 0,
@@ -185,3 +192,50 @@ def cofem(op, y, beta, K, T, cg_tol, cg_maxit, seed, alpha0=None, precond="jacob
     if return_x:
         out["X"] = X
     return out
+
+
+def cofem_multitask(ops, ys, beta, K, T, cg_tol, cg_maxit, seed, alpha0=None, precond="jacobi",
+                    alpha_max=1e12, conv="per_column", probe_fn=None, solver="pcg"):
+    """Multi-task CoFEM (reading 13): Alg. 1 with L E-steps per iteration (one
+    batched Alg. 2 over the L (K+1) columns; the tasks' columns are independent,
+    so the batch is the L per-task solves) and the shared-alpha M-step.
+
+    ops, ys   per-task operators (oracle.operators) and observations (one D)
+    probe_fn  optional callable (t, K, D, l) -> (K, D) probe block of task l
+    Returns dict(alpha, mu (L x D), s (L x D), cg_iters (T,), flags)."""
+    L = len(ops)
+    D = ops[0].D
+    bs = [beta * op.apply_t(np.asarray(y, dtype=np.float64)) for op, y in zip(ops, ys)]
+    thetas = [op.column_sq_norms() if precond == "jacobi" else np.ones(D) for op in ops]
+    alpha = np.ones(D) if alpha0 is None else np.asarray(alpha0, dtype=np.float64).copy()
+    cg_iters = np.zeros(T, dtype=np.int64)
+    flags = 0
+    mu = s = None
+    for t in range(1, T + 1):
+        mu = np.empty((L, D))
+        s = np.empty((L, D))
+        for l in range(L):
+            probes = (rademacher_probes(seed, t, K, D, task=l) if probe_fn is None
+                      else np.asarray(probe_fn(t, K, D, l), dtype=np.float64))
+            B = np.empty((D, K + 1))
+            B[:, 0] = bs[l]
+            B[:, 1:] = probes.T
+            if solver == "pcg":
+                minv = 1.0 / (beta * thetas[l] + alpha)
+                X, u, f = pcg(lambda V, op=ops[l]: apply_A(op, V, alpha, beta), B, minv, cg_tol, cg_maxit,
+                              conv=conv)
+                cg_iters[t - 1] = max(cg_iters[t - 1], u)
+                flags |= f
+            elif solver == "direct":
+                Phi = ops[l].dense()
+                X = np.linalg.solve(beta * (Phi.T @ Phi) + np.diag(alpha), B)
+            else:
+                raise ValueError(solver)
+            mu[l] = X[:, 0]
+            s[l] = diag_estimate(B[:, 1:], X[:, 1:])
+        if t < T:
+            m2 = np.sum(mu ** 2 + s, axis=0) / L
+            if np.any(m2 < 1.0 / alpha_max):
+                flags |= FLAG_ALPHA_CLAMPED
+            alpha = 1.0 / np.maximum(m2, 1.0 / alpha_max)
+    return dict(alpha=alpha, mu=mu, s=s, cg_iters=cg_iters, flags=flags)

@@ -111,3 +111,24 @@ def em(Phi, y, beta, T, alpha0=None, estep="explicit", alpha_max=np.inf, track_l
         if t < T:
             alpha = mstep(mu, dsig, alpha_max, prior)
     return dict(alpha=alpha, mu=mu, diag_sigma=dsig, loglik=np.array(loglik))
+
+
+def em_multitask(Phis, ys, beta, T, alpha0=None, alpha_max=np.inf):
+    """Multi-task EM (multi-task subsection of Sec. III): L tasks with their own
+    (y_l, Phi_l) and a shared alpha; an explicit E-step per task, then
+    alpha_j <- L / sum_l (mu_lj^2 + Sigma_l,jj) (floored at 1/alpha_max).
+    Returns alpha^(T) and the last E-step's mu (L x D) and diag Sigma (L x D)."""
+    L = len(Phis)
+    D = np.asarray(Phis[0]).shape[1]
+    alpha = np.ones(D) if alpha0 is None else np.asarray(alpha0, dtype=np.float64).copy()
+    mu = dsig = None
+    for t in range(1, T + 1):
+        mu = np.empty((L, D))
+        dsig = np.empty((L, D))
+        for l in range(L):
+            m, S = estep_explicit(np.asarray(Phis[l], dtype=np.float64), ys[l], beta, alpha)
+            mu[l], dsig[l] = m, np.diag(S)
+        if t < T:
+            m2 = np.sum(mu ** 2 + dsig, axis=0) / L
+            alpha = 1.0 / np.maximum(m2, 1.0 / alpha_max)
+    return dict(alpha=alpha, mu=mu, diag_sigma=dsig)

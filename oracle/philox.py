@@ -13,7 +13,8 @@ this project's reading): for EM iteration t (1-based), probe k (1-based) and
 coordinate j (0-based), take the 256-bit Philox4x64-10 output at
     key = (seed, 0),  counter = (j >> 8, k, t, 0)
 and its bit b = j & 255 (word b >> 6, bit b & 63).  p_{t,k,j} = +1 if that bit
-is 0 and -1 if it is 1.
+is 0 and -1 if it is 1.  With L tasks (multi-task CoFEM) task l draws its own
+probes from counter (j >> 8, k, t, l); task 0 is the single-task rule.
 
 Pinned against numpy's own Philox bit generator (a library implementation of
 the same published algorithm) in tests/test_oracle_philox.py.
@@ -69,13 +70,14 @@ def philox4x64_10(ctr, key):
     return np.stack([c0, c1, c2, c3], axis=-1)
 
 
-def probe_bits(seed: int, t: int, k: int, D: int) -> np.ndarray:
+def probe_bits(seed: int, t: int, k: int, D: int, task: int = 0) -> np.ndarray:
     """The D bits behind probe k at EM iteration t (uint8 array of 0/1)."""
     nblk = (D + 255) // 256
     ctr = np.zeros((nblk, 4), dtype=np.uint64)
     ctr[:, 0] = np.arange(nblk, dtype=np.uint64)
     ctr[:, 1] = np.uint64(k)
     ctr[:, 2] = np.uint64(t)
+    ctr[:, 3] = np.uint64(task)
     words = philox4x64_10(ctr, (seed, 0))            # (nblk, 4) uint64
     j = np.arange(D)
     b = j & 255
@@ -83,10 +85,10 @@ def probe_bits(seed: int, t: int, k: int, D: int) -> np.ndarray:
     return ((w >> (b & 63).astype(np.uint64)) & np.uint64(1)).astype(np.uint8)
 
 
-def rademacher_probes(seed: int, t: int, K: int, D: int) -> np.ndarray:
+def rademacher_probes(seed: int, t: int, K: int, D: int, task: int = 0) -> np.ndarray:
     """Probe block for EM iteration t: a (K, D) float64 array of +-1 whose row
     k-1 is p_k (Alg. 1, fresh probes each EM iteration)."""
     out = np.empty((K, D), dtype=np.float64)
     for k in range(1, K + 1):
-        out[k - 1] = 1.0 - 2.0 * probe_bits(seed, t, k, D).astype(np.float64)
+        out[k - 1] = 1.0 - 2.0 * probe_bits(seed, t, k, D, task).astype(np.float64)
     return out

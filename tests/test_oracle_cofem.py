@@ -211,3 +211,52 @@ def test_hadamard_probes_reproduce_em_with_rectified_prior():
     np.testing.assert_allclose(r["alpha"], e["alpha"], rtol=1e-7)
     g = em(op.dense(), p.y, p.beta, T, alpha_max=1e12)
     assert not np.allclose(g["alpha"], e["alpha"])
+
+
+def test_multitask_probes_are_per_task_and_task0_is_the_single_task_rule():
+    a = rademacher_probes(2, 3, 4, 700)
+    np.testing.assert_array_equal(rademacher_probes(2, 3, 4, 700, task=0), a)
+    b = rademacher_probes(2, 3, 4, 700, task=1)
+    assert not np.array_equal(a, b) and abs(np.mean(a * b)) < 0.05   # independent signs
+
+
+def test_multitask_with_one_task_is_single_task_cofem():
+    from oracle import cofem_multitask
+    p = dense_gaussian(60, 200, 6, 20.0, seed=9)
+    op = DenseOperator(p.phi)
+    m = cofem_multitask([op], [p.y], p.beta, 8, 4, 1e-8, 500, seed=2)
+    r = cofem(op, p.y, p.beta, 8, 4, 1e-8, 500, seed=2)
+    np.testing.assert_array_equal(m["alpha"], r["alpha"])
+    np.testing.assert_array_equal(m["mu"][0], r["mu"])
+    np.testing.assert_array_equal(m["cg_iters"], r["cg_iters"])
+
+
+def test_multitask_hadamard_probes_reproduce_multitask_em():
+    """Multi-task subsection: with the D Hadamard columns as every task's
+    probes and exact solves, multi-task CoFEM is multi-task EM (explicit
+    covariances, shared alpha = L / sum_l (mu_l^2 + Sigma_l,jj))."""
+    from oracle import cofem_multitask, em_multitask
+    D, L, T = 64, 3, 6
+    H = _hadamard(D)
+    probs = [dense_gaussian(24, D, 5, 25.0, seed=20 + l) for l in range(L)]
+    beta = probs[0].beta
+    ops = [DenseOperator(p.phi) for p in probs]
+    r = cofem_multitask(ops, [p.y for p in probs], beta, D, T, 1e-10, 2000, seed=0,
+                        probe_fn=lambda t, K, D_, l: H, solver="direct")
+    e = em_multitask([p.phi for p in probs], [p.y for p in probs], beta, T, alpha_max=1e12)
+    np.testing.assert_allclose(r["mu"], e["mu"], rtol=1e-7, atol=1e-10)
+    np.testing.assert_allclose(r["s"], e["diag_sigma"], rtol=1e-7)
+    np.testing.assert_allclose(r["alpha"], e["alpha"], rtol=1e-7)
+
+
+def test_multitask_em_with_identical_tasks_is_single_task_em():
+    """L copies of one task: alpha = L / (L (mu^2 + Sigma)) is the single-task
+    update, so multi-task EM follows single-task EM (up to the rounding of
+    (3 x) / 3, amplified by the E-steps' conditioning)."""
+    from oracle import em_multitask
+    p = dense_gaussian(30, 80, 5, 20.0, seed=4)
+    m = em_multitask([p.phi] * 3, [p.y] * 3, p.beta, 5)
+    e = em(p.phi, p.y, p.beta, 5)
+    np.testing.assert_allclose(m["alpha"], e["alpha"], rtol=1e-9)
+    for l in range(3):
+        np.testing.assert_allclose(m["mu"][l], e["mu"], rtol=1e-9, atol=1e-14)
