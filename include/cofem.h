@@ -12,7 +12,8 @@
  * by Alg. 2 (ParallelConjGradient) with the diagonal preconditioner
  * M = diag(beta theta + alpha) (Sec. III-C), forms mu = x_0 and the diagonal
  * estimate s_j = (1/K) sum_k p_kj x_kj (Eq. diag-estimate) and, for t < T_em,
- * applies the M-step alpha_j = 1 / (mu_j^2 + s_j) (Eq. mstep with s for Sigma_jj).
+ * applies the M-step alpha_j = 1 / (mu_j^2 + s_j) (Eq. mstep with s for Sigma_jj;
+ * or the rectified Gaussian prior's M-step, see COFEM_PRIOR_RECTIFIED).
  *
  * Conventions for every function below:
  *  - Return value is a cofem_status; COFEM_OK (0) on success.  No C++
@@ -44,7 +45,8 @@ typedef int cofem_status;
 #define COFEM_ERR_INVALID_ARG  1  /* bad size, null pointer, unsupported combination */
 #define COFEM_ERR_NOMEM        2  /* device allocation failed / over the memory budget */
 #define COFEM_ERR_CUDA         3  /* a CUDA runtime call failed (message has details) */
-#define COFEM_ERR_NONFINITE    4  /* NaN/Inf in inputs, or CG breakdown (p^T A p <= 0) */
+#define COFEM_ERR_NONFINITE    4  /* NaN/Inf in inputs (a CG breakdown during a fit is not an
+                                     error: the column is frozen and COFEM_FLAG_BREAKDOWN set) */
 #define COFEM_ERR_UNSUPPORTED  5  /* no sm_103a device, or feature not built */
 #define COFEM_ERR_NOT_FOUND    6  /* unknown ticket (serving) */
 
