@@ -48,3 +48,28 @@ def test_peaks_come_from_the_measured_file(tmp_path, monkeypatch):
     assert bench._peaks() == (6800.0, 1900.0, "fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6795.1, "bf16_tflops": 1846.0}))
     assert bench._peaks() == (6795.1, 1846.0, "measured")
+
+
+def test_fp32_alu_peak_from_unit_counts_and_clock():
+    # 152 SMs x 128 FP32 lanes x 2 flop per FMA x 2070 MHz
+    assert bench._fp32_peak_tflops(2070) == pytest.approx(80.55, rel=1e-3)
+    assert bench._fp32_peak_tflops(1035) == pytest.approx(bench._fp32_peak_tflops(2070) / 2)
+
+
+def test_roofline_object_for_hbm_and_alu_bounds():
+    # BF16 dense operator at 8192 x 32768, Q = 33: bytes over the measured copy peak
+    alg_bytes = 2.0 * 8192 * 32768 * 2 + 2.0 * 33 * 32768 * 4
+    r = bench._roofline({"bound": "hbm", "kernel": "k"}, 0.186, alg_bytes, None, 1093.6e6, 6795.1, "measured",
+                        {"sm_mhz": 2070.0})
+    assert r["unit"] == "GB/s" and r["peak"] == 6795.1 and r["traffic"] == 1093.6e6
+    assert r["achieved"] == pytest.approx(alg_bytes / 0.186e-3 / 1e9) and r["frac"] == pytest.approx(r["achieved"] / 6795.1)
+    # convolution operator (D = 1e6, L = 256, Q = 17): flops over the FP32 FMA peak at the sampled clock
+    flops = 4.0 * 256 * 1e6 * 17
+    a = bench._roofline({"bound": "alu", "kernel": "k"}, 0.427, 2.0 * 17 * 1e6 * 4, flops, None, 6795.1, "measured",
+                        {"sm_mhz": 1980.0})
+    assert a["unit"] == "TFLOP/s" and a["peak"] == pytest.approx(bench._fp32_peak_tflops(1980.0))
+    assert a["achieved"] == pytest.approx(flops / 0.427e-3 / 1e12) and 0.0 < a["frac"] < 1.0
+    assert "1980 MHz" in a["peak_source"]
+    # no clock record: the maximum SM clock
+    assert bench._roofline({"bound": "alu"}, 1.0, 0.0, 1e12, None, 1.0, "m", None)["peak"] == \
+        pytest.approx(bench._fp32_peak_tflops(2070.0))
