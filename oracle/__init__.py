@@ -24,7 +24,7 @@ independent EM routes, CG convergence theory).  No function here is marked
 "parity unpinned".
 """
 from .philox import philox4x64_10, probe_bits, rademacher_probes  # noqa: F401
-from .operators import DenseOperator, ToeplitzOperator, make_operator, apply_A  # noqa: F401
+from .operators import DenseOperator, ToeplitzOperator, DCTOperator, make_operator, apply_A  # noqa: F401
 from .em import (estep_explicit, estep_woodbury, log_marginal_likelihood,  # noqa: F401
                  mstep, em, em_multitask, second_moment)
 from .cofem import (cofem, cofem_multitask, pcg, diag_estimate, diag_estimate_general,  # noqa: F401

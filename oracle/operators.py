@@ -8,6 +8,10 @@ A v = beta Phi^T (Phi v) + diag(alpha) v, never A itself).
   N = D; column j of Phi is h delayed by j samples and truncated at N
   (Sec. V-A "Convolutional", Sec. VI-A).  Applied by FFT in FP64, as the paper
   does for calcium deconvolution (Sec. VI-A "Spike Inference").
+* DCTOperator     : Phi = M Omega^-1 with Omega the orthonormal 1-D DCT of
+  size D and M the selection of N of its D outputs (Sec. V-A "DCT").
+  Applied with scipy's fast DCT; the explicit matrix (dense()) is written
+  from the DCT-II definition.
 """
 from __future__ import annotations
 
@@ -77,6 +81,39 @@ class ToeplitzOperator:
             m = min(self.L, self.N - j)
             Phi[j:j + m, j] = self.h[:m]
         return Phi
+
+
+class DCTOperator:
+    """Phi = M Omega^-1: Omega is the orthonormal DCT-II of size D,
+    Omega_kn = c_k cos(pi k (2n + 1) / (2D)), c_0 = sqrt(1/D), c_k = sqrt(2/D);
+    Omega^-1 = Omega^T; M keeps the rows `rows` (N distinct indices < D) of
+    Omega^-1 v."""
+
+    def __init__(self, D, rows):
+        self.D = int(D)
+        self.rows = np.asarray(rows, dtype=np.int64)
+        self.N = self.rows.shape[0]
+
+    def apply(self, V):
+        from scipy import fft
+        return fft.idct(np.asarray(V, dtype=np.float64), type=2, norm="ortho", axis=0)[self.rows]
+
+    def apply_t(self, U):
+        from scipy import fft
+        U = np.asarray(U, dtype=np.float64)
+        full = np.zeros((self.D,) + U.shape[1:])
+        full[self.rows] = U
+        return fft.dct(full, type=2, norm="ortho", axis=0)
+
+    def dense(self):
+        """Explicit N x D matrix: row i of Omega^-1 is column i of Omega."""
+        n = self.rows[:, None].astype(np.float64)
+        k = np.arange(self.D, dtype=np.float64)[None, :]
+        c = np.where(k == 0, np.sqrt(1.0 / self.D), np.sqrt(2.0 / self.D))
+        return c * np.cos(np.pi * k * (2.0 * n + 1.0) / (2.0 * self.D))
+
+    def column_sq_norms(self):
+        return np.sum(self.dense() ** 2, axis=0)
 
 
 def make_operator(kind: str, phi, N: int):

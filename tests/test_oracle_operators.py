@@ -64,3 +64,42 @@ def test_apply_A_matches_explicit_matrix():
     A = beta * Phi.T @ Phi + np.diag(alpha)
     V = rng.standard_normal((9, 4))
     np.testing.assert_allclose(apply_A(DenseOperator(Phi), V, alpha, beta), A @ V, atol=1e-12)
+
+
+def test_dct_operator_matches_its_definition_and_is_orthonormal():
+    """Sec. V-A "DCT": Phi = M Omega^-1.  The fast transforms agree with the
+    matrix written from the DCT-II definition, Phi^T is the adjoint, the kept
+    rows are orthonormal (Phi Phi^T = I_N), and with all rows kept
+    Phi^T Phi = I_D."""
+    from oracle import DCTOperator
+    rng = np.random.default_rng(0)
+    D = 96
+    rows = np.sort(rng.choice(D, size=D // 3, replace=False))
+    op = DCTOperator(D, rows)
+    Phi = op.dense()
+    V = rng.standard_normal((D, 3))
+    U = rng.standard_normal((D // 3, 3))
+    np.testing.assert_allclose(op.apply(V), Phi @ V, atol=1e-12)
+    np.testing.assert_allclose(op.apply_t(U), Phi.T @ U, atol=1e-12)
+    np.testing.assert_allclose(Phi @ Phi.T, np.eye(D // 3), atol=1e-12)
+    np.testing.assert_allclose(op.column_sq_norms(), np.sum(Phi ** 2, axis=0), atol=1e-12)
+    full = DCTOperator(D, np.arange(D)).dense()
+    np.testing.assert_allclose(full.T @ full, np.eye(D), atol=1e-12)
+
+
+def test_dct_dictionary_with_all_rows_gives_the_orthonormal_closed_form():
+    """Phi^T Phi = I: A = diag(beta + alpha), so Jacobi-preconditioned CG
+    converges in one step, mu_j = beta (Phi^T y)_j / (beta + alpha_j) and
+    s_j = 1 / (beta + alpha_j) for any probes (the orthonormal case of
+    Sec. III-C's preconditioner)."""
+    from oracle import DCTOperator, cofem
+    rng = np.random.default_rng(1)
+    D = 128
+    op = DCTOperator(D, np.arange(D))
+    y = rng.standard_normal(D)
+    beta = 50.0
+    alpha0 = np.exp(rng.uniform(-1, 2, D))
+    r = cofem(op, y, beta, 6, 1, 1e-12, 50, seed=2, alpha0=alpha0)
+    assert np.all(r["cg_iters"] == 1)
+    np.testing.assert_allclose(r["mu"], beta * op.apply_t(y) / (beta + alpha0), rtol=1e-10)
+    np.testing.assert_allclose(r["s"], 1.0 / (beta + alpha0), rtol=1e-10)
