@@ -32,7 +32,9 @@ garbled or at odds with itself):
  6. b = beta Phi^T y is computed once per fit (it does not depend on t).
  7. Probes: Philox4x64-10 rule of oracle.philox, fresh for every t.
  8. T E-steps and T-1 M-steps; the returned alpha is alpha^(T).
- 9. theta: Jacobi (theta_j = ||phi_j||^2) by default, or theta = 1 ("one").
+ 9. theta: Jacobi (theta_j = ||phi_j||^2) by default, or theta = 1 ("one");
+    precond="none" runs Alg. 2 unpreconditioned (M = I), the comparison of the
+    paper's preconditioner study (Sec. V, empirical insights, Fig. 3b).
 10. The second moment mu_j^2 + s_j can be <= 0 for finite K (s is unbiased,
     not positive); alpha_j = 1 / max(mu_j^2 + s_j, 1/alpha_max), alpha_max = 1e12.
 11. Residual replacement (precision form, rr_period > 0): when the iteration
@@ -166,7 +168,7 @@ def cofem(op, y, beta, K, T, cg_tol, cg_maxit, seed, alpha0=None, precond="jacob
         B = np.empty((D, K + 1))
         B[:, 0] = b
         B[:, 1:] = probes.T
-        minv = 1.0 / (beta * theta + alpha)
+        minv = np.ones(D) if precond == "none" else 1.0 / (beta * theta + alpha)
 
         def apply_a(V, alpha=alpha):
             return apply_A(op, V, alpha, beta)

@@ -264,3 +264,22 @@ def test_multitask_em_with_identical_tasks_is_single_task_em():
     np.testing.assert_allclose(m["alpha"], e["alpha"], rtol=1e-9)
     for l in range(3):
         np.testing.assert_allclose(m["mu"][l], e["mu"], rtol=1e-9, atol=1e-14)
+
+
+def test_unpreconditioned_cg_solves_the_same_systems():
+    """precond="none" (M = I, the comparison of the paper's preconditioner
+    study) reaches the same E-step solution as the Jacobi preconditioner, in
+    more CG steps."""
+    p = dense_gaussian(80, 300, 8, 25.0, seed=12)
+    op = DenseOperator(p.phi)
+    # one E-step (alpha = 1, kappa(A) ~ 4e4): both stop at ||r|| <= 1e-12 ||b||
+    a = cofem(op, p.y, p.beta, 6, 1, 1e-12, 3000, seed=2)
+    n = cofem(op, p.y, p.beta, 6, 1, 1e-12, 3000, seed=2, precond="none")
+    assert a["flags"] == 0 and n["flags"] == 0
+    # |x error| <= kappa(A) tol |x| ~ 4e-8 |x|
+    np.testing.assert_allclose(n["mu"], a["mu"], rtol=0, atol=1e-7 * np.max(np.abs(a["mu"])))
+    np.testing.assert_allclose(n["s"], a["s"], rtol=0, atol=1e-7 * np.max(np.abs(a["s"])))
+    # later E-steps (alpha spread over orders of magnitude): Jacobi needs fewer steps
+    a3 = cofem(op, p.y, p.beta, 6, 3, 1e-8, 3000, seed=2)
+    n3 = cofem(op, p.y, p.beta, 6, 3, 1e-8, 3000, seed=2, precond="none")
+    assert n3["cg_iters"][-1] > a3["cg_iters"][-1]
