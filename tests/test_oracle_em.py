@@ -81,3 +81,32 @@ def test_mstep_formula_and_clamp():
     mu = np.array([1.0, 0.0, 2.0])
     d = np.array([1.0, 1e-20, 0.25])
     np.testing.assert_allclose(mstep(mu, d, alpha_max=1e12), [0.5, 1e12, 1.0 / 4.25])
+
+
+def test_theorem1_estimator_spread_on_inactive_and_active_sets():
+    """Thm. 1 with Lemma 1's exact spread nu_j = sqrt((1/K) sum_{j' != j}
+    Sigma_jj'^2) along exact EM: on the inactive coordinates it goes to zero
+    (halving, roughly, with each doubling of t), and on the coordinates EM
+    keeps (alpha_j finite) it stays below the theorem's bound
+    (1/sqrt(K)) ||Theta^-1 Phi_S^T Phi_S - I||_2 / (beta sigma_min^2(Phi_S))
+    with Theta = diag(Phi_S^T Phi_S)."""
+    p = dense_gaussian(64, 128, 6, 40.0, seed=1)
+    Phi = p.phi.astype(np.float64)
+    K = 8
+    inactive = np.ones(p.D, bool)
+    inactive[p.support] = False
+    med = []
+    for T in (50, 100, 200, 400):
+        a = em(Phi, p.y, p.beta, T, alpha_max=1e12)["alpha"]
+        Sig = np.linalg.inv(p.beta * Phi.T @ Phi + np.diag(a))
+        off = Sig - np.diag(np.diag(Sig))
+        nu = np.sqrt(np.sum(off ** 2, axis=1) / K)
+        med.append(np.median(nu[inactive]))
+    assert all(m1 < 0.7 * m0 for m0, m1 in zip(med, med[1:])), med
+    assert med[-1] < 1e-2 * np.median(nu[~inactive])
+    S = a < 1e6
+    PS = Phi[:, S]
+    G = PS.T @ PS
+    bound = (np.linalg.norm(np.diag(1.0 / np.diag(G)) @ G - np.eye(S.sum()), 2)
+             / (p.beta * np.linalg.svd(PS, compute_uv=False).min() ** 2) / np.sqrt(K))
+    assert np.all(nu[S] <= bound), (nu[S].max(), bound)
