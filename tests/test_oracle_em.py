@@ -110,3 +110,28 @@ def test_theorem1_estimator_spread_on_inactive_and_active_sets():
     bound = (np.linalg.norm(np.diag(1.0 / np.diag(G)) @ G - np.eye(S.sum()), 2)
              / (p.beta * np.linalg.svd(PS, compute_uv=False).min() ** 2) / np.sqrt(K))
     assert np.all(nu[S] <= bound), (nu[S].max(), bound)
+
+
+def test_theorem2_jacobi_preconditioned_condition_number_stays_bounded():
+    """Thm. 2's mechanism along exact EM: kappa(A^(t)) grows without bound
+    (alpha_j -> infinity off the support), while the Jacobi-preconditioned
+    A' = M^-1/2 A M^-1/2, M = diag(beta theta + alpha), stays below
+    (1 + delta) / (1 - delta), delta = ||Theta^-1 Phi_S^T Phi_S - I||_2 over
+    the coordinates EM keeps (alpha_j finite)."""
+    p = dense_gaussian(200, 400, 5, 40.0, seed=1)
+    Phi = p.phi.astype(np.float64)
+    theta = np.sum(Phi ** 2, axis=0)
+    kap = {}
+    for T in (100, 400):
+        a = em(Phi, p.y, p.beta, T, alpha_max=1e12)["alpha"]
+        A = p.beta * Phi.T @ Phi + np.diag(a)
+        m = p.beta * theta + a
+        ev = np.linalg.eigvalsh(A)
+        evp = np.linalg.eigvalsh(A / np.sqrt(np.outer(m, m)))
+        S = a < 1e6
+        G = Phi[:, S].T @ Phi[:, S]
+        delta = np.linalg.norm(G / np.diag(G)[:, None] - np.eye(S.sum()), 2)
+        assert delta < 1.0
+        kap[T] = (ev[-1] / ev[0], evp[-1] / evp[0])
+        assert kap[T][1] <= (1 + delta) / (1 - delta), (T, kap[T], delta)
+    assert kap[400][0] > 4.0 * kap[100][0] and kap[400][0] > 100.0 * kap[400][1]
