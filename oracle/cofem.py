@@ -41,13 +41,6 @@ garbled or at odds with itself):
     count u is a multiple of rr_period, right after the X, R update the still
     active columns take R <- B - A X before the stopping test, then W, rho and
     P continue from that R.
-13. Multi-task CoFEM (cofem_multitask; multi-task subsection of Sec. III):
-    the L tasks share alpha and beta; each task l draws its own probes
-    (Philox counter word 3 = l; task 0 is the single-task rule), its own
-    preconditioner M_l = beta theta_l + alpha, and its K+1 columns join one
-    batched PCG (per-column stopping, so each task's columns stop on their
-    own); cg_iters[t] is the batched loop's count, the largest over tasks.
-    M-step: alpha_j = L / sum_l (mu_lj^2 + s_lj), floored at 1/alpha_max.
 12. Non-negativity (prior="rectified", the rectified Gaussian prior of the
     non-negativity subsection): the M-step takes alpha_j = 1 / E[z_j^2] with
     E[z_j^2] the second moment of N(mu_j, Sigma_jj) truncated to z_j >= 0,
@@ -58,6 +51,13 @@ garbled or at odds with itself):
     the paper says); where s_j <= 0 the term is undefined and dropped, and the
     floor 1/alpha_max applies as in reading 10.  exp(-xi^2) / erfc(-xi) is
     evaluated as 1 / erfcx(-xi), the same function without overflow.
+13. Multi-task CoFEM (cofem_multitask; multi-task subsection of Sec. III):
+    the L tasks share alpha and beta; each task l draws its own probes
+    (Philox counter word 3 = l; task 0 is the single-task rule), its own
+    preconditioner M_l = beta theta_l + alpha, and its K+1 columns join one
+    batched PCG (per-column stopping, so each task's columns stop on their
+    own); cg_iters[t] is the batched loop's count, the largest over tasks.
+    M-step: alpha_j = L / sum_l (mu_lj^2 + s_lj), floored at 1/alpha_max.
 """
 from __future__ import annotations
 
