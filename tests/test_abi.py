@@ -77,6 +77,9 @@ def test_status_strings_and_defaults(cf):
     assert cf.lib.cofem_status_string(1) == b"invalid argument"
     o = cf.default_opts()
     assert o.precision == cf.COFEM_F32 and o.alpha_max == 1e12 and o.use_graph == 1 and o.seed == 2
+    # the remaining defaults as the header documents them
+    assert (o.precond, o.conv, o.rr_period, o.stream) == (cf.COFEM_PRECOND_JACOBI, cf.COFEM_CONV_PER_COLUMN, 0, None)
+    assert (o.dense_path, o.max_sms, o.overlap_launch, o.prior) == (cf.COFEM_PATH_AUTO, 0, 1, cf.COFEM_PRIOR_GAUSSIAN)
 
 
 @pytest.mark.parametrize("args,msg", [
@@ -97,7 +100,8 @@ def test_create_rejects_bad_arguments_without_gpu(cf, args, msg):
 
 
 def test_create_rejects_bad_opts(cf):
-    for kw in (dict(precision=9), dict(precond=4), dict(conv=3), dict(rr_period=-1), dict(alpha_max=-1.0)):
+    for kw in (dict(precision=9), dict(precond=4), dict(conv=3), dict(rr_period=-1), dict(alpha_max=-1.0),
+               dict(max_sms=-1), dict(dense_path=7), dict(overlap_launch=2), dict(prior=5)):
         with pytest.raises(cf.CofemError) as e:
             cf.cofem_create(4, 4, 0, np.zeros(16, np.float32), 0, cf.default_opts(**kw))
         assert e.value.status == cf.COFEM_ERR_INVALID_ARG
