@@ -528,7 +528,7 @@ def run_operator_only(args):
                       "ms_per_apply": ms}))
 
 
-def main():
+def _parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -556,7 +556,11 @@ def main():
                     help="plain stream order for the CG-step kernels (no programmatic dependent launch)")
     ap.add_argument("--operator-only", action="store_true",
                     help="apply only the operator A V (Q = K+1 columns) --steps times; for profilers")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = _parser().parse_args()
     if args.serve:
         import torch
         import paper_2105_10439_gb300 as cf

@@ -73,3 +73,20 @@ def test_roofline_object_for_hbm_and_alu_bounds():
     # no clock record: the maximum SM clock
     assert bench._roofline({"bound": "alu"}, 1.0, 0.0, 1e12, None, 1.0, "m", None)["peak"] == \
         pytest.approx(bench._fp32_peak_tflops(2070.0))
+
+
+def test_profile_commands_use_existing_bench_flags():
+    """Every `python bench.py ...` command quoted in profiles/*.md parses with
+    the current command line of bench.py."""
+    import glob
+    import re
+    import shlex
+    cmds = []
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        text = open(path).read().replace("\\\n", " ")
+        for m in re.finditer(r"python bench\.py([^\n`\"]*)", text):
+            cmds.append((os.path.basename(path), m.group(1)))
+    assert cmds
+    for name, tail in cmds:
+        argv = [a for a in shlex.split(tail) if not a.startswith("$")]
+        bench._parser().parse_args(argv)   # raises SystemExit on an unknown flag
