@@ -107,9 +107,11 @@ def pcg(apply_a, B, minv, tol, maxit, conv="per_column", rr_period=0, history=No
         Psi = apply_a(P)                                   # Apply matrix
         pi = np.sum(P * Psi, axis=0)
         a = active
-        if np.any(~(pi[a] > 0.0)) or not np.all(np.isfinite(pi[a])):
+        # a CG step needs a positive, finite p^T A p (A symmetric positive
+        # definite); any other value freezes the column (breakdown)
+        bad = a & ~((pi > 0.0) & np.isfinite(pi))
+        if np.any(bad):
             flags |= FLAG_BREAKDOWN
-            bad = a & ~(pi > 0.0)
             active = active & ~bad
             a = active
         gamma = np.zeros(Q)

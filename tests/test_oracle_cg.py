@@ -112,3 +112,40 @@ def test_maxit_sets_flag():
     B = np.random.default_rng(13).standard_normal((70, 2))
     _, iters, flags = pcg(lambda V: A @ V, B, minv, 1e-14, 3)
     assert iters == 3 and flags & 1
+
+
+def test_breakdown_flagged_and_column_frozen():
+    """Alg. 2 divides by pi_q = p_q^T A p_q, which a symmetric positive
+    definite A keeps positive.  On an indefinite A a column whose first
+    direction has p^T A p < 0 cannot take a CG step: it is flagged and frozen
+    at X = 0, while a column that only sees the positive part still solves."""
+    from oracle.cofem import FLAG_BREAKDOWN
+    d = np.array([1.0, 2.0, -1.0])
+    B = np.zeros((3, 2))
+    B[0, 0] = 1.0          # column 0: e_1, in the positive part (one step, exact)
+    B[2, 1] = 1.0          # column 1: e_3, p^T A p = -1
+    X, iters, flags = pcg(lambda V: d[:, None] * V, B, np.ones(3), 1e-12, 10)
+    assert flags & FLAG_BREAKDOWN
+    np.testing.assert_allclose(X[:, 0], [1.0, 0.0, 0.0], rtol=1e-15)
+    assert np.all(X[:, 1] == 0.0)
+    assert iters == 1
+
+
+def test_breakdown_on_non_finite_pi():
+    """A non-finite pi_q is a breakdown too.  An infinite entry of M^-1 (a zero
+    diagonal of the preconditioner) makes W = M^-1 R infinite where R is not
+    zero and NaN (inf * 0) where it is, so every column's pi is +inf or NaN:
+    all are flagged and frozen at X = 0, and no NaN reaches X."""
+    from oracle.cofem import FLAG_BREAKDOWN
+    D = 6
+    d = np.linspace(1.0, 3.0, D)
+    minv = 1.0 / d
+    minv[2] = np.inf
+    B = np.zeros((D, 2))
+    B[:, 0] = 1.0          # R[2] != 0: W[2] = inf, pi = +inf
+    B[0, 1] = 1.0          # R[2] == 0: W[2] = NaN, pi = NaN
+    with np.errstate(invalid="ignore", over="ignore"):
+        X, iters, flags = pcg(lambda V: d[:, None] * V, B, minv, 1e-12, 10)
+    assert flags & FLAG_BREAKDOWN
+    assert np.all(X == 0.0)
+    assert iters == 1
