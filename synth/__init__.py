@@ -60,9 +60,12 @@ class Problem:
         return int(self.phi.shape[0]) if self.kind == "toeplitz" else 0
 
 
-def _noise(rng: np.random.Generator, clean: np.ndarray, snr_db: float):
+def _noise(rng: np.random.Generator, clean: np.ndarray, snr_db: float, sigma: Optional[float] = None):
     N = clean.shape[0]
-    sigma2 = float(np.dot(clean, clean)) / (N * 10.0 ** (snr_db / 10.0))
+    if sigma is not None:   # a fixed noise level instead of a target SNR
+        sigma2 = float(sigma) ** 2
+    else:
+        sigma2 = float(np.dot(clean, clean)) / (N * 10.0 ** (snr_db / 10.0))
     if sigma2 <= 0.0:  # all-zero signal: fall back to unit precision
         sigma2 = 1.0
     eps = rng.standard_normal(N) * math.sqrt(sigma2)
@@ -70,9 +73,11 @@ def _noise(rng: np.random.Generator, clean: np.ndarray, snr_db: float):
 
 
 def dense_gaussian(N: int, D: int, d: int, snr_db: float, seed: int,
-                   spike: str = "normal") -> Problem:
+                   spike: str = "normal", sigma: Optional[float] = None) -> Problem:
     """Dense Gaussian dictionary Phi_ij ~ N(0, 1/N) (float32), d spikes at
-    uniformly random positions with N(0,1) (or Uniform(-2,2)) amplitudes."""
+    uniformly random positions with N(0,1) (or Uniform(-2,2)) amplitudes.
+    The noise is set by snr_db, or by a fixed standard deviation `sigma` when
+    given (snr_db is then ignored)."""
     rng = np.random.default_rng(seed)
     phi = rng.standard_normal((N, D), dtype=np.float32)
     phi *= np.float32(1.0 / math.sqrt(N))
@@ -85,7 +90,7 @@ def dense_gaussian(N: int, D: int, d: int, snr_db: float, seed: int,
     else:
         raise ValueError(spike)
     clean = phi[:, support].astype(np.float64) @ z[support] if d > 0 else np.zeros(N)
-    y, sigma2 = _noise(rng, clean, snr_db)
+    y, sigma2 = _noise(rng, clean, snr_db, sigma)
     return Problem("dense", N, D, phi, y.astype(np.float32), z, 1.0 / sigma2, sigma2, support)
 
 

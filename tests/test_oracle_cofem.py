@@ -90,29 +90,98 @@ def test_column_zero_is_mu_and_probes_are_philox():
     np.testing.assert_allclose(r["X"][:, 1:], np.linalg.solve(A, P), rtol=1e-7, atol=1e-12)
 
 
-def test_support_recovery_gaussian():
-    """Sec. V-C: CoFEM (K = 20, U = 400, theta = 1) reaches NRMSE < 2 % after
-    T = 30 EM iterations on a dense Gaussian Phi (the printed settings and
-    outcome: tests/golden/sec5_accuracy_settings.json) with N = D/4,
-    d = 0.06 D.  The paper's eps = 1e-4 leaves the mu column too inexact at
-    this SNR for the inactive alpha_j to grow; eps = 1e-5 (per column or
-    Frobenius) reproduces the < 2 % figure, as does an exact solve."""
+def _sec5_fixture():
     import json
     import os
-    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "sec5_accuracy_settings.json")))
+    return json.load(open(os.path.join(os.path.dirname(__file__), "golden", "sec5_accuracy_settings.json")))
+
+
+def _sec5_problem(g, seed=11):
+    """The printed accuracy setting: dense Gaussian Phi, N = D/4, d = 0.06 D
+    spikes Uniform(-2, 2), noise sigma = 0.01 (beta = 1/sigma^2 = 1e4)."""
+    D = g["D"]
+    p = dense_gaussian(D // 4, D, int(0.06 * D), 0.0, seed=seed, spike="uniform2", sigma=g["sigma"])
+    assert p.beta == g["beta"]
+    return p
+
+
+def _nrmse(mu, z):
+    return np.linalg.norm(mu - z) / np.linalg.norm(z)
+
+
+def test_support_recovery_gaussian():
+    """Sec. V settings and outcome (tests/golden/sec5_accuracy_settings.json:
+    sigma = 0.01, beta = 1e4, K = 20, U = 400, theta = 1, T = 30).  CoFEM with
+    eps = 1e-5 (per column or Frobenius) gives the fit of an exact E-step
+    solve with the same probes (mu within 2e-3, NRMSE within 2 %), recovers
+    every spike clearly above the noise and nothing else.  (At this noise
+    level the exact-solve fit itself has NRMSE 1.6-3.2 % over seeds 1-8,
+    2.26 % here, so the printed "< 2 %" is checked at 40 dB below.)"""
+    g = _sec5_fixture()
+    p = _sec5_problem(g)
+    op = DenseOperator(p.phi)
+    ex = cofem(op, p.y, p.beta, g["K"], g["T"], 1e-5, g["U"], seed=3, precond="one", solver="direct")
+    off = np.ones(p.D, bool)
+    off[p.support] = False
+    big = np.abs(p.z) > 0.1
+    for conv in ("per_column", "frobenius"):
+        r = cofem(op, p.y, p.beta, g["K"], g["T"], 1e-5, g["U"], seed=3, precond="one", conv=conv)
+        assert np.linalg.norm(r["mu"] - ex["mu"]) / np.linalg.norm(ex["mu"]) < 2e-3, conv
+        assert _nrmse(r["mu"], p.z) < 1.02 * _nrmse(ex["mu"], p.z), conv
+        assert np.all(np.abs(r["mu"][big]) > 0.05)
+        assert np.max(np.abs(r["mu"][off])) < 0.05
+
+
+def test_printed_cg_tolerance_leaves_mu_inexact():
+    """Reading of Sec. V-C's eps: with the per-column stopping test, the
+    printed eps = 1e-4 stops the mu column early enough that the fit departs
+    from the exact-solve fit (mu more than 1e-2 away, NRMSE over 1.5 times the
+    exact one), while eps = 1e-5 stays within 2e-3 of it; the workloads
+    therefore use 1e-5."""
+    g = _sec5_fixture()
+    p = _sec5_problem(g)
+    op = DenseOperator(p.phi)
+    ex = cofem(op, p.y, p.beta, g["K"], g["T"], 1e-5, g["U"], seed=3, precond="one", solver="direct")
+    d = {}
+    for eps in (1e-4, 1e-5):
+        r = cofem(op, p.y, p.beta, g["K"], g["T"], eps, g["U"], seed=3, precond="one")
+        d[eps] = (np.linalg.norm(r["mu"] - ex["mu"]) / np.linalg.norm(ex["mu"]),
+                  _nrmse(r["mu"], p.z) / _nrmse(ex["mu"], p.z))
+    assert d[1e-4][0] > 1e-2 and d[1e-4][1] > 1.5, d
+    assert d[1e-5][0] < 2e-3 and d[1e-5][1] < 1.02, d
+
+
+def test_support_recovery_gaussian_40db():
+    """The printed outcome, NRMSE < 2 % after T = 30 (same settings as above,
+    noise at 40 dB SNR instead of sigma = 0.01), at eps = 1e-5."""
+    g = _sec5_fixture()
     D = g["D"]
     p = dense_gaussian(D // 4, D, int(0.06 * D), 40.0, seed=11, spike="uniform2")
     for conv in ("per_column", "frobenius"):
         r = cofem(DenseOperator(p.phi), p.y, p.beta, g["K"], g["T"], 1e-5, g["U"], seed=3, precond="one",
                   conv=conv)
-        nrmse = np.linalg.norm(r["mu"] - p.z) / np.linalg.norm(p.z)
-        assert nrmse < g["nrmse_below"], (conv, nrmse)
-        # every spike clearly above the noise floor is found, nothing else is
-        off = np.ones(p.D, bool)
-        off[p.support] = False
-        big = np.abs(p.z) > 0.1
-        assert np.all(np.abs(r["mu"][big]) > 0.05)
-        assert np.max(np.abs(r["mu"][off])) < 0.05
+        assert _nrmse(r["mu"], p.z) < g["nrmse_below"], conv
+
+
+@pytest.mark.parametrize("N,D,d,snr,seed,K,T,far", [
+    (77, 301, 9, 20.0, 1, 1, 6, True), (120, 500, 15, 25.0, 11, 6, 8, True), (200, 800, 16, 25.0, 12, 8, 8, True),
+    (250, 500, 10, 15.0, 11, 16, 10, False), (200, 501, 10, 15.0, 5, 5, 8, False)])
+def test_fit_sensitivity_to_cg_tolerance(N, D, d, snr, seed, K, T, far):
+    """Why whole-fit parity at tol 1e-5 is checked on the better-conditioned
+    problems: on the ill-conditioned ones (far=True) the FP64 fit at
+    tol 1e-5 is itself more than the parity tolerance (1e-4 on mu, 1e-3 on
+    1/alpha) away from the same fit at tol 1e-7, so the result at 1e-5 is
+    not determined to that tolerance by the method; on the others it is."""
+    p = dense_gaussian(N, D, d, snr, seed=seed)
+    op = DenseOperator(p.phi)
+    a = cofem(op, p.y, p.beta, K, T, 1e-5, 400, seed=2)
+    b = cofem(op, p.y, p.beta, K, T, 1e-7, 2000, seed=2)
+    e_mu = np.linalg.norm(a["mu"] - b["mu"]) / np.linalg.norm(b["mu"])
+    e_a = np.linalg.norm(1 / a["alpha"] - 1 / b["alpha"]) / np.linalg.norm(1 / b["alpha"])
+    if far:
+        assert e_mu > 1e-3 and e_a > 1e-3, (e_mu, e_a)
+    else:
+        assert e_mu < 1e-4 and e_a < 1e-3, (e_mu, e_a)
 
 
 def test_toeplitz_cofem_matches_dense_route():
@@ -283,3 +352,25 @@ def test_unpreconditioned_cg_solves_the_same_systems():
     a3 = cofem(op, p.y, p.beta, 6, 3, 1e-8, 3000, seed=2)
     n3 = cofem(op, p.y, p.beta, 6, 3, 1e-8, 3000, seed=2, precond="none")
     assert n3["cg_iters"][-1] > a3["cg_iters"][-1]
+
+
+def test_breakdown_fit_goes_on():
+    """Phi = 0 and alpha0 = 0: the Jacobi preconditioner M = beta theta + alpha
+    is zero, so the probe columns of the first E-step break down (pi not
+    finite) and are frozen at x = 0; mu = 0 (b = 0), s = 0, the M-step clamps
+    alpha at alpha_max, and the next E-step is regular (M = alpha_max):
+    s = 1/alpha_max exactly (Phi = 0 closed form)."""
+    from oracle.cofem import FLAG_BREAKDOWN
+    D = 40
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        r1 = cofem(DenseOperator(np.zeros((10, D))), np.ones(10), 3.0, 4, 1, 1e-10, 50, seed=1,
+                   alpha0=np.zeros(D))
+        r3 = cofem(DenseOperator(np.zeros((10, D))), np.ones(10), 3.0, 4, 3, 1e-10, 50, seed=1,
+                   alpha0=np.zeros(D))
+    assert r1["flags"] & FLAG_BREAKDOWN
+    assert np.all(r1["mu"] == 0.0) and np.all(r1["s"] == 0.0)
+    assert r3["flags"] & FLAG_BREAKDOWN and r3["flags"] & FLAG_ALPHA_CLAMPED
+    for k in ("mu", "s", "alpha"):
+        assert np.all(np.isfinite(r3[k])), k
+    np.testing.assert_array_equal(r3["alpha"], 1e12)
+    np.testing.assert_allclose(r3["s"], 1e-12, rtol=1e-14)
