@@ -41,12 +41,11 @@ def _dist():
 
 
 # DRAM bytes (read + write) per operator application from one ncu capture of
-# the current kernels, keyed by (workload, operator form); the source summary
-# is named beside each entry.  An entry must be removed when its kernels change.
+# the current kernels, keyed by (workload, operator form).  An entry must be
+# removed when its kernels change.
 _MEASURED_TRAFFIC = {
-    # profiles/k_gemm_tc_bf16_two_pass_dense_n8192_d32768_q33.md and
-    # profiles/cg_vector_kernels_dense_n8192_d32768_q33.md: two k_gemm_tc
-    # launches (547.9 + 543.9 MB) and k_tc_reduce_T (1.8 MB, warm cache)
+    # two k_gemm_tc launches (547.9 + 543.9 MB) and k_tc_reduce_T (1.8 MB,
+    # warm cache)
     ("dense_n8192_d32768_k32_bf16", 1): 1093.6e6,
 }
 

@@ -21,7 +21,9 @@
  *    human-readable message for the calling thread.
  *  - "Device or host" pointers are classified with cudaPointerGetAttributes;
  *    host memory may be pageable or pinned.  "Device" pointers must be CUDA
- *    device (or managed) memory of the handle's device.
+ *    device (or managed) memory of the handle's device; device memory of
+ *    another GPU is rejected with COFEM_ERR_INVALID_ARG where the entry point
+ *    checks it (the operator output, the allocation-free entry point).
  *  - The caller owns every buffer it passes; the library never frees them.
  *    The library owns the memory it allocates inside a handle.
  *  - Floating-point inputs are IEEE binary32; vectors are dense, unit stride.
@@ -292,11 +294,18 @@ cofem_status cofem_server_destroy(cofem_server* srv);
  * floats (4 MiB) in the library's device memory, which every GPU that loads the
  * library keeps until the process exits.  All calls on a device share that
  * array: calls whose kernels can overlap on the GPU (different streams without
- * ordering) race on it and give wrong results; serialise them.  The first call
- * on each device looks up the array's device address with that device current;
- * make that first call before any stream capture begins.  Later calls do no
- * set-up.  Errors: INVALID_ARG (sizes, NULL or non-device pointers),
- * NONFINITE (beta), CUDA (launch failure). */
+ * ordering) race on it and give wrong results; serialise them.  Every call
+ * leaves its T = Phi V in the array; nothing in it needs to start at zero.
+ * The first call on each device looks up the array's device address with that
+ * device current; make that first call before any stream capture begins.
+ * Later calls do no set-up unless the device's context has changed (after a
+ * cudaDeviceReset the next call looks the address up again, so make it
+ * outside a capture too).  phi, V, alpha and Psi must be device memory of the
+ * current device (or managed memory).  A CUDA error left pending on the
+ * calling thread by earlier work is returned as COFEM_ERR_CUDA before anything
+ * is launched.  Errors: INVALID_ARG (sizes, NULL pointers, host memory or
+ * another device's memory), NONFINITE (beta), CUDA (pending error, launch
+ * failure). */
 #define COFEM_NOALLOC_MAX_ELEMS 1048576
 cofem_status cofem_apply_dense_noalloc(const float* phi, long long N, long long D, long long ld,
                                        const float* V, int Q, const float* alpha, double beta,

@@ -592,6 +592,20 @@ cofem_status cofem_apply_operator(cofem_ctx* c, const float* V, int Q, const flo
     if (Q < 1 || Q > COFEM_QMAX) return fail(COFEM_ERR_INVALID_ARG, "need 1 <= Q <= %d", COFEM_QMAX);
     if (!std::isfinite(beta)) return fail(COFEM_ERR_NONFINITE, "beta is not finite");
     CK(cudaSetDevice(c->device));
+    float* out = Psi;
+    int out_kind = 0;   // 0 host, 1 device memory of this handle's device (or managed), 2 another device's
+    {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, Psi) != cudaSuccess) {
+            cudaGetLastError();
+        } else if (a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == c->device)) {
+            out_kind = 1;
+        } else if (a.type == cudaMemoryTypeDevice) {
+            out_kind = 2;
+        }
+    }
+    if (out_kind == 2)
+        return fail(COFEM_ERR_INVALID_ARG, "Psi is device memory of another device than the handle's (%d)", c->device);
     cofem_status st = ensure_workspace(c, Q);
     if (st) return st;
     // stage V (Q x D, stride D) into the padded P block and alpha into c->alpha
@@ -608,12 +622,7 @@ cofem_status cofem_apply_operator(cofem_ctx* c, const float* V, int Q, const flo
     s.stream = c->stream;
     launch_operator(s, c, Q, c->P, OP_PLAIN);
     if (s.err) return cuda_fail(s.err, "operator launch");
-    float* out = Psi;
-    const bool dev_out = [&] {
-        cudaPointerAttributes a;
-        if (cudaPointerGetAttributes(&a, Psi) != cudaSuccess) { cudaGetLastError(); return false; }
-        return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-    }();
+    const bool dev_out = out_kind == 1;
     if (!dev_out) out = c->X;   // stage in the X block (Q x D fits in Q x Dp)
     launch_plain_psi(c->stream, c, Q, c->P, c->alpha, beta, out);
     CK(cudaGetLastError());

@@ -6,6 +6,8 @@
 #include <cstdio>
 #include <mutex>
 
+#include <cuda.h>
+
 #include "cofem_internal.cuh"
 
 namespace {
@@ -16,38 +18,67 @@ __device__ __align__(256) float g_noalloc_T[COFEM_NOALLOC_MAX_ELEMS];
 
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_na_mu;
+// Per device: the scratch address and the CUDA context it was looked up in.
+// A device reset (cudaDeviceReset) ends that context and may move the array,
+// so the address is looked up again when the current context differs.
 float* g_na_scratch[NA_MAX_DEVICES] = {};
+CUcontext g_na_ctx[NA_MAX_DEVICES] = {};
+
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext*);
+
+// The current CUDA context of this thread (the runtime makes the device's
+// primary context current on its first call), through the driver entry point
+// the runtime hands out, so the library needs no link to libcuda.
+cofem_status na_current_context(CUcontext* out) {
+    static PfnCtxGetCurrent fn = nullptr;
+    if (!fn) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !f)
+            return cofem_set_error(COFEM_ERR_CUDA, "cuCtxGetCurrent is not available from the CUDA driver");
+        fn = (PfnCtxGetCurrent)f;
+    }
+    if (fn(out) != CUDA_SUCCESS) return cofem_set_error(COFEM_ERR_CUDA, "cuCtxGetCurrent failed");
+    return COFEM_OK;
+}
 
 // Device address of the scratch array on the current device.  The array's name
-// in host code is only a host-side stand-in, so the address is looked up once
-// per device with that device current.
-cofem_status na_scratch(float** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cofem_set_error(COFEM_ERR_CUDA, cudaGetErrorString(e));
+// in host code is only a host-side stand-in, so the address is looked up with
+// that device current: once per device and context.
+cofem_status na_scratch(int dev, float** out) {
     if (dev < 0 || dev >= NA_MAX_DEVICES) return cofem_set_error(COFEM_ERR_UNSUPPORTED, "device index too large");
+    // the runtime calls before this one (cudaGetDevice, cudaPointerGetAttributes)
+    // have made the device's primary context current on this thread
+    CUcontext ctx = nullptr;
+    cofem_status st = na_current_context(&ctx);
+    if (st) return st;
     std::lock_guard<std::mutex> lock(g_na_mu);
-    if (!g_na_scratch[dev]) {
+    if (!g_na_scratch[dev] || g_na_ctx[dev] != ctx) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_T);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_T);
         if (e != cudaSuccess) {
             char msg[160];
             snprintf(msg, sizeof(msg), "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
             return cofem_set_error(COFEM_ERR_CUDA, msg);
         }
         g_na_scratch[dev] = (float*)p;
+        g_na_ctx[dev] = ctx;
     }
     *out = g_na_scratch[dev];
     return COFEM_OK;
 }
 
-bool is_device_memory(const void* p) {
+// Device (or managed) memory that the current device `dev` can address: device
+// memory of another GPU is refused (it would fault without peer access).
+bool is_device_memory(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 constexpr int NA_QB = 8;     // columns per pass of the first kernel
@@ -129,16 +160,31 @@ extern "C" cofem_status cofem_apply_dense_noalloc(const float* phi, long long N,
         return cofem_set_error(COFEM_ERR_INVALID_ARG, msg);
     }
     if (!(beta == beta) || beta - beta != 0.0) return cofem_set_error(COFEM_ERR_NONFINITE, "beta is not finite");
-    if (!is_device_memory(phi) || !is_device_memory(V) || !is_device_memory(alpha) || !is_device_memory(Psi))
-        return cofem_set_error(COFEM_ERR_INVALID_ARG, "phi, V, alpha and Psi must be device memory");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cofem_set_error(COFEM_ERR_CUDA, cudaGetErrorString(e));
+    if (!is_device_memory(phi, dev) || !is_device_memory(V, dev) || !is_device_memory(alpha, dev) ||
+        !is_device_memory(Psi, dev))
+        return cofem_set_error(COFEM_ERR_INVALID_ARG,
+                               "phi, V, alpha and Psi must be device memory of the current device");
     float* T = nullptr;
-    cofem_status st = na_scratch(&T);
+    cofem_status st = na_scratch(dev, &T);
     if (st) return st;
+    // an error left by an earlier, unrelated launch on this thread is reported
+    // as such, not as a failure of these launches
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        char msg[200];
+        snprintf(msg, sizeof(msg), "a CUDA error was pending before this call: %s", cudaGetErrorString(e));
+        return cofem_set_error(COFEM_ERR_CUDA, msg);
+    }
     cudaStream_t s = (cudaStream_t)stream;
     k_na_phiv<<<(unsigned)N, 256, 0, s>>>(phi, N, D, ld, V, Q, T);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cofem_set_error(COFEM_ERR_CUDA, cudaGetErrorString(e));
     const dim3 grid2((unsigned)((D + 127) / 128), (unsigned)((Q + NA_QB2 - 1) / NA_QB2));
     k_na_psi<<<grid2, 128, 0, s>>>(phi, N, D, ld, T, Q, V, alpha, (float)beta, Psi);
-    const cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cofem_set_error(COFEM_ERR_CUDA, cudaGetErrorString(e));
     return COFEM_OK;
 }
