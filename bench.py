@@ -169,80 +169,109 @@ def _peaks():
     return 6800.0, 1900.0, "fallback"
 
 
+# Mean CG steps per EM iteration of the library's fit of each workload (the
+# benchmark line's cg_iters of the last fit).  The reference arm, which runs
+# no GPU fit, scales its timed CG steps to this count, as the cpu_baseline leg
+# of the main arm scales to the mean of the fit it has just timed; workloads
+# without an entry are scaled to cg_maxit.
+_CG_STEPS_MEAN = {
+    "dense_n256_d1024_k20": 72.8,
+    "dense_n2500_d10000_k32": 92.7,
+    "dense_n8192_d32768_k32_bf16": 163.0,
+    "toeplitz_d1e6_l256_k16": 400.0,
+}
+
+
+def _oracle_em_sample(op, prob, run, cap):
+    """One EM iteration of the FP64 oracle with its CG loop capped at `cap`
+    steps: (seconds, CG steps taken)."""
+    from oracle import cofem as oracle_cofem
+    t0 = time.perf_counter()
+    r = oracle_cofem(op, prob.y, prob.beta, run["K"], 1, run["cg_tol"], cap, run["seed"],
+                     rr_period=run["rr_period"], prior=run.get("prior", "gaussian"))
+    return time.perf_counter() - t0, max(1, int(r["cg_iters"][0]))
+
+
+def _oracle_cap(op, prob, run, budget_s):
+    """CG steps of one oracle EM iteration that fit in budget_s (at least 3)."""
+    t, steps = _oracle_em_sample(op, prob, run, 3)
+    per_cg = t / steps
+    return int(max(3, min(run["cg_maxit"], budget_s // max(per_cg, 1e-9))))
+
+
 def _cpu_baseline(prob, run, budget_s=20.0, avg_iters=None):
     """FP64 oracle on a bounded sample of the same fit.
 
-    avg_iters None: time the leading EM iterations that fit in the budget (at
-    least one).  Otherwise: time one EM iteration whose CG loop is capped to fit
-    the budget and scale its per-CG-step time to `avg_iters` steps per EM
-    iteration (the GPU fit's mean), since the CG steps dominate."""
+    If the whole fit fits in the budget, it is timed whole.  Otherwise one EM
+    iteration is run with its CG loop capped to the budget and its time per CG
+    step is scaled to `avg_iters` steps per EM iteration (the mean of the fit
+    being compared; cg_maxit if None), since the CG steps dominate."""
     from oracle import make_operator, cofem as oracle_cofem
     op = make_operator(prob.kind, prob.phi, prob.N)
     cores = len(os.sched_getaffinity(0))
-    if avg_iters is None:
-        # calibrate the cost of one CG step, then run one EM iteration with its
-        # CG loop capped to the budget
+    cap = _oracle_cap(op, prob, run, budget_s)
+    t1, steps = _oracle_em_sample(op, prob, run, cap)
+    per_cg = t1 / steps
+    mean = float(avg_iters) if avg_iters is not None else float(run["cg_maxit"])
+    if per_cg * mean * run["T"] <= budget_s:
         t0 = time.perf_counter()
-        r = oracle_cofem(op, prob.y, prob.beta, run["K"], 1, run["cg_tol"], 3, run["seed"],
-                         rr_period=run["rr_period"],
-                         prior=run.get("prior", "gaussian"))
-        per_cg = (time.perf_counter() - t0) / max(1, int(r["cg_iters"][0]))
-        cap = int(max(3, min(run["cg_maxit"], budget_s // max(per_cg, 1e-9))))
-        t0 = time.perf_counter()
-        r = oracle_cofem(op, prob.y, prob.beta, run["K"], 1, run["cg_tol"], cap, run["seed"],
-                         rr_period=run["rr_period"],
-                         prior=run.get("prior", "gaussian"))
-        t1 = time.perf_counter() - t0
-        steps = max(1, int(r["cg_iters"][0]))
-        if steps < cap or cap >= run["cg_maxit"]:   # a whole EM iteration ran
-            n = int(max(1, min(run["T"], budget_s // max(t1, 1e-9))))
-            if n > 1:
-                t0 = time.perf_counter()
-                oracle_cofem(op, prob.y, prob.beta, run["K"], n, run["cg_tol"], run["cg_maxit"], run["seed"],
-                             rr_period=run["rr_period"],
-                         prior=run.get("prior", "gaussian"))
-                t1 = time.perf_counter() - t0
-            return {"value": n / t1, "unit": "EM-iter/s", "cores": cores, "kind": "oracle",
-                    "sample": f"first {n} EM iteration(s) of the same fit, FP64 numpy/BLAS, {t1:.1f} s"}
-        t_em = t1 * run["cg_maxit"] / steps
-        return {"value": 1.0 / t_em, "unit": "EM-iter/s", "cores": cores, "kind": "oracle",
-                "sample": f"one EM iteration with CG capped at {steps} steps ({t1:.1f} s, FP64 numpy/BLAS), "
-                          f"per-step time scaled to cg_maxit = {run['cg_maxit']} steps"}
-    t0 = time.perf_counter()
-    r = oracle_cofem(op, prob.y, prob.beta, run["K"], 1, run["cg_tol"], 3, run["seed"], rr_period=run["rr_period"],
-                         prior=run.get("prior", "gaussian"))
-    per_cg = (time.perf_counter() - t0) / max(1, int(r["cg_iters"][0]))
-    cap = int(max(3, min(run["cg_maxit"], budget_s // max(per_cg, 1e-9))))
-    t0 = time.perf_counter()
-    r = oracle_cofem(op, prob.y, prob.beta, run["K"], 1, run["cg_tol"], cap, run["seed"], rr_period=run["rr_period"],
-                         prior=run.get("prior", "gaussian"))
-    t1 = time.perf_counter() - t0
-    steps = max(1, int(r["cg_iters"][0]))
-    t_em = t1 * float(avg_iters) / steps
-    return {"value": 1.0 / t_em, "unit": "EM-iter/s", "cores": cores, "kind": "oracle",
+        oracle_cofem(op, prob.y, prob.beta, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], run["seed"],
+                     rr_period=run["rr_period"], prior=run.get("prior", "gaussian"))
+        tf = time.perf_counter() - t0
+        return {"value": run["T"] / tf, "unit": "EM-iter/s", "cores": cores, "kind": "oracle",
+                "sample": f"the whole fit ({run['T']} EM iterations), FP64 numpy/BLAS, {tf:.1f} s"}
+    return {"value": 1.0 / (per_cg * mean), "unit": "EM-iter/s", "cores": cores, "kind": "oracle",
             "sample": f"one EM iteration of the same fit, {steps} CG steps in {t1:.1f} s (FP64 numpy/BLAS), "
-                      f"per-step time scaled to {float(avg_iters):.0f} steps (the GPU fit's mean per EM iteration)"}
+                      f"per-step time scaled to {mean:.0f} steps per EM iteration "
+                      f"({'the GPU fit' + chr(39) + 's mean' if avg_iters is not None else 'cg_maxit'})"}
+
+
+def _config(name, prob, run, args, **extra):
+    """The `config` object of a bench line (the same keys in both arms)."""
+    cfg = {"workload": name, "N": prob.N, "D": prob.D, "K": run["K"], "T": run["T"], "cg_tol": run["cg_tol"],
+           "cg_maxit": run["cg_maxit"], "rr_period": run["rr_period"], "prior": args.prior}
+    cfg.update(extra)
+    return cfg
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on the host cores.  Each step is
+    one EM iteration of the workload's fit with its CG loop capped so that the
+    --steps steps take about --cpu-budget seconds; the warm-up steps calibrate
+    the cap.  value = EM iterations per second, each EM iteration counted as
+    the workload's mean CG steps (_CG_STEPS_MEAN, else cg_maxit)."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
+    from oracle import make_operator
     name = args.workload
     spec = WORKLOADS[name]
     prob, run = workload(name)
     run["prior"] = args.prior
-    vals = []
-    base = None
-    for _ in range(max(1, args.steps)):
-        base = _cpu_baseline(prob, run, budget_s=max(1.0, args.cpu_budget / max(1, args.steps)))
-        vals.append(base["value"])
-    v = float(np.mean(vals))
+    op = make_operator(prob.kind, prob.phi, prob.N)
+    cores = len(os.sched_getaffinity(0))
+    steps = max(1, args.steps)
+    cap = _oracle_cap(op, prob, run, max(0.5, args.cpu_budget / steps))
+    for _ in range(args.warmup):
+        _oracle_em_sample(op, prob, run, 3)
+    times, cgs = [], []
+    for _ in range(steps):
+        t, u = _oracle_em_sample(op, prob, run, cap)
+        times.append(t)
+        cgs.append(u)
+    total = float(np.sum(times))
+    mean = _CG_STEPS_MEAN.get(name, float(run["cg_maxit"]))
+    v = float(np.sum(cgs)) / mean / total      # EM iterations of work per second
+    sample = (f"{steps} samples of one EM iteration with the CG loop capped at {cap} steps "
+              f"({int(np.sum(cgs))} CG steps in {total:.1f} s, FP64 numpy/BLAS), each EM iteration counted as "
+              f"{mean:.0f} CG steps ({'the library fit' + chr(39) + 's mean' if name in _CG_STEPS_MEAN else 'cg_maxit'})")
     line = {"impl": "reference", "metric": _metric_name(name, spec), "value": v, "unit": "EM-iter/s",
-            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * run["T"] / v,
+            "n_gpus": ws, "steps": steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": name},
-            "cpu_baseline": dict(base, value=v),
+            "data": "synthetic",
+            "config": _config(name, prob, run, args, l2="host memory (no GPU caches)",
+                              cg_iters_last_fit=[int(u) for u in cgs], launch="host: FP64 numpy/BLAS"),
+            "cpu_baseline": {"value": v, "unit": "EM-iter/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "EM-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -395,12 +424,12 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": run["precision"], "data": "synthetic",
-        "config": {"workload": name, "N": N, "D": D, "K": K, "T": T, "cg_tol": tol, "cg_maxit": maxit,
-                   "rr_period": run["rr_period"], "prior": args.prior, "l2": "inputs larger than L2" if prob.kind == "dense" and
-                   N * D * (2 if prec == cf.COFEM_BF16 else 4) > 129e6 else "L2 not flushed between fits",
-                   "cg_iters_last_fit": [int(v) for v in all_iters[-1]],
-                   "launch": "cuda graph, programmatic edges" if graph_overlap else
-                   ("cuda graph" if not args.no_graph else "host loop")},
+        "config": _config(name, prob, run, args,
+                          l2="inputs larger than L2" if prob.kind == "dense" and
+                          N * D * (2 if prec == cf.COFEM_BF16 else 4) > 129e6 else "L2 not flushed between fits",
+                          cg_iters_last_fit=[int(v) for v in all_iters[-1]],
+                          launch="cuda graph, programmatic edges" if graph_overlap else
+                          ("cuda graph" if not args.no_graph else "host loop")),
         "nmse_db": nmse, "flags": flags,
         "roofline": roof, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk,
@@ -542,7 +571,7 @@ def _parser():
                     help="only the serving measurement (2000 requests unless --serve-requests is given)")
     ap.add_argument("--serve-precision", default="bf16", choices=["f32", "bf16", "tf32x3", "fp8"])
     ap.add_argument("--cpu-budget", type=float, default=60.0,
-                    help="seconds of oracle time the reference arm samples in total")
+                    help="seconds of oracle time the reference arm's timed steps take in total")
     ap.add_argument("--dense-path", default="auto", choices=sorted(_DENSE_PATHS),
                     help="BF16 dense operator form (default: the library's choice)")
     ap.add_argument("--em-iters", type=int, default=0,

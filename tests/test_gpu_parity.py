@@ -3,9 +3,11 @@ same seeded inputs and the same Philox probes.
 
 Tolerances: probes are bit-exact (integer work); operator applications are
 compared per column in relative l2 (FP32 accumulation over up to N*D terms,
-bound 2e-5); whole fits use relative l2 <= 1e-4 on mu and <= 1e-3 on s and on
+bound 2e-5); whole fits use relative l2 <= 1e-4 on mu and <= 1e-3 on s, on
 the second moment 1/alpha = max(mu^2 + s, 1/alpha_max) (the quantity the M-step
-forms; alpha itself near the clamp is the reciprocal of a small difference)."""
+forms) and on alpha itself where it is well determined (alpha < 1e6 and
+mu^2 + s not a cancelling difference; elsewhere alpha is the reciprocal of a
+small difference)."""
 import numpy as np
 import pytest
 
@@ -96,9 +98,22 @@ def oracle_fit(prob, K, T, tol, maxit, seed=2, phi=None, **kw):
     return oracle_cofem(op, prob.y, prob.beta, K, T, tol, maxit, seed, **kw)
 
 
+def well_determined(r):
+    """Coordinates where alpha = 1/max(mu^2 + s, 1/alpha_max) is well
+    conditioned: alpha < 1e6 and mu^2 + s >= 0.1 (mu^2 + |s|)."""
+    mu, s_ = np.asarray(r["mu"], np.float64), np.asarray(r["s"], np.float64)
+    return (r["alpha"] < 1e6) & (1.0 / r["alpha"] >= 0.1 * (mu * mu + np.abs(s_)))
+
+
 def assert_fit_close(g, r, tol_mu=1e-4, tol_s=1e-3, tol_a=1e-3):
-    e = (rel(g["mu"], r["mu"]), rel(g["s"], r["s"]), rel(1.0 / g["alpha"], 1.0 / r["alpha"]))
-    assert e[0] <= tol_mu and e[1] <= tol_s and e[2] <= tol_a, (e, g["cg_iters"], r["cg_iters"])
+    """mu, s and 1/alpha everywhere, and alpha itself where it is well
+    determined: coordinates the oracle keeps active (alpha < 1e6) whose second
+    moment mu^2 + s is not a cancelling difference (at least a tenth of
+    mu^2 + |s|; with few probes s can be negative and large)."""
+    act = well_determined(r)
+    e = (rel(g["mu"], r["mu"]), rel(g["s"], r["s"]), rel(1.0 / g["alpha"], 1.0 / r["alpha"]),
+         rel(g["alpha"][act], r["alpha"][act]) if act.any() else 0.0)
+    assert e[0] <= tol_mu and e[1] <= tol_s and e[2] <= tol_a and e[3] <= tol_a, (e, g["cg_iters"], r["cg_iters"])
     return e
 
 
