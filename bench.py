@@ -276,17 +276,16 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _launches_per_fit(cg_iters, rr_period, op_cg, op_rr, step):
+def _launches_per_fit(cg_iters, op_cg, step, n_rr=0, n_check=0, op_rr=0, graph=True):
     """Kernels of one fit: b = beta Phi^T y, finiteness check of y, fit set-up;
     per EM iteration init + M-step; per CG step the operator kernels (op_cg)
     and the update/direction kernels (step); per residual replacement the
-    operator kernels (op_rr) and the residual."""
+    accurate residual (op_rr kernels); per true-residual check the accurate
+    residual, the check kernel and (in the graph) the CG loop's gate."""
     n = 3
     for u in cg_iters:
-        u = int(u)
-        rr = u // rr_period if rr_period > 0 else 0
-        n += 2 + (op_cg + step) * u + (op_rr + 1) * rr
-    return n
+        n += 2 + (op_cg + step) * int(u)
+    return n + op_rr * n_rr + (op_rr + 1 + (1 if graph else 0)) * n_check
 
 
 def run_ours(args):
@@ -305,6 +304,8 @@ def run_ours(args):
     run["prior"] = args.prior
     if args.em_iters > 0:
         run["T"] = args.em_iters
+    if args.rr_period >= 0:
+        run["rr_period"] = args.rr_period
     K, T, tol, maxit = run["K"], run["T"], run["cg_tol"], run["cg_maxit"]
     D, N = prob.D, prob.N
     stream = torch.cuda.Stream(device=dev)
@@ -316,8 +317,9 @@ def run_ours(args):
     outs = [torch.empty(D, device=dev) for _ in range(3)]
     iters = torch.empty(T, dtype=torch.int32, device=dev)
 
-    def make(precision):
-        return cf.CoFEM(N, D, kind, phi_d, prob.L, precision=precision, rr_period=run["rr_period"],
+    def make(precision, rr_period=None):
+        rr = run["rr_period"] if rr_period is None else rr_period
+        return cf.CoFEM(N, D, kind, phi_d, prob.L, precision=precision, rr_period=rr,
                         seed=run["seed"], stream=stream, use_graph=0 if args.no_graph else 1,
                         dense_path=_DENSE_PATHS[args.dense_path], overlap_launch=0 if args.no_overlap else 1,
                         prior=cf.COFEM_PRIOR_RECTIFIED if args.prior == "rectified" else cf.COFEM_PRIOR_GAUSSIAN)
@@ -332,19 +334,20 @@ def run_ours(args):
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         flags = 0
-        all_iters = []
+        all_iters, stats = [], []
         for _ in range(steps):
             flags |= cf.cofem_fit(model.h, y_d, prob.beta, None, K, T, tol, maxit, *outs, iters)
             all_iters.append(iters.cpu().numpy().copy())
+            stats.append(cf.cofem_fit_stats(model.h))
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         ms = ev0.elapsed_time(ev1)
-        return ms, flags, all_iters
+        return ms, flags, all_iters, stats
 
     clocks = Clocks(local)
     model = make(prec)
     clocks.start()
-    ms, flags, all_iters = timed_fits(model, args.steps, args.warmup)
+    ms, flags, all_iters, fit_stats = timed_fits(model, args.steps, args.warmup)
     clk = clocks.stop()
     t_max = _aggregate_over_ranks(ms, ws, dist if ws > 1 else None, dev)
     value = ws * args.steps * T / (t_max / 1000.0)
@@ -396,8 +399,26 @@ def run_ours(args):
     e2e = {"value": ws * e2e_steps * T / e2e_s, "unit": "EM-iter/s", "h2d_bytes_per_step": int(N * 4),
            "d2h_bytes_per_step": int(3 * D * 4 + T * 4 + 4)}
 
-    launches = sum(_launches_per_fit(it, run["rr_period"], op_cg, op_rr, op_step) for it in all_iters)
+    launches = sum(_launches_per_fit(it, op_cg, op_step, nr, nc, op_rr, not args.no_graph)
+                   for it, (nr, nc) in zip(all_iters, fit_stats))
+    precision_form = None
+    if run["rr_period"] > 0:
+        res = cf.cofem_true_residuals(model.h, T, K)
+        precision_form = {"rr_period": run["rr_period"], "true_res_max": float(np.nanmax(res)),
+                          "true_res_max_last_estep": float(np.nanmax(res[-1])),
+                          "columns_above_10tol": int(np.sum(res > 10 * tol)),
+                          "replacements_last_fit": fit_stats[-1][0], "checks_last_fit": fit_stats[-1][1]}
     model.close()
+
+    # the same fit without residual replacement (recursive residuals only)
+    rr_off = None
+    if run["rr_period"] > 0 and not args.no_rr_off:
+        m0 = make(prec, rr_period=0)
+        ms0, f0, it0, _ = timed_fits(m0, 3, 1)
+        rr_off = {"value": 3 * T / (ms0 / 1000.0), "unit": "EM-iter/s", "rr_period": 0,
+                  "nmse_db": _nmse_db(outs[0].cpu().numpy(), prob.z), "flags": f0,
+                  "cg_iters_last_fit": [int(v) for v in it0[-1]]}
+        m0.close()
 
     # the FP32 forms on the same problem (precision comparison at equal NMSE):
     # tensor-core 3xTF32 and plain FP32 FMA
@@ -406,7 +427,7 @@ def run_ours(args):
         fp32 = {}
         for key, form in (("tf32x3", cf.COFEM_F32_TF32X3), ("f32_fma", cf.COFEM_F32)):
             m32 = make(form)
-            ms32, f32flags, _ = timed_fits(m32, 1, 1)
+            ms32, f32flags, _, _ = timed_fits(m32, 1, 1)
             nm32 = _nmse_db(outs[0].cpu().numpy(), prob.z)
             op32 = cf.cofem_time_operator(m32.h, Q, 10)
             m32.close()
@@ -414,7 +435,7 @@ def run_ours(args):
                          "operator_ms": op32, "flags": f32flags}
         # the FP8 E4M3 storage variant (per-row scales) on the same problem
         m8 = make(cf.COFEM_FP8_E4M3)
-        ms8, f8flags, _ = timed_fits(m8, 1, 1)
+        ms8, f8flags, _, _ = timed_fits(m8, 1, 1)
         fp8 = {"value": T / (ms8 / 1000.0), "unit": "EM-iter/s", "nmse_db": _nmse_db(outs[0].cpu().numpy(), prob.z),
                "operator_ms": cf.cofem_time_operator(m8.h, Q, 10), "flags": f8flags}
         m8.close()
@@ -434,6 +455,10 @@ def run_ours(args):
         "roofline": roof, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk,
     }
+    if precision_form is not None:
+        line["precision_form"] = precision_form
+    if rr_off is not None:
+        line["rr_off"] = rr_off
     if fp32 is not None:
         line["fp32_form"] = fp32
         line["fp8_form"] = fp8
@@ -556,6 +581,36 @@ def run_operator_only(args):
                       "ms_per_apply": ms}))
 
 
+def run_fig3b(args):
+    """The preconditioner study of Sec. V (Fig. 3b setting) on the GPU path:
+    the DCT dictionary (N = D/3 random rows of Omega^-1), 5 % spikes N(0, 25),
+    sigma = 0.01, K = 20, CG tolerance 1e-4, T EM iterations; CG steps of the
+    E-steps 1, 10, 50 and 100 with the Jacobi preconditioner and without one
+    (M = I), NRMSE and fit time per D.  One JSON line."""
+    import torch
+    import paper_2105_10439_gb300 as cf
+    from synth import dct_sparse
+    torch.cuda.set_device(0)
+    T = max(1, args.em_iters) if args.em_iters > 0 else 100
+    rows_out = []
+    for D in (1024, 4096, 16384, 32768):
+        p = dct_sparse(D, D // 3, int(0.05 * D), 0.01, seed=D)
+        for name, pre in (("jacobi", cf.COFEM_PRECOND_JACOBI), ("none", cf.COFEM_PRECOND_NONE)):
+            mu, s, al = (np.empty(D, np.float32) for _ in range(3))
+            it = np.empty(T, np.int32)
+            with cf.CoFEM(p.N, D, cf.COFEM_OP_DCT, p.rows, precond=pre) as m:
+                cf.cofem_fit(m.h, p.y, p.beta, None, 20, T, 1e-4, 1000, mu, s, al, it)   # warm-up
+                t0 = time.perf_counter()
+                flags = cf.cofem_fit(m.h, p.y, p.beta, None, 20, T, 1e-4, 1000, mu, s, al, it)
+                wall = time.perf_counter() - t0
+            rows_out.append({"D": D, "N": p.N, "precond": name, "flags": flags, "fit_s": wall,
+                             "em_iters_per_s": T / wall,
+                             "cg_steps_at": {str(t): int(it[t - 1]) for t in (1, 10, 50, 100) if t <= T},
+                             "cg_steps_total": int(it.sum()),
+                             "nrmse": float(np.linalg.norm(mu - p.z) / np.linalg.norm(p.z))})
+    print(json.dumps({"fig3b": rows_out, "T": T, "K": 20, "cg_tol": 1e-4, "dictionary": "DCT, N = D/3"}), flush=True)
+
+
 def _parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -564,6 +619,10 @@ def _parser():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp32-form", action="store_true")
+    ap.add_argument("--no-rr-off", action="store_true",
+                    help="skip the comparison fit without residual replacement")
+    ap.add_argument("--rr-period", type=int, default=-1,
+                    help="override the workload's residual-replacement period (0 = off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the serving measurement added to the line (0 = skip)")
@@ -582,6 +641,8 @@ def _parser():
                     help="M-step prior: Gaussian (Alg. 1) or rectified Gaussian (non-negativity)")
     ap.add_argument("--no-overlap", action="store_true",
                     help="plain stream order for the CG-step kernels (no programmatic dependent launch)")
+    ap.add_argument("--fig3b", action="store_true",
+                    help="the preconditioner study (DCT dictionary, CG steps vs D with and without Jacobi)")
     ap.add_argument("--operator-only", action="store_true",
                     help="apply only the operator A V (Q = K+1 columns) --steps times; for profilers")
     return ap
@@ -599,6 +660,8 @@ def main():
                           "value": rep["at_80pct"]["p99_ms"], "unit": "ms (p99)"}), flush=True)
     elif args.operator_only:
         run_operator_only(args)
+    elif args.fig3b:
+        run_fig3b(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -56,6 +56,8 @@ typedef int cofem_status;
 #define COFEM_OP_DENSE     0  /* explicit N x D matrix, row-major (Phi_ij at phi[i*D + j]) */
 #define COFEM_OP_TOEPLITZ  1  /* causal convolution, N = D: (Phi v)_i = sum_{tau<L} h[tau] v[i-tau];
                                  column j of Phi is h delayed by j and truncated at N (Sec. V-A, VI-A) */
+#define COFEM_OP_DCT       2  /* Phi = M Omega^-1: N rows of the inverse orthonormal DCT-II of size D
+                                 (Sec. V-A "DCT"); created with cofem_create_dct */
 
 /* Storage / multiply precision of a dense Phi (the CG state is always FP32,
  * CG inner products always FP64). */
@@ -78,6 +80,8 @@ typedef int cofem_status;
 /* Preconditioner theta (Sec. III-C): M = diag(beta theta + alpha). */
 #define COFEM_PRECOND_JACOBI 0  /* theta_j = sum_i Phi_ij^2  (M_jj = A_jj) */
 #define COFEM_PRECOND_ONE    1  /* theta_j = 1 (the paper's experiments, Sec. V-C) */
+#define COFEM_PRECOND_NONE   2  /* M = I: unpreconditioned CG (the comparison of the paper's
+                                   preconditioner study, Sec. V empirical insights, Fig. 3b) */
 
 /* CG stopping rule (Alg. 2). */
 #define COFEM_CONV_PER_COLUMN 0  /* column q stops (and is frozen) once ||r_q|| <= tol ||b_q|| */
@@ -105,8 +109,13 @@ typedef struct cofem_opts {
                                  last three dense only) */
     int precond;              /* COFEM_PRECOND_JACOBI | COFEM_PRECOND_ONE */
     int conv;                 /* COFEM_CONV_PER_COLUMN | COFEM_CONV_FROBENIUS */
-    int rr_period;            /* residual replacement R <- B - A X every rr_period CG
-                                 iterations (0 = off) */
+    int rr_period;            /* precision form (0 = off): every rr_period CG iterations the
+                                 active columns take R <- B - A X computed accurately (FP32
+                                 pairs, about 2^-48 relative, see cofem_true_residuals),
+                                 with X held as an exact FP32 pair; and when the CG loop
+                                 ends, every column's true residual is checked against
+                                 cg_tol: a column that misses it restarts from that
+                                 residual (P <- M^-1 R) and CG goes on within cg_maxit */
     double alpha_max;         /* alpha_j = 1 / max(mu_j^2 + s_j, 1/alpha_max); default 1e12 */
     unsigned long long seed;  /* probe seed: p_{t,k,j} from Philox4x64-10 with key (seed, 0),
                                  counter (j >> 8, k, t, 0), bit j & 255 (1 -> -1, 0 -> +1) */
@@ -124,6 +133,11 @@ typedef struct cofem_opts {
                                  finishes; data dependences still wait for completion);
                                  0: plain stream order */
     int prior;                /* COFEM_PRIOR_GAUSSIAN (default) | COFEM_PRIOR_RECTIFIED */
+    int check_residual;       /* 1: measure every column's true relative residual
+                                 ||B - A X|| / ||B|| (accurately, as for rr_period) when
+                                 each E-step's CG loop ends, without acting on it; read it
+                                 with cofem_true_residuals.  X is then held as the FP32
+                                 pair as well.  0 (default): only when rr_period > 0. */
 } cofem_opts;
 
 /* Dense BF16 operator forms.  TWO_PASS streams the dictionary for Phi V and a
@@ -142,13 +156,13 @@ typedef struct cofem_opts {
 
 /* Fill *o with the defaults: F32, Jacobi, per-column, rr_period 0,
  * alpha_max 1e12, seed 2, stream NULL, use_graph 1, dense_path AUTO, max_sms 0,
- * overlap_launch 1, prior GAUSSIAN. */
+ * overlap_launch 1, prior GAUSSIAN, check_residual 0. */
 void cofem_default_opts(cofem_opts* o);
 
 /* Create a handle for one dictionary (step a0: upload, optional BF16
  * quantisation, theta).
  *   N, D   : Phi is N x D (TOEPLITZ: N must equal D).  1 <= N, D <= 2^31 - 1.
- *   kind   : COFEM_OP_DENSE or COFEM_OP_TOEPLITZ.
+ *   kind   : COFEM_OP_DENSE or COFEM_OP_TOEPLITZ (a DCT dictionary: cofem_create_dct).
  *   phi    : DENSE: N*D floats, row-major; TOEPLITZ: the filter h[0..L).
  *            Host or device; copied (and quantised) into memory the handle owns.
  *   L      : TOEPLITZ filter length, 1 <= L <= 1024 and L <= N; must be 0 for DENSE.
@@ -157,6 +171,21 @@ void cofem_default_opts(cofem_opts* o);
  * NaN/Inf, NOMEM, CUDA, UNSUPPORTED (no sm_103a device). */
 cofem_status cofem_create(struct cofem_ctx** out, long long N, long long D, int kind,
                           const float* phi, long long L, const cofem_opts* opts);
+
+/* Create a handle for the DCT dictionary of Sec. V-A: Phi = M Omega^-1, Omega
+ * the orthonormal DCT-II of size D (Omega_kn = c_k cos(pi k (2n+1) / 2D),
+ * c_0 = sqrt(1/D), c_k = sqrt(2/D)), M keeping the N rows rows[0..N) of
+ * Omega^-1 v = Omega^T v.  Phi is never formed: Phi v and Phi^T u are a
+ * DCT-III and a DCT-II of length D, each a complex FFT of length D/2 in one
+ * thread block's shared memory, O(D log D) per column.
+ *   D    : a power of two, 16 <= D <= 32768.
+ *   rows : N distinct indices in [0, D), 1 <= N <= D (host or device ints).
+ *   opts : precision COFEM_F32 only; rr_period and check_residual must be 0
+ *          (UNSUPPORTED otherwise).
+ * Errors: INVALID_ARG (sizes, repeated or out-of-range rows), UNSUPPORTED,
+ * NOMEM, CUDA. */
+cofem_status cofem_create_dct(struct cofem_ctx** out, long long N, long long D, const int* rows,
+                              const cofem_opts* opts);
 
 /* Run one CoFEM fit (Alg. 1 with Alg. 2): steps a1-a8 of the hot path.
  *   y         : N floats (host or device).
@@ -177,6 +206,27 @@ cofem_status cofem_create(struct cofem_ctx** out, long long N, long long D, int 
 cofem_status cofem_fit(struct cofem_ctx* h, const float* y, double beta, const float* alpha0,
                        int K, int T_em, double cg_tol, int cg_maxit,
                        float* mu, float* s, float* alpha, int* cg_iters, unsigned* flags);
+
+/* Multi-task CoFEM (the multi-task subsection of Sec. III) with the handle's
+ * dictionary shared by the L tasks (multiple measurement vectors): the tasks
+ * share alpha (and beta), and their L (K+1) systems, task l's columns being
+ * l (K+1) .. l (K+1) + K, are solved together by one batched Alg. 2 with the
+ * shared preconditioner M = beta theta + alpha and per-column stopping.  Each
+ * task draws its own probes (the counter's last word is l; task 0 draws the
+ * probes of cofem_fit).  M-step: alpha_j = L / sum_l (mu_lj^2 + s_lj), floored
+ * at 1/alpha_max.
+ *   L         : tasks, >= 1, with L (K+1) <= 64 (K >= 1).
+ *   Y         : L x N floats, row l = y_l (host or device).
+ *   mu, s     : L x D floats each, row l = task l (host or device).
+ *   alpha     : D floats: the shared alpha^(T_em).
+ *   cg_iters  : T_em ints or NULL: CG iterations of each E-step's batched
+ *               loop (the largest over the tasks' columns).
+ * Everything else as cofem_fit; L = 1 is cofem_fit.  Errors: as cofem_fit,
+ * and UNSUPPORTED for L > 1 with the rectified prior (its multi-task M-step
+ * is not defined here). */
+cofem_status cofem_fit_multitask(struct cofem_ctx* h, int L, const float* Y, double beta, const float* alpha0,
+                                 int K, int T_em, double cg_tol, int cg_maxit, float* mu, float* s,
+                                 float* alpha, int* cg_iters, unsigned* flags);
 
 /* Release the handle and all memory it owns.  NULL is accepted. */
 cofem_status cofem_destroy(struct cofem_ctx* h);
@@ -326,12 +376,31 @@ cofem_status cofem_get_dictionary(struct cofem_ctx* h, float* out);
  * COFEM_PATH_SINGLE_PASS for a BF16 or 3xTF32 dense dictionary, COFEM_PATH_AUTO
  * (0) for the CUDA-core forms (FP32 FMA, convolution); *kernels_cg = kernels
  * launched per operator application inside the CG loop; *kernels_rr = per
- * application in a residual replacement; *kernels_step = kernels of the CG
+ * accurate residual (a residual replacement or a true-residual check); *kernels_step = kernels of the CG
  * update, stopping test and direction per CG step (2).  Any output pointer
  * may be NULL.  Errors:
  * INVALID_ARG (NULL handle, or no fit or application yet). */
 cofem_status cofem_operator_info(struct cofem_ctx* h, int* path, int* kernels_cg, int* kernels_rr,
                                  int* kernels_step);
+
+/* True relative residuals of the last fit (precision form, Alg. 2 stopping
+ * test applied to the returned X): out[t * (K+1) + q] = ||b_q - A x_q|| / ||b_q||
+ * for EM iteration t (0-based) and column q (0 = mu), with A = beta Phi~^T Phi~
+ * + diag(alpha^(t)) on the dictionary the handle computes with, measured on the
+ * GPU when the E-step's CG loop ended (after the last restart): A X from the
+ * FP32 pair X + Xlo with compensated FP32-pair products (TwoProduct and
+ * TwoSum, about 2^-48 relative error) and FP64 partial sums.  0 for a zero
+ * right-hand side.  out: host, T_em * (K+1) doubles of the last cofem_fit.
+ * Errors: INVALID_ARG (NULL, no fit yet, or a handle with rr_period = 0 and
+ * check_residual = 0), CUDA. */
+cofem_status cofem_true_residuals(struct cofem_ctx* h, double* out);
+
+/* Counts of the last fit's precision-form steps: *replacements = residual
+ * replacements (each one accurate residual, cofem_operator_info's
+ * kernels_rr launches), *checks = true-residual checks (each one accurate
+ * residual, one check kernel and, in the CUDA graph, one loop-gate kernel).
+ * Either pointer may be NULL.  Errors: INVALID_ARG (NULL handle, no fit). */
+cofem_status cofem_fit_stats(struct cofem_ctx* h, int* replacements, int* checks);
 
 /* The fit graph of the handle (use_graph = 1): *built = 1 once a fit has
  * recorded it, else 0; *overlapped = 1 if its CG-step kernels are joined by

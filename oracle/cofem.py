@@ -40,7 +40,13 @@ garbled or at odds with itself):
 11. Residual replacement (precision form, rr_period > 0): when the iteration
     count u is a multiple of rr_period, right after the X, R update the still
     active columns take R <- B - A X before the stopping test, then W, rho and
-    P continue from that R.
+    P continue from that R (P is kept, as in van der Vorst and Ye's reliable
+    updates).  With replacement (or check_residual) the CG loop's end is
+    verified: every column's true residual B - A X meets the stopping test, or
+    the column restarts from it (R <- B - A X, P <- M^-1 R) and the loop goes
+    on within the same budget of maxit steps; the true residuals of the
+    returned X are reported.  (In FP64 the recursive residual stays close to
+    the true one, so the check rarely restarts anything here.)
 12. Non-negativity (prior="rectified", the rectified Gaussian prior of the
     non-negativity subsection): the M-step takes alpha_j = 1 / E[z_j^2] with
     E[z_j^2] the second moment of N(mu_j, Sigma_jj) truncated to z_j >= 0,
@@ -85,11 +91,27 @@ def diag_estimate_general(P, X):
     return np.sum(P * X, axis=1) / np.sum(P * P, axis=1)
 
 
-def pcg(apply_a, B, minv, tol, maxit, conv="per_column", rr_period=0, history=None):
+def _meets_tol(rnorm, bnorm, tol, conv):
+    """Alg. 2 stopping test on residual norms: per column, or the printed
+    Frobenius test applied to all columns at once."""
+    if conv == "per_column":
+        return rnorm <= tol * bnorm
+    if conv == "frobenius":
+        ok = np.linalg.norm(rnorm) <= tol * np.linalg.norm(bnorm)
+        return np.full(rnorm.shape, ok)
+    raise ValueError(conv)
+
+
+def pcg(apply_a, B, minv, tol, maxit, conv="per_column", rr_period=0, history=None, check=False, info=None):
     """Alg. 2 (ParallelConjGradient) on the D x Q block B with M^-1 = diag(minv).
 
     Returns (X, iters, flags).  `history`, if a list, receives a copy of X after
-    every iteration (for convergence-bound tests)."""
+    every iteration (for convergence-bound tests).  check (reading 11): when
+    the loop ends, every column's true residual B - A X is tested against tol;
+    a column that misses it (not broken down, budget left) restarts from it
+    with P = M^-1 R and the loop goes on.  `info`, if a dict, receives
+    "true_res", the relative true residuals ||b_q - A x_q|| / ||b_q|| of the
+    returned X (when check is set)."""
     B = np.asarray(B, dtype=np.float64)
     D, Q = B.shape
     minv = np.asarray(minv, dtype=np.float64)[:, None]
@@ -99,54 +121,70 @@ def pcg(apply_a, B, minv, tol, maxit, conv="per_column", rr_period=0, history=No
     P = W.copy()
     rho = np.sum(R * W, axis=0)
     bnorm = np.linalg.norm(B, axis=0)
-    bnorm_f = np.linalg.norm(B)
     active = bnorm > 0.0
+    broken = np.zeros(Q, dtype=bool)
     flags = 0
     u = 0
-    while u < maxit and active.any():
-        Psi = apply_a(P)                                   # Apply matrix
-        pi = np.sum(P * Psi, axis=0)
-        a = active
-        # a CG step needs a positive, finite p^T A p (A symmetric positive
-        # definite); any other value freezes the column (breakdown)
-        bad = a & ~((pi > 0.0) & np.isfinite(pi))
-        if np.any(bad):
-            flags |= FLAG_BREAKDOWN
-            active = active & ~bad
+    true_res = None
+    while True:
+        while u < maxit and active.any():
+            Psi = apply_a(P)                                   # Apply matrix
+            pi = np.sum(P * Psi, axis=0)
             a = active
-        gamma = np.zeros(Q)
-        gamma[a] = rho[a] / pi[a]
-        X[:, a] += P[:, a] * gamma[a]
-        R[:, a] -= Psi[:, a] * gamma[a]
-        u += 1
-        if rr_period > 0 and u % rr_period == 0:
-            R[:, a] = (B - apply_a(X))[:, a]               # residual replacement
-        if conv == "per_column":
-            delta = np.full(Q, np.inf)
-            delta[a] = np.linalg.norm(R[:, a], axis=0) / bnorm[a]
-            active = active & ~(delta <= tol)
-        elif conv == "frobenius":
-            if np.linalg.norm(R) / bnorm_f <= tol:
-                active = np.zeros(Q, dtype=bool)
-        else:
-            raise ValueError(conv)
-        a = active
-        W = minv * R                                       # Apply preconditioner
-        rho_new = np.sum(R * W, axis=0)
-        eta = np.zeros(Q)
-        eta[a] = rho_new[a] / rho[a]
-        P[:, a] = W[:, a] + P[:, a] * eta[a]
-        rho[a] = rho_new[a]
-        if history is not None:
-            history.append(X.copy())
+            # a CG step needs a positive, finite p^T A p (A symmetric positive
+            # definite); any other value freezes the column (breakdown)
+            bad = a & ~((pi > 0.0) & np.isfinite(pi))
+            if np.any(bad):
+                flags |= FLAG_BREAKDOWN
+                broken |= bad
+                active = active & ~bad
+                a = active
+            gamma = np.zeros(Q)
+            gamma[a] = rho[a] / pi[a]
+            X[:, a] += P[:, a] * gamma[a]
+            R[:, a] -= Psi[:, a] * gamma[a]
+            u += 1
+            if rr_period > 0 and u % rr_period == 0:
+                R[:, a] = (B - apply_a(X))[:, a]               # residual replacement
+            rn = np.full(Q, np.inf)
+            rn[a] = np.linalg.norm(R[:, a], axis=0)
+            if conv == "frobenius":   # the printed test: all columns' residuals together
+                rn = np.linalg.norm(R, axis=0)
+            active = active & ~_meets_tol(rn, bnorm, tol, conv)
+            a = active
+            W = minv * R                                       # Apply preconditioner
+            rho_new = np.sum(R * W, axis=0)
+            eta = np.zeros(Q)
+            eta[a] = rho_new[a] / rho[a]
+            P[:, a] = W[:, a] + P[:, a] * eta[a]
+            rho[a] = rho_new[a]
+            if history is not None:
+                history.append(X.copy())
+        if not check:
+            break
+        Rt = B - apply_a(X)                                    # true residual of X
+        tn = np.linalg.norm(Rt, axis=0)
+        true_res = np.where(bnorm > 0.0, tn / np.where(bnorm > 0.0, bnorm, 1.0), 0.0)
+        miss = (bnorm > 0.0) & ~_meets_tol(tn, bnorm, tol, conv) & ~broken
+        if not miss.any() or u >= maxit:
+            if miss.any():
+                active = miss                                  # budget spent: not converged
+            break
+        R[:, miss] = Rt[:, miss]                               # restart from the true residual
+        W = minv * R
+        P[:, miss] = W[:, miss]
+        rho[miss] = np.sum(R * W, axis=0)[miss]
+        active = miss
     if active.any():
         flags |= FLAG_CG_NOT_CONVERGED
+    if info is not None:
+        info["true_res"] = true_res
     return X, u, flags
 
 
 def cofem(op, y, beta, K, T, cg_tol, cg_maxit, seed, alpha0=None, precond="jacobi",
           alpha_max=1e12, conv="per_column", rr_period=0, probe_fn=None,
-          solver="pcg", return_x=False, prior="gaussian"):
+          solver="pcg", return_x=False, prior="gaussian", check_residual=False):
     """Alg. 1 (CovarianceFreeEM) with Alg. 2 as the linear solver.
 
     op        oracle.operators.DenseOperator / ToeplitzOperator
@@ -154,7 +192,10 @@ def cofem(op, y, beta, K, T, cg_tol, cg_maxit, seed, alpha0=None, precond="jacob
               Philox Rademacher rule with `seed`.
     solver    "pcg" (Alg. 2) or "direct" (exact dense solve, small D only).
     prior     "gaussian" (Eq. mstep) or "rectified" (non-negativity, reading 12).
-    Returns dict(alpha, mu, s, cg_iters, flags[, X]).
+    check_residual  true-residual check at the end of each E-step (reading 11;
+              always on with rr_period > 0).
+    Returns dict(alpha, mu, s, cg_iters, flags, true_res (T x (K+1), NaN where
+    not checked)[, X]).
     """
     D = op.D
     yv = np.asarray(y, dtype=np.float64)
@@ -162,6 +203,7 @@ def cofem(op, y, beta, K, T, cg_tol, cg_maxit, seed, alpha0=None, precond="jacob
     theta = op.column_sq_norms() if precond == "jacobi" else np.ones(D)
     alpha = np.ones(D) if alpha0 is None else np.asarray(alpha0, dtype=np.float64).copy()
     cg_iters = np.zeros(T, dtype=np.int64)
+    true_res = np.full((T, K + 1), np.nan)
     flags = 0
     mu = s = X = None
     for t in range(1, T + 1):
@@ -176,9 +218,13 @@ def cofem(op, y, beta, K, T, cg_tol, cg_maxit, seed, alpha0=None, precond="jacob
             return apply_A(op, V, alpha, beta)
 
         if solver == "pcg":
-            X, u, f = pcg(apply_a, B, minv, cg_tol, cg_maxit, conv=conv, rr_period=rr_period)
+            info = {}
+            X, u, f = pcg(apply_a, B, minv, cg_tol, cg_maxit, conv=conv, rr_period=rr_period,
+                          check=rr_period > 0 or check_residual, info=info)
             cg_iters[t - 1] = u
             flags |= f
+            if info["true_res"] is not None:
+                true_res[t - 1] = info["true_res"]
         elif solver == "direct":
             Phi = op.dense()
             A = beta * (Phi.T @ Phi) + np.diag(alpha)
@@ -192,7 +238,7 @@ def cofem(op, y, beta, K, T, cg_tol, cg_maxit, seed, alpha0=None, precond="jacob
             if np.any(m2 < 1.0 / alpha_max):
                 flags |= FLAG_ALPHA_CLAMPED
             alpha = 1.0 / np.maximum(m2, 1.0 / alpha_max)
-    out = dict(alpha=alpha, mu=mu, s=s, cg_iters=cg_iters, flags=flags)
+    out = dict(alpha=alpha, mu=mu, s=s, cg_iters=cg_iters, flags=flags, true_res=true_res)
     if return_x:
         out["X"] = X
     return out

@@ -27,12 +27,14 @@ COFEM_ERR_NOT_FOUND = 6
 
 COFEM_OP_DENSE = 0
 COFEM_OP_TOEPLITZ = 1
+COFEM_OP_DCT = 2
 COFEM_F32 = 0
 COFEM_BF16 = 1
 COFEM_F32_TF32X3 = 2
 COFEM_FP8_E4M3 = 3
 COFEM_PRECOND_JACOBI = 0
 COFEM_PRECOND_ONE = 1
+COFEM_PRECOND_NONE = 2
 COFEM_CONV_PER_COLUMN = 0
 COFEM_CONV_FROBENIUS = 1
 COFEM_PATH_AUTO = 0
@@ -59,6 +61,7 @@ class cofem_opts(C.Structure):
         ("max_sms", C.c_int),
         ("overlap_launch", C.c_int),
         ("prior", C.c_int),
+        ("check_residual", C.c_int),
     ]
 
 
@@ -94,7 +97,9 @@ def _load():
     sig = {
         "cofem_default_opts": (None, [C.POINTER(cofem_opts)]),
         "cofem_create": (i, [C.POINTER(vp), ll, ll, i, vp, ll, C.POINTER(cofem_opts)]),
+        "cofem_create_dct": (i, [C.POINTER(vp), ll, ll, vp, C.POINTER(cofem_opts)]),
         "cofem_fit": (i, [vp, vp, d, vp, i, i, d, i, vp, vp, vp, vp, vp]),
+        "cofem_fit_multitask": (i, [vp, i, vp, d, vp, i, i, d, i, vp, vp, vp, vp, vp]),
         "cofem_destroy": (i, [vp]),
         "cofem_status_string": (C.c_char_p, [i]),
         "cofem_last_error": (C.c_char_p, []),
@@ -106,6 +111,8 @@ def _load():
         "cofem_get_dictionary": (i, [vp, vp]),
         "cofem_operator_info": (i, [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
         "cofem_graph_info": (i, [vp, C.POINTER(i), C.POINTER(i)]),
+        "cofem_true_residuals": (i, [vp, vp]),
+        "cofem_fit_stats": (i, [vp, C.POINTER(i), C.POINTER(i)]),
         "cofem_time_operator": (i, [vp, i, i, C.POINTER(d)]),
         "cofem_apply_dense_noalloc": (i, [vp, ll, ll, ll, vp, i, vp, d, vp, vp]),
         "cofem_estimate_bytes": (ll, [i, ll, ll, ll, i, i]),
@@ -166,6 +173,13 @@ def cofem_create(N: int, D: int, kind: int, phi, L: int = 0, opts: cofem_opts | 
     return h.value
 
 
+def cofem_create_dct(N: int, D: int, rows, opts: cofem_opts | None = None) -> int:
+    """rows: N distinct int32 indices in [0, D) (host or device)."""
+    h = C.c_void_p()
+    _check(lib.cofem_create_dct(C.byref(h), N, D, _ptr(rows, np.int32), C.byref(opts) if opts is not None else None))
+    return h.value
+
+
 def cofem_fit(h: int, y, beta: float, alpha0, K: int, T_em: int, cg_tol: float, cg_maxit: int,
               mu, s, alpha, cg_iters=None) -> int:
     """Returns the COFEM_FLAG_* bits of the fit."""
@@ -173,6 +187,17 @@ def cofem_fit(h: int, y, beta: float, alpha0, K: int, T_em: int, cg_tol: float, 
     _check(lib.cofem_fit(h, _ptr(y), float(beta), _ptr(alpha0, allow_none=True), int(K), int(T_em),
                          float(cg_tol), int(cg_maxit), _ptr(mu), _ptr(s), _ptr(alpha),
                          _ptr(cg_iters, np.int32, allow_none=True), C.byref(flags)))
+    return flags.value
+
+
+def cofem_fit_multitask(h: int, L: int, Y, beta: float, alpha0, K: int, T_em: int, cg_tol: float, cg_maxit: int,
+                        mu, s, alpha, cg_iters=None) -> int:
+    """L tasks sharing the handle's dictionary and alpha; Y, mu, s are L x N /
+    L x D row-major.  Returns the COFEM_FLAG_* bits of the fit."""
+    flags = C.c_uint(0)
+    _check(lib.cofem_fit_multitask(h, int(L), _ptr(Y), float(beta), _ptr(alpha0, allow_none=True), int(K),
+                                   int(T_em), float(cg_tol), int(cg_maxit), _ptr(mu), _ptr(s), _ptr(alpha),
+                                   _ptr(cg_iters, np.int32, allow_none=True), C.byref(flags)))
     return flags.value
 
 
@@ -272,6 +297,21 @@ def cofem_operator_info(h: int) -> tuple[int, int, int, int]:
     return path.value, kc.value, kr.value, ks.value
 
 
+def cofem_true_residuals(h: int, T_em: int, K: int) -> np.ndarray:
+    """(T_em, K+1) FP64 array of the last fit's true relative residuals
+    ||b_q - A x_q|| / ||b_q|| per EM iteration and column."""
+    out = np.empty((T_em, K + 1), dtype=np.float64)
+    _check(lib.cofem_true_residuals(h, out.ctypes.data))
+    return out
+
+
+def cofem_fit_stats(h: int) -> tuple[int, int]:
+    """(residual replacements, true-residual checks) of the last fit."""
+    r, c = C.c_int(), C.c_int()
+    _check(lib.cofem_fit_stats(h, C.byref(r), C.byref(c)))
+    return r.value, c.value
+
+
 def cofem_graph_info(h: int) -> tuple[int, int]:
     """(fit graph built, its CG-step kernels joined by programmatic edges)."""
     built, ov = C.c_int(), C.c_int()
@@ -280,12 +320,16 @@ def cofem_graph_info(h: int) -> tuple[int, int]:
 
 
 class CoFEM:
-    """Owning wrapper of one handle (closes it on exit / garbage collection)."""
+    """Owning wrapper of one handle (closes it on exit / garbage collection).
+    kind COFEM_OP_DCT takes the kept rows (int32) in place of phi."""
 
     def __init__(self, N, D, kind, phi, L=0, **opts):
         self.N, self.D, self.kind = int(N), int(D), kind
         self.opts = default_opts(**opts)
-        self.h = cofem_create(N, D, kind, phi, L, self.opts)
+        if kind == COFEM_OP_DCT:
+            self.h = cofem_create_dct(N, D, phi, self.opts)
+        else:
+            self.h = cofem_create(N, D, kind, phi, L, self.opts)
 
     def fit(self, y, beta, K, T, cg_tol, cg_maxit, alpha0=None, out=None):
         """Host-array convenience: returns dict(mu, s, alpha, cg_iters, flags)."""

@@ -96,6 +96,11 @@ WsSizes ws_sizes(cofem_ctx* c, int Qcap) {
         w.t = (size_t)c->Np * QP;
         w.tpart = (size_t)c->S1 * c->Np * QP;
         w.ttpart = (size_t)Qcap * (c->Np / 64 + 1);
+    } else if (c->kind == COFEM_OP_DCT) {
+        w.u = (size_t)Qcap * c->Dp;
+        w.t = 0;
+        w.tpart = 0;
+        w.ttpart = (size_t)Qcap + 1;
     } else {
         w.u = (size_t)Qcap * c->Dp;
         w.t = 0;
@@ -108,8 +113,24 @@ WsSizes ws_sizes(cofem_ctx* c, int Qcap) {
     return w;
 }
 
+// The precision form: X kept as an FP32 pair, accurate residual replacement
+// (rr_period > 0) and the true-residual check at the end of each E-step.
+bool precise(const cofem_ctx* c) { return c->opts.rr_period > 0 || c->opts.check_residual != 0; }
+
+void free_precise(cofem_ctx* c) {
+    if (!c->Xlo) return;
+    const DfSizes z = df_configure(c, c->Qcap);
+    dfree(c, &c->Xlo, (size_t)c->Qcap * c->Dp);
+    dfree(c, &c->Rt, (size_t)c->Qcap * c->Dp);
+    dfree(c, &c->df_T, z.T);
+    dfree(c, &c->df_thi, z.t);
+    dfree(c, &c->df_tlo, z.t);
+    dfree(c, &c->df_U, z.U);
+}
+
 void free_workspace(cofem_ctx* c) {
     if (c->Qcap == 0) return;
+    free_precise(c);
     const WsSizes w = ws_sizes(c, c->Qcap);
     dfree(c, &c->X, w.xrp);
     dfree(c, &c->R, w.xrp);
@@ -148,6 +169,22 @@ cofem_status ensure_workspace(cofem_ctx* c, int Q) {
         }
     }
     c->Qcap = Q;
+    if (precise(c)) {
+        const DfSizes z = df_configure(c, Q);
+        c->df_QP = z.QP;
+        c->df_S1 = z.S1;
+        c->df_S2 = z.S2;
+        c->df_k1 = z.k1;
+        c->df_k2 = z.k2;
+        if ((st = dalloc(c, &c->Xlo, w.xrp)) || (st = dalloc(c, &c->Rt, w.xrp)) ||
+            (c->kind == COFEM_OP_DENSE && (st = dalloc(c, &c->df_T, z.T))) || (st = dalloc(c, &c->df_thi, z.t)) ||
+            (st = dalloc(c, &c->df_tlo, z.t)) || (st = dalloc(c, &c->df_U, z.U))) {
+            free_workspace(c);
+            return st;
+        }
+        CK(cudaMemsetAsync(c->Xlo, 0, w.xrp * sizeof(float), c->stream));
+        CK(cudaMemsetAsync(c->Rt, 0, w.xrp * sizeof(float), c->stream));
+    }
     if (c->kind == COFEM_OP_DENSE && c->use_tc) {
         cudaError_t e = tc_setup(c, Q);
         if (e != cudaSuccess) {
@@ -169,9 +206,10 @@ cofem_status ensure_workspace(cofem_ctx* c, int Q) {
 cofem_status ensure_iters(cofem_ctx* c, int T) {
     if (c->iters_cap >= T) return COFEM_OK;
     dfree(c, &c->iters_dev, (size_t)c->iters_cap);
+    dfree(c, &c->res_dev, (size_t)c->iters_cap * COFEM_QMAX);
     c->iters_cap = 0;
     cofem_status st = dalloc(c, &c->iters_dev, (size_t)T);
-    if (st) return st;
+    if (st || (st = dalloc(c, &c->res_dev, (size_t)T * COFEM_QMAX))) return st;
     c->iters_cap = T;
     return COFEM_OK;
 }
@@ -187,9 +225,27 @@ cofem_status build_graph(cofem_ctx* c, int Q, bool pdl) {
     launch_fit_setup(root, c, Q);
     const cudaGraphConditionalHandle h_em = root.make_handle(1u, true);
     Sink em = root.conditional(h_em, cudaGraphCondTypeWhile);
-    const cudaGraphConditionalHandle h_cg = em.make_handle(0u, false);
-    launch_cg_init(em, c, Q, h_cg);
-    Sink cg = em.conditional(h_cg, cudaGraphCondTypeWhile);
+    // precision form: the CG loop sits in a verification loop whose body ends
+    // with the true-residual check (which may restart columns and go round
+    // again).  The initialisation sets the verification loop's condition in
+    // every EM iteration (a handle's default value is applied only when the
+    // whole graph is launched); the gate kernel sets the CG loop's entry
+    // condition, a handle of the verification body
+    const bool verify = precise(c);
+    Sink vf;
+    cudaGraphConditionalHandle h_vf = 0, h_cg = 0;
+    if (verify) {
+        h_vf = em.make_handle(0u, false);
+        launch_cg_init(em, c, Q, h_vf);
+        vf = em.conditional(h_vf, cudaGraphCondTypeWhile);
+        h_cg = vf.make_handle(0u, false);
+        launch_cg_gate(vf, c, h_cg);
+    } else {
+        h_cg = em.make_handle(0u, false);
+        launch_cg_init(em, c, Q, h_cg);
+    }
+    Sink& outer = verify ? vf : em;
+    Sink cg = outer.conditional(h_cg, cudaGraphCondTypeWhile);
     launch_operator(cg, c, Q, c->P, OP_CG);
     // residual replacement (an IF node) only where it is on: a conditional
     // node between the update and the direction would end their overlap
@@ -199,12 +255,16 @@ cofem_status build_graph(cofem_ctx* c, int Q, bool pdl) {
     Sink rr;
     if (with_rr) {
         rr = cg.conditional(h_rr, cudaGraphCondTypeIf);
-        launch_operator(rr, c, Q, c->X, OP_RR);
-        launch_rr_residual(rr, c, Q);
+        launch_true_residual(rr, c, Q, DF_RR);
     }
     launch_cg_direction(cg, c, Q, h_cg);
+    if (verify) {
+        launch_true_residual(vf, c, Q, DF_CHECK);
+        launch_df_check(vf, c, Q, h_vf);
+    }
     launch_mstep(em, c, Q, h_em);
-    cudaError_t e = root.err ? root.err : (em.err ? em.err : (cg.err ? cg.err : rr.err));
+    cudaError_t e = root.err ? root.err
+                             : (em.err ? em.err : (vf.err ? vf.err : (cg.err ? cg.err : rr.err)));
     if (e != cudaSuccess) {
         free_graph(c);
         return cuda_fail(e, "recording the fit graph");
@@ -231,25 +291,31 @@ cofem_status run_fit_direct(cofem_ctx* c, int Q, int T) {
     s.stream = c->stream;
     s.pdl = c->opts.overlap_launch != 0;
     launch_fit_setup(s, c, Q);
+    const bool verify = precise(c);
     for (int t = 1; t <= T; ++t) {
         launch_cg_init(s, c, Q, 0);
         if (s.err) return cuda_fail(s.err, "launch");
         cofem_status st = read_ctl(c);
         if (st) return st;
-        while (c->ctl_host->any_active && c->ctl_host->u < c->ctl_host->maxit) {
-            launch_operator(s, c, Q, c->P, OP_CG);
-            launch_cg_update(s, c, Q, 0, 0);
-            if (s.err) return cuda_fail(s.err, "launch");
-            if ((st = read_ctl(c))) return st;
-            const int u = c->ctl_host->u;
-            if (c->ctl_host->rr_period > 0 && u % c->ctl_host->rr_period == 0) {
-                launch_operator(s, c, Q, c->X, OP_RR);
-                launch_rr_residual(s, c, Q);
+        do {
+            while (c->ctl_host->any_active && c->ctl_host->u < c->ctl_host->maxit) {
+                launch_operator(s, c, Q, c->P, OP_CG);
+                launch_cg_update(s, c, Q, 0, 0);
+                if (s.err) return cuda_fail(s.err, "launch");
+                if ((st = read_ctl(c))) return st;
+                const int u = c->ctl_host->u;
+                if (c->ctl_host->rr_period > 0 && u % c->ctl_host->rr_period == 0)
+                    launch_true_residual(s, c, Q, DF_RR);
+                launch_cg_direction(s, c, Q, 0);
+                if (s.err) return cuda_fail(s.err, "launch");
+                if ((st = read_ctl(c))) return st;
             }
-            launch_cg_direction(s, c, Q, 0);
+            if (!verify) break;
+            launch_true_residual(s, c, Q, DF_CHECK);
+            launch_df_check(s, c, Q, 0);
             if (s.err) return cuda_fail(s.err, "launch");
             if ((st = read_ctl(c))) return st;
-        }
+        } while (c->ctl_host->verify_again);
         launch_mstep(s, c, Q, 0);
         if (s.err) return cuda_fail(s.err, "launch");
     }
@@ -280,6 +346,7 @@ cofem_status set_kernel_attributes(int dev) {
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     CK(tc_kernel_attributes(optin));
     CK(toeplitz_kernel_attributes());
+    CK(dct_kernel_attributes());
     g_attr_done[dev] = true;
     return COFEM_OK;
 }
@@ -315,6 +382,7 @@ void cofem_default_opts(cofem_opts* o) {
     o->stream = nullptr;
     o->use_graph = 1;
     o->overlap_launch = 1;
+    o->check_residual = 0;
 }
 
 const char* cofem_status_string(cofem_status s) {
@@ -332,13 +400,18 @@ const char* cofem_status_string(cofem_status s) {
 
 const char* cofem_last_error(void) { return g_err; }
 
-cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, const float* phi, long long L,
-                          const cofem_opts* opts) {
+}  // extern "C"
+
+// Handle creation for every dictionary kind: `data` is the dense matrix or the
+// convolution filter (floats), or the DCT dictionary's row indices (ints).
+static cofem_status create_impl(cofem_ctx** out, long long N, long long D, int kind, const void* data, long long L,
+                                const cofem_opts* opts) {
     g_err[0] = 0;
     if (!out) return fail(COFEM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (N < 1 || D < 1 || N > 0x7fffffffLL || D > 0x7fffffffLL) return fail(COFEM_ERR_INVALID_ARG, "bad N/D");
-    if (!phi) return fail(COFEM_ERR_INVALID_ARG, "phi is NULL");
+    if (!data) return fail(COFEM_ERR_INVALID_ARG, kind == COFEM_OP_DCT ? "rows is NULL" : "phi is NULL");
+    const float* phi = (const float*)data;
     cofem_opts o;
     cofem_default_opts(&o);
     if (opts) o = *opts;
@@ -355,14 +428,26 @@ cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, c
         if (N != D) return fail(COFEM_ERR_INVALID_ARG, "a convolutional dictionary needs N == D");
         if (L < 1 || L > 1024 || L > N) return fail(COFEM_ERR_INVALID_ARG, "need 1 <= L <= min(1024, N)");
         if (o.precision != COFEM_F32) return fail(COFEM_ERR_INVALID_ARG, "convolutional dictionary is FP32 only");
+    } else if (kind == COFEM_OP_DCT) {
+        if (D < 16 || D > COFEM_DCT_MAX_D || (D & (D - 1)))
+            return fail(COFEM_ERR_INVALID_ARG, "a DCT dictionary needs D a power of two, 16 <= D <= %d",
+                        COFEM_DCT_MAX_D);
+        if (N > D) return fail(COFEM_ERR_INVALID_ARG, "a DCT dictionary keeps N <= D rows");
+        if (L != 0) return fail(COFEM_ERR_INVALID_ARG, "L must be 0 for a DCT dictionary");
+        if (o.precision != COFEM_F32) return fail(COFEM_ERR_INVALID_ARG, "the DCT dictionary is FP32 only");
+        if (o.rr_period != 0 || o.check_residual != 0)
+            return fail(COFEM_ERR_UNSUPPORTED, "the precision form (rr_period, check_residual) is not built for "
+                                               "the DCT dictionary");
     } else {
         return fail(COFEM_ERR_INVALID_ARG, "unknown dictionary kind %d", kind);
     }
-    if (o.precond != COFEM_PRECOND_JACOBI && o.precond != COFEM_PRECOND_ONE)
+    if (o.precond != COFEM_PRECOND_JACOBI && o.precond != COFEM_PRECOND_ONE && o.precond != COFEM_PRECOND_NONE)
         return fail(COFEM_ERR_INVALID_ARG, "bad precond");
     if (o.conv != COFEM_CONV_PER_COLUMN && o.conv != COFEM_CONV_FROBENIUS)
         return fail(COFEM_ERR_INVALID_ARG, "bad conv");
     if (o.rr_period < 0) return fail(COFEM_ERR_INVALID_ARG, "rr_period < 0");
+    if (o.check_residual != 0 && o.check_residual != 1)
+        return fail(COFEM_ERR_INVALID_ARG, "check_residual must be 0 or 1");
     if (o.overlap_launch != 0 && o.overlap_launch != 1) return fail(COFEM_ERR_INVALID_ARG, "overlap_launch must be 0 or 1");
     if (o.prior != COFEM_PRIOR_GAUSSIAN && o.prior != COFEM_PRIOR_RECTIFIED)
         return fail(COFEM_ERR_INVALID_ARG, "prior must be COFEM_PRIOR_GAUSSIAN or COFEM_PRIOR_RECTIFIED");
@@ -449,6 +534,25 @@ cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, c
             c->phi32 = tmp;
         }
         launch_dense_colreduce(c->stream, c, nullptr, 1.0, c->theta);
+    } else if (kind == COFEM_OP_DCT) {
+        // rows: N distinct indices in [0, D), checked on the host
+        std::vector<int> rows((size_t)N);
+        CKB(cudaMemcpy(rows.data(), data, (size_t)N * sizeof(int), cudaMemcpyDefault));
+        std::vector<char> seen((size_t)D, 0);
+        for (long long i = 0; i < N; ++i) {
+            const int r = rows[(size_t)i];
+            if (r < 0 || r >= D || seen[(size_t)r]) {
+                cofem_destroy(c);
+                return fail(COFEM_ERR_INVALID_ARG, "rows must be N distinct indices in [0, D)");
+            }
+            seen[(size_t)r] = 1;
+        }
+        if ((st = dalloc(c, &c->dct_rows, (size_t)N)) || (st = dalloc(c, &c->dct_mask, (size_t)c->Dp)) ||
+            (st = dalloc(c, &c->dct_tw, (size_t)(D / 4 > 0 ? D / 4 : 1))))
+            return bail(st);
+        CKB(cudaMemcpyAsync(c->dct_rows, rows.data(), (size_t)N * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        launch_dct_setup(c->stream, c);
+        CKB(cudaStreamSynchronize(c->stream));   // rows (host vector) is read by the copy
     } else {
         if ((st = dalloc(c, &c->h, (size_t)L))) return bail(st);
         CKB(cudaMemcpyAsync(c->h, phi, L * sizeof(float), cudaMemcpyDefault, c->stream));
@@ -468,6 +572,21 @@ cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, c
     return COFEM_OK;
 }
 
+extern "C" {
+
+cofem_status cofem_create(cofem_ctx** out, long long N, long long D, int kind, const float* phi, long long L,
+                          const cofem_opts* opts) {
+    if (kind == COFEM_OP_DCT) {
+        g_err[0] = 0;
+        return fail(COFEM_ERR_INVALID_ARG, "a DCT dictionary is created with cofem_create_dct");
+    }
+    return create_impl(out, N, D, kind, phi, L, opts);
+}
+
+cofem_status cofem_create_dct(cofem_ctx** out, long long N, long long D, const int* rows, const cofem_opts* opts) {
+    return create_impl(out, N, D, COFEM_OP_DCT, rows, 0, opts);
+}
+
 cofem_status cofem_destroy(cofem_ctx* c) {
     if (!c) return COFEM_OK;
     cudaSetDevice(c->device);
@@ -479,14 +598,18 @@ cofem_status cofem_destroy(cofem_ctx* c) {
     dfree(c, &c->phi8, (size_t)c->Np * c->Dp);
     dfree(c, &c->scale8, (size_t)c->Np);
     dfree(c, &c->h, (size_t)c->L);
+    dfree(c, &c->dct_rows, (size_t)c->N);
+    dfree(c, &c->dct_mask, (size_t)c->Dp);
+    dfree(c, &c->dct_tw, (size_t)(c->D / 4 > 0 ? c->D / 4 : 1));
     dfree(c, &c->theta, (size_t)c->Dp);
     dfree(c, &c->alpha, (size_t)c->Dp);
     dfree(c, &c->minv, (size_t)c->Dp);
-    dfree(c, &c->b, (size_t)c->Dp);
-    dfree(c, &c->mu_out, (size_t)c->Dp);
-    dfree(c, &c->s_out, (size_t)c->Dp);
-    dfree(c, &c->yv, (size_t)c->Np);
+    dfree(c, &c->b, (size_t)c->Lcap * c->Dp);
+    dfree(c, &c->mu_out, (size_t)c->Lcap * c->Dp);
+    dfree(c, &c->s_out, (size_t)c->Lcap * c->Dp);
+    dfree(c, &c->yv, (size_t)c->Lcap * c->Np);
     dfree(c, &c->iters_dev, (size_t)c->iters_cap);
+    dfree(c, &c->res_dev, (size_t)c->iters_cap * COFEM_QMAX);
     dfree(c, &c->check_flag, 1);
     dfree(c, &c->ctl, 1);
     delete c->ctl_host;
@@ -495,33 +618,67 @@ cofem_status cofem_destroy(cofem_ctx* c) {
     return COFEM_OK;
 }
 
-// b = beta Phi^T y into c->b, after y is staged in c->yv.
-static cofem_status stage_y_and_b(cofem_ctx* c, const float* y, double beta) {
-    CK(cudaMemcpyAsync(c->yv, y, c->N * sizeof(float), cudaMemcpyDefault, c->stream));
-    cofem_status st = check_finite_dev(c, c->yv, c->N, "y");
-    if (st) return st;
-    if (c->kind == COFEM_OP_DENSE) launch_dense_colreduce(c->stream, c, c->yv, beta, c->b);
-    else launch_toeplitz_phit_y(c->stream, c, c->yv, beta, c->b);
+// Per-task buffers (b, y, mu, s) for L tasks; growing them drops the fit
+// graph, which holds their addresses.
+static cofem_status ensure_tasks(cofem_ctx* c, int L) {
+    if (L <= c->Lcap) return COFEM_OK;
+    dfree(c, &c->b, (size_t)c->Lcap * c->Dp);
+    dfree(c, &c->mu_out, (size_t)c->Lcap * c->Dp);
+    dfree(c, &c->s_out, (size_t)c->Lcap * c->Dp);
+    dfree(c, &c->yv, (size_t)c->Lcap * c->Np);
+    free_graph(c);
+    c->Lcap = 0;
+    cofem_status st;
+    if ((st = dalloc(c, &c->b, (size_t)L * c->Dp)) || (st = dalloc(c, &c->mu_out, (size_t)L * c->Dp)) ||
+        (st = dalloc(c, &c->s_out, (size_t)L * c->Dp)) || (st = dalloc(c, &c->yv, (size_t)L * c->Np)))
+        return st;
+    CK(cudaMemsetAsync(c->yv, 0, (size_t)L * c->Np * sizeof(float), c->stream));
+    c->Lcap = L;
+    return COFEM_OK;
+}
+
+// b_l = beta Phi^T y_l into row l of c->b, after y_l (row l of Y, N floats
+// each) is staged in row l of c->yv.
+static cofem_status stage_y_and_b(cofem_ctx* c, const float* Y, double beta, int L = 1) {
+    CK(cudaMemcpy2DAsync(c->yv, c->Np * sizeof(float), Y, c->N * sizeof(float), c->N * sizeof(float), L,
+                         cudaMemcpyDefault, c->stream));
+    for (int l = 0; l < L; ++l) {
+        cofem_status st = check_finite_dev(c, c->yv + (size_t)l * c->Np, c->N, "y");
+        if (st) return st;
+        float* yl = c->yv + (size_t)l * c->Np;
+        float* bl = c->b + (size_t)l * c->Dp;
+        if (c->kind == COFEM_OP_DENSE) launch_dense_colreduce(c->stream, c, yl, beta, bl);
+        else if (c->kind == COFEM_OP_DCT) launch_dct_phit_y(c->stream, c, yl, beta, bl, c->s_out + (size_t)l * c->Dp);
+        else launch_toeplitz_phit_y(c->stream, c, yl, beta, bl);
+    }
     CK(cudaGetLastError());
     return COFEM_OK;
 }
 
-cofem_status cofem_fit(cofem_ctx* c, const float* y, double beta, const float* alpha0, int K, int T_em,
-                       double cg_tol, int cg_maxit, float* mu, float* s, float* alpha, int* cg_iters,
-                       unsigned* flags) {
+// One fit of L tasks sharing the dictionary and alpha (L = 1: Alg. 1 as
+// printed; L > 1: the multi-task CoFEM of Sec. III with the L (K+1) columns
+// in one batched PCG).
+static cofem_status fit_impl(cofem_ctx* c, int L, const float* Y, double beta, const float* alpha0, int K,
+                             int T_em, double cg_tol, int cg_maxit, float* mu, float* s, float* alpha,
+                             int* cg_iters, unsigned* flags) {
     g_err[0] = 0;
     if (!c) return fail(COFEM_ERR_INVALID_ARG, "handle is NULL");
-    if (!y || !mu || !s || !alpha) return fail(COFEM_ERR_INVALID_ARG, "y, mu, s and alpha are required");
-    if (K < 1 || K > COFEM_QMAX - 1) return fail(COFEM_ERR_INVALID_ARG, "need 1 <= K <= %d", COFEM_QMAX - 1);
+    if (!Y || !mu || !s || !alpha) return fail(COFEM_ERR_INVALID_ARG, "y, mu, s and alpha are required");
+    if (L < 1) return fail(COFEM_ERR_INVALID_ARG, "need L >= 1");
+    if (K < 1 || L * (K + 1) > COFEM_QMAX)
+        return fail(COFEM_ERR_INVALID_ARG, L == 1 ? "need 1 <= K <= %d" : "need K >= 1 and L (K + 1) <= %d",
+                    L == 1 ? COFEM_QMAX - 1 : COFEM_QMAX);
     if (T_em < 1) return fail(COFEM_ERR_INVALID_ARG, "need T_em >= 1");
     if (cg_maxit < 1) return fail(COFEM_ERR_INVALID_ARG, "need cg_maxit >= 1");
     if (!(cg_tol > 0.0) || !std::isfinite(cg_tol)) return fail(COFEM_ERR_INVALID_ARG, "need cg_tol > 0");
     if (!std::isfinite(beta)) return fail(COFEM_ERR_NONFINITE, "beta is not finite");
     if (!(beta > 0.0)) return fail(COFEM_ERR_INVALID_ARG, "need beta > 0");
+    if (L > 1 && c->opts.prior != COFEM_PRIOR_GAUSSIAN)
+        return fail(COFEM_ERR_UNSUPPORTED, "the multi-task M-step is defined for the Gaussian prior only");
     CK(cudaSetDevice(c->device));
-    const int Q = K + 1;
+    const int Q = L * (K + 1);
     cofem_status st;
-    if ((st = ensure_workspace(c, Q)) || (st = ensure_iters(c, T_em))) return st;
+    if ((st = ensure_workspace(c, Q)) || (st = ensure_iters(c, T_em)) || (st = ensure_tasks(c, L))) return st;
 
     DevCtl* hc = c->ctl_host;
     memset(hc, 0, sizeof(DevCtl));
@@ -531,15 +688,22 @@ cofem_status cofem_fit(cofem_ctx* c, const float* y, double beta, const float* a
     hc->seed = c->opts.seed;
     hc->T = T_em;
     hc->K = K;
+    hc->L = L;
     hc->Q = Q;
     hc->maxit = cg_maxit;
     hc->conv = c->opts.conv;
     hc->rr_period = c->opts.rr_period;
     hc->prior = c->opts.prior;
+    hc->fix_residual = c->opts.rr_period > 0;
+    hc->precond_none = c->opts.precond == COFEM_PRECOND_NONE;
     hc->ap_part = c->part + (size_t)2 * Q * c->nch;   // slab 2 of the CG partials
     hc->ap_n = c->nch;
     CK(cudaMemcpyAsync(c->ctl, hc, sizeof(DevCtl), cudaMemcpyHostToDevice, c->stream));
-    if ((st = stage_y_and_b(c, y, beta))) return st;
+    // true residuals not measured stay NaN (all bits set)
+    CK(cudaMemsetAsync(c->res_dev, 0xFF, (size_t)T_em * COFEM_QMAX * sizeof(double), c->stream));
+    c->last_T = T_em;
+    c->last_Q = Q;
+    if ((st = stage_y_and_b(c, Y, beta, L))) return st;
     if (alpha0) {
         CK(cudaMemcpyAsync(c->alpha, alpha0, c->D * sizeof(float), cudaMemcpyDefault, c->stream));
         if ((st = check_finite_dev(c, c->alpha, c->D, "alpha0"))) return st;
@@ -549,29 +713,46 @@ cofem_status cofem_fit(cofem_ctx* c, const float* y, double beta, const float* a
         CK(cudaStreamSynchronize(c->stream));
     }
     if (c->opts.use_graph) {
-        if (c->graph_Q != Q || !c->gexec) {
+        if (c->graph_Q != Q || c->graph_L != L || !c->gexec) {
             // programmatic edges where the driver takes them, else plain ones
             const bool pdl = c->opts.overlap_launch != 0;
             if (!pdl || build_graph(c, Q, true) != COFEM_OK) {
                 (void)cudaGetLastError();
                 if ((st = build_graph(c, Q, false))) return st;
             }
+            c->graph_L = L;
         }
         CK(cudaGraphLaunch(c->gexec, c->stream));
     } else {
         if ((st = run_fit_direct(c, Q, T_em))) return st;
     }
-    CK(cudaMemcpyAsync(mu, c->mu_out, c->D * sizeof(float), cudaMemcpyDefault, c->stream));
-    CK(cudaMemcpyAsync(s, c->s_out, c->D * sizeof(float), cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpy2DAsync(mu, c->D * sizeof(float), c->mu_out, c->Dp * sizeof(float), c->D * sizeof(float), L,
+                         cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpy2DAsync(s, c->D * sizeof(float), c->s_out, c->Dp * sizeof(float), c->D * sizeof(float), L,
+                         cudaMemcpyDefault, c->stream));
     CK(cudaMemcpyAsync(alpha, c->alpha, c->D * sizeof(float), cudaMemcpyDefault, c->stream));
     if (cg_iters) CK(cudaMemcpyAsync(cg_iters, c->iters_dev, T_em * sizeof(int), cudaMemcpyDefault, c->stream));
     CK(cudaMemcpyAsync(hc, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     CK(cudaGetLastError());
     if (flags) *flags = hc->flags;
+    c->last_rr = hc->n_rr;
+    c->last_check = hc->n_check;
     if (hc->flags & COFEM_FLAG_DEVICE_TIMEOUT)
         return fail(COFEM_ERR_CUDA, "a bounded on-device wait timed out (tensor-core pipeline)");
     return COFEM_OK;
+}
+
+cofem_status cofem_fit(cofem_ctx* c, const float* y, double beta, const float* alpha0, int K, int T_em,
+                       double cg_tol, int cg_maxit, float* mu, float* s, float* alpha, int* cg_iters,
+                       unsigned* flags) {
+    return fit_impl(c, 1, y, beta, alpha0, K, T_em, cg_tol, cg_maxit, mu, s, alpha, cg_iters, flags);
+}
+
+cofem_status cofem_fit_multitask(cofem_ctx* c, int L, const float* Y, double beta, const float* alpha0, int K,
+                                 int T_em, double cg_tol, int cg_maxit, float* mu, float* s, float* alpha,
+                                 int* cg_iters, unsigned* flags) {
+    return fit_impl(c, L, Y, beta, alpha0, K, T_em, cg_tol, cg_maxit, mu, s, alpha, cg_iters, flags);
 }
 
 cofem_status cofem_probe_fill(unsigned long long seed, int t, int K, long long D, float* out, void* stream) {
@@ -716,12 +897,36 @@ cofem_status cofem_operator_info(cofem_ctx* c, int* path, int* kernels_cg, int* 
     if (c->kind == COFEM_OP_DENSE && c->use_tc) {
         tc_operator_info(c, &pth, &kc, &kr);
     } else if (c->kind == COFEM_OP_DENSE) {
-        kc = kr = 2;   // k_gemm1_simt, k_gemm2_simt
+        kc = 2;   // k_gemm1_simt, k_gemm2_simt
+        kr = true_residual_kernels(c);
+    } else {
+        kr = true_residual_kernels(c);
     }
     if (path) *path = pth;
     if (kernels_cg) *kernels_cg = kc;
     if (kernels_rr) *kernels_rr = kr;
     if (kernels_step) *kernels_step = 2;   // k_cg_update, k_cg_direction
+    return COFEM_OK;
+}
+
+cofem_status cofem_true_residuals(cofem_ctx* c, double* out) {
+    g_err[0] = 0;
+    if (!c || !out) return fail(COFEM_ERR_INVALID_ARG, "NULL argument");
+    if (c->last_T == 0) return fail(COFEM_ERR_INVALID_ARG, "no fit yet");
+    if (!precise(c)) return fail(COFEM_ERR_INVALID_ARG, "the handle has neither rr_period > 0 nor check_residual = 1");
+    CK(cudaSetDevice(c->device));
+    CK(cudaMemcpy2DAsync(out, c->last_Q * sizeof(double), c->res_dev, COFEM_QMAX * sizeof(double),
+                         c->last_Q * sizeof(double), c->last_T, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return COFEM_OK;
+}
+
+cofem_status cofem_fit_stats(cofem_ctx* c, int* replacements, int* checks) {
+    g_err[0] = 0;
+    if (!c) return fail(COFEM_ERR_INVALID_ARG, "handle is NULL");
+    if (c->last_T == 0) return fail(COFEM_ERR_INVALID_ARG, "no fit yet");
+    if (replacements) *replacements = c->last_rr;
+    if (checks) *checks = c->last_check;
     return COFEM_OK;
 }
 

@@ -15,6 +15,7 @@
 #define COFEM_VEC_CHUNK 4096   // elements of one column handled by a vector-kernel block
 #endif
 #define COFEM_VEC_THREADS 256
+#define COFEM_DCT_MAX_D 32768  // largest DCT dictionary (D/2 complex points in shared memory)
 
 // ---------------------------------------------------------------------------
 // Device-resident control block: fit parameters plus the per-column CG scalars
@@ -25,6 +26,8 @@ struct DevCtl {
     double beta, tol, alpha_max;
     unsigned long long seed;
     int T, K, Q, maxit, conv, rr_period, prior;
+    int L;            // tasks (multi-task fit: Q = L (K + 1), column l (K+1) + k of task l)
+    int precond_none; // M = I (unpreconditioned CG) instead of M = beta theta + alpha
     int t;            // current EM iteration, 1-based
     int u;            // CG iterations done in EM iteration t
     int any_active;   // some column still iterating
@@ -42,17 +45,34 @@ struct DevCtl {
     int ap_n;
     const double* tt_part;      // the CG operator's partials of ||Phi p||^2: [q][tt_n]
     int tt_n;
+    // precision form: accurate residual replacement and the true-residual check
+    int fix_residual;           // 1: a column whose true residual misses tol restarts from it
+    int verify_again;           // the last check restarted some column
+    int n_rr, n_check;          // replacements and checks during the fit
+    int broken[COFEM_QMAX];     // column frozen by a breakdown in this EM iteration
+    int restart[COFEM_QMAX];    // column restarted by the last check
+    double rt2[COFEM_QMAX];     // ||B - A X||^2 of the last check (FP32-pair product)
 };
+
+// Column q of the block: task q / (K+1), and k = q mod (K+1) (0: the mu system
+// beta Phi^T y_task, k >= 1: probe k of that task).
+__device__ __forceinline__ void column_task(const DevCtl* ctl, int q, int& task, int& k) {
+    const int Qt = ctl->K + 1;
+    task = q / Qt;
+    k = q - task * Qt;
+}
+
+// Modes of the accurate residual (kernels_accurate.cu).
+#define DF_RR 0      // residual replacement: R = B - A X for the active columns
+#define DF_CHECK 1   // true-residual check: Rt = B - A X for every column
 
 // Modes of the operator kernels.
 // OP_CG: apply to P inside the CG loop (forms pi, gamma; the tensor-core path
 //        reads the split of P written by the direction kernel and leaves Psi as
 //        segment partials for the update kernel);
-// OP_RR: apply to X for residual replacement (split of X made here, partials
-//        read by the residual kernel);
 // OP_PLAIN: stand-alone application (split made here, Psi summed into U);
 // OP_TIME: the OP_CG launch sequence without touching the CG scalars (timing).
-enum OpMode { OP_CG = 0, OP_RR = 1, OP_PLAIN = 2, OP_TIME = 3 };
+enum OpMode { OP_CG = 0, OP_PLAIN = 2, OP_TIME = 3 };
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) and the probe rule:
@@ -72,9 +92,10 @@ __device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64
     }
 }
 
-// The 64-bit word of the probe block that holds bits for j .. (j | 63).
-__device__ __forceinline__ uint64_t probe_word(unsigned long long seed, int t, int k, long long j) {
-    uint64_t c[4] = {(uint64_t)(j >> 8), (uint64_t)k, (uint64_t)t, 0ull};
+// The 64-bit word of the probe block that holds bits for j .. (j | 63); task
+// is the counter's last word (multi-task fits; 0 for a single task).
+__device__ __forceinline__ uint64_t probe_word(unsigned long long seed, int t, int k, long long j, int task = 0) {
+    uint64_t c[4] = {(uint64_t)(j >> 8), (uint64_t)k, (uint64_t)t, (uint64_t)task};
     philox4x64_10(c, seed, 0ull);
     const int w = (int)((j & 255) >> 6);
     return w == 0 ? c[0] : (w == 1 ? c[1] : (w == 2 ? c[2] : c[3]));
@@ -101,6 +122,16 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Sum of n per-block partials by one warp: lane l adds partials l, l + 32, ...
+// in order, then a butterfly over the lanes; every lane, and every block that
+// sums the same partials, gets the same bits.
+__device__ __forceinline__ double warp_sum_parts(const double* src, int n) {
+    double v = 0.0;
+#pragma unroll 4
+    for (int i = threadIdx.x & 31; i < n; i += 32) v += __ldcg(src + i);
+    return warp_sum(v);
 }
 
 // Block sum of per-thread FP32 values: FP32 within each warp, FP64 across warps
@@ -281,28 +312,6 @@ __device__ __forceinline__ float4 op_sum4(const OpOut& o, int Q, int q, long lon
         u.x += x.x; u.y += x.y; u.z += x.z; u.w += x.w;
     }
     return u;
-}
-
-// Psi for elements j..j+3 of column q: beta * (Phi^T Phi v) + alpha_j v_j.
-__device__ __forceinline__ float4 psi4(const OpOut& o, int Q, int q, long long Dp, long long j, float beta,
-                                       float4 av, float4 vv) {
-    float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (o.grp_seg) {
-        const int g = (int)(j / o.GR), r = (int)(j % o.GR);
-        const int s0 = o.grp_seg[2 * g], ns = o.grp_seg[2 * g + 1];
-        for (int s = 0; s < ns; ++s) {
-            const float4 w = *reinterpret_cast<const float4*>(o.U + ((size_t)(s0 + s) * Q + q) * o.GR + r);
-            u.x += w.x; u.y += w.y; u.z += w.z; u.w += w.w;
-        }
-    } else {
-        for (int s = 0; s < o.S2; ++s) {
-            const float4 w = *reinterpret_cast<const float4*>(o.U + (size_t)s * o.sstride + (size_t)q * Dp + j);
-            u.x += w.x; u.y += w.y; u.z += w.z; u.w += w.w;
-        }
-    }
-    const float bu = beta * o.uscale;
-    return make_float4(bu * u.x + av.x * vv.x, bu * u.y + av.y * vv.y, bu * u.z + av.z * vv.z,
-                       bu * u.w + av.w * vv.w);
 }
 
 // ---------------------------------------------------------------------------
@@ -513,6 +522,9 @@ struct cofem_ctx {
     void* tc = nullptr;              // tensor-core operator plan (kernels_tc.cu)
     bool use_tc = false;             // dense dictionary applied on the tensor cores
     float* h = nullptr;              // Toeplitz filter, L floats
+    int* dct_rows = nullptr;         // DCT dictionary: the N kept rows of Omega^-1
+    float* dct_mask = nullptr;       // DCT dictionary: 1 at the kept rows, Dp floats
+    float2* dct_tw = nullptr;        // DCT dictionary: FFT twiddles e^{-2 pi i m / (D/2)}, D/4 of them
     float* theta = nullptr;          // Dp
 
     // fit workspace (sized for Qcap columns)
@@ -520,8 +532,11 @@ struct cofem_ctx {
     int QP = 0;                      // padded column count of the dense intermediate T
     float *X = nullptr, *R = nullptr, *P = nullptr;   // Qcap x Dp each
     float *U = nullptr;              // operator output partials, S2 x Qcap x Dp
-    float *alpha = nullptr, *minv = nullptr, *b = nullptr, *yv = nullptr;   // Dp (yv: Np)
-    float *mu_out = nullptr, *s_out = nullptr;        // Dp
+    float *alpha = nullptr, *minv = nullptr;          // Dp
+    float *b = nullptr, *yv = nullptr;                // Lcap x Dp (yv: Lcap x Np): one per task
+    float *mu_out = nullptr, *s_out = nullptr;        // Lcap x Dp
+    int Lcap = 1;                                     // tasks the per-task buffers hold
+    int graph_L = -1;                                 // tasks of the cached fit graph
     float *T = nullptr;              // dense: Np x QP
     float *Tpart = nullptr;          // dense: S1 x Np x QP
     double* part = nullptr;          // vector-kernel partials: 3 x Qcap x nch
@@ -530,6 +545,18 @@ struct cofem_ctx {
     unsigned* check_flag = nullptr;  // one word for input finiteness checks
     uint8_t* phi8 = nullptr;         // FP8 E4M3 codes (Np x Dp), FP8 form
     float* scale8 = nullptr;         // per-row scales (Np), FP8 form
+    // precision form (rr_period > 0 or check_residual): X = X + Xlo as an FP32
+    // pair, the accurate residual's buffers, per-E-step true residuals
+    float* Xlo = nullptr;            // Qcap x Dp
+    float* Rt = nullptr;             // Qcap x Dp: the last checked true residual
+    double* df_T = nullptr;          // k-split partials of Phi~ X
+    float *df_thi = nullptr, *df_tlo = nullptr;   // Phi~ X as an FP32 pair
+    double* df_U = nullptr;          // k-split partials of Phi~^T t: [s][q][j]
+    double* res_dev = nullptr;       // iters_cap x COFEM_QMAX relative true residuals
+    int df_QP = 0, df_S1 = 1, df_S2 = 1;
+    int last_T = 0, last_Q = 0;      // EM iterations and columns of the last fit
+    int last_rr = 0, last_check = 0; // residual replacements and checks of the last fit
+    long long df_k1 = 0, df_k2 = 0;
     int* iters_dev = nullptr;        // T_em
     int iters_cap = 0;
     DevCtl* ctl = nullptr;
@@ -556,7 +583,6 @@ void launch_fit_setup(Sink& s, cofem_ctx* c, int Q);                 // alpha ->
 void launch_cg_init(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg);
 void launch_cg_update(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_rr,
                       cudaGraphConditionalHandle h_cg);
-void launch_rr_residual(Sink& s, cofem_ctx* c, int Q);
 void launch_cg_direction(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg);
 void launch_mstep(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_em);
 void launch_probe_fill(cudaStream_t st, unsigned long long seed, int t, int K, long long D,
@@ -568,6 +594,18 @@ void launch_quantize_bf16(cudaStream_t st, const float* src, long long rows, lon
 void launch_check_finite(cudaStream_t st, const float* x, long long n, unsigned* bad);
 void launch_dot_rows(cudaStream_t st, const float* a, long long lda, const float* b, long long ldb, long long n,
                      int rows, double* out);
+
+// kernels_accurate.cu (precision form)
+struct DfSizes {
+    int QP, S1, S2;
+    long long k1, k2;
+    size_t t, T, U;   // elements of df_thi / df_tlo, df_T, df_U
+};
+DfSizes df_configure(cofem_ctx* c, int Q);
+void launch_true_residual(Sink& s, cofem_ctx* c, int Q, int mode);
+int true_residual_kernels(cofem_ctx* c);
+void launch_df_check(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_vf);
+void launch_cg_gate(Sink& s, cofem_ctx* c, cudaGraphConditionalHandle h_cg);
 
 // kernels_dense.cu
 void dense_configure(cofem_ctx* c, int Q);
@@ -592,9 +630,17 @@ void launch_toeplitz_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int 
 void launch_toeplitz_theta(cudaStream_t st, cofem_ctx* c);
 void launch_toeplitz_phit_y(cudaStream_t st, cofem_ctx* c, const float* y, double scale, float* out);
 
+// kernels_dct.cu
+size_t dct_smem_bytes(long long D);
+cudaError_t dct_kernel_attributes();
+void launch_dct_setup(cudaStream_t st, cofem_ctx* c);
+void launch_dct_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode);
+void launch_dct_phit_y(cudaStream_t st, cofem_ctx* c, const float* y, double scale, float* out, float* tmp);
+
 // dispatch
 inline void launch_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode) {
     if (c->kind == COFEM_OP_DENSE) launch_dense_operator(s, c, Q, V, mode);
+    else if (c->kind == COFEM_OP_DCT) launch_dct_operator(s, c, Q, V, mode);
     else launch_toeplitz_operator(s, c, Q, V, mode);
 }
 

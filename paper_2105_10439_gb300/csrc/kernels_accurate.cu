@@ -1,0 +1,448 @@
+// Accurate residual R = B - A X of the precision form: residual replacement
+// inside the CG loop and the true-residual check at the end of each E-step.
+//
+// Why a separate path.  The CG state is FP32 and the operator of the CG loop
+// accumulates in FP32, so its error is about 2^-24 ||A| |x||.  On the
+// underdetermined dictionaries of the dense workloads most of a probe
+// solution lies in the null space of Phi, where beta Phi^T (Phi x) is a
+// cancellation of terms 10^3-10^4 times larger than the right-hand side: an
+// FP32 product then cannot tell whether ||b - A x|| <= 1e-5 ||b||.  Here X is
+// held as an unevaluated pair of FP32 numbers (X + Xlo, updated exactly by the
+// CG kernels) and A X is formed with error-free transformations in FP32 pairs
+// (TwoProduct through the FMA, Knuth's TwoSum: the compensated dot product of
+// Ogita, Rump and Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput.
+// 2005), which carries about 2^-48 relative error; partial sums across
+// threads and blocks and the residual itself are FP64.  The GB300's FP64 rate
+// is a small fraction of its FP32 rate, so the inner products stay in FP32
+// pairs on the CUDA cores.
+//
+// Dense dictionary (row-major Phi~, FP32 / BF16 / FP8 codes with row scales):
+//   k_df_gemm<E, false>   T_s = Phi~ X over a k range s (FP64 partials)
+//   k_df_combine_t        t = sum_s T_s (times s_i^2 for FP8) as an FP32 pair
+//   k_df_gemm<E, true>    U_s = Phi~^T t over an i range s (FP64 partials)
+//   k_df_residual         R = B - beta sum_s U_s - alpha X (FP64), norms
+// Convolution dictionary:
+//   k_df_conv, k_df_conv_t (direct sums over the L taps), k_df_residual.
+#include <cuda_fp8.h>
+
+#include "cofem_internal.cuh"
+
+namespace {
+
+constexpr int NT = COFEM_VEC_THREADS;
+constexpr int CH = COFEM_VEC_CHUNK;
+
+// ---------------------------------------------------------------------------
+// FP32-pair arithmetic.  The _rn intrinsics are never contracted into FMAs,
+// which the error-free transformations rely on.
+// ---------------------------------------------------------------------------
+// (S, C) += a * (xh + xl): p + e = a * xh exactly (FMA), a * xl is below the
+// pair's precision in its own rounding; S + p = s + t exactly (TwoSum).
+__device__ __forceinline__ void df_mac(float& S, float& C, float a, float xh, float xl) {
+    const float p = __fmul_rn(a, xh);
+    float e = __fmaf_rn(a, xh, -p);
+    e = __fmaf_rn(a, xl, e);
+    const float s = __fadd_rn(S, p);
+    const float z = __fsub_rn(s, S);
+    const float t = __fadd_rn(__fsub_rn(S, __fsub_rn(s, z)), __fsub_rn(p, z));
+    S = s;
+    C = __fadd_rn(C, __fadd_rn(t, e));
+}
+
+// x = hi + lo with hi = fl(x), |lo| <= ulp(hi) / 2 (split of an FP64 value).
+__device__ __forceinline__ void df_split(double x, float& hi, float& lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
+template <typename E> __device__ __forceinline__ float elem(E v);
+template <> __device__ __forceinline__ float elem<float>(float v) { return v; }
+template <> __device__ __forceinline__ float elem<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+// an E4M3 code as its value (exact: every E4M3 value is an FP16 value)
+template <> __device__ __forceinline__ float elem<uint8_t>(uint8_t v) {
+    return __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)v, __NV_E4M3)));
+}
+
+// ---------------------------------------------------------------------------
+// Dense product in FP32 pairs.  out[s][m][q] = sum over k in chunk s of
+// A(m, k) (Xh + Xl)(k, q), with A(m, k) = A[m lda + k] (TRANS false: Phi~ X)
+// or A[k lda + m] (TRANS true: Phi~^T t), X(k, q) = X[k xk + q xq].  A block
+// owns DF_BM rows of the output and all (padded) QP columns for one k chunk;
+// thread (tm, tq) keeps the DF_TM x DF_TQ micro tile of rows tm*4.. and
+// columns tq*4.. as FP32 pairs.  Operand tiles of DF_KC k values are staged
+// in shared memory ([k][m] and [k][q], so the inner loop reads float4s).
+// ---------------------------------------------------------------------------
+constexpr int DF_BM = 64, DF_KC = 32, DF_TM = 4, DF_TQ = 4;
+constexpr int DF_AP = DF_BM + 4;          // padded row of the A tile (float4 aligned)
+constexpr int DF_QMAXP = COFEM_QMAX + 4;  // padded row of the X tiles
+
+template <typename E, bool TRANS>
+__global__ __launch_bounds__(256) void k_df_gemm(const E* __restrict__ A, long long lda, long long M, long long K,
+                                                 long long kchunk, const float* __restrict__ Xh,
+                                                 const float* __restrict__ Xl, long long xk, long long xq, int Q,
+                                                 int QP, double* __restrict__ out, long long osS, long long osM,
+                                                 long long osQ) {
+    __shared__ __align__(16) float As[DF_KC][DF_AP];
+    __shared__ __align__(16) float Hs[DF_KC][DF_QMAXP];
+    __shared__ __align__(16) float Ls[DF_KC][DF_QMAXP];
+    const int nthr = blockDim.x;
+    const int tm = threadIdx.x % (DF_BM / DF_TM), tq = threadIdx.x / (DF_BM / DF_TM);
+    const long long m0 = (long long)blockIdx.x * DF_BM;
+    const long long kb = (long long)blockIdx.y * kchunk;
+    const long long ke = kb + kchunk < K ? kb + kchunk : K;
+    float S[DF_TM][DF_TQ], C[DF_TM][DF_TQ];
+#pragma unroll
+    for (int a = 0; a < DF_TM; ++a)
+#pragma unroll
+        for (int b = 0; b < DF_TQ; ++b) S[a][b] = C[a][b] = 0.0f;
+    for (long long k0 = kb; k0 < ke; k0 += DF_KC) {
+        __syncthreads();   // the previous tile has been read
+        // A tile: rows m0.., k values k0.. (zero outside M x [kb, ke))
+        for (int e = threadIdx.x; e < DF_BM * DF_KC; e += nthr) {
+            int mm, kk;
+            if (TRANS) { kk = e / DF_BM; mm = e % DF_BM; }   // contiguous in m
+            else { mm = e / DF_KC; kk = e % DF_KC; }         // contiguous in k
+            const long long m = m0 + mm, k = k0 + kk;
+            float v = 0.0f;
+            if (m < M && k < ke) v = elem<E>(TRANS ? A[k * lda + m] : A[m * lda + k]);
+            As[kk][mm] = v;
+        }
+        // X tiles (zero for q >= Q and outside the k range)
+        for (int e = threadIdx.x; e < DF_KC * QP; e += nthr) {
+            int kk, q;
+            if (xq == 1) { kk = e / QP; q = e % QP; }   // contiguous in q
+            else { q = e / DF_KC; kk = e % DF_KC; }      // contiguous in k
+            const long long k = k0 + kk;
+            float h = 0.0f, l = 0.0f;
+            if (q < Q && k < ke) {
+                const long long idx = k * xk + (long long)q * xq;
+                h = Xh[idx];
+                l = Xl[idx];
+            }
+            Hs[kk][q] = h;
+            Ls[kk][q] = l;
+        }
+        __syncthreads();
+        if (tq * DF_TQ < QP) {
+#pragma unroll 4
+            for (int kk = 0; kk < DF_KC; ++kk) {
+                const float4 a4 = *reinterpret_cast<const float4*>(&As[kk][tm * DF_TM]);
+                const float4 h4 = *reinterpret_cast<const float4*>(&Hs[kk][tq * DF_TQ]);
+                const float4 l4 = *reinterpret_cast<const float4*>(&Ls[kk][tq * DF_TQ]);
+                const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+                const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
+                const float lv[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+                for (int a = 0; a < DF_TM; ++a)
+#pragma unroll
+                    for (int b = 0; b < DF_TQ; ++b) df_mac(S[a][b], C[a][b], av[a], hv[b], lv[b]);
+            }
+        }
+    }
+    if (tq * DF_TQ >= QP) return;
+#pragma unroll
+    for (int a = 0; a < DF_TM; ++a) {
+        const long long m = m0 + tm * DF_TM + a;
+        if (m >= M) continue;
+#pragma unroll
+        for (int b = 0; b < DF_TQ; ++b) {
+            const int q = tq * DF_TQ + b;
+            if (q < Q) out[blockIdx.y * osS + m * osM + q * osQ] = (double)S[a][b] + (double)C[a][b];
+        }
+    }
+}
+
+// t[i][q] = sum_s Tpart[s][i][q] (times scale[i]^2: Phi~ = diag(scale) C for
+// the FP8 form, so Phi~^T Phi~ x = C^T diag(scale^2) C x), as an FP32 pair in
+// the [i][QP] layout the transposed product reads; zero for i >= N, q >= Q.
+__global__ void k_df_combine_t(const double* __restrict__ Tpart, int S, long long N, long long Np, int Q, int QP,
+                               const float* __restrict__ scale, float* __restrict__ thi, float* __restrict__ tlo) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= Np * QP) return;
+    const long long i = e / QP;
+    const int q = (int)(e % QP);
+    double v = 0.0;
+    if (i < N && q < Q) {
+        for (int s = 0; s < S; ++s) v += Tpart[(size_t)s * Np * QP + e];
+        if (scale) {
+            const double sc = scale[i];
+            v *= sc * sc;
+        }
+    }
+    float h, l;
+    df_split(v, h, l);
+    thi[e] = h;
+    tlo[e] = l;
+}
+
+// Convolution dictionary, (Phi x)_i = sum_{tau < L, tau <= i} h[tau] x[i - tau],
+// one thread per (i, q), FP32 pairs; t[q][i] as an FP32 pair (i < Np).
+__global__ void k_df_conv(const float* __restrict__ h, int L, long long N, long long Dp,
+                          const float* __restrict__ X, const float* __restrict__ Xlo, float* __restrict__ thi,
+                          float* __restrict__ tlo) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = blockIdx.y;
+    if (i >= Dp) return;
+    float S = 0.0f, C = 0.0f;
+    if (i < N) {
+        const float* x = X + (size_t)q * Dp;
+        const float* xl = Xlo + (size_t)q * Dp;
+        const int tmax = (long long)L - 1 < i ? L - 1 : (int)i;
+        for (int tau = 0; tau <= tmax; ++tau) df_mac(S, C, __ldg(h + tau), x[i - tau], xl[i - tau]);
+    }
+    float hh, ll;
+    df_split((double)S + (double)C, hh, ll);
+    thi[(size_t)q * Dp + i] = hh;
+    tlo[(size_t)q * Dp + i] = ll;
+}
+
+// (Phi^T t)_j = sum_{tau < L, j + tau < N} h[tau] t[j + tau] into U[q][j] (FP64).
+__global__ void k_df_conv_t(const float* __restrict__ h, int L, long long N, long long Dp,
+                            const float* __restrict__ thi, const float* __restrict__ tlo, double* __restrict__ U) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = blockIdx.y;
+    if (j >= Dp) return;
+    float S = 0.0f, C = 0.0f;
+    if (j < N) {
+        const float* th = thi + (size_t)q * Dp;
+        const float* tl = tlo + (size_t)q * Dp;
+        const long long rem = N - 1 - j;
+        const int tmax = (long long)L - 1 < rem ? L - 1 : (int)rem;
+        for (int tau = 0; tau <= tmax; ++tau) df_mac(S, C, __ldg(h + tau), th[j + tau], tl[j + tau]);
+    }
+    U[(size_t)q * Dp + j] = j < N ? (double)S + (double)C : 0.0;
+}
+
+// Right-hand side B[j][q]: b of the column's task (k = 0) or its probe k of
+// EM iteration t.
+__device__ __forceinline__ double rhs(const DevCtl* ctl, const float* b, int q, long long j, long long D,
+                                      long long Dp) {
+    int task, k;
+    column_task(ctl, q, task, k);
+    if (k == 0) return (double)b[(size_t)task * Dp + j];
+    if (j >= D) return 0.0;
+    return (double)probe_sign_from_word(probe_word(ctl->seed, ctl->t, k, j, task), j);
+}
+
+// R = B - beta U - alpha (X + Xlo) in FP64 for column q (block (ch, q)), with
+// U = sum_s Upart[s][q][j].  mode DF_RR (residual replacement): active columns
+// take R, and the partials of ||r||^2 and r^T M^-1 r go where the direction
+// kernel reads the update's (slabs 0 and 1).  mode DF_CHECK: every column's
+// true residual goes to Rt and the partials of ||r||^2 to slab 0.
+__global__ __launch_bounds__(NT) void k_df_residual(DevCtl* ctl, int mode, const float* __restrict__ b,
+                                                    const float* __restrict__ X, const float* __restrict__ Xlo,
+                                                    const double* __restrict__ Upart, int S, size_t sstride,
+                                                    const float* __restrict__ alpha, const float* __restrict__ minv,
+                                                    float* __restrict__ Rout, long long D, long long Dp, int nch,
+                                                    double* part) {
+    __shared__ double sh[NT / 32];
+    const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q;
+    const bool on = mode == DF_CHECK ? ctl->bnorm2[q] > 0.0 : ctl->active[q] != 0;
+    const double beta = ctl->beta;
+    double rr = 0.0, rz = 0.0;
+    if (on) {
+        const size_t off = (size_t)q * Dp;
+        for (int e = threadIdx.x; e < CH; e += NT) {
+            const long long j = (long long)ch * CH + e;
+            if (j >= Dp) break;
+            double r = 0.0;   // padding beyond D stays zero
+            if (j < D) {
+                double u = 0.0;
+                for (int s = 0; s < S; ++s) u += Upart[(size_t)s * sstride + off + j];
+                const double x = (double)X[off + j] + (double)Xlo[off + j];
+                r = rhs(ctl, b, q, j, D, Dp) - beta * u - (double)alpha[j] * x;
+            }
+            Rout[off + j] = (float)r;
+            rr += r * r;
+            rz += r * r * (double)minv[j];
+        }
+    }
+    rr = block_sum(rr, sh);
+    rz = block_sum(rz, sh);
+    if (threadIdx.x == 0) {
+        part[(size_t)(0 * Q + q) * nch + ch] = rr;
+        if (mode == DF_RR) part[(size_t)(1 * Q + q) * nch + ch] = rz;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// True-residual check at the end of the CG loop (block (ch, q)).  Every block
+// sums the partials of ||B - A X||^2 of its column (all columns for the
+// Frobenius test) in a fixed order, so all blocks of a column take the same
+// decision.  Block 0 of the column records ||r_q|| / ||b_q|| for EM iteration
+// t.  With fix = 1, a column whose true residual misses the tolerance (not
+// broken down, CG budget left) restarts from it: R = R_true, P = M^-1 R,
+// and the last block to arrive forms rho = R^T M^-1 R, reactivates those
+// columns and keeps the verification loop going.
+// ---------------------------------------------------------------------------
+__global__ __launch_bounds__(NT) void k_df_check(DevCtl* ctl, const float* __restrict__ Rt, float* __restrict__ R,
+                                                 float* __restrict__ P, const float* __restrict__ minv,
+                                                 const float* __restrict__ alpha, long long Dp, int nch,
+                                                 double* part, unsigned* counter, double* res,
+                                                 cudaGraphConditionalHandle h_vf, SplitOut so) {
+    __shared__ double sh[NT / 32];
+    __shared__ double s_rt[COFEM_QMAX];
+    __shared__ int s_fail;
+    const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q;
+    const int w = threadIdx.x >> 5;
+    const bool frob = ctl->conv == COFEM_CONV_FROBENIUS;
+    for (int k = w; k < Q; k += NT / 32) {
+        if (!frob && k != q) continue;
+        const double v = warp_sum_parts(part + (size_t)k * nch, nch);
+        if ((threadIdx.x & 31) == 0) s_rt[k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double t2 = ctl->tol * ctl->tol, bn2 = ctl->bnorm2[q], rt2 = s_rt[q];
+        bool pass = true;
+        if (bn2 > 0.0) {
+            if (frob) {
+                double num = 0.0, den = 0.0;
+                for (int k = 0; k < Q; ++k) {
+                    if (ctl->bnorm2[k] > 0.0) num += s_rt[k];
+                    den += ctl->bnorm2[k];
+                }
+                pass = num <= t2 * den;
+            } else {
+                pass = rt2 <= t2 * bn2;
+            }
+        }
+        const bool can = ctl->fix_residual && !ctl->broken[q] && ctl->u < ctl->maxit;
+        const int fail = !pass && can;
+        s_fail = fail;
+        if (ch == 0) {
+            ctl->restart[q] = fail;
+            ctl->rt2[q] = rt2;
+            if (res) res[(size_t)(ctl->t - 1) * COFEM_QMAX + q] = bn2 > 0.0 ? sqrt(rt2 / bn2) : 0.0;
+            if (!pass && ctl->fix_residual && !ctl->broken[q] && !can)
+                atomicOr(&ctl->flags, COFEM_FLAG_CG_NOT_CONVERGED);
+        }
+    }
+    __syncthreads();
+    float rz = 0.0f, ap = 0.0f;
+    if (s_fail) {
+        const size_t off = (size_t)q * Dp;
+        for (int e = threadIdx.x * 4; e < CH; e += NT * 4) {
+            const long long j = (long long)ch * CH + e;
+            if (j >= Dp) break;
+            const float4 r = *reinterpret_cast<const float4*>(Rt + off + j);
+            const float4 m = *reinterpret_cast<const float4*>(minv + j);
+            const float4 a = *reinterpret_cast<const float4*>(alpha + j);
+            const float4 p = make_float4(r.x * m.x, r.y * m.y, r.z * m.z, r.w * m.w);
+            *reinterpret_cast<float4*>(R + off + j) = r;
+            *reinterpret_cast<float4*>(P + off + j) = p;
+            store_split(so, q, j, p);
+            rz += r.x * p.x + r.y * p.y + r.z * p.z + r.w * p.w;
+            ap += a.x * p.x * p.x + a.y * p.y * p.y + a.z * p.z * p.z + a.w * p.w * p.w;
+        }
+    }
+    const double rzd = block_sum_f(rz, sh);
+    const double apd = block_sum_f(ap, sh);
+    if (threadIdx.x == 0 && s_fail) {   // slab 0 (the true residuals) is still read by other blocks
+        part[(size_t)(1 * Q + q) * nch + ch] = rzd;
+        part[(size_t)(2 * Q + q) * nch + ch] = apd;
+    }
+    if (!last_block_arrive(counter, gridDim.x * gridDim.y)) return;
+    int any = 0;
+    for (int k = threadIdx.x; k < Q; k += blockDim.x) {
+        if (!ctl->restart[k]) continue;
+        double v = 0.0;
+        for (int i = 0; i < nch; ++i) v += __ldcg(part + (size_t)(1 * Q + k) * nch + i);
+        ctl->rho[ctl->u & 1][k] = v;   // the next update reads rho of parity u
+        ctl->rnorm2[k] = ctl->rt2[k];
+        ctl->active[k] = 1;
+        any = 1;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        ctl->n_check += 1;
+        ctl->any_active = any;
+        ctl->verify_again = any;
+        set_cond(h_vf, any);
+    }
+}
+
+// Enters the CG loop of a verification round only if some column is active
+// and the CG budget is not spent.
+__global__ void k_cg_gate(DevCtl* ctl, cudaGraphConditionalHandle h_cg) {
+    if (threadIdx.x == 0) set_cond(h_cg, ctl->any_active && ctl->u < ctl->maxit);
+}
+
+int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// k split of a product with M output rows and K terms: enough blocks for four
+// per SM, k chunks a whole number of shared-memory tiles.
+void df_split_k(long long M, long long K, int sms, int* S, long long* kchunk) {
+    const int mb = ceil_div(M, DF_BM);
+    int s = ceil_div(4LL * sms, mb);
+    const int smax = ceil_div(K, DF_KC);
+    if (s > smax) s = smax;
+    if (s < 1) s = 1;
+    long long kc = ((K + s - 1) / s + DF_KC - 1) / DF_KC * DF_KC;
+    *kchunk = kc;
+    *S = ceil_div(K, kc);
+}
+
+template <typename E>
+void launch_df_dense(Sink& s, cofem_ctx* c, int Q, const E* phi) {
+    const int QP = c->df_QP;
+    const dim3 blk(16 * (QP / DF_TQ));
+    s.launch(k_df_gemm<E, false>, dim3(ceil_div(c->N, DF_BM), c->df_S1), blk, 0, phi, c->Dp, c->N, c->D,
+             c->df_k1, c->X, c->Xlo, 1LL, c->Dp, Q, QP, c->df_T, c->Np * QP, (long long)QP, 1LL);
+    s.launch(k_df_combine_t, dim3(ceil_div(c->Np * QP, 256)), dim3(256), 0, c->df_T, c->df_S1, c->N, c->Np, Q, QP,
+             c->phi8 ? (const float*)c->scale8 : (const float*)nullptr, c->df_thi, c->df_tlo);
+    s.launch(k_df_gemm<E, true>, dim3(ceil_div(c->D, DF_BM), c->df_S2), blk, 0, phi, c->Dp, c->D, c->N, c->df_k2,
+             c->df_thi, c->df_tlo, (long long)QP, 1LL, Q, QP, c->df_U, (long long)QP * c->Dp, 1LL, c->Dp);
+}
+
+}  // namespace
+
+// Sizes of the accurate-residual workspace for Q columns (kernels_accurate.cu
+// owns the layout): the k splits and the element counts of each buffer.
+DfSizes df_configure(cofem_ctx* c, int Q) {
+    DfSizes z{};
+    z.QP = (Q + DF_TQ - 1) / DF_TQ * DF_TQ;
+    if (c->kind == COFEM_OP_DENSE) {
+        df_split_k(c->N, c->D, c->num_sms, &z.S1, &z.k1);
+        df_split_k(c->D, c->N, c->num_sms, &z.S2, &z.k2);
+        z.t = (size_t)c->Np * z.QP;
+        z.T = (size_t)z.S1 * c->Np * z.QP;
+        z.U = (size_t)z.S2 * z.QP * c->Dp;
+    } else {
+        z.S1 = z.S2 = 1;
+        z.t = (size_t)z.QP * c->Dp;
+        z.T = 0;
+        z.U = (size_t)z.QP * c->Dp;
+    }
+    return z;
+}
+
+// R_out = B - A (X + Xlo) for the active columns (DF_RR, into R) or for every
+// column (DF_CHECK, into Rt), with the norm partials the next kernel reads.
+void launch_true_residual(Sink& s, cofem_ctx* c, int Q, int mode) {
+    if (c->kind == COFEM_OP_DENSE) {
+        if (c->phi16) launch_df_dense<__nv_bfloat16>(s, c, Q, c->phi16);
+        else if (c->phi8) launch_df_dense<uint8_t>(s, c, Q, c->phi8);
+        else launch_df_dense<float>(s, c, Q, c->phi32);
+    } else {
+        const dim3 g((unsigned)ceil_div(c->Dp, 256), Q);
+        s.launch(k_df_conv, g, dim3(256), 0, c->h, c->L, c->N, c->Dp, c->X, c->Xlo, c->df_thi, c->df_tlo);
+        s.launch(k_df_conv_t, g, dim3(256), 0, c->h, c->L, c->N, c->Dp, c->df_thi, c->df_tlo, c->df_U);
+    }
+    const size_t sstride = (size_t)c->df_QP * c->Dp;
+    s.launch(k_df_residual, dim3(c->nch, Q), dim3(NT), 0, c->ctl, mode, c->b, c->X, c->Xlo, c->df_U, c->df_S2,
+             sstride, c->alpha, c->minv, mode == DF_RR ? c->R : c->Rt, c->D, c->Dp, c->nch, c->part);
+}
+
+int true_residual_kernels(cofem_ctx* c) {
+    return c->kind == COFEM_OP_DENSE ? 4 : (c->kind == COFEM_OP_TOEPLITZ ? 3 : 0);   // not built for the DCT
+}
+
+void launch_df_check(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_vf) {
+    s.launch(k_df_check, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->Rt, c->R, c->P, c->minv, c->alpha, c->Dp, c->nch,
+             c->part, c->counters + 12, c->res_dev, h_vf, tc_direction_split(c));
+}
+
+void launch_cg_gate(Sink& s, cofem_ctx* c, cudaGraphConditionalHandle h_cg) {
+    s.launch(k_cg_gate, dim3(1), dim3(32), 0, c->ctl, h_cg);
+}

@@ -1029,13 +1029,13 @@ OpOut op_output(cofem_ctx* c) {
 
 // In the CG loop (OP_CG, OP_TIME) the split of P is already in Vs (written by
 // k_cg_init / k_cg_direction) and the update kernel reads GEMM2's segment
-// partials directly; residual replacement (OP_RR) splits X here; a stand-alone
-// application (OP_PLAIN) also sums the partials into U.
+// partials directly; a stand-alone application (OP_PLAIN) splits V here and
+// also sums the partials into U.
 void launch_tc_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode) {
     TcPlan* t = (TcPlan*)c->tc;
     const SplitOut sv{t->Vs, t->tf ? 2 : 1, t->QS, t->QH, t->f8 ? F8_BSCALE : 1.0f};
     const SplitOut st{t->Ts, t->tf ? 2 : 1, t->QS, t->QH, t->f8 ? F8_BSCALE : 1.0f};
-    if (mode == OP_RR || mode == OP_PLAIN)
+    if (mode == OP_PLAIN)
         s.launch(k_split, dim3((unsigned)((c->Dp / 4 + 255) / 256), Q), dim3(256), 0, V, c->Dp, sv);
     if (t->fused) {   // writes U and finishes pi, gamma itself
         launch_fused(s, t->fused, mode);
@@ -1061,5 +1061,5 @@ void tc_operator_info(cofem_ctx* c, int* path, int* k_cg, int* k_rr) {
     TcPlan* t = (TcPlan*)c->tc;
     *path = t->fused ? COFEM_PATH_SINGLE_PASS : COFEM_PATH_TWO_PASS;
     *k_cg = t->fused ? 1 : 3;
-    *k_rr = *k_cg + 1;   // k_split of X first
+    *k_rr = true_residual_kernels(c);
 }

@@ -1,6 +1,8 @@
 // Vector kernels of the CoFEM hot path: PCG initialisation, the fused CG
-// update (with pi and gamma), residual replacement, the per-column stopping
-// test with the direction update, and the fused diagonal-estimate + M-step.
+// update (with pi and gamma; X as an exact FP32 pair in the precision form),
+// the per-column stopping test with the direction update, and the fused
+// diagonal-estimate + M-step.  (The accurate residual of the precision form is
+// in kernels_accurate.cu.)
 //
 // Layout: each of X, R, P is Q columns of Dp floats ("column q" of Alg. 2 is
 // the contiguous run [q*Dp, q*Dp + D)); padding entries are kept at zero.
@@ -20,6 +22,16 @@ static_assert(CH % (NT * 4) == 0, "a chunk is a whole number of float4 sweeps of
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+// x + lo += d with x = fl(x + d) and the rounding error of that sum added to lo
+// (Knuth's TwoSum; the _rn intrinsics keep the compiler from fusing it).
+__device__ __forceinline__ void two_sum_acc(float& x, float& lo, float d) {
+    const float s = __fadd_rn(x, d);
+    const float z = __fsub_rn(s, x);
+    const float e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, z)), __fsub_rn(d, z));
+    x = s;
+    lo = __fadd_rn(lo, e);
+}
 
 // Sum the per-block partials part[(k*Q + q)*nch + ch] over ch for k < nk,
 // into out[k*COFEM_QMAX + q] (shared).  One warp per (k, q).
@@ -44,16 +56,6 @@ __device__ void reduce_parts(const double* part, int nk, int Q, int nch, double*
     __syncthreads();
 }
 
-// Sum of n per-block partials by one warp: lane l adds partials l, l + 32, ...
-// in order, then a butterfly over the lanes; every lane, and every block that
-// sums the same partials, gets the same bits.
-__device__ __forceinline__ double warp_sum_parts(const double* src, int n) {
-    double v = 0.0;
-#pragma unroll 4
-    for (int i = threadIdx.x & 31; i < n; i += 32) v += __ldcg(src + i);
-    return warp_sum(v);
-}
-
 // ---------------------------------------------------------------------------
 // Fit set-up: M^-1 = 1 / (beta theta + alpha); t = 1.
 // ---------------------------------------------------------------------------
@@ -61,24 +63,29 @@ __global__ void k_fit_setup(DevCtl* ctl, const float* __restrict__ theta, const 
                             float* __restrict__ minv, long long D, long long Dp) {
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const float beta = (float)ctl->beta;
-    if (j < Dp) minv[j] = j < D ? 1.0f / (beta * theta[j] + alpha[j]) : 0.0f;
+    if (j < Dp) minv[j] = j < D ? (ctl->precond_none ? 1.0f : 1.0f / (beta * theta[j] + alpha[j])) : 0.0f;
     if (j == 0) {
         ctl->t = 1;
         ctl->u = 0;
         ctl->flags = 0u;
+        ctl->n_rr = 0;
+        ctl->n_check = 0;
     }
 }
 
 // ---------------------------------------------------------------------------
 // PCG initialisation (Alg. 2 "Initialize", PCG reading: P_0 = W_0 = M^-1 B):
-// B column 0 = b = beta Phi^T y, columns q >= 1 = probe p_q of EM iteration t.
+// B column 0 = b = beta Phi^T y, columns q >= 1 = probe p_q of EM iteration t
+// (multi-task: the columns of task l are b_l and its probes).
 // X = 0, R = B, P = M^-1 B; rho_q = B^T M^-1 B, ||b_q||^2, p^T diag(alpha) p.
+// h_cg is the condition of the loop that follows: the CG loop, or in the
+// precision form the verification loop around it.
 // ---------------------------------------------------------------------------
 __global__ __launch_bounds__(NT) void k_cg_init(DevCtl* ctl, const float* __restrict__ b,
                                                 const float* __restrict__ minv, const float* __restrict__ alpha,
                                                 float* __restrict__ X, float* __restrict__ R, float* __restrict__ P,
-                                                long long D, long long Dp, int nch, double* part,
-                                                unsigned* counter, cudaGraphConditionalHandle h_cg,
+                                                float* __restrict__ Xlo, long long D, long long Dp, int nch,
+                                                double* part, unsigned* counter, cudaGraphConditionalHandle h_cg,
                                                 SplitOut so) {
     __shared__ double sh[NT / 32];
     __shared__ double red[3 * COFEM_QMAX];
@@ -90,10 +97,12 @@ __global__ __launch_bounds__(NT) void k_cg_init(DevCtl* ctl, const float* __rest
         const long long j = (long long)ch * CH + e;
         if (j >= Dp) break;
         float4 bv;
-        if (q == 0) {
-            bv = ld4(b + j);
+        int task, k;
+        column_task(ctl, q, task, k);
+        if (k == 0) {
+            bv = ld4(b + (size_t)task * Dp + j);
         } else {
-            const uint64_t w = probe_word(seed, t, q, j);   // j..j+3 share one 64-bit word
+            const uint64_t w = probe_word(seed, t, k, j, task);   // j..j+3 share one 64-bit word
             bv.x = j + 0 < D ? probe_sign_from_word(w, j + 0) : 0.0f;
             bv.y = j + 1 < D ? probe_sign_from_word(w, j + 1) : 0.0f;
             bv.z = j + 2 < D ? probe_sign_from_word(w, j + 2) : 0.0f;
@@ -102,6 +111,7 @@ __global__ __launch_bounds__(NT) void k_cg_init(DevCtl* ctl, const float* __rest
         const float4 mv = ld4(minv + j), av = ld4(alpha + j);
         const float4 wv = make_float4(bv.x * mv.x, bv.y * mv.y, bv.z * mv.z, bv.w * mv.w);
         st4(X + off + j, make_float4(0.f, 0.f, 0.f, 0.f));
+        if (Xlo) st4(Xlo + off + j, make_float4(0.f, 0.f, 0.f, 0.f));
         st4(R + off + j, bv);
         st4(P + off + j, wv);
         store_split(so, q, j, wv);
@@ -128,6 +138,7 @@ __global__ __launch_bounds__(NT) void k_cg_init(DevCtl* ctl, const float* __rest
         ctl->rnorm2[qq] = red[qq];
         act = red[qq] > 0.0;   // a zero right-hand side starts converged (x = 0)
         ctl->active[qq] = act;
+        ctl->broken[qq] = 0;
     }
     act = __syncthreads_or(act);
     if (threadIdx.x == 0) {
@@ -144,8 +155,8 @@ __global__ __launch_bounds__(NT) void k_cg_init(DevCtl* ctl, const float* __rest
 __global__ __launch_bounds__(NT, 2) void k_cg_update(DevCtl* ctl, const float* __restrict__ P, OpOut uo,
                                                   const float* __restrict__ alpha,
                                                   const float* __restrict__ minv, float* __restrict__ X,
-                                                  float* __restrict__ R, long long Dp, int nch,
-                                                  double* part, cudaGraphConditionalHandle h_rr,
+                                                  float* __restrict__ R, float* __restrict__ Xlo, long long Dp,
+                                                  int nch, double* part, cudaGraphConditionalHandle h_rr,
                                                   cudaGraphConditionalHandle h_cg) {
     __shared__ double sh[NT / 32];
     __shared__ double s_sum[2];
@@ -159,7 +170,9 @@ __global__ __launch_bounds__(NT, 2) void k_cg_update(DevCtl* ctl, const float* _
         // the stopping test and the loop condition are the direction kernel's
         // (it reads this kernel's partials)
         ctl->any_active = 0;
-        set_cond(h_rr, ctl->rr_period > 0 && u % ctl->rr_period == 0);
+        const bool rr = ctl->rr_period > 0 && u % ctl->rr_period == 0;
+        ctl->n_rr += rr;
+        set_cond(h_rr, rr);
         set_cond(h_cg, 0);
     }
     // all loads of the thread's IT float4 positions first (the kernel is bound
@@ -210,6 +223,7 @@ __global__ __launch_bounds__(NT, 2) void k_cg_update(DevCtl* ctl, const float* _
                 if (!ok) {
                     atomicOr(&ctl->flags, COFEM_FLAG_BREAKDOWN);
                     ctl->active[q] = 0;
+                    ctl->broken[q] = 1;
                 }
             }
         }
@@ -221,14 +235,31 @@ __global__ __launch_bounds__(NT, 2) void k_cg_update(DevCtl* ctl, const float* _
     if (s_act) {   // (implies the loads above were issued)
         const float gamma = s_gamma;
         const float beta = (float)ctl->beta;
+        if (Xlo) {   // precision form: X + Xlo += gamma p, the rounding error of X kept in Xlo (TwoSum)
 #pragma unroll
-        for (int it = 0; it < IT; ++it) {   // X needs no operator output: store it now
-            const long long j = (long long)ch * CH + (long long)(threadIdx.x + it * NT) * 4;
-            if (j < Dp) {
-                float4 x4 = xv[it];
-                const float4 p4 = pv[it];
-                x4.x += gamma * p4.x; x4.y += gamma * p4.y; x4.z += gamma * p4.z; x4.w += gamma * p4.w;
-                st4(X + off + j, x4);
+            for (int it = 0; it < IT; ++it) {
+                const long long j = (long long)ch * CH + (long long)(threadIdx.x + it * NT) * 4;
+                if (j < Dp) {
+                    float4 x4 = xv[it], l4 = ld4(Xlo + off + j);
+                    const float4 p4 = pv[it];
+                    two_sum_acc(x4.x, l4.x, __fmul_rn(gamma, p4.x));
+                    two_sum_acc(x4.y, l4.y, __fmul_rn(gamma, p4.y));
+                    two_sum_acc(x4.z, l4.z, __fmul_rn(gamma, p4.z));
+                    two_sum_acc(x4.w, l4.w, __fmul_rn(gamma, p4.w));
+                    st4(X + off + j, x4);
+                    st4(Xlo + off + j, l4);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int it = 0; it < IT; ++it) {   // X needs no operator output: store it now
+                const long long j = (long long)ch * CH + (long long)(threadIdx.x + it * NT) * 4;
+                if (j < Dp) {
+                    float4 x4 = xv[it];
+                    const float4 p4 = pv[it];
+                    x4.x += gamma * p4.x; x4.y += gamma * p4.y; x4.z += gamma * p4.z; x4.w += gamma * p4.w;
+                    st4(X + off + j, x4);
+                }
             }
         }
 #pragma unroll
@@ -254,50 +285,6 @@ __global__ __launch_bounds__(NT, 2) void k_cg_update(DevCtl* ctl, const float* _
     const double rrd = block_sum_f(rr, sh);
     const double rzd = block_sum_f(rz, sh);
     if (threadIdx.x == 0) {
-        part[(size_t)(0 * Q + q) * nch + ch] = rrd;
-        part[(size_t)(1 * Q + q) * nch + ch] = rzd;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Residual replacement (precision form): R = B - A X for the active columns,
-// with B regenerated (b, probes), and the partials of ||r||^2 and r^T M^-1 r.
-// ---------------------------------------------------------------------------
-__global__ __launch_bounds__(NT) void k_rr_residual(DevCtl* ctl, const float* __restrict__ b,
-                                                    const float* __restrict__ X, OpOut uo,
-                                                    const float* __restrict__ alpha, const float* __restrict__ minv,
-                                                    float* __restrict__ R, long long D, long long Dp,
-                                                    int nch, double* part) {
-    __shared__ double sh[NT / 32];
-    const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q, t = ctl->t;
-    float rr = 0.0f, rz = 0.0f;
-    if (ctl->active[q]) {
-        const float beta = (float)ctl->beta;
-        const size_t off = (size_t)q * Dp;
-        for (int e = threadIdx.x * 4; e < CH; e += NT * 4) {
-            const long long j = (long long)ch * CH + e;
-            if (j >= Dp) break;
-            float4 bv;
-            if (q == 0) {
-                bv = ld4(b + j);
-            } else {
-                const uint64_t w = probe_word(ctl->seed, t, q, j);
-                bv.x = j + 0 < D ? probe_sign_from_word(w, j + 0) : 0.0f;
-                bv.y = j + 1 < D ? probe_sign_from_word(w, j + 1) : 0.0f;
-                bv.z = j + 2 < D ? probe_sign_from_word(w, j + 2) : 0.0f;
-                bv.w = j + 3 < D ? probe_sign_from_word(w, j + 3) : 0.0f;
-            }
-            const float4 xv = ld4(X + off + j), av = ld4(alpha + j), mv = ld4(minv + j);
-            const float4 ax = psi4(uo, Q, q, Dp, j, beta, av, xv);
-            const float4 rv = make_float4(bv.x - ax.x, bv.y - ax.y, bv.z - ax.z, bv.w - ax.w);
-            st4(R + off + j, rv);
-            rr += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
-            rz += rv.x * (rv.x * mv.x) + rv.y * (rv.y * mv.y) + rv.z * (rv.z * mv.z) + rv.w * (rv.w * mv.w);
-        }
-    }
-    const double rrd = block_sum_f(rr, sh);
-    const double rzd = block_sum_f(rz, sh);
-    if (threadIdx.x == 0) {   // the direction kernel takes the stopping test from these
         part[(size_t)(0 * Q + q) * nch + ch] = rrd;
         part[(size_t)(1 * Q + q) * nch + ch] = rzd;
     }
@@ -432,27 +419,37 @@ __global__ __launch_bounds__(NT) void k_cg_direction(DevCtl* ctl, const float* _
 __global__ __launch_bounds__(NT) void k_mstep(DevCtl* ctl, const float* __restrict__ X,
                                               const float* __restrict__ theta, float* __restrict__ alpha,
                                               float* __restrict__ minv, float* __restrict__ mu_out,
-                                              float* __restrict__ s_out, int* __restrict__ iters, long long D,
-                                              long long Dp, unsigned* counter, cudaGraphConditionalHandle h_em) {
-    const int t = ctl->t, T = ctl->T, K = ctl->K;
+                                              float* __restrict__ s_out, int* __restrict__ iters,
+                                              const float* __restrict__ Xlo, long long D, long long Dp,
+                                              unsigned* counter, cudaGraphConditionalHandle h_em) {
+    const int t = ctl->t, T = ctl->T, K = ctl->K, L = ctl->L;
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int clamped = 0;
     if (j < Dp) {
-        const float mu = X[j];
-        float s = 0.0f;
-        if (j < D) {
-            const unsigned long long seed = ctl->seed;
-            for (int k = 1; k <= K; ++k) {
-                const uint64_t w = probe_word(seed, t, k, j);
-                s = fmaf(probe_sign_from_word(w, j), X[(size_t)k * Dp + j], s);
+        // per task l: mu_l = x_{l(K+1)}, s_l = (1/K) sum_k p_{l,k} x_{l(K+1)+k}; the
+        // second moment is mu^2 + s (one task) or its mean over the tasks
+        // (multi-task M-step alpha_j = L / sum_l (mu_lj^2 + s_lj))
+        float m2 = 0.0f, mu = 0.0f, s = 0.0f;
+        for (int l = 0; l < L; ++l) {
+            const size_t c0 = (size_t)l * (K + 1) * Dp + j;
+            mu = Xlo ? X[c0] + Xlo[c0] : X[c0];   // the FP32 pair X + Xlo of the precision form
+            s = 0.0f;
+            if (j < D) {
+                const unsigned long long seed = ctl->seed;
+                for (int k = 1; k <= K; ++k) {
+                    const uint64_t w = probe_word(seed, t, k, j, l);
+                    const size_t e = c0 + (size_t)k * Dp;
+                    s = fmaf(probe_sign_from_word(w, j), Xlo ? X[e] + Xlo[e] : X[e], s);
+                }
+                s /= (float)K;
             }
-            s /= (float)K;
+            mu_out[(size_t)l * Dp + j] = mu;
+            s_out[(size_t)l * Dp + j] = s;
+            m2 += fmaf(mu, mu, s);
         }
-        mu_out[j] = mu;
-        s_out[j] = s;
+        if (L > 1) m2 /= (float)L;
         if (t < T && j < D) {
-            float m2 = fmaf(mu, mu, s);
-            if (ctl->prior == COFEM_PRIOR_RECTIFIED && s > 0.0f) {
+            if (L == 1 && ctl->prior == COFEM_PRIOR_RECTIFIED && s > 0.0f) {
                 // mu^2 + s + mu sqrt(2 s / pi) exp(-xi^2) / erfc(-xi), xi = mu / sqrt(2 s);
                 // exp(-xi^2) / erfc(-xi) = 1 / erfcx(-xi).  FP64: for mu << -sqrt(s)
                 // the moment is a small difference of large terms.
@@ -465,7 +462,7 @@ __global__ __launch_bounds__(NT) void k_mstep(DevCtl* ctl, const float* __restri
             clamped = m2 < floor_;
             const float a = 1.0f / (m2 > floor_ ? m2 : floor_);
             alpha[j] = a;
-            minv[j] = 1.0f / ((float)ctl->beta * theta[j] + a);
+            minv[j] = ctl->precond_none ? 1.0f : 1.0f / ((float)ctl->beta * theta[j] + a);
         }
     }
     if (__syncthreads_or(clamped) && threadIdx.x == 0) atomicOr(&ctl->flags, COFEM_FLAG_ALPHA_CLAMPED);
@@ -536,19 +533,14 @@ void launch_fit_setup(Sink& s, cofem_ctx* c, int /*Q*/) {
 }
 
 void launch_cg_init(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg) {
-    s.launch(k_cg_init, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->b, c->minv, c->alpha, c->X, c->R, c->P, c->D, c->Dp,
-             c->nch, c->part, c->counters + 0, h_cg, tc_direction_split(c));
+    s.launch(k_cg_init, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->b, c->minv, c->alpha, c->X, c->R, c->P, c->Xlo,
+             c->D, c->Dp, c->nch, c->part, c->counters + 0, h_cg, tc_direction_split(c));
 }
 
 void launch_cg_update(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_rr,
                       cudaGraphConditionalHandle h_cg) {
     s.launch_pdl(k_cg_update, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->P, op_output(c), c->alpha, c->minv, c->X, c->R,
-                 c->Dp, c->nch, c->part, h_rr, h_cg);
-}
-
-void launch_rr_residual(Sink& s, cofem_ctx* c, int Q) {
-    s.launch(k_rr_residual, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->b, c->X, op_output(c), c->alpha, c->minv, c->R,
-             c->D, c->Dp, c->nch, c->part);
+                 c->Xlo, c->Dp, c->nch, c->part, h_rr, h_cg);
 }
 
 void launch_cg_direction(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg) {
@@ -558,7 +550,7 @@ void launch_cg_direction(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandl
 
 void launch_mstep(Sink& s, cofem_ctx* c, int /*Q*/, cudaGraphConditionalHandle h_em) {
     s.launch(k_mstep, dim3((unsigned)((c->Dp + NT - 1) / NT)), dim3(NT), 0, c->ctl, c->X, c->theta, c->alpha, c->minv,
-             c->mu_out, c->s_out, c->iters_dev, c->D, c->Dp, c->counters + 4, h_em);
+             c->mu_out, c->s_out, c->iters_dev, c->Xlo, c->D, c->Dp, c->counters + 4, h_em);
 }
 
 void launch_probe_fill(cudaStream_t st, unsigned long long seed, int t, int K, long long D, long long ld,

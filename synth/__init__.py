@@ -26,7 +26,11 @@ import numpy as np
 
 __all__ = [
     "Problem",
+    "MultiTaskProblem",
     "dense_gaussian",
+    "dense_gaussian_multitask",
+    "DCTProblem",
+    "dct_sparse",
     "double_exponential_filter",
     "toeplitz_calcium",
     "WORKLOADS",
@@ -94,6 +98,67 @@ def dense_gaussian(N: int, D: int, d: int, snr_db: float, seed: int,
     return Problem("dense", N, D, phi, y.astype(np.float32), z, 1.0 / sigma2, sigma2, support)
 
 
+@dataclasses.dataclass
+class MultiTaskProblem:
+    """L problems y_l = Phi z*_l + eps_l sharing one dense dictionary (multiple
+    measurement vectors) and one noise precision beta; Y is L x N, Z is L x D."""
+
+    N: int
+    D: int
+    L: int
+    phi: np.ndarray
+    Y: np.ndarray
+    Z: np.ndarray
+    beta: float
+    support: np.ndarray
+
+
+def dense_gaussian_multitask(N: int, D: int, d: int, snr_db: float, L: int, seed: int) -> MultiTaskProblem:
+    """Shared dense Gaussian dictionary Phi_ij ~ N(0, 1/N) (float32); the L
+    codes z*_l share d uniformly random support positions (the joint sparsity
+    a shared alpha models) with independent N(0,1) amplitudes; one noise level
+    sigma^2 = mean_l ||Phi z*_l||^2 / (N 10^(SNR/10)), beta = 1/sigma^2."""
+    rng = np.random.default_rng(seed)
+    phi = rng.standard_normal((N, D), dtype=np.float32)
+    phi *= np.float32(1.0 / math.sqrt(N))
+    support = np.sort(rng.choice(D, size=d, replace=False))
+    Z = np.zeros((L, D), dtype=np.float64)
+    Z[:, support] = rng.standard_normal((L, d))
+    clean = Z[:, support] @ phi[:, support].astype(np.float64).T          # L x N
+    sigma2 = float(np.mean(np.sum(clean * clean, axis=1))) / (N * 10.0 ** (snr_db / 10.0))
+    Y = clean + rng.standard_normal((L, N)) * math.sqrt(sigma2)
+    return MultiTaskProblem(N, D, L, phi, Y.astype(np.float32), Z, 1.0 / sigma2, support)
+
+
+@dataclasses.dataclass
+class DCTProblem:
+    """y = Phi z* + eps with the DCT dictionary Phi = M Omega^-1 (the rows
+    `rows` of the inverse orthonormal DCT-II of size D)."""
+
+    N: int
+    D: int
+    rows: np.ndarray      # int32, sorted, distinct, < D
+    y: np.ndarray         # float32, N
+    z: np.ndarray         # float64, D
+    beta: float
+    support: np.ndarray
+
+
+def dct_sparse(D: int, N: int, d: int, sigma: float, seed: int, spike_sd: float = 5.0) -> DCTProblem:
+    """The DCT dictionary of Sec. V-A: N of the D rows of Omega^-1 kept at
+    random, d spikes N(0, spike_sd^2) at uniform positions, noise sigma
+    (beta = 1/sigma^2).  y is formed with scipy's orthonormal inverse DCT."""
+    from scipy import fft
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(D, size=N, replace=False)).astype(np.int32)
+    support = np.sort(rng.choice(D, size=d, replace=False))
+    z = np.zeros(D, dtype=np.float64)
+    z[support] = rng.standard_normal(d) * spike_sd
+    clean = fft.idct(z, type=2, norm="ortho")[rows]
+    y = clean + rng.standard_normal(N) * sigma
+    return DCTProblem(N, D, rows, y.astype(np.float32), z, 1.0 / sigma ** 2, support)
+
+
 def double_exponential_filter(L: int = 256, tau_decay: float = 40.0,
                               tau_rise: float = 4.0) -> np.ndarray:
     """Calcium-style response h[t] = exp(-t/40) - exp(-t/4), t = 0..L-1 (float32).
@@ -132,14 +197,12 @@ WORKLOADS = {
     "toeplitz_d1e6_l256_k16": dict(
         kind="toeplitz", N=1_000_000, D=1_000_000, L=256, rate=0.01, snr_db=15.0,
         K=16, T=30, cg_tol=1e-5, cg_maxit=400, precision="f32", rr_period=0),
-    # Residual replacement is available (rr_period) but off here: with the
-    # FP32 CG state, replacing R every 20 steps keeps the probe columns of
-    # these E-step systems from ever meeting tol 1e-5 (their recursive and
-    # true residuals drift apart by more than tol), while the recursive test
-    # converges to the same NMSE.
+    # The precision form: residual replacement every 20 CG iterations (with X
+    # held as an FP32 pair and B - A X formed accurately) and the end-of-E-step
+    # true-residual check.
     "dense_n8192_d32768_k32_bf16": dict(
         kind="dense", N=8192, D=32768, d=327, snr_db=30.0, K=32, T=30,
-        cg_tol=1e-5, cg_maxit=400, precision="bf16", rr_period=0),
+        cg_tol=1e-5, cg_maxit=400, precision="bf16", rr_period=20),
     "dense_n8192_d32768_k32_f32": dict(
         kind="dense", N=8192, D=32768, d=327, snr_db=30.0, K=32, T=30,
         cg_tol=1e-5, cg_maxit=400, precision="f32", rr_period=0),

@@ -16,17 +16,20 @@ from synth import WORKLOADS  # noqa: E402
 
 def test_launch_count_per_fit():
     # 3 per fit (b, finiteness check of y, set-up); per EM iteration init and
-    # M-step; per CG step the operator's kernels and update + direction
-    assert bench._launches_per_fit([10, 20], 0, 3, 4, 2) == 3 + (2 + 5 * 10) + (2 + 5 * 20)
-    # a residual replacement every 3 steps adds the operator on X and the residual kernel
-    assert bench._launches_per_fit([10], 3, 3, 4, 2) == 3 + 2 + 5 * 10 + 3 * (4 + 1)
-    assert bench._launches_per_fit([], 0, 3, 4, 2) == 3
+    # M-step; per CG step the operator's kernels (3) and update + direction (2)
+    assert bench._launches_per_fit([10, 20], 3, 2) == 3 + (2 + 5 * 10) + (2 + 5 * 20)
+    # each residual replacement adds the accurate residual (4 kernels); each
+    # true-residual check the accurate residual, the check and the loop gate
+    assert bench._launches_per_fit([10], 3, 2, n_rr=3, n_check=2, op_rr=4) == 3 + 2 + 5 * 10 + 3 * 4 + 2 * 6
+    # driven from the host loop there is no gate kernel
+    assert bench._launches_per_fit([10], 3, 2, n_rr=0, n_check=2, op_rr=4, graph=False) == 3 + 2 + 5 * 10 + 2 * 5
+    assert bench._launches_per_fit([], 3, 2) == 3
 
 
 def test_launch_count_matches_the_launch_list():
     """The launch list of a fit (host loop, BF16 two-pass) has, per CG step,
     two GEMMs, the T reduction, the update and the direction: 5 kernels."""
-    per_step = bench._launches_per_fit([1], 0, 3, 4, 2) - bench._launches_per_fit([0], 0, 3, 4, 2)
+    per_step = bench._launches_per_fit([1], 3, 2) - bench._launches_per_fit([0], 3, 2)
     assert per_step == 5
 
 

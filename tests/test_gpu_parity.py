@@ -5,9 +5,9 @@ Tolerances: probes are bit-exact (integer work); operator applications are
 compared per column in relative l2 (FP32 accumulation over up to N*D terms,
 bound 2e-5); whole fits use relative l2 <= 1e-4 on mu and <= 1e-3 on s, on
 the second moment 1/alpha = max(mu^2 + s, 1/alpha_max) (the quantity the M-step
-forms) and on alpha itself where it is well determined (alpha < 1e6 and
-mu^2 + s not a cancelling difference; elsewhere alpha is the reciprocal of a
-small difference)."""
+forms) and on alpha itself where it is well determined (alpha < 1e6, its
+second moment mu^2 + s within 1e-2 of the largest and not a cancelling
+difference; elsewhere alpha is the reciprocal of a small difference)."""
 import numpy as np
 import pytest
 
@@ -69,7 +69,7 @@ def e4m3_quantise(phi):
     return s, np.sign(x) * g[pick]
 
 
-def gpu_fit(cf, prob, K, T, tol, maxit, seed=2, alpha0=None, host=False, **opts):
+def gpu_fit(cf, prob, K, T, tol, maxit, seed=2, alpha0=None, host=False, want_res=False, **opts):
     D = prob.D
     if host:
         mu, s, al = (np.empty(D, np.float32) for _ in range(3))
@@ -86,8 +86,9 @@ def gpu_fit(cf, prob, K, T, tol, maxit, seed=2, alpha0=None, host=False, **opts)
     kind = cf.COFEM_OP_DENSE if prob.kind == "dense" else cf.COFEM_OP_TOEPLITZ
     with cf.CoFEM(prob.N, D, kind, phi, prob.L, seed=seed, **opts) as m:
         flags = cf.cofem_fit(m.h, y, prob.beta, a0, K, T, tol, maxit, mu, s, al, it)
+        res = cf.cofem_true_residuals(m.h, T, K) if want_res else None
     cvt = (lambda v: v) if host else (lambda v: v.cpu().numpy())
-    return dict(mu=cvt(mu), s=cvt(s), alpha=cvt(al), cg_iters=cvt(it), flags=flags)
+    return dict(mu=cvt(mu), s=cvt(s), alpha=cvt(al), cg_iters=cvt(it), flags=flags, true_res=res)
 
 
 def oracle_fit(prob, K, T, tol, maxit, seed=2, phi=None, **kw):
@@ -100,16 +101,20 @@ def oracle_fit(prob, K, T, tol, maxit, seed=2, phi=None, **kw):
 
 def well_determined(r):
     """Coordinates where alpha = 1/max(mu^2 + s, 1/alpha_max) is well
-    conditioned: alpha < 1e6 and mu^2 + s >= 0.1 (mu^2 + |s|)."""
+    conditioned: alpha < 1e6, the second moment mu^2 + s at least 1e-2 of its
+    largest value (the relative l2 error over a set is that of its largest
+    alphas, whose second moments carry the largest relative error) and not a
+    cancelling difference (>= 0.1 (mu^2 + |s|))."""
     mu, s_ = np.asarray(r["mu"], np.float64), np.asarray(r["s"], np.float64)
-    return (r["alpha"] < 1e6) & (1.0 / r["alpha"] >= 0.1 * (mu * mu + np.abs(s_)))
+    m2 = 1.0 / np.asarray(r["alpha"], np.float64)
+    return (r["alpha"] < 1e6) & (m2 >= 1e-2 * m2.max()) & (m2 >= 0.1 * (mu * mu + np.abs(s_)))
 
 
 def assert_fit_close(g, r, tol_mu=1e-4, tol_s=1e-3, tol_a=1e-3):
     """mu, s and 1/alpha everywhere, and alpha itself where it is well
-    determined: coordinates the oracle keeps active (alpha < 1e6) whose second
-    moment mu^2 + s is not a cancelling difference (at least a tenth of
-    mu^2 + |s|; with few probes s can be negative and large)."""
+    determined (well_determined: the oracle keeps it active, its second moment
+    is within 1e-2 of the largest and not a cancelling difference; with few
+    probes s can be negative and large)."""
     act = well_determined(r)
     e = (rel(g["mu"], r["mu"]), rel(g["s"], r["s"]), rel(1.0 / g["alpha"], 1.0 / r["alpha"]),
          rel(g["alpha"][act], r["alpha"][act]) if act.any() else 0.0)
@@ -356,6 +361,66 @@ def test_fit_variants(cf, variant):
     assert_fit_close(g, r)
 
 
+@pytest.mark.parametrize("case", ["dense_under", "dense_over", "toeplitz"])
+def test_fit_precision_form_matches_oracle(cf, case):
+    """Residual replacement with the accurate residual (X as an FP32 pair,
+    B - A X in FP32-pair products) and the end-of-E-step check, against the
+    oracle's replacement in FP64: the same fit, and every reported true
+    residual within tol (none of these fits runs out of CG steps)."""
+    if case == "toeplitz":
+        p = toeplitz_calcium(6000, 256, 0.01, 15.0, seed=2)
+        args = (8, 3, 1e-14, 25)          # fixed CG steps, as in the test below
+    else:
+        p = dense_gaussian(250, 500, 10, 15.0, seed=11) if case == "dense_under" else \
+            dense_gaussian(500, 400, 10, 15.0, seed=11)
+        args = (16, 10, 1e-5, 400)
+    K, T = args[0], args[1]
+    kind = cf.COFEM_OP_DENSE if p.kind == "dense" else cf.COFEM_OP_TOEPLITZ
+    mu, s_, al = (np.empty(p.D, np.float32) for _ in range(3))
+    it = np.empty(T, np.int32)
+    with cf.CoFEM(p.N, p.D, kind, p.phi, p.L, rr_period=7) as m:
+        flags = cf.cofem_fit(m.h, p.y, p.beta, None, *args, mu, s_, al, it)
+        res = cf.cofem_true_residuals(m.h, T, K)
+        n_rr, n_check = cf.cofem_fit_stats(m.h)
+    g = dict(mu=mu, s=s_, alpha=al, cg_iters=it, flags=flags)
+    r = oracle_fit(p, *args, rr_period=7)
+    assert_fit_close(g, r)
+    assert n_rr == sum(int(u) // 7 for u in it) and n_check >= T
+    if case == "toeplitz":
+        # fixed step count: the check reports the residual left after 25 steps
+        np.testing.assert_allclose(res, r["true_res"], rtol=2e-2)
+    else:
+        assert not flags & cf.COFEM_FLAG_CG_NOT_CONVERGED and np.all(res <= args[2]), (flags, res.max())
+
+
+def test_fit_check_residual_reports_the_true_residual(cf):
+    """check_residual = 1 (no replacement; X held as the FP32 pair): the fit
+    matches the oracle, and the reported true residual of the mu column equals
+    its FP64 residual computed on the host from the returned mu (mu's own FP32
+    rounding is far below it)."""
+    p = dense_gaussian(250, 500, 10, 15.0, seed=11)
+    K, T = 16, 6
+    outs = [np.empty(p.D, np.float32) for _ in range(3)]
+    it = np.empty(T, np.int32)
+    with cf.CoFEM(p.N, p.D, cf.COFEM_OP_DENSE, p.phi, check_residual=1) as m:
+        flags = cf.cofem_fit(m.h, p.y, p.beta, None, K, T, 1e-5, 400, *outs, it)
+        res = cf.cofem_true_residuals(m.h, T, K)
+    assert_fit_close(dict(mu=outs[0], s=outs[1], alpha=outs[2], cg_iters=it, flags=flags),
+                     oracle_fit(p, K, T, 1e-5, 400))
+    # mu of the last E-step solves A(alpha^(T)) mu = b
+    Phi = p.phi.astype(np.float64)
+    b = p.beta * (Phi.T @ p.y.astype(np.float64))
+    mu = outs[0].astype(np.float64)
+    r = b - p.beta * (Phi.T @ (Phi @ mu)) - outs[2].astype(np.float64) * mu
+    host = np.linalg.norm(r) / np.linalg.norm(b.astype(np.float32).astype(np.float64))
+    assert abs(res[-1, 0] - host) <= 1e-6 + 0.05 * host, (res[-1, 0], host)
+    assert np.all(np.isfinite(res))
+    with cf.CoFEM(p.N, p.D, cf.COFEM_OP_DENSE, p.phi) as m:   # not measured without the option
+        cf.cofem_fit(m.h, p.y, p.beta, None, K, 1, 1e-5, 400, *outs)
+        with pytest.raises(cf.CofemError):
+            cf.cofem_true_residuals(m.h, 1, K)
+
+
 def test_fit_toeplitz_small(cf):
     """The calcium-style convolution makes the E-step system so ill-conditioned
     that even FP64 CG needs > 1000 steps for tol 1e-5; compare the two CG
@@ -558,9 +623,13 @@ def test_fit_dense_n8192_d32768_bf16_properties(cf):
     FP32 forms reach the same NMSE within 0.1 dB."""
     from synth import workload
     p, run = workload("dense_n8192_d32768_k32_bf16")
+    assert run["rr_period"] == 20
     g = gpu_fit(cf, p, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], seed=run["seed"],
-                precision=cf.COFEM_BF16, rr_period=run["rr_period"])
-    assert not g["flags"] & cf.COFEM_FLAG_CG_NOT_CONVERGED, g["cg_iters"]
+                precision=cf.COFEM_BF16, rr_period=run["rr_period"], want_res=True)
+    assert g["flags"] == 0, (g["flags"], g["cg_iters"])
+    # the precision form: every column's true residual, measured on the GPU at
+    # the end of every E-step, within the CG tolerance
+    assert np.all(g["true_res"] <= run["cg_tol"]), g["true_res"].max()
     assert _mu_residual(bf16_round(p.phi), p.y, p.beta, g["alpha"], g["mu"]) < 10 * run["cg_tol"]
     f = gpu_fit(cf, p, run["K"], run["T"], run["cg_tol"], run["cg_maxit"], seed=run["seed"],
                 precision=cf.COFEM_F32, rr_period=run["rr_period"])

@@ -6,7 +6,8 @@ sides take the same steps; two EM iterations, so one M-step is included.
 Compared element by element with the FP32 parity tolerances (relative l2):
 mu <= 1e-4, s <= 1e-3, the second moment 1/alpha <= 1e-3, and alpha itself
 <= 1e-3 where it is well determined (the oracle keeps it active, alpha < 1e6,
-and mu^2 + s is at least a tenth of mu^2 + |s|); elsewhere alpha_j is the
+mu^2 + s is within 1e-2 of its largest value and at least a tenth of
+mu^2 + |s|); elsewhere alpha_j is the
 reciprocal of a small difference and is not determined to that tolerance by
 any FP32 computation.
 
@@ -57,16 +58,18 @@ def _gpu(cf, p, K, T, maxit, seed, **opts):
     phi = torch.from_numpy(p.phi).to(DEV)
     with cf.CoFEM(p.N, D, kind, phi, p.L, seed=seed, **opts) as m:
         flags = cf.cofem_fit(m.h, torch.from_numpy(p.y).to(DEV), p.beta, None, K, T, TOL_FIXED, maxit, mu, s, al, it)
+        res = cf.cofem_true_residuals(m.h, T, K) if opts.get("rr_period", 0) > 0 else None
     del phi
     torch.cuda.synchronize()
     return dict(mu=mu.cpu().numpy(), s=s.cpu().numpy(), alpha=al.cpu().numpy(), cg_iters=it.cpu().numpy(),
-                flags=flags)
+                flags=flags, true_res=res)
 
 
 def _check(g, r, maxit):
     assert np.all(g["cg_iters"] == maxit) and np.all(r["cg_iters"] == maxit), (g["cg_iters"], r["cg_iters"])
     mu_o, s_o = np.asarray(r["mu"], np.float64), np.asarray(r["s"], np.float64)
-    act = (r["alpha"] < ACTIVE) & (1.0 / r["alpha"] >= 0.1 * (mu_o * mu_o + np.abs(s_o)))
+    m2 = 1.0 / np.asarray(r["alpha"], np.float64)
+    act = (r["alpha"] < ACTIVE) & (m2 >= 1e-2 * m2.max()) & (m2 >= 0.1 * (mu_o * mu_o + np.abs(s_o)))
     e = dict(mu=rel(g["mu"], r["mu"]), s=rel(g["s"], r["s"]), inv_alpha=rel(1.0 / g["alpha"], 1.0 / r["alpha"]),
              alpha_active=rel(g["alpha"][act], r["alpha"][act]), n_active=int(act.sum()))
     print("trajectory errors:", e)
@@ -85,17 +88,31 @@ def test_trajectory_dense_n2500_d10000_k32(cf, precision):
     _check(g, r, maxit)
 
 
-def test_trajectory_dense_n8192_d32768_k32_bf16(cf):
-    """The benchmark's workload and launch configuration (two-pass tcgen05
-    operator, CUDA graph); the oracle runs on the quantised dictionary."""
+@pytest.fixture(scope="module")
+def config4():
+    """The 8192 x 32768 problem and its quantised dictionary bf16(Phi)."""
     p, run = workload("dense_n8192_d32768_k32_bf16")
-    K, T, maxit = run["K"], 2, 10
-    g = _gpu(cf, p, K, T, maxit, run["seed"], precision=cf.COFEM_BF16)
     phq = np.empty(p.phi.shape, np.float32)
     for i0 in range(0, p.N, 1024):                     # quantise by row blocks
         phq[i0:i0 + 1024] = bf16_round(p.phi[i0:i0 + 1024])
-    r = oracle_cofem(DenseOperator(phq), p.y, p.beta, K, T, TOL_FIXED, maxit, run["seed"])
+    return p, run, DenseOperator(phq)
+
+
+@pytest.mark.parametrize("rr_period", [0, 4])
+def test_trajectory_dense_n8192_d32768_k32_bf16(cf, config4, rr_period):
+    """The benchmark's workload and launch configuration (two-pass tcgen05
+    operator, CUDA graph); the oracle runs on the quantised dictionary.  With
+    rr_period = 4 the CG loop takes the accurate residual B - A X (FP32-pair
+    products on the CUDA cores) at steps 4 and 8 where the oracle takes it in
+    FP64, and the end-of-E-step check reports the residual left after the
+    fixed 10 steps (the budget is spent, so nothing restarts)."""
+    p, run, op = config4
+    K, T, maxit = run["K"], 2, 10
+    g = _gpu(cf, p, K, T, maxit, run["seed"], precision=cf.COFEM_BF16, rr_period=rr_period)
+    r = oracle_cofem(op, p.y, p.beta, K, T, TOL_FIXED, maxit, run["seed"], rr_period=rr_period)
     _check(g, r, maxit)
+    if rr_period:
+        np.testing.assert_allclose(g["true_res"], r["true_res"], rtol=1e-2)
 
 
 def test_trajectory_toeplitz_d1e6_l256_k16(cf):

@@ -149,3 +149,44 @@ def test_breakdown_on_non_finite_pi():
     assert flags & FLAG_BREAKDOWN
     assert np.all(X == 0.0)
     assert iters == 1
+
+
+def test_true_residual_check_restarts_a_column_that_misses_tol():
+    """Reading 11's check: a column whose recursive residual met tol while its
+    true residual did not (here forced by an operator that is off by a
+    perturbation inside the CG loop only) restarts from the true residual and
+    ends within tol of the exact solve; the reported true residuals are those
+    of the returned X."""
+    A, minv = _system(30, 70, 1e3, 14)
+    B = np.random.default_rng(15).standard_normal((70, 3))
+    rng = np.random.default_rng(16)
+    E = 1e-4 * rng.standard_normal((70, 70))
+    calls = {"n": 0}
+
+    def perturbed(V):          # wrong operator for the first 60 applications
+        calls["n"] += 1
+        return (A + E) @ V if calls["n"] <= 60 else A @ V
+
+    info = {}
+    X, iters, flags = pcg(perturbed, B, minv, 1e-9, 500, check=True, info=info)
+    res = np.linalg.norm(B - A @ X, axis=0) / np.linalg.norm(B, axis=0)
+    assert flags == 0
+    assert np.all(res <= 1e-9 * (1 + 1e-6))
+    np.testing.assert_allclose(info["true_res"], res, rtol=1e-6)
+    # without the check the same run returns an X whose true residual misses tol
+    calls["n"] = 0
+    X0, _, _ = pcg(perturbed, B, minv, 1e-9, 500)
+    assert np.max(np.linalg.norm(B - A @ X0, axis=0) / np.linalg.norm(B, axis=0)) > 1e-8
+
+
+def test_true_residual_check_reports_without_restart_in_fp64():
+    """With an exact operator the FP64 recursive residual tracks the true
+    one: the check restarts nothing and reports residuals below tol."""
+    A, minv = _system(30, 70, 1e3, 17)
+    B = np.random.default_rng(18).standard_normal((70, 4))
+    info = {}
+    X1, it1, f1 = pcg(lambda V: A @ V, B, minv, 1e-8, 500, check=True, info=info)
+    X2, it2, f2 = pcg(lambda V: A @ V, B, minv, 1e-8, 500)
+    assert it1 == it2 and f1 == f2 == 0
+    np.testing.assert_array_equal(X1, X2)
+    assert np.all(info["true_res"] <= 1e-8 * (1 + 1e-6))
