@@ -135,6 +135,9 @@ def _nmse_db(mu, z):
 # FP32 FMA peak of the GPU: 152 SMs x 128 FP32 lanes x 2 flop per FMA x SM clock
 # (the CUDA-core roofline of the FP32 forms and of the convolution operator)
 _SMS, _FP32_LANES = 152, 128
+# FP32 instructions per multiply-add of the error-free dot product (TwoProduct
+# through the FMA, the low part's FMA, TwoSum, the compensation adds)
+_DF_OPS_PER_MAC = 11
 
 
 def _fp32_peak_tflops(sm_mhz):
@@ -317,9 +320,9 @@ def run_ours(args):
     outs = [torch.empty(D, device=dev) for _ in range(3)]
     iters = torch.empty(T, dtype=torch.int32, device=dev)
 
-    def make(precision, rr_period=None):
+    def make(precision, rr_period=None, warm_start=0):
         rr = run["rr_period"] if rr_period is None else rr_period
-        return cf.CoFEM(N, D, kind, phi_d, prob.L, precision=precision, rr_period=rr,
+        return cf.CoFEM(N, D, kind, phi_d, prob.L, precision=precision, rr_period=rr, warm_start=warm_start,
                         seed=run["seed"], stream=stream, use_graph=0 if args.no_graph else 1,
                         dense_path=_DENSE_PATHS[args.dense_path], overlap_launch=0 if args.no_overlap else 1,
                         prior=cf.COFEM_PRIOR_RECTIFIED if args.prior == "rectified" else cf.COFEM_PRIOR_GAUSSIAN)
@@ -385,6 +388,26 @@ def run_ours(args):
         roof = {"bound": "alu", "kernel": "convolution operator (k_toeplitz)"}
     traffic = _MEASURED_TRAFFIC.get((name, path)) if prob.kind == "dense" else None
     roof = _roofline(roof, op_ms, alg_bytes, alg_flops, traffic, hbm_gbs, peak_kind, clk)
+    # the precision form: the accurate residual's first product (Phi~ X in FP32
+    # pairs, CUDA cores) against the FP32 instruction rate; whichever of it and
+    # the CG operator takes more of the fit is the dominant kernel
+    roof_df = None
+    if run["rr_period"] > 0 and prob.kind == "dense":
+        ms_res, ms_first = cf.cofem_time_true_residual(model.h, Q, 5)
+        n_rr, n_check = fit_stats[-1]
+        sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+        ops = _DF_OPS_PER_MAC * float(N) * D * Q
+        peak_ops = _SMS * _FP32_LANES * float(sm_mhz) * 1e6 / 1e12
+        achieved = ops / (ms_first / 1000.0) / 1e12
+        roof_df = {"bound": "alu", "kernel": "accurate residual, first product Phi~ X in FP32 pairs (k_df_gemm)",
+                   "achieved": achieved, "peak": peak_ops, "unit": "T FP32-op/s", "frac": achieved / peak_ops,
+                   "traffic": None, "peak_source": f"derived: {_SMS} SMs x {_FP32_LANES} FP32 lanes x 1 op "
+                   f"x {sm_mhz:.0f} MHz", "ms_per_launch": ms_first, "ms_per_accurate_residual": ms_res,
+                   "algorithmic_ops_per_launch": ops,
+                   "per_fit_ms": {"accurate_residuals": ms_res * (n_rr + n_check),
+                                  "cg_operator": op_ms * float(np.sum(all_iters[-1]))}}
+        if roof_df["per_fit_ms"]["accurate_residuals"] > roof_df["per_fit_ms"]["cg_operator"]:
+            roof, roof_df = roof_df, roof
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     y_h = torch.from_numpy(prob.y).pin_memory()
@@ -420,6 +443,17 @@ def run_ours(args):
                   "cg_iters_last_fit": [int(v) for v in it0[-1]]}
         m0.close()
 
+    # warm start with probe reuse (the same problem and settings)
+    warm = None
+    if not args.no_warm_compare:
+        mw = make(prec, warm_start=1)
+        msw, fw, itw, _ = timed_fits(mw, 2, 1)
+        warm = {"value": 2 * T / (msw / 1000.0), "unit": "EM-iter/s", "warm_start": 1,
+                "nmse_db": _nmse_db(outs[0].cpu().numpy(), prob.z), "flags": fw,
+                "cg_iters_last_fit": [int(v) for v in itw[-1]], "cg_steps_total": int(np.sum(itw[-1])),
+                "cold_cg_steps_total": int(np.sum(all_iters[-1]))}
+        mw.close()
+
     # the FP32 forms on the same problem (precision comparison at equal NMSE):
     # tensor-core 3xTF32 and plain FP32 FMA
     fp32 = None
@@ -453,12 +487,15 @@ def run_ours(args):
                           ("cuda graph" if not args.no_graph else "host loop")),
         "nmse_db": nmse, "flags": flags,
         "roofline": roof, "e2e": e2e, "gpu_launches": launches,
+        "roofline_secondary": roof_df,
         "clocks": clk,
     }
     if precision_form is not None:
         line["precision_form"] = precision_form
     if rr_off is not None:
         line["rr_off"] = rr_off
+    if warm is not None:
+        line["warm_start"] = warm
     if fp32 is not None:
         line["fp32_form"] = fp32
         line["fp8_form"] = fp8
@@ -473,35 +510,49 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def serving_run(cf, dev, n, precision, rate_hz=None, slots=16, budget_bytes=96 << 30, seed=1000, max_sms=0):
+def serving_run(cf, dev, n, precision, rate_hz=None, slots=16, budget_bytes=96 << 30, seed=1000, max_sms=0,
+                window=48):
     """Continuous-batching serving: n requests through cofem_submit/cofem_wait.
 
     Requests follow synth.serving_requests (D ~ U[1024, 16384], N = D/4, 3 %
-    spikes, SNR ~ U[15, 30] dB, K in {8, 16, 32}, T = 30); D is snapped to the
-    nearest of 8 dictionary sizes (1024, 3072, ..., 15360) whose Gaussian
-    dictionaries are generated once on the device from fixed seeds.  With
-    rate_hz None every request is submitted at t = 0 (saturation); otherwise
-    each is submitted at its Poisson arrival time.  Latency = submit -> results
-    written, measured by the server."""
+    spikes, SNR ~ U[15, 30] dB, K in {8, 16, 32}, T = 30).  Each request's
+    Gaussian dictionary, spikes and noise are generated on the device from its
+    own seed when it is submitted (the dictionaries of all requests would not
+    fit in memory at once) and freed when it completes.  With rate_hz None the
+    requests are submitted back to back, at most `window` in flight
+    (capacity); otherwise each is submitted at its Poisson arrival time.
+    Latency = submit -> results written, measured by the server."""
+    import collections
     import torch
     from synth import serving_requests
-    sizes = [1024 + 2048 * i for i in range(8)]
-    bank = {}
-    for i, D in enumerate(sizes):
-        g = torch.Generator(device=dev)
-        g.manual_seed(seed + i)
-        N = D // 4
-        bank[D] = torch.randn(N, D, generator=g, device=dev) / math.sqrt(N)
     reqs = serving_requests(n, base_seed=seed, rate_hz=rate_hz or 1.0)
     prec = _PRECISIONS[precision](cf)
-    prepared = []
+    srv = cf.cofem_server_create(budget_bytes, slots)
+    inflight = collections.deque()
+    results, nm = [], []
+
+    def finish(item):
+        t, o = item
+        x = cf.cofem_wait(srv, t)
+        results.append(x)
+        if x.status == 0:
+            z = torch.zeros_like(o["mu"])
+            z[o["idx"]] = o["zv"]
+            nm.append(20.0 * math.log10(float((o["mu"] - z).norm() / z.norm())))
+
+    t0 = time.perf_counter()
     for r in reqs:
-        D = min(sizes, key=lambda v: abs(v - r["D"]))
-        N = D // 4
-        phi = bank[D]
+        if rate_hz:
+            delay = t0 + r["arrival_s"] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+        elif len(inflight) >= window:
+            finish(inflight.popleft())
+        D, N = r["D"], r["N"]
         g = torch.Generator(device=dev)
         g.manual_seed(r["seed"])
-        d = max(1, int(0.03 * D))
+        phi = torch.randn(N, D, generator=g, device=dev) / math.sqrt(N)
+        d = r["d"]
         idx = torch.randperm(D, generator=g, device=dev)[:d]
         zv = torch.randn(d, generator=g, device=dev)
         clean = phi[:, idx] @ zv
@@ -513,34 +564,23 @@ def serving_run(cf, dev, n, precision, rate_hz=None, slots=16, budget_bytes=96 <
         o["req"] = cf.make_request(cf.COFEM_OP_DENSE, N, D, phi, y, 1.0 / sigma2, r["K"], r["T"], 1e-5, 400,
                                    o["mu"], o["s"], o["alpha"], o["it"], precision=prec, seed=r["seed"],
                                    max_sms=max_sms)
-        prepared.append(o)
-    torch.cuda.synchronize(dev)
-    srv = cf.cofem_server_create(budget_bytes, slots)
-    t0 = time.perf_counter()
-    tickets = []
-    for r, o in zip(reqs, prepared):
-        if rate_hz:
-            delay = t0 + r["arrival_s"] - time.perf_counter()
-            if delay > 0:
-                time.sleep(delay)
-        tickets.append(cf.cofem_submit(srv, o["req"]))
-    results = [cf.cofem_wait(srv, t) for t in tickets]
+        torch.cuda.current_stream(dev).synchronize()   # the request's inputs are written
+        inflight.append((cf.cofem_submit(srv, o["req"]), o))
+        while inflight and cf.cofem_poll(srv, inflight[0][0]):
+            finish(inflight.popleft())
+    while inflight:
+        finish(inflight.popleft())
     makespan = time.perf_counter() - t0
     cf.cofem_server_destroy(srv)
     lat = np.array([x.queue_ms + x.run_ms for x in results])
     ok = sum(1 for x in results if x.status == 0)
     errors = sorted({x.message.decode(errors="replace") for x in results if x.status != 0})
-    nm = []
-    for o, x in zip(prepared, results):
-        if x.status != 0:
-            continue
-        z = torch.zeros_like(o["mu"])
-        z[o["idx"]] = o["zv"]
-        nm.append(20.0 * math.log10(float((o["mu"] - z).norm() / z.norm())))
-    return {"requests": n, "ok": ok, "precision": precision, "slots": slots,
-            "offered_rate_hz": rate_hz, "solves_per_s": n / makespan, "em_iters_per_s": n * 30 / makespan,
+    return {"requests": n, "ok": ok, "precision": precision, "slots": slots, "window": None if rate_hz else window,
+            "offered_rate_hz": rate_hz, "solves_per_s": n / makespan,
+            "em_iters_per_s": sum(r["T"] for r in reqs) / makespan,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_nmse_db": float(np.mean(nm)) if nm else None, "makespan_s": makespan,
+            "dictionaries": "one per request, generated on the device from its seed (D unsnapped)",
             "errors": errors[:3]}
 
 
@@ -549,6 +589,12 @@ def serving_report(cf, dev, n, precision):
     sat = serving_run(cf, dev, n, precision, rate_hz=None)
     load = serving_run(cf, dev, n, precision, rate_hz=0.8 * sat["solves_per_s"])
     return {"saturation": sat, "at_80pct": load}
+
+
+def serving_config5(cf, dev, n, precisions):
+    """The serving configuration as a whole: capacity and p50/p99 at 80 % of
+    capacity for each storage precision of the dictionary."""
+    return {p: serving_report(cf, dev, n, p) for p in precisions}
 
 
 def run_operator_only(args):
@@ -619,6 +665,8 @@ def _parser():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp32-form", action="store_true")
+    ap.add_argument("--no-warm-compare", action="store_true",
+                    help="skip the comparison fit with warm start and probe reuse")
     ap.add_argument("--no-rr-off", action="store_true",
                     help="skip the comparison fit without residual replacement")
     ap.add_argument("--rr-period", type=int, default=-1,
@@ -628,7 +676,8 @@ def _parser():
                     help="requests of the serving measurement added to the line (0 = skip)")
     ap.add_argument("--serve", action="store_true",
                     help="only the serving measurement (2000 requests unless --serve-requests is given)")
-    ap.add_argument("--serve-precision", default="bf16", choices=["f32", "bf16", "tf32x3", "fp8"])
+    ap.add_argument("--serve-precision", default="bf16",
+                    help="comma-separated dictionary precisions of the serving run (f32, bf16, tf32x3, fp8)")
     ap.add_argument("--cpu-budget", type=float, default=60.0,
                     help="seconds of oracle time the reference arm's timed steps take in total")
     ap.add_argument("--dense-path", default="auto", choices=sorted(_DENSE_PATHS),
@@ -655,9 +704,10 @@ def main():
         import paper_2105_10439_gb300 as cf
         dev = torch.device("cuda", 0)
         n = args.serve_requests if "--serve-requests" in sys.argv else 2000
-        rep = serving_report(cf, dev, n, args.serve_precision)
+        precs = args.serve_precision.split(",")
+        rep = serving_config5(cf, dev, n, precs)
         print(json.dumps({"serving": rep, "metric": "CoFEM serving p50/p99 ms at 80% of capacity",
-                          "value": rep["at_80pct"]["p99_ms"], "unit": "ms (p99)"}), flush=True)
+                          "value": rep[precs[0]]["at_80pct"]["p99_ms"], "unit": "ms (p99)"}), flush=True)
     elif args.operator_only:
         run_operator_only(args)
     elif args.fig3b:

@@ -138,6 +138,12 @@ typedef struct cofem_opts {
                                  each E-step's CG loop ends, without acting on it; read it
                                  with cofem_true_residuals.  X is then held as the FP32
                                  pair as well.  0 (default): only when rr_period > 0. */
+    int warm_start;           /* 1: warm start with probe reuse (beyond the paper, which
+                                 starts every E-step at X = 0 with fresh probes): every
+                                 E-step draws the probes of t = 1, and E-step t >= 2 starts
+                                 its K+1 columns from the previous E-step's X (R = B - A X,
+                                 one extra operator application per E-step).  0 (default):
+                                 Alg. 1 and Alg. 2 as printed. */
 } cofem_opts;
 
 /* Dense BF16 operator forms.  TWO_PASS streams the dictionary for Phi V and a
@@ -156,7 +162,7 @@ typedef struct cofem_opts {
 
 /* Fill *o with the defaults: F32, Jacobi, per-column, rr_period 0,
  * alpha_max 1e12, seed 2, stream NULL, use_graph 1, dense_path AUTO, max_sms 0,
- * overlap_launch 1, prior GAUSSIAN, check_residual 0. */
+ * overlap_launch 1, prior GAUSSIAN, check_residual 0, warm_start 0. */
 void cofem_default_opts(cofem_opts* o);
 
 /* Create a handle for one dictionary (step a0: upload, optional BF16
@@ -360,6 +366,16 @@ cofem_status cofem_server_destroy(cofem_server* srv);
 cofem_status cofem_apply_dense_noalloc(const float* phi, long long N, long long D, long long ld,
                                        const float* V, int Q, const float* alpha, double beta,
                                        float* Psi, void* stream);
+
+/* Timing of the precision form's accurate residual B - A X (row a6), in the
+ * launch configuration a fit uses, on the handle's current X, bracketed by
+ * CUDA events on the handle's stream: *ms_residual = mean time of one whole
+ * accurate residual (all its kernels), *ms_first = mean time of its first
+ * product Phi~ X in FP32 pairs (dense dictionaries; 0 otherwise).  Either
+ * pointer may be NULL (not both).  Requires a previous fit with the same Q on
+ * a handle with rr_period > 0 or check_residual = 1.  Errors: INVALID_ARG,
+ * CUDA. */
+cofem_status cofem_time_true_residual(struct cofem_ctx* h, int Q, int reps, double* ms_residual, double* ms_first);
 
 /* Bytes of device memory the handle holds (Phi copy, theta, fit workspace). */
 long long cofem_device_bytes(struct cofem_ctx* h);

@@ -57,6 +57,9 @@ garbled or at odds with itself):
     the paper says); where s_j <= 0 the term is undefined and dropped, and the
     floor 1/alpha_max applies as in reading 10.  exp(-xi^2) / erfc(-xi) is
     evaluated as 1 / erfcx(-xi), the same function without overflow.
+14. Warm start with probe reuse (beyond the paper, which starts each E-step
+    at X = 0 with fresh probes): every E-step draws the probes of t = 1 and
+    E-step t >= 2 starts Alg. 2 from the previous E-step's X with R = B - A X.
 13. Multi-task CoFEM (cofem_multitask; multi-task subsection of Sec. III):
     the L tasks share alpha and beta; each task l draws its own probes
     (Philox counter word 3 = l; task 0 is the single-task rule), its own
@@ -102,7 +105,8 @@ def _meets_tol(rnorm, bnorm, tol, conv):
     raise ValueError(conv)
 
 
-def pcg(apply_a, B, minv, tol, maxit, conv="per_column", rr_period=0, history=None, check=False, info=None):
+def pcg(apply_a, B, minv, tol, maxit, conv="per_column", rr_period=0, history=None, check=False, info=None,
+        x0=None):
     """Alg. 2 (ParallelConjGradient) on the D x Q block B with M^-1 = diag(minv).
 
     Returns (X, iters, flags).  `history`, if a list, receives a copy of X after
@@ -111,12 +115,17 @@ def pcg(apply_a, B, minv, tol, maxit, conv="per_column", rr_period=0, history=No
     a column that misses it (not broken down, budget left) restarts from it
     with P = M^-1 R and the loop goes on.  `info`, if a dict, receives
     "true_res", the relative true residuals ||b_q - A x_q|| / ||b_q|| of the
-    returned X (when check is set)."""
+    returned X (when check is set).  x0: initial X (warm start, reading 14 of
+    the oracle); R starts as B - A x0."""
     B = np.asarray(B, dtype=np.float64)
     D, Q = B.shape
     minv = np.asarray(minv, dtype=np.float64)[:, None]
-    X = np.zeros((D, Q))
-    R = B.copy()
+    if x0 is None:
+        X = np.zeros((D, Q))
+        R = B.copy()
+    else:
+        X = np.array(x0, dtype=np.float64)
+        R = B - apply_a(X)
     W = minv * R
     P = W.copy()
     rho = np.sum(R * W, axis=0)
@@ -184,7 +193,7 @@ def pcg(apply_a, B, minv, tol, maxit, conv="per_column", rr_period=0, history=No
 
 def cofem(op, y, beta, K, T, cg_tol, cg_maxit, seed, alpha0=None, precond="jacobi",
           alpha_max=1e12, conv="per_column", rr_period=0, probe_fn=None,
-          solver="pcg", return_x=False, prior="gaussian", check_residual=False):
+          solver="pcg", return_x=False, prior="gaussian", check_residual=False, warm_start=False):
     """Alg. 1 (CovarianceFreeEM) with Alg. 2 as the linear solver.
 
     op        oracle.operators.DenseOperator / ToeplitzOperator
@@ -194,6 +203,8 @@ def cofem(op, y, beta, K, T, cg_tol, cg_maxit, seed, alpha0=None, precond="jacob
     prior     "gaussian" (Eq. mstep) or "rectified" (non-negativity, reading 12).
     check_residual  true-residual check at the end of each E-step (reading 11;
               always on with rr_period > 0).
+    warm_start  probe reuse and warm start (reading 14): every E-step draws the
+              probes of t = 1 and E-step t >= 2 starts from the previous X.
     Returns dict(alpha, mu, s, cg_iters, flags, true_res (T x (K+1), NaN where
     not checked)[, X]).
     """
@@ -207,8 +218,9 @@ def cofem(op, y, beta, K, T, cg_tol, cg_maxit, seed, alpha0=None, precond="jacob
     flags = 0
     mu = s = X = None
     for t in range(1, T + 1):
-        probes = (rademacher_probes(seed, t, K, D) if probe_fn is None
-                  else np.asarray(probe_fn(t, K, D), dtype=np.float64))
+        tp = 1 if warm_start else t
+        probes = (rademacher_probes(seed, tp, K, D) if probe_fn is None
+                  else np.asarray(probe_fn(tp, K, D), dtype=np.float64))
         B = np.empty((D, K + 1))
         B[:, 0] = b
         B[:, 1:] = probes.T
@@ -220,7 +232,8 @@ def cofem(op, y, beta, K, T, cg_tol, cg_maxit, seed, alpha0=None, precond="jacob
         if solver == "pcg":
             info = {}
             X, u, f = pcg(apply_a, B, minv, cg_tol, cg_maxit, conv=conv, rr_period=rr_period,
-                          check=rr_period > 0 or check_residual, info=info)
+                          check=rr_period > 0 or check_residual, info=info,
+                          x0=X if warm_start and t > 1 else None)
             cg_iters[t - 1] = u
             flags |= f
             if info["true_res"] is not None:

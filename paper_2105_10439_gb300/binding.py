@@ -62,6 +62,7 @@ class cofem_opts(C.Structure):
         ("overlap_launch", C.c_int),
         ("prior", C.c_int),
         ("check_residual", C.c_int),
+        ("warm_start", C.c_int),
     ]
 
 
@@ -113,6 +114,7 @@ def _load():
         "cofem_graph_info": (i, [vp, C.POINTER(i), C.POINTER(i)]),
         "cofem_true_residuals": (i, [vp, vp]),
         "cofem_fit_stats": (i, [vp, C.POINTER(i), C.POINTER(i)]),
+        "cofem_time_true_residual": (i, [vp, i, i, C.POINTER(d), C.POINTER(d)]),
         "cofem_time_operator": (i, [vp, i, i, C.POINTER(d)]),
         "cofem_apply_dense_noalloc": (i, [vp, ll, ll, ll, vp, i, vp, d, vp, vp]),
         "cofem_estimate_bytes": (ll, [i, ll, ll, ll, i, i]),
@@ -303,6 +305,13 @@ def cofem_true_residuals(h: int, T_em: int, K: int) -> np.ndarray:
     out = np.empty((T_em, K + 1), dtype=np.float64)
     _check(lib.cofem_true_residuals(h, out.ctypes.data))
     return out
+
+
+def cofem_time_true_residual(h: int, Q: int, reps: int) -> tuple[float, float]:
+    """(ms per accurate residual, ms per first product Phi~ X in FP32 pairs)."""
+    a, b = C.c_double(0.0), C.c_double(0.0)
+    _check(lib.cofem_time_true_residual(h, Q, reps, C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def cofem_fit_stats(h: int) -> tuple[int, int]:

@@ -232,6 +232,9 @@ cofem_status build_graph(cofem_ctx* c, int Q, bool pdl) {
     // whole graph is launched); the gate kernel sets the CG loop's entry
     // condition, a handle of the verification body
     const bool verify = precise(c);
+    // warm start: A X of the previous E-step's X for the initial residual (at
+    // t = 1 the initialisation ignores it and starts from X = 0)
+    if (c->opts.warm_start) launch_operator(em, c, Q, c->X, OP_PLAIN);
     Sink vf;
     cudaGraphConditionalHandle h_vf = 0, h_cg = 0;
     if (verify) {
@@ -293,6 +296,7 @@ cofem_status run_fit_direct(cofem_ctx* c, int Q, int T) {
     launch_fit_setup(s, c, Q);
     const bool verify = precise(c);
     for (int t = 1; t <= T; ++t) {
+        if (c->opts.warm_start) launch_operator(s, c, Q, c->X, OP_PLAIN);
         launch_cg_init(s, c, Q, 0);
         if (s.err) return cuda_fail(s.err, "launch");
         cofem_status st = read_ctl(c);
@@ -347,6 +351,7 @@ cofem_status set_kernel_attributes(int dev) {
     CK(tc_kernel_attributes(optin));
     CK(toeplitz_kernel_attributes());
     CK(dct_kernel_attributes());
+    CK(df_kernel_attributes());
     g_attr_done[dev] = true;
     return COFEM_OK;
 }
@@ -383,6 +388,7 @@ void cofem_default_opts(cofem_opts* o) {
     o->use_graph = 1;
     o->overlap_launch = 1;
     o->check_residual = 0;
+    o->warm_start = 0;
 }
 
 const char* cofem_status_string(cofem_status s) {
@@ -448,6 +454,7 @@ static cofem_status create_impl(cofem_ctx** out, long long N, long long D, int k
     if (o.rr_period < 0) return fail(COFEM_ERR_INVALID_ARG, "rr_period < 0");
     if (o.check_residual != 0 && o.check_residual != 1)
         return fail(COFEM_ERR_INVALID_ARG, "check_residual must be 0 or 1");
+    if (o.warm_start != 0 && o.warm_start != 1) return fail(COFEM_ERR_INVALID_ARG, "warm_start must be 0 or 1");
     if (o.overlap_launch != 0 && o.overlap_launch != 1) return fail(COFEM_ERR_INVALID_ARG, "overlap_launch must be 0 or 1");
     if (o.prior != COFEM_PRIOR_GAUSSIAN && o.prior != COFEM_PRIOR_RECTIFIED)
         return fail(COFEM_ERR_INVALID_ARG, "prior must be COFEM_PRIOR_GAUSSIAN or COFEM_PRIOR_RECTIFIED");
@@ -696,6 +703,7 @@ static cofem_status fit_impl(cofem_ctx* c, int L, const float* Y, double beta, c
     hc->prior = c->opts.prior;
     hc->fix_residual = c->opts.rr_period > 0;
     hc->precond_none = c->opts.precond == COFEM_PRECOND_NONE;
+    hc->warm = c->opts.warm_start;
     hc->ap_part = c->part + (size_t)2 * Q * c->nch;   // slab 2 of the CG partials
     hc->ap_n = c->nch;
     CK(cudaMemcpyAsync(c->ctl, hc, sizeof(DevCtl), cudaMemcpyHostToDevice, c->stream));
@@ -859,6 +867,36 @@ cofem_status cofem_time_operator(cofem_ctx* c, int Q, int reps, double* ms_per_a
     cudaEventDestroy(e1);
     if (s.err) return cuda_fail(s.err, "operator launch");
     *ms_per_apply = (double)ms / reps;
+    return COFEM_OK;
+}
+
+cofem_status cofem_time_true_residual(cofem_ctx* c, int Q, int reps, double* ms_residual, double* ms_first) {
+    g_err[0] = 0;
+    if (!c || reps < 1 || (!ms_residual && !ms_first)) return fail(COFEM_ERR_INVALID_ARG, "bad arguments");
+    if (!precise(c)) return fail(COFEM_ERR_INVALID_ARG, "the handle has neither rr_period > 0 nor check_residual = 1");
+    if (Q != c->Qcap || c->last_T == 0) return fail(COFEM_ERR_INVALID_ARG, "Q must match the last fit (%d)", c->Qcap);
+    CK(cudaSetDevice(c->device));
+    cudaEvent_t e[4];
+    for (auto& x : e) CK(cudaEventCreate(&x));
+    Sink s;
+    s.stream = c->stream;
+    launch_true_residual(s, c, Q, DF_CHECK);   // warm-up
+    CK(cudaEventRecord(e[0], c->stream));
+    for (int r = 0; r < reps; ++r) launch_true_residual(s, c, Q, DF_CHECK);
+    CK(cudaEventRecord(e[1], c->stream));
+    if (c->kind == COFEM_OP_DENSE) {
+        CK(cudaEventRecord(e[2], c->stream));
+        for (int r = 0; r < reps; ++r) launch_df_first_product(s, c, Q);
+        CK(cudaEventRecord(e[3], c->stream));
+    }
+    CK(cudaEventSynchronize(c->kind == COFEM_OP_DENSE ? e[3] : e[1]));
+    float a = 0.0f, b = 0.0f;
+    CK(cudaEventElapsedTime(&a, e[0], e[1]));
+    if (c->kind == COFEM_OP_DENSE) CK(cudaEventElapsedTime(&b, e[2], e[3]));
+    for (auto& x : e) cudaEventDestroy(x);
+    if (s.err) return cuda_fail(s.err, "accurate residual launch");
+    if (ms_residual) *ms_residual = (double)a / reps;
+    if (ms_first) *ms_first = c->kind == COFEM_OP_DENSE ? (double)b / reps : 0.0;
     return COFEM_OK;
 }
 

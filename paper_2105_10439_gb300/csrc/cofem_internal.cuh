@@ -28,6 +28,8 @@ struct DevCtl {
     int T, K, Q, maxit, conv, rr_period, prior;
     int L;            // tasks (multi-task fit: Q = L (K + 1), column l (K+1) + k of task l)
     int precond_none; // M = I (unpreconditioned CG) instead of M = beta theta + alpha
+    int warm;         // warm start with probe reuse: E-step t >= 2 starts from the previous X
+                      // and every E-step draws the probes of t = 1
     int t;            // current EM iteration, 1-based
     int u;            // CG iterations done in EM iteration t
     int any_active;   // some column still iterating
@@ -604,6 +606,8 @@ struct DfSizes {
 DfSizes df_configure(cofem_ctx* c, int Q);
 void launch_true_residual(Sink& s, cofem_ctx* c, int Q, int mode);
 int true_residual_kernels(cofem_ctx* c);
+cudaError_t df_kernel_attributes();
+void launch_df_first_product(Sink& s, cofem_ctx* c, int Q);   // dense only
 void launch_df_check(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_vf);
 void launch_cg_gate(Sink& s, cofem_ctx* c, cudaGraphConditionalHandle h_cg);
 

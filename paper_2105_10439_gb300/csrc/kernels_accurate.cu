@@ -17,10 +17,17 @@
 // pairs on the CUDA cores.
 //
 // Dense dictionary (row-major Phi~, FP32 / BF16 / FP8 codes with row scales):
-//   k_df_gemm<E, false>   T_s = Phi~ X over a k range s (FP64 partials)
-//   k_df_combine_t        t = sum_s T_s (times s_i^2 for FP8) as an FP32 pair
-//   k_df_gemm<E, true>    U_s = Phi~^T t over an i range s (FP64 partials)
-//   k_df_residual         R = B - beta sum_s U_s - alpha X (FP64), norms
+//   k_df_gemm<E, false, false>  T_s = Phi~ X over a k range s, every product
+//                               and sum error-free (FP64 partials)
+//   k_df_combine_t              t = sum_s T_s (times s_i^2 for FP8) as an FP32 pair
+//   k_df_gemm<E, true, true>    U_s = Phi~^T t over an i range s: plain FP32
+//                               sums of 32 terms, folded into FP32 pairs
+//   k_df_residual               R = B - beta sum_s U_s - alpha X (FP64), norms
+// The cancellation is in T = Phi~ X (X mostly in Phi's null space); U is not
+// a cancellation of that kind, and FP32 sums of 32 terms, combined exactly,
+// leave an error near 1e-7 ||b|| in the residual (measured in an FP32
+// emulation at 1024 x 4096), so the second product takes two FMAs per term
+// instead of the eleven instructions of the error-free form.
 // Convolution dictionary:
 //   k_df_conv, k_df_conv_t (direct sums over the L taps), k_df_residual.
 #include <cuda_fp8.h>
@@ -66,90 +73,154 @@ template <> __device__ __forceinline__ float elem<uint8_t>(uint8_t v) {
 // ---------------------------------------------------------------------------
 // Dense product in FP32 pairs.  out[s][m][q] = sum over k in chunk s of
 // A(m, k) (Xh + Xl)(k, q), with A(m, k) = A[m lda + k] (TRANS false: Phi~ X)
-// or A[k lda + m] (TRANS true: Phi~^T t), X(k, q) = X[k xk + q xq].  A block
-// owns DF_BM rows of the output and all (padded) QP columns for one k chunk;
-// thread (tm, tq) keeps the DF_TM x DF_TQ micro tile of rows tm*4.. and
-// columns tq*4.. as FP32 pairs.  Operand tiles of DF_KC k values are staged
-// in shared memory ([k][m] and [k][q], so the inner loop reads float4s).
+// or A[k lda + m] (TRANS true: Phi~^T t), X(k, q) = X[k xk + q xq].  M and K
+// are the padded extents (the padding of Phi~, X and t is zero), so every
+// tile is whole.  A block owns DF_BM rows of the output and all (padded) QP
+// columns for one k chunk; thread (tm, tq) keeps the rows tm + 16 a (a < 4)
+// and the columns 4 tq .. 4 tq + 3 as FP32 pairs.  Tiles of DF_KC k values
+// arrive by cp.async, double-buffered, so the copy of tile t + 1 overlaps the
+// arithmetic on tile t; the dictionary tile stays in its storage type (FP32,
+// BF16 or E4M3 codes) in shared memory and is widened when read.
 // ---------------------------------------------------------------------------
-constexpr int DF_BM = 64, DF_KC = 32, DF_TM = 4, DF_TQ = 4;
-constexpr int DF_AP = DF_BM + 4;          // padded row of the A tile (float4 aligned)
-constexpr int DF_QMAXP = COFEM_QMAX + 4;  // padded row of the X tiles
+constexpr int DF_BM = 64, DF_KC = 32, DF_TM = 4, DF_TQ = 4, DF_NBUF = 3;
 
-template <typename E, bool TRANS>
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename E> struct DfTile {
+    // elements per 4-byte copy; row stride of the shared tile in elements
+    static constexpr int PER = 4 / (int)sizeof(E);
+    // [m][k] (TRANS false): DF_KC + pad elements per row, an odd number of
+    // 4-byte words so that 16 consecutive rows fall in 16 banks
+    static constexpr int ROWK = sizeof(E) == 4 ? DF_KC + 1 : (sizeof(E) == 2 ? DF_KC + 2 : DF_KC + 4);
+    static constexpr int ELEMS_N = DF_BM * ROWK;     // TRANS false
+    static constexpr int ELEMS_T = DF_KC * DF_BM;    // TRANS true: [k][m]
+    static constexpr int ELEMS = ELEMS_N > ELEMS_T ? ELEMS_N : ELEMS_T;
+};
+
+template <typename E, bool TRANS, bool BLOCKED>
 __global__ __launch_bounds__(256) void k_df_gemm(const E* __restrict__ A, long long lda, long long M, long long K,
                                                  long long kchunk, const float* __restrict__ Xh,
                                                  const float* __restrict__ Xl, long long xk, long long xq, int Q,
                                                  int QP, double* __restrict__ out, long long osS, long long osM,
                                                  long long osQ) {
-    __shared__ __align__(16) float As[DF_KC][DF_AP];
-    __shared__ __align__(16) float Hs[DF_KC][DF_QMAXP];
-    __shared__ __align__(16) float Ls[DF_KC][DF_QMAXP];
+    using TT = DfTile<E>;
+    extern __shared__ __align__(16) unsigned char df_smem[];
+    E* As = reinterpret_cast<E*>(df_smem);                                  // [DF_NBUF][TT::ELEMS]
+    const int QS = QP + 4;                                                  // row of the X tiles
+    float* Hs = reinterpret_cast<float*>(df_smem + ((DF_NBUF * TT::ELEMS * sizeof(E) + 15) / 16) * 16);
+    float* Ls = Hs + DF_NBUF * DF_KC * QS;                                  // [DF_NBUF][KC][QS] each
     const int nthr = blockDim.x;
     const int tm = threadIdx.x % (DF_BM / DF_TM), tq = threadIdx.x / (DF_BM / DF_TM);
     const long long m0 = (long long)blockIdx.x * DF_BM;
     const long long kb = (long long)blockIdx.y * kchunk;
     const long long ke = kb + kchunk < K ? kb + kchunk : K;
-    float S[DF_TM][DF_TQ], C[DF_TM][DF_TQ];
-#pragma unroll
-    for (int a = 0; a < DF_TM; ++a)
-#pragma unroll
-        for (int b = 0; b < DF_TQ; ++b) S[a][b] = C[a][b] = 0.0f;
-    for (long long k0 = kb; k0 < ke; k0 += DF_KC) {
-        __syncthreads();   // the previous tile has been read
-        // A tile: rows m0.., k values k0.. (zero outside M x [kb, ke))
-        for (int e = threadIdx.x; e < DF_BM * DF_KC; e += nthr) {
-            int mm, kk;
-            if (TRANS) { kk = e / DF_BM; mm = e % DF_BM; }   // contiguous in m
-            else { mm = e / DF_KC; kk = e % DF_KC; }         // contiguous in k
-            const long long m = m0 + mm, k = k0 + kk;
-            float v = 0.0f;
-            if (m < M && k < ke) v = elem<E>(TRANS ? A[k * lda + m] : A[m * lda + k]);
-            As[kk][mm] = v;
+    const int ntiles = (int)((ke - kb + DF_KC - 1) / DF_KC);
+
+    auto issue = [&](int tile, int buf) {
+        const long long k0 = kb + (long long)tile * DF_KC;
+        E* a = As + buf * TT::ELEMS;
+        constexpr int CPR = DF_KC / TT::PER;    // 4-byte copies per tile row
+        if (TRANS) {   // rows k, DF_BM contiguous elements of m
+            for (int e = threadIdx.x; e < DF_KC * (DF_BM / TT::PER); e += nthr) {
+                const int kk = e / (DF_BM / TT::PER), c = e % (DF_BM / TT::PER);
+                const long long k = k0 + kk;
+                const bool v = k < ke && m0 + c * TT::PER < M;
+                cp_async4(a + kk * DF_BM + c * TT::PER, v ? (const void*)(A + k * lda + m0 + c * TT::PER) : (const void*)A, v);
+            }
+        } else {       // rows m, DF_KC contiguous elements of k
+            for (int e = threadIdx.x; e < DF_BM * CPR; e += nthr) {
+                const int mm = e / CPR, c = e % CPR;
+                const long long m = m0 + mm;
+                const bool v = m < M && k0 + c * TT::PER < ke;
+                cp_async4(a + mm * TT::ROWK + c * TT::PER, v ? (const void*)(A + m * lda + k0 + c * TT::PER) : (const void*)A, v);
+            }
         }
-        // X tiles (zero for q >= Q and outside the k range)
+        float* h = Hs + buf * DF_KC * QS;
+        float* l = Ls + buf * DF_KC * QS;
         for (int e = threadIdx.x; e < DF_KC * QP; e += nthr) {
             int kk, q;
             if (xq == 1) { kk = e / QP; q = e % QP; }   // contiguous in q
             else { q = e / DF_KC; kk = e % DF_KC; }      // contiguous in k
             const long long k = k0 + kk;
-            float h = 0.0f, l = 0.0f;
-            if (q < Q && k < ke) {
-                const long long idx = k * xk + (long long)q * xq;
-                h = Xh[idx];
-                l = Xl[idx];
-            }
-            Hs[kk][q] = h;
-            Ls[kk][q] = l;
+            const bool v = q < Q && k < ke;
+            const long long idx = v ? k * xk + (long long)q * xq : 0;
+            cp_async4(h + kk * QS + q, Xh + idx, v);
+            cp_async4(l + kk * QS + q, Xl + idx, v);
         }
-        __syncthreads();
-        if (tq * DF_TQ < QP) {
-#pragma unroll 4
-            for (int kk = 0; kk < DF_KC; ++kk) {
-                const float4 a4 = *reinterpret_cast<const float4*>(&As[kk][tm * DF_TM]);
-                const float4 h4 = *reinterpret_cast<const float4*>(&Hs[kk][tq * DF_TQ]);
-                const float4 l4 = *reinterpret_cast<const float4*>(&Ls[kk][tq * DF_TQ]);
-                const float av[4] = {a4.x, a4.y, a4.z, a4.w};
-                const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
-                const float lv[4] = {l4.x, l4.y, l4.z, l4.w};
+        cp_async_commit();
+    };
+
+    float S[DF_TM][DF_TQ], C[DF_TM][DF_TQ];
 #pragma unroll
-                for (int a = 0; a < DF_TM; ++a)
+    for (int a = 0; a < DF_TM; ++a)
 #pragma unroll
-                    for (int b = 0; b < DF_TQ; ++b) df_mac(S[a][b], C[a][b], av[a], hv[b], lv[b]);
-            }
+        for (int b = 0; b < DF_TQ; ++b) S[a][b] = C[a][b] = 0.0f;
+    // three buffers: tile t + 2 is issued after the barrier of iteration t,
+    // into the buffer every thread finished reading in iteration t - 1, so one
+    // barrier per tile suffices
+    if (ntiles > 0) issue(0, 0);
+    if (ntiles > 1) issue(1, 1);
+    for (int t = 0; t < ntiles; ++t) {
+        const int buf = t % DF_NBUF;
+        if (t + 1 < ntiles) cp_async_wait1();
+        else cp_async_wait0();
+        __syncthreads();   // tile t has landed for every thread; tile t - 1 is done
+        if (t + 2 < ntiles) issue(t + 2, (t + 2) % DF_NBUF);
+        const E* a = As + buf * TT::ELEMS;
+        const float* h = Hs + buf * DF_KC * QS;
+        const float* l = Ls + buf * DF_KC * QS;
+        float B_[DF_TM][DF_TQ];   // BLOCKED: this tile's plain FP32 sums
+        if (BLOCKED) {
+#pragma unroll
+            for (int r = 0; r < DF_TM; ++r)
+#pragma unroll
+                for (int c = 0; c < DF_TQ; ++c) B_[r][c] = 0.0f;
+        }
+#pragma unroll 2
+        for (int kk = 0; kk < DF_KC; ++kk) {
+            float av[DF_TM];
+#pragma unroll
+            for (int r = 0; r < DF_TM; ++r)
+                av[r] = elem<E>(TRANS ? a[kk * DF_BM + tm + 16 * r] : a[(tm + 16 * r) * TT::ROWK + kk]);
+            const float4 h4 = *reinterpret_cast<const float4*>(h + kk * QS + tq * DF_TQ);
+            const float4 l4 = *reinterpret_cast<const float4*>(l + kk * QS + tq * DF_TQ);
+            const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
+            const float lv[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+            for (int r = 0; r < DF_TM; ++r)
+#pragma unroll
+                for (int c = 0; c < DF_TQ; ++c) {
+                    if (BLOCKED) B_[r][c] = fmaf(av[r], lv[c], fmaf(av[r], hv[c], B_[r][c]));
+                    else df_mac(S[r][c], C[r][c], av[r], hv[c], lv[c]);
+                }
+        }
+        if (BLOCKED) {   // fold the tile's sums into the FP32 pairs exactly (TwoSum)
+#pragma unroll
+            for (int r = 0; r < DF_TM; ++r)
+#pragma unroll
+                for (int c = 0; c < DF_TQ; ++c) df_mac(S[r][c], C[r][c], 1.0f, B_[r][c], 0.0f);
         }
     }
-    if (tq * DF_TQ >= QP) return;
 #pragma unroll
-    for (int a = 0; a < DF_TM; ++a) {
-        const long long m = m0 + tm * DF_TM + a;
+    for (int r = 0; r < DF_TM; ++r) {
+        const long long m = m0 + tm + 16 * r;
         if (m >= M) continue;
 #pragma unroll
-        for (int b = 0; b < DF_TQ; ++b) {
-            const int q = tq * DF_TQ + b;
-            if (q < Q) out[blockIdx.y * osS + m * osM + q * osQ] = (double)S[a][b] + (double)C[a][b];
+        for (int c = 0; c < DF_TQ; ++c) {
+            const int q = tq * DF_TQ + c;
+            if (q < Q) out[blockIdx.y * osS + m * osM + q * osQ] = (double)S[r][c] + (double)C[r][c];
         }
     }
+}
+
+template <typename E> size_t df_gemm_smem(int QP) {
+    return ((DF_NBUF * DfTile<E>::ELEMS * sizeof(E) + 15) / 16) * 16 + 2 * DF_NBUF * DF_KC * (QP + 4) * sizeof(float);
 }
 
 // t[i][q] = sum_s Tpart[s][i][q] (times scale[i]^2: Phi~ = diag(scale) C for
@@ -221,7 +292,7 @@ __device__ __forceinline__ double rhs(const DevCtl* ctl, const float* b, int q, 
     column_task(ctl, q, task, k);
     if (k == 0) return (double)b[(size_t)task * Dp + j];
     if (j >= D) return 0.0;
-    return (double)probe_sign_from_word(probe_word(ctl->seed, ctl->t, k, j, task), j);
+    return (double)probe_sign_from_word(probe_word(ctl->seed, ctl->warm ? 1 : ctl->t, k, j, task), j);
 }
 
 // R = B - beta U - alpha (X + Xlo) in FP64 for column q (block (ch, q)), with
@@ -371,7 +442,8 @@ __global__ void k_cg_gate(DevCtl* ctl, cudaGraphConditionalHandle h_cg) {
 int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // k split of a product with M output rows and K terms: enough blocks for four
-// per SM, k chunks a whole number of shared-memory tiles.
+// per SM, k chunks a whole number of shared-memory tiles (K a multiple of
+// DF_KC, so every chunk is whole tiles).
 void df_split_k(long long M, long long K, int sms, int* S, long long* kchunk) {
     const int mb = ceil_div(M, DF_BM);
     int s = ceil_div(4LL * sms, mb);
@@ -387,12 +459,14 @@ template <typename E>
 void launch_df_dense(Sink& s, cofem_ctx* c, int Q, const E* phi) {
     const int QP = c->df_QP;
     const dim3 blk(16 * (QP / DF_TQ));
-    s.launch(k_df_gemm<E, false>, dim3(ceil_div(c->N, DF_BM), c->df_S1), blk, 0, phi, c->Dp, c->N, c->D,
+    const size_t smem = df_gemm_smem<E>(QP);
+    // padded extents: Phi~ is Np x Dp, X is Q x Dp and t is Np x QP, all zero padded
+    s.launch(k_df_gemm<E, false, false>, dim3(ceil_div(c->Np, DF_BM), c->df_S1), blk, smem, phi, c->Dp, c->Np, c->Dp,
              c->df_k1, c->X, c->Xlo, 1LL, c->Dp, Q, QP, c->df_T, c->Np * QP, (long long)QP, 1LL);
     s.launch(k_df_combine_t, dim3(ceil_div(c->Np * QP, 256)), dim3(256), 0, c->df_T, c->df_S1, c->N, c->Np, Q, QP,
              c->phi8 ? (const float*)c->scale8 : (const float*)nullptr, c->df_thi, c->df_tlo);
-    s.launch(k_df_gemm<E, true>, dim3(ceil_div(c->D, DF_BM), c->df_S2), blk, 0, phi, c->Dp, c->D, c->N, c->df_k2,
-             c->df_thi, c->df_tlo, (long long)QP, 1LL, Q, QP, c->df_U, (long long)QP * c->Dp, 1LL, c->Dp);
+    s.launch(k_df_gemm<E, true, true>, dim3(ceil_div(c->Dp, DF_BM), c->df_S2), blk, smem, phi, c->Dp, c->Dp, c->Np,
+             c->df_k2, c->df_thi, c->df_tlo, (long long)QP, 1LL, Q, QP, c->df_U, (long long)QP * c->Dp, 1LL, c->Dp);
 }
 
 }  // namespace
@@ -403,8 +477,8 @@ DfSizes df_configure(cofem_ctx* c, int Q) {
     DfSizes z{};
     z.QP = (Q + DF_TQ - 1) / DF_TQ * DF_TQ;
     if (c->kind == COFEM_OP_DENSE) {
-        df_split_k(c->N, c->D, c->num_sms, &z.S1, &z.k1);
-        df_split_k(c->D, c->N, c->num_sms, &z.S2, &z.k2);
+        df_split_k(c->Np, c->Dp, c->num_sms, &z.S1, &z.k1);
+        df_split_k(c->Dp, c->Np, c->num_sms, &z.S2, &z.k2);
         z.t = (size_t)c->Np * z.QP;
         z.T = (size_t)z.S1 * c->Np * z.QP;
         z.U = (size_t)z.S2 * z.QP * c->Dp;
@@ -415,6 +489,20 @@ DfSizes df_configure(cofem_ctx* c, int Q) {
         z.U = (size_t)z.QP * c->Dp;
     }
     return z;
+}
+
+// The first product alone (Phi~ X in FP32 pairs; the dominant kernel of the
+// accurate residual), for timing.
+void launch_df_first_product(Sink& s, cofem_ctx* c, int Q) {
+    const int QP = c->df_QP;
+    const dim3 blk(16 * (QP / DF_TQ));
+#define DF_FIRST(E, ptr)                                                                                         \
+    s.launch(k_df_gemm<E, false, false>, dim3(ceil_div(c->Np, DF_BM), c->df_S1), blk, df_gemm_smem<E>(QP), ptr, \
+             c->Dp, c->Np, c->Dp, c->df_k1, c->X, c->Xlo, 1LL, c->Dp, Q, QP, c->df_T, c->Np * QP, (long long)QP, 1LL)
+    if (c->phi16) DF_FIRST(__nv_bfloat16, c->phi16);
+    else if (c->phi8) DF_FIRST(uint8_t, c->phi8);
+    else DF_FIRST(float, c->phi32);
+#undef DF_FIRST
 }
 
 // R_out = B - A (X + Xlo) for the active columns (DF_RR, into R) or for every
@@ -432,6 +520,19 @@ void launch_true_residual(Sink& s, cofem_ctx* c, int Q, int mode) {
     const size_t sstride = (size_t)c->df_QP * c->Dp;
     s.launch(k_df_residual, dim3(c->nch, Q), dim3(NT), 0, c->ctl, mode, c->b, c->X, c->Xlo, c->df_U, c->df_S2,
              sstride, c->alpha, c->minv, mode == DF_RR ? c->R : c->Rt, c->D, c->Dp, c->nch, c->part);
+}
+
+cudaError_t df_kernel_attributes() {
+    const int QPmax = COFEM_QMAX;
+    cudaError_t e;
+#define DF_ATTR(E, TR)                                                                                       \
+    if ((e = cudaFuncSetAttribute(k_df_gemm<E, TR, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+                                  (int)df_gemm_smem<E>(QPmax))) != cudaSuccess)                             \
+        return e;
+    DF_ATTR(float, false) DF_ATTR(float, true) DF_ATTR(__nv_bfloat16, false) DF_ATTR(__nv_bfloat16, true)
+    DF_ATTR(uint8_t, false) DF_ATTR(uint8_t, true)
+#undef DF_ATTR
+    return cudaSuccess;
 }
 
 int true_residual_kernels(cofem_ctx* c) {

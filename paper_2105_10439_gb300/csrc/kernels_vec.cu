@@ -86,10 +86,13 @@ __global__ __launch_bounds__(NT) void k_cg_init(DevCtl* ctl, const float* __rest
                                                 float* __restrict__ X, float* __restrict__ R, float* __restrict__ P,
                                                 float* __restrict__ Xlo, long long D, long long Dp, int nch,
                                                 double* part, unsigned* counter, cudaGraphConditionalHandle h_cg,
-                                                SplitOut so) {
+                                                SplitOut so, OpOut uo) {
     __shared__ double sh[NT / 32];
     __shared__ double red[3 * COFEM_QMAX];
     const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q, t = ctl->t;
+    const int tp = ctl->warm ? 1 : t;           // probe reuse draws the probes of t = 1
+    const bool warm = ctl->warm && t > 1;       // start from the previous E-step's X
+    const float beta = (float)ctl->beta;
     const unsigned long long seed = ctl->seed;
     float bb = 0.0f, rz = 0.0f, ap = 0.0f;
     const size_t off = (size_t)q * Dp;
@@ -102,21 +105,32 @@ __global__ __launch_bounds__(NT) void k_cg_init(DevCtl* ctl, const float* __rest
         if (k == 0) {
             bv = ld4(b + (size_t)task * Dp + j);
         } else {
-            const uint64_t w = probe_word(seed, t, k, j, task);   // j..j+3 share one 64-bit word
+            const uint64_t w = probe_word(seed, tp, k, j, task);   // j..j+3 share one 64-bit word
             bv.x = j + 0 < D ? probe_sign_from_word(w, j + 0) : 0.0f;
             bv.y = j + 1 < D ? probe_sign_from_word(w, j + 1) : 0.0f;
             bv.z = j + 2 < D ? probe_sign_from_word(w, j + 2) : 0.0f;
             bv.w = j + 3 < D ? probe_sign_from_word(w, j + 3) : 0.0f;
         }
         const float4 mv = ld4(minv + j), av = ld4(alpha + j);
-        const float4 wv = make_float4(bv.x * mv.x, bv.y * mv.y, bv.z * mv.z, bv.w * mv.w);
-        st4(X + off + j, make_float4(0.f, 0.f, 0.f, 0.f));
-        if (Xlo) st4(Xlo + off + j, make_float4(0.f, 0.f, 0.f, 0.f));
-        st4(R + off + j, bv);
+        float4 rv = bv;
+        if (warm) {   // R = B - A X with A X = beta Phi^T Phi X + alpha X from the operator
+            int s0, ns;
+            op_range(uo, j, s0, ns);
+            const float4 u = op_sum4(uo, Q, q, Dp, j, s0, ns);
+            const float4 xv = ld4(X + off + j);
+            const float bu = beta * uo.uscale;
+            rv = make_float4(bv.x - (bu * u.x + av.x * xv.x), bv.y - (bu * u.y + av.y * xv.y),
+                             bv.z - (bu * u.z + av.z * xv.z), bv.w - (bu * u.w + av.w * xv.w));
+        } else {
+            st4(X + off + j, make_float4(0.f, 0.f, 0.f, 0.f));
+            if (Xlo) st4(Xlo + off + j, make_float4(0.f, 0.f, 0.f, 0.f));
+        }
+        const float4 wv = make_float4(rv.x * mv.x, rv.y * mv.y, rv.z * mv.z, rv.w * mv.w);
+        st4(R + off + j, rv);
         st4(P + off + j, wv);
         store_split(so, q, j, wv);
         bb += bv.x * bv.x + bv.y * bv.y + bv.z * bv.z + bv.w * bv.w;
-        rz += bv.x * wv.x + bv.y * wv.y + bv.z * wv.z + bv.w * wv.w;
+        rz += rv.x * wv.x + rv.y * wv.y + rv.z * wv.z + rv.w * wv.w;
         ap += av.x * wv.x * wv.x + av.y * wv.y * wv.y + av.z * wv.z * wv.z + av.w * wv.w * wv.w;
     }
     const double bbd = block_sum_f(bb, sh);
@@ -135,7 +149,7 @@ __global__ __launch_bounds__(NT) void k_cg_init(DevCtl* ctl, const float* __rest
         ctl->bnorm2[qq] = red[qq];
         ctl->rho[0][qq] = red[COFEM_QMAX + qq];
         ctl->ap[qq] = red[2 * COFEM_QMAX + qq];
-        ctl->rnorm2[qq] = red[qq];
+        ctl->rnorm2[qq] = red[qq];   // (the warm start's first stopping test reads the update's)
         act = red[qq] > 0.0;   // a zero right-hand side starts converged (x = 0)
         ctl->active[qq] = act;
         ctl->broken[qq] = 0;
@@ -437,7 +451,7 @@ __global__ __launch_bounds__(NT) void k_mstep(DevCtl* ctl, const float* __restri
             if (j < D) {
                 const unsigned long long seed = ctl->seed;
                 for (int k = 1; k <= K; ++k) {
-                    const uint64_t w = probe_word(seed, t, k, j, l);
+                    const uint64_t w = probe_word(seed, ctl->warm ? 1 : t, k, j, l);
                     const size_t e = c0 + (size_t)k * Dp;
                     s = fmaf(probe_sign_from_word(w, j), Xlo ? X[e] + Xlo[e] : X[e], s);
                 }
@@ -534,7 +548,7 @@ void launch_fit_setup(Sink& s, cofem_ctx* c, int /*Q*/) {
 
 void launch_cg_init(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg) {
     s.launch(k_cg_init, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->b, c->minv, c->alpha, c->X, c->R, c->P, c->Xlo,
-             c->D, c->Dp, c->nch, c->part, c->counters + 0, h_cg, tc_direction_split(c));
+             c->D, c->Dp, c->nch, c->part, c->counters + 0, h_cg, tc_direction_split(c), op_output(c));
 }
 
 void launch_cg_update(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_rr,

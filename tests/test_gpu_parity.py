@@ -421,6 +421,23 @@ def test_fit_check_residual_reports_the_true_residual(cf):
             cf.cofem_true_residuals(m.h, 1, K)
 
 
+@pytest.mark.parametrize("precision", ["f32", "bf16"])
+def test_fit_warm_start_matches_oracle(cf, precision):
+    """Warm start with probe reuse (every E-step draws the t = 1 probes; E-step
+    t >= 2 starts from the previous X with R = B - A X): the same fit as the
+    oracle's, CG step counts included (on these problems the warm start takes
+    more CG steps than a cold start: the M-step makes the previous solution's
+    components on the inactive coordinates stiff)."""
+    p = dense_gaussian(250, 500, 10, 15.0, seed=11)
+    K, T, tol = 16, 8, 1e-6
+    prec = cf.COFEM_BF16 if precision == "bf16" else cf.COFEM_F32
+    phi = bf16_round(p.phi) if precision == "bf16" else p.phi
+    g = gpu_fit(cf, p, K, T, tol, 600, precision=prec, warm_start=1)
+    r = oracle_fit(p, K, T, tol, 600, phi=phi, warm_start=True)
+    assert_fit_close(g, r)
+    assert np.all(np.abs(g["cg_iters"] - r["cg_iters"]) <= np.maximum(3, 0.15 * r["cg_iters"]))
+
+
 def test_fit_toeplitz_small(cf):
     """The calcium-style convolution makes the E-step system so ill-conditioned
     that even FP64 CG needs > 1000 steps for tol 1e-5; compare the two CG

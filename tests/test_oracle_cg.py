@@ -190,3 +190,25 @@ def test_true_residual_check_reports_without_restart_in_fp64():
     assert it1 == it2 and f1 == f2 == 0
     np.testing.assert_array_equal(X1, X2)
     assert np.all(info["true_res"] <= 1e-8 * (1 + 1e-6))
+
+
+def test_warm_start_from_the_solution_takes_one_step():
+    """x0 = A^-1 B: the initial residual is rounding level, the first update
+    keeps X there and the column stops after one step."""
+    A, minv = _system(30, 70, 1e3, 19)
+    B = np.random.default_rng(20).standard_normal((70, 3))
+    Xs = np.linalg.solve(A, B)
+    X, iters, flags = pcg(lambda V: A @ V, B, minv, 1e-9, 100, x0=Xs)
+    assert iters == 1 and flags == 0
+    np.testing.assert_allclose(X, Xs, rtol=1e-9)
+
+
+def test_warm_start_converges_to_the_same_solution():
+    A, minv = _system(30, 70, 1e3, 21)
+    rng = np.random.default_rng(22)
+    B = rng.standard_normal((70, 3))
+    Xs = np.linalg.solve(A, B)
+    X, iters, flags = pcg(lambda V: A @ V, B, minv, 1e-10, 500, x0=rng.standard_normal((70, 3)))
+    assert flags == 0
+    kappa = np.linalg.cond(A)
+    assert np.all(np.linalg.norm(X - Xs, axis=0) / np.linalg.norm(Xs, axis=0) <= kappa * 1e-10)

@@ -374,3 +374,18 @@ def test_breakdown_fit_goes_on():
         assert np.all(np.isfinite(r3[k])), k
     np.testing.assert_array_equal(r3["alpha"], 1e12)
     np.testing.assert_allclose(r3["s"], 1e-12, rtol=1e-14)
+
+
+def test_warm_start_with_probe_reuse_is_cofem_with_fixed_probes():
+    """Probe reuse draws the t = 1 probes at every E-step; with tight CG
+    tolerances the warm-started fit is the cold-started fit whose probe_fn
+    returns those probes at every t (the same systems, solved from another
+    start), and with exact solves the warm start changes nothing."""
+    p = dense_gaussian(60, 200, 6, 20.0, seed=12)
+    op = DenseOperator(p.phi)
+    fixed = lambda t, K, D: rademacher_probes(4, 1, K, D)   # noqa: E731
+    w = cofem(op, p.y, p.beta, 8, 6, 1e-12, 2000, seed=4, warm_start=True)
+    c = cofem(op, p.y, p.beta, 8, 6, 1e-12, 2000, seed=4, probe_fn=fixed)
+    for k in ("mu", "s"):
+        np.testing.assert_allclose(w[k], c[k], rtol=1e-6, atol=1e-9)
+    np.testing.assert_allclose(1 / w["alpha"], 1 / c["alpha"], rtol=1e-7)
