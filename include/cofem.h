@@ -377,6 +377,17 @@ cofem_status cofem_apply_dense_noalloc(const float* phi, long long N, long long 
  * CUDA. */
 cofem_status cofem_time_true_residual(struct cofem_ctx* h, int Q, int reps, double* ms_residual, double* ms_first);
 
+/* Failure-detection self-test: runs the library's two bounded on-device wait
+ * routines (the grid-counter wait of the single-pass operator, bounded by
+ * `seconds` of %globaltimer, 1e-3 <= seconds <= 2, and the mbarrier wait of
+ * the tensor-core pipeline, bounded by 4096 rounds) on a counter and an
+ * mbarrier that nothing completes, on the current device.  Both waits give
+ * up by their limits (no fault, no hang), set COFEM_FLAG_DEVICE_TIMEOUT and
+ * the call returns COFEM_ERR_CUDA with that flag in *flags (NULL accepted),
+ * as a fit whose wait ran out does; the context stays usable.  Errors:
+ * INVALID_ARG (seconds), NOMEM, CUDA. */
+cofem_status cofem_selftest_bounded_wait(double seconds, unsigned* flags);
+
 /* Bytes of device memory the handle holds (Phi copy, theta, fit workspace). */
 long long cofem_device_bytes(struct cofem_ctx* h);
 

@@ -45,6 +45,7 @@ COFEM_PRIOR_RECTIFIED = 1
 COFEM_FLAG_CG_NOT_CONVERGED = 1
 COFEM_FLAG_ALPHA_CLAMPED = 2
 COFEM_FLAG_BREAKDOWN = 4
+COFEM_FLAG_DEVICE_TIMEOUT = 8
 
 
 class cofem_opts(C.Structure):
@@ -114,6 +115,7 @@ def _load():
         "cofem_graph_info": (i, [vp, C.POINTER(i), C.POINTER(i)]),
         "cofem_true_residuals": (i, [vp, vp]),
         "cofem_fit_stats": (i, [vp, C.POINTER(i), C.POINTER(i)]),
+        "cofem_selftest_bounded_wait": (i, [d, C.POINTER(C.c_uint)]),
         "cofem_time_true_residual": (i, [vp, i, i, C.POINTER(d), C.POINTER(d)]),
         "cofem_time_operator": (i, [vp, i, i, C.POINTER(d)]),
         "cofem_apply_dense_noalloc": (i, [vp, ll, ll, ll, vp, i, vp, d, vp, vp]),
@@ -312,6 +314,15 @@ def cofem_time_true_residual(h: int, Q: int, reps: int) -> tuple[float, float]:
     a, b = C.c_double(0.0), C.c_double(0.0)
     _check(lib.cofem_time_true_residual(h, Q, reps, C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def cofem_selftest_bounded_wait(seconds: float) -> tuple[int, int, str]:
+    """Runs the bounded-wait self-test: (status, flags, message), without
+    raising (the waits are meant to run out: COFEM_ERR_CUDA with
+    COFEM_FLAG_DEVICE_TIMEOUT)."""
+    f = C.c_uint(0)
+    st = lib.cofem_selftest_bounded_wait(float(seconds), C.byref(f))
+    return st, f.value, lib.cofem_last_error().decode(errors="replace")
 
 
 def cofem_fit_stats(h: int) -> tuple[int, int]:

@@ -40,7 +40,6 @@ namespace {
 constexpr int FU_NE = 4, FU_NB = 3, FU_THREADS = 192, FU_BM = 128, FU_G = 2;
 constexpr uint32_t FU_TILE = 16384;                 // 128 rows x 64 bf16
 constexpr uint32_t FU_EBYTES = FU_G * FU_TILE;      // A-ring element: one unit (G tiles), one bulk copy
-constexpr uint64_t FU_GRID_WAIT_NS = 2000000000ull; // 2 s
 constexpr int FU_ACC_STRIDE = 128;                  // TMEM columns per accumulator
 constexpr int FU_DEPTH = 2;                         // waves of phase 1 issued ahead of phase 2
 
@@ -65,38 +64,9 @@ struct FusedParams {
     int mode;
 };
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ uint64_t globaltimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 __device__ __forceinline__ void grid_arrive(unsigned* ctr) {
     __threadfence();
     atomicAdd(ctr, 1u);
-}
-// Bounded wait until *ctr >= target.  Gives up (and raises the block's abort
-// flag) after FU_GRID_WAIT_NS, when this block aborted, or when another block
-// reported a timeout.
-__device__ __noinline__ bool grid_wait(const unsigned* ctr, unsigned target, volatile int* abort_flag,
-                                       const unsigned* gflags) {
-    const uint64_t t0 = globaltimer();
-    for (uint32_t i = 0; i < (1u << 26); ++i) {
-        if (ld_acquire(ctr) >= target) return true;
-        if (*abort_flag) return false;
-        if ((i & 15) == 15) {
-            if ((*(const volatile unsigned*)gflags & COFEM_FLAG_DEVICE_TIMEOUT) ||
-                globaltimer() - t0 > FU_GRID_WAIT_NS)
-                break;
-        }
-        __nanosleep(128);
-    }
-    *abort_flag = 1;
-    return false;
 }
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 

@@ -9,6 +9,7 @@
 namespace {
 
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;   // try_wait rounds before a wait gives up
+constexpr uint64_t GRID_WAIT_NS = 2000000000ull;   // a grid-wide counter wait gives up after 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -33,13 +34,42 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 // Bounded wait for the completion of the phase with the given parity.  Returns
 // false on timeout (and raises the block's abort flag) or when another role
 // has already aborted.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-    for (uint32_t i = 0; i < TC_WAIT_LIMIT; ++i) {
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                       uint32_t limit = TC_WAIT_LIMIT) {
+    for (uint32_t i = 0; i < limit; ++i) {
         if (mbar_try(bar, parity)) return true;
         if ((i & 127) == 127) {
             if (*abort_flag) return false;
             __nanosleep(64);
         }
+    }
+    *abort_flag = 1;
+    return false;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait until *ctr >= target (a grid-wide counter other blocks raise).
+// Gives up (and raises the block's abort flag) after limit_ns of %globaltimer,
+// when this block aborted, or when another block reported a timeout in gflags.
+__device__ __noinline__ bool grid_wait(const unsigned* ctr, unsigned target, volatile int* abort_flag,
+                                       const unsigned* gflags, uint64_t limit_ns = GRID_WAIT_NS) {
+    const uint64_t t0 = globaltimer();
+    for (uint32_t i = 0; i < (1u << 26); ++i) {
+        if (ld_acquire(ctr) >= target) return true;
+        if (*abort_flag) return false;
+        if ((i & 15) == 15) {
+            if ((*(const volatile unsigned*)gflags & COFEM_FLAG_DEVICE_TIMEOUT) || globaltimer() - t0 > limit_ns)
+                break;
+        }
+        __nanosleep(128);
     }
     *abort_flag = 1;
     return false;

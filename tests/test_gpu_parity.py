@@ -652,3 +652,22 @@ def test_fit_dense_n8192_d32768_bf16_properties(cf):
                 precision=cf.COFEM_F32, rr_period=run["rr_period"])
     nm = [20 * np.log10(np.linalg.norm(x["mu"] - p.z) / np.linalg.norm(p.z)) for x in (g, f)]
     assert abs(nm[0] - nm[1]) < 0.1, nm
+
+
+def test_bounded_device_waits_run_out_and_the_context_stays_usable(cf):
+    """Failure detection without a GPU fault: the grid-counter wait and the
+    mbarrier wait of the persistent kernels, run on a counter and an mbarrier
+    that nothing completes, give up by their limits; the call reports
+    COFEM_ERR_CUDA with COFEM_FLAG_DEVICE_TIMEOUT, and a fit on a fresh
+    handle afterwards runs normally."""
+    import time
+    t0 = time.perf_counter()
+    st, flags, msg = cf.cofem_selftest_bounded_wait(0.05)
+    wall = time.perf_counter() - t0
+    assert st == cf.COFEM_ERR_CUDA and flags & cf.COFEM_FLAG_DEVICE_TIMEOUT, (st, flags, msg)
+    assert "timed out" in msg and wall < 30.0
+    p = dense_gaussian(100, 400, 10, 25.0, seed=6)
+    g = gpu_fit(cf, p, 8, 3, 1e-6, 300, precision=cf.COFEM_BF16)
+    r = oracle_fit(p, 8, 3, 1e-6, 300, phi=bf16_round(p.phi))
+    assert_fit_close(g, r)
+    assert not g["flags"] & cf.COFEM_FLAG_DEVICE_TIMEOUT
