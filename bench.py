@@ -49,8 +49,9 @@ _MEASURED_TRAFFIC = {
     ("dense_n8192_d32768_k32_bf16", 1): 1093.6e6,
 }
 
-# --dense-path -> cofem_opts.dense_path
+# --dense-path -> cofem_opts.dense_path, --toeplitz-path -> cofem_opts.toeplitz_path
 _DENSE_PATHS = {"auto": 0, "two_pass": 1, "single_pass": 2}
+_TOEPLITZ_PATHS = {"auto": 0, "direct": 1, "fft": 2}
 
 # workload precision name -> C-ABI precision code
 _PRECISIONS = {"f32": lambda cf: cf.COFEM_F32, "bf16": lambda cf: cf.COFEM_BF16,
@@ -138,6 +139,20 @@ _SMS, _FP32_LANES = 152, 128
 # FP32 instructions per multiply-add of the error-free dot product (TwoProduct
 # through the FMA, the low part's FMA, TwoSum, the compensation adds)
 _DF_OPS_PER_MAC = 11
+
+
+_FFT_F = 8192   # overlap-save block of the FFT convolution
+
+
+def _fftconv_flops(D, L, Q):
+    """Flops of one application of the FFT convolution operator: per tile of
+    F - 2(L-1) outputs and per pair of columns, four radix-2 FFTs of F points
+    ((F/2) log2 F butterflies of 10 flops) and two spectrum products (6 flops
+    per point)."""
+    Dp = (D + 127) // 128 * 128
+    tiles = -(-Dp // (_FFT_F - 2 * (L - 1)))
+    per = 4 * (_FFT_F // 2) * int(math.log2(_FFT_F)) * 10 + 2 * _FFT_F * 6
+    return float(tiles * ((Q + 1) // 2) * per)
 
 
 def _fp32_peak_tflops(sm_mhz):
@@ -323,6 +338,7 @@ def run_ours(args):
     def make(precision, rr_period=None, warm_start=0):
         rr = run["rr_period"] if rr_period is None else rr_period
         return cf.CoFEM(N, D, kind, phi_d, prob.L, precision=precision, rr_period=rr, warm_start=warm_start,
+                        toeplitz_path=_TOEPLITZ_PATHS[args.toeplitz_path],
                         seed=run["seed"], stream=stream, use_graph=0 if args.no_graph else 1,
                         dense_path=_DENSE_PATHS[args.dense_path], overlap_launch=0 if args.no_overlap else 1,
                         prior=cf.COFEM_PRIOR_RECTIFIED if args.prior == "rectified" else cf.COFEM_PRIOR_GAUSSIAN)
@@ -381,6 +397,12 @@ def run_ours(args):
             alg_bytes = 2.0 * N * D * elem + 2.0 * Q * D * 4
             gk = "k_gemm8" if prec == cf.COFEM_FP8_E4M3 else "k_gemm_tc"
             roof = {"bound": "hbm", "kernel": f"two-pass dense operator ({gk} x2 + k_tc_reduce_T)"}
+    elif path == cf.COFEM_TOEPLITZ_FFT:
+        # overlap-save FFTs: per tile and column pair four complex FFTs of F
+        # points and two spectrum products
+        alg_bytes = 2.0 * Q * D * 4                          # read V, write U
+        alg_flops = _fftconv_flops(D, prob.L, Q)
+        roof = {"bound": "alu", "kernel": "convolution operator, FFT form (k_toeplitz_fft)"}
     else:
         # direct causal convolution: Phi v and Phi^T u, 2 L flop per output each
         alg_bytes = 2.0 * Q * D * 4                          # read V, write U
@@ -460,13 +482,16 @@ def run_ours(args):
     if prob.kind == "dense" and prec == cf.COFEM_BF16 and not args.no_fp32_form:
         fp32 = {}
         for key, form in (("tf32x3", cf.COFEM_F32_TF32X3), ("f32_fma", cf.COFEM_F32)):
-            m32 = make(form)
+            # residual replacement needs products exact on the stored
+            # dictionary; the 3xTF32 form runs without it
+            rr = 0 if form == cf.COFEM_F32_TF32X3 else run["rr_period"]
+            m32 = make(form, rr_period=rr)
             ms32, f32flags, _, _ = timed_fits(m32, 1, 1)
             nm32 = _nmse_db(outs[0].cpu().numpy(), prob.z)
             op32 = cf.cofem_time_operator(m32.h, Q, 10)
             m32.close()
             fp32[key] = {"value": T / (ms32 / 1000.0), "unit": "EM-iter/s", "nmse_db": nm32,
-                         "operator_ms": op32, "flags": f32flags}
+                         "operator_ms": op32, "flags": f32flags, "rr_period": rr}
         # the FP8 E4M3 storage variant (per-row scales) on the same problem
         m8 = make(cf.COFEM_FP8_E4M3)
         ms8, f8flags, _, _ = timed_fits(m8, 1, 1)
@@ -682,6 +707,8 @@ def _parser():
                     help="seconds of oracle time the reference arm's timed steps take in total")
     ap.add_argument("--dense-path", default="auto", choices=sorted(_DENSE_PATHS),
                     help="BF16 dense operator form (default: the library's choice)")
+    ap.add_argument("--toeplitz-path", default="auto", choices=sorted(_TOEPLITZ_PATHS),
+                    help="convolution operator form (default: the library's choice)")
     ap.add_argument("--em-iters", type=int, default=0,
                     help="override T (profiling runs only; the benchmark line uses the workload's T)")
     ap.add_argument("--no-graph", action="store_true",

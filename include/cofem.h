@@ -115,7 +115,11 @@ typedef struct cofem_opts {
                                  with X held as an exact FP32 pair; and when the CG loop
                                  ends, every column's true residual is checked against
                                  cg_tol: a column that misses it restarts from that
-                                 residual (P <- M^-1 R) and CG goes on within cg_maxit */
+                                 residual (P <- M^-1 R) and CG goes on within cg_maxit.
+                                 Needs products that are exact on the stored dictionary:
+                                 COFEM_F32, COFEM_BF16, COFEM_FP8_E4M3 or a convolution
+                                 dictionary (UNSUPPORTED with COFEM_F32_TF32X3, whose split
+                                 holds Phi to about 2^-22 only) */
     double alpha_max;         /* alpha_j = 1 / max(mu_j^2 + s_j, 1/alpha_max); default 1e12 */
     unsigned long long seed;  /* probe seed: p_{t,k,j} from Philox4x64-10 with key (seed, 0),
                                  counter (j >> 8, k, t, 0), bit j & 255 (1 -> -1, 0 -> +1) */
@@ -144,7 +148,17 @@ typedef struct cofem_opts {
                                  its K+1 columns from the previous E-step's X (R = B - A X,
                                  one extra operator application per E-step).  0 (default):
                                  Alg. 1 and Alg. 2 as printed. */
+    int toeplitz_path;        /* convolution dictionary: COFEM_TOEPLITZ_AUTO (default: the
+                                 direct form, the faster one on GB300 so far),
+                                 COFEM_TOEPLITZ_DIRECT (tiled direct convolution, O(L) per
+                                 output) or COFEM_TOEPLITZ_FFT (overlap-save FFTs of 8192
+                                 points in shared memory, O(log F) per output, the paper's
+                                 method for this dictionary, Sec. VI-A) */
 } cofem_opts;
+
+#define COFEM_TOEPLITZ_AUTO   0
+#define COFEM_TOEPLITZ_DIRECT 1
+#define COFEM_TOEPLITZ_FFT    2
 
 /* Dense BF16 operator forms.  TWO_PASS streams the dictionary for Phi V and a
  * transposed copy for Phi^T T (2 N D bytes of HBM per application).
@@ -162,7 +176,7 @@ typedef struct cofem_opts {
 
 /* Fill *o with the defaults: F32, Jacobi, per-column, rr_period 0,
  * alpha_max 1e12, seed 2, stream NULL, use_graph 1, dense_path AUTO, max_sms 0,
- * overlap_launch 1, prior GAUSSIAN, check_residual 0, warm_start 0. */
+ * overlap_launch 1, prior GAUSSIAN, check_residual 0, warm_start 0, toeplitz_path AUTO. */
 void cofem_default_opts(cofem_opts* o);
 
 /* Create a handle for one dictionary (step a0: upload, optional BF16
@@ -401,7 +415,8 @@ cofem_status cofem_get_dictionary(struct cofem_ctx* h, float* out);
 /* How the CG loop of Alg. 2 runs for the current Q (valid after a fit or
  * cofem_apply_operator): *path = COFEM_PATH_TWO_PASS or
  * COFEM_PATH_SINGLE_PASS for a BF16 or 3xTF32 dense dictionary, COFEM_PATH_AUTO
- * (0) for the CUDA-core forms (FP32 FMA, convolution); *kernels_cg = kernels
+ * (0) for the FP32 FMA and DCT forms, COFEM_TOEPLITZ_DIRECT or COFEM_TOEPLITZ_FFT
+ * for a convolution dictionary; *kernels_cg = kernels
  * launched per operator application inside the CG loop; *kernels_rr = per
  * accurate residual (a residual replacement or a true-residual check); *kernels_step = kernels of the CG
  * update, stopping test and direction per CG step (2).  Any output pointer

@@ -40,6 +40,9 @@ COFEM_CONV_FROBENIUS = 1
 COFEM_PATH_AUTO = 0
 COFEM_PATH_TWO_PASS = 1
 COFEM_PATH_SINGLE_PASS = 2
+COFEM_TOEPLITZ_AUTO = 0
+COFEM_TOEPLITZ_DIRECT = 1
+COFEM_TOEPLITZ_FFT = 2
 COFEM_PRIOR_GAUSSIAN = 0
 COFEM_PRIOR_RECTIFIED = 1
 COFEM_FLAG_CG_NOT_CONVERGED = 1
@@ -64,6 +67,7 @@ class cofem_opts(C.Structure):
         ("prior", C.c_int),
         ("check_residual", C.c_int),
         ("warm_start", C.c_int),
+        ("toeplitz_path", C.c_int),
     ]
 
 

@@ -351,6 +351,7 @@ cofem_status set_kernel_attributes(int dev) {
     CK(tc_kernel_attributes(optin));
     CK(toeplitz_kernel_attributes());
     CK(dct_kernel_attributes());
+    CK(fftconv_kernel_attributes());
     CK(df_kernel_attributes());
     g_attr_done[dev] = true;
     return COFEM_OK;
@@ -389,6 +390,7 @@ void cofem_default_opts(cofem_opts* o) {
     o->overlap_launch = 1;
     o->check_residual = 0;
     o->warm_start = 0;
+    o->toeplitz_path = COFEM_TOEPLITZ_AUTO;
 }
 
 const char* cofem_status_string(cofem_status s) {
@@ -430,10 +432,19 @@ static cofem_status create_impl(cofem_ctx** out, long long N, long long D, int k
             o.precision != COFEM_FP8_E4M3)
             return fail(COFEM_ERR_INVALID_ARG,
                         "precision must be COFEM_F32, COFEM_BF16, COFEM_F32_TF32X3 or COFEM_FP8_E4M3");
+        // the 3xTF32 products hold the FP32 dictionary only to about 2^-22: CG
+        // then iterates on another dictionary than the one the accurate
+        // residual measures, a mismatch that the cancellation in Phi^T Phi x
+        // lifts far above the CG tolerance, so replacement cannot converge
+        if (o.precision == COFEM_F32_TF32X3 && o.rr_period > 0)
+            return fail(COFEM_ERR_UNSUPPORTED, "residual replacement needs products exact on the stored dictionary "
+                                               "(COFEM_F32, COFEM_BF16, COFEM_FP8_E4M3), not 3xTF32");
     } else if (kind == COFEM_OP_TOEPLITZ) {
         if (N != D) return fail(COFEM_ERR_INVALID_ARG, "a convolutional dictionary needs N == D");
         if (L < 1 || L > 1024 || L > N) return fail(COFEM_ERR_INVALID_ARG, "need 1 <= L <= min(1024, N)");
         if (o.precision != COFEM_F32) return fail(COFEM_ERR_INVALID_ARG, "convolutional dictionary is FP32 only");
+        if (o.toeplitz_path < COFEM_TOEPLITZ_AUTO || o.toeplitz_path > COFEM_TOEPLITZ_FFT)
+            return fail(COFEM_ERR_INVALID_ARG, "toeplitz_path must be AUTO, DIRECT or FFT");
     } else if (kind == COFEM_OP_DCT) {
         if (D < 16 || D > COFEM_DCT_MAX_D || (D & (D - 1)))
             return fail(COFEM_ERR_INVALID_ARG, "a DCT dictionary needs D a power of two, 16 <= D <= %d",
@@ -566,6 +577,17 @@ static cofem_status create_impl(cofem_ctx** out, long long N, long long D, int k
         if ((st = check_finite_dev(c, c->h, L, "h"))) return bail(st);
         CKB(toeplitz_prepare(c->L));
         launch_toeplitz_theta(c->stream, c);
+        // AUTO takes the direct form: on GB300 the tiled direct convolution
+        // (420 us per application at D = 10^6, L = 256, Q = 17) beats the
+        // shared-memory FFT form (890 us), whose radix-2 stages are bound by
+        // shared-memory traffic and barriers, not by its O(log F) flops
+        c->use_fftconv = o.toeplitz_path == COFEM_TOEPLITZ_FFT;
+        if (c->use_fftconv) {
+            if ((st = dalloc(c, &c->fc_H, (size_t)1 << COFEM_FFTCONV_LOGF)) ||
+                (st = dalloc(c, &c->fc_tw, (size_t)1 << (COFEM_FFTCONV_LOGF - 1))))
+                return bail(st);
+            launch_fftconv_setup(c->stream, c);
+        }
     }
     CKB(cudaGetLastError());
     if (o.precond == COFEM_PRECOND_ONE) {
@@ -605,6 +627,8 @@ cofem_status cofem_destroy(cofem_ctx* c) {
     dfree(c, &c->phi8, (size_t)c->Np * c->Dp);
     dfree(c, &c->scale8, (size_t)c->Np);
     dfree(c, &c->h, (size_t)c->L);
+    dfree(c, &c->fc_H, (size_t)1 << COFEM_FFTCONV_LOGF);
+    dfree(c, &c->fc_tw, (size_t)1 << (COFEM_FFTCONV_LOGF - 1));
     dfree(c, &c->dct_rows, (size_t)c->N);
     dfree(c, &c->dct_mask, (size_t)c->Dp);
     dfree(c, &c->dct_tw, (size_t)(c->D / 4 > 0 ? c->D / 4 : 1));
@@ -938,6 +962,7 @@ cofem_status cofem_operator_info(cofem_ctx* c, int* path, int* kernels_cg, int* 
         kc = 2;   // k_gemm1_simt, k_gemm2_simt
         kr = true_residual_kernels(c);
     } else {
+        if (c->kind == COFEM_OP_TOEPLITZ) pth = c->use_fftconv ? COFEM_TOEPLITZ_FFT : COFEM_TOEPLITZ_DIRECT;
         kr = true_residual_kernels(c);
     }
     if (path) *path = pth;

@@ -16,6 +16,7 @@
 #endif
 #define COFEM_VEC_THREADS 256
 #define COFEM_DCT_MAX_D 32768  // largest DCT dictionary (D/2 complex points in shared memory)
+#define COFEM_FFTCONV_LOGF 13  // FFT convolution: 8192-point overlap-save blocks
 
 // ---------------------------------------------------------------------------
 // Device-resident control block: fit parameters plus the per-column CG scalars
@@ -524,6 +525,9 @@ struct cofem_ctx {
     void* tc = nullptr;              // tensor-core operator plan (kernels_tc.cu)
     bool use_tc = false;             // dense dictionary applied on the tensor cores
     float* h = nullptr;              // Toeplitz filter, L floats
+    bool use_fftconv = false;        // convolution applied through FFTs (kernels_fftconv.cu)
+    float2* fc_H = nullptr;          // FFT convolution: DFT of h (8192 points)
+    float2* fc_tw = nullptr;         // FFT convolution: twiddles (4096)
     int* dct_rows = nullptr;         // DCT dictionary: the N kept rows of Omega^-1
     float* dct_mask = nullptr;       // DCT dictionary: 1 at the kept rows, Dp floats
     float2* dct_tw = nullptr;        // DCT dictionary: FFT twiddles e^{-2 pi i m / (D/2)}, D/4 of them
@@ -641,10 +645,18 @@ void launch_dct_setup(cudaStream_t st, cofem_ctx* c);
 void launch_dct_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode);
 void launch_dct_phit_y(cudaStream_t st, cofem_ctx* c, const float* y, double scale, float* out, float* tmp);
 
+// kernels_fftconv.cu
+size_t fftconv_smem_bytes();
+cudaError_t fftconv_kernel_attributes();
+int fftconv_bout(int L);
+void launch_fftconv_setup(cudaStream_t st, cofem_ctx* c);
+void launch_fftconv_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode);
+
 // dispatch
 inline void launch_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode) {
     if (c->kind == COFEM_OP_DENSE) launch_dense_operator(s, c, Q, V, mode);
     else if (c->kind == COFEM_OP_DCT) launch_dct_operator(s, c, Q, V, mode);
+    else if (c->use_fftconv) launch_fftconv_operator(s, c, Q, V, mode);
     else launch_toeplitz_operator(s, c, Q, V, mode);
 }
 

@@ -78,8 +78,8 @@ template <> __device__ __forceinline__ float elem<uint8_t>(uint8_t v) {
 // tile is whole.  A block owns DF_BM rows of the output and all (padded) QP
 // columns for one k chunk; thread (tm, tq) keeps the rows tm + 16 a (a < 4)
 // and the columns 4 tq .. 4 tq + 3 as FP32 pairs.  Tiles of DF_KC k values
-// arrive by cp.async, double-buffered, so the copy of tile t + 1 overlaps the
-// arithmetic on tile t; the dictionary tile stays in its storage type (FP32,
+// arrive by cp.async through a three-stage ring, so the copies of the next
+// tiles overlap the arithmetic on tile t; the dictionary tile stays in its storage type (FP32,
 // BF16 or E4M3 codes) in shared memory and is widened when read.
 // ---------------------------------------------------------------------------
 constexpr int DF_BM = 64, DF_KC = 32, DF_TM = 4, DF_TQ = 4, DF_NBUF = 3;

@@ -16,45 +16,12 @@
 // place, with the input in bit-reversed order and the e^{-2 pi i m / H}
 // twiddles from a table made once per handle.
 #include "cofem_internal.cuh"
+#include "fft_smem.cuh"
 
 namespace {
 
 constexpr int DCT_THREADS = 1024;
 constexpr int DCT_MAXPT = (COFEM_DCT_MAX_D / 2) / DCT_THREADS;   // FFT points a thread gathers (16)
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
-
-// e^{i pi num / den} (den a power of two, 0 <= num < 2 den: the angle is exact)
-__device__ __forceinline__ float2 expi_pi(long long num, long long den) {
-    float sn, cs;
-    sincospif((float)num / (float)den, &sn, &cs);
-    return make_float2(cs, sn);
-}
-
-__device__ __forceinline__ int brev(int m, int logH) { return (int)(__brev((unsigned)m) >> (32 - logH)); }
-
-// In-place radix-2 FFT of the H = 2^logH points in s (bit-reversed input,
-// natural-order output); forward uses e^{-2 pi i / H}, inverse its conjugate
-// (no 1/H factor).  tw[m] = e^{-2 pi i m / H}, m < H/2.
-__device__ void fft_smem(float2* s, int logH, const float2* __restrict__ tw, bool inverse) {
-    const int H = 1 << logH;
-    for (int ls = 1; ls <= logH; ++ls) {
-        const int half = 1 << (ls - 1), step = H >> ls;
-        for (int i = threadIdx.x; i < H / 2; i += blockDim.x) {
-            const int pos = i & (half - 1);
-            const int a = ((i >> (ls - 1)) << ls) + pos, b = a + half;
-            float2 w = __ldg(tw + pos * step);
-            if (inverse) w.y = -w.y;
-            const float2 x = s[a], t = cmul(w, s[b]);
-            s[a] = make_float2(x.x + t.x, x.y + t.y);
-            s[b] = make_float2(x.x - t.x, x.y - t.y);
-        }
-        __syncthreads();
-    }
-}
 
 // y_n of the DCT-III result left in s by dct3_to_smem (natural-order z):
 // y_2a = u_a, y_{2a+1} = u_{D-1-a}, u_2m = Re z_m, u_{2m+1} = Im z_m.

@@ -80,7 +80,7 @@ def test_status_strings_and_defaults(cf):
     # the remaining defaults as the header documents them
     assert (o.precond, o.conv, o.rr_period, o.stream) == (cf.COFEM_PRECOND_JACOBI, cf.COFEM_CONV_PER_COLUMN, 0, None)
     assert (o.dense_path, o.max_sms, o.overlap_launch, o.prior) == (cf.COFEM_PATH_AUTO, 0, 1, cf.COFEM_PRIOR_GAUSSIAN)
-    assert o.check_residual == 0 and o.warm_start == 0
+    assert o.check_residual == 0 and o.warm_start == 0 and o.toeplitz_path == 0
 
 
 @pytest.mark.parametrize("args,msg", [

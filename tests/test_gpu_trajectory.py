@@ -115,11 +115,14 @@ def test_trajectory_dense_n8192_d32768_k32_bf16(cf, config4, rr_period):
         np.testing.assert_allclose(g["true_res"], r["true_res"], rtol=1e-2)
 
 
-def test_trajectory_toeplitz_d1e6_l256_k16(cf):
+@pytest.mark.parametrize("path", ["fft", "direct"])
+def test_trajectory_toeplitz_d1e6_l256_k16(cf, path):
     """The convolution workload at full size: 10^6 unknowns, 245 chunk
-    partials per column in the CG kernels; the oracle applies Phi by FFT."""
+    partials per column in the CG kernels; both operator forms (the FFT form
+    is the benchmark's); the oracle applies Phi by FFT in FP64."""
     p, run = workload("toeplitz_d1e6_l256_k16")
     K, T, maxit = run["K"], 2, 10
-    g = _gpu(cf, p, K, T, maxit, run["seed"])
+    tp = cf.COFEM_TOEPLITZ_FFT if path == "fft" else cf.COFEM_TOEPLITZ_DIRECT
+    g = _gpu(cf, p, K, T, maxit, run["seed"], toeplitz_path=tp)
     r = oracle_cofem(ToeplitzOperator(p.phi, p.N), p.y, p.beta, K, T, TOL_FIXED, maxit, run["seed"])
     _check(g, r, maxit)
