@@ -524,6 +524,8 @@ def run_ours(args):
     if fp32 is not None:
         line["fp32_form"] = fp32
         line["fp8_form"] = fp8
+    if prob.kind == "dense" and not args.no_conv_form and ws == 1:
+        line["convolution_form"] = convolution_report(cf, dev, args)
     if args.serve_requests > 0 and ws == 1:
         line["serving"] = serving_report(cf, dev, args.serve_requests, run["precision"])
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
@@ -533,6 +535,44 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def convolution_report(cf, dev, args, name="toeplitz_d1e6_l256_k16"):
+    """The convolution workload (N = D = 10^6, L = 256, K = 16, T = 30) in the
+    library's default operator form: EM-iter/s over two timed fits (after one
+    warm-up), the operator against the FP32 FMA peak, NMSE.  Its E-steps run
+    to cg_maxit (the workload does not converge within its budget), so it is a
+    throughput measurement."""
+    import torch
+    prob, run = workload(name)
+    K, T, tol, maxit = run["K"], run["T"], run["cg_tol"], run["cg_maxit"]
+    D = prob.D
+    outs = [torch.empty(D, device=dev) for _ in range(3)]
+    it = torch.empty(T, dtype=torch.int32, device=dev)
+    y = torch.from_numpy(prob.y).to(dev)
+    st = torch.cuda.Stream(device=dev)
+    with cf.CoFEM(prob.N, D, cf.COFEM_OP_TOEPLITZ, prob.phi, prob.L, seed=run["seed"], stream=st) as m:
+        cf.cofem_fit(m.h, y, prob.beta, None, K, T, tol, maxit, *outs, it)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        flags = 0
+        for _ in range(2):
+            flags |= cf.cofem_fit(m.h, y, prob.beta, None, K, T, tol, maxit, *outs, it)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / 2
+        op_ms = cf.cofem_time_operator(m.h, K + 1, 20)
+        path = cf.cofem_operator_info(m.h)[0]
+    flops = 4.0 * prob.L * D * (K + 1) if path != cf.COFEM_TOEPLITZ_FFT else _fftconv_flops(D, prob.L, K + 1)
+    peak = _fp32_peak_tflops(2070.0)
+    ach = flops / (op_ms / 1000.0) / 1e12
+    return {"workload": name, "value": T / (ms / 1000.0), "unit": "EM-iter/s", "ms_per_fit": ms,
+            "nmse_db": _nmse_db(outs[0].cpu().numpy(), prob.z), "flags": flags,
+            "cg_iters_last_fit": [int(v) for v in it.cpu().numpy()],
+            "operator": {"form": "fft" if path == cf.COFEM_TOEPLITZ_FFT else "direct", "ms_per_launch": op_ms,
+                         "achieved_tflops": ach, "peak_tflops": peak, "frac": ach / peak,
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}}
 
 
 def serving_run(cf, dev, n, precision, rate_hz=None, slots=16, budget_bytes=96 << 30, seed=1000, max_sms=0,
@@ -692,6 +732,8 @@ def _parser():
     ap.add_argument("--no-fp32-form", action="store_true")
     ap.add_argument("--no-warm-compare", action="store_true",
                     help="skip the comparison fit with warm start and probe reuse")
+    ap.add_argument("--no-conv-form", action="store_true",
+                    help="skip the convolution workload's sub-object of the default line")
     ap.add_argument("--no-rr-off", action="store_true",
                     help="skip the comparison fit without residual replacement")
     ap.add_argument("--rr-period", type=int, default=-1,

@@ -30,6 +30,8 @@
 // instead of the eleven instructions of the error-free form.
 // Convolution dictionary:
 //   k_df_conv, k_df_conv_t (direct sums over the L taps), k_df_residual.
+#include <algorithm>
+
 #include <cuda_fp8.h>
 
 #include "cofem_internal.cuh"
@@ -441,18 +443,50 @@ __global__ void k_cg_gate(DevCtl* ctl, cudaGraphConditionalHandle h_cg) {
 
 int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
-// k split of a product with M output rows and K terms: enough blocks for four
-// per SM, k chunks a whole number of shared-memory tiles (K a multiple of
-// DF_KC, so every chunk is whole tiles).
-void df_split_k(long long M, long long K, int sms, int* S, long long* kchunk) {
-    const int mb = ceil_div(M, DF_BM);
-    int s = ceil_div(4LL * sms, mb);
-    const int smax = ceil_div(K, DF_KC);
-    if (s > smax) s = smax;
-    if (s < 1) s = 1;
-    long long kc = ((K + s - 1) / s + DF_KC - 1) / DF_KC * DF_KC;
+// k split of a product with M output rows and K terms (K a multiple of
+// DF_KC, so every chunk is whole tiles): the split whose grid fills the
+// resident block slots (`capacity` = blocks per SM x SMs) in whole waves best,
+// among splits that leave at least 16 tiles per block (a partial last wave
+// runs a few blocks on an otherwise idle GPU).
+void df_split_k(long long M, long long K, long long capacity, int* S, long long* kchunk) {
+    const long long mb = ceil_div(M, DF_BM);
+    const long long tiles = ceil_div(K, DF_KC);
+    const long long smax = std::max(1LL, tiles / 16);
+    long long best = 1;
+    double best_eff = -1.0;
+    for (long long sp = 1; sp <= smax; ++sp) {
+        const long long kc = ceil_div(tiles, sp) * DF_KC;          // chunk, whole tiles
+        const long long nb = mb * ceil_div(K, kc);                   // blocks launched
+        const long long waves = ceil_div(nb, capacity);
+        const double eff = (double)nb / (double)(waves * capacity);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = sp;
+        }
+    }
+    const long long kc = ceil_div(tiles, best) * DF_KC;
     *kchunk = kc;
-    *S = ceil_div(K, kc);
+    *S = (int)ceil_div(K, kc);
+}
+
+// Resident blocks per SM of the products for QP columns (the occupancy the
+// k split is chosen for).
+template <typename E, bool TRANS>
+int df_blocks_per_sm(int QP) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_df_gemm<E, TRANS, TRANS>, 16 * (QP / DF_TQ),
+                                                      df_gemm_smem<E>(QP)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        nb = 1;
+    }
+    return nb > 0 ? nb : 1;
+}
+
+template <bool TRANS>
+int df_blocks_per_sm_of(const cofem_ctx* c, int QP) {
+    if (c->phi16) return df_blocks_per_sm<__nv_bfloat16, TRANS>(QP);
+    if (c->phi8) return df_blocks_per_sm<uint8_t, TRANS>(QP);
+    return df_blocks_per_sm<float, TRANS>(QP);
 }
 
 template <typename E>
@@ -477,8 +511,8 @@ DfSizes df_configure(cofem_ctx* c, int Q) {
     DfSizes z{};
     z.QP = (Q + DF_TQ - 1) / DF_TQ * DF_TQ;
     if (c->kind == COFEM_OP_DENSE) {
-        df_split_k(c->Np, c->Dp, c->num_sms, &z.S1, &z.k1);
-        df_split_k(c->Dp, c->Np, c->num_sms, &z.S2, &z.k2);
+        df_split_k(c->Np, c->Dp, (long long)df_blocks_per_sm_of<false>(c, z.QP) * c->num_sms, &z.S1, &z.k1);
+        df_split_k(c->Dp, c->Np, (long long)df_blocks_per_sm_of<true>(c, z.QP) * c->num_sms, &z.S2, &z.k2);
         z.t = (size_t)c->Np * z.QP;
         z.T = (size_t)z.S1 * c->Np * z.QP;
         z.U = (size_t)z.S2 * z.QP * c->Dp;
