@@ -52,6 +52,7 @@ _MEASURED_TRAFFIC = {
 # --dense-path -> cofem_opts.dense_path, --toeplitz-path -> cofem_opts.toeplitz_path
 _DENSE_PATHS = {"auto": 0, "two_pass": 1, "single_pass": 2}
 _TOEPLITZ_PATHS = {"auto": 0, "direct": 1, "fft": 2}
+_RESIDUAL_PATHS = {"auto": 0, "pairs": 1, "sliced": 2}
 
 # workload precision name -> C-ABI precision code
 _PRECISIONS = {"f32": lambda cf: cf.COFEM_F32, "bf16": lambda cf: cf.COFEM_BF16,
@@ -139,6 +140,23 @@ _SMS, _FP32_LANES = 152, 128
 # FP32 instructions per multiply-add of the error-free dot product (TwoProduct
 # through the FMA, the low part's FMA, TwoSum, the compensation adds)
 _DF_OPS_PER_MAC = 11
+_SLICED_KERNELS = 7     # kernels of one accurate residual in the sliced form
+
+
+def _sliced_roofline(N, D, Q, ms_first, hbm_gbs, peak_kind):
+    """Roofline of the sliced accurate residual's first product (digits of X
+    and the tensor-core GEMM over the three slice images of Phi~): algorithmic
+    bytes = the slice images (three bf16 digits per entry, 6 N D) plus the
+    digit image of X (5 QO bf16 per row of X, QO = Q rounded up to 16) and the
+    pair X, Xlo it is made from."""
+    QO = (Q + 15) // 16 * 16
+    alg = 6.0 * N * D + 10.0 * QO * D + 8.0 * Q * D
+    achieved = alg / (ms_first / 1000.0) / 1e9
+    return {"bound": "hbm", "kernel": "accurate residual, first product Phi~ X from exact integer slices "
+            "(k_sl_colexp + k_sl_digits + k_sl_gemm)", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s",
+            "frac": achieved / hbm_gbs, "traffic": None, "peak_source": peak_kind, "ms_per_launch": ms_first,
+            "algorithmic_bytes_per_launch": alg,
+            "tensor_flop_per_launch": 2.0 * (5 + 4 + 3) * QO * N * D}
 
 
 _FFT_F = 8192   # overlap-save block of the FFT convolution
@@ -341,6 +359,7 @@ def run_ours(args):
                         toeplitz_path=_TOEPLITZ_PATHS[args.toeplitz_path],
                         seed=run["seed"], stream=stream, use_graph=0 if args.no_graph else 1,
                         dense_path=_DENSE_PATHS[args.dense_path], overlap_launch=0 if args.no_overlap else 1,
+                        residual_path=_RESIDUAL_PATHS[args.residual_path],
                         prior=cf.COFEM_PRIOR_RECTIFIED if args.prior == "rectified" else cf.COFEM_PRIOR_GAUSSIAN)
 
     def timed_fits(model, steps, warmup):
@@ -410,25 +429,30 @@ def run_ours(args):
         roof = {"bound": "alu", "kernel": "convolution operator (k_toeplitz)"}
     traffic = _MEASURED_TRAFFIC.get((name, path)) if prob.kind == "dense" else None
     roof = _roofline(roof, op_ms, alg_bytes, alg_flops, traffic, hbm_gbs, peak_kind, clk)
-    # the precision form: the accurate residual's first product (Phi~ X in FP32
-    # pairs, CUDA cores) against the FP32 instruction rate; whichever of it and
-    # the CG operator takes more of the fit is the dominant kernel
+    # the precision form: the accurate residual's first product (FP32 pairs on
+    # the CUDA cores against the FP32 instruction rate, or the sliced tensor-core
+    # product against the HBM copy rate); whichever of it and the CG operator
+    # takes more of the fit is the dominant kernel
     roof_df = None
     if run["rr_period"] > 0 and prob.kind == "dense":
         ms_res, ms_first = cf.cofem_time_true_residual(model.h, Q, 5)
         n_rr, n_check = fit_stats[-1]
-        sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
-        ops = _DF_OPS_PER_MAC * float(N) * D * Q
-        peak_ops = _SMS * _FP32_LANES * float(sm_mhz) * 1e6 / 1e12
-        achieved = ops / (ms_first / 1000.0) / 1e12
-        roof_df = {"bound": "alu", "kernel": "accurate residual, first product Phi~ X in FP32 pairs (k_df_gemm)",
-                   "achieved": achieved, "peak": peak_ops, "unit": "T FP32-op/s", "frac": achieved / peak_ops,
-                   "traffic": None, "peak_source": f"derived: {_SMS} SMs x {_FP32_LANES} FP32 lanes x 1 op "
-                   f"x {sm_mhz:.0f} MHz", "ms_per_launch": ms_first, "ms_per_accurate_residual": ms_res,
-                   "algorithmic_ops_per_launch": ops,
-                   "per_fit_ms": {"accurate_residuals": ms_res * (n_rr + n_check),
-                                  "cg_operator": op_ms * float(np.sum(all_iters[-1]))}}
-        if roof_df["per_fit_ms"]["accurate_residuals"] > roof_df["per_fit_ms"]["cg_operator"]:
+        per_fit = {"accurate_residuals": ms_res * (n_rr + n_check),
+                   "cg_operator": op_ms * float(np.sum(all_iters[-1]))}
+        if op_rr == _SLICED_KERNELS:
+            roof_df = _sliced_roofline(N, D, Q, ms_first, hbm_gbs, peak_kind)
+        else:
+            sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+            ops = _DF_OPS_PER_MAC * float(N) * D * Q
+            peak_ops = _SMS * _FP32_LANES * float(sm_mhz) * 1e6 / 1e12
+            achieved = ops / (ms_first / 1000.0) / 1e12
+            roof_df = {"bound": "alu", "kernel": "accurate residual, first product Phi~ X in FP32 pairs (k_df_gemm)",
+                       "achieved": achieved, "peak": peak_ops, "unit": "T FP32-op/s", "frac": achieved / peak_ops,
+                       "traffic": None, "peak_source": f"derived: {_SMS} SMs x {_FP32_LANES} FP32 lanes x 1 op "
+                       f"x {sm_mhz:.0f} MHz", "ms_per_launch": ms_first, "algorithmic_ops_per_launch": ops}
+        roof_df["ms_per_accurate_residual"] = ms_res
+        roof_df["per_fit_ms"] = per_fit
+        if per_fit["accurate_residuals"] > per_fit["cg_operator"]:
             roof, roof_df = roof_df, roof
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -751,6 +775,8 @@ def _parser():
                     help="BF16 dense operator form (default: the library's choice)")
     ap.add_argument("--toeplitz-path", default="auto", choices=sorted(_TOEPLITZ_PATHS),
                     help="convolution operator form (default: the library's choice)")
+    ap.add_argument("--residual-path", default="auto", choices=sorted(_RESIDUAL_PATHS),
+                    help="accurate residual form of the precision form (default: the library's choice)")
     ap.add_argument("--em-iters", type=int, default=0,
                     help="override T (profiling runs only; the benchmark line uses the workload's T)")
     ap.add_argument("--no-graph", action="store_true",

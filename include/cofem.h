@@ -110,8 +110,8 @@ typedef struct cofem_opts {
     int precond;              /* COFEM_PRECOND_JACOBI | COFEM_PRECOND_ONE */
     int conv;                 /* COFEM_CONV_PER_COLUMN | COFEM_CONV_FROBENIUS */
     int rr_period;            /* precision form (0 = off): every rr_period CG iterations the
-                                 active columns take R <- B - A X computed accurately (FP32
-                                 pairs, about 2^-48 relative, see cofem_true_residuals),
+                                 active columns take R <- B - A X computed accurately (see
+                                 residual_path and cofem_true_residuals),
                                  with X held as an exact FP32 pair; and when the CG loop
                                  ends, every column's true residual is checked against
                                  cg_tol: a column that misses it restarts from that
@@ -154,7 +154,28 @@ typedef struct cofem_opts {
                                  output) or COFEM_TOEPLITZ_FFT (overlap-save FFTs of 8192
                                  points in shared memory, O(log F) per output, the paper's
                                  method for this dictionary, Sec. VI-A) */
+    int residual_path;        /* how the precision form computes its accurate residual
+                                 B - A X (rr_period > 0 or check_residual = 1):
+                                 COFEM_RESIDUAL_AUTO (default: SLICED where it applies,
+                                 else FP32_PAIRS), COFEM_RESIDUAL_FP32_PAIRS or
+                                 COFEM_RESIDUAL_SLICED (see below) */
 } cofem_opts;
+
+/* Accurate residual forms (the precision form's B - A X; not in the paper).
+ * FP32_PAIRS: X as the FP32 pair X + Xlo, A X with compensated FP32-pair
+ * products on the CUDA cores (TwoProduct and TwoSum, about 2^-48 relative
+ * error), every dictionary kind.  SLICED: BF16 dense dictionaries with
+ * K + 1 <= 48 and N, D <= 40960: both products of A X = beta Phi~^T (Phi~ X)
+ * + alpha X from exact integer slices on the tensor cores (each dictionary
+ * entry as three signed 8-bit digits relative to a power of two per
+ * dictionary row, or per column for Phi~^T; each entry of X and of Phi~ X as
+ * five relative to a power of two per column; digit products summed exactly
+ * in integers), relative error about 2^-38 of sum_k |Phi~_ik| |x_k| per
+ * product.  Requesting SLICED where it does not apply makes the first fit
+ * fail with COFEM_ERR_UNSUPPORTED. */
+#define COFEM_RESIDUAL_AUTO       0
+#define COFEM_RESIDUAL_FP32_PAIRS 1
+#define COFEM_RESIDUAL_SLICED     2
 
 #define COFEM_TOEPLITZ_AUTO   0
 #define COFEM_TOEPLITZ_DIRECT 1
@@ -176,7 +197,8 @@ typedef struct cofem_opts {
 
 /* Fill *o with the defaults: F32, Jacobi, per-column, rr_period 0,
  * alpha_max 1e12, seed 2, stream NULL, use_graph 1, dense_path AUTO, max_sms 0,
- * overlap_launch 1, prior GAUSSIAN, check_residual 0, warm_start 0, toeplitz_path AUTO. */
+ * overlap_launch 1, prior GAUSSIAN, check_residual 0, warm_start 0, toeplitz_path AUTO,
+ * residual_path AUTO. */
 void cofem_default_opts(cofem_opts* o);
 
 /* Create a handle for one dictionary (step a0: upload, optional BF16
@@ -385,11 +407,23 @@ cofem_status cofem_apply_dense_noalloc(const float* phi, long long N, long long 
  * launch configuration a fit uses, on the handle's current X, bracketed by
  * CUDA events on the handle's stream: *ms_residual = mean time of one whole
  * accurate residual (all its kernels), *ms_first = mean time of its first
- * product Phi~ X in FP32 pairs (dense dictionaries; 0 otherwise).  Either
+ * product Phi~ X (with the digits of X in the SLICED form; dense
+ * dictionaries; 0 otherwise).  Either
  * pointer may be NULL (not both).  Requires a previous fit with the same Q on
  * a handle with rr_period > 0 or check_residual = 1.  Errors: INVALID_ARG,
  * CUDA. */
 cofem_status cofem_time_true_residual(struct cofem_ctx* h, int Q, int reps, double* ms_residual, double* ms_first);
+
+/* The accurate product of the precision form alone (row a6): out = Phi~^T
+ * (Phi~ (Xh + Xl)) in FP64 for a block of Q vectors, by the handle's accurate
+ * residual form (opts.residual_path; beta and alpha are left out), on the
+ * dictionary the handle computes with.  Xh, Xl: Q x D floats row-major (the
+ * FP32 pair of each vector); out: Q x D doubles; all three host or device
+ * pointers of the handle's device.  1 <= Q <= 64 (SLICED: Q <= 48).  Dense
+ * dictionaries on a handle with rr_period > 0 or check_residual = 1.
+ * Errors: INVALID_ARG (NULL, Q, kind, options), NONFINITE (Xh or Xl), NOMEM,
+ * UNSUPPORTED, CUDA. */
+cofem_status cofem_accurate_product(struct cofem_ctx* h, const float* Xh, const float* Xl, int Q, double* out);
 
 /* Failure-detection self-test: runs the library's two bounded on-device wait
  * routines (the grid-counter wait of the single-pass operator, bounded by
@@ -430,8 +464,8 @@ cofem_status cofem_operator_info(struct cofem_ctx* h, int* path, int* kernels_cg
  * for EM iteration t (0-based) and column q (0 = mu), with A = beta Phi~^T Phi~
  * + diag(alpha^(t)) on the dictionary the handle computes with, measured on the
  * GPU when the E-step's CG loop ended (after the last restart): A X from the
- * FP32 pair X + Xlo with compensated FP32-pair products (TwoProduct and
- * TwoSum, about 2^-48 relative error) and FP64 partial sums.  0 for a zero
+ * FP32 pair X + Xlo by the handle's accurate residual form (opts.residual_path)
+ * and FP64 partial sums.  0 for a zero
  * right-hand side.  out: host, T_em * (K+1) doubles of the last cofem_fit.
  * Errors: INVALID_ARG (NULL, no fit yet, or a handle with rr_period = 0 and
  * check_residual = 0), CUDA. */

@@ -45,6 +45,9 @@ COFEM_TOEPLITZ_DIRECT = 1
 COFEM_TOEPLITZ_FFT = 2
 COFEM_PRIOR_GAUSSIAN = 0
 COFEM_PRIOR_RECTIFIED = 1
+COFEM_RESIDUAL_AUTO = 0
+COFEM_RESIDUAL_FP32_PAIRS = 1
+COFEM_RESIDUAL_SLICED = 2
 COFEM_FLAG_CG_NOT_CONVERGED = 1
 COFEM_FLAG_ALPHA_CLAMPED = 2
 COFEM_FLAG_BREAKDOWN = 4
@@ -68,6 +71,7 @@ class cofem_opts(C.Structure):
         ("check_residual", C.c_int),
         ("warm_start", C.c_int),
         ("toeplitz_path", C.c_int),
+        ("residual_path", C.c_int),
     ]
 
 
@@ -121,6 +125,7 @@ def _load():
         "cofem_fit_stats": (i, [vp, C.POINTER(i), C.POINTER(i)]),
         "cofem_selftest_bounded_wait": (i, [d, C.POINTER(C.c_uint)]),
         "cofem_time_true_residual": (i, [vp, i, i, C.POINTER(d), C.POINTER(d)]),
+        "cofem_accurate_product": (i, [vp, vp, vp, i, vp]),
         "cofem_time_operator": (i, [vp, i, i, C.POINTER(d)]),
         "cofem_apply_dense_noalloc": (i, [vp, ll, ll, ll, vp, i, vp, d, vp, vp]),
         "cofem_estimate_bytes": (ll, [i, ll, ll, ll, i, i]),
@@ -313,8 +318,14 @@ def cofem_true_residuals(h: int, T_em: int, K: int) -> np.ndarray:
     return out
 
 
+def cofem_accurate_product(h: int, Xh, Xl, Q: int, out) -> None:
+    """out (Q x D float64) = Phi~^T Phi~ (Xh + Xl) by the handle's accurate
+    residual form; Xh, Xl are Q x D float32 (host or device)."""
+    _check(lib.cofem_accurate_product(h, _ptr(Xh), _ptr(Xl), int(Q), _ptr(out, np.float64)))
+
+
 def cofem_time_true_residual(h: int, Q: int, reps: int) -> tuple[float, float]:
-    """(ms per accurate residual, ms per first product Phi~ X in FP32 pairs)."""
+    """(ms per accurate residual, ms per first product Phi~ X)."""
     a, b = C.c_double(0.0), C.c_double(0.0)
     _check(lib.cofem_time_true_residual(h, Q, reps, C.byref(a), C.byref(b)))
     return a.value, b.value

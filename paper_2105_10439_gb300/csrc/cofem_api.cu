@@ -118,6 +118,7 @@ WsSizes ws_sizes(cofem_ctx* c, int Qcap) {
 bool precise(const cofem_ctx* c) { return c->opts.rr_period > 0 || c->opts.check_residual != 0; }
 
 void free_precise(cofem_ctx* c) {
+    sl_release(c);
     if (!c->Xlo) return;
     const DfSizes z = df_configure(c, c->Qcap);
     dfree(c, &c->Xlo, (size_t)c->Qcap * c->Dp);
@@ -193,6 +194,19 @@ cofem_status ensure_workspace(cofem_ctx* c, int Q) {
                 return fail(COFEM_ERR_UNSUPPORTED,
                             "the single-pass dense operator needs BF16, 3(K+1) <= 112 and D <= 256 x SMs");
             return cuda_fail(e, "tensor-core operator set-up");
+        }
+    }
+    if (precise(c)) {
+        if (sl_applies(c, Q)) {
+            cudaError_t e = sl_setup(c, Q);
+            if (e != cudaSuccess) {
+                free_workspace(c);
+                return cuda_fail(e, "sliced accurate residual set-up");
+            }
+        } else if (c->opts.residual_path == COFEM_RESIDUAL_SLICED) {
+            free_workspace(c);
+            return fail(COFEM_ERR_UNSUPPORTED,
+                        "the sliced accurate residual needs a BF16 dense dictionary, K + 1 <= 48 and N, D <= 40960");
         }
     }
     CK(cudaMemsetAsync(c->counters, 0, w.counters * sizeof(unsigned), c->stream));
@@ -353,6 +367,7 @@ cofem_status set_kernel_attributes(int dev) {
     CK(dct_kernel_attributes());
     CK(fftconv_kernel_attributes());
     CK(df_kernel_attributes());
+    CK(sl_kernel_attributes(optin));
     g_attr_done[dev] = true;
     return COFEM_OK;
 }
@@ -466,6 +481,8 @@ static cofem_status create_impl(cofem_ctx** out, long long N, long long D, int k
     if (o.check_residual != 0 && o.check_residual != 1)
         return fail(COFEM_ERR_INVALID_ARG, "check_residual must be 0 or 1");
     if (o.warm_start != 0 && o.warm_start != 1) return fail(COFEM_ERR_INVALID_ARG, "warm_start must be 0 or 1");
+    if (o.residual_path < COFEM_RESIDUAL_AUTO || o.residual_path > COFEM_RESIDUAL_SLICED)
+        return fail(COFEM_ERR_INVALID_ARG, "residual_path must be AUTO, FP32_PAIRS or SLICED");
     if (o.overlap_launch != 0 && o.overlap_launch != 1) return fail(COFEM_ERR_INVALID_ARG, "overlap_launch must be 0 or 1");
     if (o.prior != COFEM_PRIOR_GAUSSIAN && o.prior != COFEM_PRIOR_RECTIFIED)
         return fail(COFEM_ERR_INVALID_ARG, "prior must be COFEM_PRIOR_GAUSSIAN or COFEM_PRIOR_RECTIFIED");
@@ -921,6 +938,53 @@ cofem_status cofem_time_true_residual(cofem_ctx* c, int Q, int reps, double* ms_
     if (s.err) return cuda_fail(s.err, "accurate residual launch");
     if (ms_residual) *ms_residual = (double)a / reps;
     if (ms_first) *ms_first = c->kind == COFEM_OP_DENSE ? (double)b / reps : 0.0;
+    return COFEM_OK;
+}
+
+cofem_status cofem_accurate_product(cofem_ctx* c, const float* Xh, const float* Xl, int Q, double* out) {
+    g_err[0] = 0;
+    if (!c || !Xh || !Xl || !out) return fail(COFEM_ERR_INVALID_ARG, "NULL argument");
+    if (Q < 1 || Q > COFEM_QMAX) return fail(COFEM_ERR_INVALID_ARG, "need 1 <= Q <= %d", COFEM_QMAX);
+    if (c->kind != COFEM_OP_DENSE) return fail(COFEM_ERR_INVALID_ARG, "the accurate product is built for dense dictionaries");
+    if (!precise(c)) return fail(COFEM_ERR_INVALID_ARG, "the handle has neither rr_period > 0 nor check_residual = 1");
+    CK(cudaSetDevice(c->device));
+    for (const void* ptr : {(const void*)Xh, (const void*)Xl, (const void*)out}) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+            cudaGetLastError();
+        } else if (a.type == cudaMemoryTypeDevice && a.device != c->device) {
+            return fail(COFEM_ERR_INVALID_ARG, "device memory of another device than the handle's (%d)", c->device);
+        }
+    }
+    cofem_status st = ensure_workspace(c, Q);
+    if (st) return st;
+    // the pair into the padded X, Xlo blocks (padding stays zero)
+    CK(cudaMemsetAsync(c->X, 0, (size_t)Q * c->Dp * sizeof(float), c->stream));
+    CK(cudaMemsetAsync(c->Xlo, 0, (size_t)Q * c->Dp * sizeof(float), c->stream));
+    CK(cudaMemcpy2DAsync(c->X, c->Dp * sizeof(float), Xh, c->D * sizeof(float), c->D * sizeof(float), Q,
+                         cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpy2DAsync(c->Xlo, c->Dp * sizeof(float), Xl, c->D * sizeof(float), c->D * sizeof(float), Q,
+                         cudaMemcpyDefault, c->stream));
+    if ((st = check_finite_dev(c, c->X, (long long)Q * c->Dp, "Xh"))) return st;
+    if ((st = check_finite_dev(c, c->Xlo, (long long)Q * c->Dp, "Xl"))) return st;
+    double* dout = nullptr;
+    if ((st = dalloc(c, &dout, (size_t)Q * c->D))) return st;
+    DevCtl* hc = c->ctl_host;
+    memset(hc, 0, sizeof(DevCtl));
+    hc->Q = Q;
+    CK(cudaMemcpyAsync(c->ctl, hc, sizeof(DevCtl), cudaMemcpyHostToDevice, c->stream));
+    Sink s;
+    s.stream = c->stream;
+    launch_df_gram(s, c, Q, dout);
+    cudaError_t e = s.err;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, dout, (size_t)Q * c->D * sizeof(double), cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dfree(c, &dout, (size_t)Q * c->D);
+    if (e != cudaSuccess) return cuda_fail(e, "accurate product");
+    if (hc->flags & COFEM_FLAG_DEVICE_TIMEOUT)
+        return fail(COFEM_ERR_CUDA, "a bounded on-device wait timed out (tensor-core pipeline)");
     return COFEM_OK;
 }
 

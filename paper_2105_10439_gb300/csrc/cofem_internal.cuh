@@ -108,6 +108,17 @@ __device__ __forceinline__ float probe_sign_from_word(uint64_t word, long long j
     return ((word >> (j & 63)) & 1ull) ? -1.0f : 1.0f;
 }
 
+// Right-hand side B[j][q] of the accurate residual: b of the column's task
+// (k = 0) or its probe k of EM iteration t (of t = 1 under the warm start).
+__device__ __forceinline__ double accurate_rhs(const DevCtl* ctl, const float* b, int q, long long j, long long D,
+                                               long long Dp) {
+    int task, k;
+    column_task(ctl, q, task, k);
+    if (k == 0) return (double)b[(size_t)task * Dp + j];
+    if (j >= D) return 0.0;
+    return (double)probe_sign_from_word(probe_word(ctl->seed, ctl->warm ? 1 : ctl->t, k, j, task), j);
+}
+
 // ---------------------------------------------------------------------------
 // Reductions.  GB300 runs FP64 at a small fraction of the FP32 rate, so the
 // per-element work of every inner product stays in FP32 and only the
@@ -563,6 +574,7 @@ struct cofem_ctx {
     int last_T = 0, last_Q = 0;      // EM iterations and columns of the last fit
     int last_rr = 0, last_check = 0; // residual replacements and checks of the last fit
     long long df_k1 = 0, df_k2 = 0;
+    void* sl = nullptr;              // tensor-core form of the accurate residual (kernels_sliced.cu)
     int* iters_dev = nullptr;        // T_em
     int iters_cap = 0;
     DevCtl* ctl = nullptr;
@@ -614,6 +626,18 @@ cudaError_t df_kernel_attributes();
 void launch_df_first_product(Sink& s, cofem_ctx* c, int Q);   // dense only
 void launch_df_check(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_vf);
 void launch_cg_gate(Sink& s, cofem_ctx* c, cudaGraphConditionalHandle h_cg);
+void launch_df_gram(Sink& s, cofem_ctx* c, int Q, double* out);   // Phi~^T Phi~ (X + Xlo), dense
+
+// kernels_sliced.cu (precision form, BF16 dictionary: the accurate residual
+// from exact integer slices on the tensor cores)
+bool sl_applies(const cofem_ctx* c, int Q);
+cudaError_t sl_setup(cofem_ctx* c, int Q);
+void sl_release(cofem_ctx* c);
+cudaError_t sl_kernel_attributes(int max_smem);
+int sl_kernels();
+void launch_sl_first_product(Sink& s, cofem_ctx* c, int Q);
+void launch_sl_residual(Sink& s, cofem_ctx* c, int Q, int mode);
+void launch_sl_gram(Sink& s, cofem_ctx* c, int Q, double* out);
 
 // kernels_dense.cu
 void dense_configure(cofem_ctx* c, int Q);

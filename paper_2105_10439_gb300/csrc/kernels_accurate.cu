@@ -286,17 +286,6 @@ __global__ void k_df_conv_t(const float* __restrict__ h, int L, long long N, lon
     U[(size_t)q * Dp + j] = j < N ? (double)S + (double)C : 0.0;
 }
 
-// Right-hand side B[j][q]: b of the column's task (k = 0) or its probe k of
-// EM iteration t.
-__device__ __forceinline__ double rhs(const DevCtl* ctl, const float* b, int q, long long j, long long D,
-                                      long long Dp) {
-    int task, k;
-    column_task(ctl, q, task, k);
-    if (k == 0) return (double)b[(size_t)task * Dp + j];
-    if (j >= D) return 0.0;
-    return (double)probe_sign_from_word(probe_word(ctl->seed, ctl->warm ? 1 : ctl->t, k, j, task), j);
-}
-
 // R = B - beta U - alpha (X + Xlo) in FP64 for column q (block (ch, q)), with
 // U = sum_s Upart[s][q][j].  mode DF_RR (residual replacement): active columns
 // take R, and the partials of ||r||^2 and r^T M^-1 r go where the direction
@@ -323,7 +312,7 @@ __global__ __launch_bounds__(NT) void k_df_residual(DevCtl* ctl, int mode, const
                 double u = 0.0;
                 for (int s = 0; s < S; ++s) u += Upart[(size_t)s * sstride + off + j];
                 const double x = (double)X[off + j] + (double)Xlo[off + j];
-                r = rhs(ctl, b, q, j, D, Dp) - beta * u - (double)alpha[j] * x;
+                r = accurate_rhs(ctl, b, q, j, D, Dp) - beta * u - (double)alpha[j] * x;
             }
             Rout[off + j] = (float)r;
             rr += r * r;
@@ -336,6 +325,17 @@ __global__ __launch_bounds__(NT) void k_df_residual(DevCtl* ctl, int mode, const
         part[(size_t)(0 * Q + q) * nch + ch] = rr;
         if (mode == DF_RR) part[(size_t)(1 * Q + q) * nch + ch] = rz;
     }
+}
+
+// out[q][j] = (Phi~^T Phi~ (X + Xlo))_jq = sum_s Upart[s][q][j] in FP64, j < D.
+__global__ void k_df_gram_out(const double* __restrict__ Upart, int S, size_t sstride, long long D, long long Dp,
+                              double* __restrict__ out) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = blockIdx.y;
+    if (j >= D) return;
+    double u = 0.0;
+    for (int s = 0; s < S; ++s) u += Upart[(size_t)s * sstride + (size_t)q * Dp + j];
+    out[(size_t)q * D + j] = u;
 }
 
 // ---------------------------------------------------------------------------
@@ -528,6 +528,10 @@ DfSizes df_configure(cofem_ctx* c, int Q) {
 // The first product alone (Phi~ X in FP32 pairs; the dominant kernel of the
 // accurate residual), for timing.
 void launch_df_first_product(Sink& s, cofem_ctx* c, int Q) {
+    if (c->sl) {
+        launch_sl_first_product(s, c, Q);
+        return;
+    }
     const int QP = c->df_QP;
     const dim3 blk(16 * (QP / DF_TQ));
 #define DF_FIRST(E, ptr)                                                                                         \
@@ -542,6 +546,10 @@ void launch_df_first_product(Sink& s, cofem_ctx* c, int Q) {
 // R_out = B - A (X + Xlo) for the active columns (DF_RR, into R) or for every
 // column (DF_CHECK, into Rt), with the norm partials the next kernel reads.
 void launch_true_residual(Sink& s, cofem_ctx* c, int Q, int mode) {
+    if (c->sl) {
+        launch_sl_residual(s, c, Q, mode);
+        return;
+    }
     if (c->kind == COFEM_OP_DENSE) {
         if (c->phi16) launch_df_dense<__nv_bfloat16>(s, c, Q, c->phi16);
         else if (c->phi8) launch_df_dense<uint8_t>(s, c, Q, c->phi8);
@@ -554,6 +562,20 @@ void launch_true_residual(Sink& s, cofem_ctx* c, int Q, int mode) {
     const size_t sstride = (size_t)c->df_QP * c->Dp;
     s.launch(k_df_residual, dim3(c->nch, Q), dim3(NT), 0, c->ctl, mode, c->b, c->X, c->Xlo, c->df_U, c->df_S2,
              sstride, c->alpha, c->minv, mode == DF_RR ? c->R : c->Rt, c->D, c->Dp, c->nch, c->part);
+}
+
+// The accurate product alone (dense dictionary): out = Phi~^T Phi~ (X + Xlo)
+// in FP64, Q x D, by the handle's accurate-residual form.
+void launch_df_gram(Sink& s, cofem_ctx* c, int Q, double* out) {
+    if (c->sl) {
+        launch_sl_gram(s, c, Q, out);
+        return;
+    }
+    if (c->phi16) launch_df_dense<__nv_bfloat16>(s, c, Q, c->phi16);
+    else if (c->phi8) launch_df_dense<uint8_t>(s, c, Q, c->phi8);
+    else launch_df_dense<float>(s, c, Q, c->phi32);
+    s.launch(k_df_gram_out, dim3((unsigned)ceil_div(c->D, 256), Q), dim3(256), 0, c->df_U, c->df_S2,
+             (size_t)c->df_QP * c->Dp, c->D, c->Dp, out);
 }
 
 cudaError_t df_kernel_attributes() {
@@ -570,6 +592,7 @@ cudaError_t df_kernel_attributes() {
 }
 
 int true_residual_kernels(cofem_ctx* c) {
+    if (c->sl) return sl_kernels();
     return c->kind == COFEM_OP_DENSE ? 4 : (c->kind == COFEM_OP_TOEPLITZ ? 3 : 0);   // not built for the DCT
 }
 

@@ -81,6 +81,7 @@ def test_status_strings_and_defaults(cf):
     assert (o.precond, o.conv, o.rr_period, o.stream) == (cf.COFEM_PRECOND_JACOBI, cf.COFEM_CONV_PER_COLUMN, 0, None)
     assert (o.dense_path, o.max_sms, o.overlap_launch, o.prior) == (cf.COFEM_PATH_AUTO, 0, 1, cf.COFEM_PRIOR_GAUSSIAN)
     assert o.check_residual == 0 and o.warm_start == 0 and o.toeplitz_path == 0
+    assert o.residual_path == cf.COFEM_RESIDUAL_AUTO
 
 
 @pytest.mark.parametrize("args,msg", [
@@ -103,7 +104,7 @@ def test_create_rejects_bad_arguments_without_gpu(cf, args, msg):
 def test_create_rejects_bad_opts(cf):
     for kw in (dict(precision=9), dict(precond=4), dict(conv=3), dict(rr_period=-1), dict(alpha_max=-1.0),
                dict(max_sms=-1), dict(dense_path=7), dict(overlap_launch=2), dict(prior=5),
-               dict(check_residual=2), dict(warm_start=3)):
+               dict(check_residual=2), dict(warm_start=3), dict(residual_path=3), dict(residual_path=-1)):
         with pytest.raises(cf.CofemError) as e:
             cf.cofem_create(4, 4, 0, np.zeros(16, np.float32), 0, cf.default_opts(**kw))
         assert e.value.status == cf.COFEM_ERR_INVALID_ARG
@@ -117,6 +118,10 @@ def test_null_handle_calls(cf):
     cf.cofem_destroy(None)   # accepted
     with pytest.raises(cf.CofemError) as e:
         cf.cofem_true_residuals(None, 2, 3)
+    assert e.value.status == cf.COFEM_ERR_INVALID_ARG
+    x = np.zeros((2, 4), np.float32)
+    with pytest.raises(cf.CofemError) as e:
+        cf.cofem_accurate_product(None, x, x, 2, np.zeros((2, 4), np.float64))
     assert e.value.status == cf.COFEM_ERR_INVALID_ARG
 
 
