@@ -203,6 +203,12 @@ WORKLOADS = {
     "dense_n8192_d32768_k32_bf16": dict(
         kind="dense", N=8192, D=32768, d=327, snr_db=30.0, K=32, T=30,
         cg_tol=1e-5, cg_maxit=400, precision="bf16", rr_period=20),
+    # the precision form at a quarter of the size (Phi~ 128 MiB, its slice
+    # images 384 MiB each: larger than L2, a few GB on the device in all), for
+    # profiler captures of the same kernels
+    "dense_n4096_d16384_k32_bf16": dict(
+        kind="dense", N=4096, D=16384, d=164, snr_db=30.0, K=32, T=30,
+        cg_tol=1e-5, cg_maxit=400, precision="bf16", rr_period=20),
     "dense_n8192_d32768_k32_f32": dict(
         kind="dense", N=8192, D=32768, d=327, snr_db=30.0, K=32, T=30,
         cg_tol=1e-5, cg_maxit=400, precision="f32", rr_period=0),
