@@ -354,8 +354,32 @@ long long cofem_estimate_bytes(int kind, long long N, long long D, long long L, 
 /* Start a server with max_slots workers (1..256) and an HBM budget in bytes. */
 cofem_status cofem_server_create(cofem_server** out, long long hbm_budget_bytes, int max_slots);
 
+/* Start a server in packed mode: the CG steps of all admitted fits run in
+ * shared launches (instead of one fit per stream).  prep_threads (1..64)
+ * threads create each request's handle and run its prologue (dictionary
+ * copies and images, b = beta Phi^T y, the first E-step's initialisation);
+ * an engine thread then runs one CUDA graph per set of admitted fits whose
+ * WHILE node repeats a step on the device: one launch of a tensor-core GEMM
+ * applies Phi (then Phi^T) to the direction blocks of every fit (each fit's
+ * work cut into fixed segments, the segments of all fits spread over the
+ * SMs), and one launch each of the T reduction, the CG update, the stopping
+ * test and direction, the M-step (fits whose CG loop ended) and the next
+ * E-step's initialisation serve every fit.  The loop returns to the host
+ * when a fit finishes, new fits are ready to join, or after 4096 steps.
+ * Every fit keeps alpha, mu and its CG state on the device; a fit's
+ * arithmetic does not depend on the others, so a request gives the same bits
+ * alone and among any others (within the tolerances of the tests, the same
+ * results as cofem_fit, whose GEMM splits its work differently).
+ * Requests: dense dictionaries, precision COFEM_BF16 or COFEM_F32_TF32X3,
+ * rr_period 0, BF16 with K <= 41 (else cofem_submit returns UNSUPPORTED).
+ * At most max_fits (1..1024) fits are prepared or in the step at once; the
+ * HBM budget bounds them too.  Same submit / poll / wait / destroy calls. */
+cofem_status cofem_server_create_packed(cofem_server** out, long long hbm_budget_bytes, int max_fits,
+                                        int prep_threads);
+
 /* Queue a request (never blocks on the GPU).  *ticket identifies it.  Errors:
- * INVALID_ARG (incomplete request), NOMEM (needs more than the whole budget). */
+ * INVALID_ARG (incomplete request), NOMEM (needs more than the whole budget),
+ * UNSUPPORTED (a packed server and a request it does not take). */
 cofem_status cofem_submit(cofem_server* srv, const cofem_request* req, unsigned long long* ticket);
 
 /* *done = 1 once the request's outputs are written. NOT_FOUND for an unknown ticket. */

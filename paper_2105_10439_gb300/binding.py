@@ -130,6 +130,7 @@ def _load():
         "cofem_apply_dense_noalloc": (i, [vp, ll, ll, ll, vp, i, vp, d, vp, vp]),
         "cofem_estimate_bytes": (ll, [i, ll, ll, ll, i, i]),
         "cofem_server_create": (i, [C.POINTER(vp), ll, i]),
+        "cofem_server_create_packed": (i, [C.POINTER(vp), ll, i, i]),
         "cofem_submit": (i, [vp, C.POINTER(cofem_request), C.POINTER(C.c_ulonglong)]),
         "cofem_poll": (i, [vp, C.c_ulonglong, C.POINTER(i)]),
         "cofem_wait": (i, [vp, C.c_ulonglong, C.POINTER(cofem_result)]),
@@ -257,6 +258,12 @@ def cofem_estimate_bytes(kind: int, N: int, D: int, L: int, precision: int, K: i
 def cofem_server_create(hbm_budget_bytes: int, max_slots: int) -> int:
     h = C.c_void_p()
     _check(lib.cofem_server_create(C.byref(h), int(hbm_budget_bytes), int(max_slots)))
+    return h.value
+
+
+def cofem_server_create_packed(hbm_budget_bytes: int, max_fits: int, prep_threads: int = 4) -> int:
+    h = C.c_void_p()
+    _check(lib.cofem_server_create_packed(C.byref(h), int(hbm_budget_bytes), int(max_fits), int(prep_threads)))
     return h.value
 
 

@@ -703,13 +703,10 @@ static cofem_status stage_y_and_b(cofem_ctx* c, const float* Y, double beta, int
     return COFEM_OK;
 }
 
-// One fit of L tasks sharing the dictionary and alpha (L = 1: Alg. 1 as
-// printed; L > 1: the multi-task CoFEM of Sec. III with the L (K+1) columns
-// in one batched PCG).
-static cofem_status fit_impl(cofem_ctx* c, int L, const float* Y, double beta, const float* alpha0, int K,
-                             int T_em, double cg_tol, int cg_maxit, float* mu, float* s, float* alpha,
-                             int* cg_iters, unsigned* flags) {
-    g_err[0] = 0;
+// Arguments, workspace, control block, b = beta Phi^T y and alpha^(1) of a
+// fit of L tasks (everything before the E-steps).
+static cofem_status fit_begin(cofem_ctx* c, int L, const float* Y, double beta, const float* alpha0, int K,
+                              int T_em, double cg_tol, int cg_maxit, float* mu, float* s, float* alpha) {
     if (!c) return fail(COFEM_ERR_INVALID_ARG, "handle is NULL");
     if (!Y || !mu || !s || !alpha) return fail(COFEM_ERR_INVALID_ARG, "y, mu, s and alpha are required");
     if (L < 1) return fail(COFEM_ERR_INVALID_ARG, "need L >= 1");
@@ -761,20 +758,13 @@ static cofem_status fit_impl(cofem_ctx* c, int L, const float* Y, double beta, c
         CK(cudaMemcpyAsync(c->alpha, ones.data(), c->D * sizeof(float), cudaMemcpyHostToDevice, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     }
-    if (c->opts.use_graph) {
-        if (c->graph_Q != Q || c->graph_L != L || !c->gexec) {
-            // programmatic edges where the driver takes them, else plain ones
-            const bool pdl = c->opts.overlap_launch != 0;
-            if (!pdl || build_graph(c, Q, true) != COFEM_OK) {
-                (void)cudaGetLastError();
-                if ((st = build_graph(c, Q, false))) return st;
-            }
-            c->graph_L = L;
-        }
-        CK(cudaGraphLaunch(c->gexec, c->stream));
-    } else {
-        if ((st = run_fit_direct(c, Q, T_em))) return st;
-    }
+    return COFEM_OK;
+}
+
+// Results of the last E-step (mu, s of each task, alpha^(T), cg_iters) and the flags.
+static cofem_status fit_finish(cofem_ctx* c, int L, int T_em, float* mu, float* s, float* alpha, int* cg_iters,
+                               unsigned* flags) {
+    DevCtl* hc = c->ctl_host;
     CK(cudaMemcpy2DAsync(mu, c->D * sizeof(float), c->mu_out, c->Dp * sizeof(float), c->D * sizeof(float), L,
                          cudaMemcpyDefault, c->stream));
     CK(cudaMemcpy2DAsync(s, c->D * sizeof(float), c->s_out, c->Dp * sizeof(float), c->D * sizeof(float), L,
@@ -791,6 +781,63 @@ static cofem_status fit_impl(cofem_ctx* c, int L, const float* Y, double beta, c
         return fail(COFEM_ERR_CUDA, "a bounded on-device wait timed out (tensor-core pipeline)");
     return COFEM_OK;
 }
+
+// One fit of L tasks sharing the dictionary and alpha (L = 1: Alg. 1 as
+// printed; L > 1: the multi-task CoFEM of Sec. III with the L (K+1) columns
+// in one batched PCG).
+static cofem_status fit_impl(cofem_ctx* c, int L, const float* Y, double beta, const float* alpha0, int K,
+                             int T_em, double cg_tol, int cg_maxit, float* mu, float* s, float* alpha,
+                             int* cg_iters, unsigned* flags) {
+    g_err[0] = 0;
+    cofem_status st = fit_begin(c, L, Y, beta, alpha0, K, T_em, cg_tol, cg_maxit, mu, s, alpha);
+    if (st) return st;
+    const int Q = L * (K + 1);
+    if (c->opts.use_graph) {
+        if (c->graph_Q != Q || c->graph_L != L || !c->gexec) {
+            // programmatic edges where the driver takes them, else plain ones
+            const bool pdl = c->opts.overlap_launch != 0;
+            if (!pdl || build_graph(c, Q, true) != COFEM_OK) {
+                (void)cudaGetLastError();
+                if ((st = build_graph(c, Q, false))) return st;
+            }
+            c->graph_L = L;
+        }
+        CK(cudaGraphLaunch(c->gexec, c->stream));
+    } else {
+        if ((st = run_fit_direct(c, Q, T_em))) return st;
+    }
+    return fit_finish(c, L, T_em, mu, s, alpha, cg_iters, flags);
+}
+
+}  // extern "C"
+
+// Packed serving: the fit's prologue, the fixed segments of its products and
+// the first E-step's initialisation on the handle's stream; the packed steps
+// take it from there (phase PH_CG, or PH_START if no column needs CG).
+cofem_status packed_prepare(cofem_ctx* c, const cofem_request& r) {
+    g_err[0] = 0;
+    if (c->kind != COFEM_OP_DENSE || !c->use_tc || c->phi8)
+        return fail(COFEM_ERR_UNSUPPORTED, "packed serving takes dense BF16 or 3xTF32 dictionaries");
+    cofem_status st = fit_begin(c, 1, r.y, r.beta, r.alpha0, r.K, r.T_em, r.cg_tol, r.cg_maxit, r.mu, r.s, r.alpha);
+    if (st) return st;
+    cudaError_t e = tc_pack_setup(c);
+    if (e == cudaErrorNotSupported)
+        return fail(COFEM_ERR_UNSUPPORTED, "packed serving needs the two-pass tensor-core operator");
+    if (e != cudaSuccess) return cuda_fail(e, "packed segments");
+    Sink s;
+    s.stream = c->stream;
+    launch_fit_setup(s, c, r.K + 1);
+    launch_cg_init(s, c, r.K + 1, 0);
+    if (s.err) return cuda_fail(s.err, "launch");
+    CK(cudaStreamSynchronize(c->stream));
+    return COFEM_OK;
+}
+
+cofem_status packed_finish(cofem_ctx* c, const cofem_request& r, unsigned* flags) {
+    return fit_finish(c, 1, r.T_em, r.mu, r.s, r.alpha, r.cg_iters, flags);
+}
+
+extern "C" {
 
 cofem_status cofem_fit(cofem_ctx* c, const float* y, double beta, const float* alpha0, int K, int T_em,
                        double cg_tol, int cg_maxit, float* mu, float* s, float* alpha, int* cg_iters,

@@ -55,7 +55,19 @@ struct DevCtl {
     int broken[COFEM_QMAX];     // column frozen by a breakdown in this EM iteration
     int restart[COFEM_QMAX];    // column restarted by the last check
     double rt2[COFEM_QMAX];     // ||B - A X||^2 of the last check (FP32-pair product)
+    int phase;                  // packed serving: what the next step does for this fit (PH_*)
 };
+
+// Phase of a fit in a packed serving step (cofem_server in packed mode): the
+// kernels of one step (operator, update, direction) run only for PH_CG fits;
+// the M-step runs for fits whose CG loop ended (or was never entered,
+// PH_START), the initialisation for PH_INIT fits.  The initialisation and the
+// M-step of every fit record it; only the packed step reads it.
+#define PH_NONE 0
+#define PH_CG 1
+#define PH_START 2
+#define PH_INIT 3
+#define PH_DONE 4
 
 // Column q of the block: task q / (K+1), and k = q mod (K+1) (0: the mu system
 // beta Phi^T y_task, k >= 1: probe k of that task).
@@ -327,6 +339,51 @@ __device__ __forceinline__ float4 op_sum4(const OpOut& o, int Q, int q, long lon
     }
     return u;
 }
+
+// ---------------------------------------------------------------------------
+// Packed serving: the kernels of one CG step of several fits in one launch
+// each (serve.cu builds the tables; kernels_tc.cu and kernels_vec.cu run them).
+// ---------------------------------------------------------------------------
+// One fit's product for the packed GEMM, and a segment of it.
+struct TcSlot {
+    const uint8_t* A;     // tiled A image of the fit's product
+    const uint8_t* B;     // its B image (split block), k tile at k QS 128 bytes
+    const DevCtl* ctl;    // the fit's phase: only PH_CG fits run
+    float* part;          // the fit's segment partials [segment][Q][G 128]
+    uint32_t idesc, idesc_lo;
+    int K_tiles, M_tiles, QS, QH, Q;
+};
+struct TcSeg {
+    int slot, g, k0, k1;  // fit, row group, k tiles [k0, k1)
+    int out;              // segment index within the fit's partials
+};
+struct TcBatch {
+    const TcSlot* slots;
+    const TcSeg* segs;
+    const int* cta_seg;   // CTA c runs segments [cta_seg[c], cta_seg[c + 1])
+    int G, acc_stride, QSmax;
+    unsigned* flags;
+};
+
+// One fit's vectors and control block for the packed vector kernels.
+struct VSlot {
+    DevCtl* ctl;
+    const float* b;
+    const float* theta;
+    float *alpha, *minv, *X, *R, *P, *mu_out, *s_out;
+    int* iters;
+    long long D, Dp, Np;
+    int nch, Q;
+    double* part;          // CG partials, 3 x Q x nch
+    unsigned* counters;    // the fit's last-block counters
+    SplitOut so;           // split image of P (the first product's B operand)
+    OpOut uo;              // the second product's segment partials
+    const float* t_part;   // the first product's segment partials [segment][Q][GR]
+    const int* t_grp;      // their (first segment, count) per row group
+    int GR;
+    SplitOut st;           // split image of T (the second product's B operand)
+    double* tt_part;       // partials of ||Phi p||^2, [q][ceil(Np / 1024)]
+};
 
 // ---------------------------------------------------------------------------
 // Launch sink: the same launch sequence either runs directly on a stream or is
@@ -627,6 +684,30 @@ void launch_df_first_product(Sink& s, cofem_ctx* c, int Q);   // dense only
 void launch_df_check(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_vf);
 void launch_cg_gate(Sink& s, cofem_ctx* c, cudaGraphConditionalHandle h_cg);
 void launch_df_gram(Sink& s, cofem_ctx* c, int Q, double* out);   // Phi~^T Phi~ (X + Xlo), dense
+
+// Packed serving (kernels_tc.cu, kernels_vec.cu, cofem_api.cu)
+#define PK_SEGK 16   // k tiles per segment of the packed GEMM
+struct PackedFit {   // what serve.cu needs of one fit's tensor-core plan
+    TcSlot g1, g2;                      // the two products
+    std::vector<TcSeg> s1, s2;          // their fixed segments (slot field 0)
+    std::vector<double> c1, c2;         // bytes of the dictionary image each segment reads
+    bool tf;                            // 3xTF32 products (else BF16)
+};
+cudaError_t tc_pack_setup(cofem_ctx* c);                       // fixed segments and their partials
+void tc_pack_describe(cofem_ctx* c, PackedFit* out);
+void tc_pack_vslot(cofem_ctx* c, VSlot* out);
+size_t tc_packed_smem(bool tf, int QSmax);
+void launch_gemm_packed(Sink& s, bool tf, const TcBatch& b, int nCTA, size_t smem);
+void launch_reduce_T_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks);
+void launch_update_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks);
+void launch_direction_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks);
+void launch_mstep_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks);
+void launch_init_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks);
+void launch_packed_status(Sink& s, const VSlot* vs, int n, int* status, const volatile int* pending,
+                          unsigned* steps, unsigned max_steps, cudaGraphConditionalHandle h_loop);
+// fit prologue up to the first E-step's initialisation, and the epilogue
+cofem_status packed_prepare(cofem_ctx* c, const cofem_request& r);
+cofem_status packed_finish(cofem_ctx* c, const cofem_request& r, unsigned* flags);
 
 // kernels_sliced.cu (precision form, BF16 dictionary: the accurate residual
 // from exact integer slices on the tensor cores)

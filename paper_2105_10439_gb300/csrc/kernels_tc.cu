@@ -372,6 +372,253 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc(TcParams p) {
 }
 
 // ---------------------------------------------------------------------------
+// Packed serving: one launch of the GEMM applies the operator products of
+// several fits at once.  Each fit's (group, k tile) units are cut into fixed
+// segments of at most PK_SEGK k tiles per group, independent of the other fits
+// in the step, so a fit's partial sums (and its results) are the same bits
+// alone and among others; the host concatenates the segments of the step's
+// fits and gives each CTA a contiguous run of about equal bytes.  Segments of
+// a fit not in its CG loop (phase != PH_CG) are skipped by every role alike.
+// Roles, rings, bounded waits and the TMEM drain are those of k_gemm_tc; the
+// dictionary ring is filled only after the programmatic wait (which segments
+// run depends on the previous kernels).
+// ---------------------------------------------------------------------------
+template <bool TF>
+__global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc_packed(TcBatch p) {
+    constexpr int NA = TF ? TC_NA_TF : TC_NA;
+    constexpr int KE = TF ? TC_BK32 : TC_BK;
+    constexpr int KM = TF ? 8 : 16;
+    const int EPT = TF ? 1 : p.G;
+    const int NE = TF ? NA : NA / p.G;
+    const uint32_t E_BYTES = (uint32_t)EPT * TC_A_BYTES;
+    griddep_launch();
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t B_MAX = (uint32_t)p.QSmax * 128u;   // ring element (the largest fit's split tile)
+    uint8_t* ringA = smem;
+    uint8_t* ringL = smem + NA * TC_A_BYTES;
+    uint8_t* ringB = ringL + (TF ? NA * TC_A_BYTES : 0);
+    uint64_t* bars = (uint64_t*)(ringB + TC_NB * B_MAX);
+    uint64_t* a_full = bars;
+    uint64_t* a_empty = bars + NA;
+    uint64_t* lo_full = bars + 2 * NA;
+    uint64_t* b_full = bars + 3 * NA;
+    uint64_t* b_empty = bars + 3 * NA + TC_NB;
+    uint64_t* acc_full = bars + 3 * NA + 2 * TC_NB;
+    uint64_t* acc_empty = acc_full + 1;
+    uint64_t* drain = acc_full + 2;
+    uint32_t* tmem_slot = (uint32_t*)(acc_full + 3);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NA; ++i) {
+            mbar_init(smem_u32(a_full + i), 1);
+            mbar_init(smem_u32(a_empty + i), 1);
+            mbar_init(smem_u32(lo_full + i), 4);
+        }
+        for (int i = 0; i < TC_NB; ++i) {
+            mbar_init(smem_u32(b_full + i), 1);
+            mbar_init(smem_u32(b_empty + i), 1);
+        }
+        mbar_init(smem_u32(acc_full), 1);
+        mbar_init(smem_u32(acc_empty), tc_epi_warps(TF));
+        mbar_init(smem_u32(drain), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    griddep_wait();   // phases and B operands come from the previous kernels
+    const int i0 = p.cta_seg[blockIdx.x], i1 = p.cta_seg[blockIdx.x + 1];
+    long long na = 0, nb = 0;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- bulk-copy producer ----------------
+            uint64_t evict_first;
+            asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(evict_first));
+            bool ok = true;
+            for (int i = i0; i < i1 && ok; ++i) {
+                const TcSeg sg = p.segs[i];
+                const TcSlot& sl = p.slots[sg.slot];
+                if (sl.ctl->phase != PH_CG) continue;
+                const int valid = min(p.G, sl.M_tiles - sg.g * p.G);
+                const uint32_t bbytes = (uint32_t)sl.QS * 128u;
+                for (int k = sg.k0; k < sg.k1; ++k) {
+                    int slot = (int)(nb % TC_NB);
+                    long long use = nb / TC_NB;
+                    if (use > 0 && !mbar_wait(smem_u32(b_empty + slot), (uint32_t)((use - 1) & 1), abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(smem_u32(b_full + slot), bbytes);
+                    bulk_load(smem_u32(ringB + slot * B_MAX), sl.B + (size_t)k * bbytes, bbytes,
+                              smem_u32(b_full + slot));
+                    ++nb;
+                    const long long u = (long long)sg.g * sl.K_tiles + k;
+                    for (int r = 0; r < (TF ? valid : 1); ++r) {
+                        slot = (int)(na % NE);
+                        use = na / NE;
+                        if (use > 0 && !mbar_wait(smem_u32(a_empty + slot), (uint32_t)((use - 1) & 1), abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_expect_tx(smem_u32(a_full + slot), E_BYTES);
+                        bulk_load_hint(smem_u32(ringA + slot * E_BYTES), sl.A + ((size_t)u * p.G + r) * TC_A_BYTES,
+                                       E_BYTES, smem_u32(a_full + slot), evict_first);
+                        ++na;
+                    }
+                    if (!ok) break;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            long long ma = 0, mb = 0;
+            int nseg = 0;
+            bool ok = true;
+            for (int i = i0; i < i1 && ok; ++i) {
+                const TcSeg sg = p.segs[i];
+                const TcSlot& sl = p.slots[sg.slot];
+                if (sl.ctl->phase != PH_CG) continue;
+                const int valid = min(p.G, sl.M_tiles - sg.g * p.G);
+                const uint32_t idesc = sl.idesc, idesc_lo = sl.idesc_lo;
+                if (nseg > 0 && !mbar_wait(smem_u32(acc_empty), (uint32_t)((nseg - 1) & 1), abort_flag)) break;
+                tc_fence_after();
+                for (int k = sg.k0; k < sg.k1; ++k) {
+                    const int sb = (int)(mb % TC_NB);
+                    if (!mbar_wait(smem_u32(b_full + sb), (uint32_t)((mb / TC_NB) & 1), abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint64_t db = desc_sw128(smem_u32(ringB + sb * B_MAX));
+                    int sa = 0;
+                    for (int r = 0; r < valid; ++r) {
+                        if (TF || r == 0) {
+                            sa = (int)(ma % NE);
+                            const uint32_t par = (uint32_t)((ma / NE) & 1);
+                            if (!mbar_wait(smem_u32(a_full + sa), par, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            if (TF && !mbar_wait(smem_u32(lo_full + sa), par, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                        }
+                        const uint64_t da = desc_sw128(smem_u32(ringA + sa * E_BYTES + (TF ? 0 : r) * TC_A_BYTES));
+                        const uint32_t dt = tmem + (uint32_t)(r * p.acc_stride);
+#pragma unroll
+                        for (int kk = 0; kk < KE / KM; ++kk) {
+                            const uint32_t acc = (k > sg.k0 || kk > 0) ? 1u : 0u;
+                            if (TF) mma_tf32(dt, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc, acc);
+                            else mma_bf16(dt, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc, acc);
+                        }
+                        if (TF) {
+                            const uint64_t dl = desc_sw128(smem_u32(ringL + sa * TC_A_BYTES));
+#pragma unroll
+                            for (int kk = 0; kk < KE / KM; ++kk)
+                                mma_tf32(dt, dl + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc_lo, 1u);
+                        }
+                        if (TF || r == valid - 1) {
+                            mma_commit(smem_u32(a_empty + sa));
+                            ++ma;
+                        }
+                    }
+                    if (!ok) break;
+                    mma_commit(smem_u32(b_empty + sb));
+                    ++mb;
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(acc_full));
+                ++nseg;
+            }
+            mma_commit(smem_u32(drain));
+            mbar_drain(smem_u32(drain), 0);
+        }
+    } else {
+        // ------- epilogue warps: (TF32) Phi_lo tiles; TMEM -> the fit's partials -------
+        const int sub = warp & 3;
+        const int ew = warp - 2;
+        const int GR = p.G * TC_BM;
+        int nseg = 0;
+        long long ne = 0;
+        bool ok = true;
+        for (int i = i0; i < i1 && ok; ++i) {
+            const TcSeg sg = p.segs[i];
+            const TcSlot& sl = p.slots[sg.slot];
+            if (sl.ctl->phase != PH_CG) continue;
+            const int valid = min(p.G, sl.M_tiles - sg.g * p.G);
+            if (TF && ew < 4) {
+                for (int k = sg.k0; k < sg.k1 && ok; ++k) {
+                    for (int r = 0; r < valid; ++r) {
+                        const int sa = (int)(ne % NA);
+                        if (!mbar_wait(smem_u32(a_full + sa), (uint32_t)((ne / NA) & 1), abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        float4* src = reinterpret_cast<float4*>(ringA + sa * TC_A_BYTES) + ew * 256;
+                        float4* dst = reinterpret_cast<float4*>(ringL + sa * TC_A_BYTES) + ew * 256;
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const float4 x = src[lane + 32 * e];
+                            const float4 h = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
+                            src[lane + 32 * e] = h;
+                            dst[lane + 32 * e] = make_float4(tf32_rn(x.x - h.x), tf32_rn(x.y - h.y),
+                                                             tf32_rn(x.z - h.z), tf32_rn(x.w - h.w));
+                        }
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(lo_full + sa));
+                        ++ne;
+                    }
+                }
+                if (!ok) break;
+            }
+            if (!mbar_wait(smem_u32(acc_full), (uint32_t)(nseg & 1), abort_flag)) break;
+            tc_fence_after();
+            float* out = sl.part + (size_t)sg.out * sl.Q * GR;
+            drain_tmem<TF>(tmem + ((uint32_t)(32 * sub) << 16), ew >> 2, tc_epi_warps(TF) / 4, valid, p.acc_stride,
+                           sl.Q, sl.QH, sl.QS / 16, GR, out, 32 * sub + lane);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(acc_empty));
+            ++nseg;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag) {
+        for (int s = 0; s < NE; ++s) {
+            const long long n_s = na > s ? (na - s + NE - 1) / NE : 0;
+            if (n_s > 0) mbar_drain(smem_u32(a_full + s), (uint32_t)((n_s - 1) & 1));
+        }
+        for (int s = 0; s < TC_NB; ++s) {
+            const long long n_s = nb > s ? (nb - s + TC_NB - 1) / TC_NB : 0;
+            if (n_s > 0) mbar_drain(smem_u32(b_full + s), (uint32_t)((n_s - 1) & 1));
+        }
+    }
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+    if (threadIdx.x == 0 && *abort_flag) atomicOr(p.flags, COFEM_FLAG_DEVICE_TIMEOUT);
+}
+
+// ---------------------------------------------------------------------------
 // FP8 E4M3 dictionary.  The A image holds codes, 128 rows x 128 codes per
 // 16 KiB tile, tiles ordered (group of 2 row tiles, 128-wide k tile, row
 // tile); a unit's two tiles arrive as one 32 KiB bulk copy.  Four converter
@@ -672,15 +919,13 @@ __global__ void k_split(const float* __restrict__ V, long long Dp, SplitOut so) 
 
 // GEMM1 epilogue: T = sum of the segment partials of its group (fixed order),
 // split into the B image of GEMM2, and ||T_q||^2 partials -> pi, gamma.
-__global__ __launch_bounds__(256) void k_tc_reduce_T(const float* __restrict__ part, const int* __restrict__ grp_seg,
-                                                     int GR, int Q, long long Np, SplitOut so, double* tt_part,
-                                                     int nblk, unsigned* counter, DevCtl* ctl, int mode,
-                                                     const float* __restrict__ rscale, float rfac) {
+__device__ __forceinline__ void reduce_T_body(const float* __restrict__ part, const int* __restrict__ grp_seg, int GR,
+                                              int Q, long long Np, const SplitOut& so, double* tt_part, int nblk,
+                                              unsigned* counter, DevCtl* ctl, int mode,
+                                              const float* __restrict__ rscale, float rfac, int q, int ib,
+                                              unsigned total) {
     __shared__ double sh[8];
-    griddep_launch();
-    griddep_wait();   // the partials are the previous kernel's output
-    const int q = blockIdx.y;
-    const long long i = (long long)blockIdx.x * 1024 + threadIdx.x * 4;
+    const long long i = (long long)ib * 1024 + threadIdx.x * 4;
     float tt = 0.0f;
     if (i < Np) {
         const int g = (int)(i / GR), r = (int)(i % GR);
@@ -701,13 +946,38 @@ __global__ __launch_bounds__(256) void k_tc_reduce_T(const float* __restrict__ p
         tt = a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
     }
     const double ttd = block_sum_f(tt, sh);
-    if (threadIdx.x == 0) tt_part[(size_t)q * nblk + blockIdx.x] = ttd;
+    if (threadIdx.x == 0) tt_part[(size_t)q * nblk + ib] = ttd;
     if (mode == OP_CG) {   // the update kernel reduces the partials (op_cg_begin)
-        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) op_cg_begin(ctl, tt_part, nblk);
+        if (ib == 0 && q == 0 && threadIdx.x == 0) op_cg_begin(ctl, tt_part, nblk);
         return;
     }
-    if (!last_block_arrive(counter, gridDim.x * gridDim.y)) return;
+    if (!last_block_arrive(counter, total)) return;
     op_finalize_block(ctl, tt_part, nblk, Q);
+}
+
+__global__ __launch_bounds__(256) void k_tc_reduce_T(const float* __restrict__ part, const int* __restrict__ grp_seg,
+                                                     int GR, int Q, long long Np, SplitOut so, double* tt_part,
+                                                     int nblk, unsigned* counter, DevCtl* ctl, int mode,
+                                                     const float* __restrict__ rscale, float rfac) {
+    griddep_launch();
+    griddep_wait();   // the partials are the previous kernel's output
+    reduce_T_body(part, grp_seg, GR, Q, Np, so, tt_part, nblk, counter, ctl, mode, rscale, rfac, blockIdx.y,
+                  blockIdx.x, gridDim.x * gridDim.y);
+}
+
+// Packed serving: block b = (fit, column, 1024-row block) map[b] of the fits
+// in their CG loop (the operator's first product -> split(T), ||T||^2 partials).
+__global__ __launch_bounds__(256) void k_reduce_T_packed(const VSlot* __restrict__ vs, const int4* __restrict__ map) {
+    griddep_launch();
+    griddep_wait();
+    const int4 m = map[blockIdx.x];
+    const VSlot& f = vs[m.x];
+    DevCtl* ctl = f.ctl;
+    if (ctl->phase != PH_CG) return;
+    const SplitOut st = f.st;
+    const int nblk = (int)((f.Np + 1023) / 1024);
+    reduce_T_body(f.t_part, f.t_grp, f.GR, f.Q, f.Np, st, f.tt_part, nblk, nullptr, ctl, OP_CG, nullptr, 1.0f, m.y,
+                  m.z, 0u);
 }
 
 // GEMM2 epilogue for a stand-alone application: U (Q x Dp) = sum of the
@@ -791,6 +1061,12 @@ struct TcPlan {
     void* Ts = nullptr;              // tiled image of split(T), QS x Np
     size_t esz = 2;                  // bytes per image element
     GemmPlan g1, g2;
+    // packed serving: fixed segments of both products (PK_SEGK k tiles per
+    // segment) and their partials, independent of the other fits in a step
+    float *pk_part1 = nullptr, *pk_part2 = nullptr;
+    int *pk_grp1 = nullptr, *pk_grp2 = nullptr;
+    std::vector<TcSeg> pk_s1, pk_s2;
+    std::vector<double> pk_c1, pk_c2;
     FusedPlan* fused = nullptr;      // single-pass form (then g1, g2 are unused)
     void* fimg = nullptr;            // its tiled image of Phi~ (groups of 2 row tiles)
     size_t fimg_bytes = 0;
@@ -890,6 +1166,8 @@ void tc_release(cofem_ctx* c) {
     if (t->fimg) cudaFreeAsync(t->fimg, c->stream);
     if (t->Vs) cudaFreeAsync(t->Vs, c->stream);
     if (t->Ts) cudaFreeAsync(t->Ts, c->stream);
+    for (void* p : {(void*)t->pk_part1, (void*)t->pk_part2, (void*)t->pk_grp1, (void*)t->pk_grp2})
+        if (p) cudaFreeAsync(p, c->stream);
     c->bytes -= t->bytes;
     delete t;
     c->tc = nullptr;
@@ -1009,6 +1287,10 @@ cudaError_t tc_kernel_attributes(int max_smem) {
     if ((e = fused_kernel_attributes(max_smem)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_gemm8, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem)) != cudaSuccess)
         return e;
+    if ((e = cudaFuncSetAttribute(k_gemm_tc_packed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_gemm_tc_packed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem)))
+        return e;
     return cudaFuncSetAttribute(k_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
 }
 
@@ -1062,4 +1344,115 @@ void tc_operator_info(cofem_ctx* c, int* path, int* k_cg, int* k_rr) {
     *path = t->fused ? COFEM_PATH_SINGLE_PASS : COFEM_PATH_TWO_PASS;
     *k_cg = t->fused ? 1 : 3;
     *k_rr = true_residual_kernels(c);
+}
+
+// ---------------------------------------------------------------------------
+// Packed serving (host side)
+// ---------------------------------------------------------------------------
+namespace {
+
+// Fixed segments of one product: row group g, k tiles [k0, k0 + PK_SEGK);
+// segment g * spg + s; cost = bytes of the dictionary image it reads.
+cudaError_t pack_product(TcPlan* t, const GemmPlan& gp, bool tf, int Q, std::vector<TcSeg>& segs,
+                         std::vector<double>& cost, float** part, int** grp, cudaStream_t st) {
+    const int K_tiles = gp.p.K_tiles, M_tiles = gp.p.M_tiles, G = gp.p.G, groups = gp.groups;
+    const int spg = (K_tiles + PK_SEGK - 1) / PK_SEGK;
+    segs.clear();
+    cost.clear();
+    std::vector<int> tab(2 * (size_t)groups);
+    for (int g = 0; g < groups; ++g) {
+        const int valid = std::min(G, M_tiles - g * G);
+        tab[2 * g] = g * spg;
+        tab[2 * g + 1] = spg;
+        for (int sgi = 0; sgi < spg; ++sgi) {
+            const int k0 = sgi * PK_SEGK, k1 = std::min(K_tiles, k0 + PK_SEGK);
+            segs.push_back(TcSeg{0, g, k0, k1, g * spg + sgi});
+            cost.push_back((double)(k1 - k0) * (tf ? valid : G) * TC_A_BYTES);
+        }
+    }
+    const size_t part_elems = segs.size() * (size_t)Q * G * TC_BM;
+    cudaError_t e;
+    if ((e = cudaMallocAsync((void**)part, part_elems * sizeof(float), st))) return e;
+    if ((e = cudaMallocAsync((void**)grp, tab.size() * sizeof(int), st))) return e;
+    t->bytes += (long long)(part_elems * sizeof(float) + tab.size() * sizeof(int));
+    if ((e = cudaMemcpyAsync(*grp, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, st))) return e;
+    return cudaStreamSynchronize(st);   // the host table goes out of scope
+}
+
+}  // namespace
+
+cudaError_t tc_pack_setup(cofem_ctx* c) {
+    TcPlan* t = (TcPlan*)c->tc;
+    if (!t || t->fused || t->f8) return cudaErrorNotSupported;
+    if (t->pk_part1) return cudaSuccess;
+    const long long before = t->bytes;
+    cudaError_t e = pack_product(t, t->g1, t->tf, t->Q, t->pk_s1, t->pk_c1, &t->pk_part1, &t->pk_grp1, c->stream);
+    if (e == cudaSuccess)
+        e = pack_product(t, t->g2, t->tf, t->Q, t->pk_s2, t->pk_c2, &t->pk_part2, &t->pk_grp2, c->stream);
+    c->bytes += t->bytes - before;
+    return e;
+}
+
+void tc_pack_describe(cofem_ctx* c, PackedFit* out) {
+    TcPlan* t = (TcPlan*)c->tc;
+    auto fill = [&](TcSlot& sl, const GemmPlan& gp, const void* B, float* part) {
+        sl.A = (const uint8_t*)gp.A;
+        sl.B = (const uint8_t*)B;
+        sl.ctl = c->ctl;
+        sl.part = part;
+        sl.idesc = gp.p.idesc;
+        sl.idesc_lo = gp.p.idesc_lo;
+        sl.K_tiles = gp.p.K_tiles;
+        sl.M_tiles = gp.p.M_tiles;
+        sl.QS = gp.p.QS;
+        sl.QH = gp.p.QH;
+        sl.Q = gp.p.Q;
+    };
+    fill(out->g1, t->g1, t->Vs, t->pk_part1);
+    fill(out->g2, t->g2, t->Ts, t->pk_part2);
+    out->s1 = t->pk_s1;
+    out->s2 = t->pk_s2;
+    out->c1 = t->pk_c1;
+    out->c2 = t->pk_c2;
+    out->tf = t->tf;
+}
+
+void tc_pack_vslot(cofem_ctx* c, VSlot* v) {
+    TcPlan* t = (TcPlan*)c->tc;
+    v->ctl = c->ctl;
+    v->b = c->b;
+    v->theta = c->theta;
+    v->alpha = c->alpha;
+    v->minv = c->minv;
+    v->X = c->X;
+    v->R = c->R;
+    v->P = c->P;
+    v->mu_out = c->mu_out;
+    v->s_out = c->s_out;
+    v->iters = c->iters_dev;
+    v->D = c->D;
+    v->Dp = c->Dp;
+    v->Np = c->Np;
+    v->nch = c->nch;
+    v->Q = t->Q;
+    v->part = c->part;
+    v->counters = c->counters;
+    v->so = SplitOut{t->Vs, t->tf ? 2 : 1, t->QS, t->QH, 1.0f};
+    v->uo = OpOut{t->pk_part2, 1, 0, t->pk_grp2, t->G * TC_BM, 1.0f};
+    v->t_part = t->pk_part1;
+    v->t_grp = t->pk_grp1;
+    v->GR = t->G * TC_BM;
+    v->st = SplitOut{t->Ts, t->tf ? 2 : 1, t->QS, t->QH, 1.0f};
+    v->tt_part = c->tt_part;
+}
+
+size_t tc_packed_smem(bool tf, int QSmax) { return gemm_smem(tf, QSmax); }
+
+void launch_gemm_packed(Sink& s, bool tf, const TcBatch& b, int nCTA, size_t smem) {
+    if (tf) s.launch_pdl(k_gemm_tc_packed<true>, dim3(nCTA), dim3(tc_threads(true)), smem, b);
+    else s.launch_pdl(k_gemm_tc_packed<false>, dim3(nCTA), dim3(tc_threads(false)), smem, b);
+}
+
+void launch_reduce_T_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks) {
+    s.launch_pdl(k_reduce_T_packed, dim3(nblocks), dim3(256), 0, vs, map);
 }

@@ -81,15 +81,18 @@ __global__ void k_fit_setup(DevCtl* ctl, const float* __restrict__ theta, const 
 // h_cg is the condition of the loop that follows: the CG loop, or in the
 // precision form the verification loop around it.
 // ---------------------------------------------------------------------------
-__global__ __launch_bounds__(NT) void k_cg_init(DevCtl* ctl, const float* __restrict__ b,
-                                                const float* __restrict__ minv, const float* __restrict__ alpha,
-                                                float* __restrict__ X, float* __restrict__ R, float* __restrict__ P,
-                                                float* __restrict__ Xlo, long long D, long long Dp, int nch,
-                                                double* part, unsigned* counter, cudaGraphConditionalHandle h_cg,
-                                                SplitOut so, OpOut uo) {
+// Block (ch, q) of one handle's grid; `total` = blocks of that grid (the
+// last-block reduction).  The last block also records the phase a packed
+// serving step reads (PH_CG: the CG loop runs; PH_START: it is not entered).
+__device__ __forceinline__ void cg_init_body(DevCtl* ctl, const float* __restrict__ b,
+                                             const float* __restrict__ minv, const float* __restrict__ alpha,
+                                             float* __restrict__ X, float* __restrict__ R, float* __restrict__ P,
+                                             float* __restrict__ Xlo, long long D, long long Dp, int nch,
+                                             double* part, unsigned* counter, cudaGraphConditionalHandle h_cg,
+                                             const SplitOut& so, const OpOut& uo, int q, int ch, unsigned total) {
     __shared__ double sh[NT / 32];
     __shared__ double red[3 * COFEM_QMAX];
-    const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q, t = ctl->t;
+    const int Q = ctl->Q, t = ctl->t;
     const int tp = ctl->warm ? 1 : t;           // probe reuse draws the probes of t = 1
     const bool warm = ctl->warm && t > 1;       // start from the previous E-step's X
     const float beta = (float)ctl->beta;
@@ -141,7 +144,7 @@ __global__ __launch_bounds__(NT) void k_cg_init(DevCtl* ctl, const float* __rest
         part[(size_t)(1 * Q + q) * nch + ch] = rzd;
         part[(size_t)(2 * Q + q) * nch + ch] = apd;
     }
-    if (!last_block_arrive(counter, gridDim.x * gridDim.y)) return;
+    if (!last_block_arrive(counter, total)) return;
     reduce_parts(part, 3, Q, nch, red);
     const int qq = threadIdx.x;
     int act = 0;
@@ -158,29 +161,38 @@ __global__ __launch_bounds__(NT) void k_cg_init(DevCtl* ctl, const float* __rest
     if (threadIdx.x == 0) {
         ctl->u = 0;
         ctl->any_active = act;
+        ctl->phase = act && ctl->maxit > 0 ? PH_CG : PH_START;
         set_cond(h_cg, act && ctl->maxit > 0);
     }
+}
+
+__global__ __launch_bounds__(NT) void k_cg_init(DevCtl* ctl, const float* __restrict__ b,
+                                                const float* __restrict__ minv, const float* __restrict__ alpha,
+                                                float* __restrict__ X, float* __restrict__ R, float* __restrict__ P,
+                                                float* __restrict__ Xlo, long long D, long long Dp, int nch,
+                                                double* part, unsigned* counter, cudaGraphConditionalHandle h_cg,
+                                                SplitOut so, OpOut uo) {
+    cg_init_body(ctl, b, minv, alpha, X, R, P, Xlo, D, Dp, nch, part, counter, h_cg, so, uo, blockIdx.y, blockIdx.x,
+                 gridDim.x * gridDim.y);
 }
 
 // ---------------------------------------------------------------------------
 // Fused CG update (Alg. 2: X += P Gamma, R -= Psi Gamma, and the per-block
 // partials of ||r||^2 and r^T M^-1 r), for the active columns.
 // ---------------------------------------------------------------------------
-__global__ __launch_bounds__(NT, 2) void k_cg_update(DevCtl* ctl, const float* __restrict__ P, OpOut uo,
-                                                  const float* __restrict__ alpha,
-                                                  const float* __restrict__ minv, float* __restrict__ X,
-                                                  float* __restrict__ R, float* __restrict__ Xlo, long long Dp,
-                                                  int nch, double* part, cudaGraphConditionalHandle h_rr,
-                                                  cudaGraphConditionalHandle h_cg) {
+__device__ __forceinline__ void cg_update_body(DevCtl* ctl, const float* __restrict__ P, const OpOut& uo,
+                                               const float* __restrict__ alpha, const float* __restrict__ minv,
+                                               float* __restrict__ X, float* __restrict__ R,
+                                               float* __restrict__ Xlo, long long Dp, int nch, double* part,
+                                               cudaGraphConditionalHandle h_rr, cudaGraphConditionalHandle h_cg,
+                                               int q, int ch) {
     __shared__ double sh[NT / 32];
     __shared__ double s_sum[2];
     __shared__ int s_act;
     __shared__ float s_gamma;
-    griddep_launch();
-    griddep_wait();   // the operator's output and partials come from the previous kernels
-    const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q;
+    const int Q = ctl->Q;
     const int u = ctl->u;   // this CG iteration (counted by the operator)
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    if (ch == 0 && q == 0 && threadIdx.x == 0) {
         // the stopping test and the loop condition are the direction kernel's
         // (it reads this kernel's partials)
         ctl->any_active = 0;
@@ -304,6 +316,17 @@ __global__ __launch_bounds__(NT, 2) void k_cg_update(DevCtl* ctl, const float* _
     }
 }
 
+__global__ __launch_bounds__(NT, 2) void k_cg_update(DevCtl* ctl, const float* __restrict__ P, OpOut uo,
+                                                  const float* __restrict__ alpha,
+                                                  const float* __restrict__ minv, float* __restrict__ X,
+                                                  float* __restrict__ R, float* __restrict__ Xlo, long long Dp,
+                                                  int nch, double* part, cudaGraphConditionalHandle h_rr,
+                                                  cudaGraphConditionalHandle h_cg) {
+    griddep_launch();
+    griddep_wait();   // the operator's output and partials come from the previous kernels
+    cg_update_body(ctl, P, uo, alpha, minv, X, R, Xlo, Dp, nch, part, h_rr, h_cg, blockIdx.y, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // Stopping test and direction update (Alg. 2, PCG reading: W = M^-1 R,
 // P = W + P H) for the active columns, plus the partials of p^T diag(alpha) p
@@ -315,19 +338,17 @@ __global__ __launch_bounds__(NT, 2) void k_cg_update(DevCtl* ctl, const float* _
 // sum_q ||r_q||^2 <= tol^2 sum_q ||b_q||^2 ends all of them (Frobenius test);
 // otherwise eta_q = rho_new / rho_old.
 // ---------------------------------------------------------------------------
-__global__ __launch_bounds__(NT) void k_cg_direction(DevCtl* ctl, const float* __restrict__ R,
-                                                     const float* __restrict__ alpha,
-                                                     const float* __restrict__ minv, float* __restrict__ P,
-                                                     long long Dp, int nch, double* part,
-                                                     cudaGraphConditionalHandle h_cg, SplitOut so) {
+__device__ __forceinline__ void cg_direction_body(DevCtl* ctl, const float* __restrict__ R,
+                                                  const float* __restrict__ alpha, const float* __restrict__ minv,
+                                                  float* __restrict__ P, long long Dp, int nch, double* part,
+                                                  cudaGraphConditionalHandle h_cg, const SplitOut& so, int q,
+                                                  int ch) {
     __shared__ double sh[NT / 32];
     __shared__ double s_rr[COFEM_QMAX];
     __shared__ double s_sum[2];
     __shared__ int s_act;
     __shared__ float s_eta;
-    griddep_launch();
-    griddep_wait();   // R and the partials come from the previous kernel
-    const int q = blockIdx.y, ch = blockIdx.x, Q = ctl->Q;
+    const int Q = ctl->Q;
     const int u = ctl->u;
     // a column that left the loop stays out; block 0 of this column may already
     // have recorded this iteration's decision, which gives the same result
@@ -423,6 +444,16 @@ __global__ __launch_bounds__(NT) void k_cg_direction(DevCtl* ctl, const float* _
     if (threadIdx.x == 0) part[(size_t)(2 * Q + q) * nch + ch] = apd;   // reduced by the operator's finish
 }
 
+__global__ __launch_bounds__(NT) void k_cg_direction(DevCtl* ctl, const float* __restrict__ R,
+                                                     const float* __restrict__ alpha,
+                                                     const float* __restrict__ minv, float* __restrict__ P,
+                                                     long long Dp, int nch, double* part,
+                                                     cudaGraphConditionalHandle h_cg, SplitOut so) {
+    griddep_launch();
+    griddep_wait();   // R and the partials come from the previous kernel
+    cg_direction_body(ctl, R, alpha, minv, P, Dp, nch, part, h_cg, so, blockIdx.y, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // Fused diagonal estimate + M-step (Alg. 1: s_j = (1/K) sum_k p_kj x_kj; if t < T,
 // alpha_j = 1 / max(E[z_j^2], 1/alpha_max) with E[z_j^2] = mu_j^2 + s_j, or under
@@ -430,14 +461,17 @@ __global__ __launch_bounds__(NT) void k_cg_direction(DevCtl* ctl, const float* _
 // z_j >= 0 (non-negativity subsection of Sec. III); then M^-1 for the next
 // E-step), probes regenerated from Philox, plus EM loop bookkeeping.
 // ---------------------------------------------------------------------------
-__global__ __launch_bounds__(NT) void k_mstep(DevCtl* ctl, const float* __restrict__ X,
-                                              const float* __restrict__ theta, float* __restrict__ alpha,
-                                              float* __restrict__ minv, float* __restrict__ mu_out,
-                                              float* __restrict__ s_out, int* __restrict__ iters,
-                                              const float* __restrict__ Xlo, long long D, long long Dp,
-                                              unsigned* counter, cudaGraphConditionalHandle h_em) {
+// Block jb of one handle's grid of `total` blocks (blockDim.x elements each);
+// the last block also records the phase of a packed serving step (PH_INIT:
+// another E-step follows; PH_DONE: the fit is complete).
+__device__ __forceinline__ void mstep_body(DevCtl* ctl, const float* __restrict__ X, const float* __restrict__ theta,
+                                           float* __restrict__ alpha, float* __restrict__ minv,
+                                           float* __restrict__ mu_out, float* __restrict__ s_out,
+                                           int* __restrict__ iters, const float* __restrict__ Xlo, long long D,
+                                           long long Dp, unsigned* counter, cudaGraphConditionalHandle h_em,
+                                           int jb, unsigned total) {
     const int t = ctl->t, T = ctl->T, K = ctl->K, L = ctl->L;
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long j = (long long)jb * blockDim.x + threadIdx.x;
     int clamped = 0;
     if (j < Dp) {
         // per task l: mu_l = x_{l(K+1)}, s_l = (1/K) sum_k p_{l,k} x_{l(K+1)+k}; the
@@ -480,11 +514,96 @@ __global__ __launch_bounds__(NT) void k_mstep(DevCtl* ctl, const float* __restri
         }
     }
     if (__syncthreads_or(clamped) && threadIdx.x == 0) atomicOr(&ctl->flags, COFEM_FLAG_ALPHA_CLAMPED);
-    if (!last_block_arrive(counter, gridDim.x)) return;
+    if (!last_block_arrive(counter, total)) return;
     if (threadIdx.x == 0) {
         iters[t - 1] = ctl->u;
         ctl->t = t + 1;
+        ctl->phase = t + 1 <= T ? PH_INIT : PH_DONE;
         set_cond(h_em, t + 1 <= T);
+    }
+}
+
+__global__ __launch_bounds__(NT) void k_mstep(DevCtl* ctl, const float* __restrict__ X,
+                                              const float* __restrict__ theta, float* __restrict__ alpha,
+                                              float* __restrict__ minv, float* __restrict__ mu_out,
+                                              float* __restrict__ s_out, int* __restrict__ iters,
+                                              const float* __restrict__ Xlo, long long D, long long Dp,
+                                              unsigned* counter, cudaGraphConditionalHandle h_em) {
+    mstep_body(ctl, X, theta, alpha, minv, mu_out, s_out, iters, Xlo, D, Dp, counter, h_em, blockIdx.x, gridDim.x);
+}
+
+// ---------------------------------------------------------------------------
+// Packed serving: the same kernels over the fits of one step, block b of a
+// launch being map[b] = (fit, column, chunk) or (fit, element block, blocks
+// of that fit's grid).  A fit takes part only in the phase its kernel is for.
+// ---------------------------------------------------------------------------
+__global__ __launch_bounds__(NT, 2) void k_cg_update_packed(const VSlot* __restrict__ vs,
+                                                         const int4* __restrict__ map) {
+    griddep_launch();
+    griddep_wait();
+    const int4 m = map[blockIdx.x];
+    const VSlot& f = vs[m.x];
+    DevCtl* ctl = f.ctl;
+    if (ctl->phase != PH_CG) return;
+    const OpOut uo = f.uo;
+    cg_update_body(ctl, f.P, uo, f.alpha, f.minv, f.X, f.R, nullptr, f.Dp, f.nch, f.part, 0, 0, m.y, m.z);
+}
+
+__global__ __launch_bounds__(NT) void k_cg_direction_packed(const VSlot* __restrict__ vs,
+                                                            const int4* __restrict__ map) {
+    griddep_launch();
+    griddep_wait();
+    const int4 m = map[blockIdx.x];
+    const VSlot& f = vs[m.x];
+    DevCtl* ctl = f.ctl;
+    if (ctl->phase != PH_CG) return;
+    const SplitOut so = f.so;
+    cg_direction_body(ctl, f.R, f.alpha, f.minv, f.P, f.Dp, f.nch, f.part, 0, so, m.y, m.z);
+}
+
+// The M-step of the fits whose CG loop ended in this step (the direction
+// kernel continued no column, or the budget is spent) or was never entered.
+__global__ __launch_bounds__(NT) void k_mstep_packed(const VSlot* __restrict__ vs, const int4* __restrict__ map) {
+    const int4 m = map[blockIdx.x];
+    const VSlot& f = vs[m.x];
+    DevCtl* ctl = f.ctl;
+    const int ph = ctl->phase;
+    const bool go = ph == PH_START || (ph == PH_CG && !(ctl->any_active && ctl->u < ctl->maxit));
+    if (!go) return;
+    mstep_body(ctl, f.X, f.theta, f.alpha, f.minv, f.mu_out, f.s_out, f.iters, nullptr, f.D, f.Dp, f.counters + 4,
+               0, m.y, (unsigned)m.z);
+}
+
+// The initialisation of the next E-step of the fits the M-step left in PH_INIT.
+__global__ __launch_bounds__(NT) void k_cg_init_packed(const VSlot* __restrict__ vs, const int4* __restrict__ map) {
+    const int4 m = map[blockIdx.x];
+    const VSlot& f = vs[m.x];
+    DevCtl* ctl = f.ctl;
+    if (ctl->phase != PH_INIT) return;
+    const SplitOut so = f.so;
+    const OpOut uo = f.uo;
+    cg_init_body(ctl, f.b, f.minv, f.alpha, f.X, f.R, f.P, nullptr, f.D, f.Dp, f.nch, f.part, f.counters + 0, 0, so,
+                 uo, m.y, m.z, (unsigned)m.w);
+}
+
+// End of a packed step: status[i] = phase of fit i; the step loop goes on
+// (h_loop) unless a fit reached PH_DONE in this step, the host flagged new
+// fits to admit (*pending), or max_steps steps have run in this launch.
+__global__ void k_packed_status(const VSlot* __restrict__ vs, int n, int* status, const volatile int* pending,
+                                unsigned* steps, unsigned max_steps, cudaGraphConditionalHandle h_loop) {
+    __shared__ int s_done;
+    if (threadIdx.x == 0) s_done = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int ph = vs[i].ctl->phase;
+        if (ph == PH_DONE && status[i] != PH_DONE) s_done = 1;
+        status[i] = ph;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned k = *steps + 1;
+        *steps = k;
+        set_cond(h_loop, !s_done && *pending == 0 && k < max_steps);
     }
 }
 
@@ -594,4 +713,25 @@ void launch_check_finite(cudaStream_t st, const float* x, long long n, unsigned*
     long long blocks = (n + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     k_check_finite<<<(unsigned)blocks, 256, 0, st>>>(x, n, bad);
+}
+
+void launch_update_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks) {
+    s.launch_pdl(k_cg_update_packed, dim3(nblocks), dim3(NT), 0, vs, map);
+}
+
+void launch_direction_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks) {
+    s.launch_pdl(k_cg_direction_packed, dim3(nblocks), dim3(NT), 0, vs, map);
+}
+
+void launch_mstep_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks) {
+    s.launch(k_mstep_packed, dim3(nblocks), dim3(NT), 0, vs, map);
+}
+
+void launch_init_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks) {
+    s.launch(k_cg_init_packed, dim3(nblocks), dim3(NT), 0, vs, map);
+}
+
+void launch_packed_status(Sink& s, const VSlot* vs, int n, int* status, const volatile int* pending, unsigned* steps,
+                          unsigned max_steps, cudaGraphConditionalHandle h_loop) {
+    s.launch(k_packed_status, dim3(1), dim3(256), 0, vs, n, status, pending, steps, max_steps, h_loop);
 }

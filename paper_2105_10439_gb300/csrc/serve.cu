@@ -1,19 +1,38 @@
-// Serving loop: continuous batching of independent CoFEM fits.
+// Serving loop: continuous batching of CoFEM fits, in two modes.
 //
-// A server owns `max_slots` worker threads, each with its own CUDA stream.
-// Requests enter a FIFO queue; a worker takes the request at the head as soon
-// as it is idle and the request's device-memory estimate fits in what is left
-// of the HBM budget, then runs the whole fit (create -> one graph launch ->
-// results -> destroy) on its stream.  Fits of different workers overlap on the
-// GPU; a request that arrives while others run is admitted as soon as a slot
-// and memory free up.  Handle memory is stream-ordered, so finishing one
-// request never synchronises the device under the others.
+// Independent (cofem_server_create): a server owns `max_slots` worker
+// threads, each with its own CUDA stream.  Requests enter a FIFO queue; a
+// worker takes the request at the head as soon as it is idle and the
+// request's device-memory estimate fits in what is left of the HBM budget,
+// then runs the whole fit (create -> one graph launch -> results -> destroy)
+// on its stream.  Fits of different workers overlap on the GPU; a request
+// that arrives while others run is admitted as soon as a slot and memory free
+// up.  Handle memory is stream-ordered, so finishing one request never
+// synchronises the device under the others.
+//
+// Packed (cofem_server_create_packed): the CG steps of all admitted fits run
+// in shared launches.  Preparation threads create each request's handle and
+// run its prologue (dictionary images, b = beta Phi^T y, the first E-step's
+// initialisation) on the handle's own stream; an engine thread keeps the
+// prepared fits in one step: the packed GEMM applies the operator's first
+// product to every fit (each fit's units cut into fixed segments, the
+// segments of all fits spread over the CTAs), one kernel sums and splits T of
+// every fit, the packed GEMM applies the second product, and one launch each
+// of the CG update, the direction, the M-step (fits whose CG loop ended) and
+// the next E-step's initialisation follow.  The step is a CUDA graph whose
+// WHILE node repeats it on the device until a fit finishes, the host has new
+// fits to admit (a mapped host flag), or a step budget is spent; every fit
+// keeps its alpha, mu and CG state on the device throughout.  A fit's
+// segments do not depend on the others, so its results are the same bits
+// alone and in any mix.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <map>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -36,6 +55,34 @@ long long round_up_ll(long long x, long long m) { return (x + m - 1) / m * m; }
 
 }  // namespace
 
+namespace {
+
+// A prepared fit of the packed engine.
+struct PFit {
+    Job* job = nullptr;
+    cofem_ctx* h = nullptr;
+    PackedFit pf;
+    VSlot vs{};
+};
+
+// Device tables of one packed step (reallocated when they grow).
+struct StepTables {
+    TcSlot* sl[2][2] = {};   // [precision group][product]
+    TcSeg* sg[2][2] = {};
+    int* cta[2][2] = {};
+    size_t cap_sl[2][2] = {}, cap_sg[2][2] = {}, cap_cta[2][2] = {};
+    VSlot* vs = nullptr;
+    size_t cap_vs = 0;
+    int4* map[4] = {};       // vector blocks, T blocks, M-step blocks, (unused)
+    size_t cap_map[4] = {};
+    int* status = nullptr;
+    size_t cap_status = 0;
+    unsigned* steps = nullptr;   // steps of the current launch
+    unsigned* flags = nullptr;   // COFEM_FLAG_DEVICE_TIMEOUT of the packed GEMMs
+};
+
+}  // namespace
+
 struct cofem_server {
     int device = 0;
     long long budget = 0, in_use = 0;
@@ -48,6 +95,16 @@ struct cofem_server {
     std::condition_variable cv_work, cv_done;
     std::vector<std::thread> workers;
     int running = 0;
+    // packed mode
+    bool packed = false;
+    int max_fits = 0;          // fits in a step (preparing, ready and active together)
+    int num_sms = 0;
+    int in_flight = 0;         // preparing + ready + active
+    std::deque<PFit*> ready;   // prepared, waiting to join the step
+    std::thread engine;
+    std::condition_variable cv_engine;
+    volatile int* pending_h = nullptr;   // mapped host flag: new fits are ready
+    int* pending_d = nullptr;
 };
 
 extern "C" long long cofem_estimate_bytes(int kind, long long N, long long D, long long L, int precision, int K) {
@@ -139,7 +196,363 @@ void worker_loop(cofem_server* s) {
 
 }  // namespace
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// Packed mode
+// ---------------------------------------------------------------------------
+bool packed_eligible(const cofem_request& r, const char** why) {
+    if (r.kind != COFEM_OP_DENSE) return *why = "packed serving takes dense dictionaries", false;
+    if (r.precision != COFEM_BF16 && r.precision != COFEM_F32_TF32X3)
+        return *why = "packed serving takes COFEM_BF16 or COFEM_F32_TF32X3 dictionaries", false;
+    if (r.rr_period != 0) return *why = "packed serving runs without residual replacement", false;
+    const int Q = r.K + 1;
+    const int QS = r.precision == COFEM_BF16 ? (3 * Q + 15) / 16 * 16 : 2 * ((Q + 15) / 16 * 16);
+    if (QS > 128) return *why = "packed serving needs the split block in 128 rows (BF16: K <= 41)", false;
+    return true;
+}
+
+long long packed_estimate(const cofem_request& r) {
+    const long long Np = round_up_ll(r.N, 128), Dp = round_up_ll(r.D, 128), Q = r.K + 1;
+    const long long segs = (round_up_ll(Np, 512) / 512) * ((Dp / 64 + PK_SEGK - 1) / PK_SEGK) +
+                           (round_up_ll(Dp, 512) / 512) * ((Np / 64 + PK_SEGK - 1) / PK_SEGK);
+    return cofem_estimate_bytes(r.kind, r.N, r.D, r.L, r.precision, r.K) + segs * Q * 512 * 4;
+}
+
+void finish_job(cofem_server* s, Job* job, cofem_status stat, unsigned flags, const char* msg) {
+    job->t_end = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        job->result.status = stat;
+        job->result.flags = flags;
+        if (stat != COFEM_OK && msg) snprintf(job->result.message, sizeof(job->result.message), "%s", msg);
+        job->result.queue_ms = std::chrono::duration<double, std::milli>(job->t_start - job->t_submit).count();
+        job->result.run_ms = std::chrono::duration<double, std::milli>(job->t_end - job->t_start).count();
+        job->done = true;
+        s->in_use -= job->estimate;
+        --s->running;
+        --s->in_flight;
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+}
+
+// Preparation thread: create the handle, run the prologue, hand it to the engine.
+void prep_loop(cofem_server* s) {
+    cudaSetDevice(s->device);
+    for (;;) {
+        Job* job = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_work.wait(lk, [&] {
+                return s->stop || (!s->queue.empty() && s->in_use + s->queue.front()->estimate <= s->budget &&
+                                   s->in_flight < s->max_fits);
+            });
+            if (s->queue.empty() || s->in_use + s->queue.front()->estimate > s->budget ||
+                s->in_flight >= s->max_fits) {
+                if (s->stop) break;
+                continue;
+            }
+            job = s->queue.front();
+            s->queue.pop_front();
+            s->in_use += job->estimate;
+            ++s->running;
+            ++s->in_flight;
+        }
+        job->t_start = Clock::now();
+        const cofem_request& r = job->req;
+        cofem_opts o;
+        cofem_default_opts(&o);
+        o.precision = r.precision;
+        o.precond = r.precond;
+        o.conv = r.conv;
+        o.alpha_max = r.alpha_max > 0.0 ? r.alpha_max : 1e12;
+        o.seed = r.seed;
+        o.stream = nullptr;   // the handle's own stream
+        o.use_graph = 0;
+        o.prior = r.prior;
+        PFit* f = new PFit();
+        f->job = job;
+        cofem_status stat = cofem_create(&f->h, r.N, r.D, r.kind, r.phi, r.L, &o);
+        if (stat == COFEM_OK) stat = packed_prepare(f->h, r);
+        if (stat != COFEM_OK) {
+            const std::string msg = cofem_last_error();
+            cofem_destroy(f->h);
+            delete f;
+            finish_job(s, job, stat, 0u, msg.c_str());
+            continue;
+        }
+        tc_pack_describe(f->h, &f->pf);
+        tc_pack_vslot(f->h, &f->vs);
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->ready.push_back(f);
+            *s->pending_h = 1;
+        }
+        s->cv_engine.notify_all();
+    }
+}
+
+template <typename T>
+cudaError_t grow(T** p, size_t* cap, size_t n) {
+    if (n <= *cap && *p) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    const size_t c = std::max<size_t>(n, 16) * 2;
+    cudaError_t e = cudaMalloc((void**)p, c * sizeof(T));
+    if (e == cudaSuccess) *cap = c;
+    return e;
+}
+
+template <typename T>
+cudaError_t upload(T** p, size_t* cap, const std::vector<T>& v, cudaStream_t st) {
+    cudaError_t e = grow(p, cap, v.size());
+    if (e != cudaSuccess || v.empty()) return e;
+    return cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+// CTA ranges over a concatenated segment list: contiguous runs of about equal cost.
+std::vector<int> cta_ranges(const std::vector<double>& cost, int nCTA) {
+    double total = 0.0;
+    for (double c : cost) total += c;
+    std::vector<int> r(nCTA + 1, (int)cost.size());
+    r[0] = 0;
+    double acc = 0.0;
+    int c = 1;
+    for (size_t i = 0; i < cost.size() && c < nCTA; ++i) {
+        acc += cost[i];
+        while (c < nCTA && acc >= total * c / nCTA) r[c++] = (int)i + 1;
+    }
+    return r;
+}
+
+struct StepGraph {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    void reset() {
+        if (x) cudaGraphExecDestroy(x);
+        if (g) cudaGraphDestroy(g);
+        x = nullptr;
+        g = nullptr;
+    }
+};
+
+// Tables and graph of one packed step over `fits`.
+cudaError_t build_step(cofem_server* s, std::vector<PFit*>& fits, StepTables& tb, StepGraph& sg, cudaStream_t st,
+                       bool pdl) {
+    const int n = (int)fits.size();
+    struct Group {
+        std::vector<TcSlot> sl[2];
+        std::vector<TcSeg> seg[2];
+        std::vector<double> cost[2];
+        int QSmax = 16;
+    } grp[2];
+    for (int i = 0; i < n; ++i) {
+        PackedFit& pf = fits[i]->pf;
+        Group& G = grp[pf.tf ? 1 : 0];
+        for (int pr = 0; pr < 2; ++pr) {
+            const int idx = (int)G.sl[pr].size();
+            G.sl[pr].push_back(pr == 0 ? pf.g1 : pf.g2);
+            const std::vector<TcSeg>& src = pr == 0 ? pf.s1 : pf.s2;
+            const std::vector<double>& cs = pr == 0 ? pf.c1 : pf.c2;
+            for (size_t k = 0; k < src.size(); ++k) {
+                TcSeg x = src[k];
+                x.slot = idx;
+                G.seg[pr].push_back(x);
+                G.cost[pr].push_back(cs[k]);
+            }
+        }
+        G.QSmax = std::max(G.QSmax, pf.g1.QS);
+    }
+    std::vector<VSlot> vs(n);
+    std::vector<int4> mvec, mrt, mms;
+    for (int i = 0; i < n; ++i) {
+        const VSlot& v = fits[i]->vs;
+        vs[i] = v;
+        for (int q = 0; q < v.Q; ++q)
+            for (int ch = 0; ch < v.nch; ++ch) mvec.push_back(make_int4(i, q, ch, v.nch * v.Q));
+        const int nblk = (int)((v.Np + 1023) / 1024);
+        for (int q = 0; q < v.Q; ++q)
+            for (int ib = 0; ib < nblk; ++ib) mrt.push_back(make_int4(i, q, ib, 0));
+        const int mb = (int)((v.Dp + COFEM_VEC_THREADS - 1) / COFEM_VEC_THREADS);
+        for (int jb = 0; jb < mb; ++jb) mms.push_back(make_int4(i, jb, mb, 0));
+    }
+    cudaError_t e;
+    int ncta[2][2] = {};
+    for (int gi = 0; gi < 2; ++gi)
+        for (int pr = 0; pr < 2; ++pr) {
+            Group& G = grp[gi];
+            if (G.seg[pr].empty()) continue;
+            ncta[gi][pr] = std::min<int>(s->num_sms, (int)G.seg[pr].size());
+            const std::vector<int> r = cta_ranges(G.cost[pr], ncta[gi][pr]);
+            if ((e = upload(&tb.sl[gi][pr], &tb.cap_sl[gi][pr], G.sl[pr], st))) return e;
+            if ((e = upload(&tb.sg[gi][pr], &tb.cap_sg[gi][pr], G.seg[pr], st))) return e;
+            if ((e = upload(&tb.cta[gi][pr], &tb.cap_cta[gi][pr], r, st))) return e;
+        }
+    if ((e = upload(&tb.vs, &tb.cap_vs, vs, st))) return e;
+    if ((e = upload(&tb.map[0], &tb.cap_map[0], mvec, st))) return e;
+    if ((e = upload(&tb.map[1], &tb.cap_map[1], mrt, st))) return e;
+    if ((e = upload(&tb.map[2], &tb.cap_map[2], mms, st))) return e;
+    if ((e = grow(&tb.status, &tb.cap_status, (size_t)n))) return e;
+    if ((e = cudaMemsetAsync(tb.status, 0, (size_t)n * sizeof(int), st))) return e;
+    if (!tb.steps && (e = cudaMalloc((void**)&tb.steps, sizeof(unsigned)))) return e;
+    if (!tb.flags && (e = cudaMalloc((void**)&tb.flags, sizeof(unsigned)))) return e;
+    if ((e = cudaMemsetAsync(tb.flags, 0, sizeof(unsigned), st))) return e;
+    if ((e = cudaStreamSynchronize(st))) return e;   // the host vectors go out of scope
+
+    sg.reset();
+    if ((e = cudaGraphCreate(&sg.g, 0))) return e;
+    Sink root;
+    root.stream = st;
+    root.graph = sg.g;
+    root.pdl = pdl;
+    const cudaGraphConditionalHandle h = root.make_handle(1u, true);
+    Sink body = root.conditional(h, cudaGraphCondTypeWhile);
+    for (int pr = 0; pr < 2; ++pr) {
+        for (int gi = 0; gi < 2; ++gi) {
+            if (!ncta[gi][pr]) continue;
+            TcBatch b{};
+            b.slots = tb.sl[gi][pr];
+            b.segs = tb.sg[gi][pr];
+            b.cta_seg = tb.cta[gi][pr];
+            b.G = 4;
+            b.acc_stride = 128;
+            b.QSmax = grp[gi].QSmax;
+            b.flags = tb.flags;   // a timeout fails every fit of the step
+            launch_gemm_packed(body, gi == 1, b, ncta[gi][pr], tc_packed_smem(gi == 1, grp[gi].QSmax));
+        }
+        if (pr == 0) launch_reduce_T_packed(body, tb.vs, tb.map[1], (int)mrt.size());
+    }
+    launch_update_packed(body, tb.vs, tb.map[0], (int)mvec.size());
+    launch_direction_packed(body, tb.vs, tb.map[0], (int)mvec.size());
+    launch_mstep_packed(body, tb.vs, tb.map[2], (int)mms.size());
+    launch_init_packed(body, tb.vs, tb.map[0], (int)mvec.size());
+    // a launch runs at most 4096 steps before the host looks again
+    launch_packed_status(body, tb.vs, n, tb.status, s->pending_d, tb.steps, 4096u, h);
+    e = root.err ? root.err : body.err;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&sg.x, sg.g, 0);
+    return e;
+}
+
+void engine_loop(cofem_server* s) {
+    cudaSetDevice(s->device);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    StepTables tb;
+    StepGraph sg;
+    std::vector<PFit*> active;
+    std::vector<int> status;
+    bool pdl = true;
+    for (;;) {
+        bool changed = false;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_engine.wait(lk, [&] { return !s->ready.empty() || !active.empty() || (s->stop && s->in_flight == 0); });
+            if (active.empty() && s->ready.empty() && s->stop && s->in_flight == 0) break;
+            while (!s->ready.empty()) {
+                active.push_back(s->ready.front());
+                s->ready.pop_front();
+                changed = true;
+            }
+            *s->pending_h = 0;
+        }
+        cudaError_t e = cudaSuccess;
+        if (changed || !sg.x) {
+            e = build_step(s, active, tb, sg, st, pdl);
+            if (e != cudaSuccess && pdl) {   // programmatic edges refused: plain ones
+                (void)cudaGetLastError();
+                pdl = false;
+                e = build_step(s, active, tb, sg, st, pdl);
+            }
+        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(tb.steps, 0, sizeof(unsigned), st);
+        if (e == cudaSuccess) e = cudaGraphLaunch(sg.x, st);
+        status.assign(active.size(), PH_NONE);
+        unsigned dflags = 0;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(status.data(), tb.status, active.size() * sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&dflags, tb.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess || (dflags & COFEM_FLAG_DEVICE_TIMEOUT)) {   // every fit of the step fails
+            const char* msg = e != cudaSuccess ? cudaGetErrorString(e)
+                                               : "a bounded on-device wait timed out (packed tensor-core pipeline)";
+            (void)cudaGetLastError();
+            for (PFit* f : active) {
+                cofem_destroy(f->h);
+                finish_job(s, f->job, COFEM_ERR_CUDA, dflags, msg);
+                delete f;
+            }
+            active.clear();
+            sg.reset();
+            continue;
+        }
+        std::vector<PFit*> keep;
+        for (size_t i = 0; i < active.size(); ++i) {
+            PFit* f = active[i];
+            if (status[i] != PH_DONE) {
+                keep.push_back(f);
+                continue;
+            }
+            unsigned flags = 0;
+            const cofem_status stat = packed_finish(f->h, f->job->req, &flags);
+            const std::string msg = stat != COFEM_OK ? cofem_last_error() : "";
+            cofem_destroy(f->h);
+            finish_job(s, f->job, stat, flags, msg.c_str());
+            delete f;
+        }
+        if (keep.size() != active.size()) {
+            active.swap(keep);
+            sg.reset();   // rebuilt for the new set
+        }
+    }
+    sg.reset();
+    for (int gi = 0; gi < 2; ++gi)
+        for (int pr = 0; pr < 2; ++pr) {
+            if (tb.sl[gi][pr]) cudaFree(tb.sl[gi][pr]);
+            if (tb.sg[gi][pr]) cudaFree(tb.sg[gi][pr]);
+            if (tb.cta[gi][pr]) cudaFree(tb.cta[gi][pr]);
+        }
+    if (tb.vs) cudaFree(tb.vs);
+    for (auto* m : tb.map)
+        if (m) cudaFree(m);
+    if (tb.status) cudaFree(tb.status);
+    if (tb.steps) cudaFree(tb.steps);
+    if (tb.flags) cudaFree(tb.flags);
+    cudaStreamDestroy(st);
+}
+
+}  // namespace
+
 extern "C" {
+
+cofem_status cofem_server_create_packed(cofem_server** out, long long hbm_budget_bytes, int max_fits,
+                                        int prep_threads) {
+    if (!out || hbm_budget_bytes <= 0 || max_fits < 1 || max_fits > 1024 || prep_threads < 1 || prep_threads > 64)
+        return cofem_set_error(COFEM_ERR_INVALID_ARG,
+                               "need out, hbm_budget_bytes > 0, 1 <= max_fits <= 1024, 1 <= prep_threads <= 64");
+    cofem_server* s = new cofem_server();
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
+    int* hp = nullptr;
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&hp, sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&s->pending_d, hp, 0);
+    if (e != cudaSuccess) {
+        if (hp) cudaFreeHost(hp);
+        delete s;
+        return cofem_set_error(COFEM_ERR_CUDA, cudaGetErrorString(e));
+    }
+    *hp = 0;
+    s->pending_h = hp;
+    s->packed = true;
+    s->budget = hbm_budget_bytes;
+    s->max_fits = max_fits;
+    s->max_slots = prep_threads;
+    for (int i = 0; i < prep_threads; ++i) s->workers.emplace_back(prep_loop, s);
+    s->engine = std::thread(engine_loop, s);
+    *out = s;
+    return COFEM_OK;
+}
 
 cofem_status cofem_server_create(cofem_server** out, long long hbm_budget_bytes, int max_slots) {
     if (!out || hbm_budget_bytes <= 0 || max_slots < 1 || max_slots > 256)
@@ -161,9 +574,14 @@ cofem_status cofem_submit(cofem_server* s, const cofem_request* r, unsigned long
     if (!s || !r || !ticket) return cofem_set_error(COFEM_ERR_INVALID_ARG, "NULL argument");
     if (!r->phi || !r->y || !r->mu || !r->s || !r->alpha || r->N < 1 || r->D < 1 || r->K < 1 || r->T_em < 1)
         return cofem_set_error(COFEM_ERR_INVALID_ARG, "incomplete request");
+    if (s->packed) {
+        const char* why = nullptr;
+        if (!packed_eligible(*r, &why)) return cofem_set_error(COFEM_ERR_UNSUPPORTED, why);
+    }
     Job* job = new Job();
     job->req = *r;
-    job->estimate = cofem_estimate_bytes(r->kind, r->N, r->D, r->L, r->precision, r->K);
+    job->estimate = s->packed ? packed_estimate(*r)
+                              : cofem_estimate_bytes(r->kind, r->N, r->D, r->L, r->precision, r->K);
     if (job->estimate > s->budget) {
         delete job;
         return cofem_set_error(COFEM_ERR_NOMEM, "request needs more device memory than the server's whole budget");
@@ -217,8 +635,11 @@ cofem_status cofem_server_destroy(cofem_server* s) {
         s->stop = true;
     }
     s->cv_work.notify_all();
+    s->cv_engine.notify_all();
     for (auto& t : s->workers) t.join();
+    if (s->engine.joinable()) s->engine.join();
     for (auto& kv : s->jobs) delete kv.second;
+    if (s->pending_h) cudaFreeHost((void*)s->pending_h);
     delete s;
     return COFEM_OK;
 }
