@@ -551,7 +551,7 @@ def run_ours(args):
     if prob.kind == "dense" and not args.no_conv_form and ws == 1:
         line["convolution_form"] = convolution_report(cf, dev, args)
     if args.serve_requests > 0 and ws == 1:
-        line["serving"] = serving_report(cf, dev, args.serve_requests, run["precision"])
+        line["serving"] = serving_report(cf, dev, args.serve_requests, run["precision"], args.serve_mode)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = _cpu_baseline(prob, run, avg_iters=float(np.mean(all_iters[-1])))
     if rank == 0:
@@ -600,7 +600,7 @@ def convolution_report(cf, dev, args, name="toeplitz_d1e6_l256_k16"):
 
 
 def serving_run(cf, dev, n, precision, rate_hz=None, slots=16, budget_bytes=96 << 30, seed=1000, max_sms=0,
-                window=48):
+                window=48, mode="packed", max_fits=64, prep_threads=4):
     """Continuous-batching serving: n requests through cofem_submit/cofem_wait.
 
     Requests follow synth.serving_requests (D ~ U[1024, 16384], N = D/4, 3 %
@@ -610,24 +610,38 @@ def serving_run(cf, dev, n, precision, rate_hz=None, slots=16, budget_bytes=96 <
     fit in memory at once) and freed when it completes.  With rate_hz None the
     requests are submitted back to back, at most `window` in flight
     (capacity); otherwise each is submitted at its Poisson arrival time.
-    Latency = submit -> results written, measured by the server."""
+    Latency = submit -> results written, measured by the server.  mode
+    "packed": cofem_server_create_packed (the CG steps of up to max_fits
+    admitted fits in shared launches); "independent": cofem_server_create
+    (one fit per worker stream, `slots` workers)."""
     import collections
     import torch
     from synth import serving_requests
     reqs = serving_requests(n, base_seed=seed, rate_hz=rate_hz or 1.0)
     prec = _PRECISIONS[precision](cf)
-    srv = cf.cofem_server_create(budget_bytes, slots)
+    if mode == "packed":
+        srv = cf.cofem_server_create_packed(budget_bytes, max_fits, prep_threads)
+        window = max(window, 2 * max_fits)
+    else:
+        srv = cf.cofem_server_create(budget_bytes, slots)
     inflight = collections.deque()
     results, nm = [], []
+
+    # the client works on a stream of the highest priority (generating each
+    # request, scoring each result): on the default stream its kernels would
+    # queue behind the server's (every SM busy) and the client, not the
+    # server, would set the rate
+    gen = torch.cuda.Stream(device=dev, priority=-1)
 
     def finish(item):
         t, o = item
         x = cf.cofem_wait(srv, t)
         results.append(x)
         if x.status == 0:
-            z = torch.zeros_like(o["mu"])
-            z[o["idx"]] = o["zv"]
-            nm.append(20.0 * math.log10(float((o["mu"] - z).norm() / z.norm())))
+            with torch.cuda.stream(gen):
+                z = torch.zeros_like(o["mu"])
+                z[o["idx"]] = o["zv"]
+                nm.append(20.0 * math.log10(float((o["mu"] - z).norm() / z.norm())))
 
     t0 = time.perf_counter()
     for r in reqs:
@@ -638,52 +652,61 @@ def serving_run(cf, dev, n, precision, rate_hz=None, slots=16, budget_bytes=96 <
         elif len(inflight) >= window:
             finish(inflight.popleft())
         D, N = r["D"], r["N"]
-        g = torch.Generator(device=dev)
-        g.manual_seed(r["seed"])
-        phi = torch.randn(N, D, generator=g, device=dev) / math.sqrt(N)
-        d = r["d"]
-        idx = torch.randperm(D, generator=g, device=dev)[:d]
-        zv = torch.randn(d, generator=g, device=dev)
-        clean = phi[:, idx] @ zv
-        sigma2 = float(clean.square().sum()) / (N * 10.0 ** (r["snr_db"] / 10.0))
-        y = (clean + torch.randn(N, generator=g, device=dev) * math.sqrt(sigma2)).contiguous()
+        with torch.cuda.stream(gen):
+            g = torch.Generator(device=dev)
+            g.manual_seed(r["seed"])
+            phi = torch.randn(N, D, generator=g, device=dev) / math.sqrt(N)
+            d = r["d"]
+            idx = torch.randperm(D, generator=g, device=dev)[:d]
+            zv = torch.randn(d, generator=g, device=dev)
+            clean = phi[:, idx] @ zv
+            sigma2 = float(clean.square().sum()) / (N * 10.0 ** (r["snr_db"] / 10.0))
+            y = (clean + torch.randn(N, generator=g, device=dev) * math.sqrt(sigma2)).contiguous()
         o = dict(phi=phi, y=y, mu=torch.empty(D, device=dev), s=torch.empty(D, device=dev),
                  alpha=torch.empty(D, device=dev), it=torch.empty(r["T"], dtype=torch.int32, device=dev),
                  idx=idx, zv=zv)
         o["req"] = cf.make_request(cf.COFEM_OP_DENSE, N, D, phi, y, 1.0 / sigma2, r["K"], r["T"], 1e-5, 400,
                                    o["mu"], o["s"], o["alpha"], o["it"], precision=prec, seed=r["seed"],
                                    max_sms=max_sms)
-        torch.cuda.current_stream(dev).synchronize()   # the request's inputs are written
+        gen.synchronize()   # the request's inputs are written
         inflight.append((cf.cofem_submit(srv, o["req"]), o))
         while inflight and cf.cofem_poll(srv, inflight[0][0]):
             finish(inflight.popleft())
     while inflight:
         finish(inflight.popleft())
     makespan = time.perf_counter() - t0
+    stats = cf.cofem_server_get_stats(srv)
     cf.cofem_server_destroy(srv)
     lat = np.array([x.queue_ms + x.run_ms for x in results])
     ok = sum(1 for x in results if x.status == 0)
     errors = sorted({x.message.decode(errors="replace") for x in results if x.status != 0})
-    return {"requests": n, "ok": ok, "precision": precision, "slots": slots, "window": None if rate_hz else window,
+    return {"requests": n, "ok": ok, "precision": precision, "mode": mode,
+            "slots": max_fits if mode == "packed" else slots, "window": None if rate_hz else window,
             "offered_rate_hz": rate_hz, "solves_per_s": n / makespan,
             "em_iters_per_s": sum(r["T"] for r in reqs) / makespan,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_nmse_db": float(np.mean(nm)) if nm else None, "makespan_s": makespan,
             "dictionaries": "one per request, generated on the device from its seed (D unsnapped)",
+            "packed": ({"launches": stats["launches"], "steps": stats["steps"],
+                        "mean_fits_per_step": stats["fit_steps"] / max(1, stats["steps"]),
+                        "graphs_built": stats["graphs_built"]} if mode == "packed" else None),
             "errors": errors[:3]}
 
 
-def serving_report(cf, dev, n, precision):
-    """Capacity at saturation, then p50/p99 at 80 % of that capacity."""
-    sat = serving_run(cf, dev, n, precision, rate_hz=None)
-    load = serving_run(cf, dev, n, precision, rate_hz=0.8 * sat["solves_per_s"])
+def serving_report(cf, dev, n, precision, mode="packed"):
+    """Capacity at saturation, then p50/p99 at 80 % of that capacity.  The
+    packed server takes FP32 dictionaries in the tensor-core 3xTF32 form."""
+    if mode == "packed" and precision == "f32":
+        precision = "tf32x3"
+    sat = serving_run(cf, dev, n, precision, rate_hz=None, mode=mode)
+    load = serving_run(cf, dev, n, precision, rate_hz=0.8 * sat["solves_per_s"], mode=mode)
     return {"saturation": sat, "at_80pct": load}
 
 
-def serving_config5(cf, dev, n, precisions):
+def serving_config5(cf, dev, n, precisions, mode="packed"):
     """The serving configuration as a whole: capacity and p50/p99 at 80 % of
     capacity for each storage precision of the dictionary."""
-    return {p: serving_report(cf, dev, n, p) for p in precisions}
+    return {p: serving_report(cf, dev, n, p, mode) for p in precisions}
 
 
 def run_operator_only(args):
@@ -769,6 +792,8 @@ def _parser():
                     help="only the serving measurement (2000 requests unless --serve-requests is given)")
     ap.add_argument("--serve-precision", default="bf16",
                     help="comma-separated dictionary precisions of the serving run (f32, bf16, tf32x3, fp8)")
+    ap.add_argument("--serve-mode", default="packed", choices=["packed", "independent"],
+                    help="serving loop: packed CG steps of all admitted fits, or one fit per worker stream")
     ap.add_argument("--cpu-budget", type=float, default=60.0,
                     help="seconds of oracle time the reference arm's timed steps take in total")
     ap.add_argument("--dense-path", default="auto", choices=sorted(_DENSE_PATHS),
@@ -800,7 +825,7 @@ def main():
         dev = torch.device("cuda", 0)
         n = args.serve_requests if "--serve-requests" in sys.argv else 2000
         precs = args.serve_precision.split(",")
-        rep = serving_config5(cf, dev, n, precs)
+        rep = serving_config5(cf, dev, n, precs, args.serve_mode)
         print(json.dumps({"serving": rep, "metric": "CoFEM serving p50/p99 ms at 80% of capacity",
                           "value": rep[precs[0]]["at_80pct"]["p99_ms"], "unit": "ms (p99)"}), flush=True)
     elif args.operator_only:

@@ -377,6 +377,15 @@ cofem_status cofem_server_create(cofem_server** out, long long hbm_budget_bytes,
 cofem_status cofem_server_create_packed(cofem_server** out, long long hbm_budget_bytes, int max_fits,
                                         int prep_threads);
 
+/* Counters of a packed server (zero for an independent one): graph launches
+ * of the step loop, steps run, fit-steps (the sum over steps of the fits in
+ * the step: fit_steps / steps is the mean number of fits a step serves), and
+ * step graphs built (once per table capacity and dictionary-precision mix). */
+typedef struct cofem_server_stats {
+    long long launches, steps, fit_steps, graphs_built;
+} cofem_server_stats;
+cofem_status cofem_server_get_stats(cofem_server* srv, cofem_server_stats* out);
+
 /* Queue a request (never blocks on the GPU).  *ticket identifies it.  Errors:
  * INVALID_ARG (incomplete request), NOMEM (needs more than the whole budget),
  * UNSUPPORTED (a packed server and a request it does not take). */

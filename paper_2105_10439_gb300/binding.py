@@ -92,6 +92,11 @@ class cofem_result(C.Structure):
                 ("message", C.c_char * 160)]
 
 
+class cofem_server_stats(C.Structure):
+    _fields_ = [("launches", C.c_longlong), ("steps", C.c_longlong), ("fit_steps", C.c_longlong),
+                ("graphs_built", C.c_longlong)]
+
+
 class CofemError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"libcofem status {status}: {message}")
@@ -131,6 +136,7 @@ def _load():
         "cofem_estimate_bytes": (ll, [i, ll, ll, ll, i, i]),
         "cofem_server_create": (i, [C.POINTER(vp), ll, i]),
         "cofem_server_create_packed": (i, [C.POINTER(vp), ll, i, i]),
+        "cofem_server_get_stats": (i, [vp, C.POINTER(cofem_server_stats)]),
         "cofem_submit": (i, [vp, C.POINTER(cofem_request), C.POINTER(C.c_ulonglong)]),
         "cofem_poll": (i, [vp, C.c_ulonglong, C.POINTER(i)]),
         "cofem_wait": (i, [vp, C.c_ulonglong, C.POINTER(cofem_result)]),
@@ -265,6 +271,12 @@ def cofem_server_create_packed(hbm_budget_bytes: int, max_fits: int, prep_thread
     h = C.c_void_p()
     _check(lib.cofem_server_create_packed(C.byref(h), int(hbm_budget_bytes), int(max_fits), int(prep_threads)))
     return h.value
+
+
+def cofem_server_get_stats(srv: int) -> dict:
+    st = cofem_server_stats()
+    _check(lib.cofem_server_get_stats(srv, C.byref(st)))
+    return {k: getattr(st, k) for k, _ in cofem_server_stats._fields_}
 
 
 def make_request(kind, N, D, phi, y, beta, K, T_em, cg_tol, cg_maxit, mu, s, alpha, cg_iters=None, L=0,

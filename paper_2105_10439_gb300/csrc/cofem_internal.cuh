@@ -698,12 +698,13 @@ void tc_pack_describe(cofem_ctx* c, PackedFit* out);
 void tc_pack_vslot(cofem_ctx* c, VSlot* out);
 size_t tc_packed_smem(bool tf, int QSmax);
 void launch_gemm_packed(Sink& s, bool tf, const TcBatch& b, int nCTA, size_t smem);
-void launch_reduce_T_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks);
-void launch_update_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks);
-void launch_direction_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks);
-void launch_mstep_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks);
-void launch_init_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks);
-void launch_packed_status(Sink& s, const VSlot* vs, int n, int* status, const volatile int* pending,
+// grids are sized for a capacity (nblocks); blocks at or beyond *count return
+void launch_reduce_T_packed(Sink& s, const VSlot* vs, const int4* map, const int* count, int nblocks);
+void launch_update_packed(Sink& s, const VSlot* vs, const int4* map, const int* count, int nblocks);
+void launch_direction_packed(Sink& s, const VSlot* vs, const int4* map, const int* count, int nblocks);
+void launch_mstep_packed(Sink& s, const VSlot* vs, const int4* map, const int* count, int nblocks);
+void launch_init_packed(Sink& s, const VSlot* vs, const int4* map, const int* count, int nblocks);
+void launch_packed_status(Sink& s, const VSlot* vs, const int* nfits, int* status, const volatile int* pending,
                           unsigned* steps, unsigned max_steps, cudaGraphConditionalHandle h_loop);
 // fit prologue up to the first E-step's initialisation, and the epilogue
 cofem_status packed_prepare(cofem_ctx* c, const cofem_request& r);

@@ -466,6 +466,9 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc_packed(TcBatch p)
                               smem_u32(b_full + slot));
                     ++nb;
                     const long long u = (long long)sg.g * sl.K_tiles + k;
+                    // BF16: the unit's row tiles that hold rows (the image's
+                    // tiles past the last row are zero and never multiplied)
+                    const uint32_t a_bytes = TF ? E_BYTES : (uint32_t)valid * TC_A_BYTES;
                     for (int r = 0; r < (TF ? valid : 1); ++r) {
                         slot = (int)(na % NE);
                         use = na / NE;
@@ -473,9 +476,9 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc_packed(TcBatch p)
                             ok = false;
                             break;
                         }
-                        mbar_expect_tx(smem_u32(a_full + slot), E_BYTES);
+                        mbar_expect_tx(smem_u32(a_full + slot), a_bytes);
                         bulk_load_hint(smem_u32(ringA + slot * E_BYTES), sl.A + ((size_t)u * p.G + r) * TC_A_BYTES,
-                                       E_BYTES, smem_u32(a_full + slot), evict_first);
+                                       a_bytes, smem_u32(a_full + slot), evict_first);
                         ++na;
                     }
                     if (!ok) break;
@@ -967,8 +970,10 @@ __global__ __launch_bounds__(256) void k_tc_reduce_T(const float* __restrict__ p
 
 // Packed serving: block b = (fit, column, 1024-row block) map[b] of the fits
 // in their CG loop (the operator's first product -> split(T), ||T||^2 partials).
-__global__ __launch_bounds__(256) void k_reduce_T_packed(const VSlot* __restrict__ vs, const int4* __restrict__ map) {
+__global__ __launch_bounds__(256) void k_reduce_T_packed(const VSlot* __restrict__ vs, const int4* __restrict__ map,
+                                                         const int* __restrict__ count) {
     griddep_launch();
+    if ((int)blockIdx.x >= *count) return;   // the grid is sized for the server's capacity
     griddep_wait();
     const int4 m = map[blockIdx.x];
     const VSlot& f = vs[m.x];
@@ -1367,7 +1372,7 @@ cudaError_t pack_product(TcPlan* t, const GemmPlan& gp, bool tf, int Q, std::vec
         for (int sgi = 0; sgi < spg; ++sgi) {
             const int k0 = sgi * PK_SEGK, k1 = std::min(K_tiles, k0 + PK_SEGK);
             segs.push_back(TcSeg{0, g, k0, k1, g * spg + sgi});
-            cost.push_back((double)(k1 - k0) * (tf ? valid : G) * TC_A_BYTES);
+            cost.push_back((double)(k1 - k0) * valid * TC_A_BYTES);
         }
     }
     const size_t part_elems = segs.size() * (size_t)Q * G * TC_BM;
@@ -1453,6 +1458,6 @@ void launch_gemm_packed(Sink& s, bool tf, const TcBatch& b, int nCTA, size_t sme
     else s.launch_pdl(k_gemm_tc_packed<false>, dim3(nCTA), dim3(tc_threads(false)), smem, b);
 }
 
-void launch_reduce_T_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks) {
-    s.launch_pdl(k_reduce_T_packed, dim3(nblocks), dim3(256), 0, vs, map);
+void launch_reduce_T_packed(Sink& s, const VSlot* vs, const int4* map, const int* count, int nblocks) {
+    s.launch_pdl(k_reduce_T_packed, dim3(nblocks), dim3(256), 0, vs, map, count);
 }

@@ -537,9 +537,10 @@ __global__ __launch_bounds__(NT) void k_mstep(DevCtl* ctl, const float* __restri
 // launch being map[b] = (fit, column, chunk) or (fit, element block, blocks
 // of that fit's grid).  A fit takes part only in the phase its kernel is for.
 // ---------------------------------------------------------------------------
-__global__ __launch_bounds__(NT, 2) void k_cg_update_packed(const VSlot* __restrict__ vs,
-                                                         const int4* __restrict__ map) {
+__global__ __launch_bounds__(NT, 2) void k_cg_update_packed(const VSlot* __restrict__ vs, const int4* __restrict__ map,
+                                                            const int* __restrict__ count) {
     griddep_launch();
+    if ((int)blockIdx.x >= *count) return;   // the grid is sized for the server's capacity
     griddep_wait();
     const int4 m = map[blockIdx.x];
     const VSlot& f = vs[m.x];
@@ -549,9 +550,10 @@ __global__ __launch_bounds__(NT, 2) void k_cg_update_packed(const VSlot* __restr
     cg_update_body(ctl, f.P, uo, f.alpha, f.minv, f.X, f.R, nullptr, f.Dp, f.nch, f.part, 0, 0, m.y, m.z);
 }
 
-__global__ __launch_bounds__(NT) void k_cg_direction_packed(const VSlot* __restrict__ vs,
-                                                            const int4* __restrict__ map) {
+__global__ __launch_bounds__(NT) void k_cg_direction_packed(const VSlot* __restrict__ vs, const int4* __restrict__ map,
+                                                            const int* __restrict__ count) {
     griddep_launch();
+    if ((int)blockIdx.x >= *count) return;   // the grid is sized for the server's capacity
     griddep_wait();
     const int4 m = map[blockIdx.x];
     const VSlot& f = vs[m.x];
@@ -563,7 +565,9 @@ __global__ __launch_bounds__(NT) void k_cg_direction_packed(const VSlot* __restr
 
 // The M-step of the fits whose CG loop ended in this step (the direction
 // kernel continued no column, or the budget is spent) or was never entered.
-__global__ __launch_bounds__(NT) void k_mstep_packed(const VSlot* __restrict__ vs, const int4* __restrict__ map) {
+__global__ __launch_bounds__(NT) void k_mstep_packed(const VSlot* __restrict__ vs, const int4* __restrict__ map,
+                                                     const int* __restrict__ count) {
+    if ((int)blockIdx.x >= *count) return;
     const int4 m = map[blockIdx.x];
     const VSlot& f = vs[m.x];
     DevCtl* ctl = f.ctl;
@@ -575,7 +579,9 @@ __global__ __launch_bounds__(NT) void k_mstep_packed(const VSlot* __restrict__ v
 }
 
 // The initialisation of the next E-step of the fits the M-step left in PH_INIT.
-__global__ __launch_bounds__(NT) void k_cg_init_packed(const VSlot* __restrict__ vs, const int4* __restrict__ map) {
+__global__ __launch_bounds__(NT) void k_cg_init_packed(const VSlot* __restrict__ vs, const int4* __restrict__ map,
+                                                       const int* __restrict__ count) {
+    if ((int)blockIdx.x >= *count) return;
     const int4 m = map[blockIdx.x];
     const VSlot& f = vs[m.x];
     DevCtl* ctl = f.ctl;
@@ -589,11 +595,13 @@ __global__ __launch_bounds__(NT) void k_cg_init_packed(const VSlot* __restrict__
 // End of a packed step: status[i] = phase of fit i; the step loop goes on
 // (h_loop) unless a fit reached PH_DONE in this step, the host flagged new
 // fits to admit (*pending), or max_steps steps have run in this launch.
-__global__ void k_packed_status(const VSlot* __restrict__ vs, int n, int* status, const volatile int* pending,
-                                unsigned* steps, unsigned max_steps, cudaGraphConditionalHandle h_loop) {
+__global__ void k_packed_status(const VSlot* __restrict__ vs, const int* __restrict__ nfits, int* status,
+                                const volatile int* pending, unsigned* steps, unsigned max_steps,
+                                cudaGraphConditionalHandle h_loop) {
     __shared__ int s_done;
     if (threadIdx.x == 0) s_done = 0;
     __syncthreads();
+    const int n = *nfits;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int ph = vs[i].ctl->phase;
         if (ph == PH_DONE && status[i] != PH_DONE) s_done = 1;
@@ -715,23 +723,23 @@ void launch_check_finite(cudaStream_t st, const float* x, long long n, unsigned*
     k_check_finite<<<(unsigned)blocks, 256, 0, st>>>(x, n, bad);
 }
 
-void launch_update_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks) {
-    s.launch_pdl(k_cg_update_packed, dim3(nblocks), dim3(NT), 0, vs, map);
+void launch_update_packed(Sink& s, const VSlot* vs, const int4* map, const int* count, int nblocks) {
+    s.launch_pdl(k_cg_update_packed, dim3(nblocks), dim3(NT), 0, vs, map, count);
 }
 
-void launch_direction_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks) {
-    s.launch_pdl(k_cg_direction_packed, dim3(nblocks), dim3(NT), 0, vs, map);
+void launch_direction_packed(Sink& s, const VSlot* vs, const int4* map, const int* count, int nblocks) {
+    s.launch_pdl(k_cg_direction_packed, dim3(nblocks), dim3(NT), 0, vs, map, count);
 }
 
-void launch_mstep_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks) {
-    s.launch(k_mstep_packed, dim3(nblocks), dim3(NT), 0, vs, map);
+void launch_mstep_packed(Sink& s, const VSlot* vs, const int4* map, const int* count, int nblocks) {
+    s.launch(k_mstep_packed, dim3(nblocks), dim3(NT), 0, vs, map, count);
 }
 
-void launch_init_packed(Sink& s, const VSlot* vs, const int4* map, int nblocks) {
-    s.launch(k_cg_init_packed, dim3(nblocks), dim3(NT), 0, vs, map);
+void launch_init_packed(Sink& s, const VSlot* vs, const int4* map, const int* count, int nblocks) {
+    s.launch(k_cg_init_packed, dim3(nblocks), dim3(NT), 0, vs, map, count);
 }
 
-void launch_packed_status(Sink& s, const VSlot* vs, int n, int* status, const volatile int* pending, unsigned* steps,
-                          unsigned max_steps, cudaGraphConditionalHandle h_loop) {
-    s.launch(k_packed_status, dim3(1), dim3(256), 0, vs, n, status, pending, steps, max_steps, h_loop);
+void launch_packed_status(Sink& s, const VSlot* vs, const int* nfits, int* status, const volatile int* pending,
+                          unsigned* steps, unsigned max_steps, cudaGraphConditionalHandle h_loop) {
+    s.launch(k_packed_status, dim3(1), dim3(256), 0, vs, nfits, status, pending, steps, max_steps, h_loop);
 }

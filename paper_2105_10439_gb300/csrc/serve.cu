@@ -32,6 +32,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <queue>
 #include <string>
 #include <thread>
 #include <vector>
@@ -61,22 +62,24 @@ namespace {
 struct PFit {
     Job* job = nullptr;
     cofem_ctx* h = nullptr;
+    cudaStream_t st = nullptr;   // the handle's stream (high priority: preparation is not starved by the step)
     PackedFit pf;
     VSlot vs{};
 };
 
-// Device tables of one packed step (reallocated when they grow).
+// Device tables of the packed step, sized for a capacity: the step's CUDA
+// graph is built for the capacities and reads the counts, so admitting or
+// retiring a fit only rewrites the tables (the graph is rebuilt only when a
+// capacity grows).
 struct StepTables {
+    int cap_fits = 0, cap_blk[3] = {}, cap_seg[2][2] = {}, cap_sl[2][2] = {};
     TcSlot* sl[2][2] = {};   // [precision group][product]
     TcSeg* sg[2][2] = {};
-    int* cta[2][2] = {};
-    size_t cap_sl[2][2] = {}, cap_sg[2][2] = {}, cap_cta[2][2] = {};
+    int* cta[2][2] = {};     // num_sms + 1 entries each
     VSlot* vs = nullptr;
-    size_t cap_vs = 0;
-    int4* map[4] = {};       // vector blocks, T blocks, M-step blocks, (unused)
-    size_t cap_map[4] = {};
+    int4* map[3] = {};       // vector blocks, T blocks, M-step blocks
+    int* counts = nullptr;   // blocks of each map, then fits
     int* status = nullptr;
-    size_t cap_status = 0;
     unsigned* steps = nullptr;   // steps of the current launch
     unsigned* flags = nullptr;   // COFEM_FLAG_DEVICE_TIMEOUT of the packed GEMMs
 };
@@ -105,6 +108,7 @@ struct cofem_server {
     std::condition_variable cv_engine;
     volatile int* pending_h = nullptr;   // mapped host flag: new fits are ready
     int* pending_d = nullptr;
+    cofem_server_stats stats{};
 };
 
 extern "C" long long cofem_estimate_bytes(int kind, long long N, long long D, long long L, int precision, int K) {
@@ -268,16 +272,27 @@ void prep_loop(cofem_server* s) {
         o.conv = r.conv;
         o.alpha_max = r.alpha_max > 0.0 ? r.alpha_max : 1e12;
         o.seed = r.seed;
-        o.stream = nullptr;   // the handle's own stream
         o.use_graph = 0;
         o.prior = r.prior;
         PFit* f = new PFit();
         f->job = job;
-        cofem_status stat = cofem_create(&f->h, r.N, r.D, r.kind, r.phi, r.L, &o);
+        // the preparation's kernels run while the step loop keeps every SM
+        // busy: a stream of the highest priority gets them scheduled first
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        cofem_status stat = COFEM_OK;
+        if (cudaStreamCreateWithPriority(&f->st, cudaStreamNonBlocking, hi) != cudaSuccess) {
+            (void)cudaGetLastError();
+            f->st = nullptr;
+            stat = cofem_set_error(COFEM_ERR_CUDA, "cudaStreamCreateWithPriority");
+        }
+        o.stream = f->st;
+        if (stat == COFEM_OK) stat = cofem_create(&f->h, r.N, r.D, r.kind, r.phi, r.L, &o);
         if (stat == COFEM_OK) stat = packed_prepare(f->h, r);
         if (stat != COFEM_OK) {
             const std::string msg = cofem_last_error();
             cofem_destroy(f->h);
+            if (f->st) cudaStreamDestroy(f->st);
             delete f;
             finish_job(s, job, stat, 0u, msg.c_str());
             continue;
@@ -293,37 +308,33 @@ void prep_loop(cofem_server* s) {
     }
 }
 
-template <typename T>
-cudaError_t grow(T** p, size_t* cap, size_t n) {
-    if (n <= *cap && *p) return cudaSuccess;
-    if (*p) cudaFree(*p);
-    *p = nullptr;
-    *cap = 0;
-    const size_t c = std::max<size_t>(n, 16) * 2;
-    cudaError_t e = cudaMalloc((void**)p, c * sizeof(T));
-    if (e == cudaSuccess) *cap = c;
-    return e;
-}
-
-template <typename T>
-cudaError_t upload(T** p, size_t* cap, const std::vector<T>& v, cudaStream_t st) {
-    cudaError_t e = grow(p, cap, v.size());
-    if (e != cudaSuccess || v.empty()) return e;
-    return cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
-}
-
-// CTA ranges over a concatenated segment list: contiguous runs of about equal cost.
-std::vector<int> cta_ranges(const std::vector<double>& cost, int nCTA) {
-    double total = 0.0;
-    for (double c : cost) total += c;
-    std::vector<int> r(nCTA + 1, (int)cost.size());
-    r[0] = 0;
-    double acc = 0.0;
-    int c = 1;
-    for (size_t i = 0; i < cost.size() && c < nCTA; ++i) {
-        acc += cost[i];
-        while (c < nCTA && acc >= total * c / nCTA) r[c++] = (int)i + 1;
+// Segments to CTAs, longest first to the least loaded CTA (the LPT rule:
+// every CTA within one segment's cost of the others); `seg` is reordered so
+// that CTA c's segments are seg[r[c] .. r[c + 1]).
+std::vector<int> assign_ctas(std::vector<TcSeg>& seg, const std::vector<double>& cost, int nCTA) {
+    std::vector<int> order(seg.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    using Load = std::pair<double, int>;   // (bytes so far, CTA)
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int c = 0; c < nCTA; ++c) heap.push({0.0, c});
+    std::vector<std::vector<int>> mine(nCTA);
+    for (int i : order) {
+        Load l = heap.top();
+        heap.pop();
+        mine[l.second].push_back(i);
+        l.first += cost[i];
+        heap.push(l);
     }
+    std::vector<TcSeg> out;
+    out.reserve(seg.size());
+    std::vector<int> r(nCTA + 1, 0);
+    for (int c = 0; c < nCTA; ++c) {
+        std::sort(mine[c].begin(), mine[c].end());   // a fit's segments in their order
+        for (int i : mine[c]) out.push_back(seg[i]);
+        r[c + 1] = (int)out.size();
+    }
+    seg.swap(out);
     return r;
 }
 
@@ -338,175 +349,16 @@ struct StepGraph {
     }
 };
 
-// Tables and graph of one packed step over `fits`.
-cudaError_t build_step(cofem_server* s, std::vector<PFit*>& fits, StepTables& tb, StepGraph& sg, cudaStream_t st,
-                       bool pdl) {
-    const int n = (int)fits.size();
-    struct Group {
-        std::vector<TcSlot> sl[2];
-        std::vector<TcSeg> seg[2];
-        std::vector<double> cost[2];
-        int QSmax = 16;
-    } grp[2];
-    for (int i = 0; i < n; ++i) {
-        PackedFit& pf = fits[i]->pf;
-        Group& G = grp[pf.tf ? 1 : 0];
-        for (int pr = 0; pr < 2; ++pr) {
-            const int idx = (int)G.sl[pr].size();
-            G.sl[pr].push_back(pr == 0 ? pf.g1 : pf.g2);
-            const std::vector<TcSeg>& src = pr == 0 ? pf.s1 : pf.s2;
-            const std::vector<double>& cs = pr == 0 ? pf.c1 : pf.c2;
-            for (size_t k = 0; k < src.size(); ++k) {
-                TcSeg x = src[k];
-                x.slot = idx;
-                G.seg[pr].push_back(x);
-                G.cost[pr].push_back(cs[k]);
-            }
-        }
-        G.QSmax = std::max(G.QSmax, pf.g1.QS);
-    }
-    std::vector<VSlot> vs(n);
-    std::vector<int4> mvec, mrt, mms;
-    for (int i = 0; i < n; ++i) {
-        const VSlot& v = fits[i]->vs;
-        vs[i] = v;
-        for (int q = 0; q < v.Q; ++q)
-            for (int ch = 0; ch < v.nch; ++ch) mvec.push_back(make_int4(i, q, ch, v.nch * v.Q));
-        const int nblk = (int)((v.Np + 1023) / 1024);
-        for (int q = 0; q < v.Q; ++q)
-            for (int ib = 0; ib < nblk; ++ib) mrt.push_back(make_int4(i, q, ib, 0));
-        const int mb = (int)((v.Dp + COFEM_VEC_THREADS - 1) / COFEM_VEC_THREADS);
-        for (int jb = 0; jb < mb; ++jb) mms.push_back(make_int4(i, jb, mb, 0));
-    }
-    cudaError_t e;
-    int ncta[2][2] = {};
-    for (int gi = 0; gi < 2; ++gi)
-        for (int pr = 0; pr < 2; ++pr) {
-            Group& G = grp[gi];
-            if (G.seg[pr].empty()) continue;
-            ncta[gi][pr] = std::min<int>(s->num_sms, (int)G.seg[pr].size());
-            const std::vector<int> r = cta_ranges(G.cost[pr], ncta[gi][pr]);
-            if ((e = upload(&tb.sl[gi][pr], &tb.cap_sl[gi][pr], G.sl[pr], st))) return e;
-            if ((e = upload(&tb.sg[gi][pr], &tb.cap_sg[gi][pr], G.seg[pr], st))) return e;
-            if ((e = upload(&tb.cta[gi][pr], &tb.cap_cta[gi][pr], r, st))) return e;
-        }
-    if ((e = upload(&tb.vs, &tb.cap_vs, vs, st))) return e;
-    if ((e = upload(&tb.map[0], &tb.cap_map[0], mvec, st))) return e;
-    if ((e = upload(&tb.map[1], &tb.cap_map[1], mrt, st))) return e;
-    if ((e = upload(&tb.map[2], &tb.cap_map[2], mms, st))) return e;
-    if ((e = grow(&tb.status, &tb.cap_status, (size_t)n))) return e;
-    if ((e = cudaMemsetAsync(tb.status, 0, (size_t)n * sizeof(int), st))) return e;
-    if (!tb.steps && (e = cudaMalloc((void**)&tb.steps, sizeof(unsigned)))) return e;
-    if (!tb.flags && (e = cudaMalloc((void**)&tb.flags, sizeof(unsigned)))) return e;
-    if ((e = cudaMemsetAsync(tb.flags, 0, sizeof(unsigned), st))) return e;
-    if ((e = cudaStreamSynchronize(st))) return e;   // the host vectors go out of scope
+constexpr int PK_QSMAX = 128;   // the packed GEMM's split tile ring fits every admitted fit
 
-    sg.reset();
-    if ((e = cudaGraphCreate(&sg.g, 0))) return e;
-    Sink root;
-    root.stream = st;
-    root.graph = sg.g;
-    root.pdl = pdl;
-    const cudaGraphConditionalHandle h = root.make_handle(1u, true);
-    Sink body = root.conditional(h, cudaGraphCondTypeWhile);
-    for (int pr = 0; pr < 2; ++pr) {
-        for (int gi = 0; gi < 2; ++gi) {
-            if (!ncta[gi][pr]) continue;
-            TcBatch b{};
-            b.slots = tb.sl[gi][pr];
-            b.segs = tb.sg[gi][pr];
-            b.cta_seg = tb.cta[gi][pr];
-            b.G = 4;
-            b.acc_stride = 128;
-            b.QSmax = grp[gi].QSmax;
-            b.flags = tb.flags;   // a timeout fails every fit of the step
-            launch_gemm_packed(body, gi == 1, b, ncta[gi][pr], tc_packed_smem(gi == 1, grp[gi].QSmax));
-        }
-        if (pr == 0) launch_reduce_T_packed(body, tb.vs, tb.map[1], (int)mrt.size());
-    }
-    launch_update_packed(body, tb.vs, tb.map[0], (int)mvec.size());
-    launch_direction_packed(body, tb.vs, tb.map[0], (int)mvec.size());
-    launch_mstep_packed(body, tb.vs, tb.map[2], (int)mms.size());
-    launch_init_packed(body, tb.vs, tb.map[0], (int)mvec.size());
-    // a launch runs at most 4096 steps before the host looks again
-    launch_packed_status(body, tb.vs, n, tb.status, s->pending_d, tb.steps, 4096u, h);
-    e = root.err ? root.err : body.err;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&sg.x, sg.g, 0);
-    return e;
+template <typename T>
+cudaError_t realloc_dev(T** p, size_t n) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    return cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T));
 }
 
-void engine_loop(cofem_server* s) {
-    cudaSetDevice(s->device);
-    cudaStream_t st = nullptr;
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-    StepTables tb;
-    StepGraph sg;
-    std::vector<PFit*> active;
-    std::vector<int> status;
-    bool pdl = true;
-    for (;;) {
-        bool changed = false;
-        {
-            std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_engine.wait(lk, [&] { return !s->ready.empty() || !active.empty() || (s->stop && s->in_flight == 0); });
-            if (active.empty() && s->ready.empty() && s->stop && s->in_flight == 0) break;
-            while (!s->ready.empty()) {
-                active.push_back(s->ready.front());
-                s->ready.pop_front();
-                changed = true;
-            }
-            *s->pending_h = 0;
-        }
-        cudaError_t e = cudaSuccess;
-        if (changed || !sg.x) {
-            e = build_step(s, active, tb, sg, st, pdl);
-            if (e != cudaSuccess && pdl) {   // programmatic edges refused: plain ones
-                (void)cudaGetLastError();
-                pdl = false;
-                e = build_step(s, active, tb, sg, st, pdl);
-            }
-        }
-        if (e == cudaSuccess) e = cudaMemsetAsync(tb.steps, 0, sizeof(unsigned), st);
-        if (e == cudaSuccess) e = cudaGraphLaunch(sg.x, st);
-        status.assign(active.size(), PH_NONE);
-        unsigned dflags = 0;
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(status.data(), tb.status, active.size() * sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&dflags, tb.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess || (dflags & COFEM_FLAG_DEVICE_TIMEOUT)) {   // every fit of the step fails
-            const char* msg = e != cudaSuccess ? cudaGetErrorString(e)
-                                               : "a bounded on-device wait timed out (packed tensor-core pipeline)";
-            (void)cudaGetLastError();
-            for (PFit* f : active) {
-                cofem_destroy(f->h);
-                finish_job(s, f->job, COFEM_ERR_CUDA, dflags, msg);
-                delete f;
-            }
-            active.clear();
-            sg.reset();
-            continue;
-        }
-        std::vector<PFit*> keep;
-        for (size_t i = 0; i < active.size(); ++i) {
-            PFit* f = active[i];
-            if (status[i] != PH_DONE) {
-                keep.push_back(f);
-                continue;
-            }
-            unsigned flags = 0;
-            const cofem_status stat = packed_finish(f->h, f->job->req, &flags);
-            const std::string msg = stat != COFEM_OK ? cofem_last_error() : "";
-            cofem_destroy(f->h);
-            finish_job(s, f->job, stat, flags, msg.c_str());
-            delete f;
-        }
-        if (keep.size() != active.size()) {
-            active.swap(keep);
-            sg.reset();   // rebuilt for the new set
-        }
-    }
-    sg.reset();
+void free_tables(StepTables& tb) {
     for (int gi = 0; gi < 2; ++gi)
         for (int pr = 0; pr < 2; ++pr) {
             if (tb.sl[gi][pr]) cudaFree(tb.sl[gi][pr]);
@@ -516,9 +368,259 @@ void engine_loop(cofem_server* s) {
     if (tb.vs) cudaFree(tb.vs);
     for (auto* m : tb.map)
         if (m) cudaFree(m);
-    if (tb.status) cudaFree(tb.status);
-    if (tb.steps) cudaFree(tb.steps);
-    if (tb.flags) cudaFree(tb.flags);
+    for (void* p : {(void*)tb.counts, (void*)tb.status, (void*)tb.steps, (void*)tb.flags})
+        if (p) cudaFree(p);
+    tb = StepTables{};
+}
+
+// Host copy of a step's tables.
+struct StepHost {
+    std::vector<TcSlot> sl[2][2];
+    std::vector<TcSeg> seg[2][2];
+    std::vector<int> cta[2][2];
+    std::vector<VSlot> vs;
+    std::vector<int4> map[3];
+    int mask = 0;   // 1: BF16 fits, 2: 3xTF32 fits
+};
+
+void compose(const std::vector<PFit*>& fits, int num_sms, StepHost& h) {
+    h = StepHost{};
+    std::vector<double> cost[2][2];
+    for (size_t i = 0; i < fits.size(); ++i) {
+        const PackedFit& pf = fits[i]->pf;
+        const int gi = pf.tf ? 1 : 0;
+        h.mask |= 1 << gi;
+        for (int pr = 0; pr < 2; ++pr) {
+            const int idx = (int)h.sl[gi][pr].size();
+            h.sl[gi][pr].push_back(pr == 0 ? pf.g1 : pf.g2);
+            const std::vector<TcSeg>& src = pr == 0 ? pf.s1 : pf.s2;
+            const std::vector<double>& cs = pr == 0 ? pf.c1 : pf.c2;
+            for (size_t k = 0; k < src.size(); ++k) {
+                TcSeg x = src[k];
+                x.slot = idx;
+                h.seg[gi][pr].push_back(x);
+                cost[gi][pr].push_back(cs[k]);
+            }
+        }
+        const VSlot& v = fits[i]->vs;
+        h.vs.push_back(v);
+        const int ii = (int)i;
+        for (int q = 0; q < v.Q; ++q)
+            for (int ch = 0; ch < v.nch; ++ch) h.map[0].push_back(make_int4(ii, q, ch, v.nch * v.Q));
+        const int nblk = (int)((v.Np + 1023) / 1024);
+        for (int q = 0; q < v.Q; ++q)
+            for (int ib = 0; ib < nblk; ++ib) h.map[1].push_back(make_int4(ii, q, ib, 0));
+        const int mb = (int)((v.Dp + COFEM_VEC_THREADS - 1) / COFEM_VEC_THREADS);
+        for (int jb = 0; jb < mb; ++jb) h.map[2].push_back(make_int4(ii, jb, mb, 0));
+    }
+    for (int gi = 0; gi < 2; ++gi)
+        for (int pr = 0; pr < 2; ++pr) h.cta[gi][pr] = assign_ctas(h.seg[gi][pr], cost[gi][pr], num_sms);
+}
+
+// Grow the device tables to hold `h` (false: the graphs must be rebuilt).
+cudaError_t ensure_capacity(StepTables& tb, const StepHost& h, int num_sms, bool* kept) {
+    *kept = true;
+    cudaError_t e;
+    const int nf = (int)h.vs.size();
+    if (nf > tb.cap_fits || !tb.vs) {
+        const int cap = std::max(nf, std::max(16, 2 * tb.cap_fits));
+        if ((e = realloc_dev(&tb.vs, cap)) || (e = realloc_dev(&tb.status, cap))) return e;
+        tb.cap_fits = cap;
+        *kept = false;
+    }
+    for (int k = 0; k < 3; ++k)
+        if ((int)h.map[k].size() > tb.cap_blk[k] || !tb.map[k]) {
+            const int cap = std::max((int)h.map[k].size(), std::max(1024, 2 * tb.cap_blk[k]));
+            if ((e = realloc_dev(&tb.map[k], cap))) return e;
+            tb.cap_blk[k] = cap;
+            *kept = false;
+        }
+    for (int gi = 0; gi < 2; ++gi)
+        for (int pr = 0; pr < 2; ++pr) {
+            if ((int)h.seg[gi][pr].size() > tb.cap_seg[gi][pr] || !tb.sg[gi][pr]) {
+                const int cap = std::max((int)h.seg[gi][pr].size(), std::max(1024, 2 * tb.cap_seg[gi][pr]));
+                if ((e = realloc_dev(&tb.sg[gi][pr], cap))) return e;
+                tb.cap_seg[gi][pr] = cap;
+                *kept = false;
+            }
+            if (!tb.sl[gi][pr] || (int)h.sl[gi][pr].size() > tb.cap_sl[gi][pr]) {
+                const int cap = std::max(tb.cap_fits, nf);
+                if ((e = realloc_dev(&tb.sl[gi][pr], cap))) return e;
+                tb.cap_sl[gi][pr] = cap;
+                *kept = false;
+            }
+            if (!tb.cta[gi][pr]) {
+                if ((e = realloc_dev(&tb.cta[gi][pr], num_sms + 1))) return e;
+                *kept = false;
+            }
+        }
+    if (!tb.counts) {
+        if ((e = realloc_dev(&tb.counts, 4)) || (e = realloc_dev(&tb.steps, 1)) || (e = realloc_dev(&tb.flags, 1)))
+            return e;
+        *kept = false;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t put(T* dst, const std::vector<T>& v, cudaStream_t st) {
+    if (v.empty()) return cudaSuccess;
+    return cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+cudaError_t upload(StepTables& tb, const StepHost& h, cudaStream_t st) {
+    cudaError_t e;
+    for (int gi = 0; gi < 2; ++gi)
+        for (int pr = 0; pr < 2; ++pr) {
+            if ((e = put(tb.sl[gi][pr], h.sl[gi][pr], st))) return e;
+            if ((e = put(tb.sg[gi][pr], h.seg[gi][pr], st))) return e;
+            if ((e = put(tb.cta[gi][pr], h.cta[gi][pr], st))) return e;
+        }
+    if ((e = put(tb.vs, h.vs, st))) return e;
+    for (int k = 0; k < 3; ++k)
+        if ((e = put(tb.map[k], h.map[k], st))) return e;
+    const std::vector<int> counts = {(int)h.map[0].size(), (int)h.map[1].size(), (int)h.map[2].size(),
+                                     (int)h.vs.size()};
+    if ((e = put(tb.counts, counts, st))) return e;
+    if ((e = cudaMemsetAsync(tb.status, 0, h.vs.size() * sizeof(int), st))) return e;
+    if ((e = cudaMemsetAsync(tb.flags, 0, sizeof(unsigned), st))) return e;
+    return cudaMemsetAsync(tb.steps, 0, sizeof(unsigned), st);
+}
+
+// The step graph for the fits of the groups in `mask`, at the tables' capacities.
+cudaError_t build_graph(cofem_server* s, const StepTables& tb, int mask, StepGraph& sg, cudaStream_t st, bool pdl) {
+    sg.reset();
+    cudaError_t e = cudaGraphCreate(&sg.g, 0);
+    if (e) return e;
+    Sink root;
+    root.stream = st;
+    root.graph = sg.g;
+    root.pdl = pdl;
+    const cudaGraphConditionalHandle h = root.make_handle(1u, true);
+    Sink body = root.conditional(h, cudaGraphCondTypeWhile);
+    for (int pr = 0; pr < 2; ++pr) {
+        for (int gi = 0; gi < 2; ++gi) {
+            if (!(mask & (1 << gi))) continue;
+            TcBatch b{};
+            b.slots = tb.sl[gi][pr];
+            b.segs = tb.sg[gi][pr];
+            b.cta_seg = tb.cta[gi][pr];
+            b.G = 4;
+            b.acc_stride = 128;
+            b.QSmax = PK_QSMAX;
+            b.flags = tb.flags;   // a timeout fails every fit of the step
+            launch_gemm_packed(body, gi == 1, b, s->num_sms, tc_packed_smem(gi == 1, PK_QSMAX));
+        }
+        if (pr == 0) launch_reduce_T_packed(body, tb.vs, tb.map[1], tb.counts + 1, tb.cap_blk[1]);
+    }
+    launch_update_packed(body, tb.vs, tb.map[0], tb.counts + 0, tb.cap_blk[0]);
+    launch_direction_packed(body, tb.vs, tb.map[0], tb.counts + 0, tb.cap_blk[0]);
+    launch_mstep_packed(body, tb.vs, tb.map[2], tb.counts + 2, tb.cap_blk[2]);
+    launch_init_packed(body, tb.vs, tb.map[0], tb.counts + 0, tb.cap_blk[0]);
+    // a launch runs at most 4096 steps before the host looks again
+    launch_packed_status(body, tb.vs, tb.counts + 3, tb.status, s->pending_d, tb.steps, 4096u, h);
+    e = root.err ? root.err : body.err;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&sg.x, sg.g, 0);
+    if (e != cudaSuccess) sg.reset();
+    return e;
+}
+
+void retire(cofem_server* s, std::vector<PFit*>& done) {
+    for (PFit* f : done) {
+        unsigned flags = 0;
+        const cofem_status stat = packed_finish(f->h, f->job->req, &flags);
+        const std::string msg = stat != COFEM_OK ? cofem_last_error() : "";
+        cofem_destroy(f->h);
+        if (f->st) cudaStreamDestroy(f->st);
+        finish_job(s, f->job, stat, flags, msg.c_str());
+        delete f;
+    }
+    done.clear();
+}
+
+void engine_loop(cofem_server* s) {
+    cudaSetDevice(s->device);
+    cudaStream_t st = nullptr;
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, lo);   // the step loop yields to preparation
+    StepTables tb;
+    StepGraph graphs[4];
+    StepHost host;
+    std::vector<PFit*> active, done;
+    std::vector<int> status;
+    bool pdl = true;
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_engine.wait(lk, [&] {
+                return !s->ready.empty() || !active.empty() || !done.empty() || (s->stop && s->in_flight == 0);
+            });
+            if (active.empty() && s->ready.empty() && done.empty() && s->stop && s->in_flight == 0) break;
+            while (!s->ready.empty()) {
+                active.push_back(s->ready.front());
+                s->ready.pop_front();
+            }
+            *s->pending_h = 0;
+        }
+        cudaError_t e = cudaSuccess;
+        const bool run = !active.empty();
+        if (run) {
+            compose(active, s->num_sms, host);
+            bool kept = true;
+            e = ensure_capacity(tb, host, s->num_sms, &kept);
+            if (!kept)
+                for (auto& g : graphs) g.reset();
+            if (e == cudaSuccess) e = upload(tb, host, st);
+            if (e == cudaSuccess && !graphs[host.mask].x) {
+                e = build_graph(s, tb, host.mask, graphs[host.mask], st, pdl);
+                if (e != cudaSuccess && pdl) {   // programmatic edges refused: plain ones
+                    (void)cudaGetLastError();
+                    pdl = false;
+                    e = build_graph(s, tb, host.mask, graphs[host.mask], st, pdl);
+                }
+                if (e == cudaSuccess) {
+                    std::lock_guard<std::mutex> lk(s->mu);
+                    ++s->stats.graphs_built;
+                }
+            }
+            if (e == cudaSuccess) e = cudaGraphLaunch(graphs[host.mask].x, st);
+        }
+        retire(s, done);   // the fits that finished in the previous launch, while this one runs
+        if (!run) continue;
+        status.assign(active.size(), PH_NONE);
+        unsigned dflags = 0, steps = 0;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(status.data(), tb.status, active.size() * sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&dflags, tb.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&steps, tb.steps, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess || (dflags & COFEM_FLAG_DEVICE_TIMEOUT)) {   // every fit of the step fails
+            const char* msg = e != cudaSuccess ? cudaGetErrorString(e)
+                                               : "a bounded on-device wait timed out (packed tensor-core pipeline)";
+            (void)cudaGetLastError();
+            for (PFit* f : active) {
+                cofem_destroy(f->h);
+                if (f->st) cudaStreamDestroy(f->st);
+                finish_job(s, f->job, COFEM_ERR_CUDA, dflags, msg);
+                delete f;
+            }
+            active.clear();
+            for (auto& g : graphs) g.reset();
+            continue;
+        }
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->stats.launches += 1;
+            s->stats.steps += steps;
+            s->stats.fit_steps += (long long)steps * (long long)active.size();
+        }
+        std::vector<PFit*> keep;
+        for (size_t i = 0; i < active.size(); ++i) (status[i] == PH_DONE ? done : keep).push_back(active[i]);
+        active.swap(keep);
+    }
+    for (auto& g : graphs) g.reset();
+    free_tables(tb);
     cudaStreamDestroy(st);
 }
 
@@ -551,6 +653,13 @@ cofem_status cofem_server_create_packed(cofem_server** out, long long hbm_budget
     for (int i = 0; i < prep_threads; ++i) s->workers.emplace_back(prep_loop, s);
     s->engine = std::thread(engine_loop, s);
     *out = s;
+    return COFEM_OK;
+}
+
+cofem_status cofem_server_get_stats(cofem_server* s, cofem_server_stats* out) {
+    if (!s || !out) return cofem_set_error(COFEM_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    *out = s->stats;
     return COFEM_OK;
 }
 

@@ -51,7 +51,8 @@ def test_struct_layouts_match_binding(cf, tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no host C compiler")
-    structs = {"cofem_opts": cf.cofem_opts, "cofem_request": cf.cofem_request, "cofem_result": cf.cofem_result}
+    structs = {"cofem_opts": cf.cofem_opts, "cofem_request": cf.cofem_request, "cofem_result": cf.cofem_result,
+               "cofem_server_stats": cf.cofem_server_stats}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cofem.h"', "int main(void) {"]
     for sname, cls in structs.items():
         lines.append(f'    printf("{sname} size %zu\\n", sizeof({sname}));')

@@ -97,30 +97,34 @@ def test_packed_same_alone_and_in_mix_and_matches_oracle(cf, precision):
 
 def test_packed_many_requests_with_arrivals(cf):
     """Requests of different sizes and probe counts submitted while others
-    run (admission between steps): every one completes, and a sample matches
-    its own fit alone on a fresh packed server bit for bit."""
+    run (admission between steps), more of them at once than the step tables
+    first hold (so the tables and the step graph grow): every one completes,
+    and a sample matches its own fit alone on a fresh packed server bit for
+    bit."""
     rng = np.random.default_rng(4)
     probs = []
-    for i in range(20):
-        D = int(rng.integers(256, 4097))
+    for i in range(48):
+        D = int(rng.integers(256, 3073))
         probs.append((dense_gaussian(max(1, D // 4), D, max(1, int(0.03 * D)), float(rng.uniform(15, 30)),
                                      seed=100 + i), int(rng.choice([8, 16, 32]))))
-    srv = cf.cofem_server_create_packed(40 << 30, 8, 3)
+    srv = cf.cofem_server_create_packed(40 << 30, 40, 4)
     import time
     try:
         reqs, tickets = [], []
         for i, (p, K) in enumerate(probs):
             reqs.append(_make(cf, p, K, 5, cf.COFEM_BF16))
             tickets.append(cf.cofem_submit(srv, reqs[-1]["req"]))
-            if i % 5 == 4:
+            if i % 12 == 11:
                 time.sleep(0.05)
         rs = [cf.cofem_wait(srv, t) for t in tickets]
+        stats = cf.cofem_server_get_stats(srv)
     finally:
         cf.cofem_server_destroy(srv)
     assert all(r.status == 0 for r in rs), [r.message for r in rs if r.status != 0]
+    assert stats["fit_steps"] > 16 * stats["launches"], stats   # steps served many fits at once
     srv = cf.cofem_server_create_packed(8 << 30, 1, 1)
     try:
-        for i in (0, 7, 19):
+        for i in (0, 7, 19, 47):
             p, K = probs[i]
             a = _make(cf, p, K, 5, cf.COFEM_BF16)
             assert cf.cofem_wait(srv, cf.cofem_submit(srv, a["req"])).status == 0
