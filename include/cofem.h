@@ -164,14 +164,14 @@ typedef struct cofem_opts {
 /* Accurate residual forms (the precision form's B - A X; not in the paper).
  * FP32_PAIRS: X as the FP32 pair X + Xlo, A X with compensated FP32-pair
  * products on the CUDA cores (TwoProduct and TwoSum, about 2^-48 relative
- * error), every dictionary kind.  SLICED: BF16 dense dictionaries with
- * K + 1 <= 48 and N, D <= 40960: both products of A X = beta Phi~^T (Phi~ X)
- * + alpha X from exact integer slices on the tensor cores (each dictionary
- * entry as three signed 8-bit digits relative to a power of two per
- * dictionary row, or per column for Phi~^T; each entry of X and of Phi~ X as
- * five relative to a power of two per column; digit products summed exactly
- * in integers), relative error about 2^-38 of sum_k |Phi~_ik| |x_k| per
- * product.  Requesting SLICED where it does not apply makes the first fit
+ * error), every dictionary kind.  SLICED: BF16 or FP8 E4M3 dense dictionaries
+ * with K + 1 <= 48 and N, D <= 40960: both products of A X = beta Phi~^T
+ * (Phi~ X) + alpha X from exact integer slices on the tensor cores (each
+ * dictionary entry, or FP8 code, as three signed 8-bit digits relative to a
+ * power of two per dictionary row, or per column for Phi~^T; each entry of X
+ * and of Phi~ X as five relative to a power of two per column; digit products
+ * summed exactly in integers; the FP8 row scales applied to Phi~ X in FP64),
+ * relative error about 2^-38 of sum_k |Phi~_ik| |x_k| per product.  Requesting SLICED where it does not apply makes the first fit
  * fail with COFEM_ERR_UNSUPPORTED. */
 #define COFEM_RESIDUAL_AUTO       0
 #define COFEM_RESIDUAL_FP32_PAIRS 1

@@ -192,7 +192,8 @@ cofem_status ensure_workspace(cofem_ctx* c, int Q) {
             free_workspace(c);
             if (e == cudaErrorNotSupported)
                 return fail(COFEM_ERR_UNSUPPORTED,
-                            "the single-pass dense operator needs BF16, 3(K+1) <= 112 and D <= 256 x SMs");
+                            c->phi8 ? "the FP8 dense operator needs 3(K+1) <= 128"
+                                    : "the single-pass dense operator needs BF16, 3(K+1) <= 112 and D <= 256 x SMs");
             return cuda_fail(e, "tensor-core operator set-up");
         }
     }
@@ -206,7 +207,8 @@ cofem_status ensure_workspace(cofem_ctx* c, int Q) {
         } else if (c->opts.residual_path == COFEM_RESIDUAL_SLICED) {
             free_workspace(c);
             return fail(COFEM_ERR_UNSUPPORTED,
-                        "the sliced accurate residual needs a BF16 dense dictionary, K + 1 <= 48 and N, D <= 40960");
+                        "the sliced accurate residual needs a BF16 or FP8 dense dictionary, K + 1 <= 48 and N, "
+                        "D <= 40960");
         }
     }
     CK(cudaMemsetAsync(c->counters, 0, w.counters * sizeof(unsigned), c->stream));
@@ -251,19 +253,28 @@ cofem_status build_graph(cofem_ctx* c, int Q, bool pdl) {
     if (c->opts.warm_start) launch_operator(em, c, Q, c->X, OP_PLAIN);
     Sink vf;
     cudaGraphConditionalHandle h_vf = 0, h_cg = 0;
+    // two-pass tensor-core operator: the loop is rotated so that the first
+    // product of the next CG step follows the direction kernel inside the
+    // body (a programmatic edge: its prologue and first dictionary tiles
+    // overlap the direction kernel); the first step's product runs before the
+    // loop.  When the loop ends, the product of the step not taken is unused.
+    const bool rot = tc_rotatable(c);
     if (verify) {
         h_vf = em.make_handle(0u, false);
         launch_cg_init(em, c, Q, h_vf);
         vf = em.conditional(h_vf, cudaGraphCondTypeWhile);
         h_cg = vf.make_handle(0u, false);
         launch_cg_gate(vf, c, h_cg);
+        if (rot) launch_tc_first_product(vf, c);
     } else {
         h_cg = em.make_handle(0u, false);
         launch_cg_init(em, c, Q, h_cg);
+        if (rot) launch_tc_first_product(em, c);
     }
     Sink& outer = verify ? vf : em;
     Sink cg = outer.conditional(h_cg, cudaGraphCondTypeWhile);
-    launch_operator(cg, c, Q, c->P, OP_CG);
+    if (rot) launch_tc_rest(cg, c, Q, OP_CG);
+    else launch_operator(cg, c, Q, c->P, OP_CG);
     // residual replacement (an IF node) only where it is on: a conditional
     // node between the update and the direction would end their overlap
     const bool with_rr = c->opts.rr_period > 0;
@@ -275,6 +286,7 @@ cofem_status build_graph(cofem_ctx* c, int Q, bool pdl) {
         launch_true_residual(rr, c, Q, DF_RR);
     }
     launch_cg_direction(cg, c, Q, h_cg);
+    if (rot) launch_tc_first_product(cg, c);
     if (verify) {
         launch_true_residual(vf, c, Q, DF_CHECK);
         launch_df_check(vf, c, Q, h_vf);

@@ -731,6 +731,11 @@ cudaError_t tc_setup(cofem_ctx* c, int Q);
 cudaError_t tc_kernel_attributes(int max_smem);
 void tc_release(cofem_ctx* c);
 void launch_tc_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode);
+// the operator of the CG loop split in two: the first product alone, and the
+// T reduction with the second product (two-pass tensor-core forms)
+bool tc_rotatable(cofem_ctx* c);
+void launch_tc_first_product(Sink& s, cofem_ctx* c);
+void launch_tc_rest(Sink& s, cofem_ctx* c, int Q, int mode);
 // Split image of the CG direction block (written by k_cg_init / k_cg_direction)
 // and the description of the operator output (null / dense slices otherwise).
 SplitOut tc_direction_split(cofem_ctx* c);

@@ -1,6 +1,6 @@
 // Accurate residual R = B - A X of the precision form on the tensor cores:
 // both products of A X = beta Phi~^T (Phi~ X) + alpha X formed from exact
-// integer slices, for a BF16 dictionary.  The splitting idea is the
+// integer slices, for a BF16 dictionary or the FP8 form's codes.  The splitting idea is the
 // error-free matrix product of Ozaki, Ogita, Oishi and Rump ("Error-free
 // transformations of matrix multiplication by using fast routines of matrix
 // multiplication and its applications", Numer. Algorithms 59, 2012), here with
@@ -57,6 +57,8 @@
 // copies and MMAs finish, frees TMEM and returns.
 #include <algorithm>
 #include <vector>
+
+#include <cuda_fp8.h>
 
 #include "cofem_internal.cuh"
 #include "tc_ptx.cuh"
@@ -146,15 +148,23 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 }
 
 // ---------------------------------------------------------------------------
-// Dictionary slice images (once per handle).
+// Dictionary slice images (once per handle).  The dictionary is the BF16
+// copy, or the FP8 form's E4M3 codes C (Phi~ = diag(s) C: the slices are
+// those of C, exact with three digits since a code has 4 significant bits
+// and spans 2^-9 .. 448, and the row scales enter t = s^2 (C X)).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float dict_value(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float dict_value(uint8_t v) {   // an E4M3 code's value (exact in FP16)
+    return __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)v, __NV_E4M3)));
+}
+
 // E[i] for each row i of the row-major Np x Dp dictionary (one block per row).
-__global__ __launch_bounds__(256) void k_sl_row_exp(const __nv_bfloat16* __restrict__ phi, long long Dp,
-                                                    int* __restrict__ E) {
+template <typename TE>
+__global__ __launch_bounds__(256) void k_sl_row_exp(const TE* __restrict__ phi, long long Dp, int* __restrict__ E) {
     __shared__ float sh[8];
     const long long i = blockIdx.x;
     float m = 0.0f;
-    for (long long j = threadIdx.x; j < Dp; j += blockDim.x) m = fmaxf(m, fabsf(__bfloat162float(phi[i * Dp + j])));
+    for (long long j = threadIdx.x; j < Dp; j += blockDim.x) m = fmaxf(m, fabsf(dict_value(phi[i * Dp + j])));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
@@ -167,14 +177,15 @@ __global__ __launch_bounds__(256) void k_sl_row_exp(const __nv_bfloat16* __restr
 
 // Column maxima of the dictionary as FP32 bit patterns (non-negative floats
 // order like their bit patterns): rows split over blockIdx.y, atomicMax.
-__global__ __launch_bounds__(256) void k_sl_col_max(const __nv_bfloat16* __restrict__ phi, long long Np,
-                                                    long long Dp, int rows_per_block, unsigned* __restrict__ cmax) {
+template <typename TE>
+__global__ __launch_bounds__(256) void k_sl_col_max(const TE* __restrict__ phi, long long Np, long long Dp,
+                                                    int rows_per_block, unsigned* __restrict__ cmax) {
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= Dp) return;
     const long long i0 = (long long)blockIdx.y * rows_per_block;
     const long long i1 = std::min(Np, i0 + rows_per_block);
     float m = 0.0f;
-    for (long long i = i0; i < i1; ++i) m = fmaxf(m, fabsf(__bfloat162float(phi[i * Dp + j])));
+    for (long long i = i0; i < i1; ++i) m = fmaxf(m, fabsf(dict_value(phi[i * Dp + j])));
     atomicMax(cmax + j, __float_as_uint(m));
 }
 
@@ -187,23 +198,22 @@ __global__ void k_sl_col_exp(const unsigned* __restrict__ cmax, long long Dp, in
 // m 128 + 127 and columns kt 64 .. kt 64 + 63 of the dictionary, rows of 128
 // bytes, 16-byte chunk c of row r at chunk c ^ (r & 7).  Grid (KT, MT), one
 // thread per row.
-__global__ __launch_bounds__(128) void k_sl_tile_rows(const __nv_bfloat16* __restrict__ phi, long long Dp, int KT,
+template <typename TE>
+__global__ __launch_bounds__(128) void k_sl_tile_rows(const TE* __restrict__ phi, long long Dp, int KT,
                                                       const int* __restrict__ E, uint8_t* __restrict__ img) {
     const int kt = blockIdx.x, m = blockIdx.y, rr = threadIdx.x;
     const long long i = (long long)m * SL_BM + rr;
     const int e = E[i];
-    const uint4* src = reinterpret_cast<const uint4*>(phi + i * Dp + (long long)kt * SL_BK);
+    const TE* src = phi + i * Dp + (long long)kt * SL_BK;
     uint8_t* tile = img + ((size_t)m * KT + kt) * SL_ABYTES;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        const uint4 raw = src[c];
-        const __nv_bfloat16* v = reinterpret_cast<const __nv_bfloat16*>(&raw);
         uint32_t out[SL_NA][4];
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
             float d0[SL_NA], d1[SL_NA];
-            dict_digits(__bfloat162float(v[2 * h]), e, d0);
-            dict_digits(__bfloat162float(v[2 * h + 1]), e, d1);
+            dict_digits(dict_value(src[c * 8 + 2 * h]), e, d0);
+            dict_digits(dict_value(src[c * 8 + 2 * h + 1]), e, d1);
 #pragma unroll
             for (int a = 0; a < SL_NA; ++a) out[a][h] = pack_bf16(d0[a], d1[a]);
         }
@@ -217,11 +227,13 @@ __global__ __launch_bounds__(128) void k_sl_tile_rows(const __nv_bfloat16* __res
 // Slice image of product 2 (rows = columns of the dictionary): tile (m, kt, a)
 // holds digit a of element (rr, cc) = phi[kt 64 + cc][m 128 + rr] with the
 // exponent of dictionary column m 128 + rr.  Grid (KT, MT).
-__global__ __launch_bounds__(128) void k_sl_tile_cols(const __nv_bfloat16* __restrict__ phi, long long Dp, int KT,
+template <typename TE>
+__global__ __launch_bounds__(128) void k_sl_tile_cols(const TE* __restrict__ phi, long long Dp, int KT,
                                                       const int* __restrict__ E, uint8_t* __restrict__ img) {
-    __shared__ __nv_bfloat16 sm[SL_BK][SL_BM + 8];
+    __shared__ float sm[SL_BK][SL_BM + 1];
     const int kt = blockIdx.x, m = blockIdx.y, t = threadIdx.x;
-    for (int n = 0; n < SL_BK; ++n) sm[n][t] = phi[((long long)kt * SL_BK + n) * Dp + (long long)m * SL_BM + t];
+    for (int n = 0; n < SL_BK; ++n)
+        sm[n][t] = dict_value(phi[((long long)kt * SL_BK + n) * Dp + (long long)m * SL_BM + t]);
     __syncthreads();
     const int e = E[(long long)m * SL_BM + t];
     uint8_t* tile = img + ((size_t)m * KT + kt) * SL_ABYTES;
@@ -231,8 +243,8 @@ __global__ __launch_bounds__(128) void k_sl_tile_cols(const __nv_bfloat16* __res
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
             float d0[SL_NA], d1[SL_NA];
-            dict_digits(__bfloat162float(sm[c * 8 + 2 * h][t]), e, d0);
-            dict_digits(__bfloat162float(sm[c * 8 + 2 * h + 1][t]), e, d1);
+            dict_digits(sm[c * 8 + 2 * h][t], e, d0);
+            dict_digits(sm[c * 8 + 2 * h + 1][t], e, d1);
 #pragma unroll
             for (int a = 0; a < SL_NA; ++a) out[a][h] = pack_bf16(d0[a], d1[a]);
         }
@@ -543,12 +555,14 @@ __device__ __forceinline__ long long seg_sum(const long long* __restrict__ part,
     return z;
 }
 
-// t[q][i] = (Phi~ X)_iq in FP64 (Np rows, zero for q >= Q) and G[q] with
+// t[q][i] = (Phi~ X)_iq in FP64 (Np rows, zero for q >= Q; the FP8 form's
+// rows times s_i^2) and G[q] with
 // 2^G >= 4 max_i |t_iq| (one block per column of the padded block).
 __global__ __launch_bounds__(1024) void k_sl_finish_t(const long long* __restrict__ part,
                                                       const int* __restrict__ grp_seg, int QO, int Q, long long Np,
                                                       const int* __restrict__ E, const int* __restrict__ F,
-                                                      double* __restrict__ t, int* __restrict__ G) {
+                                                      const float* __restrict__ rscale, double* __restrict__ t,
+                                                      int* __restrict__ G) {
     __shared__ double sh[32];
     griddep_launch();
     griddep_wait();
@@ -556,7 +570,13 @@ __global__ __launch_bounds__(1024) void k_sl_finish_t(const long long* __restric
     double m = 0.0;
     for (long long i = threadIdx.x; i < Np; i += blockDim.x) {
         double v = 0.0;
-        if (q < Q) v = ldexp((double)seg_sum(part, grp_seg, QO, q, i), E[i] + F[q] - 48);
+        if (q < Q) {
+            v = ldexp((double)seg_sum(part, grp_seg, QO, q, i), E[i] + F[q] - 48);
+            if (rscale) {   // FP8 form: t = s^2 (C X), Phi~^T Phi~ = C^T diag(s^2) C
+                const double sc = rscale[i];
+                v *= sc * sc;
+            }
+        }
         t[(size_t)q * Np + i] = v;
         m = fmax(m, fabs(v));
     }
@@ -723,7 +743,8 @@ int ceil_div_i(long long a, long long b) { return (int)((a + b - 1) / b); }
 }  // namespace
 
 bool sl_applies(const cofem_ctx* c, int Q) {
-    return c->kind == COFEM_OP_DENSE && c->phi16 != nullptr && c->opts.residual_path != COFEM_RESIDUAL_FP32_PAIRS &&
+    return c->kind == COFEM_OP_DENSE && (c->phi16 != nullptr || c->phi8 != nullptr) &&
+           c->opts.residual_path != COFEM_RESIDUAL_FP32_PAIRS &&
            (Q + 15) / 16 * 16 <= SL_QOMAX && c->Np <= SL_KMAX && c->Dp <= SL_KMAX;
 }
 
@@ -771,12 +792,22 @@ cudaError_t sl_build(cofem_ctx* c, SlPlan* s, int Q) {
     e = cudaMemsetAsync(cmax, 0, (size_t)Dp * sizeof(unsigned), st);
     if (e == cudaSuccess) {
         const int rpb = 256;   // rows per block of the column maxima
-        k_sl_row_exp<<<(unsigned)Np, 256, 0, st>>>(c->phi16, Dp, s->E1);
-        k_sl_col_max<<<dim3((unsigned)ceil_div_i(Dp, 256), (unsigned)ceil_div_i(Np, rpb)), 256, 0, st>>>(
-            c->phi16, Np, Dp, rpb, cmax);
+        const dim3 gcm((unsigned)ceil_div_i(Dp, 256), (unsigned)ceil_div_i(Np, rpb));
+        if (c->phi16) {
+            k_sl_row_exp<<<(unsigned)Np, 256, 0, st>>>(c->phi16, Dp, s->E1);
+            k_sl_col_max<<<gcm, 256, 0, st>>>(c->phi16, Np, Dp, rpb, cmax);
+        } else {
+            k_sl_row_exp<<<(unsigned)Np, 256, 0, st>>>(c->phi8, Dp, s->E1);
+            k_sl_col_max<<<gcm, 256, 0, st>>>(c->phi8, Np, Dp, rpb, cmax);
+        }
         k_sl_col_exp<<<(unsigned)ceil_div_i(Dp, 256), 256, 0, st>>>(cmax, Dp, s->E2);
-        k_sl_tile_rows<<<dim3((unsigned)KT1, (unsigned)MT1), 128, 0, st>>>(c->phi16, Dp, KT1, s->E1, s->A1);
-        k_sl_tile_cols<<<dim3((unsigned)KT2, (unsigned)MT2), 128, 0, st>>>(c->phi16, Dp, KT2, s->E2, s->A2);
+        if (c->phi16) {
+            k_sl_tile_rows<<<dim3((unsigned)KT1, (unsigned)MT1), 128, 0, st>>>(c->phi16, Dp, KT1, s->E1, s->A1);
+            k_sl_tile_cols<<<dim3((unsigned)KT2, (unsigned)MT2), 128, 0, st>>>(c->phi16, Dp, KT2, s->E2, s->A2);
+        } else {
+            k_sl_tile_rows<<<dim3((unsigned)KT1, (unsigned)MT1), 128, 0, st>>>(c->phi8, Dp, KT1, s->E1, s->A1);
+            k_sl_tile_cols<<<dim3((unsigned)KT2, (unsigned)MT2), 128, 0, st>>>(c->phi8, Dp, KT2, s->E2, s->A2);
+        }
         e = cudaGetLastError();
     }
     cudaFreeAsync(cmax, st);
@@ -832,7 +863,8 @@ void launch_sl_products(Sink& s, cofem_ctx* c, int Q) {
     SlPlan* p = (SlPlan*)c->sl;
     const int QO = p->QO;
     launch_sl_first_product(s, c, Q);
-    s.launch_pdl(k_sl_finish_t, dim3(QO), dim3(1024), 0, p->g1.part, p->g1.grp_seg, QO, Q, c->Np, p->E1, p->F, p->t,
+    s.launch_pdl(k_sl_finish_t, dim3(QO), dim3(1024), 0, p->g1.part, p->g1.grp_seg, QO, Q, c->Np, p->E1, p->F,
+                 c->phi8 ? (const float*)c->scale8 : (const float*)nullptr, p->t,
                  p->G);
     s.launch_pdl(k_sl_digits<false>, dim3((unsigned)ceil_div_i(c->Np / 8, 256), QO), dim3(256), 0,
                  (const float*)nullptr, (const float*)nullptr, p->t, c->Np, c->Np, Q, QO, p->G, p->B2);

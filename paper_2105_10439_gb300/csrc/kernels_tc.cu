@@ -44,7 +44,9 @@ constexpr int TC_BK32 = 32;               // TF32 tile: 128 rows x 32 fp32 (128-
 constexpr int TC_NA = 8, TC_NA_TF = 5, TC_NB = 3;
 // Epilogue warps: four (one per TMEM sub-partition) convert the TF32 tiles;
 // all of them drain the accumulators, the warps of a sub-partition splitting
-// the row tiles.  A lone warp per scheduler drained a 4-tile segment in ~6 us
+// the row tiles.  (Eight converter warps instead of four left the 3xTF32
+// operator as it was, 0.717 against 0.708 ms at 8192 x 32768: the split is not
+// what paces it.)  A lone warp per scheduler drained a 4-tile segment in ~6 us
 // (dependent TMEM load -> add -> store chains at one warp's issue rate).
 constexpr int tc_epi_warps(bool tf) { return tf ? 8 : 16; }
 constexpr int tc_threads(bool tf) { return 64 + 32 * tc_epi_warps(tf); }
@@ -319,10 +321,11 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc(TcParams p) {
                         }
                         // this warp's quarter of the tile: 1024 floats, 8 float4 per lane;
                         // x -> hi = tf32_rn(x) in place, lo = tf32_rn(x - hi) beside it
-                        float4* src = reinterpret_cast<float4*>(ringA + sa * TC_A_BYTES) + ew * 256;
-                        float4* dst = reinterpret_cast<float4*>(ringL + sa * TC_A_BYTES) + ew * 256;
+                        constexpr int PW = 256;   // float4 per converter warp
+                        float4* src = reinterpret_cast<float4*>(ringA + sa * TC_A_BYTES) + ew * PW;
+                        float4* dst = reinterpret_cast<float4*>(ringL + sa * TC_A_BYTES) + ew * PW;
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
+                        for (int i = 0; i < PW / 32; ++i) {
                             const float4 x = src[lane + 32 * i];
                             const float4 h = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
                             src[lane + 32 * i] = h;
@@ -572,10 +575,11 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc_packed(TcBatch p)
                             ok = false;
                             break;
                         }
-                        float4* src = reinterpret_cast<float4*>(ringA + sa * TC_A_BYTES) + ew * 256;
-                        float4* dst = reinterpret_cast<float4*>(ringL + sa * TC_A_BYTES) + ew * 256;
+                        constexpr int PW = 256;   // float4 per converter warp
+                        float4* src = reinterpret_cast<float4*>(ringA + sa * TC_A_BYTES) + ew * PW;
+                        float4* dst = reinterpret_cast<float4*>(ringL + sa * TC_A_BYTES) + ew * PW;
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) {
+                        for (int e = 0; e < PW / 32; ++e) {
                             const float4 x = src[lane + 32 * e];
                             const float4 h = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
                             src[lane + 32 * e] = h;
@@ -1312,6 +1316,34 @@ OpOut op_output(cofem_ctx* c) {
         return OpOut{t->g2.part, 1, 0, t->g2.grp_seg, t->G * TC_BM, t->f8 ? F8_RFAC : 1.0f};
     const int S2 = c->kind == COFEM_OP_DENSE ? c->S2 : 1;
     return OpOut{c->U, S2, (size_t)c->Qcap * c->Dp, nullptr, 0};
+}
+
+// The CG loop of the fit graph runs the operator's first product at the end
+// of the loop body, after the direction kernel that writes its input (so that
+// it joins the step by a programmatic edge), and the rest of the operator at
+// the start of the next iteration: the two-pass tensor-core forms only.
+bool tc_rotatable(cofem_ctx* c) {
+    TcPlan* t = (TcPlan*)c->tc;
+    return c->kind == COFEM_OP_DENSE && t && !t->fused;
+}
+
+void launch_tc_first_product(Sink& s, cofem_ctx* c) {
+    TcPlan* t = (TcPlan*)c->tc;
+    void (*gemm)(TcParams) = t->f8 ? k_gemm8 : (t->tf ? k_gemm_tc<true> : k_gemm_tc<false>);
+    const unsigned nthreads = t->f8 ? F8_THREADS : (unsigned)tc_threads(t->tf);
+    s.launch_pdl(gemm, dim3(t->g1.nCTA), dim3(nthreads), t->smem, t->g1.p);
+}
+
+void launch_tc_rest(Sink& s, cofem_ctx* c, int Q, int mode) {
+    TcPlan* t = (TcPlan*)c->tc;
+    const SplitOut st{t->Ts, t->tf ? 2 : 1, t->QS, t->QH, t->f8 ? F8_BSCALE : 1.0f};
+    void (*gemm)(TcParams) = t->f8 ? k_gemm8 : (t->tf ? k_gemm_tc<true> : k_gemm_tc<false>);
+    const unsigned nthreads = t->f8 ? F8_THREADS : (unsigned)tc_threads(t->tf);
+    const int nblk = (int)((c->Np + 1023) / 1024);
+    s.launch_pdl(k_tc_reduce_T, dim3(nblk, Q), dim3(256), 0, t->g1.part, t->g1.grp_seg, t->G * TC_BM, Q, c->Np, st,
+                 c->tt_part, nblk, c->counters + 8, c->ctl, mode, t->f8 ? (const float*)c->scale8 : (const float*)nullptr,
+                 t->f8 ? F8_RFAC : 1.0f);
+    s.launch_pdl(gemm, dim3(t->g2.nCTA), dim3(nthreads), t->smem, t->g2.p);
 }
 
 // In the CG loop (OP_CG, OP_TIME) the split of P is already in Vs (written by

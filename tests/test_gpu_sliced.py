@@ -89,22 +89,35 @@ def _check_product(out, phi_b, Xh, Xl, cols=None, tol1=TOL_S1, tol2=TOL_S2):
 SLICED_TOL = (2.0 ** -34, 2.0 ** -26)
 
 
+def _stored_dictionary(phi, precision):
+    """The dictionary the handle computes with, FP64: bf16(Phi), or the FP8
+    form's diag(s) decode(codes) (the parity module's E4M3 quantiser)."""
+    if precision == "bf16":
+        return bf16_round(phi).astype(np.float64)
+    from test_gpu_parity import e4m3_quantise
+    sc, dec = e4m3_quantise(phi)
+    return sc.astype(np.float64)[:, None] * dec
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
 @pytest.mark.parametrize("path", ["sliced", "pairs"])
 @pytest.mark.parametrize("N,D,Q", [(256, 1024, 1), (300, 1000, 17), (512, 2048, 33), (640, 1536, 48),
                                    (129, 4100, 21)])
-def test_accurate_product_matches_fp64(cf, path, N, D, Q):
+def test_accurate_product_matches_fp64(cf, precision, path, N, D, Q):
+    if precision == "fp8" and 3 * Q > 128:
+        pytest.skip("the FP8 operator takes 3(K+1) <= 128")
     rng = np.random.default_rng(N * 7 + Q)
     phi = (rng.standard_normal((N, D)) / np.sqrt(N)).astype(np.float32)
     Xh, Xl = _pair_block(rng, Q, D)
     rp = cf.COFEM_RESIDUAL_SLICED if path == "sliced" else cf.COFEM_RESIDUAL_FP32_PAIRS
+    prec = cf.COFEM_BF16 if precision == "bf16" else cf.COFEM_FP8_E4M3
     out = np.empty((Q, D), np.float64)
-    with cf.CoFEM(N, D, cf.COFEM_OP_DENSE, phi, precision=cf.COFEM_BF16, check_residual=1,
-                  residual_path=rp) as m:
+    with cf.CoFEM(N, D, cf.COFEM_OP_DENSE, phi, precision=prec, check_residual=1, residual_path=rp) as m:
         cf.cofem_accurate_product(m.h, Xh, Xl, Q, out)
         out2 = np.empty_like(out)
         cf.cofem_accurate_product(m.h, Xh, Xl, Q, out2)   # the same bits on a second call
     np.testing.assert_array_equal(out, out2)
-    pb = bf16_round(phi).astype(np.float64)
+    pb = _stored_dictionary(phi, precision)
     _check_product(out, pb, Xh, Xl)
     if path == "sliced":
         _check_product(out, pb, Xh, Xl, None, *SLICED_TOL)
@@ -145,19 +158,27 @@ def _sliced_model(M, e, digits):
     return sum(acc[d] * (1 << (8 * (4 - d))) for d in range(5))
 
 
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
 @pytest.mark.parametrize("N,D,Q", [(256, 1024, 1), (300, 1000, 17), (512, 2048, 33)])
-def test_sliced_product_is_the_exact_integer_scheme(cf, N, D, Q):
+def test_sliced_product_is_the_exact_integer_scheme(cf, precision, N, D, Q):
     """The tensor cores sum the digit products exactly: the sliced product
     equals, bit for bit, the same slicing evaluated in 64-bit integers on the
-    host (both products, exponents and digits as the kernels define them)."""
+    host (both products, exponents and digits as the kernels define them; the
+    FP8 form slices the codes' values and scales t by s_i^2)."""
     rng = np.random.default_rng(N * 7 + Q)
     phi = (rng.standard_normal((N, D)) / np.sqrt(N)).astype(np.float32)
     Xh, Xl = _pair_block(rng, Q, D)
     out = np.empty((Q, D), np.float64)
-    with cf.CoFEM(N, D, cf.COFEM_OP_DENSE, phi, precision=cf.COFEM_BF16, check_residual=1,
+    prec = cf.COFEM_BF16 if precision == "bf16" else cf.COFEM_FP8_E4M3
+    with cf.CoFEM(N, D, cf.COFEM_OP_DENSE, phi, precision=prec, check_residual=1,
                   residual_path=cf.COFEM_RESIDUAL_SLICED) as m:
         cf.cofem_accurate_product(m.h, Xh, Xl, Q, out)
-    pb = bf16_round(phi)
+    if precision == "bf16":
+        pb, rs2 = bf16_round(phi), None
+    else:
+        from test_gpu_parity import e4m3_quantise
+        sc, dec = e4m3_quantise(phi)
+        pb, rs2 = dec.astype(np.float32), sc.astype(np.float64) ** 2
     E1 = _ilogb(np.abs(pb).max(axis=1)) + 2
     E2 = _ilogb(np.abs(pb).max(axis=0)) + 2
     mx = np.abs(Xh).max(axis=1)
@@ -166,6 +187,8 @@ def test_sliced_product_is_the_exact_integer_scheme(cf, N, D, Q):
     I = np.rint(Xh.astype(np.float64) * sc).astype(np.int64) + np.rint(Xl.astype(np.float64) * sc).astype(np.int64)
     Z1 = _sliced_model(pb, E1, [d.T for d in _int_digits(I)])                      # N x Q
     t = Z1.astype(np.float64) * 2.0 ** (E1[:, None] + F[None, :] - 48)
+    if rs2 is not None:
+        t = t * rs2[:, None]
     tm = np.abs(t).max(axis=0)
     G = np.where(tm > 0, _ilogb(np.where(tm > 0, tm, 1.0)) + 3, 0)
     It = np.rint(t * 2.0 ** (40 - G[None, :])).astype(np.int64)
