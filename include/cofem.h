@@ -373,9 +373,12 @@ cofem_status cofem_server_create(cofem_server** out, long long hbm_budget_bytes,
  * Requests: dense dictionaries, precision COFEM_BF16 or COFEM_F32_TF32X3,
  * rr_period 0, BF16 with K <= 41 (else cofem_submit returns UNSUPPORTED).
  * At most max_fits (1..1024) fits are prepared or in the step at once; the
- * HBM budget bounds them too.  Same submit / poll / wait / destroy calls. */
+ * HBM budget bounds them too.  flags: 0, or COFEM_SERVE_HOST_LOOP to launch
+ * every step from the host (no graph; slower, but profilers see each
+ * kernel).  Same submit / poll / wait / destroy calls. */
+#define COFEM_SERVE_HOST_LOOP 1
 cofem_status cofem_server_create_packed(cofem_server** out, long long hbm_budget_bytes, int max_fits,
-                                        int prep_threads);
+                                        int prep_threads, int flags);
 
 /* Counters of a packed server (zero for an independent one): graph launches
  * of the step loop, steps run, fit-steps (the sum over steps of the fits in

@@ -45,6 +45,7 @@ COFEM_TOEPLITZ_DIRECT = 1
 COFEM_TOEPLITZ_FFT = 2
 COFEM_PRIOR_GAUSSIAN = 0
 COFEM_PRIOR_RECTIFIED = 1
+COFEM_SERVE_HOST_LOOP = 1
 COFEM_RESIDUAL_AUTO = 0
 COFEM_RESIDUAL_FP32_PAIRS = 1
 COFEM_RESIDUAL_SLICED = 2
@@ -135,7 +136,7 @@ def _load():
         "cofem_apply_dense_noalloc": (i, [vp, ll, ll, ll, vp, i, vp, d, vp, vp]),
         "cofem_estimate_bytes": (ll, [i, ll, ll, ll, i, i]),
         "cofem_server_create": (i, [C.POINTER(vp), ll, i]),
-        "cofem_server_create_packed": (i, [C.POINTER(vp), ll, i, i]),
+        "cofem_server_create_packed": (i, [C.POINTER(vp), ll, i, i, i]),
         "cofem_server_get_stats": (i, [vp, C.POINTER(cofem_server_stats)]),
         "cofem_submit": (i, [vp, C.POINTER(cofem_request), C.POINTER(C.c_ulonglong)]),
         "cofem_poll": (i, [vp, C.c_ulonglong, C.POINTER(i)]),
@@ -267,9 +268,10 @@ def cofem_server_create(hbm_budget_bytes: int, max_slots: int) -> int:
     return h.value
 
 
-def cofem_server_create_packed(hbm_budget_bytes: int, max_fits: int, prep_threads: int = 4) -> int:
+def cofem_server_create_packed(hbm_budget_bytes: int, max_fits: int, prep_threads: int = 4, flags: int = 0) -> int:
     h = C.c_void_p()
-    _check(lib.cofem_server_create_packed(C.byref(h), int(hbm_budget_bytes), int(max_fits), int(prep_threads)))
+    _check(lib.cofem_server_create_packed(C.byref(h), int(hbm_budget_bytes), int(max_fits), int(prep_threads),
+                                          int(flags)))
     return h.value
 
 

@@ -108,6 +108,7 @@ struct cofem_server {
     std::condition_variable cv_engine;
     volatile int* pending_h = nullptr;   // mapped host flag: new fits are ready
     int* pending_d = nullptr;
+    bool host_loop = false;    // COFEM_SERVE_HOST_LOOP: one step per host launch, no graph
     cofem_server_stats stats{};
 };
 
@@ -487,17 +488,9 @@ cudaError_t upload(StepTables& tb, const StepHost& h, cudaStream_t st) {
     return cudaMemsetAsync(tb.steps, 0, sizeof(unsigned), st);
 }
 
-// The step graph for the fits of the groups in `mask`, at the tables' capacities.
-cudaError_t build_graph(cofem_server* s, const StepTables& tb, int mask, StepGraph& sg, cudaStream_t st, bool pdl) {
-    sg.reset();
-    cudaError_t e = cudaGraphCreate(&sg.g, 0);
-    if (e) return e;
-    Sink root;
-    root.stream = st;
-    root.graph = sg.g;
-    root.pdl = pdl;
-    const cudaGraphConditionalHandle h = root.make_handle(1u, true);
-    Sink body = root.conditional(h, cudaGraphCondTypeWhile);
+// One packed step's launches into `body` (a graph's loop body, or a stream
+// when the host drives the loop); h is the loop's condition (0: none).
+void record_step(cofem_server* s, const StepTables& tb, int mask, Sink& body, cudaGraphConditionalHandle h) {
     for (int pr = 0; pr < 2; ++pr) {
         for (int gi = 0; gi < 2; ++gi) {
             if (!(mask & (1 << gi))) continue;
@@ -519,6 +512,20 @@ cudaError_t build_graph(cofem_server* s, const StepTables& tb, int mask, StepGra
     launch_init_packed(body, tb.vs, tb.map[0], tb.counts + 0, tb.cap_blk[0]);
     // a launch runs at most 4096 steps before the host looks again
     launch_packed_status(body, tb.vs, tb.counts + 3, tb.status, s->pending_d, tb.steps, 4096u, h);
+}
+
+// The step graph for the fits of the groups in `mask`, at the tables' capacities.
+cudaError_t build_graph(cofem_server* s, const StepTables& tb, int mask, StepGraph& sg, cudaStream_t st, bool pdl) {
+    sg.reset();
+    cudaError_t e = cudaGraphCreate(&sg.g, 0);
+    if (e) return e;
+    Sink root;
+    root.stream = st;
+    root.graph = sg.g;
+    root.pdl = pdl;
+    const cudaGraphConditionalHandle h = root.make_handle(1u, true);
+    Sink body = root.conditional(h, cudaGraphCondTypeWhile);
+    record_step(s, tb, mask, body, h);
     e = root.err ? root.err : body.err;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&sg.x, sg.g, 0);
     if (e != cudaSuccess) sg.reset();
@@ -572,7 +579,13 @@ void engine_loop(cofem_server* s) {
             if (!kept)
                 for (auto& g : graphs) g.reset();
             if (e == cudaSuccess) e = upload(tb, host, st);
-            if (e == cudaSuccess && !graphs[host.mask].x) {
+            if (e == cudaSuccess && s->host_loop) {   // one step from the host (profilers see each launch)
+                Sink direct;
+                direct.stream = st;
+                direct.pdl = pdl;
+                record_step(s, tb, host.mask, direct, 0);
+                e = direct.err;
+            } else if (e == cudaSuccess && !graphs[host.mask].x) {
                 e = build_graph(s, tb, host.mask, graphs[host.mask], st, pdl);
                 if (e != cudaSuccess && pdl) {   // programmatic edges refused: plain ones
                     (void)cudaGetLastError();
@@ -584,7 +597,7 @@ void engine_loop(cofem_server* s) {
                     ++s->stats.graphs_built;
                 }
             }
-            if (e == cudaSuccess) e = cudaGraphLaunch(graphs[host.mask].x, st);
+            if (e == cudaSuccess && !s->host_loop) e = cudaGraphLaunch(graphs[host.mask].x, st);
         }
         retire(s, done);   // the fits that finished in the previous launch, while this one runs
         if (!run) continue;
@@ -629,10 +642,12 @@ void engine_loop(cofem_server* s) {
 extern "C" {
 
 cofem_status cofem_server_create_packed(cofem_server** out, long long hbm_budget_bytes, int max_fits,
-                                        int prep_threads) {
-    if (!out || hbm_budget_bytes <= 0 || max_fits < 1 || max_fits > 1024 || prep_threads < 1 || prep_threads > 64)
+                                        int prep_threads, int flags) {
+    if (!out || hbm_budget_bytes <= 0 || max_fits < 1 || max_fits > 1024 || prep_threads < 1 || prep_threads > 64 ||
+        (flags & ~COFEM_SERVE_HOST_LOOP))
         return cofem_set_error(COFEM_ERR_INVALID_ARG,
-                               "need out, hbm_budget_bytes > 0, 1 <= max_fits <= 1024, 1 <= prep_threads <= 64");
+                               "need out, hbm_budget_bytes > 0, 1 <= max_fits <= 1024, 1 <= prep_threads <= 64 "
+                               "and flags in COFEM_SERVE_HOST_LOOP");
     cofem_server* s = new cofem_server();
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
@@ -647,6 +662,7 @@ cofem_status cofem_server_create_packed(cofem_server** out, long long hbm_budget
     *hp = 0;
     s->pending_h = hp;
     s->packed = true;
+    s->host_loop = (flags & COFEM_SERVE_HOST_LOOP) != 0;
     s->budget = hbm_budget_bytes;
     s->max_fits = max_fits;
     s->max_slots = prep_threads;

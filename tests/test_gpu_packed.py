@@ -164,3 +164,25 @@ def test_packed_failing_request_is_isolated(cf):
         cf.cofem_server_destroy(srv)
     assert rb.status == cf.COFEM_ERR_NONFINITE and b"y contains NaN" in rb.message
     assert rg.status == 0 and np.all(np.isfinite(g["mu"].cpu().numpy()))
+
+
+def test_packed_host_loop_matches_graph(cf):
+    """The host-driven step loop (COFEM_SERVE_HOST_LOOP: the same kernels
+    launched one step at a time, no graph) gives the same bits as the graph's
+    device-side loop; dictionaries of 8192 to 16384 columns (together larger
+    than L2, as for a profiler's capture of the packed GEMM)."""
+    probs = [(dense_gaussian(D // 4, D, D // 50, 20.0, seed=200 + i), K)
+             for i, (D, K) in enumerate([(16384, 16), (8192, 32), (12288, 8), (16384, 32)])]
+    outs = []
+    for flags in (0, cf.COFEM_SERVE_HOST_LOOP):
+        srv = cf.cofem_server_create_packed(40 << 30, 8, 2, flags)
+        try:
+            reqs = [_make(cf, p, K, 2, cf.COFEM_BF16) for p, K in probs]
+            rs = [cf.cofem_wait(srv, t) for t in [cf.cofem_submit(srv, r["req"]) for r in reqs]]
+            assert all(r.status == 0 for r in rs), [r.message for r in rs if r.status != 0]
+            outs.append([_np(r) for r in reqs])
+        finally:
+            cf.cofem_server_destroy(srv)
+    for a, b in zip(*outs):
+        for k in ("mu", "s", "alpha", "it"):
+            np.testing.assert_array_equal(a[k], b[k])
