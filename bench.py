@@ -451,6 +451,10 @@ def run_ours(args):
                        "traffic": None, "peak_source": f"derived: {_SMS} SMs x {_FP32_LANES} FP32 lanes x 1 op "
                        f"x {sm_mhz:.0f} MHz", "ms_per_launch": ms_first, "algorithmic_ops_per_launch": ops}
         roof_df["ms_per_accurate_residual"] = ms_res
+        # the rest of a fit (CG update and direction, the operator's hand-offs
+        # inside the step, initialisation, M-step), per CG step
+        per_fit["other"] = ms / max(1, args.steps) - per_fit["accurate_residuals"] - per_fit["cg_operator"]
+        per_fit["other_us_per_cg_step"] = 1000.0 * per_fit["other"] / max(1.0, float(np.sum(all_iters[-1])))
         roof_df["per_fit_ms"] = per_fit
         if per_fit["accurate_residuals"] > per_fit["cg_operator"]:
             roof, roof_df = roof_df, roof

@@ -209,6 +209,14 @@ WORKLOADS = {
     "dense_n4096_d16384_k32_bf16": dict(
         kind="dense", N=4096, D=16384, d=164, snr_db=30.0, K=32, T=30,
         cg_tol=1e-5, cg_maxit=400, precision="bf16", rr_period=20),
+    # profiling sizes of the FP8 and 3xTF32 operators (each product's image
+    # larger than L2: 128 MiB of codes, 256 MiB of FP32)
+    "dense_n8192_d16384_k32_fp8": dict(
+        kind="dense", N=8192, D=16384, d=164, snr_db=30.0, K=32, T=30,
+        cg_tol=1e-5, cg_maxit=400, precision="fp8", rr_period=0),
+    "dense_n4096_d16384_k32_tf32x3": dict(
+        kind="dense", N=4096, D=16384, d=164, snr_db=30.0, K=32, T=30,
+        cg_tol=1e-5, cg_maxit=400, precision="tf32x3", rr_period=0),
     "dense_n8192_d32768_k32_f32": dict(
         kind="dense", N=8192, D=32768, d=327, snr_db=30.0, K=32, T=30,
         cg_tol=1e-5, cg_maxit=400, precision="f32", rr_period=0),
