@@ -312,16 +312,29 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _launches_per_fit(cg_iters, op_cg, step, n_rr=0, n_check=0, op_rr=0, graph=True):
+def _launches_per_fit(cg_iters, op_cg, step, n_rr=0, n_check=0, op_rr=0, graph=True, rotated=False):
     """Kernels of one fit: b = beta Phi^T y, finiteness check of y, fit set-up;
     per EM iteration init + M-step; per CG step the operator kernels (op_cg)
     and the update/direction kernels (step); per residual replacement the
     accurate residual (op_rr kernels); per true-residual check the accurate
-    residual, the check kernel and (in the graph) the CG loop's gate."""
+    residual, the check kernel and (in the graph) the CG loop's gate.  In the
+    graph a rotated CG loop (two-pass tensor-core operator: the first product
+    of a step at the end of the previous one) adds the first product before
+    each entry into the loop (every EM iteration, or every verification round
+    when checks run); with replacement, the graph's loop ends at each
+    replacement step, and the direction (and the first product, rotated) run
+    again after the replacement, with two gate kernels per run of steps (one
+    run per replacement, plus one per verification round)."""
     n = 3
     for u in cg_iters:
         n += 2 + (op_cg + step) * int(u)
-    return n + op_rr * n_rr + (op_rr + 1 + (1 if graph else 0)) * n_check
+    n += op_rr * n_rr + (op_rr + 1 + (1 if graph else 0)) * n_check
+    if graph:
+        if rotated:
+            n += n_check if n_check else len(cg_iters)
+        if n_rr:
+            n += n_rr * (2 if rotated else 1) + 2 * (n_rr + n_check)
+    return n
 
 
 def run_ours(args):
@@ -472,7 +485,8 @@ def run_ours(args):
     e2e = {"value": ws * e2e_steps * T / e2e_s, "unit": "EM-iter/s", "h2d_bytes_per_step": int(N * 4),
            "d2h_bytes_per_step": int(3 * D * 4 + T * 4 + 4)}
 
-    launches = sum(_launches_per_fit(it, op_cg, op_step, nr, nc, op_rr, not args.no_graph)
+    rotated = prob.kind == "dense" and path == cf.COFEM_PATH_TWO_PASS
+    launches = sum(_launches_per_fit(it, op_cg, op_step, nr, nc, op_rr, not args.no_graph, rotated)
                    for it, (nr, nc) in zip(all_iters, fit_stats))
     precision_form = None
     if run["rr_period"] > 0:

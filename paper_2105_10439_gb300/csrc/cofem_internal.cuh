@@ -573,6 +573,13 @@ __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, int v) {
     if (h) cudaGraphSetConditional(h, v ? 1u : 0u);
 }
 
+// CG step u is a residual-replacement step (Alg. 2 with replacement every
+// rr_period steps): the update's decision, read again by the kernels of the
+// step that a fit graph defers until after the replacement.
+__device__ __forceinline__ bool rr_step(const DevCtl* ctl) {
+    return ctl->rr_period > 0 && ctl->u % ctl->rr_period == 0;
+}
+
 // ---------------------------------------------------------------------------
 // Handle
 // ---------------------------------------------------------------------------
@@ -658,7 +665,7 @@ void launch_fit_setup(Sink& s, cofem_ctx* c, int Q);                 // alpha ->
 void launch_cg_init(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg);
 void launch_cg_update(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_rr,
                       cudaGraphConditionalHandle h_cg);
-void launch_cg_direction(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg);
+void launch_cg_direction(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg, bool defer_rr = false);
 void launch_mstep(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_em);
 void launch_probe_fill(cudaStream_t st, unsigned long long seed, int t, int K, long long D,
                        long long ld, float* out);
@@ -682,7 +689,7 @@ int true_residual_kernels(cofem_ctx* c);
 cudaError_t df_kernel_attributes();
 void launch_df_first_product(Sink& s, cofem_ctx* c, int Q);   // dense only
 void launch_df_check(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_vf);
-void launch_cg_gate(Sink& s, cofem_ctx* c, cudaGraphConditionalHandle h_cg);
+void launch_cg_gate(Sink& s, cofem_ctx* c, cudaGraphConditionalHandle h_set, cudaGraphConditionalHandle h_clear = 0);
 void launch_df_gram(Sink& s, cofem_ctx* c, int Q, double* out);   // Phi~^T Phi~ (X + Xlo), dense
 
 // Packed serving (kernels_tc.cu, kernels_vec.cu, cofem_api.cu)
@@ -734,7 +741,7 @@ void launch_tc_operator(Sink& s, cofem_ctx* c, int Q, const float* V, int mode);
 // the operator of the CG loop split in two: the first product alone, and the
 // T reduction with the second product (two-pass tensor-core forms)
 bool tc_rotatable(cofem_ctx* c);
-void launch_tc_first_product(Sink& s, cofem_ctx* c);
+void launch_tc_first_product(Sink& s, cofem_ctx* c, bool defer_rr = false);
 void launch_tc_rest(Sink& s, cofem_ctx* c, int Q, int mode);
 // Split image of the CG direction block (written by k_cg_init / k_cg_direction)
 // and the description of the operator output (null / dense slices otherwise).

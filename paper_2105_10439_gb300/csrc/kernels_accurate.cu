@@ -435,10 +435,14 @@ __global__ __launch_bounds__(NT) void k_df_check(DevCtl* ctl, const float* __res
     }
 }
 
-// Enters the CG loop of a verification round only if some column is active
-// and the CG budget is not spent.
-__global__ void k_cg_gate(DevCtl* ctl, cudaGraphConditionalHandle h_cg) {
-    if (threadIdx.x == 0) set_cond(h_cg, ctl->any_active && ctl->u < ctl->maxit);
+// Loop gate: h_set = (some column is active and the CG budget is not spent),
+// the entry condition of a CG loop (or of a run of CG steps up to a residual
+// replacement); h_clear = 0.
+__global__ void k_cg_gate(DevCtl* ctl, cudaGraphConditionalHandle h_set, cudaGraphConditionalHandle h_clear) {
+    if (threadIdx.x == 0) {
+        set_cond(h_set, ctl->any_active && ctl->u < ctl->maxit);
+        set_cond(h_clear, 0);
+    }
 }
 
 int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
@@ -601,6 +605,6 @@ void launch_df_check(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_
              c->part, c->counters + 12, c->res_dev, h_vf, tc_direction_split(c));
 }
 
-void launch_cg_gate(Sink& s, cofem_ctx* c, cudaGraphConditionalHandle h_cg) {
-    s.launch(k_cg_gate, dim3(1), dim3(32), 0, c->ctl, h_cg);
+void launch_cg_gate(Sink& s, cofem_ctx* c, cudaGraphConditionalHandle h_set, cudaGraphConditionalHandle h_clear) {
+    s.launch(k_cg_gate, dim3(1), dim3(32), 0, c->ctl, h_set, h_clear);
 }

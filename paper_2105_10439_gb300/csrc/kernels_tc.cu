@@ -41,7 +41,8 @@ namespace {
 
 constexpr int TC_BM = 128, TC_BK = 64;   // BF16 tile: 128 rows x 64 bf16 (128-byte rows)
 constexpr int TC_BK32 = 32;               // TF32 tile: 128 rows x 32 fp32 (128-byte rows)
-constexpr int TC_NA = 8, TC_NA_TF = 5, TC_NB = 3;
+constexpr int TC_NA = 8, TC_NB = 3;
+constexpr int TC_NLO = 3;   // TF32: Phi_lo tiles in a ring of their own
 // Epilogue warps: four (one per TMEM sub-partition) convert the TF32 tiles;
 // all of them drain the accumulators, the warps of a sub-partition splitting
 // the row tiles.  (Eight converter warps instead of four left the 3xTF32
@@ -69,7 +70,13 @@ struct TcParams {
     const int* seg_base;  // first segment id of each CTA
     float* part;          // [segment][Q][G * 128]
     unsigned* flags;      // error flag word (DevCtl::flags)
+    const DevCtl* defer;  // the CG step's first product in a fit graph's loop: skipped at replacement steps
 };
+
+// The first product of a CG step that a fit graph's loop defers past a
+// residual replacement (it runs again after the replacement, outside the
+// loop): the launch does nothing.  Read after the programmatic wait.
+__device__ __forceinline__ bool gemm_deferred(const TcParams& p) { return p.defer && rr_step(p.defer); }
 
 // TMEM -> segment partials for one epilogue warp: accumulator r (r0 <= r <
 // valid, step rstep) holds, in this warp's 32 TMEM lanes (rows), the split
@@ -110,17 +117,21 @@ __device__ __forceinline__ void drain_tmem(uint32_t tbase, int r0, int rstep, in
 // Tensor-core skinny GEMM.  TF = false: A, B bf16 (B = 3-term split), one MMA
 // chain per tile.  TF = true: A, B fp32 read as TF32 (B = [P_hi | P_lo]); the
 // epilogue warps round each A tile to Phi_hi = tf32_rn(A) in place and write
-// Phi_lo = tf32_rn(A - Phi_hi) beside it, and a second MMA chain adds
-// Phi_lo [P_hi | P_lo] into the same accumulator columns (all four products).
+// Phi_lo = tf32_rn(A - Phi_hi) into a ring of its own (TC_NLO tiles, so that
+// the A ring holds whole units fetched by one 64 KiB copy, as in the BF16
+// form: 0.657 against 0.707 ms per application at 8192 x 32768 with single
+// tiles and Phi_lo beside each), and a second MMA chain adds Phi_lo [P_hi |
+// P_lo] into the same accumulator columns (all four products).
 template <bool TF>
 __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc(TcParams p) {
-    constexpr int NA = TF ? TC_NA_TF : TC_NA;
+    constexpr int NA = TC_NA;
     constexpr int KE = TF ? TC_BK32 : TC_BK;    // elements per 128-byte tile row
-    // A-ring element: one tile (TF32, converted tile by tile) or the G row
-    // tiles of a unit, fetched as one bulk copy (a copy costs a fixed ~0.3 us
-    // of issue time, so fewer, larger copies keep the stream at HBM rate)
-    const int EPT = TF ? 1 : p.G;
-    const int NE = TF ? NA : NA / p.G;           // ring elements
+    // A-ring element: the G row tiles of a unit, fetched as one bulk copy (a
+    // copy costs a fixed ~0.3 us of issue time, so fewer, larger copies keep
+    // the stream at HBM rate); TF32 converts it tile by tile, Phi_lo into a
+    // ring of its own
+    const int EPT = p.G;
+    const int NE = NA / p.G;                     // ring elements
     const uint32_t E_BYTES = (uint32_t)EPT * TC_A_BYTES;
     constexpr int KM = TF ? 8 : 16;             // K of one MMA instruction
     griddep_launch();   // the next kernel may start its prologue; it waits for this grid's completion
@@ -129,14 +140,15 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc(TcParams p) {
     const uint32_t B_BYTES = (uint32_t)p.QS * 128u;
     uint8_t* ringA = smem;
     uint8_t* ringL = smem + NA * TC_A_BYTES;                      // TF32 only: Phi_lo tiles
-    uint8_t* ringB = ringL + (TF ? NA * TC_A_BYTES : 0);
+    uint8_t* ringB = ringL + (TF ? TC_NLO * TC_A_BYTES : 0);
     uint64_t* bars = (uint64_t*)(ringB + TC_NB * B_BYTES);
     uint64_t* a_full = bars;
     uint64_t* a_empty = bars + NA;
-    uint64_t* lo_full = bars + 2 * NA;                            // TF32 only
-    uint64_t* b_full = bars + 3 * NA;
-    uint64_t* b_empty = bars + 3 * NA + TC_NB;
-    uint64_t* acc_full = bars + 3 * NA + 2 * TC_NB;
+    uint64_t* lo_full = bars + 2 * NA;                            // TF32 only [TC_NLO]
+    uint64_t* lo_empty = lo_full + TC_NLO;                        // TF32 only [TC_NLO]
+    uint64_t* b_full = lo_empty + TC_NLO;
+    uint64_t* b_empty = b_full + TC_NB;
+    uint64_t* acc_full = b_empty + TC_NB;
     uint64_t* acc_empty = acc_full + 1;
     uint64_t* drain = acc_full + 2;
     uint32_t* tmem_slot = (uint32_t*)(acc_full + 3);
@@ -147,7 +159,10 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc(TcParams p) {
         for (int i = 0; i < NA; ++i) {
             mbar_init(smem_u32(a_full + i), 1);
             mbar_init(smem_u32(a_empty + i), 1);
+        }
+        for (int i = 0; i < TC_NLO; ++i) {
             mbar_init(smem_u32(lo_full + i), 4);
+            mbar_init(smem_u32(lo_empty + i), 1);
         }
         for (int i = 0; i < TC_NB; ++i) {
             mbar_init(smem_u32(b_full + i), 1);
@@ -172,7 +187,7 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc(TcParams p) {
     const uint32_t tmem = *tmem_slot;
 
     const long long u0 = (long long)blockIdx.x * p.W / gridDim.x;
-    const long long u1 = (long long)(blockIdx.x + 1) * p.W / gridDim.x;
+    long long u1 = (long long)(blockIdx.x + 1) * p.W / gridDim.x;   // u0 when the launch is deferred
     long long na = 0, nb = 0;   // bulk loads issued into the A and B rings (producer thread)
     const char* Ab = (const char*)p.A;
     const char* Bb = (const char*)p.B;
@@ -186,51 +201,45 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc(TcParams p) {
             // writes: fill the A ring before waiting for the previous kernel
             // (programmatic launch), whose output is the B operand.
             long long npre = 0;
-            for (long long u = u0; u < u1 && npre < NE; ++u) {
-                const int valid = min(p.G, p.M_tiles - (int)(u / p.K_tiles) * p.G);
-                for (int r = 0; r < (TF ? valid : 1) && npre < NE; ++r, ++npre) {
-                    mbar_expect_tx(smem_u32(a_full + npre), E_BYTES);
-                    bulk_load_hint(smem_u32(ringA + npre * E_BYTES), Ab + ((size_t)u * p.G + r) * TC_A_BYTES,
-                                   E_BYTES, smem_u32(a_full + npre), evict_first);
-                }
+            for (long long u = u0; u < u1 && npre < NE; ++u, ++npre) {
+                mbar_expect_tx(smem_u32(a_full + npre), E_BYTES);
+                bulk_load_hint(smem_u32(ringA + npre * E_BYTES), Ab + (size_t)u * p.G * TC_A_BYTES, E_BYTES,
+                               smem_u32(a_full + npre), evict_first);
             }
             na = npre;
             griddep_wait();
+            if (gemm_deferred(p)) {   // the ring fill issued above lands before the CTA exits
+                for (long long s = 0; s < npre; ++s) mbar_drain(smem_u32(a_full + s), 0);
+                u1 = u0;
+            }
             long long ea = 0;   // A ring elements walked
             for (long long u = u0; u < u1; ++u) {
-                const int g = (int)(u / p.K_tiles), k = (int)(u % p.K_tiles);
-                const int valid = min(p.G, p.M_tiles - g * p.G);
+                const int k = (int)(u % p.K_tiles);
                 int slot = (int)(nb % TC_NB);
                 long long use = nb / TC_NB;
                 if (use > 0 && !mbar_wait(smem_u32(b_empty + slot), (uint32_t)((use - 1) & 1), abort_flag)) break;
                 mbar_expect_tx(smem_u32(b_full + slot), B_BYTES);
                 bulk_load(smem_u32(ringB + slot * B_BYTES), Bb + (size_t)k * B_BYTES, B_BYTES, smem_u32(b_full + slot));
                 ++nb;
-                bool ok = true;
-                for (int r = 0; r < (TF ? valid : 1); ++r, ++ea) {
-                    if (ea < npre) continue;   // issued before the wait
-                    slot = (int)(ea % NE);
-                    use = ea / NE;
-                    if (use > 0 && !mbar_wait(smem_u32(a_empty + slot), (uint32_t)((use - 1) & 1), abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    // BF16: all G tiles of the unit (tiles beyond M_tiles are zero in the image)
-                    mbar_expect_tx(smem_u32(a_full + slot), E_BYTES);
-                    bulk_load_hint(smem_u32(ringA + slot * E_BYTES), Ab + ((size_t)u * p.G + r) * TC_A_BYTES,
-                                   E_BYTES, smem_u32(a_full + slot), evict_first);
-                    ++na;
-                }
-                if (!ok) break;
+                if (ea++ < npre) continue;   // issued before the wait
+                slot = (int)((ea - 1) % NE);
+                use = (ea - 1) / NE;
+                if (use > 0 && !mbar_wait(smem_u32(a_empty + slot), (uint32_t)((use - 1) & 1), abort_flag)) break;
+                // all G tiles of the unit (tiles beyond M_tiles are zero in the image)
+                mbar_expect_tx(smem_u32(a_full + slot), E_BYTES);
+                bulk_load_hint(smem_u32(ringA + slot * E_BYTES), Ab + (size_t)u * p.G * TC_A_BYTES, E_BYTES,
+                               smem_u32(a_full + slot), evict_first);
+                ++na;
             }
         }
     } else if (warp == 1) {
         // the bounded barrier waits below start once the previous kernel has
         // completed (a programmatic launch can begin while it still runs)
         griddep_wait();
+        if (gemm_deferred(p)) u1 = u0;
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            long long ma = 0, mb = 0;   // ring positions consumed
+            long long ma = 0, mb = 0, ml = 0;   // ring positions consumed (A, B, Phi_lo)
             int nseg = 0;
             long long u = u0;
             bool ok = true;
@@ -248,23 +257,22 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc(TcParams p) {
                         break;
                     }
                     const uint64_t db = desc_sw128(smem_u32(ringB + sb * B_BYTES));
-                    int sa = 0;
+                    const int sa = (int)(ma % NE);
+                    if (!mbar_wait(smem_u32(a_full + sa), (uint32_t)((ma / NE) & 1), abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
                     for (int r = 0; r < valid; ++r) {
-                        if (TF || r == 0) {
-                            sa = (int)(ma % NE);
-                            const uint32_t par = (uint32_t)((ma / NE) & 1);
-                            if (!mbar_wait(smem_u32(a_full + sa), par, abort_flag)) {
-                                ok = false;
-                                break;
-                            }
-                            if (TF && !mbar_wait(smem_u32(lo_full + sa), par, abort_flag)) {   // hi / lo written
+                        const int sl = (int)(ml % TC_NLO);
+                        if (TF) {   // tile r of the element rounded in place, its Phi_lo in slot sl
+                            if (!mbar_wait(smem_u32(lo_full + sl), (uint32_t)((ml / TC_NLO) & 1), abort_flag)) {
                                 ok = false;
                                 break;
                             }
                             tc_fence_after();
                         }
-                        const uint64_t da =
-                            desc_sw128(smem_u32(ringA + sa * E_BYTES + (TF ? 0 : r) * TC_A_BYTES));
+                        const uint64_t da = desc_sw128(smem_u32(ringA + sa * E_BYTES + r * TC_A_BYTES));
                         const uint32_t dt = tmem + (uint32_t)(r * p.acc_stride);
 #pragma unroll
                         for (int kk = 0; kk < KE / KM; ++kk) {
@@ -273,17 +281,17 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc(TcParams p) {
                             else mma_bf16(dt, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), p.idesc, acc);
                         }
                         if (TF) {
-                            const uint64_t dl = desc_sw128(smem_u32(ringL + sa * TC_A_BYTES));
+                            const uint64_t dl = desc_sw128(smem_u32(ringL + sl * TC_A_BYTES));
 #pragma unroll
                             for (int kk = 0; kk < KE / KM; ++kk)
                                 mma_tf32(dt, dl + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), p.idesc_lo, 1u);
-                        }
-                        if (TF || r == valid - 1) {   // the element is free once its MMAs are done
-                            mma_commit(smem_u32(a_empty + sa));
-                            ++ma;
+                            mma_commit(smem_u32(lo_empty + sl));   // the Phi_lo slot is free once these are done
+                            ++ml;
                         }
                     }
                     if (!ok) break;
+                    mma_commit(smem_u32(a_empty + sa));   // the element is free once its MMAs are done
+                    ++ma;
                     mma_commit(smem_u32(b_empty + sb));
                     ++mb;
                 }
@@ -303,8 +311,9 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc(TcParams p) {
         const int GR = p.G * TC_BM;
         const int NC = p.QS / 16;
         griddep_wait();
+        if (gemm_deferred(p)) u1 = u0;
         int nseg = 0;
-        long long ne = 0;   // A tiles converted
+        long long ne = 0, nlo = 0;   // A ring elements and Phi_lo slots walked (converter warps)
         long long u = u0;
         bool ok = true;
         while (u < u1 && ok) {
@@ -313,17 +322,25 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc(TcParams p) {
             const int valid = min(p.G, p.M_tiles - g * p.G);
             if (TF && ew < 4) {
                 for (long long uu = u; uu < seg_end && ok; ++uu) {
+                    const int sa = (int)(ne % NE);
+                    if (!mbar_wait(smem_u32(a_full + sa), (uint32_t)((ne / NE) & 1), abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    ++ne;
                     for (int r = 0; r < valid; ++r) {
-                        const int sa = (int)(ne % NA);
-                        if (!mbar_wait(smem_u32(a_full + sa), (uint32_t)((ne / NA) & 1), abort_flag)) {
+                        const int sl = (int)(nlo % TC_NLO);
+                        const long long use = nlo / TC_NLO;
+                        if (use > 0 &&
+                            !mbar_wait(smem_u32(lo_empty + sl), (uint32_t)((use - 1) & 1), abort_flag)) {
                             ok = false;
                             break;
                         }
-                        // this warp's quarter of the tile: 1024 floats, 8 float4 per lane;
-                        // x -> hi = tf32_rn(x) in place, lo = tf32_rn(x - hi) beside it
+                        // this warp's quarter of tile r: 1024 floats, 8 float4 per lane;
+                        // x -> hi = tf32_rn(x) in place, lo = tf32_rn(x - hi) into slot sl
                         constexpr int PW = 256;   // float4 per converter warp
-                        float4* src = reinterpret_cast<float4*>(ringA + sa * TC_A_BYTES) + ew * PW;
-                        float4* dst = reinterpret_cast<float4*>(ringL + sa * TC_A_BYTES) + ew * PW;
+                        float4* src = reinterpret_cast<float4*>(ringA + sa * E_BYTES + r * TC_A_BYTES) + ew * PW;
+                        float4* dst = reinterpret_cast<float4*>(ringL + sl * TC_A_BYTES) + ew * PW;
 #pragma unroll
                         for (int i = 0; i < PW / 32; ++i) {
                             const float4 x = src[lane + 32 * i];
@@ -334,8 +351,8 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc(TcParams p) {
                         }
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                         __syncwarp();
-                        if (lane == 0) mbar_arrive(smem_u32(lo_full + sa));
-                        ++ne;
+                        if (lane == 0) mbar_arrive(smem_u32(lo_full + sl));
+                        ++nlo;
                     }
                 }
                 if (!ok) break;
@@ -388,11 +405,11 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc(TcParams p) {
 // ---------------------------------------------------------------------------
 template <bool TF>
 __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc_packed(TcBatch p) {
-    constexpr int NA = TF ? TC_NA_TF : TC_NA;
+    constexpr int NA = TC_NA;
     constexpr int KE = TF ? TC_BK32 : TC_BK;
     constexpr int KM = TF ? 8 : 16;
-    const int EPT = TF ? 1 : p.G;
-    const int NE = TF ? NA : NA / p.G;
+    const int EPT = p.G;
+    const int NE = NA / p.G;
     const uint32_t E_BYTES = (uint32_t)EPT * TC_A_BYTES;
     griddep_launch();
     extern __shared__ uint8_t smem_raw[];
@@ -400,14 +417,15 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc_packed(TcBatch p)
     const uint32_t B_MAX = (uint32_t)p.QSmax * 128u;   // ring element (the largest fit's split tile)
     uint8_t* ringA = smem;
     uint8_t* ringL = smem + NA * TC_A_BYTES;
-    uint8_t* ringB = ringL + (TF ? NA * TC_A_BYTES : 0);
+    uint8_t* ringB = ringL + (TF ? TC_NLO * TC_A_BYTES : 0);
     uint64_t* bars = (uint64_t*)(ringB + TC_NB * B_MAX);
     uint64_t* a_full = bars;
     uint64_t* a_empty = bars + NA;
     uint64_t* lo_full = bars + 2 * NA;
-    uint64_t* b_full = bars + 3 * NA;
-    uint64_t* b_empty = bars + 3 * NA + TC_NB;
-    uint64_t* acc_full = bars + 3 * NA + 2 * TC_NB;
+    uint64_t* lo_empty = lo_full + TC_NLO;
+    uint64_t* b_full = lo_empty + TC_NLO;
+    uint64_t* b_empty = b_full + TC_NB;
+    uint64_t* acc_full = b_empty + TC_NB;
     uint64_t* acc_empty = acc_full + 1;
     uint64_t* drain = acc_full + 2;
     uint32_t* tmem_slot = (uint32_t*)(acc_full + 3);
@@ -418,7 +436,10 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc_packed(TcBatch p)
         for (int i = 0; i < NA; ++i) {
             mbar_init(smem_u32(a_full + i), 1);
             mbar_init(smem_u32(a_empty + i), 1);
+        }
+        for (int i = 0; i < TC_NLO; ++i) {
             mbar_init(smem_u32(lo_full + i), 4);
+            mbar_init(smem_u32(lo_empty + i), 1);
         }
         for (int i = 0; i < TC_NB; ++i) {
             mbar_init(smem_u32(b_full + i), 1);
@@ -469,29 +490,26 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc_packed(TcBatch p)
                               smem_u32(b_full + slot));
                     ++nb;
                     const long long u = (long long)sg.g * sl.K_tiles + k;
-                    // BF16: the unit's row tiles that hold rows (the image's
-                    // tiles past the last row are zero and never multiplied)
-                    const uint32_t a_bytes = TF ? E_BYTES : (uint32_t)valid * TC_A_BYTES;
-                    for (int r = 0; r < (TF ? valid : 1); ++r) {
-                        slot = (int)(na % NE);
-                        use = na / NE;
-                        if (use > 0 && !mbar_wait(smem_u32(a_empty + slot), (uint32_t)((use - 1) & 1), abort_flag)) {
-                            ok = false;
-                            break;
-                        }
-                        mbar_expect_tx(smem_u32(a_full + slot), a_bytes);
-                        bulk_load_hint(smem_u32(ringA + slot * E_BYTES), sl.A + ((size_t)u * p.G + r) * TC_A_BYTES,
-                                       a_bytes, smem_u32(a_full + slot), evict_first);
-                        ++na;
+                    // the unit's row tiles that hold rows (the image's tiles
+                    // past the last row are zero and never multiplied)
+                    const uint32_t a_bytes = (uint32_t)valid * TC_A_BYTES;
+                    slot = (int)(na % NE);
+                    use = na / NE;
+                    if (use > 0 && !mbar_wait(smem_u32(a_empty + slot), (uint32_t)((use - 1) & 1), abort_flag)) {
+                        ok = false;
+                        break;
                     }
-                    if (!ok) break;
+                    mbar_expect_tx(smem_u32(a_full + slot), a_bytes);
+                    bulk_load_hint(smem_u32(ringA + slot * E_BYTES), sl.A + (size_t)u * p.G * TC_A_BYTES, a_bytes,
+                                   smem_u32(a_full + slot), evict_first);
+                    ++na;
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            long long ma = 0, mb = 0;
+            long long ma = 0, mb = 0, ml = 0;   // ring positions consumed (A, B, Phi_lo)
             int nseg = 0;
             bool ok = true;
             for (int i = i0; i < i1 && ok; ++i) {
@@ -509,22 +527,22 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc_packed(TcBatch p)
                         break;
                     }
                     const uint64_t db = desc_sw128(smem_u32(ringB + sb * B_MAX));
-                    int sa = 0;
+                    const int sa = (int)(ma % NE);
+                    if (!mbar_wait(smem_u32(a_full + sa), (uint32_t)((ma / NE) & 1), abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
                     for (int r = 0; r < valid; ++r) {
-                        if (TF || r == 0) {
-                            sa = (int)(ma % NE);
-                            const uint32_t par = (uint32_t)((ma / NE) & 1);
-                            if (!mbar_wait(smem_u32(a_full + sa), par, abort_flag)) {
-                                ok = false;
-                                break;
-                            }
-                            if (TF && !mbar_wait(smem_u32(lo_full + sa), par, abort_flag)) {
+                        const int sl_lo = (int)(ml % TC_NLO);
+                        if (TF) {
+                            if (!mbar_wait(smem_u32(lo_full + sl_lo), (uint32_t)((ml / TC_NLO) & 1), abort_flag)) {
                                 ok = false;
                                 break;
                             }
                             tc_fence_after();
                         }
-                        const uint64_t da = desc_sw128(smem_u32(ringA + sa * E_BYTES + (TF ? 0 : r) * TC_A_BYTES));
+                        const uint64_t da = desc_sw128(smem_u32(ringA + sa * E_BYTES + r * TC_A_BYTES));
                         const uint32_t dt = tmem + (uint32_t)(r * p.acc_stride);
 #pragma unroll
                         for (int kk = 0; kk < KE / KM; ++kk) {
@@ -533,17 +551,17 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc_packed(TcBatch p)
                             else mma_bf16(dt, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc, acc);
                         }
                         if (TF) {
-                            const uint64_t dl = desc_sw128(smem_u32(ringL + sa * TC_A_BYTES));
+                            const uint64_t dl = desc_sw128(smem_u32(ringL + sl_lo * TC_A_BYTES));
 #pragma unroll
                             for (int kk = 0; kk < KE / KM; ++kk)
                                 mma_tf32(dt, dl + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc_lo, 1u);
-                        }
-                        if (TF || r == valid - 1) {
-                            mma_commit(smem_u32(a_empty + sa));
-                            ++ma;
+                            mma_commit(smem_u32(lo_empty + sl_lo));
+                            ++ml;
                         }
                     }
                     if (!ok) break;
+                    mma_commit(smem_u32(a_empty + sa));
+                    ++ma;
                     mma_commit(smem_u32(b_empty + sb));
                     ++mb;
                 }
@@ -560,7 +578,7 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc_packed(TcBatch p)
         const int ew = warp - 2;
         const int GR = p.G * TC_BM;
         int nseg = 0;
-        long long ne = 0;
+        long long ne = 0, nlo = 0;   // A ring elements and Phi_lo slots walked (converter warps)
         bool ok = true;
         for (int i = i0; i < i1 && ok; ++i) {
             const TcSeg sg = p.segs[i];
@@ -569,15 +587,23 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc_packed(TcBatch p)
             const int valid = min(p.G, sl.M_tiles - sg.g * p.G);
             if (TF && ew < 4) {
                 for (int k = sg.k0; k < sg.k1 && ok; ++k) {
+                    const int sa = (int)(ne % NE);
+                    if (!mbar_wait(smem_u32(a_full + sa), (uint32_t)((ne / NE) & 1), abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    ++ne;
                     for (int r = 0; r < valid; ++r) {
-                        const int sa = (int)(ne % NA);
-                        if (!mbar_wait(smem_u32(a_full + sa), (uint32_t)((ne / NA) & 1), abort_flag)) {
+                        const int sl_lo = (int)(nlo % TC_NLO);
+                        const long long use = nlo / TC_NLO;
+                        if (use > 0 &&
+                            !mbar_wait(smem_u32(lo_empty + sl_lo), (uint32_t)((use - 1) & 1), abort_flag)) {
                             ok = false;
                             break;
                         }
                         constexpr int PW = 256;   // float4 per converter warp
-                        float4* src = reinterpret_cast<float4*>(ringA + sa * TC_A_BYTES) + ew * PW;
-                        float4* dst = reinterpret_cast<float4*>(ringL + sa * TC_A_BYTES) + ew * PW;
+                        float4* src = reinterpret_cast<float4*>(ringA + sa * E_BYTES + r * TC_A_BYTES) + ew * PW;
+                        float4* dst = reinterpret_cast<float4*>(ringL + sl_lo * TC_A_BYTES) + ew * PW;
 #pragma unroll
                         for (int e = 0; e < PW / 32; ++e) {
                             const float4 x = src[lane + 32 * e];
@@ -588,8 +614,8 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc_packed(TcBatch p)
                         }
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                         __syncwarp();
-                        if (lane == 0) mbar_arrive(smem_u32(lo_full + sa));
-                        ++ne;
+                        if (lane == 0) mbar_arrive(smem_u32(lo_full + sl_lo));
+                        ++nlo;
                     }
                 }
                 if (!ok) break;
@@ -628,7 +654,7 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc_packed(TcBatch p)
 // ---------------------------------------------------------------------------
 // FP8 E4M3 dictionary.  The A image holds codes, 128 rows x 128 codes per
 // 16 KiB tile, tiles ordered (group of 2 row tiles, 128-wide k tile, row
-// tile); a unit's two tiles arrive as one 32 KiB bulk copy.  Four converter
+// tile); a unit's two tiles arrive as one 32 KiB bulk copy.  Eight converter
 // warps widen each tile to two BF16 sub-tiles (128 x 64, 128-byte swizzle) in
 // shared memory: the BF16 bit pattern (b & 0x80) << 8 | (b & 0x7F) << 4 is the
 // code's value times 2^-120 exactly (zero and subnormals included), so the
@@ -637,9 +663,14 @@ __global__ void __launch_bounds__(tc_threads(TF), 1) k_gemm_tc_packed(TcBatch p)
 // the T reduction applies s_i 2^56 and the U partials carry 2^-56.
 // Warp roles (448 threads): 0 producer, 1 TMEM + MMA, 2-5 epilogue,
 // 6-13 converters.  Accumulators are double-buffered (2 x 2 x 128 columns).
+// Rings: 3 landing units (32 KiB each), 4 BF16 sub-tiles (one unit), 2 B
+// tiles.  (2 landing units and 6 sub-tiles, which lets the converters work
+// half a unit further ahead of the MMAs, measured slower: 0.246 against
+// 0.237 ms per application at 8192 x 32768.)
 // ---------------------------------------------------------------------------
 constexpr int F8_THREADS = 448, F8_G = 2, F8_NL = 3, F8_NC = 4, F8_NB = 2, F8_CW = 8;   // F8_CW converter warps
 constexpr uint32_t F8_LAND = F8_G * TC_A_BYTES;     // one unit of codes
+static_assert(F8_NC % 2 == 0, "the converters fill the sub-tile ring in pairs");
 constexpr float F8_BSCALE = 18446744073709551616.0f;   // 2^64 on the split vector blocks
 constexpr float F8_RFAC = 72057594037927936.0f;        // 2^56 = 2^120 / 2^64 back on the products
 
@@ -704,7 +735,7 @@ __global__ void __launch_bounds__(F8_THREADS, 1) k_gemm8(TcParams p) {
     griddep_wait();   // B is the previous kernel's output; bounded waits start after it completed
 
     const long long u0 = (long long)blockIdx.x * p.W / gridDim.x;
-    const long long u1 = (long long)(blockIdx.x + 1) * p.W / gridDim.x;
+    const long long u1 = gemm_deferred(p) ? u0 : (long long)(blockIdx.x + 1) * p.W / gridDim.x;
     long long nl = 0, nb = 0;   // copies issued into the landing and B rings (producer thread)
 
     if (warp == 0) {
@@ -1100,6 +1131,7 @@ cudaError_t plan_gemm(GemmPlan& gp, int num_sms, long long M_rows, long long K_c
     p.idesc = make_idesc(TC_BM, QS, tf);
     p.idesc_lo = make_idesc(TC_BM, QS, tf);   // TF32: Phi_lo times [P_hi | P_lo]
     p.flags = flags;
+    p.defer = nullptr;
     gp.groups = (p.M_tiles + G - 1) / G;
     p.W = (long long)gp.groups * p.K_tiles;
     // at least ~16 units per CTA: small problems then leave SMs to other work
@@ -1159,9 +1191,8 @@ size_t gemm8_smem(int QS) {
     return 1024 + (size_t)F8_NL * F8_LAND + (size_t)F8_NC * TC_A_BYTES + (size_t)F8_NB * 2 * QS * 128 + 512;
 }
 
-size_t gemm_smem(bool tf, int QS) {
-    const int na = tf ? TC_NA_TF : TC_NA;
-    return 1024 + (size_t)na * TC_A_BYTES * (tf ? 2 : 1) + (size_t)TC_NB * QS * 128 + 512;
+size_t gemm_smem(bool tf, int QS) {   // k_gemm_tc, k_gemm_tc_packed
+    return 1024 + (size_t)TC_NA * TC_A_BYTES + (tf ? (size_t)TC_NLO * TC_A_BYTES : 0) + (size_t)TC_NB * QS * 128 + 512;
 }
 
 }  // namespace
@@ -1327,11 +1358,13 @@ bool tc_rotatable(cofem_ctx* c) {
     return c->kind == COFEM_OP_DENSE && t && !t->fused;
 }
 
-void launch_tc_first_product(Sink& s, cofem_ctx* c) {
+void launch_tc_first_product(Sink& s, cofem_ctx* c, bool defer_rr) {
     TcPlan* t = (TcPlan*)c->tc;
     void (*gemm)(TcParams) = t->f8 ? k_gemm8 : (t->tf ? k_gemm_tc<true> : k_gemm_tc<false>);
     const unsigned nthreads = t->f8 ? F8_THREADS : (unsigned)tc_threads(t->tf);
-    s.launch_pdl(gemm, dim3(t->g1.nCTA), dim3(nthreads), t->smem, t->g1.p);
+    TcParams p = t->g1.p;
+    p.defer = defer_rr ? c->ctl : nullptr;
+    s.launch_pdl(gemm, dim3(t->g1.nCTA), dim3(nthreads), t->smem, p);
 }
 
 void launch_tc_rest(Sink& s, cofem_ctx* c, int Q, int mode) {

@@ -342,7 +342,10 @@ __device__ __forceinline__ void cg_direction_body(DevCtl* ctl, const float* __re
                                                   const float* __restrict__ alpha, const float* __restrict__ minv,
                                                   float* __restrict__ P, long long Dp, int nch, double* part,
                                                   cudaGraphConditionalHandle h_cg, const SplitOut& so, int q,
-                                                  int ch) {
+                                                  int ch, int defer_rr) {
+    // deferred (a fit graph's CG loop): at a replacement step the loop ends
+    // here and the direction runs after the replacement, outside the loop
+    if (defer_rr && rr_step(ctl)) return;
     __shared__ double sh[NT / 32];
     __shared__ double s_rr[COFEM_QMAX];
     __shared__ double s_sum[2];
@@ -448,10 +451,10 @@ __global__ __launch_bounds__(NT) void k_cg_direction(DevCtl* ctl, const float* _
                                                      const float* __restrict__ alpha,
                                                      const float* __restrict__ minv, float* __restrict__ P,
                                                      long long Dp, int nch, double* part,
-                                                     cudaGraphConditionalHandle h_cg, SplitOut so) {
+                                                     cudaGraphConditionalHandle h_cg, SplitOut so, int defer_rr) {
     griddep_launch();
     griddep_wait();   // R and the partials come from the previous kernel
-    cg_direction_body(ctl, R, alpha, minv, P, Dp, nch, part, h_cg, so, blockIdx.y, blockIdx.x);
+    cg_direction_body(ctl, R, alpha, minv, P, Dp, nch, part, h_cg, so, blockIdx.y, blockIdx.x, defer_rr);
 }
 
 // ---------------------------------------------------------------------------
@@ -560,7 +563,7 @@ __global__ __launch_bounds__(NT) void k_cg_direction_packed(const VSlot* __restr
     DevCtl* ctl = f.ctl;
     if (ctl->phase != PH_CG) return;
     const SplitOut so = f.so;
-    cg_direction_body(ctl, f.R, f.alpha, f.minv, f.P, f.Dp, f.nch, f.part, 0, so, m.y, m.z);
+    cg_direction_body(ctl, f.R, f.alpha, f.minv, f.P, f.Dp, f.nch, f.part, 0, so, m.y, m.z, 0);
 }
 
 // The M-step of the fits whose CG loop ended in this step (the direction
@@ -684,9 +687,9 @@ void launch_cg_update(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h
                  c->Xlo, c->Dp, c->nch, c->part, h_rr, h_cg);
 }
 
-void launch_cg_direction(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg) {
+void launch_cg_direction(Sink& s, cofem_ctx* c, int Q, cudaGraphConditionalHandle h_cg, bool defer_rr) {
     s.launch_pdl(k_cg_direction, dim3(c->nch, Q), dim3(NT), 0, c->ctl, c->R, c->alpha, c->minv, c->P, c->Dp, c->nch,
-                 c->part, h_cg, tc_direction_split(c));
+                 c->part, h_cg, tc_direction_split(c), defer_rr ? 1 : 0);
 }
 
 void launch_mstep(Sink& s, cofem_ctx* c, int /*Q*/, cudaGraphConditionalHandle h_em) {

@@ -18,12 +18,24 @@ def test_launch_count_per_fit():
     # 3 per fit (b, finiteness check of y, set-up); per EM iteration init and
     # M-step; per CG step the operator's kernels (3) and update + direction (2)
     assert bench._launches_per_fit([10, 20], 3, 2) == 3 + (2 + 5 * 10) + (2 + 5 * 20)
-    # each residual replacement adds the accurate residual (4 kernels); each
-    # true-residual check the accurate residual, the check and the loop gate
-    assert bench._launches_per_fit([10], 3, 2, n_rr=3, n_check=2, op_rr=4) == 3 + 2 + 5 * 10 + 3 * 4 + 2 * 6
+    # each residual replacement adds the accurate residual (4 kernels) and, in
+    # the graph, the direction again and two gates per run of CG steps (one
+    # run per replacement and per round); each true-residual check the
+    # accurate residual, the check and the loop gate
+    assert (bench._launches_per_fit([10], 3, 2, n_rr=3, n_check=2, op_rr=4)
+            == 3 + 2 + 5 * 10 + 3 * 4 + 2 * 6 + 3 * 1 + 2 * (3 + 2))
     # driven from the host loop there is no gate kernel
     assert bench._launches_per_fit([10], 3, 2, n_rr=0, n_check=2, op_rr=4, graph=False) == 3 + 2 + 5 * 10 + 2 * 5
     assert bench._launches_per_fit([], 3, 2) == 3
+    # the graph's rotated loop: a first product before each entry into the CG
+    # loop (per EM iteration, or per verification round)
+    assert bench._launches_per_fit([10, 20], 3, 2, rotated=True) == 3 + (2 + 5 * 10) + (2 + 5 * 20) + 2
+    # with replacement: per replacement the direction and the first product
+    # again, and two gates per run of CG steps (replacements + rounds)
+    assert (bench._launches_per_fit([10], 3, 2, n_rr=3, n_check=2, op_rr=4, rotated=True)
+            == 3 + 2 + 5 * 10 + 3 * 4 + 2 * 6 + 2 + 3 * 2 + 2 * (3 + 2))
+    assert (bench._launches_per_fit([10], 3, 2, n_rr=3, n_check=2, op_rr=4, graph=False, rotated=True)
+            == 3 + 2 + 5 * 10 + 3 * 4 + 2 * 5)
 
 
 def test_launch_count_matches_the_launch_list():

@@ -684,3 +684,28 @@ def test_bounded_device_waits_run_out_and_the_context_stays_usable(cf):
     r = oracle_fit(p, 16, 10, 1e-5, 400, phi=bf16_round(p.phi))
     assert_fit_close(g, r)
     assert not g["flags"] & cf.COFEM_FLAG_DEVICE_TIMEOUT
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_fit_replacement_on_the_last_cg_step_graph_matches_host(cf, precision):
+    """The fit graph's CG loop ends at every replacement step and goes round
+    again after the replacement; with the CG budget a multiple of the
+    replacement period (and a tolerance no column meets) the last step is a
+    replacement step: the graph gives the host loop's bits, flags and counts."""
+    prec = {"bf16": cf.COFEM_BF16, "fp8": cf.COFEM_FP8_E4M3}[precision]
+    p = dense_gaussian(300, 1200, 12, 20.0, seed=21)
+    out = []
+    for use_graph in (1, 0):
+        with cf.CoFEM(p.N, p.D, cf.COFEM_OP_DENSE, p.phi, 0, precision=prec, rr_period=7,
+                      use_graph=use_graph) as m:
+            K, T = 8, 3
+            mu, s, alpha = (np.zeros(p.D, np.float32) for _ in range(3))
+            it = np.zeros(T, np.int32)
+            flags = cf.cofem_fit(m.h, p.y, p.beta, None, K, T, 1e-12, 14, mu, s, alpha, it)
+            out.append((mu, s, alpha, it, flags, cf.cofem_fit_stats(m.h)))
+    (a, b) = out
+    for x, y in zip(a[:4], b[:4]):
+        np.testing.assert_array_equal(x, y)
+    assert a[4] == b[4] and a[4] & cf.COFEM_FLAG_CG_NOT_CONVERGED
+    assert a[5] == b[5] and a[5][0] >= 2 * T
+    assert np.all(a[3] >= 14)
