@@ -44,9 +44,10 @@ def _dist():
 # the current kernels, keyed by (workload, operator form).  An entry must be
 # removed when its kernels change.
 _MEASURED_TRAFFIC = {
-    # two k_gemm_tc launches (547.9 + 543.9 MB) and k_tc_reduce_T (1.8 MB,
-    # warm cache)
-    ("dense_n8192_d32768_k32_bf16", 1): 1093.6e6,
+    # two k_gemm_tc launches captured at 4096 x 16384 (140.9 + 138.1 MB),
+    # scaled by the units processed (x 4), and k_tc_reduce_T (1.8 MB, warm
+    # cache)
+    ("dense_n8192_d32768_k32_bf16", 1): 1117.9e6,
 }
 
 # --dense-path -> cofem_opts.dense_path, --toeplitz-path -> cofem_opts.toeplitz_path
