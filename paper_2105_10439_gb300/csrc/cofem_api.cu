@@ -270,8 +270,8 @@ cofem_status build_graph(cofem_ctx* c, int Q, bool pdl) {
     // kernels of every step are those of the host-driven loop, in the same
     // order.  (Measured at 8192 x 32768, K = 32, 10 EM iterations: 1.2 %
     // less fit time than an IF node between the update and the direction at
-    // every step; a replacement costs ~0.13 ms in the graph beyond the
-    // 0.65 ms of its kernels timed alone.)
+    // every step.  Timeline stamps around a replacement: the loop exit, the
+    // IF node, the gates and the re-entry take about 25 us in all.)
     const bool with_rr = c->opts.rr_period > 0;   // implies verify
     cudaGraphConditionalHandle h_run = 0;
     if (verify) {
