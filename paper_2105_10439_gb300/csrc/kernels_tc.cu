@@ -26,9 +26,11 @@
 // at most a few group boundaries; each (CTA, group) segment writes a partial
 // sum, and a small kernel adds the partials of each group in a fixed order.
 //
-// Warp roles (192 threads): warp 0 lane 0 issues TMA loads, warp 1 allocates
-// TMEM and lane 0 issues the MMAs, warps 2-5 drain TMEM (each its 32-lane
-// sub-partition).  Every mbarrier wait is bounded: on timeout the kernel sets
+// Warp roles: warp 0 lane 0 issues the bulk copies, warp 1 allocates TMEM and
+// lane 0 issues the MMAs, and the epilogue warps (16 in the BF16 form, 8 in the
+// TF32 form; warp id mod 4 selects the 32-lane TMEM sub-partition) drain the
+// accumulators, four of them first splitting the TF32 tiles.  (The FP8 kernel
+// further down has its own roles.)  Every mbarrier wait is bounded: on timeout the kernel sets
 // COFEM_FLAG_DEVICE_TIMEOUT, waits (bounded) for its in-flight copies and MMAs,
 // frees TMEM and returns.
 #include <algorithm>
